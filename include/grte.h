@@ -1,0 +1,133 @@
+/*
+ * grte.h - C ABI of the GB300 (sm_103a) implementation of the asymptotic-preserving
+ * prediction / correction / projection scheme for the nonlinear gray radiative
+ * transfer equation (Tang, Wang, Zhang, arXiv:1811.05579).
+ *
+ * Scope: the 1D even/odd staggered scheme of Sec. 4 (Algorithm 2) for a
+ * temperature-independent opacity sigma(x), and its sigma_0(x)/T^3 form of Sec. 5,
+ * for any number of independent slab instances advanced together.
+ *
+ * Conventions (every entry point):
+ *  - Plain C types only.  Pointers marked "host" are read or written on the host and
+ *    copied; the library keeps no reference to them after the call returns.
+ *  - Pointers marked "device" are CUDA device addresses owned by the caller.
+ *  - Every call returns a grte_status and never aborts the process.  A failed call
+ *    leaves a message readable with grte_last_error().  Size arguments are checked
+ *    against the exact size the call needs (GRTE_EINVAL otherwise).
+ *  - Steps are launched asynchronously on the handle's stream.  Problems found on
+ *    the device (non-converged Krylov or Newton solve, negative right-hand side of
+ *    the temperature equation, NaN) are recorded per instance and reported, sticky,
+ *    by grte_sync() and the grte_get_* calls, which synchronise the stream.
+ *  - Layout of the angular unknowns in device memory: per instance, angle-major
+ *    lines, E[k][j] (k = 0..M-1 positive angles, j = 0..nx-1 cells) and
+ *    O[k][i] (i = 0..nx nodes).  Host copies returned by grte_get_E/O use the
+ *    cell-major order [j][k] / [i][k].
+ */
+#ifndef GRTE_H
+#define GRTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grte_ctx* grte_t;
+
+typedef enum {
+  GRTE_OK = 0,
+  GRTE_EINVAL = 1,     /* bad argument (size, range, NULL, state)                    */
+  GRTE_ENOMEM = 2,     /* device or host allocation failed                           */
+  GRTE_ECUDA = 3,      /* a CUDA runtime call failed                                 */
+  GRTE_ENONCONV = 4,   /* a Krylov or Newton solve did not reach its tolerance       */
+  GRTE_ENEGATIVE = 5,  /* right-hand side R <= 0 in the temperature equation: T = 0  */
+  GRTE_ENAN = 6,       /* NaN or Inf met in the state                                */
+  GRTE_ETIMEOUT = 7,   /* a device-side wait gave up                                 */
+  GRTE_ESTATE = 8      /* handle used before its state was set                       */
+} grte_status;
+
+enum { GRTE_SIGMA_CONST = 0, /* sigma(x), independent of T (Sec. 4)            */
+       GRTE_SIGMA_T3 = 1     /* sigma_0(x) / T^3 (Sec. 5, Eq. marshak00)        */ };
+enum { GRTE_BC_INFLOW = 0,   /* I(0,v) = b_L(v), I(L,-v) = b_R(-v), v > 0 (Eq. BC1d, Eq. bc-pre) */
+       GRTE_BC_REFLECT = 1   /* I(wall, v) = I(wall, -v): odd part zero at the walls             */ };
+enum { GRTE_FP64 = 0,        /* every per-element operation in binary64                         */
+       GRTE_MIXED = 1        /* angular bulk in binary32; per-cell Newton and sums in binary64   */ };
+
+/* One 1D slab instance on [x0, x1] with nx uniform cells (Sec. 4, Eq. E000/O000). */
+typedef struct {
+  int64_t nx;            /* cells, >= 2                                                      */
+  int n_angle;           /* M, positive angles (the quadrature has 2M directions +-v_k)       */
+  const double* v;       /* host, M angles in (0,1], or NULL: Gauss-Legendre with 2M nodes   */
+  const double* w;       /* host, M weights summing to 1 (= int_0^1 dv), or NULL with v NULL */
+  const double* sigma;   /* host, nx values of sigma(x) (CONST) or sigma_0(x) (T3), >= 0     */
+  int sigma_kind;        /* GRTE_SIGMA_CONST or GRTE_SIGMA_T3                                */
+  int bc;                /* GRTE_BC_INFLOW or GRTE_BC_REFLECT                                */
+  const double* bL;      /* host, M values I(x0, +v_k) (INFLOW only; NULL = 0)               */
+  const double* bR;      /* host, M values I(x1, -v_k) (INFLOW only; NULL = 0)               */
+  double x0, x1;         /* slab, x1 > x0                                                    */
+  double dt;             /* time step > 0                                                    */
+  double a, c, Cv;       /* radiation constant, light speed, heat capacity (> 0)            */
+  double eps;            /* scaled mean free path epsilon > 0                                */
+} grte_instance1d;
+
+typedef struct {
+  int precision;         /* GRTE_FP64 (default) or GRTE_MIXED                                */
+  double krylov_rtol;    /* prediction solve: relative preconditioned residual (1e-14)       */
+  int krylov_restart;    /* GMRES restart length (10)                                        */
+  int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (6)            */
+  int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */
+  void* stream;          /* cudaStream_t to run on; NULL: the library makes its own          */
+} grte_options;
+
+/* Statistics of the last grte_step call (summed over its steps and instances). */
+typedef struct {
+  int64_t steps;             /* steps taken by the handle so far                   */
+  int64_t krylov_iters;      /* GMRES iterations in the last grte_step call        */
+  int64_t krylov_cycles;     /* GMRES restart cycles in the last grte_step call    */
+  int64_t newton_iters_max;  /* largest per-cell Newton count in the last step     */
+  double newton_iters_mean;  /* mean per-cell Newton count in the last step        */
+  int64_t status_flags;      /* OR over instances of (1 << grte_status) seen       */
+} grte_stats_t;
+
+/* Fill *opt with the defaults. */
+void grte_default_options(grte_options* opt);
+
+/* Create a handle for n_inst independent 1D instances (Sec. 4 / Sec. 5).  All
+ * inputs are copied.  opt may be NULL (defaults).  The state is unset until
+ * grte_set_state().  Errors: EINVAL (bad sizes/values), ENOMEM, ECUDA. */
+grte_status grte_create_1d(int n_inst, const grte_instance1d* inst, const grte_options* opt,
+                           grte_t* out);
+
+/* Set the state of instance `inst` from host arrays: T (nx), and either
+ * E (nx*M, [j][k]) and O ((nx+1)*M, [i][k]), or E = O = NULL for the equilibrium
+ * I = a c T^4 (E = a c T^4, O = 0).  U is set to T^4 (Algorithm 2 input). */
+grte_status grte_set_state(grte_t h, int inst, const double* T, const double* E, const double* O);
+
+/* Advance every instance by nsteps steps of Algorithm 2 (asynchronous). */
+grte_status grte_step(grte_t h, int64_t nsteps);
+
+/* Wait for the stream; return the first device-side status (sticky). */
+grte_status grte_sync(grte_t h);
+
+/* Copy results of instance `inst` to host arrays (synchronises).  len = element count. */
+grte_status grte_get_T(grte_t h, int inst, double* T, size_t len);           /* nx              */
+grte_status grte_get_rho(grte_t h, int inst, double* rho, size_t len);       /* nx, rho = <I> = sum_k w_k E_k */
+grte_status grte_get_E(grte_t h, int inst, double* E, size_t len);           /* nx*M,  [j][k]   */
+grte_status grte_get_O(grte_t h, int inst, double* O, size_t len);           /* (nx+1)*M, [i][k] */
+/* Cell-centre intensities I(+v_k) = E + eps (O_j + O_{j+1})/2 and I(-v_k) = E - eps(...), [j][k]. */
+grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t len);
+/* Intermediate per-cell results of the last step: which = 0 U*, 1 F* =
+ * sum_k w_k v_k (O*_{j+1,k} - O*_{j,k}), 2 rho*, 3 Newton iterations (as double). */
+grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t len);
+/* Quadrature actually used by instance `inst` (M values each). */
+grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len);
+
+grte_status grte_stats(grte_t h, grte_stats_t* st);
+const char* grte_last_error(grte_t h);
+void grte_destroy(grte_t h);   /* NULL is a no-op */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1030 @@
+// GB300 (sm_103a) implementation of one step of the 1D AP scheme for the gray
+// radiative transfer equation (Tang, Wang, Zhang, arXiv:1811.05579): Algorithm 2 of
+// Sec. 4 (sigma(x)) and its sigma_0/T^3 form of Sec. 5, for many independent
+// instances at once.  The C ABI is declared in include/grte.h.
+//
+// Formulation (exact rewrite of the paper's equations, see the per-kernel comments):
+// per angle line (instance, k) the even part is split as E = rho + e with
+// rho = sum_k w_k E_k; O is eliminated with the node equation and the wall rows, U*
+// with the U equation.  The prediction (Eq. dis-pre / Eq. dis-pre-marshak) becomes
+//   e-equation  (A + G_k) e_k = h_k - alpha rho - G_k rho       (tridiagonal per line)
+//   conservation  alpha rho + sum_k w_k [G_k(rho + e_k) + phi_k] = kappa rho^n/(c dt) + s a c U^n
+// and is solved for rho by GMRES whose matrix-vector product is M independent
+// tridiagonal line solves (factorised once per step and reused), preconditioned by
+// the same construction with a single effective angle (sum_k w_k G_k), which is one
+// more tridiagonal solve per instance.  The temperature equation (Eq. Tnp1) is a
+// per-cell quartic solved by monotone Newton; correction substep 2 (Eq. dis-cor) is
+// one tridiagonal solve per line in E_J with the same operator family; projection
+// (Eq. dis-proj) is fused into that kernel's epilogue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grte.h"
+#include "tridiag.cuh"
+
+namespace grte {
+
+constexpr int kMaxRestart = 16;
+
+struct Inst {
+  int N, M, kind, bc;
+  double eps, dt, dx, a, c, Cv;
+  double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
+  int64_t cell_off;        // per-cell arrays
+  int64_t elem_off;        // E-like arrays, line k at elem_off + k*N
+  int64_t nelem_off;       // O-like arrays, line k at nelem_off + k*(N+1)
+  int64_t red_off;         // reduced-system storage of the preconditioner
+  int ang_off;             // v, w, bL, bR
+  int line_off;            // first line of this instance
+};
+
+struct Line {
+  int inst, k;
+  int64_t red_off;         // reduced-system storage of this line
+};
+
+// Per-cell coefficient arrays (length = total cells) for one operator family.
+struct CellCoef {
+  double *kc, *s, *alpha, *A, *gam, *gl, *gu, *gb, *dl;  // dl_j = d at the left node of cell j
+};
+
+struct Dev {
+  Inst* inst;
+  Line* lines;
+  double *v, *w, *bL, *bR;
+  // state
+  double *E, *O, *T, *U, *sig;
+  // per-cell
+  double *rho_n, *rho_s, *Fs, *Us, *newton_its;
+  CellCoef cf;
+  // per-element work
+  double *xb, *S, *F, *Rd, *onode;
+  // preconditioner factors
+  double *pF, *pRd;
+  // GMRES
+  double *gx, *gV, *gz, *gH, *gg, *gcs, *gsn, *gbeta, *gxn;
+  int *gactive, *gk, *gdone, *gits, *gcycles;
+  int* status;
+  int m;  // restart length
+  double rtol;
+  int newton_maxit;
+};
+
+__device__ __forceinline__ void flag(int* status, int inst, int code) { atomicOr(status + inst, 1 << code); }
+
+// ----------------------------------------------------------------------------- cells
+// Per-cell coefficients at temperature Tc (T^n for the prediction, T^{n+1} for
+// correction substep 2).  kappa/theta as in Eq. dis-pre (sigma(x): kappa = 1,
+// theta = T^3) or Eq. dis-pre-marshak (sigma_0/T^3: kappa = T^3 with node means,
+// theta = 1).  d_i = kappa_i / (kappa_i eps^2/(c dt) + sig_i) with sig_i the
+// harmonic mean of the two cells; gl/gu/gb are the tridiagonal streaming operator
+// G (per unit v^2 and v) of kappa v (O_{j+1} - O_j)/dx after eliminating O.
+__global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start,
+                            int64_t ncell, int use_new_T) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  // locate instance by binary search over cell offsets
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
+  }
+  const Inst I = D.inst[lo];
+  const int64_t j = gid - I.cell_off;
+  const int N = I.N;
+  const double* T = use_new_T ? D.T : D.T;  // T holds T^n or T^{n+1} depending on the caller
+  auto kap = [&](int64_t jj) -> double {
+    if (I.kind == GRTE_SIGMA_CONST) return 1.0;
+    double t = T[I.cell_off + jj];
+    return t * t * t;
+  };
+  auto sig = [&](int64_t jj) -> double { return D.sig[I.cell_off + jj]; };
+  const double eps2 = I.eps * I.eps;
+  const double cdt = I.c * I.dt;
+  auto dnode = [&](int64_t i) -> double {  // interior node i (1..N-1)
+    double kn = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : 0.5 * (kap(i - 1) + kap(i));
+    double sl = sig(i - 1), sr = sig(i);
+    double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
+    return kn / (kn * eps2 / cdt + sn);
+  };
+  const double kc = kap(j);
+  const double sj = sig(j);
+  const double Tj = T[gid];
+  const double theta = (I.kind == GRTE_SIGMA_CONST) ? Tj * Tj * Tj : 1.0;
+  const double s = sj * I.Cv / (I.Cv * eps2 + 4.0 * sj * theta * I.dt * I.a * I.c);
+  const double dx2 = I.dx * I.dx;
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  double dl = (j >= 1) ? dnode(j) : 0.0;
+  double dr = (j <= N - 2) ? dnode(j + 1) : 0.0;
+  double mL = (inflow && j == N - 1) ? 2.0 : 1.0;
+  double mR = (inflow && j == 0) ? 2.0 : 1.0;
+  D.cf.kc[gid] = kc;
+  D.cf.s[gid] = s;
+  D.cf.alpha[gid] = kc / cdt + s;
+  D.cf.A[gid] = kc / cdt + sj / eps2;
+  D.cf.gam[gid] = 4.0 * sj * theta * I.dt / (eps2 * I.Cv);
+  D.cf.gl[gid] = kc * mL * dl / dx2;
+  D.cf.gu[gid] = kc * mR * dr / dx2;
+  D.cf.gb[gid] = (inflow && (j == 0 || j == N - 1)) ? 2.0 * kc / (I.eps * I.dx) : 0.0;
+  D.cf.dl[gid] = dl;
+}
+
+// rho^n = sum_k w_k E^n_k (fixed angle order).
+__global__ void k_rho(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
+                      double* __restrict__ out, const double* __restrict__ Esrc) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
+  }
+  const Inst I = D.inst[lo];
+  const int64_t j = gid - I.cell_off;
+  double acc = 0.0;
+  for (int k = 0; k < I.M; ++k) acc += D.w[I.ang_off + k] * Esrc[I.elem_off + (int64_t)k * I.N + j];
+  out[gid] = acc;
+}
+
+// ----------------------------------------------------------------------------- lines
+struct LineCoef {  // A + v^2 Gint + v Gbdry of one line
+  const double *A, *gl, *gu, *gb;
+  double v, v2;
+  int64_t N;
+  __device__ double a(int64_t j) const { return j > 0 ? -v2 * gl[j] : 0.0; }
+  __device__ double c(int64_t j) const { return j < N - 1 ? -v2 * gu[j] : 0.0; }
+  __device__ double b(int64_t j) const { return A[j] + v2 * (gl[j] + gu[j]) + v * gb[j]; }
+};
+
+enum { PRED_FULL_FACTOR = 0, PRED_FULL = 1, PRED_HOM = 2 };
+
+// One prediction pass over a line (instance, k): build the e-equation right-hand
+// side for the per-instance vector x (rho or a Krylov direction), solve, and write
+// w_k v_k (O_{j+1,k} - O_{j,k}) of E = x + e into S (the angular sum over k is
+// taken by the instance kernel).  FULL passes carry the data h_k and phi_k (E^n,
+// O^n, inflow); HOM passes apply the linear part only.
+template <int MODE>
+__global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* __restrict__ xvec) {
+  __shared__ TriSmem<double> sm;
+  const Line L = D.lines[blockIdx.x];
+  const Inst I = D.inst[L.inst];
+  if (MODE == PRED_HOM && !D.gactive[L.inst]) return;
+  const int64_t N = I.N;
+  const int k = L.k;
+  const double v = D.v[I.ang_off + k], w = D.w[I.ang_off + k];
+  const double eps = I.eps, eps2 = eps * eps, cdt = I.c * I.dt, dx = I.dx;
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  const double bL = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bL[I.ang_off + k];
+  const double bR = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bR[I.ang_off + k];
+  const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
+  const double* x = xvec + co;
+  double* xb = D.xb + eo;
+  const double *kc = D.cf.kc + co, *s = D.cf.s + co, *alpha = D.cf.alpha + co, *gl = D.cf.gl + co,
+               *gu = D.cf.gu + co, *gb = D.cf.gb + co, *dl = D.cf.dl + co;
+  const double* En = D.E + eo;
+  const double* On = D.O + oo;
+  const double* Un = D.U + co;
+  const double v2 = v * v;
+  const double ac = I.a * I.c;
+  // o_i = d_i eps^2 O^n_i/(c dt) at interior nodes (d at node j is dl[j])
+  auto onode = [&](int64_t i) -> double {
+    if (MODE == PRED_HOM) return 0.0;
+    if (i <= 0 || i >= N) return 0.0;
+    return dl[i] * eps2 * On[i] / cdt;
+  };
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double xj = x[j];
+    const double xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
+    const double Gx = v2 * (gl[j] * (xj - xl) + gu[j] * (xj - xr)) + v * gb[j] * xj;
+    double r = -alpha[j] * xj - Gx;
+    if (MODE != PRED_HOM) {
+      // data part phi of kappa v (O_{j+1} - O_j)/dx (Eq. dis-pre1 node values, Eq. bc-pre walls)
+      double Dj = onode(j + 1) - onode(j);
+      if (inflow && j == 0) Dj = 2.0 * onode(1) - 2.0 / eps * bL;
+      if (inflow && j == N - 1) Dj = -2.0 / eps * bR - 2.0 * onode(N - 1);
+      const double h = kc[j] * En[j] / cdt + s[j] * ac * Un[j] - kc[j] * v * Dj / dx;
+      r += h;
+    }
+    xb[j] = r;
+  }
+  __syncthreads();
+  LineCoef cfl{D.cf.A + co, gl, gu, gb, v, v2, N};
+  if (MODE == PRED_FULL_FACTOR)
+    tri_solve<true>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
+  else
+    tri_solve<false>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
+  // flux contribution of E = x + e:
+  //   O_i = o_i - d_i v (E_i - E_{i-1})/dx (interior), walls from Eq. bc-pre
+  double* Sk = D.S + eo;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    auto Oint = [&](int64_t i) { return onode(i) - dl[i] * v * ((x[i] - x[i - 1]) + (xb[i] - xb[i - 1])) / dx; };
+    double OR, OLft;
+    if (j + 1 <= N - 1) OR = Oint(j + 1);
+    else OR = inflow ? 2.0 / eps * ((x[N - 1] - bR) + xb[N - 1]) - Oint(N - 1) : 0.0;
+    if (j >= 1) OLft = Oint(j);
+    else OLft = inflow ? 2.0 / eps * ((bL - x[0]) - xb[0]) - Oint(1) : 0.0;
+    Sk[j] = w * v * (OR - OLft);
+  }
+}
+
+// ----------------------------------------------------------------------------- instance (GMRES)
+struct PrecCoef {  // A + (A/alpha) (wv2 Gint + wv Gbdry)
+  const double *A, *alpha, *gl, *gu, *gb;
+  double wv, wv2;
+  int64_t N;
+  __device__ double f(int64_t j) const { return A[j] / alpha[j]; }
+  __device__ double a(int64_t j) const { return j > 0 ? -f(j) * wv2 * gl[j] : 0.0; }
+  __device__ double c(int64_t j) const { return j < N - 1 ? -f(j) * wv2 * gu[j] : 0.0; }
+  __device__ double b(int64_t j) const { return A[j] + f(j) * (wv2 * (gl[j] + gu[j]) + wv * gb[j]); }
+};
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];   // same order in every thread
+  return t;
+}
+
+// z = P^{-1} r, P the single-effective-angle Schur operator:
+//   u = (A + (1 + beta/alpha) Gbar)^{-1} (beta/alpha) r,  z = (r - Gbar u)/alpha,
+//   Gbar = sum_k w_k G_k, beta = A - alpha.
+template <bool FACTOR>
+__device__ void prec_apply(const Dev& D, const Inst& I, const double* r, double* z, double* work,
+                           TriSmem<double>& sm) {
+  const int64_t N = I.N, co = I.cell_off;
+  const double *A = D.cf.A + co, *alpha = D.cf.alpha + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co,
+               *gb = D.cf.gb + co;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) work[j] = (A[j] - alpha[j]) / alpha[j] * r[j];
+  __syncthreads();
+  PrecCoef pc{A, alpha, gl, gu, gb, I.wv, I.wv2, N};
+  tri_solve<FACTOR>(pc, N, work, D.pF + 4 * co, D.pRd + I.red_off, sm);
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double uj = work[j], ul = j > 0 ? work[j - 1] : 0.0, ur = j < N - 1 ? work[j + 1] : 0.0;
+    const double Gu = I.wv2 * (gl[j] * (uj - ul) + gu[j] * (uj - ur)) + I.wv * gb[j] * uj;
+    z[j] = (r[j] - Gu) / alpha[j];
+  }
+  __syncthreads();
+}
+
+// Angular sum of a pass: flux_j = kappa_j/dx sum_k S[k][j].
+__device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t j) {
+  double acc = 0.0;
+  for (int k = 0; k < I.M; ++k) acc += D.S[I.elem_off + (int64_t)k * I.N + j];
+  return acc;
+}
+
+enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
+
+// GMRES bookkeeping for one instance per CTA (restart length m).  Vectors live in
+// global memory: x (current iterate), V[0..m] (Krylov basis), z (scratch).
+template <int MODE>
+__global__ void __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
+  __shared__ TriSmem<double> sm;
+  __shared__ double red[32];
+  __shared__ double hcol[kMaxRestart + 2];
+  const int ii = blockIdx.x;
+  const Inst I = D.inst[ii];
+  const int64_t N = I.N, co = I.cell_off;
+  const int m = D.m;
+  double* x = D.gx + co;
+  double* z = D.gz + co;
+  double* work = D.xb + I.elem_off;          // the line buffers are free between passes
+  double* V = D.gV;                          // V_i at V + i*ncell_total ... stride given below
+  double* H = D.gH + (int64_t)ii * (kMaxRestart + 1) * kMaxRestart;
+  double* g = D.gg + (int64_t)ii * (kMaxRestart + 1);
+  double* cs = D.gcs + (int64_t)ii * kMaxRestart;
+  double* sn = D.gsn + (int64_t)ii * kMaxRestart;
+  const int64_t ncell_tot = D.gz - D.gx;     // gz = gx + ncell_total (allocation layout)
+  auto Vi = [&](int i) { return V + (int64_t)i * ncell_tot + co; };
+  const double *kc = D.cf.kc + co, *alpha = D.cf.alpha + co, *s = D.cf.s + co;
+  const double cdt = I.c * I.dt, ac = I.a * I.c;
+
+  if (MODE == G_RESTART_FIRST || MODE == G_RESTART) {
+    if (MODE == G_RESTART && D.gdone[ii]) return;
+    // r = -R(x) from the FULL pass that just ran at x
+    double* r = z;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      const double Rj = alpha[j] * x[j] - kc[j] * D.rho_n[co + j] / cdt - s[j] * ac * D.U[co + j] +
+                        kc[j] * flux_sum(D, I, j) / I.dx;
+      r[j] = -Rj;
+      D.Fs[co + j] = flux_sum(D, I, j);     // F* of the current iterate (final at convergence)
+    }
+    __syncthreads();
+    double* v0 = Vi(0);
+    if (MODE == G_RESTART_FIRST) prec_apply<true>(D, I, r, v0, work, sm);
+    else prec_apply<false>(D, I, r, v0, work, sm);
+    double nrm = 0.0, xn = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      nrm += v0[j] * v0[j];
+      xn += x[j] * x[j];
+    }
+    nrm = sqrt(block_sum(nrm, red));
+    xn = sqrt(block_sum(xn, red));
+    const bool conv = !(nrm > D.rtol * xn);   // also true for nrm == 0
+    if (threadIdx.x == 0) {
+      if (MODE == G_RESTART) D.gcycles[ii] += 1;
+      D.gbeta[ii] = nrm;
+      D.gxn[ii] = xn;
+      if (conv) {
+        D.gactive[ii] = 0;
+        D.gdone[ii] = 1;
+      } else {
+        D.gactive[ii] = 1;
+        D.gdone[ii] = 0;
+        g[0] = nrm;
+        for (int i = 1; i <= m; ++i) g[i] = 0.0;
+        D.gk[ii] = 0;
+      }
+      if (!isfinite(nrm)) flag(D.status, ii, GRTE_ENAN);
+    }
+    if (!conv) {
+      const double inv = 1.0 / nrm;
+      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) v0[j] *= inv;
+    }
+    return;
+  }
+
+  if (MODE == G_ARNOLDI) {
+    if (!D.gactive[ii]) return;
+    // C v_j = alpha v_j + kappa/dx * sum_k S_k  (the HOM pass just ran on v_j)
+    const double* vj = Vi(jcol);
+    double* cv = z;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x)
+      cv[j] = alpha[j] * vj[j] + kc[j] * flux_sum(D, I, j) / I.dx;
+    __syncthreads();
+    double* wv = Vi(jcol + 1);
+    prec_apply<false>(D, I, cv, wv, work, sm);
+    // modified Gram-Schmidt
+    for (int i = 0; i <= jcol; ++i) {
+      const double* vi = Vi(i);
+      double d = 0.0;
+      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) d += wv[j] * vi[j];
+      d = block_sum(d, red);
+      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) wv[j] -= d * vi[j];
+      if (threadIdx.x == 0) hcol[i] = d;
+      __syncthreads();
+    }
+    double nrm = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) nrm += wv[j] * wv[j];
+    nrm = sqrt(block_sum(nrm, red));
+    if (threadIdx.x == 0) {
+      hcol[jcol + 1] = nrm;
+      // apply previous Givens rotations, then a new one
+      for (int i = 0; i < jcol; ++i) {
+        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = t;
+      }
+      const double a0 = hcol[jcol], b0 = hcol[jcol + 1];
+      const double rr = hypot(a0, b0);
+      const double c0 = rr > 0.0 ? a0 / rr : 1.0, s0 = rr > 0.0 ? b0 / rr : 0.0;
+      cs[jcol] = c0;
+      sn[jcol] = s0;
+      hcol[jcol] = rr;
+      hcol[jcol + 1] = 0.0;
+      g[jcol + 1] = -s0 * g[jcol];
+      g[jcol] = c0 * g[jcol];
+      for (int i = 0; i <= jcol; ++i) H[i * kMaxRestart + jcol] = hcol[i];
+      D.gk[ii] = jcol + 1;
+      D.gits[ii] += 1;
+      // estimate of the new preconditioned residual against the iterate norm
+      if (fabs(g[jcol + 1]) <= 0.5 * D.rtol * D.gxn[ii] || nrm == 0.0 || jcol + 1 >= m) D.gactive[ii] = 0;
+    }
+    __syncthreads();
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) wv[j] *= inv;
+    return;
+  }
+
+  if (MODE == G_UPDATE) {
+    if (D.gdone[ii]) return;
+    __shared__ double y[kMaxRestart];
+    const int kk = D.gk[ii];
+    if (threadIdx.x == 0) {
+      for (int i = kk - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int l = i + 1; l < kk; ++l) t -= H[i * kMaxRestart + l] * y[l];
+        y[i] = t / H[i * kMaxRestart + i];
+      }
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      double t = x[j];
+      for (int i = 0; i < kk; ++i) t += y[i] * Vi(i)[j];
+      x[j] = t;
+    }
+    return;
+  }
+}
+
+// ----------------------------------------------------------------------------- Newton
+// Correction substep 1 (Eq. Tnp1; sigma_0/T^3: sum of Eq. dis-cor-marshak4/5),
+// multiplied through by sig:  A T^4 + B T = R,
+//   A = sig a/dt,  B = sig Cv/dt + eps^2 kap Cv/(c dt^2),  R = sig (rho^n/(c dt) - F*/dx) + B T^n,
+// kap = 1 (sigma(x)) or K* = max(U*,0)^{3/4} (sigma_0/T^3).  Newton from
+// T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the unique root
+// (convex increasing left side); it stops when the iterate stops decreasing.
+__global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
+  }
+  const Inst I = D.inst[lo];
+  const double rho = D.gx[gid];
+  const double gam = D.cf.gam[gid];
+  const double Un = D.U[gid];
+  const double Us = (Un + gam * rho) / (1.0 + gam * I.a * I.c);
+  D.Us[gid] = Us;
+  D.rho_s[gid] = rho;
+  const double sig = D.sig[gid];
+  const double kap = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : pow(fmax(Us, 0.0), 0.75);
+  const double dt = I.dt;
+  const double A = sig * I.a / dt;
+  const double B = sig * I.Cv / dt + I.eps * I.eps * kap * I.Cv / (I.c * dt * dt);
+  const double Tn = D.T[gid];
+  const double R = sig * (D.rho_n[gid] / (I.c * dt) - D.Fs[gid] / I.dx) + B * Tn;
+  double T;
+  int its = 0;
+  if (A == 0.0 && B == 0.0) {
+    T = Tn;
+  } else if (!(R > 0.0)) {
+    T = 0.0;
+    if (R <= 0.0) flag(D.status, lo, GRTE_ENEGATIVE);
+  } else {
+    double t = INFINITY;
+    if (A > 0.0) t = sqrt(sqrt(R / A));
+    if (B > 0.0) t = fmin(t, R / B);
+    for (its = 1; its <= D.newton_maxit; ++its) {
+      const double t2 = t * t;
+      const double f = A * t2 * t2 + B * t - R;
+      const double fp = 4.0 * A * t2 * t + B;
+      const double tn = t - f / fp;
+      if (!(tn < t)) break;
+      t = tn;
+    }
+    if (its > D.newton_maxit) flag(D.status, lo, GRTE_ENONCONV);
+    T = t;
+  }
+  if (!isfinite(T) || !isfinite(R)) flag(D.status, lo, GRTE_ENAN);
+  D.newton_its[gid] = its;
+  D.T[gid] = T;            // T^{n+1}
+}
+
+// ----------------------------------------------------------------------------- correction
+// Correction substep 2 (Eq. dis-cor1/2 with Eq. dis-cor4; Eq. dis-cor-marshak1/2
+// with Eq. 9171 and K -> (T^{n+1})^3) and projection (Eq. dis-proj), one line per
+// CTA.  With U = (T^{n+1})^4 and O eliminated by the node equation,
+//   O_i = o'_i - d_i eps v (E_J,i - E_J,i-1)/dx,  o'_i = d_i [eps^2 O^n_i/(c dt) - a c v (U_i - U_{i-1})/dx],
+// the cell equation divided by eps reads (A + v^2 Gint + v Gbdry) E_J = rhs with the
+// coefficients of k_cell_coef at T^{n+1}; the walls use O_{J,0} = 2/eps (b_L - E_0) - O_1
+// and O_{J,N} = 2/eps (E_{N-1} - b_R) - O_{N-1}.  Then E^{n+1} = a c U + eps E_J,
+// O^{n+1} = O_J (in place: each CTA owns its line).
+__global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
+  __shared__ TriSmem<double> sm;
+  const Line L = D.lines[blockIdx.x];
+  const Inst I = D.inst[L.inst];
+  const int64_t N = I.N;
+  const int k = L.k;
+  const double v = D.v[I.ang_off + k];
+  const double eps = I.eps, eps2 = eps * eps, cdt = I.c * I.dt, dx = I.dx, ac = I.a * I.c;
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  const double bL = inflow ? D.bL[I.ang_off + k] : 0.0, bR = inflow ? D.bR[I.ang_off + k] : 0.0;
+  const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
+  double* E = D.E + eo;
+  double* O = D.O + oo;
+  const double* T = D.T + co;   // T^{n+1}
+  double* xb = D.xb + eo;
+  double* on = D.onode + oo;
+  const double *kc = D.cf.kc + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
+               *dl = D.cf.dl + co;
+  auto U = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
+  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
+    double o = 0.0;
+    if (i >= 1 && i <= N - 1) o = dl[i] * (eps2 * O[i] / cdt - ac * v * (U(i) - U(i - 1)) / dx);
+    on[i] = o;
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    double Dj = on[j + 1] - on[j];
+    if (inflow && j == 0) Dj = 2.0 * on[1] - 2.0 / eps * (bL - ac * U(0));
+    if (inflow && j == N - 1) Dj = 2.0 / eps * (ac * U(N - 1) - bR) - 2.0 * on[N - 1];
+    xb[j] = (kc[j] * (E[j] - ac * U(j)) / cdt - kc[j] * v * Dj / dx) / eps;
+  }
+  __syncthreads();
+  LineCoef cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
+  tri_solve<true>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
+  // projection
+  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
+    double Oi;
+    auto Oint = [&](int64_t n) { return on[n] - dl[n] * eps * v * (xb[n] - xb[n - 1]) / dx; };
+    if (i >= 1 && i <= N - 1) Oi = Oint(i);
+    else if (!inflow) Oi = 0.0;
+    else if (i == 0) Oi = 2.0 / eps * (bL - ac * U(0)) - 2.0 * xb[0] - Oint(1);
+    else Oi = 2.0 / eps * (ac * U(N - 1) - bR) + 2.0 * xb[N - 1] - Oint(N - 1);
+    O[i] = Oi;
+  }
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) E[j] = ac * U(j) + eps * xb[j];
+}
+
+// U^{n+1} = (T^{n+1})^4 (Eq. dis-proj1)
+__global__ void k_project_U(Dev D, int64_t ncell) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  const double t = D.T[gid];
+  D.U[gid] = (t * t) * (t * t);
+}
+
+}  // namespace grte
+
+// =============================================================================== host
+using namespace grte;
+
+struct grte_ctx {
+  int n_inst = 0;
+  std::vector<Inst> inst;
+  std::vector<Line> lines;
+  std::vector<double> hv, hw;
+  int64_t ncell = 0, nelem = 0, nnelem = 0, nred = 0, npred = 0;
+  grte_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool state_set = false;
+  std::vector<char> inst_set;
+  Dev D{};
+  int64_t* d_cell_start = nullptr;
+  Inst* d_inst = nullptr;
+  Line* d_lines = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+  grte_stats_t stats{};
+  int* h_flags = nullptr;   // pinned: gdone per instance
+};
+
+static grte_status fail(grte_t h, grte_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(h, GRTE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(grte_t h, T** p, int64_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  if (e == cudaSuccess) {
+    h->allocs.push_back(q);
+    cudaMemset(q, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  }
+  *p = (T*)q;
+  return e;
+}
+
+// Gauss-Legendre nodes on [-1,1] by Newton on P_n (three-term recurrence); the
+// positive half, weights normalised to sum 1 (= int_0^1 dv).
+static void gauss_legendre_half(int n, std::vector<double>& v, std::vector<double>& w) {
+  const int M = n / 2;
+  v.resize(M);
+  w.resize(M);
+  for (int i = 0; i < M; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+    }
+    v[M - 1 - i] = x;                       // increasing order
+    w[M - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+extern "C" {
+
+void grte_default_options(grte_options* o) {
+  if (!o) return;
+  o->precision = GRTE_FP64;
+  o->krylov_rtol = 1e-14;
+  o->krylov_restart = 10;
+  o->krylov_maxcycles = 6;
+  o->newton_maxit = 60;
+  o->stream = nullptr;
+}
+
+const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle"; }
+
+void grte_destroy(grte_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_options* opt, grte_t* out) {
+  if (!out) return GRTE_EINVAL;
+  *out = nullptr;
+  if (n_inst <= 0 || !in) return GRTE_EINVAL;
+  grte_t h = new (std::nothrow) grte_ctx();
+  if (!h) return GRTE_ENOMEM;
+  grte_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  auto bad = [&](const std::string& m) { grte_status s = fail(h, GRTE_EINVAL, m); *out = h; return s; };
+  if (h->opt.precision != GRTE_FP64) return bad("only GRTE_FP64 is available in this build");
+  if (h->opt.krylov_restart < 1 || h->opt.krylov_restart > kMaxRestart) return bad("krylov_restart out of range [1,16]");
+  if (h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1 || !(h->opt.krylov_rtol > 0)) return bad("bad solver options");
+  h->n_inst = n_inst;
+  int64_t coff = 0, eoff = 0, noff = 0, roff = 0, poff = 0;
+  int aoff = 0, loff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const grte_instance1d& p = in[i];
+    if (p.nx < 2 || p.nx > (1 << 24)) return bad("nx must be in [2, 2^24]");
+    if (p.n_angle < 1 || p.n_angle > 4096) return bad("n_angle must be in [1, 4096]");
+    if (!p.sigma) return bad("sigma is NULL");
+    if (p.sigma_kind != GRTE_SIGMA_CONST && p.sigma_kind != GRTE_SIGMA_T3) return bad("bad sigma_kind");
+    if (p.bc != GRTE_BC_INFLOW && p.bc != GRTE_BC_REFLECT) return bad("bad bc");
+    if (!(p.x1 > p.x0) || !(p.dt > 0) || !(p.a > 0) || !(p.c > 0) || !(p.Cv > 0) || !(p.eps > 0))
+      return bad("x1 > x0, dt, a, c, Cv, eps must be positive");
+    if ((p.v == nullptr) != (p.w == nullptr)) return bad("v and w must both be given or both NULL");
+    std::vector<double> v, w;
+    if (p.v) {
+      v.assign(p.v, p.v + p.n_angle);
+      w.assign(p.w, p.w + p.n_angle);
+    } else {
+      gauss_legendre_half(2 * p.n_angle, v, w);
+    }
+    double sw = 0.0;
+    for (int k = 0; k < p.n_angle; ++k) {
+      if (!(v[k] > 0.0 && v[k] <= 1.0) || !(w[k] > 0.0)) return bad("angles must lie in (0,1], weights > 0");
+      sw += w[k];
+    }
+    for (int k = 0; k < p.n_angle; ++k) w[k] /= sw;   // sum_k w_k = 1 exactly as possible
+    for (int64_t j = 0; j < p.nx; ++j)
+      if (!(p.sigma[j] >= 0.0) || !std::isfinite(p.sigma[j])) return bad("sigma must be finite and >= 0");
+    Inst I{};
+    I.N = (int)p.nx;
+    I.M = p.n_angle;
+    I.kind = p.sigma_kind;
+    I.bc = p.bc;
+    I.eps = p.eps;
+    I.dt = p.dt;
+    I.dx = (p.x1 - p.x0) / (double)p.nx;
+    I.a = p.a;
+    I.c = p.c;
+    I.Cv = p.Cv;
+    double wv = 0, wv2 = 0;
+    for (int k = 0; k < p.n_angle; ++k) {
+      wv += w[k] * v[k];
+      wv2 += w[k] * v[k] * v[k];
+    }
+    I.wv = wv;
+    I.wv2 = wv2;
+    I.cell_off = coff;
+    I.elem_off = eoff;
+    I.nelem_off = noff;
+    I.red_off = poff;
+    I.ang_off = aoff;
+    I.line_off = loff;
+    for (int k = 0; k < p.n_angle; ++k) {
+      h->lines.push_back(Line{i, k, roff});
+      roff += tri_red_size(p.nx);
+    }
+    poff += tri_red_size(p.nx);
+    coff += p.nx;
+    eoff += p.nx * p.n_angle;
+    noff += (p.nx + 1) * p.n_angle;
+    aoff += p.n_angle;
+    loff += p.n_angle;
+    h->inst.push_back(I);
+    h->hv.insert(h->hv.end(), v.begin(), v.end());
+    h->hw.insert(h->hw.end(), w.begin(), w.end());
+  }
+  h->ncell = coff;
+  h->nelem = eoff;
+  h->nnelem = noff;
+  h->nred = roff;
+  h->npred = poff;
+  *out = h;
+  if (h->opt.stream) {
+    h->stream = (cudaStream_t)h->opt.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  Dev& D = h->D;
+  const int m = h->opt.krylov_restart;
+  D.m = m;
+  D.rtol = h->opt.krylov_rtol;
+  D.newton_maxit = h->opt.newton_maxit;
+  const int64_t nc = h->ncell, ne = h->nelem, nn = h->nnelem, na = aoff;
+#define AL(ptr, n) do { if (dalloc(h, &(ptr), (n)) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc failed for " #ptr); } while (0)
+  AL(h->d_inst, n_inst);
+  AL(h->d_lines, (int64_t)h->lines.size());
+  AL(h->d_cell_start, n_inst);
+  AL(D.v, na); AL(D.w, na); AL(D.bL, na); AL(D.bR, na);
+  AL(D.E, ne); AL(D.O, nn); AL(D.T, nc); AL(D.U, nc); AL(D.sig, nc);
+  AL(D.rho_n, nc); AL(D.rho_s, nc); AL(D.Fs, nc); AL(D.Us, nc); AL(D.newton_its, nc);
+  AL(D.cf.kc, nc); AL(D.cf.s, nc); AL(D.cf.alpha, nc); AL(D.cf.A, nc); AL(D.cf.gam, nc);
+  AL(D.cf.gl, nc); AL(D.cf.gu, nc); AL(D.cf.gb, nc); AL(D.cf.dl, nc);
+  AL(D.xb, ne); AL(D.S, ne); AL(D.F, 4 * ne); AL(D.Rd, h->nred); AL(D.onode, nn);
+  AL(D.pF, 4 * nc); AL(D.pRd, h->npred);
+  // x, z contiguous so that the GMRES kernel can recover the total cell count
+  double* xz = nullptr;
+  AL(xz, 2 * nc);
+  D.gx = xz;
+  D.gz = xz + nc;
+  AL(D.gV, (int64_t)(m + 1) * nc);
+  AL(D.gH, (int64_t)n_inst * (kMaxRestart + 1) * kMaxRestart);
+  AL(D.gg, (int64_t)n_inst * (kMaxRestart + 1));
+  AL(D.gcs, (int64_t)n_inst * kMaxRestart);
+  AL(D.gsn, (int64_t)n_inst * kMaxRestart);
+  AL(D.gbeta, n_inst);
+  AL(D.gxn, n_inst);
+  AL(D.gactive, n_inst); AL(D.gk, n_inst); AL(D.gdone, n_inst); AL(D.gits, n_inst); AL(D.gcycles, n_inst);
+  AL(D.status, n_inst);
+#undef AL
+  D.inst = h->d_inst;
+  D.lines = h->d_lines;
+  std::vector<int64_t> cstart(n_inst);
+  std::vector<double> hbL(na, 0.0), hbR(na, 0.0), hsig(nc);
+  for (int i = 0; i < n_inst; ++i) {
+    const Inst& I = h->inst[i];
+    cstart[i] = I.cell_off;
+    for (int k = 0; k < I.M; ++k) {
+      hbL[I.ang_off + k] = in[i].bL ? in[i].bL[k] : 0.0;
+      hbR[I.ang_off + k] = in[i].bR ? in[i].bR[k] : 0.0;
+    }
+    std::memcpy(hsig.data() + I.cell_off, in[i].sigma, sizeof(double) * I.N);
+  }
+  CK(cudaMemcpy(h->d_inst, h->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_lines, h->lines.data(), sizeof(Line) * h->lines.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_cell_start, cstart.data(), sizeof(int64_t) * n_inst, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.v, h->hv.data(), sizeof(double) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.w, h->hw.data(), sizeof(double) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.bL, hbL.data(), sizeof(double) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.bR, hbR.data(), sizeof(double) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.sig, hsig.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+  CK(cudaMallocHost(&h->h_flags, sizeof(int) * n_inst));
+  h->inst_set.assign(n_inst, 0);
+  return GRTE_OK;
+}
+
+grte_status grte_set_state(grte_t h, int inst, const double* T, const double* E, const double* O) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !T) return fail(h, GRTE_EINVAL, "bad instance or T NULL");
+  if ((E == nullptr) != (O == nullptr)) return fail(h, GRTE_EINVAL, "E and O must both be given or both NULL");
+  const Inst& I = h->inst[inst];
+  const int64_t N = I.N, M = I.M;
+  std::vector<double> hE(N * M), hO((N + 1) * M), hU(N);
+  for (int64_t j = 0; j < N; ++j) {
+    if (!(T[j] >= 0.0) || !std::isfinite(T[j])) return fail(h, GRTE_EINVAL, "T must be finite and >= 0");
+    hU[j] = (T[j] * T[j]) * (T[j] * T[j]);
+  }
+  for (int64_t k = 0; k < M; ++k) {
+    for (int64_t j = 0; j < N; ++j) hE[k * N + j] = E ? E[j * M + k] : I.a * I.c * hU[j];
+    for (int64_t i = 0; i <= N; ++i) hO[k * (N + 1) + i] = O ? O[i * M + k] : 0.0;
+  }
+  Dev& D = h->D;
+  CK(cudaMemcpyAsync(D.T + I.cell_off, T, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(D.U + I.cell_off, hU.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(D.E + I.elem_off, hE.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(D.O + I.nelem_off, hO.data(), sizeof(double) * (N + 1) * M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->inst_set[inst] = 1;
+  h->state_set = std::all_of(h->inst_set.begin(), h->inst_set.end(), [](char c) { return c != 0; });
+  return GRTE_OK;
+}
+
+static grte_status step_once(grte_t h) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const int ni = h->n_inst;
+  const int nl = (int)h->lines.size();
+  const int64_t nc = h->ncell;
+  const int cb = 256;
+  const unsigned cgrid = (unsigned)((nc + cb - 1) / cb);
+  // prediction coefficients at T^n, rho^n, initial iterate x = rho^n
+  k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 0);
+  k_rho<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n, D.E);
+  CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
+  CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
+  k_pred_line<PRED_FULL_FACTOR><<<nl, kTriThreads, 0, st>>>(D, D.gx);
+  k_gmres<G_RESTART_FIRST><<<ni, kTriThreads, 0, st>>>(D, 0);
+  int cycles = 0;
+  for (;;) {
+    for (int j = 0; j < D.m; ++j) {
+      k_pred_line<PRED_HOM><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc);
+      k_gmres<G_ARNOLDI><<<ni, kTriThreads, 0, st>>>(D, j);
+    }
+    k_gmres<G_UPDATE><<<ni, kTriThreads, 0, st>>>(D, 0);
+    k_pred_line<PRED_FULL><<<nl, kTriThreads, 0, st>>>(D, D.gx);
+    k_gmres<G_RESTART><<<ni, kTriThreads, 0, st>>>(D, 0);
+    ++cycles;
+    CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int i = 0; i < ni; ++i) all = all && h->h_flags[i];
+    if (all) break;
+    if (cycles >= h->opt.krylov_maxcycles) {
+      // flag the instances that did not converge
+      std::vector<int> s(ni);
+      CK(cudaMemcpy(s.data(), D.status, sizeof(int) * ni, cudaMemcpyDeviceToHost));
+      for (int i = 0; i < ni; ++i)
+        if (!h->h_flags[i]) s[i] |= 1 << GRTE_ENONCONV;
+      CK(cudaMemcpy(D.status, s.data(), sizeof(int) * ni, cudaMemcpyHostToDevice));
+      break;
+    }
+  }
+  h->stats.krylov_cycles += cycles;
+  // correction substep 1 (per-cell Newton); T now holds T^{n+1}
+  k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc);
+  // correction substep 2 + projection at T^{n+1}
+  k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1);
+  k_corr_line<<<nl, kTriThreads, 0, st>>>(D);
+  k_project_U<<<cgrid, cb, 0, st>>>(D, nc);
+  CK(cudaGetLastError());
+  return GRTE_OK;
+}
+
+grte_status grte_step(grte_t h, int64_t nsteps) {
+  if (!h) return GRTE_EINVAL;
+  if (!h->state_set) return fail(h, GRTE_ESTATE, "state not set for every instance");
+  if (nsteps < 0) return fail(h, GRTE_EINVAL, "nsteps < 0");
+  h->stats.krylov_cycles = 0;
+  h->stats.krylov_iters = 0;
+  int64_t its = 0;
+  std::vector<int> hits(h->n_inst);
+  for (int64_t n = 0; n < nsteps; ++n) {
+    grte_status s = step_once(h);
+    if (s != GRTE_OK) return s;
+    CK(cudaMemcpyAsync(hits.data(), h->D.gits, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int v : hits) its += v;
+    h->stats.steps += 1;
+  }
+  h->stats.krylov_iters = its;
+  return GRTE_OK;
+}
+
+static grte_status device_status(grte_t h) {
+  std::vector<int> s(h->n_inst);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(s.data(), h->D.status, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost));
+  int64_t all = 0;
+  for (int v : s) all |= v;
+  h->stats.status_flags = all;
+  for (int code : {GRTE_ENAN, GRTE_ENONCONV, GRTE_ENEGATIVE, GRTE_ETIMEOUT})
+    if (all & (1 << code)) return fail(h, (grte_status)code, "device reported status " + std::to_string(code));
+  return GRTE_OK;
+}
+
+grte_status grte_sync(grte_t h) {
+  if (!h) return GRTE_EINVAL;
+  return device_status(h);
+}
+
+static grte_status get_cells(grte_t h, int inst, const double* src, double* out, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !out) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.N) return fail(h, GRTE_EINVAL, "len must equal nx");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(out, src + I.cell_off, sizeof(double) * I.N, cudaMemcpyDeviceToHost));
+  return device_status(h);
+}
+
+grte_status grte_get_T(grte_t h, int inst, double* T, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  return get_cells(h, inst, h->D.T, T, len);
+}
+
+grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  const double* src = which == 0 ? h->D.Us : which == 1 ? h->D.Fs : which == 2 ? h->D.rho_s
+                    : which == 3 ? h->D.newton_its : nullptr;
+  if (!src) return fail(h, GRTE_EINVAL, "which must be 0..3");
+  return get_cells(h, inst, src, out, len);
+}
+
+grte_status grte_get_E(grte_t h, int inst, double* E, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !E) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.N * I.M) return fail(h, GRTE_EINVAL, "len must equal nx*M");
+  std::vector<double> t((size_t)I.N * I.M);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(t.data(), h->D.E + I.elem_off, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < I.M; ++k)
+    for (int64_t j = 0; j < I.N; ++j) E[j * I.M + k] = t[k * I.N + j];
+  return device_status(h);
+}
+
+grte_status grte_get_O(grte_t h, int inst, double* O, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !O) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)(I.N + 1) * I.M) return fail(h, GRTE_EINVAL, "len must equal (nx+1)*M");
+  std::vector<double> t((size_t)(I.N + 1) * I.M);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(t.data(), h->D.O + I.nelem_off, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < I.M; ++k)
+    for (int64_t i = 0; i <= I.N; ++i) O[i * I.M + k] = t[k * (I.N + 1) + i];
+  return device_status(h);
+}
+
+grte_status grte_get_rho(grte_t h, int inst, double* rho, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !rho) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.N) return fail(h, GRTE_EINVAL, "len must equal nx");
+  std::vector<double> E((size_t)I.N * I.M);
+  grte_status s = grte_get_E(h, inst, E.data(), E.size());
+  if (s != GRTE_OK && s != GRTE_ENEGATIVE) return s;
+  for (int64_t j = 0; j < I.N; ++j) {
+    double acc = 0.0;
+    for (int k = 0; k < I.M; ++k) acc += h->hw[I.ang_off + k] * E[j * I.M + k];
+    rho[j] = acc;
+  }
+  return s;
+}
+
+grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !Ipos || !Ineg) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.N * I.M) return fail(h, GRTE_EINVAL, "len must equal nx*M");
+  std::vector<double> E((size_t)I.N * I.M), O((size_t)(I.N + 1) * I.M);
+  grte_status s = grte_get_E(h, inst, E.data(), E.size());
+  if (s != GRTE_OK && s != GRTE_ENEGATIVE) return s;
+  s = grte_get_O(h, inst, O.data(), O.size());
+  if (s != GRTE_OK && s != GRTE_ENEGATIVE) return s;
+  for (int64_t j = 0; j < I.N; ++j)
+    for (int k = 0; k < I.M; ++k) {
+      const double oc = 0.5 * (O[j * I.M + k] + O[(j + 1) * I.M + k]);
+      Ipos[j * I.M + k] = E[j * I.M + k] + I.eps * oc;
+      Ineg[j * I.M + k] = E[j * I.M + k] - I.eps * oc;
+    }
+  return s;
+}
+
+grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !v || !w) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.M) return fail(h, GRTE_EINVAL, "len must equal n_angle");
+  std::memcpy(v, h->hv.data() + I.ang_off, sizeof(double) * I.M);
+  std::memcpy(w, h->hw.data() + I.ang_off, sizeof(double) * I.M);
+  return GRTE_OK;
+}
+
+grte_status grte_stats(grte_t h, grte_stats_t* st) {
+  if (!h || !st) return GRTE_EINVAL;
+  std::vector<double> its(h->ncell);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(its.data(), h->D.newton_its, sizeof(double) * h->ncell, cudaMemcpyDeviceToHost));
+  double mx = 0, sum = 0;
+  for (double v : its) {
+    mx = std::max(mx, v);
+    sum += v;
+  }
+  h->stats.newton_iters_max = (int64_t)mx;
+  h->stats.newton_iters_mean = h->ncell ? sum / h->ncell : 0.0;
+  grte_status s = device_status(h);
+  *st = h->stats;
+  return s;
+}
+
+}  // extern "C"

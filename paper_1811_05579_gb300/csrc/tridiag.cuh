@@ -1,0 +1,200 @@
+// CTA-cooperative partitioned tridiagonal solver (sm_103a).
+//
+// Solves  a_j x_{j-1} + b_j x_j + c_j x_{j+1} = r_j,  j = 0..n-1  (a_0 = c_{n-1} = 0)
+// for strictly diagonally dominant systems (no pivoting).  The n unknowns are cut
+// into P contiguous chunks (one per thread).  Each thread eliminates its chunk's
+// interior so that the interior unknowns depend only on the chunk's first and last
+// unknowns; the 2P first/last unknowns form a tridiagonal reduced system (a Schur
+// complement, still diagonally dominant) that the CTA solves by parallel cyclic
+// reduction in shared memory; each thread then back-substitutes its interior.
+//
+// FACTOR mode also stores everything that depends on the matrix only (per element:
+// 1/den, c-hat, c-check, a-check; per system: the PCR multipliers and the final
+// reciprocal diagonal), so later SOLVE calls with the same matrix do only the
+// right-hand-side recurrences: 5 flops per element plus 2 per reduced equation and
+// PCR level.
+//
+// The right-hand side is read from x[] and the solution written back to x[] (global
+// memory, unit stride).  Storage sizes: 4*n values in F, tri_red_size(n) in Rd.
+#pragma once
+#include <cstdint>
+
+namespace grte {
+
+constexpr int kTriThreads = 256;          // threads (and at most this many chunks) per CTA
+constexpr int kTriMaxRed = 2 * kTriThreads;
+
+__host__ __device__ inline int tri_chunks(int64_t n) {
+  int64_t p = n / 2;
+  return (int)(p < kTriThreads ? p : kTriThreads);
+}
+__host__ __device__ inline int tri_levels(int nr) {
+  int L = 0;
+  while ((1 << L) < nr) ++L;
+  return L;
+}
+__host__ __device__ inline int64_t tri_red_size(int64_t n) {
+  int nr = 2 * tri_chunks(n);
+  return (int64_t)tri_levels(nr) * 2 * nr + nr;
+}
+
+template <typename R>
+struct TriSmem {
+  R a[2][kTriMaxRed];
+  R b[2][kTriMaxRed];
+  R c[2][kTriMaxRed];
+  R r[2][kTriMaxRed];
+};
+
+// Coefficient provider interface (Cf): R a(int64_t j), b(j), c(j); a(0) and c(n-1)
+// must be 0.  b() is called in FACTOR mode only.
+template <bool FACTOR, typename R, class Cf>
+__device__ void tri_solve(const Cf& cf, int64_t n, R* __restrict__ x, R* __restrict__ F,
+                          R* __restrict__ Rd, TriSmem<R>& sm) {
+  const int P = tri_chunks(n);
+  const int nr = 2 * P;
+  const int L = tri_levels(nr);
+  const int tid = threadIdx.x;
+  R* f_inv = F;
+  R* f_ch = F + n;
+  R* f_cc = F + 2 * n;
+  R* f_ac = F + 3 * n;
+  const int64_t base = n / P;
+  const int64_t rem = n % P;
+
+  // ---- phase A: chunk elimination -------------------------------------------------
+  if (tid < P) {
+    const int64_t s = tid * base + (tid < rem ? tid : rem);
+    const int64_t len = base + (tid < rem ? 1 : 0);
+    const int64_t e = s + len - 1;
+    R rs, re, As = 0, Bs = 0, Cs = 0, Ae = 0, Be = 0, Ce = 0;
+    if (len >= 3) {
+      // down sweep over the interior s+1..e-1:
+      //   x_j = rhat_j - chat_j x_{j+1} - ahat_j x_s
+      R rh = 0, ch = 0, ah = 0;
+      for (int64_t j = s + 1; j <= e - 1; ++j) {
+        R aj = cf.a(j);
+        R rj = x[j];
+        R inv;
+        if (FACTOR) {
+          R bj = cf.b(j), cj = cf.c(j);
+          R den = (j == s + 1) ? bj : bj - aj * ch;
+          inv = R(1) / den;
+          ah = (j == s + 1) ? aj * inv : -aj * ah * inv;
+          ch = cj * inv;
+          f_inv[j] = inv;
+          f_ch[j] = ch;
+          f_ac[j] = ah;            // a-hat for now; becomes a-check in the up sweep
+        } else {
+          inv = f_inv[j];
+        }
+        rh = (j == s + 1) ? rj * inv : (rj - aj * rh) * inv;
+        x[j] = rh;
+      }
+      // up sweep: x_j = rcheck_j - ccheck_j x_e - acheck_j x_s
+      R rc = x[e - 1];
+      R cc = 0, ac = 0;
+      if (FACTOR) {
+        cc = f_ch[e - 1];
+        ac = f_ac[e - 1];
+        f_cc[e - 1] = cc;
+      }
+      for (int64_t j = e - 2; j >= s + 1; --j) {
+        R chj = f_ch[j];
+        rc = x[j] - chj * rc;
+        x[j] = rc;
+        if (FACTOR) {
+          cc = -chj * cc;
+          ac = f_ac[j] - chj * ac;
+          f_cc[j] = cc;
+          f_ac[j] = ac;
+        }
+      }
+      // reduced rows of x_s and x_e
+      R cS = cf.c(s), aE = cf.a(e);
+      rs = x[s] - cS * x[s + 1];           // x[s+1] holds rcheck_{s+1}
+      re = x[e] - aE * x[e - 1];           // x[e-1] holds rhat_{e-1} (= rcheck_{e-1})
+      if (FACTOR) {
+        As = cf.a(s);
+        Bs = cf.b(s) - cS * f_ac[s + 1];
+        Cs = -cS * f_cc[s + 1];
+        Ae = -aE * f_ac[e - 1];           // a-hat_{e-1} = a-check_{e-1}
+        Be = cf.b(e) - aE * f_ch[e - 1];
+        Ce = cf.c(e);
+      }
+    } else {  // len == 2: no interior
+      rs = x[s];
+      re = x[e];
+      if (FACTOR) {
+        As = cf.a(s); Bs = cf.b(s); Cs = cf.c(s);
+        Ae = cf.a(e); Be = cf.b(e); Ce = cf.c(e);
+      }
+    }
+    sm.r[0][2 * tid] = rs;
+    sm.r[0][2 * tid + 1] = re;
+    if (FACTOR) {
+      sm.a[0][2 * tid] = As; sm.b[0][2 * tid] = Bs; sm.c[0][2 * tid] = Cs;
+      sm.a[0][2 * tid + 1] = Ae; sm.b[0][2 * tid + 1] = Be; sm.c[0][2 * tid + 1] = Ce;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: parallel cyclic reduction on the nr reduced equations -----------
+  int cur = 0;
+  for (int l = 0; l < L; ++l) {
+    const int st = 1 << l;
+    R* k1s = Rd + (int64_t)l * 2 * nr;
+    R* k2s = k1s + nr;
+    for (int i = tid; i < nr; i += blockDim.x) {
+      const bool hasL = i - st >= 0, hasR = i + st < nr;
+      R k1, k2;
+      if (FACTOR) {
+        k1 = hasL ? sm.a[cur][i] / sm.b[cur][i - st] : R(0);
+        k2 = hasR ? sm.c[cur][i] / sm.b[cur][i + st] : R(0);
+        k1s[i] = k1;
+        k2s[i] = k2;
+        sm.a[cur ^ 1][i] = hasL ? -sm.a[cur][i - st] * k1 : R(0);
+        sm.c[cur ^ 1][i] = hasR ? -sm.c[cur][i + st] * k2 : R(0);
+        R bn = sm.b[cur][i];
+        if (hasL) bn -= sm.c[cur][i - st] * k1;
+        if (hasR) bn -= sm.a[cur][i + st] * k2;
+        sm.b[cur ^ 1][i] = bn;
+      } else {
+        k1 = k1s[i];
+        k2 = k2s[i];
+      }
+      R rn = sm.r[cur][i];
+      if (hasL) rn -= sm.r[cur][i - st] * k1;
+      if (hasR) rn -= sm.r[cur][i + st] * k2;
+      sm.r[cur ^ 1][i] = rn;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  R* ib = Rd + (int64_t)L * 2 * nr;
+  for (int i = tid; i < nr; i += blockDim.x) {
+    R inv;
+    if (FACTOR) {
+      inv = R(1) / sm.b[cur][i];
+      ib[i] = inv;
+    } else {
+      inv = ib[i];
+    }
+    sm.r[cur][i] *= inv;
+  }
+  __syncthreads();
+
+  // ---- phase C: back substitution ---------------------------------------------------
+  if (tid < P) {
+    const int64_t s = tid * base + (tid < rem ? tid : rem);
+    const int64_t len = base + (tid < rem ? 1 : 0);
+    const int64_t e = s + len - 1;
+    const R xs = sm.r[cur][2 * tid], xe = sm.r[cur][2 * tid + 1];
+    x[s] = xs;
+    x[e] = xe;
+    for (int64_t j = s + 1; j <= e - 1; ++j) x[j] = x[j] - f_cc[j] * xe - f_ac[j] * xs;
+  }
+  __syncthreads();
+}
+
+}  // namespace grte

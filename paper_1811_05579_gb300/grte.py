@@ -1,0 +1,204 @@
+"""Thin ctypes binding of the C ABI in include/grte.h (argument marshalling only).
+
+Every step of the scheme runs in the CUDA library `libgrte.so` built in-tree by
+`paper_1811_05579_gb300.build.build_library()`.  Importing this module loads that
+library and raises if it is missing; there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrte.so")
+
+GRTE_OK = 0
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONCONV", 5: "ENEGATIVE",
+                6: "ENAN", 7: "ETIMEOUT", 8: "ESTATE"}
+SIGMA_CONST, SIGMA_T3 = 0, 1
+BC_INFLOW, BC_REFLECT = 0, 1
+FP64, MIXED = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Instance1D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("n_angle", ctypes.c_int), ("v", _dp), ("w", _dp),
+                ("sigma", _dp), ("sigma_kind", ctypes.c_int), ("bc", ctypes.c_int),
+                ("bL", _dp), ("bR", _dp), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
+                ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
+                ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
+                ("newton_maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("krylov_iters", ctypes.c_int64),
+                ("krylov_cycles", ctypes.c_int64), ("newton_iters_max", ctypes.c_int64),
+                ("newton_iters_mean", ctypes.c_double), ("status_flags", ctypes.c_int64)]
+
+
+EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
+            "grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O", "grte_get_I", "grte_get_stage",
+            "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy"]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError("libgrte.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    lib.grte_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.grte_default_options.restype = None
+    lib.grte_create_1d.argtypes = [ctypes.c_int, ctypes.POINTER(Instance1D), ctypes.POINTER(Options),
+                                   ctypes.POINTER(ctypes.c_void_p)]
+    lib.grte_set_state.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp]
+    lib.grte_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    lib.grte_sync.argtypes = [ctypes.c_void_p]
+    for name in ("grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O"):
+        getattr(lib, name).argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_get_I.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_size_t]
+    lib.grte_get_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_get_quadrature.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_size_t]
+    lib.grte_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
+    lib.grte_last_error.argtypes = [ctypes.c_void_p]
+    lib.grte_last_error.restype = ctypes.c_char_p
+    lib.grte_destroy.argtypes = [ctypes.c_void_p]
+    lib.grte_destroy.restype = None
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+class GrteError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Grte:
+    """Handle over n independent 1D instances (grte_create_1d)."""
+
+    def __init__(self, instances, precision=FP64, krylov_rtol=1e-14, krylov_restart=10,
+                 krylov_maxcycles=6, newton_maxit=60, stream=None):
+        L = lib()
+        self._keep = []
+        arr = (Instance1D * len(instances))()
+        self.specs = []
+        for i, p in enumerate(instances):
+            sig = _f64(np.broadcast_to(p["sigma"], (p["nx"],)))
+            v = _f64(p.get("v"))
+            w = _f64(p.get("w"))
+            M = p["n_angle"]
+            bL = _f64(np.broadcast_to(p.get("bL", 0.0), (M,)))
+            bR = _f64(np.broadcast_to(p.get("bR", 0.0), (M,)))
+            self._keep += [sig, v, w, bL, bR]
+            arr[i] = Instance1D(p["nx"], M, _ptr(v), _ptr(w), _ptr(sig), p.get("kind", SIGMA_T3),
+                                p.get("bc", BC_INFLOW), _ptr(bL), _ptr(bR), p.get("x0", 0.0),
+                                p.get("x1", 1.0), p["dt"], p.get("a", 1.0), p.get("c", 1.0),
+                                p.get("Cv", 1.0), p["eps"])
+            self.specs.append(dict(nx=int(p["nx"]), M=int(M), eps=float(p["eps"])))
+        opt = Options()
+        L.grte_default_options(ctypes.byref(opt))
+        opt.precision = precision
+        opt.krylov_rtol = krylov_rtol
+        opt.krylov_restart = krylov_restart
+        opt.krylov_maxcycles = krylov_maxcycles
+        opt.newton_maxit = newton_maxit
+        opt.stream = stream
+        h = ctypes.c_void_p()
+        st = L.grte_create_1d(len(instances), arr, ctypes.byref(opt), ctypes.byref(h))
+        self.h = h
+        if st != GRTE_OK:
+            msg = L.grte_last_error(h).decode() if h.value else "create failed"
+            L.grte_destroy(h)
+            self.h = None
+            raise GrteError(st, msg)
+
+    def _check(self, st, allow=()):
+        if st != GRTE_OK and st not in allow:
+            raise GrteError(st, lib().grte_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if self.h is not None:
+            lib().grte_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, inst, T, E=None, O=None):
+        T, E, O = _f64(T), _f64(E), _f64(O)
+        return self._check(lib().grte_set_state(self.h, inst, _ptr(T), _ptr(E), _ptr(O)))
+
+    def step(self, n=1):
+        return self._check(lib().grte_step(self.h, n))
+
+    def sync(self, allow=()):
+        return self._check(lib().grte_sync(self.h), allow)
+
+    def _get(self, fn, inst, shape, allow):
+        out = np.empty(shape, dtype=np.float64)
+        self._check(fn(self.h, inst, _ptr(out), out.size), allow)
+        return out
+
+    def T(self, inst, allow=()):
+        return self._get(lib().grte_get_T, inst, self.specs[inst]["nx"], allow)
+
+    def rho(self, inst, allow=()):
+        return self._get(lib().grte_get_rho, inst, self.specs[inst]["nx"], allow)
+
+    def E(self, inst, allow=()):
+        s = self.specs[inst]
+        return self._get(lib().grte_get_E, inst, (s["nx"], s["M"]), allow)
+
+    def O(self, inst, allow=()):
+        s = self.specs[inst]
+        return self._get(lib().grte_get_O, inst, (s["nx"] + 1, s["M"]), allow)
+
+    def I(self, inst, allow=()):
+        s = self.specs[inst]
+        ip = np.empty((s["nx"], s["M"]))
+        im = np.empty((s["nx"], s["M"]))
+        self._check(lib().grte_get_I(self.h, inst, _ptr(ip), _ptr(im), ip.size), allow)
+        return ip, im
+
+    def stage(self, inst, which, allow=()):
+        out = np.empty(self.specs[inst]["nx"])
+        self._check(lib().grte_get_stage(self.h, inst, which, _ptr(out), out.size), allow)
+        return out
+
+    def quadrature(self, inst):
+        M = self.specs[inst]["M"]
+        v = np.empty(M)
+        w = np.empty(M)
+        self._check(lib().grte_get_quadrature(self.h, inst, _ptr(v), _ptr(w), M))
+        return v, w
+
+    def stats(self, allow=()):
+        s = Stats()
+        self._check(lib().grte_stats(self.h, ctypes.byref(s)), allow)
+        return {f: getattr(s, f) for f, _ in Stats._fields_}

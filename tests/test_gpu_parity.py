@@ -1,0 +1,197 @@
+"""GPU path vs the CPU oracle, element by element, on seeded inputs.
+
+Tolerances (FP64 mode): 1e-12 relative in the interior.  In the two wall cells the
+paper's wall rows O = (2/eps)(b - E) - O (Eq. bc-pre) turn a rounding error of E
+into an error of O that grows like u/eps, and it feeds T through the flux there;
+those cells get 1e-12 + 4e-15/eps (the same bound the oracle's own pins use)."""
+import numpy as np
+import pytest
+
+from oracle import grte1d as og
+from oracle.quadrature import gauss_legendre_half
+from paper_1811_05579_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+KIND = {"const": 0, "t3": 1}
+BC = {"inflow": 0, "reflect": 1}
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_05579_gb300 import grte
+    return grte
+
+
+def make(N, nv, eps, kind="t3", bc="inflow", sig=1.0, bL=1.0, bR=0.0, cfl=0.5, seed=0):
+    v, w = gauss_legendre_half(nv)
+    sig = np.broadcast_to(np.asarray(sig, dtype=np.float64), (N,)).copy()
+    P = og.Problem(N=N, v=v, w=w, sig=sig, eps=eps, dt=cfl / N, kind=kind, bc=bc,
+                   bL=np.full(v.size, bL), bR=np.full(v.size, bR))
+    spec = dict(nx=N, n_angle=v.size, v=v, w=w, sigma=sig, kind=KIND[kind], bc=BC[bc],
+                bL=P.bL, bR=P.bR, dt=P.dt, eps=eps)
+    return P, spec
+
+
+def state(P, seed, lo=0.05, hi=1.0, equilibrium=False):
+    rng = wl.SplitMix64(1000 + seed)
+    T, E, O = wl.random_state_1d(rng, P.N, P.M, (lo, hi))
+    if equilibrium:
+        return og.equilibrium_state(P, T)
+    if P.bc == "reflect":
+        O[0] = O[-1] = 0.0
+    return og.State(E=E, O=O, U=T ** 4, T=T)
+
+
+def tol_cells(P, base=1e-12):
+    t = np.full(P.N, base)
+    t[0] = t[-1] = base + 4e-15 / P.eps
+    return t
+
+
+def check(a, b, tol, what, scale=None):
+    scale = np.abs(b) if scale is None else scale
+    err = np.abs(a - b) / np.maximum(scale, 1e-300)
+    tol = np.broadcast_to(tol, err.shape)
+    bad = err > tol
+    i = np.unravel_index(np.argmax(err), err.shape)
+    assert not np.any(bad), "%s: max rel err %.3e at %s (tol %s)" % (what, err[i], i, tol[i])
+
+
+@pytest.mark.parametrize("kind", ["const", "t3"])
+@pytest.mark.parametrize("bc", ["inflow", "reflect"])
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4])
+def test_one_step_stages(G, kind, bc, eps):
+    P, spec = make(37, 8, eps, kind, bc)
+    S = state(P, 1)
+    h = G.Grte([spec])
+    h.set_state(0, S.T, S.E, S.O)
+    h.step(1)
+    info = og.StepInfo()
+    S1 = og.step(P, S, info)
+    tc = tol_cells(P)
+    check(h.stage(0, 0, allow=(5,)), info.Ustar, tc, "U*")
+    check(h.stage(0, 2, allow=(5,)), og.rho_of(P, info.Estar), tc, "rho*")
+    Fs = h.stage(0, 1, allow=(5,))
+    assert np.max(np.abs(Fs - info.Fstar)) <= 1e-12 * np.max(np.abs(info.Fstar)) + 4e-15 / eps * np.max(np.abs(info.Fstar))
+    check(h.T(0, allow=(5,)), S1.T, tc, "T")
+    E = h.E(0, allow=(5,))
+    check(E, S1.E, np.repeat(tc[:, None], P.M, 1), "E")
+    O = h.O(0, allow=(5,))
+    scaleO = np.max(np.abs(S1.O))
+    assert np.max(np.abs(O - S1.O)) <= (1e-12 + 4e-15 / eps) * scaleO * (1.0 / eps if eps < 1 else 1.0) + 1e-300
+    h.close()
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 513, 1000, 2053])
+def test_sizes_ragged_and_multilevel(G, N):
+    """Chunk counts and PCR levels: N = 2 (one chunk of 2), odd N, N past 2*256 chunks,
+    a ragged tail (N not a multiple of the chunk count)."""
+    P, spec = make(N, 4, 1e-2, "t3", "inflow")
+    S = state(P, N)
+    h = G.Grte([spec])
+    h.set_state(0, S.T, S.E, S.O)
+    h.step(1)
+    S1 = og.step(P, S)
+    check(h.T(0, allow=(5,)), S1.T, tol_cells(P), "T")
+    check(h.E(0, allow=(5,)), S1.E, np.repeat(tol_cells(P)[:, None], P.M, 1), "E")
+    h.close()
+
+
+def test_batched_uneven_instances_match_one_by_one(G):
+    rng = wl.SplitMix64(77)
+    specs, probs, states = [], [], []
+    for i, (N, nv, eps, kind) in enumerate([(64, 16, 1e-3, "t3"), (130, 4, 1.0, "const"),
+                                            (300, 8, 1e-5, "t3"), (17, 2, 1e-2, "const")]):
+        sig = 0.5 + 10 * rng.uniform(N)
+        P, spec = make(N, nv, eps, kind, "inflow", sig=sig, bL=0.8, bR=0.1)
+        specs.append(spec)
+        probs.append(P)
+        states.append(state(P, 10 + i))
+    h = G.Grte(specs)
+    for i, S in enumerate(states):
+        h.set_state(i, S.T, S.E, S.O)
+    h.step(3)
+    for i, (P, S) in enumerate(zip(probs, states)):
+        S3 = og.run(P, S, 3)
+        check(h.T(i, allow=(5,)), S3.T, tol_cells(P, 3e-12), "T inst %d" % i)
+    h.close()
+
+
+def test_equilibrium_preserved_on_gpu(G):
+    T0 = 0.6
+    P, spec = make(100, 16, 1e-3, "t3", "inflow", sig=4.0, bL=T0 ** 4, bR=T0 ** 4)
+    h = G.Grte([spec])
+    h.set_state(0, np.full(P.N, T0))
+    h.step(5)
+    T = h.T(0)
+    assert np.max(np.abs(T - T0)) < 1e-14 + 5e-16 / P.eps
+    h.close()
+
+
+def test_marshak_config_128_cells_full_run(G):
+    """1D slab, 128 cells, 16 directions, sigma = 1/T^3, eps = 1e-3, T_in = 1e-2, left
+    inflow 1, right vacuum, dt = 0.5 dx, run to t = 0.5 (128 steps), FP64."""
+    inst = wl.marshak_1d()
+    v, w = gauss_legendre_half(inst.n_dir)
+    P = og.Problem(N=inst.nx, v=v, w=w, sig=inst.sigma, eps=inst.eps, dt=inst.dt, kind="t3",
+                   bL=np.ones(v.size), bR=np.zeros(v.size))
+    spec = dict(nx=inst.nx, n_angle=v.size, v=v, w=w, sigma=inst.sigma, kind=1, bc=0,
+                bL=P.bL, bR=P.bR, dt=inst.dt, eps=inst.eps)
+    h = G.Grte([spec])
+    h.set_state(0, inst.T0)
+    h.step(inst.steps)
+    Tg = h.T(0, allow=(5,))
+    ipg, ing = h.I(0, allow=(5,))
+    S = og.run(P, og.equilibrium_state(P, inst.T0), inst.steps)
+    ip, im = og.intensity(P, S)
+    # accumulated over 128 steps: relative 1e-10 (the per-step bound is 1e-12)
+    check(Tg, S.T, np.full(P.N, 1e-10), "T")
+    # I(+-v) = E +- eps O: rounding is relative to |E| + |eps O| of the cell (I(-v) of the
+    # cold far field is a cancellation down to ~1e-24)
+    Oc = 0.5 * (S.O[:-1] + S.O[1:])
+    scale = np.abs(S.E) + np.abs(P.eps * Oc)
+    check(ipg, ip, 1e-10, "I+", scale)
+    check(ing, im, 1e-10, "I-", scale)
+    h.close()
+
+
+def test_free_streaming_matches_oracle(G):
+    inst, alpha, phi = wl.free_streaming_1d(nx=64, n_dir=8)
+    v, w = gauss_legendre_half(8)
+    bL = wl.free_streaming_intensity(0.0, v, alpha, phi)
+    bR = wl.free_streaming_intensity(1.0, -v, alpha, phi)
+    P = og.Problem(N=64, v=v, w=w, sig=0.0, eps=1.0, dt=inst.dt, kind="const", bL=bL, bR=bR)
+    xc = (np.arange(64) + 0.5) / 64
+    S = og.state_from_intensity(P, np.ones(64), wl.free_streaming_intensity(xc[:, None], v[None], alpha, phi),
+                                wl.free_streaming_intensity(xc[:, None], -v[None], alpha, phi))
+    spec = dict(nx=64, n_angle=4, v=v, w=w, sigma=np.zeros(64), kind=0, bc=0, bL=bL, bR=bR,
+                dt=inst.dt, eps=1.0)
+    h = G.Grte([spec])
+    h.set_state(0, S.T, S.E, S.O)
+    h.step(10)
+    S10 = og.run(P, S, 10)
+    check(h.E(0), S10.E, np.full(S10.E.shape, 1e-12), "E")
+    assert np.all(h.T(0) == 1.0)
+    h.close()
+
+
+def test_full_size_slab_one_step(G):
+    """8192 cells x 64 directions (32 angle pairs), one (sigma0, eps) run of the six,
+    one step against the oracle (every cell compared)."""
+    runs = wl.slab_1d_runs(steps=1)
+    r = runs[1]                       # sigma0 = 1, eps = 1e-2
+    v, w = gauss_legendre_half(r.n_dir)
+    P = og.Problem(N=r.nx, v=v, w=w, sig=r.sigma, eps=r.eps, dt=r.dt, kind="t3",
+                   bL=np.ones(v.size), bR=np.zeros(v.size))
+    spec = dict(nx=r.nx, n_angle=v.size, v=v, w=w, sigma=r.sigma, kind=1, bc=0, bL=P.bL, bR=P.bR,
+                dt=r.dt, eps=r.eps)
+    h = G.Grte([spec])
+    h.set_state(0, r.T0)
+    h.step(1)
+    S1 = og.step(P, og.equilibrium_state(P, r.T0))
+    check(h.T(0, allow=(5,)), S1.T, tol_cells(P), "T")
+    h.close()
