@@ -1,0 +1,303 @@
+"""Throughput of the 1D AP step (cell-angle updates/s) on GB300.
+
+Workload (default): the 1D slab runs - 8192 cells, Gauss-Legendre 64 directions
+(32 +-v pairs), sigma = sigma0/T^3 with sigma0 in {1, 10} x eps in {1, 1e-2, 1e-4}
+(six independent runs advanced together in one handle), T_in log-uniform in
+[1e-3, 1e-2] then smoothed, left inflow a c 1^4, right vacuum, dt = 0.5 dx.  A
+step advances all six runs by one time step of Algorithm 2.  Inputs are seeded
+synthetic data; the state is resident in HBM before timing starts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank runs its own six runs (weak
+scaling); the timed region is bracketed by barriers and the max over ranks is used.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "cell-angle updates/s"
+UNIT = "cell-angle updates/s"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_PEAK_GFLOPS = 1250.0           # nominal GB300 FP64 (the profiling recipe's figure)
+
+# Algorithmic FP64 flops per line element of the Krylov direction pass
+# (k_pred_line<HOM>): right-hand side 11, tridiagonal solve with stored factors 10,
+# flux of the two faces 10.
+HOM_FLOPS_PER_ELEM = 31
+
+
+def workload_instances(name):
+    from paper_1811_05579_gb300 import workloads as wl
+    if name == "slab6":
+        runs = wl.slab_1d_runs(steps=1)
+        cfg = {"workload": "1d_slab_8192x64_sigma0_over_T3_6runs", "nx": 8192, "n_dir": 64,
+               "runs": 6, "sigma0": [1, 10], "eps": [1, 1e-2, 1e-4], "dt": "0.5 dx"}
+    elif name == "marshak128":
+        runs = [wl.marshak_1d()]
+        cfg = {"workload": "1d_marshak_128x16", "nx": 128, "n_dir": 16, "runs": 1}
+    elif name == "batched256":
+        runs = wl.batched_1d(256, steps=1)
+        cfg = {"workload": "1d_batched_256_uneven", "runs": 256}
+    else:
+        raise SystemExit("unknown workload " + name)
+    return runs, cfg
+
+
+def specs_of(runs):
+    from paper_1811_05579_gb300 import grte as G
+    out = []
+    for r in runs:
+        M = r.n_dir // 2
+        out.append(dict(nx=r.nx, n_angle=M, v=None, w=None, sigma=r.sigma, kind=r.kind, bc=r.bc,
+                        bL=np.full(M, r.bL), bR=np.full(M, r.bR),
+                        dt=r.dt, eps=r.eps, a=r.a, c=r.c, Cv=r.Cv))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_1811_05579_gb300 import workloads as wl
+from oracle import grte1d as og
+from oracle.quadrature import gauss_legendre_half
+runs, _ = None, None
+r = wl.slab_1d_runs(steps=1)[1]
+v, w = gauss_legendre_half(r.n_dir)
+P = og.Problem(N=r.nx, v=v, w=w, sig=r.sigma, eps=r.eps, dt=r.dt, kind="t3",
+               bL=np.ones(v.size), bR=np.zeros(v.size))
+S = og.equilibrium_state(P, r.T0)
+S = og.step(P, S)          # untimed warm-up step
+n = {nsteps}
+t0 = time.perf_counter()
+for _ in range(n):
+    S = og.step(P, S)
+dt = time.perf_counter() - t0
+print(json.dumps({{"updates": n * r.nx * r.n_dir, "seconds": dt, "steps": n}}))
+"""
+
+
+def cpu_baseline(nsteps=3):
+    """The oracle as it stands, single-threaded, on one of the six runs
+    (sigma0 = 1, eps = 1e-2; 8192 cells x 64 directions) for nsteps steps."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, nsteps=nsteps)],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + out.stderr.strip()[-200:]}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d steps of one run (sigma0=1, eps=1e-2, 8192 cells x 64 dirs), %.1f s, 1 thread"
+                      % (d["steps"], d["seconds"])}
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(nsteps=max(1, min(args.steps, 3)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    runs, cfg = workload_instances(args.workload)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1811_05579_gb300 import grte as G
+
+    stream = torch.cuda.current_stream()
+    specs = specs_of(runs)
+    h = G.Grte(specs, stream=stream.cuda_stream)
+    for i, r in enumerate(runs):
+        h.set_state(i, r.T0)
+    updates_per_step = sum(r.nx * r.n_dir for r in runs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        h.step(1)
+    h.sync(allow=(5,))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    h.profile_begin(G.KERNELS)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    kry_its = 0
+    kry_cycles = 0
+    for k in range(args.steps):
+        flush.zero_()                 # L2 flushed between timed steps (not timed)
+        starts[k].record(stream)
+        h.step(1)
+        ends[k].record(stream)
+        launches += h.last_launches()
+        st = h.stats(allow=(5,))
+        kry_its += st["krylov_iters"]
+        kry_cycles += st["krylov_cycles"]
+    barrier()
+    prof = h.profile_end()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    total_updates = updates_per_step * args.steps * world
+    value = total_updates / (t_ms * 1e-3)
+
+    # end to end through the public API with host buffers: state in (H2D), one step,
+    # temperature out (D2H), timed on the host clock with the stream synchronised
+    host_state = []
+    for i, r in enumerate(runs):
+        host_state.append((h.T(i, allow=(5,)), h.E(i, allow=(5,)), h.O(i, allow=(5,))))
+    h2d = sum(T.nbytes + E.nbytes + O.nbytes for T, E, O in host_state)
+    d2h = sum(T.nbytes for T, _, _ in host_state)
+    ke = min(args.steps, 5)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        for i, (T, E, O) in enumerate(host_state):
+            h.set_state(i, T, E, O)
+        h.step(1)
+        for i in range(len(runs)):
+            h.T(i, allow=(5,))
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e_val = updates_per_step * ke / te
+
+    # dominant kernel (largest share of device time in the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    tot_prof = sum(v[0] for v in prof.values())
+    nelem = sum(r.nx * (r.n_dir // 2) for r in runs)
+    roof = None
+    if dom_name == "pred_hom":
+        flops = HOM_FLOPS_PER_ELEM * nelem
+        achieved = flops / (dom_ms / dom_n * 1e-3) / 1e9
+        roof = {"kernel": "k_pred_line<HOM>", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)", "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": None, "avg_launch_us": dom_ms / dom_n * 1e3, "launches": dom_n}
+    else:
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
+                "avg_launch_us": dom_ms / dom_n * 1e3, "launches": dom_n}
+    hbm_peak = None
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        hbm_peak = 6800.0
+    step_s = t_ms * 1e-3 / args.steps
+    hbm_alg = updates_per_step * 24 / step_s / 1e9     # 24 B per update (FP64 state read twice, written once)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded; no dataset)",
+                "config": dict(cfg, l2="flushed between timed steps (flush not timed)", precision="fp64",
+                               parallelism="replicas" if world > 1 else "single"),
+                "gpu_launches": launches,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "roofline": roof,
+                "step_hbm_roofline": {"algorithmic_bytes_per_update": 24, "achieved_gbs": hbm_alg,
+                                      "peak_gbs": hbm_peak, "frac": hbm_alg / hbm_peak},
+                "kernel_share": {k: round(v[0] / tot_prof, 4) for k, v in sorted(prof.items())},
+                "krylov_iters_per_step": kry_its / args.steps / len(runs),
+                "krylov_cycles_per_step": kry_cycles / args.steps,
+                "clocks": clk}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,7 +73,8 @@ typedef struct {
 
 typedef struct {
   int precision;         /* GRTE_FP64 (default) or GRTE_MIXED                                */
-  double krylov_rtol;    /* prediction solve: relative preconditioned residual (1e-14)       */
+  double krylov_rtol;    /* prediction solve stops at |P^-1 r| <= rtol |rho| (1e-14), or when a
+                            restart cycle stalls below 1e-9 |rho| (rounding floor of r)      */
   int krylov_restart;    /* GMRES restart length (10)                                        */
   int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (6)            */
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */
@@ -124,6 +125,19 @@ grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t le
 grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len);
 
 grte_status grte_stats(grte_t h, grte_stats_t* st);
+
+/* Kernel ids for per-kernel timing. */
+enum { GRTE_K_CELL_COEF = 0, GRTE_K_RHO = 1, GRTE_K_PRED_FACTOR = 2, GRTE_K_PRED_HOM = 3,
+       GRTE_K_PRED_FULL = 4, GRTE_K_GMRES = 5, GRTE_K_NEWTON = 6, GRTE_K_CORR = 7,
+       GRTE_K_PROJECT = 8, GRTE_NKERNELS = 9 };
+/* Start recording a CUDA event pair around every launch of the kernels whose bit
+ * (1 << id) is set in kernel_mask, on the handle's stream (device-side timing). */
+grte_status grte_profile_begin(grte_t h, uint32_t kernel_mask);
+/* Stop recording, synchronise, and return per kernel id the summed event time (ms)
+ * and the launch count; n must be >= GRTE_NKERNELS (host arrays). */
+grte_status grte_profile_end(grte_t h, double* ms, int64_t* launches, size_t n);
+/* Kernel launches issued by the last grte_step call (all kernels, profiled or not). */
+int64_t grte_last_launches(grte_t h);
 const char* grte_last_error(grte_t h);
 void grte_destroy(grte_t h);   /* NULL is a no-op */
 

@@ -330,7 +330,13 @@ __global__ void __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
     }
     nrm = sqrt(block_sum(nrm, red));
     xn = sqrt(block_sum(xn, red));
-    const bool conv = !(nrm > D.rtol * xn);   // also true for nrm == 0
+    // Converged when the true preconditioned residual is below rtol |x|.  Restarted
+    // GMRES cannot go below the rounding floor of the residual evaluation itself (a
+    // sum of terms much larger than the residual); a restart cycle that did not
+    // reduce it by 4x while it is below 1e-9 |x| has reached that floor and stops.
+    bool conv = !(nrm > D.rtol * xn);   // also true for nrm == 0
+    if (MODE == G_RESTART && !conv && nrm >= 0.25 * D.gbeta[ii] && nrm <= 1e-9 * xn) conv = true;
+    __syncthreads();
     if (threadIdx.x == 0) {
       if (MODE == G_RESTART) D.gcycles[ii] += 1;
       D.gbeta[ii] = nrm;
@@ -571,7 +577,34 @@ struct grte_ctx {
   std::string err;
   grte_stats_t stats{};
   int* h_flags = nullptr;   // pinned: gdone per instance
+  // per-kernel event timing
+  uint32_t prof_mask = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  int64_t launches = 0;
 };
+
+static cudaEvent_t pool_event(grte_t h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Launch wrapper: counts launches and, for profiled kernel ids, brackets the launch
+// with an event pair on the handle's stream.
+#define LAUNCH(kid, ...)                                                         \
+  do {                                                                           \
+    const bool prof_ = (h->prof_mask >> (kid)) & 1u;                             \
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;                                    \
+    if (prof_) { e0_ = pool_event(h); e1_ = pool_event(h); cudaEventRecord(e0_, st); } \
+    __VA_ARGS__;                                                                 \
+    if (prof_) { cudaEventRecord(e1_, st); h->prof_ev.push_back({(kid), {e0_, e1_}}); } \
+    ++h->launches;                                                               \
+  } while (0)
 
 static grte_status fail(grte_t h, grte_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -649,6 +682,7 @@ void grte_destroy(grte_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -836,22 +870,22 @@ static grte_status step_once(grte_t h) {
   const int cb = 256;
   const unsigned cgrid = (unsigned)((nc + cb - 1) / cb);
   // prediction coefficients at T^n, rho^n, initial iterate x = rho^n
-  k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 0);
-  k_rho<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n, D.E);
+  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 0));
+  LAUNCH(GRTE_K_RHO, k_rho<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n, D.E));
   CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
   CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
-  k_pred_line<PRED_FULL_FACTOR><<<nl, kTriThreads, 0, st>>>(D, D.gx);
-  k_gmres<G_RESTART_FIRST><<<ni, kTriThreads, 0, st>>>(D, 0);
+  LAUNCH(GRTE_K_PRED_FACTOR, k_pred_line<PRED_FULL_FACTOR><<<nl, kTriThreads, 0, st>>>(D, D.gx));
+  LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART_FIRST><<<ni, kTriThreads, 0, st>>>(D, 0));
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
-      k_pred_line<PRED_HOM><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc);
-      k_gmres<G_ARNOLDI><<<ni, kTriThreads, 0, st>>>(D, j);
+      LAUNCH(GRTE_K_PRED_HOM, k_pred_line<PRED_HOM><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc));
+      LAUNCH(GRTE_K_GMRES, k_gmres<G_ARNOLDI><<<ni, kTriThreads, 0, st>>>(D, j));
     }
-    k_gmres<G_UPDATE><<<ni, kTriThreads, 0, st>>>(D, 0);
-    k_pred_line<PRED_FULL><<<nl, kTriThreads, 0, st>>>(D, D.gx);
-    k_gmres<G_RESTART><<<ni, kTriThreads, 0, st>>>(D, 0);
+    LAUNCH(GRTE_K_GMRES, k_gmres<G_UPDATE><<<ni, kTriThreads, 0, st>>>(D, 0));
+    LAUNCH(GRTE_K_PRED_FULL, k_pred_line<PRED_FULL><<<nl, kTriThreads, 0, st>>>(D, D.gx));
+    LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART><<<ni, kTriThreads, 0, st>>>(D, 0));
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -870,11 +904,11 @@ static grte_status step_once(grte_t h) {
   }
   h->stats.krylov_cycles += cycles;
   // correction substep 1 (per-cell Newton); T now holds T^{n+1}
-  k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc);
+  LAUNCH(GRTE_K_NEWTON, k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
   // correction substep 2 + projection at T^{n+1}
-  k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1);
-  k_corr_line<<<nl, kTriThreads, 0, st>>>(D);
-  k_project_U<<<cgrid, cb, 0, st>>>(D, nc);
+  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
+  LAUNCH(GRTE_K_CORR, k_corr_line<<<nl, kTriThreads, 0, st>>>(D));
+  LAUNCH(GRTE_K_PROJECT, k_project_U<<<cgrid, cb, 0, st>>>(D, nc));
   CK(cudaGetLastError());
   return GRTE_OK;
 }
@@ -885,6 +919,7 @@ grte_status grte_step(grte_t h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, GRTE_EINVAL, "nsteps < 0");
   h->stats.krylov_cycles = 0;
   h->stats.krylov_iters = 0;
+  h->launches = 0;
   int64_t its = 0;
   std::vector<int> hits(h->n_inst);
   for (int64_t n = 0; n < nsteps; ++n) {
@@ -1026,5 +1061,33 @@ grte_status grte_stats(grte_t h, grte_stats_t* st) {
   *st = h->stats;
   return s;
 }
+
+grte_status grte_profile_begin(grte_t h, uint32_t kernel_mask) {
+  if (!h) return GRTE_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  h->prof_ev.clear();
+  h->ev_used = 0;
+  h->prof_mask = kernel_mask;
+  return GRTE_OK;
+}
+
+grte_status grte_profile_end(grte_t h, double* ms, int64_t* launches, size_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (!ms || !launches || n < (size_t)GRTE_NKERNELS) return fail(h, GRTE_EINVAL, "need GRTE_NKERNELS outputs");
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < n; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  for (auto& pe : h->prof_ev) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, pe.second.first, pe.second.second));
+    ms[pe.first] += t;
+    launches[pe.first] += 1;
+  }
+  h->prof_ev.clear();
+  h->ev_used = 0;
+  h->prof_mask = 0;
+  return GRTE_OK;
+}
+
+int64_t grte_last_launches(grte_t h) { return h ? h->launches : 0; }
 
 }  // extern "C"

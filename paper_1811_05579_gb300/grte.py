@@ -44,7 +44,10 @@ class Stats(ctypes.Structure):
 
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
             "grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O", "grte_get_I", "grte_get_stage",
-            "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy"]
+            "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy",
+            "grte_profile_begin", "grte_profile_end", "grte_last_launches"]
+KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
+           "project"]
 
 
 def load_library(path=LIB_PATH):
@@ -68,6 +71,10 @@ def load_library(path=LIB_PATH):
     lib.grte_last_error.restype = ctypes.c_char_p
     lib.grte_destroy.argtypes = [ctypes.c_void_p]
     lib.grte_destroy.restype = None
+    lib.grte_profile_begin.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
+    lib.grte_profile_end.argtypes = [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t]
+    lib.grte_last_launches.argtypes = [ctypes.c_void_p]
+    lib.grte_last_launches.restype = ctypes.c_int64
     return lib
 
 
@@ -197,6 +204,22 @@ class Grte:
         w = np.empty(M)
         self._check(lib().grte_get_quadrature(self.h, inst, _ptr(v), _ptr(w), M))
         return v, w
+
+    def profile_begin(self, kernels):
+        mask = 0
+        for k in kernels:
+            mask |= 1 << KERNELS.index(k)
+        return self._check(lib().grte_profile_begin(self.h, mask))
+
+    def profile_end(self):
+        n = len(KERNELS)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        self._check(lib().grte_profile_end(self.h, _ptr(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS) if cnt[i]}
+
+    def last_launches(self):
+        return int(lib().grte_last_launches(self.h))
 
     def stats(self, allow=()):
         s = Stats()

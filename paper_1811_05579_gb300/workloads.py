@@ -64,8 +64,8 @@ class Instance1D:
     T0: np.ndarray             # (nx,) initial temperature; I = a c T0^4 initially
     kind: int = SIGMA_T3
     bc: int = BC_INFLOW
-    bL: float = 1.0            # isotropic inflow value at x = 0 (v > 0)
-    bR: float = 0.0            # isotropic inflow value at x = 1 (v < 0)
+    bL: float = 1.0            # isotropic inflow intensity I(0, v > 0) (a c 1^4 with a = c = 1)
+    bR: float = 0.0            # isotropic inflow intensity I(1, v < 0)
     a: float = 1.0
     c: float = 1.0
     Cv: float = 1.0
