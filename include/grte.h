@@ -73,8 +73,9 @@ typedef struct {
 
 typedef struct {
   int precision;         /* GRTE_FP64 (default) or GRTE_MIXED                                */
-  double krylov_rtol;    /* prediction solve stops at |P^-1 r| <= rtol |rho| (1e-14), or when a
-                            restart cycle stalls below 1e-9 |rho| (rounding floor of r)      */
+  double krylov_rtol;    /* prediction solve stops when every cell's preconditioned residual
+                            is <= rtol |rho_j| (1e-13), or when a restart cycle stalls below
+                            1e-9 (the rounding floor of the residual)                        */
   int krylov_restart;    /* GMRES restart length (10)                                        */
   int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (6)            */
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */

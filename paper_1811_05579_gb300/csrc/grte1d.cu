@@ -16,6 +16,7 @@
 // per-cell quartic solved by monotone Newton; correction substep 2 (Eq. dis-cor) is
 // one tridiagonal solve per line in E_J with the same operator family; projection
 // (Eq. dis-proj) is fused into that kernel's epilogue.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,12 +31,14 @@
 
 namespace grte {
 
+namespace cg = cooperative_groups;
 constexpr int kMaxRestart = 16;
 
 struct Inst {
   int N, M, kind, bc;
   double eps, dt, dx, a, c, Cv;
   double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
+  double two_eps, inv_eps; // 2/eps, 1/eps
   int64_t cell_off;        // per-cell arrays
   int64_t elem_off;        // E-like arrays, line k at elem_off + k*N
   int64_t nelem_off;       // O-like arrays, line k at nelem_off + k*(N+1)
@@ -52,6 +55,14 @@ struct Line {
 // Per-cell coefficient arrays (length = total cells) for one operator family.
 struct CellCoef {
   double *kc, *s, *alpha, *A, *gam, *gl, *gu, *gb, *dl;  // dl_j = d at the left node of cell j
+  // products and reciprocals precomputed per cell so that no line kernel divides:
+  double *od;    // dl_j eps^2/(c dt): o_j = od_j O^n_j
+  double *dlx;   // dl_j / dx
+  double *kcd;   // kappa_j/(c dt)
+  double *kdx;   // kappa_j / dx
+  double *sac;   // s_j a c
+  double *ralpha;  // 1/alpha_j
+  double *ratio;   // (A_j - alpha_j)/alpha_j = beta/alpha
 };
 
 struct Dev {
@@ -66,10 +77,10 @@ struct Dev {
   // per-element work
   double *xb, *S, *F, *Rd, *onode;
   // preconditioner factors
-  double *pF, *pRd;
+  double *pF, *pRd, *pG, *pH, *gw;
   // GMRES
   double *gx, *gV, *gz, *gH, *gg, *gcs, *gsn, *gbeta, *gxn;
-  int *gactive, *gk, *gdone, *gits, *gcycles;
+  int *gactive, *gk, *gdone, *gits, *gcycles, *gestconv;
   int* status;
   int m;  // restart length
   double rtol;
@@ -133,6 +144,14 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
   D.cf.gu[gid] = kc * mR * dr / dx2;
   D.cf.gb[gid] = (inflow && (j == 0 || j == N - 1)) ? 2.0 * kc / (I.eps * I.dx) : 0.0;
   D.cf.dl[gid] = dl;
+  D.cf.od[gid] = dl * eps2 / cdt;
+  D.cf.dlx[gid] = dl / I.dx;
+  D.cf.kcd[gid] = kc / cdt;
+  D.cf.kdx[gid] = kc / I.dx;
+  D.cf.sac[gid] = s * I.a * I.c;
+  const double alpha = kc / cdt + s;
+  D.cf.ralpha[gid] = 1.0 / alpha;
+  D.cf.ratio[gid] = (sj / eps2 - s) / alpha;
 }
 
 // rho^n = sum_k w_k E^n_k (fixed angle order).
@@ -178,25 +197,25 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
   const int64_t N = I.N;
   const int k = L.k;
   const double v = D.v[I.ang_off + k], w = D.w[I.ang_off + k];
-  const double eps = I.eps, eps2 = eps * eps, cdt = I.c * I.dt, dx = I.dx;
   const bool inflow = I.bc == GRTE_BC_INFLOW;
   const double bL = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bL[I.ang_off + k];
   const double bR = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bR[I.ang_off + k];
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
   const double* x = xvec + co;
   double* xb = D.xb + eo;
-  const double *kc = D.cf.kc + co, *s = D.cf.s + co, *alpha = D.cf.alpha + co, *gl = D.cf.gl + co,
-               *gu = D.cf.gu + co, *gb = D.cf.gb + co, *dl = D.cf.dl + co;
+  const double *alpha = D.cf.alpha + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
+               *od = D.cf.od + co, *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co,
+               *sac = D.cf.sac + co;
   const double* En = D.E + eo;
   const double* On = D.O + oo;
   const double* Un = D.U + co;
   const double v2 = v * v;
-  const double ac = I.a * I.c;
+  const double two_eps = I.two_eps;
   // o_i = d_i eps^2 O^n_i/(c dt) at interior nodes (d at node j is dl[j])
   auto onode = [&](int64_t i) -> double {
     if (MODE == PRED_HOM) return 0.0;
     if (i <= 0 || i >= N) return 0.0;
-    return dl[i] * eps2 * On[i] / cdt;
+    return od[i] * On[i];
   };
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
     const double xj = x[j];
@@ -206,9 +225,9 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
     if (MODE != PRED_HOM) {
       // data part phi of kappa v (O_{j+1} - O_j)/dx (Eq. dis-pre1 node values, Eq. bc-pre walls)
       double Dj = onode(j + 1) - onode(j);
-      if (inflow && j == 0) Dj = 2.0 * onode(1) - 2.0 / eps * bL;
-      if (inflow && j == N - 1) Dj = -2.0 / eps * bR - 2.0 * onode(N - 1);
-      const double h = kc[j] * En[j] / cdt + s[j] * ac * Un[j] - kc[j] * v * Dj / dx;
+      if (inflow && j == 0) Dj = 2.0 * onode(1) - two_eps * bL;
+      if (inflow && j == N - 1) Dj = -two_eps * bR - 2.0 * onode(N - 1);
+      const double h = kcd[j] * En[j] + sac[j] * Un[j] - kdx[j] * v * Dj;
       r += h;
     }
     xb[j] = r;
@@ -223,28 +242,77 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
   //   O_i = o_i - d_i v (E_i - E_{i-1})/dx (interior), walls from Eq. bc-pre
   double* Sk = D.S + eo;
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    auto Oint = [&](int64_t i) { return onode(i) - dl[i] * v * ((x[i] - x[i - 1]) + (xb[i] - xb[i - 1])) / dx; };
+    auto Oint = [&](int64_t i) { return onode(i) - dlx[i] * v * ((x[i] - x[i - 1]) + (xb[i] - xb[i - 1])); };
     double OR, OLft;
     if (j + 1 <= N - 1) OR = Oint(j + 1);
-    else OR = inflow ? 2.0 / eps * ((x[N - 1] - bR) + xb[N - 1]) - Oint(N - 1) : 0.0;
+    else OR = inflow ? two_eps * ((x[N - 1] - bR) + xb[N - 1]) - Oint(N - 1) : 0.0;
     if (j >= 1) OLft = Oint(j);
-    else OLft = inflow ? 2.0 / eps * ((bL - x[0]) - xb[0]) - Oint(1) : 0.0;
+    else OLft = inflow ? two_eps * ((bL - x[0]) - xb[0]) - Oint(1) : 0.0;
     Sk[j] = w * v * (OR - OLft);
   }
 }
 
 // ----------------------------------------------------------------------------- instance (GMRES)
+// The per-instance Krylov work runs on a thread-block cluster of kCL CTAs: each CTA
+// owns a contiguous slice of the instance's cells; dot products are reduced through
+// distributed shared memory (fixed rank order, so every CTA gets the same value);
+// the preconditioner's tridiagonal solve is partitioned across the cluster by the
+// spike method (local solves plus a 2*kCL interface system).
+constexpr int kCL = 8;
+
 struct PrecCoef {  // A + (A/alpha) (wv2 Gint + wv Gbdry)
-  const double *A, *alpha, *gl, *gu, *gb;
+  const double *A, *gl, *gu, *gb, *ralpha;
   double wv, wv2;
   int64_t N;
-  __device__ double f(int64_t j) const { return A[j] / alpha[j]; }
+  __device__ double f(int64_t j) const { return A[j] * ralpha[j]; }
   __device__ double a(int64_t j) const { return j > 0 ? -f(j) * wv2 * gl[j] : 0.0; }
   __device__ double c(int64_t j) const { return j < N - 1 ? -f(j) * wv2 * gu[j] : 0.0; }
   __device__ double b(int64_t j) const { return A[j] + f(j) * (wv2 * (gl[j] + gu[j]) + wv * gb[j]); }
 };
 
-__device__ double block_sum(double v, double* red) {
+struct SliceCoef {  // the rows [c0, c0+n) of a system, decoupled from the rest
+  PrecCoef p;
+  int64_t c0, n;
+  __device__ double a(int64_t j) const { return j > 0 ? p.a(c0 + j) : 0.0; }
+  __device__ double c(int64_t j) const { return j < n - 1 ? p.c(c0 + j) : 0.0; }
+  __device__ double b(int64_t j) const { return p.b(c0 + j); }
+};
+
+struct Slice {
+  int nact;        // CTAs that own cells (>= 1)
+  int64_t c0, n;   // this CTA's cells [c0, c0+n) (n = 0 if rank >= nact)
+};
+
+__device__ __forceinline__ Slice slice_of(int64_t N, int rank) {
+  Slice sl;
+  int64_t half = N / 2;
+  sl.nact = (int)(half < kCL ? half : kCL);
+  if (rank >= sl.nact) { sl.c0 = N; sl.n = 0; return sl; }
+  const int64_t base = N / sl.nact, rem = N % sl.nact;
+  sl.c0 = rank * base + (rank < rem ? rank : rem);
+  sl.n = base + (rank < rem ? 1 : 0);
+  return sl;
+}
+
+// Reduced-system storage of the preconditioner: kCL slices, each tri_red_size(slice).
+__host__ __device__ inline int64_t prec_red_size(int64_t N) {
+  int64_t half = N / 2;
+  int nact = (int)(half < kCL ? half : kCL);
+  int64_t base = N / nact;
+  return (int64_t)kCL * tri_red_size(base + 1);
+}
+
+struct GmresSmem {
+  TriSmem<double> tri;
+  double red[32];
+  double part[2][kMaxRestart + 2];   // double-buffered partial sums exchanged by DSMEM
+  double ends[6];                    // y_first, y_last, g_first, g_last, h_first, h_last
+  double xlr[2];                     // interface values left of and right of this slice
+  double hcol[kMaxRestart + 2];
+  double y[kMaxRestart];
+};
+
+__device__ double cta_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
@@ -255,28 +323,143 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-// z = P^{-1} r, P the single-effective-angle Schur operator:
-//   u = (A + (1 + beta/alpha) Gbar)^{-1} (beta/alpha) r,  z = (r - Gbar u)/alpha,
-//   Gbar = sum_k w_k G_k, beta = A - alpha.
-template <bool FACTOR>
-__device__ void prec_apply(const Dev& D, const Inst& I, const double* r, double* z, double* work,
-                           TriSmem<double>& sm) {
-  const int64_t N = I.N, co = I.cell_off;
-  const double *A = D.cf.A + co, *alpha = D.cf.alpha + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co,
-               *gb = D.cf.gb + co;
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) work[j] = (A[j] - alpha[j]) / alpha[j] * r[j];
-  __syncthreads();
-  PrecCoef pc{A, alpha, gl, gu, gb, I.wv, I.wv2, N};
-  tri_solve<FACTOR>(pc, N, work, D.pF + 4 * co, D.pRd + I.red_off, sm);
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    const double uj = work[j], ul = j > 0 ? work[j - 1] : 0.0, ur = j < N - 1 ? work[j + 1] : 0.0;
-    const double Gu = I.wv2 * (gl[j] * (uj - ul) + gu[j] * (uj - ur)) + I.wv * gb[j] * uj;
-    z[j] = (r[j] - Gu) / alpha[j];
+// Sum nv per-CTA partial values over the cluster (fixed rank order).  `buf` selects
+// the half of the double buffer; two consecutive calls must use different halves.
+__device__ void cluster_sums(cg::cluster_group& cl, GmresSmem& sm, int buf, const double* mine, int nv,
+                             double* out) {
+  if (threadIdx.x < nv) sm.part[buf][threadIdx.x] = mine[threadIdx.x];
+  cl.sync();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int r = 0; r < kCL; ++r) t += cl.map_shared_rank(&sm.part[buf][0], r)[threadIdx.x];
+    out[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
-// Angular sum of a pass: flux_j = kappa_j/dx sum_k S[k][j].
+// Max of nv per-CTA values over the cluster.
+__device__ void cluster_maxs(cg::cluster_group& cl, GmresSmem& sm, int buf, const double* mine, int nv,
+                             double* out) {
+  if (threadIdx.x < nv) sm.part[buf][threadIdx.x] = mine[threadIdx.x];
+  cl.sync();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int r = 0; r < kCL; ++r) t = fmax(t, cl.map_shared_rank(&sm.part[buf][0], r)[threadIdx.x]);
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+__device__ double cta_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  return t;
+}
+
+// z = P^{-1} r on this CTA's slice, P the single-effective-angle Schur operator:
+//   u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) r,  z = (r - Gbar u)/alpha,
+//   Gbar = sum_k w_k G_k, beta = A - alpha.
+// The tridiagonal solve is split over the cluster: each slice solves its own rows
+// (y), and in FACTOR mode also the two spike vectors g, h (its response to the
+// coupling with the neighbouring slices); the 2*nact end values then give the
+// slice-boundary unknowns, and u = y - u_left g - u_right h.
+template <bool FACTOR>
+__device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int rank, cg::cluster_group& cl,
+                              const double* r, double* z, double* work, GmresSmem& sm) {
+  const int64_t N = I.N, co = I.cell_off, c0 = sl.c0, n = sl.n;
+  const double *A = D.cf.A + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
+               *ratio = D.cf.ratio + co, *ralpha = D.cf.ralpha + co;
+  double* pg = D.pG + co;
+  double* ph = D.pH + co;
+  PrecCoef pc{A, gl, gu, gb, ralpha, I.wv, I.wv2, N};
+  SliceCoef sc{pc, c0, n};
+  double* F = D.pF + 4 * (co + c0);
+  double* Rd = D.pRd + I.red_off + (int64_t)rank * (prec_red_size(N) / kCL);
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) work[c0 + j] = ratio[c0 + j] * r[c0 + j];
+  __syncthreads();
+  if (n > 0) {
+    tri_solve<FACTOR>(sc, n, work + c0, F, Rd, sm.tri);
+    if (FACTOR) {
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        pg[c0 + j] = (j == 0) ? pc.a(c0) : 0.0;
+        ph[c0 + j] = (j == n - 1) ? pc.c(c0 + n - 1) : 0.0;
+      }
+      __syncthreads();
+      tri_solve<false>(sc, n, pg + c0, F, Rd, sm.tri);
+      tri_solve<false>(sc, n, ph + c0, F, Rd, sm.tri);
+    }
+    if (threadIdx.x == 0) {
+      sm.ends[0] = work[c0];
+      sm.ends[1] = work[c0 + n - 1];
+      sm.ends[2] = pg[c0];
+      sm.ends[3] = pg[c0 + n - 1];
+      sm.ends[4] = ph[c0];
+      sm.ends[5] = ph[c0 + n - 1];
+    }
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    // interface unknowns X[2q] = u at the first cell of slice q, X[2q+1] = at its last:
+    //   X[2q]   + g_first(q) X[2q-1] + h_first(q) X[2q+2] = y_first(q)
+    //   X[2q+1] + g_last(q)  X[2q-1] + h_last(q)  X[2q+2] = y_last(q)
+    const int na = sl.nact, m2 = 2 * na;
+    double Mx[2 * kCL][2 * kCL + 1];
+    for (int i = 0; i < m2; ++i)
+      for (int j = 0; j <= m2; ++j) Mx[i][j] = 0.0;
+    for (int q = 0; q < na; ++q) {
+      const double* e = cl.map_shared_rank(&sm.ends[0], q);
+      for (int t = 0; t < 2; ++t) {
+        const int row = 2 * q + t;
+        Mx[row][row] = 1.0;
+        if (q > 0) Mx[row][2 * q - 1] += e[2 + t];
+        if (q < na - 1) Mx[row][2 * q + 2] += e[4 + t];
+        Mx[row][m2] = e[t];
+      }
+    }
+    for (int col = 0; col < m2; ++col) {   // Gaussian elimination, partial pivoting
+      int piv = col;
+      for (int i = col + 1; i < m2; ++i)
+        if (fabs(Mx[i][col]) > fabs(Mx[piv][col])) piv = i;
+      if (piv != col)
+        for (int j = 0; j <= m2; ++j) { double t = Mx[col][j]; Mx[col][j] = Mx[piv][j]; Mx[piv][j] = t; }
+      const double inv = 1.0 / Mx[col][col];
+      for (int i = col + 1; i < m2; ++i) {
+        const double f = Mx[i][col] * inv;
+        if (f != 0.0)
+          for (int j = col; j <= m2; ++j) Mx[i][j] -= f * Mx[col][j];
+      }
+    }
+    double X[2 * kCL];
+    for (int i = m2 - 1; i >= 0; --i) {
+      double t = Mx[i][m2];
+      for (int j = i + 1; j < m2; ++j) t -= Mx[i][j] * X[j];
+      X[i] = t / Mx[i][i];
+    }
+    sm.xlr[0] = (rank > 0 && rank < na) ? X[2 * rank - 1] : 0.0;
+    sm.xlr[1] = (rank < na - 1) ? X[2 * rank + 2] : 0.0;
+  }
+  __syncthreads();
+  const double ul = sm.xlr[0], ur = sm.xlr[1];
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+    work[c0 + j] = work[c0 + j] - ul * pg[c0 + j] - ur * ph[c0 + j];
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const int64_t g = c0 + j;
+    const double uj = work[g];
+    const double uL = g > 0 ? (j > 0 ? work[g - 1] : ul) : 0.0;
+    const double uR = g < N - 1 ? (j < n - 1 ? work[g + 1] : ur) : 0.0;
+    const double Gu = I.wv2 * (gl[g] * (uj - uL) + gu[g] * (uj - uR)) + I.wv * gb[g] * uj;
+    z[g] = (r[g] - Gu) * ralpha[g];
+  }
+  __syncthreads();
+}
+
+// Angular sum of a pass: sum_k S[k][j] (fixed angle order).
 __device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t j) {
   double acc = 0.0;
   for (int k = 0; k < I.M; ++k) acc += D.S[I.elem_off + (int64_t)k * I.N + j];
@@ -285,62 +468,80 @@ __device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t 
 
 enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
 
-// GMRES bookkeeping for one instance per CTA (restart length m).  Vectors live in
-// global memory: x (current iterate), V[0..m] (Krylov basis), z (scratch).
+// GMRES bookkeeping, one cluster per instance (restart length m, left
+// preconditioned).  Vectors live in global memory: x (iterate), V[0..m] (Krylov
+// basis), z (scratch).  Scalars (H, g, Givens) are computed identically by every
+// CTA; rank 0 stores them.
 template <int MODE>
-__global__ void __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
-  __shared__ TriSmem<double> sm;
-  __shared__ double red[32];
-  __shared__ double hcol[kMaxRestart + 2];
-  const int ii = blockIdx.x;
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
+  __shared__ GmresSmem sm;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int ii = blockIdx.x / kCL;
   const Inst I = D.inst[ii];
   const int64_t N = I.N, co = I.cell_off;
+  const Slice sl = slice_of(N, rank);
+  const int64_t c0 = sl.c0, n = sl.n;
   const int m = D.m;
   double* x = D.gx + co;
   double* z = D.gz + co;
   double* work = D.xb + I.elem_off;          // the line buffers are free between passes
-  double* V = D.gV;                          // V_i at V + i*ncell_total ... stride given below
+  const int64_t ncell_tot = D.gz - D.gx;     // gz = gx + ncell_total (allocation layout)
+  auto Vi = [&](int i) { return D.gV + (int64_t)i * ncell_tot + co; };
   double* H = D.gH + (int64_t)ii * (kMaxRestart + 1) * kMaxRestart;
   double* g = D.gg + (int64_t)ii * (kMaxRestart + 1);
   double* cs = D.gcs + (int64_t)ii * kMaxRestart;
   double* sn = D.gsn + (int64_t)ii * kMaxRestart;
-  const int64_t ncell_tot = D.gz - D.gx;     // gz = gx + ncell_total (allocation layout)
-  auto Vi = [&](int i) { return V + (int64_t)i * ncell_tot + co; };
-  const double *kc = D.cf.kc + co, *alpha = D.cf.alpha + co, *s = D.cf.s + co;
-  const double cdt = I.c * I.dt, ac = I.a * I.c;
+  const double *alpha = D.cf.alpha + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *sac = D.cf.sac + co;
 
   if (MODE == G_RESTART_FIRST || MODE == G_RESTART) {
-    if (MODE == G_RESTART && D.gdone[ii]) return;
+    if (MODE == G_RESTART && D.gdone[ii]) return;        // uniform over the cluster
     // r = -R(x) from the FULL pass that just ran at x
     double* r = z;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-      const double Rj = alpha[j] * x[j] - kc[j] * D.rho_n[co + j] / cdt - s[j] * ac * D.U[co + j] +
-                        kc[j] * flux_sum(D, I, j) / I.dx;
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
+      const double fl = flux_sum(D, I, j);
+      const double Rj = alpha[j] * x[j] - kcd[j] * D.rho_n[co + j] - sac[j] * D.U[co + j] + kdx[j] * fl;
       r[j] = -Rj;
-      D.Fs[co + j] = flux_sum(D, I, j);     // F* of the current iterate (final at convergence)
+      D.Fs[co + j] = fl;                    // F* of the current iterate (final at convergence)
     }
+    // per-cell weights of the stopping test: the preconditioned residual relative to
+    // |x_j| (floor 1e-13 max|x|), so that the test bounds every cell's relative
+    // correction and not only the large cells' share of a 2-norm
+    double xm = 0.0;
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) xm = fmax(xm, fabs(x[j]));
+    xm = cta_max(xm, sm.red);
+    __shared__ double xms[1];
+    cluster_maxs(cl, sm, 0, &xm, 1, xms);
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
+      D.gw[co + j] = 1.0 / (fabs(x[j]) + 1e-13 * xms[0] + 1e-300);
     __syncthreads();
     double* v0 = Vi(0);
-    if (MODE == G_RESTART_FIRST) prec_apply<true>(D, I, r, v0, work, sm);
-    else prec_apply<false>(D, I, r, v0, work, sm);
-    double nrm = 0.0, xn = 0.0;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-      nrm += v0[j] * v0[j];
-      xn += x[j] * x[j];
+    if (MODE == G_RESTART_FIRST) prec_apply_cl<true>(D, I, sl, rank, cl, r, v0, work, sm);
+    else prec_apply_cl<false>(D, I, sl, rank, cl, r, v0, work, sm);
+    double loc[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
+      loc[0] += v0[j] * v0[j];
+      loc[1] += x[j] * x[j];
+      loc[2] = fmax(loc[2], fabs(v0[j]) * D.gw[co + j]);
     }
-    nrm = sqrt(block_sum(nrm, red));
-    xn = sqrt(block_sum(xn, red));
-    // Converged when the true preconditioned residual is below rtol |x|.  Restarted
-    // GMRES cannot go below the rounding floor of the residual evaluation itself (a
-    // sum of terms much larger than the residual); a restart cycle that did not
-    // reduce it by 4x while it is below 1e-9 |x| has reached that floor and stops.
-    bool conv = !(nrm > D.rtol * xn);   // also true for nrm == 0
-    if (MODE == G_RESTART && !conv && nrm >= 0.25 * D.gbeta[ii] && nrm <= 1e-9 * xn) conv = true;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    loc[0] = cta_sum(loc[0], sm.red);
+    loc[1] = cta_sum(loc[1], sm.red);
+    loc[2] = cta_max(loc[2], sm.red);
+    __shared__ double tots[2], tmax[1];
+    cluster_sums(cl, sm, 1, loc, 2, tots);
+    cluster_maxs(cl, sm, 0, loc + 2, 1, tmax);
+    const double nrm = sqrt(tots[0]), xn = sqrt(tots[1]), rinf = tmax[0];
+    // Converged when every cell's relative preconditioned correction is below rtol.
+    // Restarted GMRES cannot go below the rounding floor of the residual evaluation
+    // itself (a sum of terms much larger than the residual): a restart cycle that
+    // did not reduce it by 4x while it is below 1e-9 has reached that floor.
+    bool conv = !(rinf > D.rtol);   // also true for rinf == 0
+    if (MODE == G_RESTART && !conv && rinf <= 1e-9 && rinf >= 0.25 * D.gbeta[ii]) conv = true;
+    if (rank == 0 && threadIdx.x == 0) {
       if (MODE == G_RESTART) D.gcycles[ii] += 1;
-      D.gbeta[ii] = nrm;
+      D.gbeta[ii] = rinf;
       D.gxn[ii] = xn;
+      D.gestconv[ii] = 0;
       if (conv) {
         D.gactive[ii] = 0;
         D.gdone[ii] = 1;
@@ -355,78 +556,96 @@ __global__ void __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
     }
     if (!conv) {
       const double inv = 1.0 / nrm;
-      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) v0[j] *= inv;
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) v0[j] *= inv;
     }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
     return;
   }
 
   if (MODE == G_ARNOLDI) {
-    if (!D.gactive[ii]) return;
+    if (!D.gactive[ii]) return;                           // uniform over the cluster
     // C v_j = alpha v_j + kappa/dx * sum_k S_k  (the HOM pass just ran on v_j)
     const double* vj = Vi(jcol);
     double* cv = z;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x)
-      cv[j] = alpha[j] * vj[j] + kc[j] * flux_sum(D, I, j) / I.dx;
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
+      cv[j] = alpha[j] * vj[j] + kdx[j] * flux_sum(D, I, j);
     __syncthreads();
     double* wv = Vi(jcol + 1);
-    prec_apply<false>(D, I, cv, wv, work, sm);
-    // modified Gram-Schmidt
-    for (int i = 0; i <= jcol; ++i) {
-      const double* vi = Vi(i);
-      double d = 0.0;
-      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) d += wv[j] * vi[j];
-      d = block_sum(d, red);
-      for (int64_t j = threadIdx.x; j < N; j += blockDim.x) wv[j] -= d * vi[j];
-      if (threadIdx.x == 0) hcol[i] = d;
+    prec_apply_cl<false>(D, I, sl, rank, cl, cv, wv, work, sm);
+    // classical Gram-Schmidt, twice (CGS2): two cluster reductions instead of j+1
+    __shared__ double dots[kMaxRestart + 2];
+    double hc[kMaxRestart + 2];
+    for (int i = 0; i <= jcol + 1; ++i) hc[i] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      double loc[kMaxRestart + 1];
+      for (int i = 0; i <= jcol; ++i) {
+        const double* vi = Vi(i);
+        double d = 0.0;
+        for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) d += wv[j] * vi[j];
+        loc[i] = cta_sum(d, sm.red);
+      }
+      cluster_sums(cl, sm, pass, loc, jcol + 1, dots);
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
+        double t = wv[j];
+        for (int i = 0; i <= jcol; ++i) t -= dots[i] * Vi(i)[j];
+        wv[j] = t;
+      }
+      for (int i = 0; i <= jcol; ++i) hc[i] += dots[i];
       __syncthreads();
     }
-    double nrm = 0.0;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) nrm += wv[j] * wv[j];
-    nrm = sqrt(block_sum(nrm, red));
+    double loc1 = 0.0;
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) loc1 += wv[j] * wv[j];
+    loc1 = cta_sum(loc1, sm.red);
+    __shared__ double nn[1];
+    cluster_sums(cl, sm, 0, &loc1, 1, nn);
+    const double nrm = sqrt(nn[0]);
     if (threadIdx.x == 0) {
-      hcol[jcol + 1] = nrm;
-      // apply previous Givens rotations, then a new one
-      for (int i = 0; i < jcol; ++i) {
-        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
-        hcol[i] = t;
+      hc[jcol + 1] = nrm;
+      for (int i = 0; i < jcol; ++i) {           // previous Givens rotations
+        const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+        hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+        hc[i] = t;
       }
-      const double a0 = hcol[jcol], b0 = hcol[jcol + 1];
+      const double a0 = hc[jcol], b0 = hc[jcol + 1];
       const double rr = hypot(a0, b0);
-      const double c0 = rr > 0.0 ? a0 / rr : 1.0, s0 = rr > 0.0 ? b0 / rr : 0.0;
-      cs[jcol] = c0;
-      sn[jcol] = s0;
-      hcol[jcol] = rr;
-      hcol[jcol + 1] = 0.0;
-      g[jcol + 1] = -s0 * g[jcol];
-      g[jcol] = c0 * g[jcol];
-      for (int i = 0; i <= jcol; ++i) H[i * kMaxRestart + jcol] = hcol[i];
-      D.gk[ii] = jcol + 1;
-      D.gits[ii] += 1;
-      // estimate of the new preconditioned residual against the iterate norm
-      if (fabs(g[jcol + 1]) <= 0.5 * D.rtol * D.gxn[ii] || nrm == 0.0 || jcol + 1 >= m) D.gactive[ii] = 0;
+      const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
+      hc[jcol] = rr;
+      const double gj = g[jcol];
+      const double gnext = -s0g * gj;
+      if (rank == 0) {
+        cs[jcol] = c0g;
+        sn[jcol] = s0g;
+        g[jcol + 1] = gnext;
+        g[jcol] = c0g * gj;
+        for (int i = 0; i <= jcol; ++i) H[i * kMaxRestart + jcol] = hc[i];
+        D.gk[ii] = jcol + 1;
+        D.gits[ii] += 1;
+        // GMRES's own (2-norm) estimate; the per-cell test runs on the true residual
+        const bool est = fabs(gnext) <= 0.05 * D.rtol * D.gxn[ii];
+        if (est) D.gestconv[ii] = 1;
+        if (est || nrm == 0.0 || jcol + 1 >= m) D.gactive[ii] = 0;
+      }
     }
-    __syncthreads();
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) wv[j] *= inv;
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) wv[j] *= inv;
+    cl.sync();
     return;
   }
 
   if (MODE == G_UPDATE) {
     if (D.gdone[ii]) return;
-    __shared__ double y[kMaxRestart];
     const int kk = D.gk[ii];
     if (threadIdx.x == 0) {
       for (int i = kk - 1; i >= 0; --i) {
         double t = g[i];
-        for (int l = i + 1; l < kk; ++l) t -= H[i * kMaxRestart + l] * y[l];
-        y[i] = t / H[i * kMaxRestart + i];
+        for (int l = i + 1; l < kk; ++l) t -= H[i * kMaxRestart + l] * sm.y[l];
+        sm.y[i] = t / H[i * kMaxRestart + i];
       }
     }
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
       double t = x[j];
-      for (int i = 0; i < kk; ++i) t += y[i] * Vi(i)[j];
+      for (int i = 0; i < kk; ++i) t += sm.y[i] * Vi(i)[j];
       x[j] = t;
     }
     return;
@@ -505,7 +724,7 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   const int64_t N = I.N;
   const int k = L.k;
   const double v = D.v[I.ang_off + k];
-  const double eps = I.eps, eps2 = eps * eps, cdt = I.c * I.dt, dx = I.dx, ac = I.a * I.c;
+  const double eps = I.eps, ac = I.a * I.c;
   const bool inflow = I.bc == GRTE_BC_INFLOW;
   const double bL = inflow ? D.bL[I.ang_off + k] : 0.0, bR = inflow ? D.bR[I.ang_off + k] : 0.0;
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
@@ -514,20 +733,21 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   const double* T = D.T + co;   // T^{n+1}
   double* xb = D.xb + eo;
   double* on = D.onode + oo;
-  const double *kc = D.cf.kc + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
-               *dl = D.cf.dl + co;
+  const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
+               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co;
+  const double two_eps = I.two_eps, inv_eps = I.inv_eps;
   auto U = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
   for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
     double o = 0.0;
-    if (i >= 1 && i <= N - 1) o = dl[i] * (eps2 * O[i] / cdt - ac * v * (U(i) - U(i - 1)) / dx);
+    if (i >= 1 && i <= N - 1) o = od[i] * O[i] - dlx[i] * ac * v * (U(i) - U(i - 1));
     on[i] = o;
   }
   __syncthreads();
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
     double Dj = on[j + 1] - on[j];
-    if (inflow && j == 0) Dj = 2.0 * on[1] - 2.0 / eps * (bL - ac * U(0));
-    if (inflow && j == N - 1) Dj = 2.0 / eps * (ac * U(N - 1) - bR) - 2.0 * on[N - 1];
-    xb[j] = (kc[j] * (E[j] - ac * U(j)) / cdt - kc[j] * v * Dj / dx) / eps;
+    if (inflow && j == 0) Dj = 2.0 * on[1] - two_eps * (bL - ac * U(0));
+    if (inflow && j == N - 1) Dj = two_eps * (ac * U(N - 1) - bR) - 2.0 * on[N - 1];
+    xb[j] = (kcd[j] * (E[j] - ac * U(j)) - kdx[j] * v * Dj) * inv_eps;
   }
   __syncthreads();
   LineCoef cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
@@ -535,11 +755,11 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   // projection
   for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
     double Oi;
-    auto Oint = [&](int64_t n) { return on[n] - dl[n] * eps * v * (xb[n] - xb[n - 1]) / dx; };
+    auto Oint = [&](int64_t n) { return on[n] - dlx[n] * eps * v * (xb[n] - xb[n - 1]); };
     if (i >= 1 && i <= N - 1) Oi = Oint(i);
     else if (!inflow) Oi = 0.0;
-    else if (i == 0) Oi = 2.0 / eps * (bL - ac * U(0)) - 2.0 * xb[0] - Oint(1);
-    else Oi = 2.0 / eps * (ac * U(N - 1) - bR) + 2.0 * xb[N - 1] - Oint(N - 1);
+    else if (i == 0) Oi = two_eps * (bL - ac * U(0)) - 2.0 * xb[0] - Oint(1);
+    else Oi = two_eps * (ac * U(N - 1) - bR) + 2.0 * xb[N - 1] - Oint(N - 1);
     O[i] = Oi;
   }
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) E[j] = ac * U(j) + eps * xb[j];
@@ -668,7 +888,7 @@ extern "C" {
 void grte_default_options(grte_options* o) {
   if (!o) return;
   o->precision = GRTE_FP64;
-  o->krylov_rtol = 1e-14;
+  o->krylov_rtol = 1e-13;
   o->krylov_restart = 10;
   o->krylov_maxcycles = 6;
   o->newton_maxit = 60;
@@ -745,6 +965,8 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     }
     I.wv = wv;
     I.wv2 = wv2;
+    I.two_eps = 2.0 / p.eps;
+    I.inv_eps = 1.0 / p.eps;
     I.cell_off = coff;
     I.elem_off = eoff;
     I.nelem_off = noff;
@@ -755,7 +977,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
       h->lines.push_back(Line{i, k, roff});
       roff += tri_red_size(p.nx);
     }
-    poff += tri_red_size(p.nx);
+    poff += prec_red_size(p.nx);
     coff += p.nx;
     eoff += p.nx * p.n_angle;
     noff += (p.nx + 1) * p.n_angle;
@@ -792,8 +1014,10 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.rho_n, nc); AL(D.rho_s, nc); AL(D.Fs, nc); AL(D.Us, nc); AL(D.newton_its, nc);
   AL(D.cf.kc, nc); AL(D.cf.s, nc); AL(D.cf.alpha, nc); AL(D.cf.A, nc); AL(D.cf.gam, nc);
   AL(D.cf.gl, nc); AL(D.cf.gu, nc); AL(D.cf.gb, nc); AL(D.cf.dl, nc);
+  AL(D.cf.od, nc); AL(D.cf.dlx, nc); AL(D.cf.kcd, nc); AL(D.cf.kdx, nc); AL(D.cf.sac, nc);
+  AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc);
   AL(D.xb, ne); AL(D.S, ne); AL(D.F, 4 * ne); AL(D.Rd, h->nred); AL(D.onode, nn);
-  AL(D.pF, 4 * nc); AL(D.pRd, h->npred);
+  AL(D.pF, 4 * nc); AL(D.pRd, h->npred); AL(D.pG, nc); AL(D.pH, nc); AL(D.gw, nc);
   // x, z contiguous so that the GMRES kernel can recover the total cell count
   double* xz = nullptr;
   AL(xz, 2 * nc);
@@ -807,6 +1031,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.gbeta, n_inst);
   AL(D.gxn, n_inst);
   AL(D.gactive, n_inst); AL(D.gk, n_inst); AL(D.gdone, n_inst); AL(D.gits, n_inst); AL(D.gcycles, n_inst);
+  AL(D.gestconv, n_inst);
   AL(D.status, n_inst);
 #undef AL
   D.inst = h->d_inst;
@@ -876,16 +1101,25 @@ static grte_status step_once(grte_t h) {
   CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
   CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
   LAUNCH(GRTE_K_PRED_FACTOR, k_pred_line<PRED_FULL_FACTOR><<<nl, kTriThreads, 0, st>>>(D, D.gx));
-  LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART_FIRST><<<ni, kTriThreads, 0, st>>>(D, 0));
+  LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART_FIRST><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
       LAUNCH(GRTE_K_PRED_HOM, k_pred_line<PRED_HOM><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc));
-      LAUNCH(GRTE_K_GMRES, k_gmres<G_ARNOLDI><<<ni, kTriThreads, 0, st>>>(D, j));
+      LAUNCH(GRTE_K_GMRES, k_gmres<G_ARNOLDI><<<ni * kCL, kTriThreads, 0, st>>>(D, j));
+      // a Krylov direction pass costs far more than a round trip: after the first
+      // iteration, stop launching once no instance is still iterating
+      if (j >= 1 && j + 1 < D.m) {
+        CK(cudaMemcpyAsync(h->h_flags, D.gactive, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int i = 0; i < ni; ++i) any = any || h->h_flags[i];
+        if (!any) break;
+      }
     }
-    LAUNCH(GRTE_K_GMRES, k_gmres<G_UPDATE><<<ni, kTriThreads, 0, st>>>(D, 0));
+    LAUNCH(GRTE_K_GMRES, k_gmres<G_UPDATE><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
     LAUNCH(GRTE_K_PRED_FULL, k_pred_line<PRED_FULL><<<nl, kTriThreads, 0, st>>>(D, D.gx));
-    LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART><<<ni, kTriThreads, 0, st>>>(D, 0));
+    LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -105,7 +105,7 @@ def _f64(a):
 class Grte:
     """Handle over n independent 1D instances (grte_create_1d)."""
 
-    def __init__(self, instances, precision=FP64, krylov_rtol=1e-14, krylov_restart=10,
+    def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
                  krylov_maxcycles=6, newton_maxit=60, stream=None):
         L = lib()
         self._keep = []
