@@ -79,6 +79,7 @@ typedef struct {
   int krylov_restart;    /* GMRES restart length (10)                                        */
   int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (6)            */
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */
+  int energy_every;      /* 1: accumulate the energy sums of grte_get_energy every step; 0 off */
   void* stream;          /* cudaStream_t to run on; NULL: the library makes its own          */
 } grte_options;
 
@@ -122,6 +123,14 @@ grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t le
 /* Intermediate per-cell results of the last step: which = 0 U*, 1 F* =
  * sum_k w_k v_k (O*_{j+1,k} - O*_{j,k}), 2 rho*, 3 Newton iterations (as double). */
 grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t len);
+/* Energy diagnostics of instance `inst` (FP64 sums on the device; Eq. energybalance and
+ * Eq. semiconservative of Sec. 3, 1D): out[0] = sum_j dx (rho_j/c + Cv T_j) now;
+ * out[1] = sum over the steps taken with energy_every = 1 of dt sum_j F*_j (the
+ * telescoped wall flux sum_k w_k v_k (O*_N - O*_0) of the prediction);
+ * out[2] = sum over those steps of dt sum_j eps^2/(c sig_j dt + eps^2) (F*_j - F^{n+1}_j),
+ * F = sum_k w_k v_k (O_{j+1,k} - O_{j,k}).  For a T-independent sigma
+ * out[0] + out[1] - out[2] is constant in time (n = 3). */
+grte_status grte_get_energy(grte_t h, int inst, double* out, size_t n);
 /* Quadrature actually used by instance `inst` (M values each). */
 grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len);
 
@@ -130,7 +139,7 @@ grte_status grte_stats(grte_t h, grte_stats_t* st);
 /* Kernel ids for per-kernel timing. */
 enum { GRTE_K_CELL_COEF = 0, GRTE_K_RHO = 1, GRTE_K_PRED_FACTOR = 2, GRTE_K_PRED_HOM = 3,
        GRTE_K_PRED_FULL = 4, GRTE_K_GMRES = 5, GRTE_K_NEWTON = 6, GRTE_K_CORR = 7,
-       GRTE_K_PROJECT = 8, GRTE_NKERNELS = 9 };
+       GRTE_K_PROJECT = 8, GRTE_K_ENERGY = 9, GRTE_NKERNELS = 10 };
 /* Start recording a CUDA event pair around every launch of the kernels whose bit
  * (1 << id) is set in kernel_mask, on the handle's stream (device-side timing). */
 grte_status grte_profile_begin(grte_t h, uint32_t kernel_mask);

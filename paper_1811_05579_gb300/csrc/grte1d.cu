@@ -82,6 +82,7 @@ struct Dev {
   double *gx, *gV, *gz, *gH, *gg, *gcs, *gsn, *gbeta, *gxn;
   int *gactive, *gk, *gdone, *gits, *gcycles, *gestconv;
   int* status;
+  double* energy;   // 3 per instance
   int m;  // restart length
   double rtol;
   int newton_maxit;
@@ -765,6 +766,42 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) E[j] = ac * U(j) + eps * xb[j];
 }
 
+// Energy sums of one instance per CTA (FP64, fixed reduction order):
+//   acc[0] = sum_j dx (rho_j/c + Cv T_j)                     (energy now)
+//   acc[1] += dt sum_j F*_j                                  (wall flux of the prediction)
+//   acc[2] += dt sum_j eps^2/(c sig_j dt + eps^2) (F*_j - F^{n+1}_j)   (Eq. semiconservative defect)
+__global__ void __launch_bounds__(kTriThreads) k_energy(Dev D, int accumulate) {
+  __shared__ double red[32];
+  const int ii = blockIdx.x;
+  const Inst I = D.inst[ii];
+  const int64_t N = I.N, co = I.cell_off;
+  double e = 0.0, f = 0.0, dft = 0.0;
+  const double eps2 = I.eps * I.eps, cdt = I.c * I.dt;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    double rho = 0.0, Fn = 0.0;
+    for (int k = 0; k < I.M; ++k) {
+      const double w = D.w[I.ang_off + k], v = D.v[I.ang_off + k];
+      rho += w * D.E[I.elem_off + (int64_t)k * N + j];
+      const double* O = D.O + I.nelem_off + (int64_t)k * (N + 1);
+      Fn += w * v * (O[j + 1] - O[j]);
+    }
+    e += I.dx * (rho / I.c + I.Cv * D.T[co + j]);
+    const double Fs = D.Fs[co + j];
+    f += Fs;
+    dft += eps2 / (cdt * D.sig[co + j] + eps2) * (Fs - Fn);
+  }
+  e = cta_sum(e, red);
+  f = cta_sum(f, red);
+  dft = cta_sum(dft, red);
+  if (threadIdx.x == 0) {
+    D.energy[3 * ii + 0] = e;
+    if (accumulate) {
+      D.energy[3 * ii + 1] += I.dt * f;
+      D.energy[3 * ii + 2] += I.dt * dft;
+    }
+  }
+}
+
 // U^{n+1} = (T^{n+1})^4 (Eq. dis-proj1)
 __global__ void k_project_U(Dev D, int64_t ncell) {
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -892,6 +929,7 @@ void grte_default_options(grte_options* o) {
   o->krylov_restart = 10;
   o->krylov_maxcycles = 6;
   o->newton_maxit = 60;
+  o->energy_every = 0;
   o->stream = nullptr;
 }
 
@@ -1033,6 +1071,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.gactive, n_inst); AL(D.gk, n_inst); AL(D.gdone, n_inst); AL(D.gits, n_inst); AL(D.gcycles, n_inst);
   AL(D.gestconv, n_inst);
   AL(D.status, n_inst);
+  AL(D.energy, 3 * (int64_t)n_inst);
 #undef AL
   D.inst = h->d_inst;
   D.lines = h->d_lines;
@@ -1143,6 +1182,7 @@ static grte_status step_once(grte_t h) {
   LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
   LAUNCH(GRTE_K_CORR, k_corr_line<<<nl, kTriThreads, 0, st>>>(D));
   LAUNCH(GRTE_K_PROJECT, k_project_U<<<cgrid, cb, 0, st>>>(D, nc));
+  if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<<<ni, kTriThreads, 0, st>>>(D, 1));
   CK(cudaGetLastError());
   return GRTE_OK;
 }
@@ -1267,6 +1307,18 @@ grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t le
       Ineg[j * I.M + k] = E[j * I.M + k] - I.eps * oc;
     }
   return s;
+}
+
+grte_status grte_get_energy(grte_t h, int inst, double* out, size_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !out || n != 3) return fail(h, GRTE_EINVAL, "bad instance, NULL output or n != 3");
+  if (!h->state_set) return fail(h, GRTE_ESTATE, "state not set");
+  // refresh the energy of the current state; the accumulated terms are untouched
+  k_energy<<<h->n_inst, kTriThreads, 0, h->stream>>>(h->D, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(out, h->D.energy + 3 * inst, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+  return GRTE_OK;
 }
 
 grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len) {

@@ -33,7 +33,8 @@ class Instance1D(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
-                ("newton_maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("newton_maxit", ctypes.c_int), ("energy_every", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -45,9 +46,9 @@ class Stats(ctypes.Structure):
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
             "grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O", "grte_get_I", "grte_get_stage",
             "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy",
-            "grte_profile_begin", "grte_profile_end", "grte_last_launches"]
+            "grte_profile_begin", "grte_profile_end", "grte_last_launches", "grte_get_energy"]
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
-           "project"]
+           "project", "energy"]
 
 
 def load_library(path=LIB_PATH):
@@ -75,6 +76,7 @@ def load_library(path=LIB_PATH):
     lib.grte_profile_end.argtypes = [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_size_t]
     lib.grte_last_launches.argtypes = [ctypes.c_void_p]
     lib.grte_last_launches.restype = ctypes.c_int64
+    lib.grte_get_energy.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
     return lib
 
 
@@ -106,7 +108,7 @@ class Grte:
     """Handle over n independent 1D instances (grte_create_1d)."""
 
     def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
-                 krylov_maxcycles=6, newton_maxit=60, stream=None):
+                 krylov_maxcycles=6, newton_maxit=60, energy_every=0, stream=None):
         L = lib()
         self._keep = []
         arr = (Instance1D * len(instances))()
@@ -131,6 +133,7 @@ class Grte:
         opt.krylov_restart = krylov_restart
         opt.krylov_maxcycles = krylov_maxcycles
         opt.newton_maxit = newton_maxit
+        opt.energy_every = energy_every
         opt.stream = stream
         h = ctypes.c_void_p()
         st = L.grte_create_1d(len(instances), arr, ctypes.byref(opt), ctypes.byref(h))
@@ -196,6 +199,11 @@ class Grte:
     def stage(self, inst, which, allow=()):
         out = np.empty(self.specs[inst]["nx"])
         self._check(lib().grte_get_stage(self.h, inst, which, _ptr(out), out.size), allow)
+        return out
+
+    def energy(self, inst):
+        out = np.empty(3)
+        self._check(lib().grte_get_energy(self.h, inst, _ptr(out), 3))
         return out
 
     def quadrature(self, inst):

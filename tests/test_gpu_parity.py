@@ -195,3 +195,44 @@ def test_full_size_slab_one_step(G):
     S1 = og.step(P, og.equilibrium_state(P, r.T0))
     check(h.T(0, allow=(5,)), S1.T, tol_cells(P), "T")
     h.close()
+
+
+def test_energy_sums_conserved_reflecting(G):
+    """Eq. energybalance summed over a reflecting slab with uniform T-independent sigma:
+    sum_j dx (rho_j/c + Cv T_j) is constant (FP64 sums on the device)."""
+    P, spec = make(200, 8, 1e-2, "const", "reflect", sig=2.0)
+    S = state(P, 5, equilibrium=True)
+    h = G.Grte([spec], energy_every=1)
+    h.set_state(0, S.T)
+    e0 = h.energy(0)[0]
+    assert abs(e0 - og.energy(P, S)) < 1e-13 * e0
+    h.step(6)
+    e = h.energy(0)
+    assert abs(e[0] - e0) < 1e-12 * e0
+    h.close()
+
+
+def test_energy_sums_balance_inflow(G):
+    """With inflow walls and uniform sigma, energy + dt sum F* - defect is constant
+    (Eq. semiconservative summed over cells), and each term matches the oracle."""
+    P, spec = make(150, 8, 1e-1, "const", "inflow", sig=3.0, bL=0.9, bR=0.2)
+    S = state(P, 6, equilibrium=True)
+    h = G.Grte([spec], energy_every=1)
+    h.set_state(0, S.T)
+    e0 = h.energy(0)
+    assert e0[1] == 0.0 and e0[2] == 0.0
+    fsum = 0.0
+    dsum = 0.0
+    for _ in range(4):
+        info = og.StepInfo()
+        S1 = og.step(P, S, info)
+        F1 = og.flux_div(P, S1.O)
+        fsum += P.dt * np.sum(info.Fstar)
+        dsum += P.dt * np.sum(P.eps ** 2 / (P.c * P.sig * P.dt + P.eps ** 2) * (info.Fstar - F1))
+        S = S1
+    h.step(4)
+    e = h.energy(0)
+    assert abs(e[0] - og.energy(P, S)) < 1e-12 * e[0]
+    assert abs(e[1] - fsum) < 1e-11 * max(abs(fsum), 1e-300)
+    assert abs((e[0] + e[1] - e[2]) - (e0[0])) < 1e-12 * e0[0]
+    h.close()
