@@ -34,6 +34,9 @@ FP64_PEAK_GFLOPS = 1250.0           # nominal GB300 FP64 (the profiling recipe's
 # (k_pred_line<HOM>): right-hand side 11, tridiagonal solve with stored factors 10,
 # flux of the two faces 10.
 HOM_FLOPS_PER_ELEM = 31
+# Bytes a binary32 line pass moves per line element with stored factors: 4 factors,
+# right-hand side written and solution read back, flux contribution written.
+LINE_BYTES_PER_ELEM_F32 = 4 * 4 + 2 * 4 + 4
 
 
 def workload_instances(name):
@@ -166,6 +169,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     runs, cfg = workload_instances(args.workload)
@@ -186,7 +191,8 @@ def main():
 
     stream = torch.cuda.current_stream()
     specs = specs_of(runs)
-    h = G.Grte(specs, stream=stream.cuda_stream)
+    prec = G.MIXED if args.precision == "mixed" else G.FP64
+    h = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
     for i, r in enumerate(runs):
         h.set_state(i, r.T0)
     updates_per_step = sum(r.nx * r.n_dir for r in runs)
@@ -251,46 +257,97 @@ def main():
     te = time.perf_counter() - t0
     e2e_val = updates_per_step * ke / te
 
+    # the same workload in FP64 (the plain form): timed the same way, and the
+    # temperature error of the benchmarked form against it after the same steps
+    cmp = None
+    if prec == G.MIXED and not args.no_fp64_compare:
+        hd = G.Grte(specs, precision=G.FP64, stream=stream.cuda_stream)
+        for i, r in enumerate(runs):
+            hd.set_state(i, r.T0)
+        hm = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
+        for i, r in enumerate(runs):
+            hm.set_state(i, r.T0)
+        for _ in range(args.warmup):
+            hd.step(1)
+            hm.step(1)
+        t64 = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hd.step(1)
+            e1.record(stream)
+            hm.step(1)
+            torch.cuda.synchronize()
+            t64 += e0.elapsed_time(e1)
+        errs = []
+        for i in range(len(runs)):
+            a_ = hm.T(i, allow=(5,))
+            b_ = hd.T(i, allow=(5,))
+            errs.append(float(np.max(np.abs(a_ - b_) / np.maximum(np.abs(b_), 1e-300))))
+        cmp = {"fp64_value": updates_per_step * args.steps / (t64 * 1e-3), "fp64_ms_per_step": t64 / args.steps,
+               "t_max_rel_err_vs_fp64": max(errs), "t_rel_err_per_run": errs,
+               "steps_compared": args.warmup + args.steps}
+        hd.close()
+        hm.close()
+
+    hbm_peak = 6800.0
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
     # dominant kernel (largest share of device time in the timed region)
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_n) = dom
     tot_prof = sum(v[0] for v in prof.values())
     nelem = sum(r.nx * (r.n_dir // 2) for r in runs)
     roof = None
-    if dom_name == "pred_hom":
+    avg_s = dom_ms / dom_n * 1e-3
+    if prec == G.FP64 and dom_name in ("pred_hom", "pred_full"):
         flops = HOM_FLOPS_PER_ELEM * nelem
-        achieved = flops / (dom_ms / dom_n * 1e-3) / 1e9
-        roof = {"kernel": "k_pred_line<HOM>", "bound": "alu", "achieved": achieved,
+        achieved = flops / avg_s / 1e9
+        roof = {"kernel": "k_pred_line<%s,double>" % dom_name[5:].upper(), "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": None, "avg_launch_us": dom_ms / dom_n * 1e3, "launches": dom_n}
+                "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s)",
+                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n}
+    elif dom_name in ("pred_hom", "pred_full", "pred_factor", "corr"):
+        # binary32 line pass: bytes it must move per line element with stored factors
+        # (4 factors + right-hand side/solution buffer write and read + flux out, 4 B each)
+        byts = LINE_BYTES_PER_ELEM_F32 * nelem
+        achieved = byts / avg_s / 1e9
+        roof = {"kernel": "k_pred_line<%s,float>" % dom_name[5:].upper() if dom_name.startswith("pred") else "k_corr_line<float>",
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n,
+                "bytes_per_elem": LINE_BYTES_PER_ELEM_F32}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
-                "avg_launch_us": dom_ms / dom_n * 1e3, "launches": dom_n}
-    hbm_peak = None
-    try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except Exception:
-        hbm_peak = 6800.0
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n}
     step_s = t_ms * 1e-3 / args.steps
-    hbm_alg = updates_per_step * 24 / step_s / 1e9     # 24 B per update (FP64 state read twice, written once)
+    bpu = 24 if prec == G.FP64 else 12
+    hbm_alg = updates_per_step * bpu / step_s / 1e9    # state read twice, written once per update
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == G.FP64 else "f32 bulk / f64 per-cell, Newton, sums",
                 "data": "synthetic (seeded; no dataset)",
-                "config": dict(cfg, l2="flushed between timed steps (flush not timed)", precision="fp64",
+                "config": dict(cfg, l2="flushed between timed steps (flush not timed)", precision=args.precision,
                                parallelism="replicas" if world > 1 else "single"),
                 "gpu_launches": launches,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "roofline": roof,
-                "step_hbm_roofline": {"algorithmic_bytes_per_update": 24, "achieved_gbs": hbm_alg,
+                "step_hbm_roofline": {"algorithmic_bytes_per_update": bpu, "achieved_gbs": hbm_alg,
                                       "peak_gbs": hbm_peak, "frac": hbm_alg / hbm_peak},
                 "kernel_share": {k: round(v[0] / tot_prof, 4) for k, v in sorted(prof.items())},
                 "krylov_iters_per_step": kry_its / args.steps / len(runs),
                 "krylov_cycles_per_step": kry_cycles / args.steps,
                 "clocks": clk}
+        if cmp is not None:
+            line["vs_fp64"] = cmp
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

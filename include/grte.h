@@ -75,9 +75,11 @@ typedef struct {
   int precision;         /* GRTE_FP64 (default) or GRTE_MIXED                                */
   double krylov_rtol;    /* prediction solve stops when every cell's preconditioned residual
                             is <= rtol |rho_j| (1e-13), or when a restart cycle stalls below
-                            1e-9 (the rounding floor of the residual)                        */
+                            1e-9 (the rounding floor of the residual).  MIXED: rtol is
+                            floored at 1e-9, cells below 1e-6 max|rho| are measured against
+                            that floor, and a second restart below 1e-4 ends the solve       */
   int krylov_restart;    /* GMRES restart length (10)                                        */
-  int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (6)            */
+  int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (30)           */
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */
   int energy_every;      /* 1: accumulate the energy sums of grte_get_energy every step; 0 off */
   void* stream;          /* cudaStream_t to run on; NULL: the library makes its own          */

@@ -39,6 +39,7 @@ struct Inst {
   double eps, dt, dx, a, c, Cv;
   double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
   double two_eps, inv_eps; // 2/eps, 1/eps
+  double bLflux, bRflux;   // sum_k w_k v_k b_L,k and sum_k w_k v_k b_R,k
   int64_t cell_off;        // per-cell arrays
   int64_t elem_off;        // E-like arrays, line k at elem_off + k*N
   int64_t nelem_off;       // O-like arrays, line k at nelem_off + k*(N+1)
@@ -63,28 +64,37 @@ struct CellCoef {
   double *sac;   // s_j a c
   double *ralpha;  // 1/alpha_j
   double *ratio;   // (A_j - alpha_j)/alpha_j = beta/alpha
+  double *fR, *fL; // m^R d_{j+1}/dx, m^L d_j/dx (streaming flux of a per-cell field, unscaled by kappa)
+  double *gbx;     // 2/eps in the inflow wall cells, else 0
 };
 
 struct Dev {
   Inst* inst;
   Line* lines;
   double *v, *w, *bL, *bR;
-  // state
-  double *E, *O, *T, *U, *sig;
+  // state: per element the deviation Eh = E - a c U (E = a c U + Eh) and O, in the
+  // bulk type of the precision mode (double or float); per cell T, U in double
+  void *Eh, *O;
+  double *T, *U, *sig;
   // per-cell
   double *rho_n, *rho_s, *Fs, *Us, *newton_its;
+  // per-cell parts of a line pass, computed once per cell in double
+  double *P1, *P2, *P3, *Frho, *gU, *Q1, *Q2;
+  double *gwork;   // per-cell double work vector of the Krylov kernels
+  double *Swall;   // per (instance, angle): the two inflow-wall flux contributions in double
   CellCoef cf;
-  // per-element work
-  double *xb, *S, *F, *Rd, *onode;
+  // per-element work (bulk type)
+  void *xb, *S, *F, *Rd, *onode;
   // preconditioner factors
-  double *pF, *pRd, *pG, *pH, *gw;
+  double *pF, *pRd, *pG, *pH, *gw, *pInv;
   // GMRES
   double *gx, *gV, *gz, *gH, *gg, *gcs, *gsn, *gbeta, *gxn;
   int *gactive, *gk, *gdone, *gits, *gcycles, *gestconv;
   int* status;
   double* energy;   // 3 per instance
   int m;  // restart length
-  double rtol;
+  double rtol, stall, wfloor;
+  int mixed;
   int newton_maxit;
 };
 
@@ -153,45 +163,107 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
   const double alpha = kc / cdt + s;
   D.cf.ralpha[gid] = 1.0 / alpha;
   D.cf.ratio[gid] = (sj / eps2 - s) / alpha;
+  D.cf.fR[gid] = mR * dr / I.dx;
+  D.cf.fL[gid] = mL * dl / I.dx;
+  D.cf.gbx[gid] = (inflow && (j == 0 || j == N - 1)) ? I.two_eps : 0.0;
 }
 
-// rho^n = sum_k w_k E^n_k (fixed angle order).
-__global__ void k_rho(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
-                      double* __restrict__ out, const double* __restrict__ Esrc) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= ncell) return;
+__device__ __forceinline__ int inst_of(const int64_t* __restrict__ cell_inst_start, int n_inst, int64_t gid) {
   int lo = 0, hi = n_inst - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
   }
-  const Inst I = D.inst[lo];
+  return lo;
+}
+
+// rho^n = sum_k w_k E^n_k = a c U^n + sum_k w_k Eh_k (sum_k w_k = 1), fixed angle order.
+template <typename R>
+__global__ void k_rho(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
+                      double* __restrict__ out) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  const Inst I = D.inst[inst_of(cell_inst_start, n_inst, gid)];
   const int64_t j = gid - I.cell_off;
+  const R* Eh = (const R*)D.Eh;
   double acc = 0.0;
-  for (int k = 0; k < I.M; ++k) acc += D.w[I.ang_off + k] * Esrc[I.elem_off + (int64_t)k * I.N + j];
-  out[gid] = acc;
+  for (int k = 0; k < I.M; ++k) acc += D.w[I.ang_off + k] * (double)Eh[I.elem_off + (int64_t)k * I.N + j];
+  out[gid] = I.a * I.c * D.U[gid] + acc;
+}
+
+// Per-cell parts of a prediction pass at the per-cell vector x (double, once per
+// cell, so that the line kernels only combine them with per-angle factors):
+//   P1 = -alpha x (+ s a c U^n + kappa/(c dt) a c U^n for a data pass)
+//   P2 = (Gint x)_j,  P3 = gb_j x_j  (G_k x = v^2 P2 + v P3)
+//   Frho = sum_k w_k v_k (O_{j+1,k} - O_{j,k}) of the rho part of O:
+//          wv2 [fR (x_j - x_{j+1}) + fL (x_j - x_{j-1})] + wv gbx x_j
+//          (data pass: minus 2/eps sum_k w_k v_k b at the inflow walls).
+__global__ void k_cellpart_pred(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
+                                const double* __restrict__ xvec, int full) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  const int ii = inst_of(cell_inst_start, n_inst, gid);
+  const Inst I = D.inst[ii];
+  if (!full && !D.gactive[ii]) return;
+  const int64_t j = gid - I.cell_off, N = I.N;
+  const double* x = xvec + I.cell_off;
+  const double xj = x[j], xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
+  double p1 = -D.cf.alpha[gid] * xj;
+  if (full) p1 += (D.cf.sac[gid] + D.cf.kcd[gid] * I.a * I.c) * D.U[gid];
+  D.P1[gid] = p1;
+  D.P2[gid] = D.cf.gl[gid] * (xj - xl) + D.cf.gu[gid] * (xj - xr);
+  D.P3[gid] = D.cf.gb[gid] * xj;
+  double fr = I.wv2 * (D.cf.fR[gid] * (xj - xr) + D.cf.fL[gid] * (xj - xl)) + I.wv * D.cf.gbx[gid] * xj;
+  if (full && I.bc == GRTE_BC_INFLOW) {
+    if (j == 0) fr -= I.two_eps * I.bLflux;
+    if (j == N - 1) fr -= I.two_eps * I.bRflux;
+  }
+  D.Frho[gid] = fr;
+}
+
+// Per-cell parts of correction substep 2 at T^{n+1} (U^n still in D.U):
+//   Q1 = kappa/(c dt) a c (U^n - U^{n+1}) / eps,
+//   gU_j = d_j/dx a c (U^{n+1}_j - U^{n+1}_{j-1}) at node j (0 at the wall node),
+//   Q2 = gU_{j+1} - gU_j (interior; the wall cells are formed in double by the line kernel).
+__global__ void k_cellpart_corr(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  const Inst I = D.inst[inst_of(cell_inst_start, n_inst, gid)];
+  const int64_t j = gid - I.cell_off, N = I.N;
+  const double* T = D.T + I.cell_off;
+  auto U1 = [&](int64_t jj) { const double t = T[jj]; const double t2 = t * t; return t2 * t2; };
+  const double ac = I.a * I.c;
+  D.Q1[gid] = D.cf.kcd[gid] * ac * (D.U[gid] - U1(j)) * I.inv_eps;
+  const double gl = (j >= 1) ? D.cf.dlx[gid] * ac * (U1(j) - U1(j - 1)) : 0.0;
+  const double gr = (j <= N - 2) ? D.cf.dlx[gid + 1] * ac * (U1(j + 1) - U1(j)) : 0.0;
+  D.gU[gid] = gl;
+  D.Q2[gid] = gr - gl;
 }
 
 // ----------------------------------------------------------------------------- lines
-struct LineCoef {  // A + v^2 Gint + v Gbdry of one line
+template <typename R>
+struct LineCoef {  // A + v^2 Gint + v Gbdry of one line, in the bulk type R
   const double *A, *gl, *gu, *gb;
   double v, v2;
   int64_t N;
-  __device__ double a(int64_t j) const { return j > 0 ? -v2 * gl[j] : 0.0; }
-  __device__ double c(int64_t j) const { return j < N - 1 ? -v2 * gu[j] : 0.0; }
-  __device__ double b(int64_t j) const { return A[j] + v2 * (gl[j] + gu[j]) + v * gb[j]; }
+  __device__ R a(int64_t j) const { return j > 0 ? R(-v2 * gl[j]) : R(0); }
+  __device__ R c(int64_t j) const { return j < N - 1 ? R(-v2 * gu[j]) : R(0); }
+  __device__ R b(int64_t j) const { return R(A[j] + v2 * (gl[j] + gu[j]) + v * gb[j]); }
 };
 
 enum { PRED_FULL_FACTOR = 0, PRED_FULL = 1, PRED_HOM = 2 };
 
-// One prediction pass over a line (instance, k): build the e-equation right-hand
-// side for the per-instance vector x (rho or a Krylov direction), solve, and write
-// w_k v_k (O_{j+1,k} - O_{j,k}) of E = x + e into S (the angular sum over k is
-// taken by the instance kernel).  FULL passes carry the data h_k and phi_k (E^n,
-// O^n, inflow); HOM passes apply the linear part only.
-template <int MODE>
+// One prediction pass over a line (instance, k) for the per-cell vector x (rho or a
+// Krylov direction): right-hand side of the e-equation
+//   r = h_k - alpha x - G_k x = P1 - v^2 P2 - v P3 + kappa/(c dt) Eh^n_k - kappa v D_k/dx
+// (D_k = o_{j+1} - o_j, o_i = d_i eps^2 O^n_i/(c dt), Eq. dis-pre1; walls Eq. bc-pre),
+// tridiagonal solve for e_k in R, and the e/o part of w_k v_k (O_{j+1,k} - O_{j,k})
+// into S (the rho part is Frho, per cell in double).  In the two wall cells the
+// right-hand side and the flux are formed in double: there (2/eps)(b - x) is an
+// O(eps) difference of O(1) numbers.  HOM passes carry no data.
+template <int MODE, typename R>
 __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* __restrict__ xvec) {
-  __shared__ TriSmem<double> sm;
+  __shared__ TriSmem<R> sm;
   const Line L = D.lines[blockIdx.x];
   const Inst I = D.inst[L.inst];
   if (MODE == PRED_HOM && !D.gactive[L.inst]) return;
@@ -203,53 +275,85 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
   const double bR = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bR[I.ang_off + k];
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
   const double* x = xvec + co;
-  double* xb = D.xb + eo;
-  const double *alpha = D.cf.alpha + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
-               *od = D.cf.od + co, *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co,
-               *sac = D.cf.sac + co;
-  const double* En = D.E + eo;
-  const double* On = D.O + oo;
-  const double* Un = D.U + co;
+  R* xb = (R*)D.xb + eo;
+  const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
+               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *P1 = D.P1 + co,
+               *P2 = D.P2 + co, *P3 = D.P3 + co;
+  const R* Ehn = (const R*)D.Eh + eo;
+  const R* On = (const R*)D.O + oo;
   const double v2 = v * v;
+  const R vr = R(v), v2r = R(v2);
   const double two_eps = I.two_eps;
-  // o_i = d_i eps^2 O^n_i/(c dt) at interior nodes (d at node j is dl[j])
-  auto onode = [&](int64_t i) -> double {
-    if (MODE == PRED_HOM) return 0.0;
-    if (i <= 0 || i >= N) return 0.0;
-    return od[i] * On[i];
+  auto onode = [&](int64_t i) -> R {   // o_i in R
+    if (MODE == PRED_HOM) return R(0);
+    if (i <= 0 || i >= N) return R(0);
+    return R(od[i]) * On[i];
   };
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    const double xj = x[j];
-    const double xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
-    const double Gx = v2 * (gl[j] * (xj - xl) + gu[j] * (xj - xr)) + v * gb[j] * xj;
-    double r = -alpha[j] * xj - Gx;
+  // right-hand side of an inflow wall row, in double:
+  // -v gb x + kappa v (2/eps) b/dx = kappa v (2/eps)(b - x)/dx is an O(eps) difference
+  auto wall_rhs = [&](int64_t j) -> double {
+    const double b = (j == 0) ? bL : bR;
+    double r = P1[j] - v2 * P2[j] + kdx[j] * v * two_eps * (b - x[j]);
     if (MODE != PRED_HOM) {
-      // data part phi of kappa v (O_{j+1} - O_j)/dx (Eq. dis-pre1 node values, Eq. bc-pre walls)
-      double Dj = onode(j + 1) - onode(j);
-      if (inflow && j == 0) Dj = 2.0 * onode(1) - two_eps * bL;
-      if (inflow && j == N - 1) Dj = -two_eps * bR - 2.0 * onode(N - 1);
-      const double h = kcd[j] * En[j] + sac[j] * Un[j] - kdx[j] * v * Dj;
-      r += h;
+      const double o = (j == 0) ? 2.0 * (double)onode(1) : -2.0 * (double)onode(N - 1);
+      r += kcd[j] * (double)Ehn[j] - kdx[j] * v * o;
     }
-    xb[j] = r;
+    return r;
+  };
+#pragma unroll 4
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const bool wall = inflow && (j == 0 || j == N - 1);
+    if (!wall) {
+      R r = R(P1[j]) - v2r * R(P2[j]) - vr * R(P3[j]);
+      if (MODE != PRED_HOM) r += R(kcd[j]) * Ehn[j] - R(kdx[j]) * vr * (onode(j + 1) - onode(j));
+      xb[j] = r;
+    } else {
+      xb[j] = R(wall_rhs(j));
+    }
   }
   __syncthreads();
-  LineCoef cfl{D.cf.A + co, gl, gu, gb, v, v2, N};
-  if (MODE == PRED_FULL_FACTOR)
-    tri_solve<true>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
-  else
-    tri_solve<false>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
-  // flux contribution of E = x + e:
-  //   O_i = o_i - d_i v (E_i - E_{i-1})/dx (interior), walls from Eq. bc-pre
-  double* Sk = D.S + eo;
+  LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v2, N};
+  R* F = (R*)D.F + 4 * I.elem_off + 4 * (int64_t)k * N;
+  R* Rd = (R*)D.Rd + L.red_off;
+  if (MODE == PRED_FULL_FACTOR) tri_solve<true>(cfl, N, xb, F, Rd, sm);
+  else tri_solve<false>(cfl, N, xb, F, Rd, sm);
+  // the wall unknowns enter the wall flux multiplied by 2/eps: re-solve their rows in
+  // double from the neighbours (the rows are dominated by v gb ~ 1/eps, so the
+  // neighbour's bulk-precision error is damped by |c/b|)
+  __shared__ double ew[2];
+  if (inflow && threadIdx.x == 0) {
+    const double b0 = D.cf.A[co] + v2 * (gl[0] + gu[0]) + v * gb[0];
+    ew[0] = (wall_rhs(0) + v2 * gu[0] * (double)xb[1]) / b0;
+    const double bN = D.cf.A[co + N - 1] + v2 * (gl[N - 1] + gu[N - 1]) + v * gb[N - 1];
+    ew[1] = (wall_rhs(N - 1) + v2 * gl[N - 1] * (double)xb[N - 2]) / bN;
+  }
+  __syncthreads();
+  // e/o part of w_k v_k (O_{j+1,k} - O_{j,k}):
+  //   O^eo_i = o_i - d_i v (e_i - e_{i-1})/dx (interior nodes)
+  //   j = 0:   2 O^eo_1 + (2/eps) e_0       (the b_L and x parts are in Frho)
+  //   j = N-1: (2/eps) e_{N-1} - 2 O^eo_{N-1}
+  R* Sk = (R*)D.S + eo;
+  const R wvr = R(w * v);
+  if (inflow && threadIdx.x == 0) {   // wall cells: e/o flux in double, kept in Swall
+    const double eL = ew[0], eR = ew[1];
+    const double e1 = (N > 2) ? (double)xb[1] : eR, eN2 = (N > 2) ? (double)xb[N - 2] : eL;
+    const double O1 = (double)onode(1) - dlx[1] * v * (e1 - eL);
+    const double ON1 = (double)onode(N - 1) - dlx[N - 1] * v * (eR - eN2);
+    D.Swall[2 * (I.ang_off + k) + 0] = w * v * (2.0 * O1 + two_eps * eL);
+    D.Swall[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1);
+  }
+#pragma unroll 4
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    auto Oint = [&](int64_t i) { return onode(i) - dlx[i] * v * ((x[i] - x[i - 1]) + (xb[i] - xb[i - 1])); };
-    double OR, OLft;
-    if (j + 1 <= N - 1) OR = Oint(j + 1);
-    else OR = inflow ? two_eps * ((x[N - 1] - bR) + xb[N - 1]) - Oint(N - 1) : 0.0;
-    if (j >= 1) OLft = Oint(j);
-    else OLft = inflow ? two_eps * ((bL - x[0]) - xb[0]) - Oint(1) : 0.0;
-    Sk[j] = w * v * (OR - OLft);
+    auto Oeo = [&](int64_t i) -> R { return onode(i) - R(dlx[i]) * vr * (xb[i] - xb[i - 1]); };
+    R val;
+    if (inflow && (j == 0 || j == N - 1)) {
+      val = R(0);                       // in Swall
+    } else {
+      const R OR = (j + 1 <= N - 1) ? Oeo(j + 1) : R(0);
+      const R OL = (j >= 1) ? Oeo(j) : R(0);
+      val = OR - OL;
+    }
+    Sk[j] = wvr * val;
   }
 }
 
@@ -311,6 +415,9 @@ struct GmresSmem {
   double xlr[2];                     // interface values left of and right of this slice
   double hcol[kMaxRestart + 2];
   double y[kMaxRestart];
+  double gj[2 * kCL][4 * kCL];          // Gauss-Jordan workspace of the interface system
+  double yv[2 * kCL];                   // gathered slice-end values
+  double redm[32][kMaxRestart + 2];     // per-warp partials of a multi-value reduction
 };
 
 __device__ double cta_sum(double v, double* red) {
@@ -404,45 +511,73 @@ __device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int 
     }
   }
   cl.sync();
-  if (threadIdx.x == 0) {
-    // interface unknowns X[2q] = u at the first cell of slice q, X[2q+1] = at its last:
-    //   X[2q]   + g_first(q) X[2q-1] + h_first(q) X[2q+2] = y_first(q)
-    //   X[2q+1] + g_last(q)  X[2q-1] + h_last(q)  X[2q+2] = y_last(q)
-    const int na = sl.nact, m2 = 2 * na;
-    double Mx[2 * kCL][2 * kCL + 1];
-    for (int i = 0; i < m2; ++i)
-      for (int j = 0; j <= m2; ++j) Mx[i][j] = 0.0;
-    for (int q = 0; q < na; ++q) {
+  // interface unknowns X[2q] = u at the first cell of slice q, X[2q+1] = at its last:
+  //   X[2q]   + g_first(q) X[2q-1] + h_first(q) X[2q+2] = y_first(q)
+  //   X[2q+1] + g_last(q)  X[2q-1] + h_last(q)  X[2q+2] = y_last(q)
+  // The matrix depends only on the operator: FACTOR inverts it once per step (one
+  // warp, Gauss-Jordan with partial pivoting) and stores the two rows this slice
+  // needs; every apply is then two short dot products.
+  const int na = sl.nact, m2 = 2 * na;
+  double* inv_rows = D.pInv + ((int64_t)blockIdx.x) * 2 * (2 * kCL);
+  if (FACTOR && threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int w2 = 2 * m2;
+    for (int idx = lane; idx < m2 * w2; idx += 32) {
+      const int i = idx / w2, j = idx % w2;
+      sm.gj[i][j] = 0.0;
+    }
+    __syncwarp();
+    if (lane < m2) {
+      const int q = lane / 2, t = lane % 2;
       const double* e = cl.map_shared_rank(&sm.ends[0], q);
-      for (int t = 0; t < 2; ++t) {
-        const int row = 2 * q + t;
-        Mx[row][row] = 1.0;
-        if (q > 0) Mx[row][2 * q - 1] += e[2 + t];
-        if (q < na - 1) Mx[row][2 * q + 2] += e[4 + t];
-        Mx[row][m2] = e[t];
-      }
+      sm.gj[lane][lane] = 1.0;
+      if (q > 0) sm.gj[lane][2 * q - 1] += e[2 + t];
+      if (q < na - 1) sm.gj[lane][2 * q + 2] += e[4 + t];
+      sm.gj[lane][m2 + lane] = 1.0;
     }
-    for (int col = 0; col < m2; ++col) {   // Gaussian elimination, partial pivoting
+    __syncwarp();
+    for (int col = 0; col < m2; ++col) {
       int piv = col;
-      for (int i = col + 1; i < m2; ++i)
-        if (fabs(Mx[i][col]) > fabs(Mx[piv][col])) piv = i;
+      if (lane == 0)
+        for (int i = col + 1; i < m2; ++i)
+          if (fabs(sm.gj[i][col]) > fabs(sm.gj[piv][col])) piv = i;
+      piv = __shfl_sync(0xffffffffu, piv, 0);
       if (piv != col)
-        for (int j = 0; j <= m2; ++j) { double t = Mx[col][j]; Mx[col][j] = Mx[piv][j]; Mx[piv][j] = t; }
-      const double inv = 1.0 / Mx[col][col];
-      for (int i = col + 1; i < m2; ++i) {
-        const double f = Mx[i][col] * inv;
-        if (f != 0.0)
-          for (int j = col; j <= m2; ++j) Mx[i][j] -= f * Mx[col][j];
+        for (int j = lane; j < w2; j += 32) {
+          const double t = sm.gj[col][j];
+          sm.gj[col][j] = sm.gj[piv][j];
+          sm.gj[piv][j] = t;
+        }
+      __syncwarp();
+      const double ip = 1.0 / sm.gj[col][col];
+      __syncwarp();
+      for (int j = lane; j < w2; j += 32) sm.gj[col][j] *= ip;
+      __syncwarp();
+      double f = (lane < m2 && lane != col) ? sm.gj[lane][col] : 0.0;
+      __syncwarp();
+      for (int i = 0; i < m2; ++i) {
+        const double fi = __shfl_sync(0xffffffffu, f, i);
+        if (i != col && fi != 0.0)
+          for (int j = lane; j < w2; j += 32) sm.gj[i][j] -= fi * sm.gj[col][j];
       }
+      __syncwarp();
     }
-    double X[2 * kCL];
-    for (int i = m2 - 1; i >= 0; --i) {
-      double t = Mx[i][m2];
-      for (int j = i + 1; j < m2; ++j) t -= Mx[i][j] * X[j];
-      X[i] = t / Mx[i][i];
+    // rows 2 rank - 1 and 2 rank + 2 of the inverse (columns m2 .. 2 m2 - 1)
+    for (int j = lane; j < m2; j += 32) {
+      inv_rows[j] = (rank > 0 && rank < na) ? sm.gj[2 * rank - 1][m2 + j] : 0.0;
+      inv_rows[2 * kCL + j] = (rank < na - 1) ? sm.gj[2 * rank + 2][m2 + j] : 0.0;
     }
-    sm.xlr[0] = (rank > 0 && rank < na) ? X[2 * rank - 1] : 0.0;
-    sm.xlr[1] = (rank < na - 1) ? X[2 * rank + 2] : 0.0;
+  }
+  if (threadIdx.x < m2) {
+    const int q = threadIdx.x / 2, t = threadIdx.x % 2;
+    sm.yv[threadIdx.x] = cl.map_shared_rank(&sm.ends[0], q)[t];
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double acc = 0.0;
+    const double* row = inv_rows + threadIdx.x * 2 * kCL;
+    for (int j = 0; j < m2; ++j) acc += row[j] * sm.yv[j];
+    sm.xlr[threadIdx.x] = acc;
   }
   __syncthreads();
   const double ul = sm.xlr[0], ur = sm.xlr[1];
@@ -460,10 +595,18 @@ __device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int 
   __syncthreads();
 }
 
-// Angular sum of a pass: sum_k S[k][j] (fixed angle order).
+// F_j = sum_k w_k v_k (O_{j+1,k} - O_{j,k}) of a pass: the per-cell rho part plus the
+// per-angle e/o parts (summed in double, fixed angle order).
+template <typename R>
 __device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t j) {
-  double acc = 0.0;
-  for (int k = 0; k < I.M; ++k) acc += D.S[I.elem_off + (int64_t)k * I.N + j];
+  const R* S = (const R*)D.S + I.elem_off + j;
+  double acc = D.Frho[I.cell_off + j];
+  if (I.bc == GRTE_BC_INFLOW && (j == 0 || j == I.N - 1)) {
+    const int side = (j == 0) ? 0 : 1;
+    for (int k = 0; k < I.M; ++k) acc += D.Swall[2 * (I.ang_off + k) + side];
+  } else {
+    for (int k = 0; k < I.M; ++k) acc += (double)S[(int64_t)k * I.N];
+  }
   return acc;
 }
 
@@ -473,7 +616,7 @@ enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
 // preconditioned).  Vectors live in global memory: x (iterate), V[0..m] (Krylov
 // basis), z (scratch).  Scalars (H, g, Givens) are computed identically by every
 // CTA; rank 0 stores them.
-template <int MODE>
+template <int MODE, typename R>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
   __shared__ GmresSmem sm;
   cg::cluster_group cl = cg::this_cluster();
@@ -486,7 +629,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
   const int m = D.m;
   double* x = D.gx + co;
   double* z = D.gz + co;
-  double* work = D.xb + I.elem_off;          // the line buffers are free between passes
+  double* work = D.gwork + co;
   const int64_t ncell_tot = D.gz - D.gx;     // gz = gx + ncell_total (allocation layout)
   auto Vi = [&](int i) { return D.gV + (int64_t)i * ncell_tot + co; };
   double* H = D.gH + (int64_t)ii * (kMaxRestart + 1) * kMaxRestart;
@@ -500,21 +643,22 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     // r = -R(x) from the FULL pass that just ran at x
     double* r = z;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
-      const double fl = flux_sum(D, I, j);
+      const double fl = flux_sum<R>(D, I, j);
       const double Rj = alpha[j] * x[j] - kcd[j] * D.rho_n[co + j] - sac[j] * D.U[co + j] + kdx[j] * fl;
       r[j] = -Rj;
       D.Fs[co + j] = fl;                    // F* of the current iterate (final at convergence)
     }
     // per-cell weights of the stopping test: the preconditioned residual relative to
-    // |x_j| (floor 1e-13 max|x|), so that the test bounds every cell's relative
-    // correction and not only the large cells' share of a 2-norm
+    // |x_j| (floor wfloor max|x|: 1e-13 in FP64, 1e-8 with binary32 line solves), so
+    // that the test bounds every cell's relative correction and not only the large
+    // cells' share of a 2-norm
     double xm = 0.0;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) xm = fmax(xm, fabs(x[j]));
     xm = cta_max(xm, sm.red);
     __shared__ double xms[1];
     cluster_maxs(cl, sm, 0, &xm, 1, xms);
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
-      D.gw[co + j] = 1.0 / (fabs(x[j]) + 1e-13 * xms[0] + 1e-300);
+      D.gw[co + j] = 1.0 / (fabs(x[j]) + D.wfloor * xms[0] + 1e-300);
     __syncthreads();
     double* v0 = Vi(0);
     if (MODE == G_RESTART_FIRST) prec_apply_cl<true>(D, I, sl, rank, cl, r, v0, work, sm);
@@ -531,13 +675,15 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     __shared__ double tots[2], tmax[1];
     cluster_sums(cl, sm, 1, loc, 2, tots);
     cluster_maxs(cl, sm, 0, loc + 2, 1, tmax);
-    const double nrm = sqrt(tots[0]), xn = sqrt(tots[1]), rinf = tmax[0];
+    const double nrm = sqrt(tots[0]), xn = sqrt(tots[1]);
+    const double rinf = tmax[0];
     // Converged when every cell's relative preconditioned correction is below rtol.
     // Restarted GMRES cannot go below the rounding floor of the residual evaluation
     // itself (a sum of terms much larger than the residual): a restart cycle that
     // did not reduce it by 4x while it is below 1e-9 has reached that floor.
     bool conv = !(rinf > D.rtol);   // also true for rinf == 0
-    if (MODE == G_RESTART && !conv && rinf <= 1e-9 && rinf >= 0.25 * D.gbeta[ii]) conv = true;
+    if (MODE == G_RESTART && !conv && rinf <= D.stall &&
+        (rinf >= 0.25 * D.gbeta[ii] || (D.mixed && D.gcycles[ii] >= 1))) conv = true;
     if (rank == 0 && threadIdx.x == 0) {
       if (MODE == G_RESTART) D.gcycles[ii] += 1;
       D.gbeta[ii] = rinf;
@@ -569,7 +715,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     const double* vj = Vi(jcol);
     double* cv = z;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
-      cv[j] = alpha[j] * vj[j] + kdx[j] * flux_sum(D, I, j);
+      cv[j] = alpha[j] * vj[j] + kdx[j] * flux_sum<R>(D, I, j);
     __syncthreads();
     double* wv = Vi(jcol + 1);
     prec_apply_cl<false>(D, I, sl, rank, cl, cv, wv, work, sm);
@@ -578,13 +724,26 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     double hc[kMaxRestart + 2];
     for (int i = 0; i <= jcol + 1; ++i) hc[i] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
+      // all jcol+1 dot products in one sweep and one CTA reduction
       double loc[kMaxRestart + 1];
-      for (int i = 0; i <= jcol; ++i) {
-        const double* vi = Vi(i);
-        double d = 0.0;
-        for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) d += wv[j] * vi[j];
-        loc[i] = cta_sum(d, sm.red);
+      for (int i = 0; i <= jcol; ++i) loc[i] = 0.0;
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
+        const double wj = wv[j];
+        for (int i = 0; i <= jcol; ++i) loc[i] += wj * Vi(i)[j];
       }
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = 0; i <= jcol; ++i) {
+        double v = loc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sm.redm[wid][i] = v;
+      }
+      __syncthreads();
+      for (int i = 0; i <= jcol; ++i) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sm.redm[w][i];   // same order in every thread
+        loc[i] = t;
+      }
+      __syncthreads();
       cluster_sums(cl, sm, pass, loc, jcol + 1, dots);
       for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
         double t = wv[j];
@@ -718,8 +877,11 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
 // coefficients of k_cell_coef at T^{n+1}; the walls use O_{J,0} = 2/eps (b_L - E_0) - O_1
 // and O_{J,N} = 2/eps (E_{N-1} - b_R) - O_{N-1}.  Then E^{n+1} = a c U + eps E_J,
 // O^{n+1} = O_J (in place: each CTA owns its line).
+// Per-angle parts in R; the U parts (Q1, gU, Q2) come in double from
+// k_cellpart_corr, and the two inflow wall cells are formed in double.
+template <typename R>
 __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
-  __shared__ TriSmem<double> sm;
+  __shared__ TriSmem<R> sm;
   const Line L = D.lines[blockIdx.x];
   const Inst I = D.inst[L.inst];
   const int64_t N = I.N;
@@ -729,47 +891,55 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   const bool inflow = I.bc == GRTE_BC_INFLOW;
   const double bL = inflow ? D.bL[I.ang_off + k] : 0.0, bR = inflow ? D.bR[I.ang_off + k] : 0.0;
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
-  double* E = D.E + eo;
-  double* O = D.O + oo;
+  R* Eh = (R*)D.Eh + eo;
+  R* O = (R*)D.O + oo;
   const double* T = D.T + co;   // T^{n+1}
-  double* xb = D.xb + eo;
-  double* on = D.onode + oo;
+  const double* Un = D.U + co;  // U^n
+  R* xb = (R*)D.xb + eo;
+  R* on = (R*)D.onode + oo;
   const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
-               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co;
+               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *Q1 = D.Q1 + co,
+               *Q2 = D.Q2 + co, *gU = D.gU + co;
   const double two_eps = I.two_eps, inv_eps = I.inv_eps;
-  auto U = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
-  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
-    double o = 0.0;
-    if (i >= 1 && i <= N - 1) o = od[i] * O[i] - dlx[i] * ac * v * (U(i) - U(i - 1));
-    on[i] = o;
-  }
+  const R vr = R(v);
+  auto U1 = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
+  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x)
+    on[i] = (i >= 1 && i <= N - 1) ? R(od[i]) * O[i] : R(0);   // eps^2 d O^n/(c dt) part of o'
   __syncthreads();
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    double Dj = on[j + 1] - on[j];
-    if (inflow && j == 0) Dj = 2.0 * on[1] - two_eps * (bL - ac * U(0));
-    if (inflow && j == N - 1) Dj = two_eps * (ac * U(N - 1) - bR) - 2.0 * on[N - 1];
-    xb[j] = (kcd[j] * (E[j] - ac * U(j)) - kdx[j] * v * Dj) * inv_eps;
+    const bool wall = inflow && (j == 0 || j == N - 1);
+    if (!wall) {
+      xb[j] = R(Q1[j]) + R(kcd[j] * inv_eps) * Eh[j] - R(kdx[j] * v * inv_eps) * (on[j + 1] - on[j]) +
+              R(kdx[j] * v * v * inv_eps) * R(Q2[j]);
+    } else {
+      double Dj;
+      if (j == 0) Dj = 2.0 * ((double)on[1] - v * gU[1]) - two_eps * (bL - ac * U1(0));
+      else Dj = two_eps * (ac * U1(N - 1) - bR) - 2.0 * ((double)on[N - 1] - v * gU[N - 1]);
+      xb[j] = R((kcd[j] * ((double)Eh[j] + ac * (Un[j] - U1(j))) - kdx[j] * v * Dj) * inv_eps);
+    }
   }
   __syncthreads();
-  LineCoef cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
-  tri_solve<true>(cfl, N, xb, D.F + 4 * I.elem_off + 4 * (int64_t)k * N, D.Rd + L.red_off, sm);
-  // projection
+  LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
+  tri_solve<true>(cfl, N, xb, (R*)D.F + 4 * I.elem_off + 4 * (int64_t)k * N, (R*)D.Rd + L.red_off, sm);
+  // projection: O^{n+1} = O_J, Eh^{n+1} = eps E_J (E^{n+1} = a c U^{n+1} + Eh^{n+1})
+  const R epsr = R(eps);
   for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
-    double Oi;
-    auto Oint = [&](int64_t n) { return on[n] - dlx[n] * eps * v * (xb[n] - xb[n - 1]); };
+    auto Oint = [&](int64_t n) -> R { return on[n] - vr * R(gU[n]) - R(dlx[n] * eps) * vr * (xb[n] - xb[n - 1]); };
+    R Oi;
     if (i >= 1 && i <= N - 1) Oi = Oint(i);
-    else if (!inflow) Oi = 0.0;
-    else if (i == 0) Oi = two_eps * (bL - ac * U(0)) - 2.0 * xb[0] - Oint(1);
-    else Oi = two_eps * (ac * U(N - 1) - bR) + 2.0 * xb[N - 1] - Oint(N - 1);
+    else if (!inflow) Oi = R(0);
+    else if (i == 0) Oi = R(two_eps * (bL - ac * U1(0)) - 2.0 * (double)xb[0] - (double)Oint(1));
+    else Oi = R(two_eps * (ac * U1(N - 1) - bR) + 2.0 * (double)xb[N - 1] - (double)Oint(N - 1));
     O[i] = Oi;
   }
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) E[j] = ac * U(j) + eps * xb[j];
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) Eh[j] = epsr * xb[j];
 }
 
 // Energy sums of one instance per CTA (FP64, fixed reduction order):
 //   acc[0] = sum_j dx (rho_j/c + Cv T_j)                     (energy now)
 //   acc[1] += dt sum_j F*_j                                  (wall flux of the prediction)
 //   acc[2] += dt sum_j eps^2/(c sig_j dt + eps^2) (F*_j - F^{n+1}_j)   (Eq. semiconservative defect)
+template <typename R>
 __global__ void __launch_bounds__(kTriThreads) k_energy(Dev D, int accumulate) {
   __shared__ double red[32];
   const int ii = blockIdx.x;
@@ -778,12 +948,12 @@ __global__ void __launch_bounds__(kTriThreads) k_energy(Dev D, int accumulate) {
   double e = 0.0, f = 0.0, dft = 0.0;
   const double eps2 = I.eps * I.eps, cdt = I.c * I.dt;
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-    double rho = 0.0, Fn = 0.0;
+    double rho = I.a * I.c * D.U[co + j], Fn = 0.0;
     for (int k = 0; k < I.M; ++k) {
       const double w = D.w[I.ang_off + k], v = D.v[I.ang_off + k];
-      rho += w * D.E[I.elem_off + (int64_t)k * N + j];
-      const double* O = D.O + I.nelem_off + (int64_t)k * (N + 1);
-      Fn += w * v * (O[j + 1] - O[j]);
+      rho += w * (double)((const R*)D.Eh)[I.elem_off + (int64_t)k * N + j];
+      const R* O = (const R*)D.O + I.nelem_off + (int64_t)k * (N + 1);
+      Fn += w * v * ((double)O[j + 1] - (double)O[j]);
     }
     e += I.dx * (rho / I.c + I.Cv * D.T[co + j]);
     const double Fs = D.Fs[co + j];
@@ -927,7 +1097,7 @@ void grte_default_options(grte_options* o) {
   o->precision = GRTE_FP64;
   o->krylov_rtol = 1e-13;
   o->krylov_restart = 10;
-  o->krylov_maxcycles = 6;
+  o->krylov_maxcycles = 30;
   o->newton_maxit = 60;
   o->energy_every = 0;
   o->stream = nullptr;
@@ -954,7 +1124,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   grte_default_options(&h->opt);
   if (opt) h->opt = *opt;
   auto bad = [&](const std::string& m) { grte_status s = fail(h, GRTE_EINVAL, m); *out = h; return s; };
-  if (h->opt.precision != GRTE_FP64) return bad("only GRTE_FP64 is available in this build");
+  if (h->opt.precision != GRTE_FP64 && h->opt.precision != GRTE_MIXED) return bad("precision must be GRTE_FP64 or GRTE_MIXED");
   if (h->opt.krylov_restart < 1 || h->opt.krylov_restart > kMaxRestart) return bad("krylov_restart out of range [1,16]");
   if (h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1 || !(h->opt.krylov_rtol > 0)) return bad("bad solver options");
   h->n_inst = n_inst;
@@ -1004,6 +1174,15 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     I.wv = wv;
     I.wv2 = wv2;
     I.two_eps = 2.0 / p.eps;
+    {
+      double fl = 0.0, fr = 0.0;
+      for (int k = 0; k < p.n_angle; ++k) {
+        if (p.bc == GRTE_BC_INFLOW && p.bL) fl += w[k] * v[k] * p.bL[k];
+        if (p.bc == GRTE_BC_INFLOW && p.bR) fr += w[k] * v[k] * p.bR[k];
+      }
+      I.bLflux = fl;
+      I.bRflux = fr;
+    }
     I.inv_eps = 1.0 / p.eps;
     I.cell_off = coff;
     I.elem_off = eoff;
@@ -1040,7 +1219,15 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   Dev& D = h->D;
   const int m = h->opt.krylov_restart;
   D.m = m;
-  D.rtol = h->opt.krylov_rtol;
+  // binary32 line solves leave noise in the residual of cells far below the maximum:
+  // the mixed mode floors the tolerance at 1e-9, measures cells below 1e-6 of the
+  // maximum against that floor, and accepts a second restart below 1e-4
+  const bool mixed = h->opt.precision == GRTE_MIXED;
+  D.rtol = mixed ? std::max(h->opt.krylov_rtol, 1e-9) : h->opt.krylov_rtol;
+  D.stall = mixed ? 1e-4 : 1e-9;
+  D.wfloor = mixed ? 1e-6 : 1e-13;
+  D.mixed = mixed ? 1 : 0;
+  const int64_t es = mixed ? 4 : 8;   // bytes per bulk element
   D.newton_maxit = h->opt.newton_maxit;
   const int64_t nc = h->ncell, ne = h->nelem, nn = h->nnelem, na = aoff;
 #define AL(ptr, n) do { if (dalloc(h, &(ptr), (n)) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc failed for " #ptr); } while (0)
@@ -1048,14 +1235,27 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(h->d_lines, (int64_t)h->lines.size());
   AL(h->d_cell_start, n_inst);
   AL(D.v, na); AL(D.w, na); AL(D.bL, na); AL(D.bR, na);
-  AL(D.E, ne); AL(D.O, nn); AL(D.T, nc); AL(D.U, nc); AL(D.sig, nc);
+  { char* p_; if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Eh"); D.Eh = p_; }
+  { char* p_; if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc O"); D.O = p_; }
+  AL(D.T, nc); AL(D.U, nc); AL(D.sig, nc);
+  AL(D.P1, nc); AL(D.P2, nc); AL(D.P3, nc); AL(D.Frho, nc); AL(D.gU, nc); AL(D.Q1, nc); AL(D.Q2, nc);
+  AL(D.gwork, nc);
+  AL(D.Swall, 2 * na);
   AL(D.rho_n, nc); AL(D.rho_s, nc); AL(D.Fs, nc); AL(D.Us, nc); AL(D.newton_its, nc);
   AL(D.cf.kc, nc); AL(D.cf.s, nc); AL(D.cf.alpha, nc); AL(D.cf.A, nc); AL(D.cf.gam, nc);
   AL(D.cf.gl, nc); AL(D.cf.gu, nc); AL(D.cf.gb, nc); AL(D.cf.dl, nc);
   AL(D.cf.od, nc); AL(D.cf.dlx, nc); AL(D.cf.kcd, nc); AL(D.cf.kdx, nc); AL(D.cf.sac, nc);
-  AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc);
-  AL(D.xb, ne); AL(D.S, ne); AL(D.F, 4 * ne); AL(D.Rd, h->nred); AL(D.onode, nn);
+  AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc); AL(D.cf.fR, nc); AL(D.cf.fL, nc); AL(D.cf.gbx, nc);
+  {
+    char* p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc xb"); D.xb = p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S"); D.S = p_;
+    if (dalloc(h, &p_, es * 4 * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc F"); D.F = p_;
+    if (dalloc(h, &p_, es * h->nred) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Rd"); D.Rd = p_;
+    if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc onode"); D.onode = p_;
+  }
   AL(D.pF, 4 * nc); AL(D.pRd, h->npred); AL(D.pG, nc); AL(D.pH, nc); AL(D.gw, nc);
+  AL(D.pInv, (int64_t)n_inst * kCL * 2 * (2 * kCL));
   // x, z contiguous so that the GMRES kernel can recover the total cell count
   double* xz = nullptr;
   AL(xz, 2 * nc);
@@ -1110,21 +1310,32 @@ grte_status grte_set_state(grte_t h, int inst, const double* T, const double* E,
     if (!(T[j] >= 0.0) || !std::isfinite(T[j])) return fail(h, GRTE_EINVAL, "T must be finite and >= 0");
     hU[j] = (T[j] * T[j]) * (T[j] * T[j]);
   }
+  // device layout: line-major, E stored as its deviation Eh = E - a c U
   for (int64_t k = 0; k < M; ++k) {
-    for (int64_t j = 0; j < N; ++j) hE[k * N + j] = E ? E[j * M + k] : I.a * I.c * hU[j];
+    for (int64_t j = 0; j < N; ++j) hE[k * N + j] = E ? E[j * M + k] - I.a * I.c * hU[j] : 0.0;
     for (int64_t i = 0; i <= N; ++i) hO[k * (N + 1) + i] = O ? O[i * M + k] : 0.0;
   }
   Dev& D = h->D;
   CK(cudaMemcpyAsync(D.T + I.cell_off, T, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(D.U + I.cell_off, hU.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(D.E + I.elem_off, hE.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(D.O + I.nelem_off, hO.data(), sizeof(double) * (N + 1) * M, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  if (h->opt.precision == GRTE_MIXED) {
+    std::vector<float> fE(hE.begin(), hE.end()), fO(hO.begin(), hO.end());
+    CK(cudaMemcpyAsync((float*)D.Eh + I.elem_off, fE.data(), sizeof(float) * N * M, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync((float*)D.O + I.nelem_off, fO.data(), sizeof(float) * (N + 1) * M, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } else {
+    CK(cudaMemcpyAsync((double*)D.Eh + I.elem_off, hE.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync((double*)D.O + I.nelem_off, hO.data(), sizeof(double) * (N + 1) * M, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   h->inst_set[inst] = 1;
   h->state_set = std::all_of(h->inst_set.begin(), h->inst_set.end(), [](char c) { return c != 0; });
   return GRTE_OK;
 }
 
+}  // extern "C"
+
+template <typename R>
 static grte_status step_once(grte_t h) {
   Dev& D = h->D;
   cudaStream_t st = h->stream;
@@ -1135,17 +1346,19 @@ static grte_status step_once(grte_t h) {
   const unsigned cgrid = (unsigned)((nc + cb - 1) / cb);
   // prediction coefficients at T^n, rho^n, initial iterate x = rho^n
   LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 0));
-  LAUNCH(GRTE_K_RHO, k_rho<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n, D.E));
+  LAUNCH(GRTE_K_RHO, k_rho<R><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n));
   CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
   CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
-  LAUNCH(GRTE_K_PRED_FACTOR, k_pred_line<PRED_FULL_FACTOR><<<nl, kTriThreads, 0, st>>>(D, D.gx));
-  LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART_FIRST><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
+  LAUNCH(GRTE_K_PRED_FACTOR, (k_pred_line<PRED_FULL_FACTOR, R><<<nl, kTriThreads, 0, st>>>(D, D.gx)));
+  LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART_FIRST, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
-      LAUNCH(GRTE_K_PRED_HOM, k_pred_line<PRED_HOM><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc));
-      LAUNCH(GRTE_K_GMRES, k_gmres<G_ARNOLDI><<<ni * kCL, kTriThreads, 0, st>>>(D, j));
+      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gV + (int64_t)j * nc, 0));
+      LAUNCH(GRTE_K_PRED_HOM, (k_pred_line<PRED_HOM, R><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc)));
+      LAUNCH(GRTE_K_GMRES, (k_gmres<G_ARNOLDI, R><<<ni * kCL, kTriThreads, 0, st>>>(D, j)));
       // a Krylov direction pass costs far more than a round trip: after the first
       // iteration, stop launching once no instance is still iterating
       if (j >= 1 && j + 1 < D.m) {
@@ -1156,9 +1369,10 @@ static grte_status step_once(grte_t h) {
         if (!any) break;
       }
     }
-    LAUNCH(GRTE_K_GMRES, k_gmres<G_UPDATE><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
-    LAUNCH(GRTE_K_PRED_FULL, k_pred_line<PRED_FULL><<<nl, kTriThreads, 0, st>>>(D, D.gx));
-    LAUNCH(GRTE_K_GMRES, k_gmres<G_RESTART><<<ni * kCL, kTriThreads, 0, st>>>(D, 0));
+    LAUNCH(GRTE_K_GMRES, (k_gmres<G_UPDATE, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
+    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
+    LAUNCH(GRTE_K_PRED_FULL, (k_pred_line<PRED_FULL, R><<<nl, kTriThreads, 0, st>>>(D, D.gx)));
+    LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1180,12 +1394,15 @@ static grte_status step_once(grte_t h) {
   LAUNCH(GRTE_K_NEWTON, k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
   // correction substep 2 + projection at T^{n+1}
   LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
-  LAUNCH(GRTE_K_CORR, k_corr_line<<<nl, kTriThreads, 0, st>>>(D));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_corr<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
+  LAUNCH(GRTE_K_CORR, k_corr_line<R><<<nl, kTriThreads, 0, st>>>(D));
   LAUNCH(GRTE_K_PROJECT, k_project_U<<<cgrid, cb, 0, st>>>(D, nc));
-  if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<<<ni, kTriThreads, 0, st>>>(D, 1));
+  if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<R><<<ni, kTriThreads, 0, st>>>(D, 1));
   CK(cudaGetLastError());
   return GRTE_OK;
 }
+
+extern "C" {
 
 grte_status grte_step(grte_t h, int64_t nsteps) {
   if (!h) return GRTE_EINVAL;
@@ -1197,7 +1414,7 @@ grte_status grte_step(grte_t h, int64_t nsteps) {
   int64_t its = 0;
   std::vector<int> hits(h->n_inst);
   for (int64_t n = 0; n < nsteps; ++n) {
-    grte_status s = step_once(h);
+    grte_status s = h->opt.precision == GRTE_MIXED ? step_once<float>(h) : step_once<double>(h);
     if (s != GRTE_OK) return s;
     CK(cudaMemcpyAsync(hits.data(), h->D.gits, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1248,16 +1465,30 @@ grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t le
   return get_cells(h, inst, src, out, len);
 }
 
+// Copy n bulk elements from device offset `off` (in elements) of `base` into doubles.
+static grte_status copy_bulk(grte_t h, const void* base, int64_t off, int64_t n, double* out) {
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->opt.precision == GRTE_MIXED) {
+    std::vector<float> t(n);
+    CK(cudaMemcpy(t.data(), (const float*)base + off, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) out[i] = t[i];
+  } else {
+    CK(cudaMemcpy(out, (const double*)base + off, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  }
+  return GRTE_OK;
+}
+
 grte_status grte_get_E(grte_t h, int inst, double* E, size_t len) {
   if (!h) return GRTE_EINVAL;
   if (inst < 0 || inst >= h->n_inst || !E) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
   const Inst& I = h->inst[inst];
   if (len != (size_t)I.N * I.M) return fail(h, GRTE_EINVAL, "len must equal nx*M");
-  std::vector<double> t((size_t)I.N * I.M);
-  CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpy(t.data(), h->D.E + I.elem_off, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+  std::vector<double> t((size_t)I.N * I.M), U(I.N);
+  grte_status s = copy_bulk(h, h->D.Eh, I.elem_off, (int64_t)t.size(), t.data());
+  if (s != GRTE_OK) return s;
+  CK(cudaMemcpy(U.data(), h->D.U + I.cell_off, sizeof(double) * I.N, cudaMemcpyDeviceToHost));
   for (int64_t k = 0; k < I.M; ++k)
-    for (int64_t j = 0; j < I.N; ++j) E[j * I.M + k] = t[k * I.N + j];
+    for (int64_t j = 0; j < I.N; ++j) E[j * I.M + k] = I.a * I.c * U[j] + t[k * I.N + j];
   return device_status(h);
 }
 
@@ -1267,8 +1498,8 @@ grte_status grte_get_O(grte_t h, int inst, double* O, size_t len) {
   const Inst& I = h->inst[inst];
   if (len != (size_t)(I.N + 1) * I.M) return fail(h, GRTE_EINVAL, "len must equal (nx+1)*M");
   std::vector<double> t((size_t)(I.N + 1) * I.M);
-  CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpy(t.data(), h->D.O + I.nelem_off, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+  grte_status s = copy_bulk(h, h->D.O, I.nelem_off, (int64_t)t.size(), t.data());
+  if (s != GRTE_OK) return s;
   for (int64_t k = 0; k < I.M; ++k)
     for (int64_t i = 0; i <= I.N; ++i) O[i * I.M + k] = t[k * (I.N + 1) + i];
   return device_status(h);
@@ -1314,7 +1545,8 @@ grte_status grte_get_energy(grte_t h, int inst, double* out, size_t n) {
   if (inst < 0 || inst >= h->n_inst || !out || n != 3) return fail(h, GRTE_EINVAL, "bad instance, NULL output or n != 3");
   if (!h->state_set) return fail(h, GRTE_ESTATE, "state not set");
   // refresh the energy of the current state; the accumulated terms are untouched
-  k_energy<<<h->n_inst, kTriThreads, 0, h->stream>>>(h->D, 0);
+  if (h->opt.precision == GRTE_MIXED) k_energy<float><<<h->n_inst, kTriThreads, 0, h->stream>>>(h->D, 0);
+  else k_energy<double><<<h->n_inst, kTriThreads, 0, h->stream>>>(h->D, 0);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(out, h->D.energy + 3 * inst, sizeof(double) * 3, cudaMemcpyDeviceToHost));

@@ -23,6 +23,8 @@ namespace grte {
 
 constexpr int kTriThreads = 256;          // threads (and at most this many chunks) per CTA
 constexpr int kTriMaxRed = 2 * kTriThreads;
+constexpr int kB = 8;                     // elements per block of the serial sweeps
+constexpr int kMaxLevels = 10;            // PCR levels for up to 2*kTriThreads reduced equations
 
 __host__ __device__ inline int tri_chunks(int64_t n) {
   int64_t p = n / 2;
@@ -71,43 +73,83 @@ __device__ void tri_solve(const Cf& cf, int64_t n, R* __restrict__ x, R* __restr
     if (len >= 3) {
       // down sweep over the interior s+1..e-1:
       //   x_j = rhat_j - chat_j x_{j+1} - ahat_j x_s
+      // The recurrences are serial, so the loads of each block of kB elements are
+      // issued together ahead of the dependent arithmetic (one memory latency per
+      // block instead of one per element).
       R rh = 0, ch = 0, ah = 0;
-      for (int64_t j = s + 1; j <= e - 1; ++j) {
-        R aj = cf.a(j);
-        R rj = x[j];
-        R inv;
-        if (FACTOR) {
-          R bj = cf.b(j), cj = cf.c(j);
-          R den = (j == s + 1) ? bj : bj - aj * ch;
-          inv = R(1) / den;
+      int64_t j = s + 1;
+      if (FACTOR) {
+        for (; j <= e - 1; ++j) {
+          const R aj = cf.a(j), bj = cf.b(j), cj = cf.c(j), rj = x[j];
+          const R den = (j == s + 1) ? bj : bj - aj * ch;
+          const R inv = R(1) / den;
           ah = (j == s + 1) ? aj * inv : -aj * ah * inv;
           ch = cj * inv;
           f_inv[j] = inv;
           f_ch[j] = ch;
           f_ac[j] = ah;            // a-hat for now; becomes a-check in the up sweep
-        } else {
-          inv = f_inv[j];
+          rh = (j == s + 1) ? rj * inv : (rj - aj * rh) * inv;
+          x[j] = rh;
         }
-        rh = (j == s + 1) ? rj * inv : (rj - aj * rh) * inv;
+      } else {
+        rh = x[j] * f_inv[j];
         x[j] = rh;
+        ++j;
+        for (; j + kB - 1 <= e - 1; j += kB) {
+          R xv[kB], iv[kB], av[kB];
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            xv[u] = x[j + u];
+            iv[u] = f_inv[j + u];
+            av[u] = cf.a(j + u);
+          }
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            rh = (xv[u] - av[u] * rh) * iv[u];
+            xv[u] = rh;
+          }
+#pragma unroll
+          for (int u = 0; u < kB; ++u) x[j + u] = xv[u];
+        }
+        for (; j <= e - 1; ++j) {
+          rh = (x[j] - cf.a(j) * rh) * f_inv[j];
+          x[j] = rh;
+        }
       }
       // up sweep: x_j = rcheck_j - ccheck_j x_e - acheck_j x_s
       R rc = x[e - 1];
-      R cc = 0, ac = 0;
       if (FACTOR) {
-        cc = f_ch[e - 1];
-        ac = f_ac[e - 1];
+        R cc = f_ch[e - 1], ac = f_ac[e - 1];
         f_cc[e - 1] = cc;
-      }
-      for (int64_t j = e - 2; j >= s + 1; --j) {
-        R chj = f_ch[j];
-        rc = x[j] - chj * rc;
-        x[j] = rc;
-        if (FACTOR) {
+        for (int64_t jj = e - 2; jj >= s + 1; --jj) {
+          const R chj = f_ch[jj];
+          rc = x[jj] - chj * rc;
+          x[jj] = rc;
           cc = -chj * cc;
-          ac = f_ac[j] - chj * ac;
-          f_cc[j] = cc;
-          f_ac[j] = ac;
+          ac = f_ac[jj] - chj * ac;
+          f_cc[jj] = cc;
+          f_ac[jj] = ac;
+        }
+      } else {
+        int64_t jj = e - 2;
+        for (; jj - (kB - 1) >= s + 1; jj -= kB) {
+          R xv[kB], cv[kB];
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            xv[u] = x[jj - u];
+            cv[u] = f_ch[jj - u];
+          }
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            rc = xv[u] - cv[u] * rc;
+            xv[u] = rc;
+          }
+#pragma unroll
+          for (int u = 0; u < kB; ++u) x[jj - u] = xv[u];
+        }
+        for (; jj >= s + 1; --jj) {
+          rc = x[jj] - f_ch[jj] * rc;
+          x[jj] = rc;
         }
       }
       // reduced rows of x_s and x_e
@@ -140,12 +182,32 @@ __device__ void tri_solve(const Cf& cf, int64_t n, R* __restrict__ x, R* __restr
   __syncthreads();
 
   // ---- phase B: parallel cyclic reduction on the nr reduced equations -----------
+  // SOLVE mode: every level's multipliers of this thread's equations are loaded
+  // before the first level (one memory latency instead of one per level)
+  R pk1[kMaxLevels][2], pk2[kMaxLevels][2];
+  if (!FACTOR) {
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int i = tid + q * blockDim.x;
+        if (l < L && i < nr) {
+          pk1[l][q] = Rd[(int64_t)l * 2 * nr + i];
+          pk2[l][q] = Rd[(int64_t)l * 2 * nr + nr + i];
+        }
+      }
+  }
   int cur = 0;
-  for (int l = 0; l < L; ++l) {
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l >= L) break;
     const int st = 1 << l;
     R* k1s = Rd + (int64_t)l * 2 * nr;
     R* k2s = k1s + nr;
-    for (int i = tid; i < nr; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = tid + q * blockDim.x;
+      if (i >= nr) continue;
       const bool hasL = i - st >= 0, hasR = i + st < nr;
       R k1, k2;
       if (FACTOR) {
@@ -160,8 +222,8 @@ __device__ void tri_solve(const Cf& cf, int64_t n, R* __restrict__ x, R* __restr
         if (hasR) bn -= sm.a[cur][i + st] * k2;
         sm.b[cur ^ 1][i] = bn;
       } else {
-        k1 = k1s[i];
-        k2 = k2s[i];
+        k1 = pk1[l][q];
+        k2 = pk2[l][q];
       }
       R rn = sm.r[cur][i];
       if (hasL) rn -= sm.r[cur][i - st] * k1;
@@ -192,6 +254,7 @@ __device__ void tri_solve(const Cf& cf, int64_t n, R* __restrict__ x, R* __restr
     const R xs = sm.r[cur][2 * tid], xe = sm.r[cur][2 * tid + 1];
     x[s] = xs;
     x[e] = xe;
+#pragma unroll 4
     for (int64_t j = s + 1; j <= e - 1; ++j) x[j] = x[j] - f_cc[j] * xe - f_ac[j] * xs;
   }
   __syncthreads();

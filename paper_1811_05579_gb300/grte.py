@@ -108,7 +108,7 @@ class Grte:
     """Handle over n independent 1D instances (grte_create_1d)."""
 
     def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
-                 krylov_maxcycles=6, newton_maxit=60, energy_every=0, stream=None):
+                 krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None):
         L = lib()
         self._keep = []
         arr = (Instance1D * len(instances))()

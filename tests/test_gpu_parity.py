@@ -236,3 +236,58 @@ def test_energy_sums_balance_inflow(G):
     assert abs(e[1] - fsum) < 1e-11 * max(abs(fsum), 1e-300)
     assert abs((e[0] + e[1] - e[2]) - (e0[0])) < 1e-12 * e0[0]
     h.close()
+
+
+# ------------------------------------------------------------------ mixed precision
+# Binary32 angular bulk, binary64 per-cell parts, Newton and sums: T within 1e-5
+# relative of the FP64 oracle (the tolerance stated for reduced precision).
+MIXED_TOL = 1e-5
+
+
+@pytest.mark.parametrize("kind", ["const", "t3"])
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4])
+def test_mixed_one_step_vs_oracle(G, kind, eps):
+    P, spec = make(300, 16, eps, kind, "inflow")
+    S = state(P, 3, equilibrium=True)
+    h = G.Grte([spec], precision=G.MIXED)
+    h.set_state(0, S.T)
+    h.step(2)
+    S2 = og.run(P, S, 2)
+    check(h.T(0, allow=(5,)), S2.T, MIXED_TOL, "T (mixed)")
+    Oc = 0.5 * (S2.O[:-1] + S2.O[1:])
+    check(h.E(0, allow=(5,)), S2.E, 1e-4, "E (mixed)", np.abs(S2.E) + np.abs(P.eps * Oc))
+    h.close()
+
+
+def test_mixed_marshak_full_run(G):
+    inst = wl.marshak_1d()
+    v, w = gauss_legendre_half(inst.n_dir)
+    P = og.Problem(N=inst.nx, v=v, w=w, sig=inst.sigma, eps=inst.eps, dt=inst.dt, kind="t3",
+                   bL=np.ones(v.size), bR=np.zeros(v.size))
+    spec = dict(nx=inst.nx, n_angle=v.size, v=v, w=w, sigma=inst.sigma, kind=1, bc=0,
+                bL=P.bL, bR=P.bR, dt=inst.dt, eps=inst.eps)
+    h = G.Grte([spec], precision=G.MIXED)
+    h.set_state(0, inst.T0)
+    h.step(inst.steps)
+    S = og.run(P, og.equilibrium_state(P, inst.T0), inst.steps)
+    check(h.T(0, allow=(5,)), S.T, MIXED_TOL, "T (mixed, 128 steps)")
+    h.close()
+
+
+def test_mixed_vs_fp64_full_size_slab(G):
+    """The six 8192-cell, 64-direction runs, 20 steps: mixed vs FP64 on the GPU (FP64
+    itself is checked against the oracle above)."""
+    from bench import workload_instances, specs_of
+    runs, _ = workload_instances("slab6")
+    specs = specs_of(runs)
+    hd = G.Grte(specs)
+    hm = G.Grte(specs, precision=G.MIXED)
+    for i, r in enumerate(runs):
+        hd.set_state(i, r.T0)
+        hm.set_state(i, r.T0)
+    hd.step(20)
+    hm.step(20)
+    for i in range(len(runs)):
+        check(hm.T(i, allow=(5,)), hd.T(i, allow=(5,)), MIXED_TOL, "T run %d" % i)
+    hd.close()
+    hm.close()
