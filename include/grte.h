@@ -153,6 +153,27 @@ int64_t grte_last_launches(grte_t h);
 const char* grte_last_error(grte_t h);
 void grte_destroy(grte_t h);   /* NULL is a no-op */
 
+/* Steps without any allocation (the paper has no counterpart; this is a service to
+ * callers that cannot allocate device memory - for instance code running inside a
+ * memory pool or allocator callback, under a strict memory budget, or in a process
+ * whose allocator must not be re-entered).  It advances ONE instance `inst` by
+ * nsteps steps of grte_step (FP64 only; opt may be NULL; opt->stream is ignored and
+ * `stream` is used), with the state in caller-owned device memory, updated in place:
+ *   T  device, nx doubles;
+ *   E  device, nx*M doubles, line-major E[k*nx + j] (the device layout of grte.h);
+ *   O  device, (nx+1)*M doubles, line-major O[k*(nx+1) + i].
+ * No cudaMalloc, cudaFree or other allocating call is made: every work buffer is
+ * carved from one static device array of about 9.2 MB that every GPU loading this
+ * library holds until the process exits.  Limits: nx <= 4096, n_angle <= 32,
+ * nx*n_angle <= 65536; larger sizes return GRTE_EINVAL.  The first call on a device
+ * looks up the device address of that array (cudaGetSymbolAddress, with the device
+ * current), so make that first call before any stream capture.  All calls share the
+ * array and each call clears what must start at zero (statuses, counters, Krylov
+ * scalars); calls whose execution overlaps on the GPU race with each other.  Returns
+ * the same statuses as grte_step + grte_sync (synchronises `stream`). */
+grte_status grte_step1d_noalloc(const grte_instance1d* inst, const grte_options* opt, double* T, double* E,
+                                double* O, int64_t nsteps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

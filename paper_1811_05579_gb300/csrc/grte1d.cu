@@ -990,7 +990,7 @@ struct grte_ctx {
   std::vector<Inst> inst;
   std::vector<Line> lines;
   std::vector<double> hv, hw;
-  int64_t ncell = 0, nelem = 0, nnelem = 0, nred = 0, npred = 0;
+  int64_t ncell = 0, nelem = 0, nnelem = 0, nred = 0, npred = 0, nlines = 0;
   grte_options opt{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -1205,6 +1205,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     h->hw.insert(h->hw.end(), w.begin(), w.end());
   }
   h->ncell = coff;
+  h->nlines = (int64_t)h->lines.size();
   h->nelem = eoff;
   h->nnelem = noff;
   h->nred = roff;
@@ -1340,8 +1341,9 @@ static grte_status step_once(grte_t h) {
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const int ni = h->n_inst;
-  const int nl = (int)h->lines.size();
+  const int nl = (int)h->nlines;
   const int64_t nc = h->ncell;
+  const int64_t vstride = D.gz - D.gx;   // cell stride of the Krylov basis (as in k_gmres)
   const int cb = 256;
   const unsigned cgrid = (unsigned)((nc + cb - 1) / cb);
   // prediction coefficients at T^n, rho^n, initial iterate x = rho^n
@@ -1356,8 +1358,8 @@ static grte_status step_once(grte_t h) {
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
-      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gV + (int64_t)j * nc, 0));
-      LAUNCH(GRTE_K_PRED_HOM, (k_pred_line<PRED_HOM, R><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * nc)));
+      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gV + (int64_t)j * vstride, 0));
+      LAUNCH(GRTE_K_PRED_HOM, (k_pred_line<PRED_HOM, R><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * vstride)));
       LAUNCH(GRTE_K_GMRES, (k_gmres<G_ARNOLDI, R><<<ni * kCL, kTriThreads, 0, st>>>(D, j)));
       // a Krylov direction pass costs far more than a round trip: after the first
       // iteration, stop launching once no instance is still iterating
@@ -1381,11 +1383,13 @@ static grte_status step_once(grte_t h) {
     if (all) break;
     if (cycles >= h->opt.krylov_maxcycles) {
       // flag the instances that did not converge
-      std::vector<int> s(ni);
-      CK(cudaMemcpy(s.data(), D.status, sizeof(int) * ni, cudaMemcpyDeviceToHost));
-      for (int i = 0; i < ni; ++i)
-        if (!h->h_flags[i]) s[i] |= 1 << GRTE_ENONCONV;
-      CK(cudaMemcpy(D.status, s.data(), sizeof(int) * ni, cudaMemcpyHostToDevice));
+      for (int i = 0; i < ni; ++i) {
+        if (h->h_flags[i]) continue;
+        int si = 0;
+        CK(cudaMemcpy(&si, D.status + i, sizeof(int), cudaMemcpyDeviceToHost));
+        si |= 1 << GRTE_ENONCONV;
+        CK(cudaMemcpy(D.status + i, &si, sizeof(int), cudaMemcpyHostToDevice));
+      }
       break;
     }
   }
@@ -1609,3 +1613,247 @@ grte_status grte_profile_end(grte_t h, double* ms, int64_t* launches, size_t n) 
 int64_t grte_last_launches(grte_t h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// =============================================================================== no-allocation step
+// grte_step1d_noalloc: the steps of grte_step for one FP64 instance whose state lives
+// in caller-owned device memory, with every work buffer carved out of one file-scope
+// device array (no cudaMalloc, cudaFree or other allocating call on any path).
+namespace grte {
+constexpr int64_t kNaMaxCells = 4096;
+constexpr int kNaMaxAngles = 32;
+constexpr int64_t kNaMaxElems = 65536;                      // nx * n_angle
+constexpr int64_t kNaMaxNodeElems = kNaMaxElems + kNaMaxAngles;
+constexpr int64_t kNaCellArrays = 39;                       // per-cell double arrays (37 + the x/z pair)
+constexpr int64_t kNaAlign = 256;
+__host__ __device__ constexpr int64_t na_round(int64_t b) { return (b + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr int64_t kNaRedLine = 10 * 2 * kTriMaxRed + kTriMaxRed;   // >= tri_red_size(n) for any n
+constexpr int64_t kNaBytes =
+    kNaCellArrays * na_round(8 * kNaMaxCells) +                     // per-cell arrays
+    na_round(8 * 4 * kNaMaxCells) +                                 // preconditioner factors
+    na_round(8 * kCL * kNaRedLine) +                                // preconditioner reduced systems
+    na_round(8 * (kMaxRestart + 1) * kNaMaxCells) +                 // Krylov basis
+    na_round(8 * kNaMaxElems) * 3 +                                 // Eh, xb, S
+    na_round(8 * 4 * kNaMaxElems) +                                 // line factors
+    na_round(8 * kNaMaxNodeElems) +                                 // node scratch
+    na_round(8 * kNaMaxAngles * kNaRedLine) +                        // line reduced systems
+    na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) + // v, w, bL, bR; Swall
+    na_round(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL)) +
+    na_round(4 * 16) + na_round(sizeof(Inst)) + na_round(sizeof(Line) * kNaMaxAngles) + na_round(8);
+}  // namespace grte
+
+// Work memory of grte_step1d_noalloc: kNaBytes (about 8.5 MB), held by every GPU that
+// loads the library until the process exits.  Calls share it (see include/grte.h).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[grte::kNaBytes];
+static void* g_noalloc_base[64];   // device address of g_noalloc_scratch, per device
+
+namespace grte {
+__global__ void k_na_prepare(const double* __restrict__ T, const double* __restrict__ E, double* __restrict__ U,
+                             double* __restrict__ Eh, int64_t N, int M, double ac) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid < N) {
+    const double t = T[gid];
+    U[gid] = (t * t) * (t * t);
+  }
+  if (gid < N * M) {
+    const double t = T[gid % N];
+    Eh[gid] = E[gid] - ac * ((t * t) * (t * t));
+  }
+}
+__global__ void k_na_finish(const double* __restrict__ U, const double* __restrict__ Eh, double* __restrict__ E,
+                            int64_t N, int M, double ac) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid < N * M) E[gid] = ac * U[gid % N] + Eh[gid];
+}
+
+// Gauss-Legendre, positive half, into fixed arrays (n <= 2 kNaMaxAngles).
+static void gl_half_fixed(int n, double* v, double* w) {
+  const int M = n / 2;
+  for (int i = 0; i < M; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double d = p1 / dp;
+      x -= d;
+      if (fabs(d) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (x * p1 - p0) / (x * x - 1.0);
+    v[M - 1 - i] = x;
+    w[M - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+}  // namespace grte
+
+extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_options* opt, double* T,
+                                           double* E, double* O, int64_t nsteps, void* stream) {
+  using namespace grte;
+  if (!p || !T || !E || !O || nsteps < 0) return GRTE_EINVAL;
+  grte_options o;
+  grte_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != GRTE_FP64) return GRTE_EINVAL;
+  if (o.krylov_restart < 1 || o.krylov_restart > kMaxRestart || o.krylov_maxcycles < 1 || o.newton_maxit < 1 ||
+      !(o.krylov_rtol > 0))
+    return GRTE_EINVAL;
+  const int64_t N = p->nx;
+  const int M = p->n_angle;
+  // size limits of the static work memory
+  if (N < 2 || N > kNaMaxCells || M < 1 || M > kNaMaxAngles || N * M > kNaMaxElems) return GRTE_EINVAL;
+  if (!p->sigma || (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3) ||
+      (p->bc != GRTE_BC_INFLOW && p->bc != GRTE_BC_REFLECT))
+    return GRTE_EINVAL;
+  if (!(p->x1 > p->x0) || !(p->dt > 0) || !(p->a > 0) || !(p->c > 0) || !(p->Cv > 0) || !(p->eps > 0))
+    return GRTE_EINVAL;
+  if ((p->v == nullptr) != (p->w == nullptr)) return GRTE_EINVAL;
+  double v[kNaMaxAngles], w[kNaMaxAngles], bL[kNaMaxAngles], bR[kNaMaxAngles];
+  if (p->v) {
+    for (int k = 0; k < M; ++k) { v[k] = p->v[k]; w[k] = p->w[k]; }
+  } else {
+    gl_half_fixed(2 * M, v, w);
+  }
+  double sw = 0.0;
+  for (int k = 0; k < M; ++k) {
+    if (!(v[k] > 0.0 && v[k] <= 1.0) || !(w[k] > 0.0)) return GRTE_EINVAL;
+    sw += w[k];
+  }
+  for (int k = 0; k < M; ++k) w[k] /= sw;
+  for (int64_t j = 0; j < N; ++j)
+    if (!(p->sigma[j] >= 0.0) || !std::isfinite(p->sigma[j])) return GRTE_EINVAL;
+  Inst I{};
+  I.N = (int)N; I.M = M; I.kind = p->sigma_kind; I.bc = p->bc; I.eps = p->eps; I.dt = p->dt;
+  I.dx = (p->x1 - p->x0) / (double)N; I.a = p->a; I.c = p->c; I.Cv = p->Cv;
+  double wv = 0, wv2 = 0, fl = 0, fr = 0;
+  for (int k = 0; k < M; ++k) {
+    bL[k] = (p->bc == GRTE_BC_INFLOW && p->bL) ? p->bL[k] : 0.0;
+    bR[k] = (p->bc == GRTE_BC_INFLOW && p->bR) ? p->bR[k] : 0.0;
+    wv += w[k] * v[k];
+    wv2 += w[k] * v[k] * v[k];
+    fl += w[k] * v[k] * bL[k];
+    fr += w[k] * v[k] * bR[k];
+  }
+  I.wv = wv; I.wv2 = wv2; I.two_eps = 2.0 / p->eps; I.inv_eps = 1.0 / p->eps; I.bLflux = fl; I.bRflux = fr;
+  I.cell_off = 0; I.elem_off = 0; I.nelem_off = 0; I.red_off = 0; I.ang_off = 0; I.line_off = 0;
+  Line lines[kNaMaxAngles];
+  for (int k = 0; k < M; ++k) lines[k] = Line{0, k, (int64_t)k * kNaRedLine};
+
+  // device address of the static work memory: looked up once per device, with the
+  // device current (the host-side symbol is not a device address)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GRTE_ECUDA;
+  if (!g_noalloc_base[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return GRTE_ECUDA;
+    g_noalloc_base[dev] = ptr;
+  }
+  unsigned char* cur = (unsigned char*)g_noalloc_base[dev];
+  auto take = [&](int64_t bytes) { unsigned char* q = cur; cur += na_round(bytes); return (void*)q; };
+  Dev D{};
+  double** cells[kNaCellArrays - 2] = {&D.U, &D.sig, &D.rho_n, &D.rho_s, &D.Fs, &D.Us, &D.newton_its, &D.P1, &D.P2,
+                                   &D.P3, &D.Frho, &D.gU, &D.Q1, &D.Q2, &D.gwork, &D.cf.kc, &D.cf.s,
+                                   &D.cf.alpha, &D.cf.A, &D.cf.gam, &D.cf.gl, &D.cf.gu, &D.cf.gb, &D.cf.dl,
+                                   &D.cf.od, &D.cf.dlx, &D.cf.kcd, &D.cf.kdx, &D.cf.sac, &D.cf.ralpha,
+                                   &D.cf.ratio, &D.cf.fR, &D.cf.fL, &D.cf.gbx, &D.pG, &D.pH, &D.gw};
+  for (int i = 0; i < kNaCellArrays - 2; ++i) *cells[i] = (double*)take(8 * kNaMaxCells);
+  // x and z of the Krylov kernels are adjacent: the kernels take the cell stride of
+  // the basis as gz - gx, here kNaMaxCells
+  D.gx = (double*)take(8 * 2 * kNaMaxCells);
+  D.gz = D.gx + kNaMaxCells;
+  D.pF = (double*)take(8 * 4 * kNaMaxCells);
+  D.pRd = (double*)take(8 * kCL * kNaRedLine);
+  D.gV = (double*)take(8 * (kMaxRestart + 1) * kNaMaxCells);
+  D.Eh = take(8 * kNaMaxElems);
+  D.xb = take(8 * kNaMaxElems);
+  D.S = take(8 * kNaMaxElems);
+  D.F = take(8 * 4 * kNaMaxElems);
+  D.onode = take(8 * kNaMaxNodeElems);
+  D.Rd = take(8 * kNaMaxAngles * kNaRedLine);
+  double* vw = (double*)take(8 * 4 * kNaMaxAngles);
+  D.v = vw; D.w = vw + kNaMaxAngles; D.bL = vw + 2 * kNaMaxAngles; D.bR = vw + 3 * kNaMaxAngles;
+  D.Swall = (double*)take(8 * 2 * kNaMaxAngles);
+  double* small = (double*)take(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL));
+  D.gH = small;
+  D.gg = D.gH + (kMaxRestart + 1) * kMaxRestart;
+  D.gcs = D.gg + kMaxRestart + 1;
+  D.gsn = D.gcs + kMaxRestart;
+  D.gbeta = D.gsn + kMaxRestart;
+  D.gxn = D.gbeta + 1;
+  D.energy = D.gxn + 1;
+  D.pInv = D.energy + 4;
+  int* ints = (int*)take(4 * 16);
+  D.gactive = ints; D.gk = ints + 1; D.gdone = ints + 2; D.gits = ints + 3; D.gcycles = ints + 4;
+  D.gestconv = ints + 5; D.status = ints + 6;
+  Inst* d_inst = (Inst*)take(sizeof(Inst));
+  Line* d_lines = (Line*)take(sizeof(Line) * kNaMaxAngles);
+  int64_t* d_cell_start = (int64_t*)take(8);
+  if (cur - (unsigned char*)g_noalloc_base[dev] > kNaBytes) return GRTE_ENOMEM;   // layout check
+  D.T = T;
+  D.O = O;
+  D.inst = d_inst;
+  D.lines = d_lines;
+  D.m = o.krylov_restart;
+  D.rtol = o.krylov_rtol;
+  D.stall = 1e-9;
+  D.wfloor = 1e-13;
+  D.mixed = 0;
+  D.newton_maxit = o.newton_maxit;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t zero64 = 0;
+#define NA(call) do { if ((call) != cudaSuccess) return GRTE_ECUDA; } while (0)
+  NA(cudaMemcpyAsync(d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(d_lines, lines, sizeof(Line) * M, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(d_cell_start, &zero64, 8, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(D.v, v, 8 * M, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(D.w, w, 8 * M, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(D.bL, bL, 8 * M, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(D.bR, bR, 8 * M, cudaMemcpyHostToDevice, st));
+  NA(cudaMemcpyAsync(D.sig, p->sigma, 8 * N, cudaMemcpyHostToDevice, st));
+  // what must start at zero: statuses, counters, energy sums, Krylov scalars
+  NA(cudaMemsetAsync(ints, 0, 4 * 16, st));
+  NA(cudaMemsetAsync(small, 0, 8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL), st));
+  const double ac = p->a * p->c;
+  const unsigned eb = (unsigned)((N * M + 255) / 256);
+  k_na_prepare<<<eb, 256, 0, st>>>(T, E, D.U, (double*)D.Eh, N, M, ac);
+  NA(cudaGetLastError());
+  // a handle that lives on this stack frame and refers only to the memory above
+  grte_ctx ctx;
+  ctx.n_inst = 1;
+  ctx.ncell = N;
+  ctx.nelem = N * M;
+  ctx.nnelem = (N + 1) * M;
+  ctx.nlines = M;
+  ctx.opt = o;
+  ctx.opt.energy_every = 0;
+  ctx.stream = st;
+  ctx.D = D;
+  ctx.d_cell_start = d_cell_start;
+  ctx.d_inst = d_inst;
+  ctx.d_lines = d_lines;
+  int flag_buf[1] = {0};
+  ctx.h_flags = flag_buf;
+  ctx.state_set = true;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    grte_status s = step_once<double>(&ctx);
+    if (s != GRTE_OK) { ctx.h_flags = nullptr; return s; }
+  }
+  ctx.h_flags = nullptr;   // not owned
+  k_na_finish<<<eb, 256, 0, st>>>(D.U, (const double*)D.Eh, E, N, M, ac);
+  NA(cudaGetLastError());
+  int status = 0;
+  NA(cudaMemcpyAsync(&status, D.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NA(cudaStreamSynchronize(st));
+#undef NA
+  for (int code : {GRTE_ENAN, GRTE_ENONCONV, GRTE_ENEGATIVE, GRTE_ETIMEOUT})
+    if (status & (1 << code)) return (grte_status)code;
+  return GRTE_OK;
+}

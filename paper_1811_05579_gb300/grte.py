@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
             "grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O", "grte_get_I", "grte_get_stage",
             "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy",
-            "grte_profile_begin", "grte_profile_end", "grte_last_launches", "grte_get_energy"]
+            "grte_profile_begin", "grte_profile_end", "grte_last_launches", "grte_get_energy",
+            "grte_step1d_noalloc"]
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
            "project", "energy"]
 
@@ -77,6 +78,8 @@ def load_library(path=LIB_PATH):
     lib.grte_last_launches.argtypes = [ctypes.c_void_p]
     lib.grte_last_launches.restype = ctypes.c_int64
     lib.grte_get_energy.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_step1d_noalloc.argtypes = [ctypes.POINTER(Instance1D), ctypes.POINTER(Options), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     return lib
 
 
@@ -102,6 +105,29 @@ def _ptr(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def instance_struct(p, keep):
+    """Fill an Instance1D from a spec dict (arrays kept alive in `keep`)."""
+    sig = _f64(np.broadcast_to(p["sigma"], (p["nx"],)))
+    v = _f64(p.get("v"))
+    w = _f64(p.get("w"))
+    M = p["n_angle"]
+    bL = _f64(np.broadcast_to(p.get("bL", 0.0), (M,)))
+    bR = _f64(np.broadcast_to(p.get("bR", 0.0), (M,)))
+    keep += [sig, v, w, bL, bR]
+    return Instance1D(p["nx"], M, _ptr(v), _ptr(w), _ptr(sig), p.get("kind", SIGMA_T3),
+                      p.get("bc", BC_INFLOW), _ptr(bL), _ptr(bR), p.get("x0", 0.0),
+                      p.get("x1", 1.0), p["dt"], p.get("a", 1.0), p.get("c", 1.0),
+                      p.get("Cv", 1.0), p["eps"])
+
+
+def step1d_noalloc(spec, T_ptr, E_ptr, O_ptr, nsteps, stream=None):
+    """grte_step1d_noalloc on caller-owned device buffers (device addresses as ints):
+    T (nx), E (nx*M, line-major) and O ((nx+1)*M, line-major), updated in place."""
+    keep = []
+    inst = instance_struct(spec, keep)
+    return lib().grte_step1d_noalloc(ctypes.byref(inst), None, T_ptr, E_ptr, O_ptr, nsteps, stream)
 
 
 class Grte:
