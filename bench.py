@@ -171,6 +171,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--sequential-compare", action="store_true",
+                    help="also time the same instances advanced one handle at a time")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     runs, cfg = workload_instances(args.workload)
@@ -292,6 +294,29 @@ def main():
         hd.close()
         hm.close()
 
+    # the same instances, one handle each, stepped one after the other
+    seq = None
+    if args.sequential_compare:
+        hs = [G.Grte([sp], precision=prec, stream=stream.cuda_stream) for sp in specs]
+        for hh, r in zip(hs, runs):
+            hh.set_state(0, r.T0)
+        for hh in hs:
+            hh.step(1)
+        ks = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ks):
+            for hh in hs:
+                hh.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tseq = e0.elapsed_time(e1)
+        seq = {"value": updates_per_step * ks / (tseq * 1e-3), "ms_per_step": tseq / ks, "steps": ks,
+               "handles": len(hs)}
+        for hh in hs:
+            hh.close()
     hbm_peak = 6800.0
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -348,6 +373,8 @@ def main():
                 "clocks": clk}
         if cmp is not None:
             line["vs_fp64"] = cmp
+        if seq is not None:
+            line["sequential"] = seq
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

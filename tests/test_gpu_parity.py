@@ -291,3 +291,26 @@ def test_mixed_vs_fp64_full_size_slab(G):
         check(hm.T(i, allow=(5,)), hd.T(i, allow=(5,)), MIXED_TOL, "T run %d" % i)
     hd.close()
     hm.close()
+
+
+def test_batched_generator_instances_vs_oracle(G):
+    """Uneven batch from the batched-workload generator (sizes scaled down so that the
+    oracle runs in seconds): nx in [64, 512], 8/16/32 directions, eps in [1e-5, 1],
+    sigma_0 in [0.5, 50], all advanced in one handle, each compared with the oracle."""
+    insts = wl.batched_1d(10, seed=99, nx_range=(64, 512), n_dirs=(8, 16, 32))
+    specs, probs = [], []
+    for r in insts:
+        v, w = gauss_legendre_half(r.n_dir)
+        P = og.Problem(N=r.nx, v=v, w=w, sig=r.sigma, eps=r.eps, dt=r.dt, kind="t3",
+                       bL=np.full(v.size, r.bL), bR=np.full(v.size, r.bR))
+        probs.append(P)
+        specs.append(dict(nx=r.nx, n_angle=v.size, v=v, w=w, sigma=r.sigma, kind=1, bc=0, bL=P.bL,
+                          bR=P.bR, dt=r.dt, eps=r.eps))
+    h = G.Grte(specs)
+    for i, r in enumerate(insts):
+        h.set_state(i, r.T0)
+    h.step(2)
+    for i, (r, P) in enumerate(zip(insts, probs)):
+        S = og.run(P, og.equilibrium_state(P, r.T0), 2)
+        check(h.T(i, allow=(5,)), S.T, tol_cells(P, 2e-12), "T inst %d (nx %d, eps %.1e)" % (i, r.nx, r.eps))
+    h.close()
