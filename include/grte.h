@@ -153,6 +153,51 @@ int64_t grte_last_launches(grte_t h);
 const char* grte_last_error(grte_t h);
 void grte_destroy(grte_t h);   /* NULL is a no-op */
 
+/* ---- Learned initial guess of the per-cell Newton solve --------------------------------
+ * The paper solves the per-cell quartic of Eq. Tnp1 with "standard iterative solvers";
+ * it has no learned component.  This optional part supplies Newton's starting point from
+ * a small network 6 -> 64 -> 64 -> 64 -> 1 (GELU, BF16 weights, FP32 accumulation)
+ * trained on the GPU on (local state -> converged T^{n+1}) pairs that the scheme itself
+ * produces.  Newton still runs to convergence from the guess (one Newton step from any
+ * positive guess lands at or above the root of the convex quartic, and the start is
+ * clamped to the plain upper bound min((R/A)^{1/4}, R/B), so the residual can only shrink),
+ * so the converged T is the same as without the guess.
+ * Raw features, per cell: log10 T^n, log10 rho*, log10 sigma_eff (sigma or sigma_0/T^3),
+ * log10 eps, log10 dt, log10 Cv; target y = log10(T^{n+1}/T^n). */
+enum { GRTE_MLP_IN = 6, GRTE_MLP_HIDDEN = 64, GRTE_MLP_NPARAMS = 8833 };
+typedef struct grte_mlp* grte_mlp_t;
+/* He-normal weights from `seed`, zero biases, identity standardisation. */
+grte_status grte_mlp_create(uint64_t seed, grte_mlp_t* out);
+void grte_mlp_destroy(grte_mlp_t m);   /* NULL is a no-op */
+const char* grte_mlp_last_error(grte_mlp_t m);
+/* Standardisation: network input (f - mean_in)/std_in, output y = out*std_out + mean_out. */
+grte_status grte_mlp_set_norm(grte_mlp_t m, const float* mean_in, const float* std_in, float mean_out, float std_out);
+/* FP32 master parameters, layout W1[64][6] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4 (host). */
+grte_status grte_mlp_get_params(grte_mlp_t m, float* p, size_t n);
+grte_status grte_mlp_set_params(grte_mlp_t m, const float* p, size_t n);
+/* y[i] (un-standardised) for n raw feature rows X[i*6 .. i*6+5] (host arrays). */
+grte_status grte_mlp_forward(grte_mlp_t m, const float* X, int64_t n, float* y);
+/* Gradient (n_grad = GRTE_MLP_NPARAMS) of the mean squared standardised error at the current
+ * BF16 weights, and that loss (host arrays). */
+grte_status grte_mlp_grad(grte_mlp_t m, const float* X, const float* y, int64_t n, float* grad, size_t n_grad,
+                          float* loss);
+/* Adam (lr, beta 0.9/0.999) over `epochs` seeded shuffles of the n samples in mini-batches. */
+grte_status grte_mlp_train(grte_mlp_t m, const float* X, const float* y, int64_t n, int epochs, int batch, float lr,
+                           uint64_t seed, float* loss);
+/* Use `m` (not owned; keep it alive while the handle steps) for Newton's starting point in
+ * every later step of h; NULL restores the plain start. */
+grte_status grte_set_guess(grte_t h, grte_mlp_t m);
+/* Newton's starting point: BOUND (default) min((R/A)^{1/4}, R/B), from which Newton
+ * decreases monotonically to the root; PREVIOUS one Newton step from T^n (the textbook
+ * start); LEARNED one Newton step from the network's guess, clamped to BOUND (set by
+ * grte_set_guess).  All three converge to the same root. */
+enum { GRTE_START_BOUND = 0, GRTE_START_PREVIOUS = 1, GRTE_START_LEARNED = 2 };
+grte_status grte_set_newton_start(grte_t h, int mode);
+/* 1: record the features and the converged target of every cell at each step (the last
+ * step's are returned by grte_get_newton_samples); 0: off. */
+grte_status grte_set_sample_logging(grte_t h, int on);
+grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size_t nx);
+
 /* Steps without any allocation (the paper has no counterpart; this is a service to
  * callers that cannot allocate device memory - for instance code running inside a
  * memory pool or allocator callback, under a strict memory budget, or in a process

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/grte.h"
+#include "mlp.cuh"
 #include "tridiag.cuh"
 
 namespace grte {
@@ -92,6 +93,10 @@ struct Dev {
   int *gactive, *gk, *gdone, *gits, *gcycles, *gestconv;
   int* status;
   double* energy;   // 3 per instance
+  // learned Newton guess: per-cell features (6 floats), predicted and logged targets
+  float *feat, *guess, *ytrue;
+  int use_guess, log_samples;
+  int start_prev;   // 1: Newton starts one step from T^n instead of the closed-form bound
   int m;  // restart length
   double rtol, stall, wfloor;
   int mixed;
@@ -819,6 +824,26 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
 // kap = 1 (sigma(x)) or K* = max(U*,0)^{3/4} (sigma_0/T^3).  Newton from
 // T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the unique root
 // (convex increasing left side); it stops when the iterate stops decreasing.
+// Raw features of the learned Newton guess for each cell (after the prediction):
+// log10 T^n, log10 rho*, log10 sigma_eff, log10 eps, log10 dt, log10 Cv.
+__global__ void k_newton_feat(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= ncell) return;
+  const Inst I = D.inst[inst_of(cell_inst_start, n_inst, gid)];
+  const double Tn = D.T[gid];
+  const double rho = D.gx[gid];
+  const double t3 = Tn * Tn * Tn;
+  const double sig_eff = (I.kind == GRTE_SIGMA_CONST) ? D.sig[gid] : D.sig[gid] / fmax(t3, 1e-300);
+  auto lg = [](double x) { return (float)log10(fmin(fmax(x, 1e-300), 1e300)); };
+  float* f = D.feat + 6 * gid;
+  f[0] = lg(Tn);
+  f[1] = lg(rho);
+  f[2] = lg(sig_eff);
+  f[3] = lg(I.eps);
+  f[4] = lg(I.dt);
+  f[5] = lg(I.Cv);
+}
+
 __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell) {
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= ncell) return;
@@ -852,7 +877,25 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
     double t = INFINITY;
     if (A > 0.0) t = sqrt(sqrt(R / A));
     if (B > 0.0) t = fmin(t, R / B);
-    for (its = 1; its <= D.newton_maxit; ++its) {
+    // the learned start is used where the network predicts a change of more than
+    // 10^0.01 - 1 (about 2.3%) in the step (above its prediction noise); elsewhere the
+    // closed-form bound is already within a step of the root and an extra guess step
+    // would only cost one
+    const bool learned = D.use_guess && fabs((double)D.guess[gid]) > 1e-2;
+    if (learned || D.start_prev) {
+      // learned (or previous-T) start: one Newton step from any positive guess lands
+      // at or above the root (convex left side).  The learned start is clamped to the
+      // closed-form bound, so its residual is never larger than the plain start's; the
+      // previous-T start is kept unclamped (the textbook start, for comparison).
+      const double g = learned ? Tn * exp10((double)D.guess[gid]) : Tn;
+      if (isfinite(g) && g > 0.0) {
+        const double g2 = g * g;
+        const double t1 = g - (A * g2 * g2 + B * g - R) / (4.0 * A * g2 * g + B);
+        if (isfinite(t1) && t1 > 0.0) t = learned ? fmin(t, t1) : t1;
+        ++its;
+      }
+    }
+    for (its = its + 1; its <= D.newton_maxit; ++its) {
       const double t2 = t * t;
       const double f = A * t2 * t2 + B * t - R;
       const double fp = 4.0 * A * t2 * t + B;
@@ -866,6 +909,7 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
   if (!isfinite(T) || !isfinite(R)) flag(D.status, lo, GRTE_ENAN);
   D.newton_its[gid] = its;
   D.T[gid] = T;            // T^{n+1}
+  if (D.log_samples) D.ytrue[gid] = (T > 0.0 && Tn > 0.0) ? (float)log10(T / Tn) : 0.0f;
 }
 
 // ----------------------------------------------------------------------------- correction
@@ -1010,6 +1054,7 @@ struct grte_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   int64_t launches = 0;
+  grte_mlp_t mlp = nullptr;   // learned Newton guess (not owned)
 };
 
 static cudaEvent_t pool_event(grte_t h) {
@@ -1395,6 +1440,13 @@ static grte_status step_once(grte_t h) {
   }
   h->stats.krylov_cycles += cycles;
   // correction substep 1 (per-cell Newton); T now holds T^{n+1}
+  if (D.use_guess || D.log_samples)
+    LAUNCH(GRTE_K_NEWTON, k_newton_feat<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
+  if (D.use_guess) {
+    cudaError_t e = mlp_guess_launch(h->mlp, D.feat, nc, D.guess, st);
+    if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("mlp guess: ") + cudaGetErrorString(e));
+    ++h->launches;
+  }
   LAUNCH(GRTE_K_NEWTON, k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
   // correction substep 2 + projection at T^{n+1}
   LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
@@ -1611,6 +1663,63 @@ grte_status grte_profile_end(grte_t h, double* ms, int64_t* launches, size_t n) 
 }
 
 int64_t grte_last_launches(grte_t h) { return h ? h->launches : 0; }
+
+static grte_status ensure_feat(grte_t h) {
+  Dev& D = h->D;
+  if (!D.feat) {
+    if (dalloc(h, &D.feat, 6 * h->ncell) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc feat");
+    if (dalloc(h, &D.guess, h->ncell) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc guess");
+    if (dalloc(h, &D.ytrue, h->ncell) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc ytrue");
+  }
+  return GRTE_OK;
+}
+
+grte_status grte_set_guess(grte_t h, grte_mlp_t m) {
+  if (!h) return GRTE_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  if (m) {
+    grte_status s = ensure_feat(h);
+    if (s != GRTE_OK) return s;
+  }
+  h->mlp = m;
+  h->D.use_guess = m ? 1 : 0;
+  h->D.start_prev = 0;
+  return GRTE_OK;
+}
+
+grte_status grte_set_newton_start(grte_t h, int mode) {
+  if (!h) return GRTE_EINVAL;
+  if (mode != GRTE_START_BOUND && mode != GRTE_START_PREVIOUS && mode != GRTE_START_LEARNED)
+    return fail(h, GRTE_EINVAL, "bad start mode");
+  if (mode == GRTE_START_LEARNED && !h->mlp) return fail(h, GRTE_ESTATE, "no network set (grte_set_guess)");
+  CK(cudaStreamSynchronize(h->stream));
+  h->D.start_prev = mode == GRTE_START_PREVIOUS ? 1 : 0;
+  h->D.use_guess = mode == GRTE_START_LEARNED ? 1 : 0;
+  return GRTE_OK;
+}
+
+grte_status grte_set_sample_logging(grte_t h, int on) {
+  if (!h) return GRTE_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  if (on) {
+    grte_status s = ensure_feat(h);
+    if (s != GRTE_OK) return s;
+  }
+  h->D.log_samples = on ? 1 : 0;
+  return GRTE_OK;
+}
+
+grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size_t nx) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !X || !y) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (nx != (size_t)I.N) return fail(h, GRTE_EINVAL, "nx must equal the instance's cell count");
+  if (!h->D.log_samples) return fail(h, GRTE_ESTATE, "sample logging is off");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(X, h->D.feat + 6 * I.cell_off, sizeof(float) * 6 * I.N, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(y, h->D.ytrue + I.cell_off, sizeof(float) * I.N, cudaMemcpyDeviceToHost));
+  return GRTE_OK;
+}
 
 }  // extern "C"
 

@@ -47,7 +47,13 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_get_T", "grte_get_rho", "grte_get_E", "grte_get_O", "grte_get_I", "grte_get_stage",
             "grte_get_quadrature", "grte_stats", "grte_last_error", "grte_destroy",
             "grte_profile_begin", "grte_profile_end", "grte_last_launches", "grte_get_energy",
-            "grte_step1d_noalloc"]
+            "grte_step1d_noalloc", "grte_mlp_create", "grte_mlp_destroy", "grte_mlp_last_error",
+            "grte_mlp_set_norm", "grte_mlp_get_params", "grte_mlp_set_params", "grte_mlp_forward",
+            "grte_mlp_grad", "grte_mlp_train", "grte_set_guess", "grte_set_sample_logging",
+            "grte_get_newton_samples", "grte_set_newton_start"]
+START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
+MLP_NPARAMS = 8833
+_fp = ctypes.POINTER(ctypes.c_float)
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
            "project", "energy"]
 
@@ -78,6 +84,22 @@ def load_library(path=LIB_PATH):
     lib.grte_last_launches.argtypes = [ctypes.c_void_p]
     lib.grte_last_launches.restype = ctypes.c_int64
     lib.grte_get_energy.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
+    lib.grte_mlp_destroy.argtypes = [ctypes.c_void_p]
+    lib.grte_mlp_destroy.restype = None
+    lib.grte_mlp_last_error.argtypes = [ctypes.c_void_p]
+    lib.grte_mlp_last_error.restype = ctypes.c_char_p
+    lib.grte_mlp_set_norm.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_float, ctypes.c_float]
+    lib.grte_mlp_get_params.argtypes = [ctypes.c_void_p, _fp, ctypes.c_size_t]
+    lib.grte_mlp_set_params.argtypes = [ctypes.c_void_p, _fp, ctypes.c_size_t]
+    lib.grte_mlp_forward.argtypes = [ctypes.c_void_p, _fp, ctypes.c_int64, _fp]
+    lib.grte_mlp_grad.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, _fp, ctypes.c_size_t, _fp]
+    lib.grte_mlp_train.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_float, ctypes.c_uint64, _fp]
+    lib.grte_set_guess.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.grte_set_sample_logging.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.grte_set_newton_start.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.grte_get_newton_samples.argtypes = [ctypes.c_void_p, ctypes.c_int, _fp, _fp, ctypes.c_size_t]
     lib.grte_step1d_noalloc.argtypes = [ctypes.POINTER(Instance1D), ctypes.POINTER(Options), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     return lib
@@ -128,6 +150,74 @@ def step1d_noalloc(spec, T_ptr, E_ptr, O_ptr, nsteps, stream=None):
     keep = []
     inst = instance_struct(spec, keep)
     return lib().grte_step1d_noalloc(ctypes.byref(inst), None, T_ptr, E_ptr, O_ptr, nsteps, stream)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_fp)
+
+
+class MLP:
+    """Learned Newton guess network (grte_mlp_*)."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        st = lib().grte_mlp_create(seed, ctypes.byref(h))
+        self.h = h
+        if st != GRTE_OK:
+            raise GrteError(st, "grte_mlp_create")
+
+    def _check(self, st):
+        if st != GRTE_OK:
+            raise GrteError(st, lib().grte_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if self.h is not None:
+            lib().grte_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_norm(self, mean_in, std_in, mean_out, std_out):
+        mi, si = _f32(mean_in), _f32(std_in)
+        self._check(lib().grte_mlp_set_norm(self.h, _fptr(mi), _fptr(si), float(mean_out), float(std_out)))
+
+    def params(self):
+        p = np.empty(MLP_NPARAMS, dtype=np.float32)
+        self._check(lib().grte_mlp_get_params(self.h, _fptr(p), p.size))
+        return p
+
+    def set_params(self, p):
+        p = _f32(p)
+        self._check(lib().grte_mlp_set_params(self.h, _fptr(p), p.size))
+
+    def forward(self, X):
+        X = _f32(X)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        self._check(lib().grte_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(y)))
+        return y
+
+    def grad(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        g = np.empty(MLP_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(lib().grte_mlp_grad(self.h, _fptr(X), _fptr(Y), X.shape[0], _fptr(g), g.size,
+                                        ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def train(self, X, Y, epochs=10, batch=1024, lr=1e-3, seed=0):
+        X, Y = _f32(X), _f32(Y)
+        loss = ctypes.c_float()
+        self._check(lib().grte_mlp_train(self.h, _fptr(X), _fptr(Y), X.shape[0], epochs, batch, lr, seed,
+                                         ctypes.byref(loss)))
+        return float(loss.value)
 
 
 class Grte:
@@ -254,6 +344,22 @@ class Grte:
 
     def last_launches(self):
         return int(lib().grte_last_launches(self.h))
+
+    def set_guess(self, mlp):
+        return self._check(lib().grte_set_guess(self.h, mlp.h if mlp is not None else None))
+
+    def set_newton_start(self, mode):
+        return self._check(lib().grte_set_newton_start(self.h, mode))
+
+    def set_sample_logging(self, on):
+        return self._check(lib().grte_set_sample_logging(self.h, 1 if on else 0))
+
+    def newton_samples(self, inst):
+        nx = self.specs[inst]["nx"]
+        X = np.empty((nx, 6), dtype=np.float32)
+        y = np.empty(nx, dtype=np.float32)
+        self._check(lib().grte_get_newton_samples(self.h, inst, _fptr(X), _fptr(y), nx))
+        return X, y
 
     def stats(self, allow=()):
         s = Stats()

@@ -424,3 +424,32 @@ def test_free_streaming_first_order():
         assert np.max(np.abs(S.T - 1.0)) == 0.0      # sigma = 0: T frozen exactly
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert min(rates) > 0.8, (errs, rates)
+
+
+# ---------------------------------------------------------------- learned-guess network (oracle)
+def test_mlp_oracle_backprop_matches_finite_differences():
+    """The FP64 backpropagation of oracle/mlp.py against central differences of its own
+    loss (weights kept in FP64 here, so the derivative is exact up to O(h^2))."""
+    from oracle import mlp as om
+    rng = np.random.default_rng(11)
+    p = 0.3 * rng.standard_normal(om.N_PARAMS)
+    x = rng.standard_normal((7, om.N_IN))
+    t = rng.standard_normal(7)
+    loss, g = om.loss_and_grad(p, x, t, bf16=False)
+    idx = rng.choice(om.N_PARAMS, 60, replace=False)
+    idx = np.concatenate([idx, [om.N_PARAMS - 1, 0]])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (om.loss_and_grad(p + e, x, t, bf16=False)[0] - om.loss_and_grad(p - e, x, t, bf16=False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_bf16_rounding_is_nearest_even():
+    from oracle import mlp as om
+    assert om.to_bf16(np.float32(1.0)) == 1.0
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7 in bf16: ties to even (1.0)
+    assert om.to_bf16(np.float32(1.0 + 2 ** -8)) == 1.0
+    assert om.to_bf16(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6
+    assert om.to_bf16(np.float32(-2.5)) == -2.5
