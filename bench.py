@@ -34,9 +34,10 @@ FP64_PEAK_GFLOPS = 1250.0           # nominal GB300 FP64 (the profiling recipe's
 # (k_pred_line<HOM>): right-hand side 11, tridiagonal solve with stored factors 10,
 # flux of the two faces 10.
 HOM_FLOPS_PER_ELEM = 31
-# Bytes a binary32 line pass moves per line element with stored factors: 4 factors,
-# right-hand side written and solution read back, flux contribution written.
-LINE_BYTES_PER_ELEM_F32 = 4 * 4 + 2 * 4 + 4
+# Bytes a binary32 line pass with stored factors moves per line element: the five
+# factor values read (1/den, a, c-hat, c-check, a-check) and the flux contribution
+# written; the line's unknowns stay in shared memory.
+LINE_BYTES_PER_ELEM_F32 = 5 * 4 + 4
 
 
 def workload_instances(name):
@@ -171,6 +172,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--line-threads", type=int, default=0, choices=[0, 256, 512, 1024],
+                    help="threads per line solve (0: the library's autotuner)")
     ap.add_argument("--sequential-compare", action="store_true",
                     help="also time the same instances advanced one handle at a time")
     args = ap.parse_args()
@@ -194,7 +197,7 @@ def main():
     stream = torch.cuda.current_stream()
     specs = specs_of(runs)
     prec = G.MIXED if args.precision == "mixed" else G.FP64
-    h = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
+    h = G.Grte(specs, precision=prec, stream=stream.cuda_stream, line_threads=args.line_threads)
     for i, r in enumerate(runs):
         h.set_state(i, r.T0)
     updates_per_step = sum(r.nx * r.n_dir for r in runs)
@@ -203,6 +206,7 @@ def main():
     for _ in range(args.warmup):
         h.step(1)
     h.sync(allow=(5,))
+    tune = h.tuning()
 
     def barrier():
         if dist is not None:
@@ -370,6 +374,7 @@ def main():
                 "kernel_share": {k: round(v[0] / tot_prof, 4) for k, v in sorted(prof.items())},
                 "krylov_iters_per_step": kry_its / args.steps / len(runs),
                 "krylov_cycles_per_step": kry_cycles / args.steps,
+                "line_tuning": {"threads": tune[0], "candidates_ms": tune[1], "smem": bool(h.stats(allow=(5,))["line_smem"])},
                 "clocks": clk}
         if cmp is not None:
             line["vs_fp64"] = cmp

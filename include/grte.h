@@ -83,6 +83,9 @@ typedef struct {
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */
   int energy_every;      /* 1: accumulate the energy sums of grte_get_energy every step; 0 off */
   void* stream;          /* cudaStream_t to run on; NULL: the library makes its own          */
+  int line_threads;      /* threads per line solve: 0 (default) = autotune at the first step
+                            (times the line kernels at 256, 512 and 1024 threads on this
+                            handle's instances and keeps the fastest), or 256, 512, 1024    */
 } grte_options;
 
 /* Statistics of the last grte_step call (summed over its steps and instances). */
@@ -93,6 +96,8 @@ typedef struct {
   int64_t newton_iters_max;  /* largest per-cell Newton count in the last step     */
   double newton_iters_mean;  /* mean per-cell Newton count in the last step        */
   int64_t status_flags;      /* OR over instances of (1 << grte_status) seen       */
+  int64_t line_threads;      /* threads per line solve in use (0 before the first step) */
+  int64_t line_smem;         /* 1: the line unknowns stay in shared memory           */
 } grte_stats_t;
 
 /* Fill *opt with the defaults. */
@@ -137,6 +142,11 @@ grte_status grte_get_energy(grte_t h, int inst, double* out, size_t n);
 grte_status grte_get_quadrature(grte_t h, int inst, double* v, double* w, size_t len);
 
 grte_status grte_stats(grte_t h, grte_stats_t* st);
+
+/* Line-solver tuning of the handle: *line_threads as in grte_stats_t, and ms[i] the
+ * timed cost (factor pass + 4 solve passes + correction pass, ms) of candidate
+ * 256 << i (i = 0..2; -1: not timed or not feasible).  n >= 3.  Errors: EINVAL. */
+grte_status grte_get_tuning(grte_t h, int* line_threads, double* ms, size_t n);
 
 /* Kernel ids for per-kernel timing. */
 enum { GRTE_K_CELL_COEF = 0, GRTE_K_RHO = 1, GRTE_K_PRED_FACTOR = 2, GRTE_K_PRED_HOM = 3,

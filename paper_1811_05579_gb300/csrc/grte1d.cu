@@ -52,6 +52,7 @@ struct Inst {
 struct Line {
   int inst, k;
   int64_t red_off;         // reduced-system storage of this line
+  int64_t f_off;           // factor storage of this line (tri_fac_size values)
 };
 
 // Per-cell coefficient arrays (length = total cells) for one operator family.
@@ -258,6 +259,17 @@ struct LineCoef {  // A + v^2 Gint + v Gbdry of one line, in the bulk type R
 
 enum { PRED_FULL_FACTOR = 0, PRED_FULL = 1, PRED_HOM = 2 };
 
+// Shared-memory layout of a line CTA: [x (padded), if XS] [reduced system].
+template <typename R, bool XS>
+__device__ __forceinline__ XAcc<R, XS> line_x(unsigned char* dsm, R* xglob) {
+  return XAcc<R, XS>{XS ? (R*)dsm : xglob};
+}
+template <typename R, bool XS>
+__device__ __forceinline__ R* line_red(unsigned char* dsm, int64_t N) {
+  const int64_t off = XS ? ((tri_xs_len(N) * (int64_t)sizeof(R) + 15) / 16) * 16 : 0;
+  return (R*)(dsm + off);
+}
+
 // One prediction pass over a line (instance, k) for the per-cell vector x (rho or a
 // Krylov direction): right-hand side of the e-equation
 //   r = h_k - alpha x - G_k x = P1 - v^2 P2 - v P3 + kappa/(c dt) Eh^n_k - kappa v D_k/dx
@@ -265,10 +277,12 @@ enum { PRED_FULL_FACTOR = 0, PRED_FULL = 1, PRED_HOM = 2 };
 // tridiagonal solve for e_k in R, and the e/o part of w_k v_k (O_{j+1,k} - O_{j,k})
 // into S (the rho part is Frho, per cell in double).  In the two wall cells the
 // right-hand side and the flux are formed in double: there (2/eps)(b - x) is an
-// O(eps) difference of O(1) numbers.  HOM passes carry no data.
-template <int MODE, typename R>
-__global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* __restrict__ xvec) {
-  __shared__ TriSmem<R> sm;
+// O(eps) difference of O(1) numbers.  HOM passes carry no data.  NT threads per
+// line; with XS the line's unknowns stay in shared memory for the whole pass (only
+// the flux leaves the CTA), else they live in the global scratch xb.
+template <int MODE, typename R, int NT, bool XS>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double* __restrict__ xvec) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   const Line L = D.lines[blockIdx.x];
   const Inst I = D.inst[L.inst];
   if (MODE == PRED_HOM && !D.gactive[L.inst]) return;
@@ -280,7 +294,7 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
   const double bR = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bR[I.ang_off + k];
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
   const double* x = xvec + co;
-  R* xb = (R*)D.xb + eo;
+  const XAcc<R, XS> xb = line_x<R, XS>(dsm, (R*)D.xb + eo);
   const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
                *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *P1 = D.P1 + co,
                *P2 = D.P2 + co, *P3 = D.P3 + co;
@@ -306,7 +320,7 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
     return r;
   };
 #pragma unroll 4
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+  for (int64_t j = threadIdx.x; j < N; j += NT) {
     const bool wall = inflow && (j == 0 || j == N - 1);
     if (!wall) {
       R r = R(P1[j]) - v2r * R(P2[j]) - vr * R(P3[j]);
@@ -318,10 +332,11 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
   }
   __syncthreads();
   LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v2, N};
-  R* F = (R*)D.F + 4 * I.elem_off + 4 * (int64_t)k * N;
+  R* F = (R*)D.F + L.f_off;
   R* Rd = (R*)D.Rd + L.red_off;
-  if (MODE == PRED_FULL_FACTOR) tri_solve<true>(cfl, N, xb, F, Rd, sm);
-  else tri_solve<false>(cfl, N, xb, F, Rd, sm);
+  R* red = line_red<R, XS>(dsm, N);
+  if (MODE == PRED_FULL_FACTOR) tri_solve<true>(cfl, N, xb, F, Rd, red);
+  else tri_solve<false>(cfl, N, xb, F, Rd, red);
   // the wall unknowns enter the wall flux multiplied by 2/eps: re-solve their rows in
   // double from the neighbours (the rows are dominated by v gb ~ 1/eps, so the
   // neighbour's bulk-precision error is damped by |c/b|)
@@ -348,7 +363,7 @@ __global__ void __launch_bounds__(kTriThreads) k_pred_line(Dev D, const double* 
     D.Swall[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1);
   }
 #pragma unroll 4
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+  for (int64_t j = threadIdx.x; j < N; j += NT) {
     auto Oeo = [&](int64_t i) -> R { return onode(i) - R(dlx[i]) * vr * (xb[i] - xb[i - 1]); };
     R val;
     if (inflow && (j == 0 || j == N - 1)) {
@@ -409,11 +424,16 @@ __host__ __device__ inline int64_t prec_red_size(int64_t N) {
   int64_t half = N / 2;
   int nact = (int)(half < kCL ? half : kCL);
   int64_t base = N / nact;
-  return (int64_t)kCL * tri_red_size(base + 1);
+  return (int64_t)kCL * tri_red_size(base + 1, kTriThreads);
+}
+// Factor storage of the preconditioner slices: slice (instance ii, rank) starts at
+// 5 (cell_off + c0 + (ii kCL + rank) kTriThreads), room for tri_fac_size(n, kTriThreads).
+__host__ __device__ inline int64_t prec_fac_off(int64_t cell_off, int64_t c0, int ii, int rank) {
+  return 5 * (cell_off + c0 + ((int64_t)ii * kCL + rank) * kTriThreads);
 }
 
 struct GmresSmem {
-  TriSmem<double> tri;
+  double tri[4 * 2 * kTriThreads];   // reduced system of the slice solves
   double red[32];
   double part[2][kMaxRestart + 2];   // double-buffered partial sums exchanged by DSMEM
   double ends[6];                    // y_first, y_last, g_first, g_last, h_first, h_last
@@ -491,20 +511,21 @@ __device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int 
   double* ph = D.pH + co;
   PrecCoef pc{A, gl, gu, gb, ralpha, I.wv, I.wv2, N};
   SliceCoef sc{pc, c0, n};
-  double* F = D.pF + 4 * (co + c0);
+  double* F = D.pF + prec_fac_off(co, c0, blockIdx.x / kCL, rank);
   double* Rd = D.pRd + I.red_off + (int64_t)rank * (prec_red_size(N) / kCL);
+  const XAcc<double, false> wx{work + c0}, gx{pg + c0}, hx{ph + c0};
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) work[c0 + j] = ratio[c0 + j] * r[c0 + j];
   __syncthreads();
   if (n > 0) {
-    tri_solve<FACTOR>(sc, n, work + c0, F, Rd, sm.tri);
+    tri_solve<FACTOR>(sc, n, wx, F, Rd, sm.tri);
     if (FACTOR) {
       for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
         pg[c0 + j] = (j == 0) ? pc.a(c0) : 0.0;
         ph[c0 + j] = (j == n - 1) ? pc.c(c0 + n - 1) : 0.0;
       }
       __syncthreads();
-      tri_solve<false>(sc, n, pg + c0, F, Rd, sm.tri);
-      tri_solve<false>(sc, n, ph + c0, F, Rd, sm.tri);
+      tri_solve<false>(sc, n, gx, F, Rd, sm.tri);
+      tri_solve<false>(sc, n, hx, F, Rd, sm.tri);
     }
     if (threadIdx.x == 0) {
       sm.ends[0] = work[c0];
@@ -922,10 +943,12 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
 // and O_{J,N} = 2/eps (E_{N-1} - b_R) - O_{N-1}.  Then E^{n+1} = a c U + eps E_J,
 // O^{n+1} = O_J (in place: each CTA owns its line).
 // Per-angle parts in R; the U parts (Q1, gU, Q2) come in double from
-// k_cellpart_corr, and the two inflow wall cells are formed in double.
-template <typename R>
-__global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
-  __shared__ TriSmem<R> sm;
+// k_cellpart_corr, and the two inflow wall cells are formed in double.  NT and XS as
+// in k_pred_line.  With dry != 0 the state is left unchanged (the solve runs, the
+// projection is not stored): a side-effect-free pass for timing.
+template <typename R, int NT, bool XS>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_corr_line(Dev D, int dry) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   const Line L = D.lines[blockIdx.x];
   const Inst I = D.inst[L.inst];
   const int64_t N = I.N;
@@ -939,7 +962,7 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   R* O = (R*)D.O + oo;
   const double* T = D.T + co;   // T^{n+1}
   const double* Un = D.U + co;  // U^n
-  R* xb = (R*)D.xb + eo;
+  const XAcc<R, XS> xb = line_x<R, XS>(dsm, (R*)D.xb + eo);
   R* on = (R*)D.onode + oo;
   const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
                *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *Q1 = D.Q1 + co,
@@ -947,10 +970,10 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   const double two_eps = I.two_eps, inv_eps = I.inv_eps;
   const R vr = R(v);
   auto U1 = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
-  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x)
+  for (int64_t i = threadIdx.x; i <= N; i += NT)
     on[i] = (i >= 1 && i <= N - 1) ? R(od[i]) * O[i] : R(0);   // eps^2 d O^n/(c dt) part of o'
   __syncthreads();
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+  for (int64_t j = threadIdx.x; j < N; j += NT) {
     const bool wall = inflow && (j == 0 || j == N - 1);
     if (!wall) {
       xb[j] = R(Q1[j]) + R(kcd[j] * inv_eps) * Eh[j] - R(kdx[j] * v * inv_eps) * (on[j + 1] - on[j]) +
@@ -964,10 +987,11 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
   }
   __syncthreads();
   LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
-  tri_solve<true>(cfl, N, xb, (R*)D.F + 4 * I.elem_off + 4 * (int64_t)k * N, (R*)D.Rd + L.red_off, sm);
+  tri_solve<true>(cfl, N, xb, (R*)D.F + L.f_off, (R*)D.Rd + L.red_off, line_red<R, XS>(dsm, N));
+  if (dry) return;
   // projection: O^{n+1} = O_J, Eh^{n+1} = eps E_J (E^{n+1} = a c U^{n+1} + Eh^{n+1})
   const R epsr = R(eps);
-  for (int64_t i = threadIdx.x; i <= N; i += blockDim.x) {
+  for (int64_t i = threadIdx.x; i <= N; i += NT) {
     auto Oint = [&](int64_t n) -> R { return on[n] - vr * R(gU[n]) - R(dlx[n] * eps) * vr * (xb[n] - xb[n - 1]); };
     R Oi;
     if (i >= 1 && i <= N - 1) Oi = Oint(i);
@@ -976,7 +1000,7 @@ __global__ void __launch_bounds__(kTriThreads) k_corr_line(Dev D) {
     else Oi = R(two_eps * (ac * U1(N - 1) - bR) + 2.0 * (double)xb[N - 1] - (double)Oint(N - 1));
     O[i] = Oi;
   }
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) Eh[j] = epsr * xb[j];
+  for (int64_t j = threadIdx.x; j < N; j += NT) Eh[j] = epsr * xb[j];
 }
 
 // Energy sums of one instance per CTA (FP64, fixed reduction order):
@@ -1055,6 +1079,11 @@ struct grte_ctx {
   size_t ev_used = 0;
   int64_t launches = 0;
   grte_mlp_t mlp = nullptr;   // learned Newton guess (not owned)
+  // line solves: threads per CTA (0 until chosen), unknowns in shared memory or not
+  int nt = 0;
+  bool xs = false;
+  int64_t maxN = 0;
+  double tune_ms[3] = {-1.0, -1.0, -1.0};
 };
 
 static cudaEvent_t pool_event(grte_t h) {
@@ -1097,6 +1126,130 @@ static cudaError_t dalloc(grte_t h, T** p, int64_t n) {
     cudaMemset(q, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
   }
   *p = (T*)q;
+  return e;
+}
+
+// ----------------------------------------------------------------------------- line launches
+// Dynamic shared memory of a line CTA: the padded unknowns of the longest line (when
+// they stay in shared memory) and the reduced system.
+static int64_t line_smem(const grte_ctx* h, int nt, bool factor) {
+  const int es = h->opt.precision == GRTE_MIXED ? 4 : 8;
+  return (h->xs ? (tri_xs_len(h->maxN) * es + 15) / 16 * 16 : 0) + tri_smem_bytes(nt, factor, es);
+}
+
+static int g_smem_optin = 0;   // largest dynamic shared memory a line kernel may request
+
+static bool line_fits(const grte_ctx* h, int nt) {
+  const int es = h->opt.precision == GRTE_MIXED ? 4 : 8;
+  const int64_t need = (tri_xs_len(h->maxN) * es + 15) / 16 * 16 + tri_smem_bytes(nt, true, es);
+  return need <= g_smem_optin;
+}
+
+template <class K>
+static cudaError_t smem_attr(K k, int bytes) {
+  return cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename R, int NT, bool XS>
+static cudaError_t line_attrs_one(int bytes) {
+  cudaError_t e = smem_attr(k_pred_line<PRED_FULL_FACTOR, R, NT, XS>, bytes);
+  if (e == cudaSuccess) e = smem_attr(k_pred_line<PRED_FULL, R, NT, XS>, bytes);
+  if (e == cudaSuccess) e = smem_attr(k_pred_line<PRED_HOM, R, NT, XS>, bytes);
+  if (e == cudaSuccess) e = smem_attr(k_corr_line<R, NT, XS>, bytes);
+  return e;
+}
+
+// Allow every line kernel the device's opt-in shared memory (less a margin for the
+// kernels' static shared memory); once per device.
+static cudaError_t line_kernel_attrs() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const int bytes = optin - 256;
+  e = line_attrs_one<double, 256, false>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<double, 256, true>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<double, 512, true>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<double, 1024, true>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<float, 256, false>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<float, 256, true>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<float, 512, true>(bytes);
+  if (e == cudaSuccess) e = line_attrs_one<float, 1024, true>(bytes);
+  if (e != cudaSuccess) return e;
+  g_smem_optin = bytes;
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+template <int MODE, typename R, int NT, bool XS>
+static void pred_launch(grte_ctx* h, const double* x) {
+  k_pred_line<MODE, R, NT, XS><<<(unsigned)h->nlines, NT, (size_t)line_smem(h, NT, MODE == PRED_FULL_FACTOR),
+                                 h->stream>>>(h->D, x);
+}
+template <int MODE, typename R>
+static void pred_pass(grte_ctx* h, const double* x) {
+  if (!h->xs) return pred_launch<MODE, R, 256, false>(h, x);
+  switch (h->nt) {
+    case 1024: pred_launch<MODE, R, 1024, true>(h, x); break;
+    case 512: pred_launch<MODE, R, 512, true>(h, x); break;
+    default: pred_launch<MODE, R, 256, true>(h, x); break;
+  }
+}
+template <typename R, int NT, bool XS>
+static void corr_launch(grte_ctx* h, int dry) {
+  k_corr_line<R, NT, XS><<<(unsigned)h->nlines, NT, (size_t)line_smem(h, NT, true), h->stream>>>(h->D, dry);
+}
+template <typename R>
+static void corr_pass(grte_ctx* h, int dry) {
+  if (!h->xs) return corr_launch<R, 256, false>(h, dry);
+  switch (h->nt) {
+    case 1024: corr_launch<R, 1024, true>(h, dry); break;
+    case 512: corr_launch<R, 512, true>(h, dry); break;
+    default: corr_launch<R, 256, true>(h, dry); break;
+  }
+}
+
+// Autotuner of the line solves: times, for 256, 512 and 1024 threads per line (those
+// whose shared memory fits), one factor pass, four solve passes and one correction
+// pass (dry: the state is not touched) on this handle's own instances, twice, and
+// keeps the thread count with the smallest second time.  Needs the per-cell parts of
+// the current step (k_cell_coef, k_cellpart_pred) on the stream; synchronises.
+template <typename R>
+static cudaError_t autotune_lines(grte_ctx* h) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  int best = 256;
+  float best_ms = 3.0e38f;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    const int nt = 256 << i;
+    h->tune_ms[i] = -1.0;
+    if (!line_fits(h, nt)) continue;
+    h->nt = nt;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      pred_pass<PRED_FULL_FACTOR, R>(h, h->D.gx);
+      for (int q = 0; q < 4; ++q) pred_pass<PRED_FULL, R>(h, h->D.gx);
+      corr_pass<R>(h, 1);
+      cudaEventRecord(e1, h->stream);
+      e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e != cudaSuccess) break;
+    h->tune_ms[i] = ms;
+    if (ms < best_ms) { best_ms = ms; best = nt; }
+  }
+  h->nt = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return e;
 }
 
@@ -1146,6 +1299,7 @@ void grte_default_options(grte_options* o) {
   o->newton_maxit = 60;
   o->energy_every = 0;
   o->stream = nullptr;
+  o->line_threads = 0;
 }
 
 const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle"; }
@@ -1173,8 +1327,11 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   if (h->opt.krylov_restart < 1 || h->opt.krylov_restart > kMaxRestart) return bad("krylov_restart out of range [1,16]");
   if (h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1 || !(h->opt.krylov_rtol > 0)) return bad("bad solver options");
   h->n_inst = n_inst;
-  int64_t coff = 0, eoff = 0, noff = 0, roff = 0, poff = 0;
+  int64_t coff = 0, eoff = 0, noff = 0, roff = 0, poff = 0, foff = 0;
   int aoff = 0, loff = 0;
+  if (h->opt.line_threads != 0 && h->opt.line_threads != 256 && h->opt.line_threads != 512 &&
+      h->opt.line_threads != 1024)
+    return bad("line_threads must be 0, 256, 512 or 1024");
   for (int i = 0; i < n_inst; ++i) {
     const grte_instance1d& p = in[i];
     if (p.nx < 2 || p.nx > (1 << 24)) return bad("nx must be in [2, 2^24]");
@@ -1236,9 +1393,11 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     I.ang_off = aoff;
     I.line_off = loff;
     for (int k = 0; k < p.n_angle; ++k) {
-      h->lines.push_back(Line{i, k, roff});
-      roff += tri_red_size(p.nx);
+      h->lines.push_back(Line{i, k, roff, foff});
+      roff += tri_red_size(p.nx, kTriMaxNT);
+      foff += 5 * (p.nx + std::min<int64_t>(p.nx / 2, kTriMaxNT));   // >= tri_fac_size(nx, nt), nt <= 1024
     }
+    h->maxN = std::max<int64_t>(h->maxN, p.nx);
     poff += prec_red_size(p.nx);
     coff += p.nx;
     eoff += p.nx * p.n_angle;
@@ -1296,11 +1455,11 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     char* p_;
     if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc xb"); D.xb = p_;
     if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S"); D.S = p_;
-    if (dalloc(h, &p_, es * 4 * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc F"); D.F = p_;
+    if (dalloc(h, &p_, es * foff) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc F"); D.F = p_;
     if (dalloc(h, &p_, es * h->nred) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Rd"); D.Rd = p_;
     if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc onode"); D.onode = p_;
   }
-  AL(D.pF, 4 * nc); AL(D.pRd, h->npred); AL(D.pG, nc); AL(D.pH, nc); AL(D.gw, nc);
+  AL(D.pF, 5 * (nc + (int64_t)n_inst * kCL * kTriThreads)); AL(D.pRd, h->npred); AL(D.pG, nc); AL(D.pH, nc); AL(D.gw, nc);
   AL(D.pInv, (int64_t)n_inst * kCL * 2 * (2 * kCL));
   // x, z contiguous so that the GMRES kernel can recover the total cell count
   double* xz = nullptr;
@@ -1342,6 +1501,11 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   CK(cudaMemcpy(D.sig, hsig.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
   CK(cudaMallocHost(&h->h_flags, sizeof(int) * n_inst));
   h->inst_set.assign(n_inst, 0);
+  CK(line_kernel_attrs());
+  // line solves: unknowns in shared memory when the largest line fits at 256 threads
+  h->xs = line_fits(h, 256);
+  if (h->opt.line_threads != 0) h->nt = (h->xs && line_fits(h, h->opt.line_threads)) ? h->opt.line_threads : 256;
+  else if (!h->xs) h->nt = 256;   // nothing to tune: the global-memory variant runs at 256
   return GRTE_OK;
 }
 
@@ -1386,7 +1550,6 @@ static grte_status step_once(grte_t h) {
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const int ni = h->n_inst;
-  const int nl = (int)h->nlines;
   const int64_t nc = h->ncell;
   const int64_t vstride = D.gz - D.gx;   // cell stride of the Krylov basis (as in k_gmres)
   const int cb = 256;
@@ -1398,13 +1561,17 @@ static grte_status step_once(grte_t h) {
   CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
   CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
   LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
-  LAUNCH(GRTE_K_PRED_FACTOR, (k_pred_line<PRED_FULL_FACTOR, R><<<nl, kTriThreads, 0, st>>>(D, D.gx)));
+  if (h->nt == 0) {
+    cudaError_t e = autotune_lines<R>(h);
+    if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("line autotune: ") + cudaGetErrorString(e));
+  }
+  LAUNCH(GRTE_K_PRED_FACTOR, (pred_pass<PRED_FULL_FACTOR, R>(h, D.gx)));
   LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART_FIRST, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
       LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gV + (int64_t)j * vstride, 0));
-      LAUNCH(GRTE_K_PRED_HOM, (k_pred_line<PRED_HOM, R><<<nl, kTriThreads, 0, st>>>(D, D.gV + (int64_t)j * vstride)));
+      LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, D.gV + (int64_t)j * vstride)));
       LAUNCH(GRTE_K_GMRES, (k_gmres<G_ARNOLDI, R><<<ni * kCL, kTriThreads, 0, st>>>(D, j)));
       // a Krylov direction pass costs far more than a round trip: after the first
       // iteration, stop launching once no instance is still iterating
@@ -1418,7 +1585,7 @@ static grte_status step_once(grte_t h) {
     }
     LAUNCH(GRTE_K_GMRES, (k_gmres<G_UPDATE, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
     LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
-    LAUNCH(GRTE_K_PRED_FULL, (k_pred_line<PRED_FULL, R><<<nl, kTriThreads, 0, st>>>(D, D.gx)));
+    LAUNCH(GRTE_K_PRED_FULL, (pred_pass<PRED_FULL, R>(h, D.gx)));
     LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
@@ -1451,7 +1618,7 @@ static grte_status step_once(grte_t h) {
   // correction substep 2 + projection at T^{n+1}
   LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
   LAUNCH(GRTE_K_CELL_COEF, k_cellpart_corr<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
-  LAUNCH(GRTE_K_CORR, k_corr_line<R><<<nl, kTriThreads, 0, st>>>(D));
+  LAUNCH(GRTE_K_CORR, corr_pass<R>(h, 0));
   LAUNCH(GRTE_K_PROJECT, k_project_U<<<cgrid, cb, 0, st>>>(D, nc));
   if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<R><<<ni, kTriThreads, 0, st>>>(D, 1));
   CK(cudaGetLastError());
@@ -1631,9 +1798,19 @@ grte_status grte_stats(grte_t h, grte_stats_t* st) {
   }
   h->stats.newton_iters_max = (int64_t)mx;
   h->stats.newton_iters_mean = h->ncell ? sum / h->ncell : 0.0;
+  h->stats.line_threads = h->nt;
+  h->stats.line_smem = h->xs ? 1 : 0;
   grte_status s = device_status(h);
   *st = h->stats;
   return s;
+}
+
+grte_status grte_get_tuning(grte_t h, int* line_threads, double* ms, size_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (!line_threads || !ms || n < 3) return fail(h, GRTE_EINVAL, "need line_threads and ms[3]");
+  *line_threads = h->nt;
+  for (int i = 0; i < 3; ++i) ms[i] = h->tune_ms[i];
+  return GRTE_OK;
 }
 
 grte_status grte_profile_begin(grte_t h, uint32_t kernel_mask) {
@@ -1735,14 +1912,17 @@ constexpr int64_t kNaMaxNodeElems = kNaMaxElems + kNaMaxAngles;
 constexpr int64_t kNaCellArrays = 39;                       // per-cell double arrays (37 + the x/z pair)
 constexpr int64_t kNaAlign = 256;
 __host__ __device__ constexpr int64_t na_round(int64_t b) { return (b + kNaAlign - 1) / kNaAlign * kNaAlign; }
-constexpr int64_t kNaRedLine = 10 * 2 * kTriMaxRed + kTriMaxRed;   // >= tri_red_size(n) for any n
+// line solves run at kTriThreads threads here: per line at most 2 kTriThreads reduced
+// equations and 9 PCR levels
+constexpr int64_t kNaRedLine = 10 * 2 * (2 * kTriThreads) + 2 * kTriThreads;   // >= tri_red_size(n, kTriThreads)
+constexpr int64_t kNaFacLine = 5 * kTriThreads;   // tri_fac_size(n, kTriThreads) <= 5 n + kNaFacLine
 constexpr int64_t kNaBytes =
     kNaCellArrays * na_round(8 * kNaMaxCells) +                     // per-cell arrays
-    na_round(8 * 4 * kNaMaxCells) +                                 // preconditioner factors
+    na_round(8 * 5 * (kNaMaxCells + kCL * kTriThreads)) +           // preconditioner factors
     na_round(8 * kCL * kNaRedLine) +                                // preconditioner reduced systems
     na_round(8 * (kMaxRestart + 1) * kNaMaxCells) +                 // Krylov basis
     na_round(8 * kNaMaxElems) * 3 +                                 // Eh, xb, S
-    na_round(8 * 4 * kNaMaxElems) +                                 // line factors
+    na_round(8 * (5 * kNaMaxElems + kNaMaxAngles * kNaFacLine)) +   // line factors
     na_round(8 * kNaMaxNodeElems) +                                 // node scratch
     na_round(8 * kNaMaxAngles * kNaRedLine) +                        // line reduced systems
     na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) + // v, w, bL, bR; Swall
@@ -1854,7 +2034,7 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   I.wv = wv; I.wv2 = wv2; I.two_eps = 2.0 / p->eps; I.inv_eps = 1.0 / p->eps; I.bLflux = fl; I.bRflux = fr;
   I.cell_off = 0; I.elem_off = 0; I.nelem_off = 0; I.red_off = 0; I.ang_off = 0; I.line_off = 0;
   Line lines[kNaMaxAngles];
-  for (int k = 0; k < M; ++k) lines[k] = Line{0, k, (int64_t)k * kNaRedLine};
+  for (int k = 0; k < M; ++k) lines[k] = Line{0, k, (int64_t)k * kNaRedLine, (int64_t)k * (5 * N + kNaFacLine)};
 
   // device address of the static work memory: looked up once per device, with the
   // device current (the host-side symbol is not a device address)
@@ -1878,13 +2058,13 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   // the basis as gz - gx, here kNaMaxCells
   D.gx = (double*)take(8 * 2 * kNaMaxCells);
   D.gz = D.gx + kNaMaxCells;
-  D.pF = (double*)take(8 * 4 * kNaMaxCells);
+  D.pF = (double*)take(8 * 5 * (kNaMaxCells + kCL * kTriThreads));
   D.pRd = (double*)take(8 * kCL * kNaRedLine);
   D.gV = (double*)take(8 * (kMaxRestart + 1) * kNaMaxCells);
   D.Eh = take(8 * kNaMaxElems);
   D.xb = take(8 * kNaMaxElems);
   D.S = take(8 * kNaMaxElems);
-  D.F = take(8 * 4 * kNaMaxElems);
+  D.F = take(8 * (5 * kNaMaxElems + kNaMaxAngles * kNaFacLine));
   D.onode = take(8 * kNaMaxNodeElems);
   D.Rd = take(8 * kNaMaxAngles * kNaRedLine);
   double* vw = (double*)take(8 * 4 * kNaMaxAngles);
@@ -1951,6 +2131,11 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   int flag_buf[1] = {0};
   ctx.h_flags = flag_buf;
   ctx.state_set = true;
+  // line solves at kTriThreads threads, unknowns in shared memory when they fit
+  if (line_kernel_attrs() != cudaSuccess) { ctx.h_flags = nullptr; return GRTE_ECUDA; }
+  ctx.maxN = N;
+  ctx.xs = line_fits(&ctx, kTriThreads);
+  ctx.nt = kTriThreads;
   for (int64_t n = 0; n < nsteps; ++n) {
     grte_status s = step_once<double>(&ctx);
     if (s != GRTE_OK) { ctx.h_flags = nullptr; return s; }

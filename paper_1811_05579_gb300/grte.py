@@ -34,13 +34,14 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("energy_every", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("krylov_iters", ctypes.c_int64),
                 ("krylov_cycles", ctypes.c_int64), ("newton_iters_max", ctypes.c_int64),
-                ("newton_iters_mean", ctypes.c_double), ("status_flags", ctypes.c_int64)]
+                ("newton_iters_mean", ctypes.c_double), ("status_flags", ctypes.c_int64),
+                ("line_threads", ctypes.c_int64), ("line_smem", ctypes.c_int64)]
 
 
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
@@ -50,7 +51,7 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_step1d_noalloc", "grte_mlp_create", "grte_mlp_destroy", "grte_mlp_last_error",
             "grte_mlp_set_norm", "grte_mlp_get_params", "grte_mlp_set_params", "grte_mlp_forward",
             "grte_mlp_grad", "grte_mlp_train", "grte_set_guess", "grte_set_sample_logging",
-            "grte_get_newton_samples", "grte_set_newton_start"]
+            "grte_get_newton_samples", "grte_set_newton_start", "grte_get_tuning"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -224,7 +225,7 @@ class Grte:
     """Handle over n independent 1D instances (grte_create_1d)."""
 
     def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
-                 krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None):
+                 krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None, line_threads=0):
         L = lib()
         self._keep = []
         arr = (Instance1D * len(instances))()
@@ -251,6 +252,7 @@ class Grte:
         opt.newton_maxit = newton_maxit
         opt.energy_every = energy_every
         opt.stream = stream
+        opt.line_threads = line_threads
         h = ctypes.c_void_p()
         st = L.grte_create_1d(len(instances), arr, ctypes.byref(opt), ctypes.byref(h))
         self.h = h
@@ -360,6 +362,13 @@ class Grte:
         y = np.empty(nx, dtype=np.float32)
         self._check(lib().grte_get_newton_samples(self.h, inst, _fptr(X), _fptr(y), nx))
         return X, y
+
+    def tuning(self):
+        """(threads per line solve, {candidate threads: timed ms}) of the autotuner."""
+        nt = ctypes.c_int()
+        ms = np.full(3, -1.0)
+        self._check(lib().grte_get_tuning(self.h, ctypes.byref(nt), _ptr(ms), 3))
+        return int(nt.value), {256 << i: float(ms[i]) for i in range(3) if ms[i] >= 0}
 
     def stats(self, allow=()):
         s = Stats()
