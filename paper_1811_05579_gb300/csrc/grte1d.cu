@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/grte.h"
@@ -70,6 +71,16 @@ struct CellCoef {
   double *gbx;     // 2/eps in the inflow wall cells, else 0
 };
 
+// Binary32 copies of the per-cell values that the line and Krylov kernels use per
+// element in the mixed mode (each converted once per cell, so that no per-element
+// work touches the FP64 pipe).  Null in the FP64 mode.
+struct CellF {
+  float *A, *gl, *gu, *gb, *od, *dlx, *kcd, *kdx, *ratio, *ralpha, *alpha;
+  float *kcde, *kdxe, *dlxe;    // kcd/eps, kdx/eps, dlx*eps (correction substep 2)
+  float *P1, *P2, *P3, *Frho;   // per-cell parts of a prediction pass
+  float *Q1, *Q2, *gU;          // per-cell parts of correction substep 2
+};
+
 struct Dev {
   Inst* inst;
   Line* lines;
@@ -85,6 +96,7 @@ struct Dev {
   double *gwork;   // per-cell double work vector of the Krylov kernels
   double *Swall;   // per (instance, angle): the two inflow-wall flux contributions in double
   CellCoef cf;
+  CellF fc;
   // per-element work (bulk type)
   void *xb, *S, *F, *Rd, *onode;
   // preconditioner factors
@@ -105,6 +117,20 @@ struct Dev {
 };
 
 __device__ __forceinline__ void flag(int* status, int inst, int code) { atomicOr(status + inst, 1 << code); }
+
+// The per-cell array of the bulk type R: the double original or its binary32 copy.
+template <typename R>
+__device__ __forceinline__ const R* pick(const double* d, const float* f);
+template <>
+__device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
+template <>
+__device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
+
+// Arithmetic type of the Krylov vectors, preconditioner and Gram-Schmidt for a bulk
+// type: double in both modes.  (With binary32 Krylov vectors the mixed mode's second
+// restart accepted iterates whose wall-cell temperature was off by ~1e-5.)
+template <typename R>
+struct KryT { using type = double; };
 
 // ----------------------------------------------------------------------------- cells
 // Per-cell coefficients at temperature Tc (T^n for the prediction, T^{n+1} for
@@ -172,6 +198,23 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
   D.cf.fR[gid] = mR * dr / I.dx;
   D.cf.fL[gid] = mL * dl / I.dx;
   D.cf.gbx[gid] = (inflow && (j == 0 || j == N - 1)) ? I.two_eps : 0.0;
+  if (D.mixed) {
+    const CellF& f = D.fc;
+    f.A[gid] = (float)D.cf.A[gid];
+    f.gl[gid] = (float)D.cf.gl[gid];
+    f.gu[gid] = (float)D.cf.gu[gid];
+    f.gb[gid] = (float)D.cf.gb[gid];
+    f.od[gid] = (float)D.cf.od[gid];
+    f.dlx[gid] = (float)D.cf.dlx[gid];
+    f.kcd[gid] = (float)D.cf.kcd[gid];
+    f.kdx[gid] = (float)D.cf.kdx[gid];
+    f.ratio[gid] = (float)D.cf.ratio[gid];
+    f.ralpha[gid] = (float)D.cf.ralpha[gid];
+    f.alpha[gid] = (float)alpha;
+    f.kcde[gid] = (float)(D.cf.kcd[gid] * I.inv_eps);
+    f.kdxe[gid] = (float)(D.cf.kdx[gid] * I.inv_eps);
+    f.dlxe[gid] = (float)(D.cf.dlx[gid] * I.eps);
+  }
 }
 
 __device__ __forceinline__ int inst_of(const int64_t* __restrict__ cell_inst_start, int n_inst, int64_t gid) {
@@ -204,16 +247,19 @@ __global__ void k_rho(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_s
 //   Frho = sum_k w_k v_k (O_{j+1,k} - O_{j,k}) of the rho part of O:
 //          wv2 [fR (x_j - x_{j+1}) + fL (x_j - x_{j-1})] + wv gbx x_j
 //          (data pass: minus 2/eps sum_k w_k v_k b at the inflow walls).
+// X: type of the input vector (double for the iterate, the bulk type for a Krylov
+// direction).
+template <typename X>
 __global__ void k_cellpart_pred(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
-                                const double* __restrict__ xvec, int full) {
+                                const X* __restrict__ xvec, int full) {
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= ncell) return;
   const int ii = inst_of(cell_inst_start, n_inst, gid);
   const Inst I = D.inst[ii];
   if (!full && !D.gactive[ii]) return;
   const int64_t j = gid - I.cell_off, N = I.N;
-  const double* x = xvec + I.cell_off;
-  const double xj = x[j], xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
+  const X* x = xvec + I.cell_off;
+  const double xj = x[j], xl = j > 0 ? (double)x[j - 1] : 0.0, xr = j < N - 1 ? (double)x[j + 1] : 0.0;
   double p1 = -D.cf.alpha[gid] * xj;
   if (full) p1 += (D.cf.sac[gid] + D.cf.kcd[gid] * I.a * I.c) * D.U[gid];
   D.P1[gid] = p1;
@@ -225,6 +271,12 @@ __global__ void k_cellpart_pred(Dev D, int n_inst, const int64_t* __restrict__ c
     if (j == N - 1) fr -= I.two_eps * I.bRflux;
   }
   D.Frho[gid] = fr;
+  if (D.mixed) {
+    D.fc.P1[gid] = (float)p1;
+    D.fc.P2[gid] = (float)D.P2[gid];
+    D.fc.P3[gid] = (float)D.P3[gid];
+    D.fc.Frho[gid] = (float)fr;
+  }
 }
 
 // Per-cell parts of correction substep 2 at T^{n+1} (U^n still in D.U):
@@ -244,17 +296,22 @@ __global__ void k_cellpart_corr(Dev D, int n_inst, const int64_t* __restrict__ c
   const double gr = (j <= N - 2) ? D.cf.dlx[gid + 1] * ac * (U1(j + 1) - U1(j)) : 0.0;
   D.gU[gid] = gl;
   D.Q2[gid] = gr - gl;
+  if (D.mixed) {
+    D.fc.Q1[gid] = (float)D.Q1[gid];
+    D.fc.Q2[gid] = (float)(gr - gl);
+    D.fc.gU[gid] = (float)gl;
+  }
 }
 
 // ----------------------------------------------------------------------------- lines
 template <typename R>
 struct LineCoef {  // A + v^2 Gint + v Gbdry of one line, in the bulk type R
-  const double *A, *gl, *gu, *gb;
-  double v, v2;
+  const R *A, *gl, *gu, *gb;
+  R v, v2;
   int64_t N;
-  __device__ R a(int64_t j) const { return j > 0 ? R(-v2 * gl[j]) : R(0); }
-  __device__ R c(int64_t j) const { return j < N - 1 ? R(-v2 * gu[j]) : R(0); }
-  __device__ R b(int64_t j) const { return R(A[j] + v2 * (gl[j] + gu[j]) + v * gb[j]); }
+  __device__ R a(int64_t j) const { return j > 0 ? -v2 * gl[j] : R(0); }
+  __device__ R c(int64_t j) const { return j < N - 1 ? -v2 * gu[j] : R(0); }
+  __device__ R b(int64_t j) const { return A[j] + v2 * (gl[j] + gu[j]) + v * gb[j]; }
 };
 
 enum { PRED_FULL_FACTOR = 0, PRED_FULL = 1, PRED_HOM = 2 };
@@ -281,7 +338,8 @@ __device__ __forceinline__ R* line_red(unsigned char* dsm, int64_t N) {
 // line; with XS the line's unknowns stay in shared memory for the whole pass (only
 // the flux leaves the CTA), else they live in the global scratch xb.
 template <int MODE, typename R, int NT, bool XS>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double* __restrict__ xvec) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const void* __restrict__ xvec) {
+  using XT = typename std::conditional<MODE == PRED_HOM, typename KryT<R>::type, double>::type;   // Krylov direction or iterate
   extern __shared__ __align__(16) unsigned char dsm[];
   const Line L = D.lines[blockIdx.x];
   const Inst I = D.inst[L.inst];
@@ -293,11 +351,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double
   const double bL = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bL[I.ang_off + k];
   const double bR = (MODE == PRED_HOM || !inflow) ? 0.0 : D.bR[I.ang_off + k];
   const int64_t co = I.cell_off, eo = I.elem_off + (int64_t)k * N, oo = I.nelem_off + (int64_t)k * (N + 1);
-  const double* x = xvec + co;
+  const XT* x = (const XT*)xvec + co;
   const XAcc<R, XS> xb = line_x<R, XS>(dsm, (R*)D.xb + eo);
-  const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
-               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *P1 = D.P1 + co,
-               *P2 = D.P2 + co, *P3 = D.P3 + co;
+  // per-cell values in the bulk type for the per-element work
+  const R *P1r = pick<R>(D.P1, D.fc.P1) + co, *P2r = pick<R>(D.P2, D.fc.P2) + co,
+          *P3r = pick<R>(D.P3, D.fc.P3) + co, *kcdr = pick<R>(D.cf.kcd, D.fc.kcd) + co,
+          *kdxr = pick<R>(D.cf.kdx, D.fc.kdx) + co, *odr = pick<R>(D.cf.od, D.fc.od) + co,
+          *dlxr = pick<R>(D.cf.dlx, D.fc.dlx) + co;
+  // double originals for the two inflow wall cells
+  const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *dlx = D.cf.dlx + co,
+               *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *P1 = D.P1 + co, *P2 = D.P2 + co;
   const R* Ehn = (const R*)D.Eh + eo;
   const R* On = (const R*)D.O + oo;
   const double v2 = v * v;
@@ -306,13 +369,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double
   auto onode = [&](int64_t i) -> R {   // o_i in R
     if (MODE == PRED_HOM) return R(0);
     if (i <= 0 || i >= N) return R(0);
-    return R(od[i]) * On[i];
+    return odr[i] * On[i];
   };
   // right-hand side of an inflow wall row, in double:
   // -v gb x + kappa v (2/eps) b/dx = kappa v (2/eps)(b - x)/dx is an O(eps) difference
   auto wall_rhs = [&](int64_t j) -> double {
     const double b = (j == 0) ? bL : bR;
-    double r = P1[j] - v2 * P2[j] + kdx[j] * v * two_eps * (b - x[j]);
+    double r = P1[j] - v2 * P2[j] + kdx[j] * v * two_eps * (b - (double)x[j]);
     if (MODE != PRED_HOM) {
       const double o = (j == 0) ? 2.0 * (double)onode(1) : -2.0 * (double)onode(N - 1);
       r += kcd[j] * (double)Ehn[j] - kdx[j] * v * o;
@@ -323,15 +386,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double
   for (int64_t j = threadIdx.x; j < N; j += NT) {
     const bool wall = inflow && (j == 0 || j == N - 1);
     if (!wall) {
-      R r = R(P1[j]) - v2r * R(P2[j]) - vr * R(P3[j]);
-      if (MODE != PRED_HOM) r += R(kcd[j]) * Ehn[j] - R(kdx[j]) * vr * (onode(j + 1) - onode(j));
+      R r = P1r[j] - v2r * P2r[j] - vr * P3r[j];
+      if (MODE != PRED_HOM) r += kcdr[j] * Ehn[j] - kdxr[j] * vr * (onode(j + 1) - onode(j));
       xb[j] = r;
     } else {
       xb[j] = R(wall_rhs(j));
     }
   }
   __syncthreads();
-  LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v2, N};
+  LineCoef<R> cfl{pick<R>(D.cf.A, D.fc.A) + co, pick<R>(D.cf.gl, D.fc.gl) + co, pick<R>(D.cf.gu, D.fc.gu) + co,
+                  pick<R>(D.cf.gb, D.fc.gb) + co, vr, v2r, N};
   R* F = (R*)D.F + L.f_off;
   R* Rd = (R*)D.Rd + L.red_off;
   R* red = line_red<R, XS>(dsm, N);
@@ -364,7 +428,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double
   }
 #pragma unroll 4
   for (int64_t j = threadIdx.x; j < N; j += NT) {
-    auto Oeo = [&](int64_t i) -> R { return onode(i) - R(dlx[i]) * vr * (xb[i] - xb[i - 1]); };
+    auto Oeo = [&](int64_t i) -> R { return onode(i) - dlxr[i] * vr * (xb[i] - xb[i - 1]); };
     R val;
     if (inflow && (j == 0 || j == N - 1)) {
       val = R(0);                       // in Swall
@@ -385,22 +449,24 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const double
 // spike method (local solves plus a 2*kCL interface system).
 constexpr int kCL = 8;
 
-struct PrecCoef {  // A + (A/alpha) (wv2 Gint + wv Gbdry)
+template <typename K>
+struct PrecCoef {  // A + (A/alpha) (wv2 Gint + wv Gbdry), evaluated in double, stored in K
   const double *A, *gl, *gu, *gb, *ralpha;
   double wv, wv2;
   int64_t N;
   __device__ double f(int64_t j) const { return A[j] * ralpha[j]; }
-  __device__ double a(int64_t j) const { return j > 0 ? -f(j) * wv2 * gl[j] : 0.0; }
-  __device__ double c(int64_t j) const { return j < N - 1 ? -f(j) * wv2 * gu[j] : 0.0; }
-  __device__ double b(int64_t j) const { return A[j] + f(j) * (wv2 * (gl[j] + gu[j]) + wv * gb[j]); }
+  __device__ K a(int64_t j) const { return j > 0 ? K(-f(j) * wv2 * gl[j]) : K(0); }
+  __device__ K c(int64_t j) const { return j < N - 1 ? K(-f(j) * wv2 * gu[j]) : K(0); }
+  __device__ K b(int64_t j) const { return K(A[j] + f(j) * (wv2 * (gl[j] + gu[j]) + wv * gb[j])); }
 };
 
+template <typename K>
 struct SliceCoef {  // the rows [c0, c0+n) of a system, decoupled from the rest
-  PrecCoef p;
+  PrecCoef<K> p;
   int64_t c0, n;
-  __device__ double a(int64_t j) const { return j > 0 ? p.a(c0 + j) : 0.0; }
-  __device__ double c(int64_t j) const { return j < n - 1 ? p.c(c0 + j) : 0.0; }
-  __device__ double b(int64_t j) const { return p.b(c0 + j); }
+  __device__ K a(int64_t j) const { return j > 0 ? p.a(c0 + j) : K(0); }
+  __device__ K c(int64_t j) const { return j < n - 1 ? p.c(c0 + j) : K(0); }
+  __device__ K b(int64_t j) const { return p.b(c0 + j); }
 };
 
 struct Slice {
@@ -501,39 +567,46 @@ __device__ double cta_max(double v, double* red) {
 // (y), and in FACTOR mode also the two spike vectors g, h (its response to the
 // coupling with the neighbouring slices); the 2*nact end values then give the
 // slice-boundary unknowns, and u = y - u_left g - u_right h.
-template <bool FACTOR>
+// K: arithmetic type of the Krylov vectors (the bulk type); RT: type of r.
+template <bool FACTOR, bool XS, typename K, typename RT>
 __device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int rank, cg::cluster_group& cl,
-                              const double* r, double* z, double* work, GmresSmem& sm) {
+                              const RT* r, K* z, K* work, K* wsm, GmresSmem& sm) {
   const int64_t N = I.N, co = I.cell_off, c0 = sl.c0, n = sl.n;
   const double *A = D.cf.A + co, *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co,
-               *ratio = D.cf.ratio + co, *ralpha = D.cf.ralpha + co;
-  double* pg = D.pG + co;
-  double* ph = D.pH + co;
-  PrecCoef pc{A, gl, gu, gb, ralpha, I.wv, I.wv2, N};
-  SliceCoef sc{pc, c0, n};
-  double* F = D.pF + prec_fac_off(co, c0, blockIdx.x / kCL, rank);
-  double* Rd = D.pRd + I.red_off + (int64_t)rank * (prec_red_size(N) / kCL);
-  const XAcc<double, false> wx{work + c0}, gx{pg + c0}, hx{ph + c0};
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) work[c0 + j] = ratio[c0 + j] * r[c0 + j];
+               *ralpha = D.cf.ralpha + co;
+  const K *ratio_k = pick<K>(D.cf.ratio, D.fc.ratio) + co, *ralpha_k = pick<K>(D.cf.ralpha, D.fc.ralpha) + co,
+          *gl_k = pick<K>(D.cf.gl, D.fc.gl) + co, *gu_k = pick<K>(D.cf.gu, D.fc.gu) + co,
+          *gb_k = pick<K>(D.cf.gb, D.fc.gb) + co;
+  K* pg = (K*)D.pG + co;
+  K* ph = (K*)D.pH + co;
+  PrecCoef<K> pc{A, gl, gu, gb, ralpha, I.wv, I.wv2, N};
+  SliceCoef<K> sc{pc, c0, n};
+  K* F = (K*)D.pF + prec_fac_off(co, c0, blockIdx.x / kCL, rank);
+  K* Rd = (K*)D.pRd + I.red_off + (int64_t)rank * (prec_red_size(N) / kCL);
+  K* red = (K*)sm.tri;
+  // the slice's unknowns: shared memory (XS) or the global work vector
+  const XAcc<K, XS> wx{XS ? wsm : work + c0};
+  const XAcc<K, false> gx{pg + c0}, hx{ph + c0};
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) wx[j] = ratio_k[c0 + j] * K(r[c0 + j]);
   __syncthreads();
   if (n > 0) {
-    tri_solve<FACTOR>(sc, n, wx, F, Rd, sm.tri);
+    tri_solve<FACTOR>(sc, n, wx, F, Rd, red);
     if (FACTOR) {
       for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        pg[c0 + j] = (j == 0) ? pc.a(c0) : 0.0;
-        ph[c0 + j] = (j == n - 1) ? pc.c(c0 + n - 1) : 0.0;
+        pg[c0 + j] = (j == 0) ? pc.a(c0) : K(0);
+        ph[c0 + j] = (j == n - 1) ? pc.c(c0 + n - 1) : K(0);
       }
       __syncthreads();
-      tri_solve<false>(sc, n, gx, F, Rd, sm.tri);
-      tri_solve<false>(sc, n, hx, F, Rd, sm.tri);
+      tri_solve<false>(sc, n, gx, F, Rd, red);
+      tri_solve<false>(sc, n, hx, F, Rd, red);
     }
     if (threadIdx.x == 0) {
-      sm.ends[0] = work[c0];
-      sm.ends[1] = work[c0 + n - 1];
-      sm.ends[2] = pg[c0];
-      sm.ends[3] = pg[c0 + n - 1];
-      sm.ends[4] = ph[c0];
-      sm.ends[5] = ph[c0 + n - 1];
+      sm.ends[0] = (double)wx[0];
+      sm.ends[1] = (double)wx[n - 1];
+      sm.ends[2] = (double)pg[c0];
+      sm.ends[3] = (double)pg[c0 + n - 1];
+      sm.ends[4] = (double)ph[c0];
+      sm.ends[5] = (double)ph[c0 + n - 1];
     }
   }
   cl.sync();
@@ -606,45 +679,80 @@ __device__ void prec_apply_cl(const Dev& D, const Inst& I, const Slice& sl, int 
     sm.xlr[threadIdx.x] = acc;
   }
   __syncthreads();
-  const double ul = sm.xlr[0], ur = sm.xlr[1];
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-    work[c0 + j] = work[c0 + j] - ul * pg[c0 + j] - ur * ph[c0 + j];
+  const K ul = K(sm.xlr[0]), ur = K(sm.xlr[1]);
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) wx[j] = wx[j] - ul * pg[c0 + j] - ur * ph[c0 + j];
   __syncthreads();
+  const K wv2 = K(I.wv2), wv = K(I.wv);
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
     const int64_t g = c0 + j;
-    const double uj = work[g];
-    const double uL = g > 0 ? (j > 0 ? work[g - 1] : ul) : 0.0;
-    const double uR = g < N - 1 ? (j < n - 1 ? work[g + 1] : ur) : 0.0;
-    const double Gu = I.wv2 * (gl[g] * (uj - uL) + gu[g] * (uj - uR)) + I.wv * gb[g] * uj;
-    z[g] = (r[g] - Gu) * ralpha[g];
+    const K uj = wx[j];
+    const K uL = g > 0 ? (j > 0 ? wx[j - 1] : ul) : K(0);
+    const K uR = g < N - 1 ? (j < n - 1 ? wx[j + 1] : ur) : K(0);
+    const K Gu = wv2 * (gl_k[g] * (uj - uL) + gu_k[g] * (uj - uR)) + wv * gb_k[g] * uj;
+    z[g] = (K(r[g]) - Gu) * ralpha_k[g];
   }
   __syncthreads();
 }
 
 // F_j = sum_k w_k v_k (O_{j+1,k} - O_{j,k}) of a pass: the per-cell rho part plus the
-// per-angle e/o parts (summed in double, fixed angle order).
-template <typename R>
-__device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t j) {
+// per-angle e/o parts, 16 loads issued together, four partial sums (type A) combined
+// in a fixed order; the two inflow wall cells sum their double wall fluxes.
+template <typename R, typename A = R>
+__device__ __forceinline__ A eo_sum(const Dev& D, const Inst& I, int64_t j) {
   const R* S = (const R*)D.S + I.elem_off + j;
-  double acc = D.Frho[I.cell_off + j];
-  if (I.bc == GRTE_BC_INFLOW && (j == 0 || j == I.N - 1)) {
-    const int side = (j == 0) ? 0 : 1;
-    for (int k = 0; k < I.M; ++k) acc += D.Swall[2 * (I.ang_off + k) + side];
-  } else {
-    for (int k = 0; k < I.M; ++k) acc += (double)S[(int64_t)k * I.N];
+  const int64_t N = I.N;
+  A p[4] = {A(0), A(0), A(0), A(0)};
+  int k = 0;
+  for (; k + 16 <= I.M; k += 16) {
+    R t[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) t[q] = S[(int64_t)(k + q) * N];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) p[q & 3] += A(t[q]);
   }
+  for (; k < I.M; ++k) p[k & 3] += A(S[(int64_t)k * N]);
+  return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
+__device__ __forceinline__ bool wall_cell(const Inst& I, int64_t j) {
+  return I.bc == GRTE_BC_INFLOW && (j == 0 || j == I.N - 1);
+}
+
+__device__ __forceinline__ double wall_sum(const Dev& D, const Inst& I, int64_t j) {
+  const int side = (j == 0) ? 0 : 1;
+  double acc = 0.0;
+  for (int k = 0; k < I.M; ++k) acc += D.Swall[2 * (I.ang_off + k) + side];
   return acc;
 }
 
+// in double (true residual): each e/o part converted and summed in double
+template <typename R>
+__device__ __forceinline__ double flux_sum(const Dev& D, const Inst& I, int64_t j) {
+  const double fr = D.Frho[I.cell_off + j];
+  if (wall_cell(I, j)) return fr + wall_sum(D, I, j);
+  return fr + eo_sum<R, double>(D, I, j);
+}
+
+// in the bulk type (Krylov directions)
+template <typename R>
+__device__ __forceinline__ R flux_sum_k(const Dev& D, const Inst& I, int64_t j) {
+  if (wall_cell(I, j)) return R(D.Frho[I.cell_off + j] + wall_sum(D, I, j));
+  return pick<R>(D.Frho, D.fc.Frho)[I.cell_off + j] + eo_sum<R>(D, I, j);
+}
+
 enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
+
 
 // GMRES bookkeeping, one cluster per instance (restart length m, left
 // preconditioned).  Vectors live in global memory: x (iterate), V[0..m] (Krylov
 // basis), z (scratch).  Scalars (H, g, Givens) are computed identically by every
 // CTA; rank 0 stores them.
-template <int MODE, typename R>
+template <int MODE, typename R, bool XS>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
+  using K = typename KryT<R>::type;   // arithmetic of the Krylov vectors
   __shared__ GmresSmem sm;
+  extern __shared__ __align__(16) unsigned char gdsm[];   // the slice's unknowns (XS)
+  K* wsm = (K*)gdsm;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int ii = blockIdx.x / kCL;
@@ -653,11 +761,12 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
   const Slice sl = slice_of(N, rank);
   const int64_t c0 = sl.c0, n = sl.n;
   const int m = D.m;
-  double* x = D.gx + co;
-  double* z = D.gz + co;
-  double* work = D.gwork + co;
+  double* x = D.gx + co;           // iterate, double
+  double* zd = D.gz + co;          // scratch as double (residual) ...
+  K* zk = (K*)D.gz + co;           // ... or as K (a preconditioner input)
+  K* work = (K*)D.gwork + co;
   const int64_t ncell_tot = D.gz - D.gx;     // gz = gx + ncell_total (allocation layout)
-  auto Vi = [&](int i) { return D.gV + (int64_t)i * ncell_tot + co; };
+  auto Vi = [&](int i) { return (K*)D.gV + (int64_t)i * ncell_tot + co; };
   double* H = D.gH + (int64_t)ii * (kMaxRestart + 1) * kMaxRestart;
   double* g = D.gg + (int64_t)ii * (kMaxRestart + 1);
   double* cs = D.gcs + (int64_t)ii * kMaxRestart;
@@ -667,7 +776,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
   if (MODE == G_RESTART_FIRST || MODE == G_RESTART) {
     if (MODE == G_RESTART && D.gdone[ii]) return;        // uniform over the cluster
     // r = -R(x) from the FULL pass that just ran at x
-    double* r = z;
+    double* r = zd;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
       const double fl = flux_sum<R>(D, I, j);
       const double Rj = alpha[j] * x[j] - kcd[j] * D.rho_n[co + j] - sac[j] * D.U[co + j] + kdx[j] * fl;
@@ -686,15 +795,18 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
       D.gw[co + j] = 1.0 / (fabs(x[j]) + D.wfloor * xms[0] + 1e-300);
     __syncthreads();
-    double* v0 = Vi(0);
-    if (MODE == G_RESTART_FIRST) prec_apply_cl<true>(D, I, sl, rank, cl, r, v0, work, sm);
-    else prec_apply_cl<false>(D, I, sl, rank, cl, r, v0, work, sm);
+    K* v0 = Vi(0);
+    if (MODE == G_RESTART_FIRST) prec_apply_cl<true, XS, K, double>(D, I, sl, rank, cl, r, v0, work, wsm, sm);
+    else prec_apply_cl<false, XS, K, double>(D, I, sl, rank, cl, r, v0, work, wsm, sm);
     double loc[3] = {0.0, 0.0, 0.0};
+    K ss = K(0);
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
-      loc[0] += v0[j] * v0[j];
+      const K vj = v0[j];
+      ss += vj * vj;
       loc[1] += x[j] * x[j];
-      loc[2] = fmax(loc[2], fabs(v0[j]) * D.gw[co + j]);
+      loc[2] = fmax(loc[2], fabs((double)vj) * D.gw[co + j]);
     }
+    loc[0] = (double)ss;
     loc[0] = cta_sum(loc[0], sm.red);
     loc[1] = cta_sum(loc[1], sm.red);
     loc[2] = cta_max(loc[2], sm.red);
@@ -728,7 +840,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       if (!isfinite(nrm)) flag(D.status, ii, GRTE_ENAN);
     }
     if (!conv) {
-      const double inv = 1.0 / nrm;
+      const K inv = K(1.0 / nrm);
       for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) v0[j] *= inv;
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
@@ -738,28 +850,31 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
   if (MODE == G_ARNOLDI) {
     if (!D.gactive[ii]) return;                           // uniform over the cluster
     // C v_j = alpha v_j + kappa/dx * sum_k S_k  (the HOM pass just ran on v_j)
-    const double* vj = Vi(jcol);
-    double* cv = z;
+    const K* vj = Vi(jcol);
+    K* cv = zk;
+    const K *alpha_k = pick<K>(D.cf.alpha, D.fc.alpha) + co, *kdx_k = pick<K>(D.cf.kdx, D.fc.kdx) + co;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x)
-      cv[j] = alpha[j] * vj[j] + kdx[j] * flux_sum<R>(D, I, j);
+      cv[j] = alpha_k[j] * vj[j] + kdx_k[j] * K(flux_sum_k<R>(D, I, j));
     __syncthreads();
-    double* wv = Vi(jcol + 1);
-    prec_apply_cl<false>(D, I, sl, rank, cl, cv, wv, work, sm);
+    K* wv = Vi(jcol + 1);
+    prec_apply_cl<false, XS, K, K>(D, I, sl, rank, cl, cv, wv, work, wsm, sm);
     // classical Gram-Schmidt, twice (CGS2): two cluster reductions instead of j+1
     __shared__ double dots[kMaxRestart + 2];
-    double hc[kMaxRestart + 2];
-    for (int i = 0; i <= jcol + 1; ++i) hc[i] = 0.0;
+    __shared__ double hc[kMaxRestart + 2];   // Hessenberg column (thread 0 finishes it)
+    if (threadIdx.x <= jcol + 1) hc[threadIdx.x] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
       // all jcol+1 dot products in one sweep and one CTA reduction
+      // per-thread partial sums in K, reductions in double
+      K lk[kMaxRestart + 1];
       double loc[kMaxRestart + 1];
-      for (int i = 0; i <= jcol; ++i) loc[i] = 0.0;
+      for (int i = 0; i <= jcol; ++i) lk[i] = K(0);
       for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
-        const double wj = wv[j];
-        for (int i = 0; i <= jcol; ++i) loc[i] += wj * Vi(i)[j];
+        const K wj = wv[j];
+        for (int i = 0; i <= jcol; ++i) lk[i] += wj * Vi(i)[j];
       }
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int i = 0; i <= jcol; ++i) {
-        double v = loc[i];
+        double v = (double)lk[i];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) sm.redm[wid][i] = v;
       }
@@ -772,16 +887,16 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       __syncthreads();
       cluster_sums(cl, sm, pass, loc, jcol + 1, dots);
       for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
-        double t = wv[j];
-        for (int i = 0; i <= jcol; ++i) t -= dots[i] * Vi(i)[j];
+        K t = wv[j];
+        for (int i = 0; i <= jcol; ++i) t -= K(dots[i]) * Vi(i)[j];
         wv[j] = t;
       }
-      for (int i = 0; i <= jcol; ++i) hc[i] += dots[i];
+      if (threadIdx.x <= jcol) hc[threadIdx.x] += dots[threadIdx.x];
       __syncthreads();
     }
-    double loc1 = 0.0;
-    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) loc1 += wv[j] * wv[j];
-    loc1 = cta_sum(loc1, sm.red);
+    K l1 = K(0);
+    for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) l1 += wv[j] * wv[j];
+    double loc1 = cta_sum((double)l1, sm.red);
     __shared__ double nn[1];
     cluster_sums(cl, sm, 0, &loc1, 1, nn);
     const double nrm = sqrt(nn[0]);
@@ -812,7 +927,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
         if (est || nrm == 0.0 || jcol + 1 >= m) D.gactive[ii] = 0;
       }
     }
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    const K inv = K(nrm > 0.0 ? 1.0 / nrm : 0.0);
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) wv[j] *= inv;
     cl.sync();
     return;
@@ -831,7 +946,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     __syncthreads();
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
       double t = x[j];
-      for (int i = 0; i < kk; ++i) t += sm.y[i] * Vi(i)[j];
+      for (int i = 0; i < kk; ++i) t += sm.y[i] * (double)Vi(i)[j];
       x[j] = t;
     }
     return;
@@ -964,20 +1079,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_corr_line(Dev D, int dry) {
   const double* Un = D.U + co;  // U^n
   const XAcc<R, XS> xb = line_x<R, XS>(dsm, (R*)D.xb + eo);
   R* on = (R*)D.onode + oo;
-  const double *gl = D.cf.gl + co, *gu = D.cf.gu + co, *gb = D.cf.gb + co, *od = D.cf.od + co,
-               *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *Q1 = D.Q1 + co,
+  const double *dlx = D.cf.dlx + co, *kcd = D.cf.kcd + co, *kdx = D.cf.kdx + co, *Q1 = D.Q1 + co,
                *Q2 = D.Q2 + co, *gU = D.gU + co;
   const double two_eps = I.two_eps, inv_eps = I.inv_eps;
-  const R vr = R(v);
+  const R vr = R(v), v2r = R(v * v);
+  constexpr bool F32 = sizeof(R) == 4;
+  const R* odr = pick<R>(D.cf.od, D.fc.od) + co;
   auto U1 = [&](int64_t j) { const double t = T[j]; const double t2 = t * t; return t2 * t2; };
   for (int64_t i = threadIdx.x; i <= N; i += NT)
-    on[i] = (i >= 1 && i <= N - 1) ? R(od[i]) * O[i] : R(0);   // eps^2 d O^n/(c dt) part of o'
+    on[i] = (i >= 1 && i <= N - 1) ? odr[i] * O[i] : R(0);   // eps^2 d O^n/(c dt) part of o'
   __syncthreads();
   for (int64_t j = threadIdx.x; j < N; j += NT) {
     const bool wall = inflow && (j == 0 || j == N - 1);
     if (!wall) {
-      xb[j] = R(Q1[j]) + R(kcd[j] * inv_eps) * Eh[j] - R(kdx[j] * v * inv_eps) * (on[j + 1] - on[j]) +
-              R(kdx[j] * v * v * inv_eps) * R(Q2[j]);
+      if constexpr (F32) {
+        const int64_t g = co + j;
+        const R ke = (R)D.fc.kdxe[g];
+        xb[j] = D.fc.Q1[g] + D.fc.kcde[g] * Eh[j] - ke * vr * (on[j + 1] - on[j]) + ke * v2r * D.fc.Q2[g];
+      } else {
+        xb[j] = R(Q1[j]) + R(kcd[j] * inv_eps) * Eh[j] - R(kdx[j] * v * inv_eps) * (on[j + 1] - on[j]) +
+                R(kdx[j] * v * v * inv_eps) * R(Q2[j]);
+      }
     } else {
       double Dj;
       if (j == 0) Dj = 2.0 * ((double)on[1] - v * gU[1]) - two_eps * (bL - ac * U1(0));
@@ -986,13 +1108,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_corr_line(Dev D, int dry) {
     }
   }
   __syncthreads();
-  LineCoef<R> cfl{D.cf.A + co, gl, gu, gb, v, v * v, N};
+  LineCoef<R> cfl{pick<R>(D.cf.A, D.fc.A) + co, pick<R>(D.cf.gl, D.fc.gl) + co, pick<R>(D.cf.gu, D.fc.gu) + co,
+                  pick<R>(D.cf.gb, D.fc.gb) + co, vr, v2r, N};
   tri_solve<true>(cfl, N, xb, (R*)D.F + L.f_off, (R*)D.Rd + L.red_off, line_red<R, XS>(dsm, N));
   if (dry) return;
   // projection: O^{n+1} = O_J, Eh^{n+1} = eps E_J (E^{n+1} = a c U^{n+1} + Eh^{n+1})
   const R epsr = R(eps);
   for (int64_t i = threadIdx.x; i <= N; i += NT) {
-    auto Oint = [&](int64_t n) -> R { return on[n] - vr * R(gU[n]) - R(dlx[n] * eps) * vr * (xb[n] - xb[n - 1]); };
+    auto Oint = [&](int64_t n) -> R {
+      if constexpr (F32) return on[n] - vr * D.fc.gU[co + n] - D.fc.dlxe[co + n] * vr * (xb[n] - xb[n - 1]);
+      else return on[n] - vr * R(gU[n]) - R(dlx[n] * eps) * vr * (xb[n] - xb[n - 1]);
+    };
     R Oi;
     if (i >= 1 && i <= N - 1) Oi = Oint(i);
     else if (!inflow) Oi = R(0);
@@ -1083,6 +1209,9 @@ struct grte_ctx {
   int nt = 0;
   bool xs = false;
   int64_t maxN = 0;
+  // Krylov kernels: largest preconditioner slice, slice unknowns in shared memory or not
+  int64_t max_slice = 0;
+  bool gxs = false;
   double tune_ms[3] = {-1.0, -1.0, -1.0};
 };
 
@@ -1138,6 +1267,7 @@ static int64_t line_smem(const grte_ctx* h, int nt, bool factor) {
 }
 
 static int g_smem_optin = 0;   // largest dynamic shared memory a line kernel may request
+static int g_gmres_dyn = 0;    // largest dynamic shared memory a Krylov kernel may request
 
 static bool line_fits(const grte_ctx* h, int nt) {
   const int es = h->opt.precision == GRTE_MIXED ? 4 : 8;
@@ -1181,17 +1311,43 @@ static cudaError_t line_kernel_attrs() {
   if (e == cudaSuccess) e = line_attrs_one<float, 1024, true>(bytes);
   if (e != cudaSuccess) return e;
   g_smem_optin = bytes;
+  // Krylov kernels: the opt-in size less their static shared memory
+  int gdyn = bytes;
+  auto gm = [&](const void* f) {
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+    if (e == cudaSuccess) gdyn = std::min(gdyn, bytes - (int)fa.sharedSizeBytes);
+  };
+  const void* gk[] = {(const void*)k_gmres<G_RESTART_FIRST, double, true>, (const void*)k_gmres<G_RESTART, double, true>,
+                      (const void*)k_gmres<G_ARNOLDI, double, true>, (const void*)k_gmres<G_UPDATE, double, true>,
+                      (const void*)k_gmres<G_RESTART_FIRST, float, true>, (const void*)k_gmres<G_RESTART, float, true>,
+                      (const void*)k_gmres<G_ARNOLDI, float, true>, (const void*)k_gmres<G_UPDATE, float, true>};
+  for (const void* f : gk) gm(f);
+  for (const void* f : gk)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, gdyn);
+  if (e != cudaSuccess) return e;
+  g_gmres_dyn = gdyn;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return cudaSuccess;
 }
 
+static int64_t gmres_dyn_smem(const grte_ctx* h) {
+  return h->gxs ? (tri_xs_len(h->max_slice) * 8 + 15) / 16 * 16 : 0;
+}
+template <int MODE, typename R>
+static void gmres_launch(grte_ctx* h, int jcol) {
+  const unsigned grid = (unsigned)(h->n_inst * kCL);
+  if (h->gxs) k_gmres<MODE, R, true><<<grid, kTriThreads, (size_t)gmres_dyn_smem(h), h->stream>>>(h->D, jcol);
+  else k_gmres<MODE, R, false><<<grid, kTriThreads, 0, h->stream>>>(h->D, jcol);
+}
+
 template <int MODE, typename R, int NT, bool XS>
-static void pred_launch(grte_ctx* h, const double* x) {
+static void pred_launch(grte_ctx* h, const void* x) {
   k_pred_line<MODE, R, NT, XS><<<(unsigned)h->nlines, NT, (size_t)line_smem(h, NT, MODE == PRED_FULL_FACTOR),
                                  h->stream>>>(h->D, x);
 }
 template <int MODE, typename R>
-static void pred_pass(grte_ctx* h, const double* x) {
+static void pred_pass(grte_ctx* h, const void* x) {
   if (!h->xs) return pred_launch<MODE, R, 256, false>(h, x);
   switch (h->nt) {
     case 1024: pred_launch<MODE, R, 1024, true>(h, x); break;
@@ -1398,6 +1554,10 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
       foff += 5 * (p.nx + std::min<int64_t>(p.nx / 2, kTriMaxNT));   // >= tri_fac_size(nx, nt), nt <= 1024
     }
     h->maxN = std::max<int64_t>(h->maxN, p.nx);
+    {
+      const int64_t nact = std::min<int64_t>(p.nx / 2, kCL);
+      h->max_slice = std::max<int64_t>(h->max_slice, p.nx / nact + 1);
+    }
     poff += prec_red_size(p.nx);
     coff += p.nx;
     eoff += p.nx * p.n_angle;
@@ -1424,9 +1584,10 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   Dev& D = h->D;
   const int m = h->opt.krylov_restart;
   D.m = m;
-  // binary32 line solves leave noise in the residual of cells far below the maximum:
-  // the mixed mode floors the tolerance at 1e-9, measures cells below 1e-6 of the
-  // maximum against that floor, and accepts a second restart below 1e-4
+  // binary32 line solves and Krylov vectors leave noise in the residual of cells far
+  // below the maximum: the mixed mode floors the tolerance at 1e-9, measures cells
+  // below 1e-6 of the maximum against that floor, and accepts a second restart below
+  // 1e-4 (FP64: a restart that stalls below 1e-9)
   const bool mixed = h->opt.precision == GRTE_MIXED;
   D.rtol = mixed ? std::max(h->opt.krylov_rtol, 1e-9) : h->opt.krylov_rtol;
   D.stall = mixed ? 1e-4 : 1e-9;
@@ -1451,6 +1612,13 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.cf.gl, nc); AL(D.cf.gu, nc); AL(D.cf.gb, nc); AL(D.cf.dl, nc);
   AL(D.cf.od, nc); AL(D.cf.dlx, nc); AL(D.cf.kcd, nc); AL(D.cf.kdx, nc); AL(D.cf.sac, nc);
   AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc); AL(D.cf.fR, nc); AL(D.cf.fL, nc); AL(D.cf.gbx, nc);
+  if (mixed) {
+    CellF& f = D.fc;
+    AL(f.A, nc); AL(f.gl, nc); AL(f.gu, nc); AL(f.gb, nc); AL(f.od, nc); AL(f.dlx, nc); AL(f.kcd, nc);
+    AL(f.kdx, nc); AL(f.ratio, nc); AL(f.ralpha, nc); AL(f.alpha, nc); AL(f.kcde, nc); AL(f.kdxe, nc);
+    AL(f.dlxe, nc); AL(f.P1, nc); AL(f.P2, nc); AL(f.P3, nc); AL(f.Frho, nc); AL(f.Q1, nc); AL(f.Q2, nc);
+    AL(f.gU, nc);
+  }
   {
     char* p_;
     if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc xb"); D.xb = p_;
@@ -1504,6 +1672,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   CK(line_kernel_attrs());
   // line solves: unknowns in shared memory when the largest line fits at 256 threads
   h->xs = line_fits(h, 256);
+  h->gxs = (tri_xs_len(h->max_slice) * 8 + 15) / 16 * 16 <= g_gmres_dyn;
   if (h->opt.line_threads != 0) h->nt = (h->xs && line_fits(h, h->opt.line_threads)) ? h->opt.line_threads : 256;
   else if (!h->xs) h->nt = 256;   // nothing to tune: the global-memory variant runs at 256
   return GRTE_OK;
@@ -1560,19 +1729,21 @@ static grte_status step_once(grte_t h) {
   CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
   CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
-  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
   if (h->nt == 0) {
     cudaError_t e = autotune_lines<R>(h);
     if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("line autotune: ") + cudaGetErrorString(e));
   }
   LAUNCH(GRTE_K_PRED_FACTOR, (pred_pass<PRED_FULL_FACTOR, R>(h, D.gx)));
-  LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART_FIRST, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
+  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART_FIRST, R>(h, 0)));
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
-      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gV + (int64_t)j * vstride, 0));
-      LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, D.gV + (int64_t)j * vstride)));
-      LAUNCH(GRTE_K_GMRES, (k_gmres<G_ARNOLDI, R><<<ni * kCL, kTriThreads, 0, st>>>(D, j)));
+      using K = typename KryT<R>::type;
+      const K* vj = (const K*)D.gV + (int64_t)j * vstride;   // Krylov direction
+      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<K><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, vj, 0));
+      LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, vj)));
+      LAUNCH(GRTE_K_GMRES, (gmres_launch<G_ARNOLDI, R>(h, j)));
       // a Krylov direction pass costs far more than a round trip: after the first
       // iteration, stop launching once no instance is still iterating
       if (j >= 1 && j + 1 < D.m) {
@@ -1583,10 +1754,10 @@ static grte_status step_once(grte_t h) {
         if (!any) break;
       }
     }
-    LAUNCH(GRTE_K_GMRES, (k_gmres<G_UPDATE, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
-    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
+    LAUNCH(GRTE_K_GMRES, (gmres_launch<G_UPDATE, R>(h, 0)));
+    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
     LAUNCH(GRTE_K_PRED_FULL, (pred_pass<PRED_FULL, R>(h, D.gx)));
-    LAUNCH(GRTE_K_GMRES, (k_gmres<G_RESTART, R><<<ni * kCL, kTriThreads, 0, st>>>(D, 0)));
+    LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART, R>(h, 0)));
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -2135,6 +2306,8 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   if (line_kernel_attrs() != cudaSuccess) { ctx.h_flags = nullptr; return GRTE_ECUDA; }
   ctx.maxN = N;
   ctx.xs = line_fits(&ctx, kTriThreads);
+  ctx.max_slice = N / std::min<int64_t>(N / 2, kCL) + 1;
+  ctx.gxs = (tri_xs_len(ctx.max_slice) * 8 + 15) / 16 * 16 <= g_gmres_dyn;
   ctx.nt = kTriThreads;
   for (int64_t n = 0; n < nsteps; ++n) {
     grte_status s = step_once<double>(&ctx);
