@@ -86,6 +86,10 @@ typedef struct {
   int line_threads;      /* threads per line solve: 0 (default) = autotune at the first step
                             (times the line kernels at 256, 512 and 1024 threads on this
                             handle's instances and keeps the fastest), or 256, 512, 1024    */
+  int use_graph;         /* 1 (default): from the second step on, each step is one CUDA graph
+                            launch (captured once; the Krylov loop runs under device-side
+                            conditional nodes, no host round trip inside a step).  Steps
+                            taken while per-kernel profiling is on run eagerly.  0: eager    */
 } grte_options;
 
 /* Statistics of the last grte_step call (summed over its steps and instances). */

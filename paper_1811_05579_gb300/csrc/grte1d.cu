@@ -1212,8 +1212,23 @@ struct grte_ctx {
   // Krylov kernels: largest preconditioner slice, slice unknowns in shared memory or not
   int64_t max_slice = 0;
   bool gxs = false;
+  // captured step (after the first step): graph, executable, device counters
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int* d_cycles = nullptr;          // restart cycles of the current step
+  long long* d_acc = nullptr;       // Krylov iterations, cycles, iterations run, condition kernels run
+  int64_t graph_fixed_launches = 0;
   double tune_ms[3] = {-1.0, -1.0, -1.0};
 };
+
+// The captured step depends on values passed by value to its kernels (the device
+// description, the Newton start, the learned guess): setters that change them drop it.
+static void drop_step_graph(grte_t h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+}
 
 static cudaEvent_t pool_event(grte_t h) {
   if (h->ev_used == h->ev_pool.size()) {
@@ -1456,6 +1471,7 @@ void grte_default_options(grte_options* o) {
   o->energy_every = 0;
   o->stream = nullptr;
   o->line_threads = 0;
+  o->use_graph = 1;
 }
 
 const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle"; }
@@ -1463,6 +1479,7 @@ const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle
 void grte_destroy(grte_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_step_graph(h);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1645,6 +1662,8 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.gestconv, n_inst);
   AL(D.status, n_inst);
   AL(D.energy, 3 * (int64_t)n_inst);
+  AL(h->d_cycles, 1);
+  AL(h->d_acc, 4);
 #undef AL
   D.inst = h->d_inst;
   D.lines = h->d_lines;
@@ -1714,36 +1733,109 @@ grte_status grte_set_state(grte_t h, int inst, const double* T, const double* E,
 
 }  // extern "C"
 
+// ----------------------------------------------------------------------------- one step
+// The step is built from four pieces shared by the eager path (host loop over the
+// Krylov iterations) and the CUDA graph (device-side conditionals):
+//   prologue  coefficients at T^n, rho^n, x = rho^n, factor pass, first restart
+//   iteration cellpart(V_j), direction pass, Arnoldi step j
+//   tail      update x, cellpart(x), data pass, restart (residual, stopping test)
+//   epilogue  Newton (Eq. Tnp1), coefficients at T^{n+1}, substep 2 and projection
+struct StepGeom {
+  int ni;
+  int64_t nc, vstride;
+  unsigned cgrid;
+  static constexpr int cb = 256;
+};
+static StepGeom step_geom(grte_t h) {
+  StepGeom g;
+  g.ni = h->n_inst;
+  g.nc = h->ncell;
+  g.vstride = h->D.gz - h->D.gx;   // cell stride of the Krylov basis (as in k_gmres)
+  g.cgrid = (unsigned)((g.nc + StepGeom::cb - 1) / StepGeom::cb);
+  return g;
+}
+
 template <typename R>
-static grte_status step_once(grte_t h) {
+static grte_status step_prologue(grte_t h, bool allow_tune) {
   Dev& D = h->D;
   cudaStream_t st = h->stream;
-  const int ni = h->n_inst;
-  const int64_t nc = h->ncell;
-  const int64_t vstride = D.gz - D.gx;   // cell stride of the Krylov basis (as in k_gmres)
-  const int cb = 256;
-  const unsigned cgrid = (unsigned)((nc + cb - 1) / cb);
-  // prediction coefficients at T^n, rho^n, initial iterate x = rho^n
-  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 0));
-  LAUNCH(GRTE_K_RHO, k_rho<R><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.rho_n));
-  CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * ni, st));
-  CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * ni, st));
-  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
+  const StepGeom G = step_geom(h);
+  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, 0));
+  LAUNCH(GRTE_K_RHO, k_rho<R><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.rho_n));
+  CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * G.nc, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(D.gits, 0, sizeof(int) * G.ni, st));
+  CK(cudaMemsetAsync(D.gcycles, 0, sizeof(int) * G.ni, st));
+  if (h->d_cycles) CK(cudaMemsetAsync(h->d_cycles, 0, sizeof(int), st));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.gx, 1));
   if (h->nt == 0) {
+    if (!allow_tune) return fail(h, GRTE_ESTATE, "line solves not tuned");
     cudaError_t e = autotune_lines<R>(h);
     if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("line autotune: ") + cudaGetErrorString(e));
   }
   LAUNCH(GRTE_K_PRED_FACTOR, (pred_pass<PRED_FULL_FACTOR, R>(h, D.gx)));
   LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART_FIRST, R>(h, 0)));
+  return GRTE_OK;
+}
+
+template <typename R>
+static void step_iteration(grte_t h, int j) {
+  using K = typename KryT<R>::type;
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const StepGeom G = step_geom(h);
+  const K* vj = (const K*)D.gV + (int64_t)j * G.vstride;   // Krylov direction
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<K><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, vj, 0));
+  LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, vj)));
+  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_ARNOLDI, R>(h, j)));
+}
+
+template <typename R>
+static void step_tail(grte_t h) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const StepGeom G = step_geom(h);
+  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_UPDATE, R>(h, 0)));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.gx, 1));
+  LAUNCH(GRTE_K_PRED_FULL, (pred_pass<PRED_FULL, R>(h, D.gx)));
+  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART, R>(h, 0)));
+}
+
+template <typename R>
+static grte_status step_epilogue(grte_t h) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const StepGeom G = step_geom(h);
+  // correction substep 1 (per-cell Newton); T now holds T^{n+1}
+  if (D.use_guess || D.log_samples)
+    LAUNCH(GRTE_K_NEWTON, k_newton_feat<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc));
+  if (D.use_guess) {
+    cudaError_t e = mlp_guess_launch(h->mlp, D.feat, G.nc, D.guess, st);
+    if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("mlp guess: ") + cudaGetErrorString(e));
+    ++h->launches;
+  }
+  LAUNCH(GRTE_K_NEWTON, k_newton<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc));
+  // correction substep 2 + projection at T^{n+1}
+  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, 1));
+  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_corr<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc));
+  LAUNCH(GRTE_K_CORR, corr_pass<R>(h, 0));
+  LAUNCH(GRTE_K_PROJECT, k_project_U<<<G.cgrid, G.cb, 0, st>>>(D, G.nc));
+  if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<R><<<G.ni, kTriThreads, 0, st>>>(D, 1));
+  CK(cudaGetLastError());
+  return GRTE_OK;
+}
+
+// Eager step: the host reads the solver flags between launches.
+template <typename R>
+static grte_status step_once(grte_t h) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const int ni = h->n_inst;
+  grte_status s0 = step_prologue<R>(h, true);
+  if (s0 != GRTE_OK) return s0;
   int cycles = 0;
   for (;;) {
     for (int j = 0; j < D.m; ++j) {
-      using K = typename KryT<R>::type;
-      const K* vj = (const K*)D.gV + (int64_t)j * vstride;   // Krylov direction
-      LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<K><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, vj, 0));
-      LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, vj)));
-      LAUNCH(GRTE_K_GMRES, (gmres_launch<G_ARNOLDI, R>(h, j)));
+      step_iteration<R>(h, j);
       // a Krylov direction pass costs far more than a round trip: after the first
       // iteration, stop launching once no instance is still iterating
       if (j >= 1 && j + 1 < D.m) {
@@ -1754,10 +1846,7 @@ static grte_status step_once(grte_t h) {
         if (!any) break;
       }
     }
-    LAUNCH(GRTE_K_GMRES, (gmres_launch<G_UPDATE, R>(h, 0)));
-    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, D.gx, 1));
-    LAUNCH(GRTE_K_PRED_FULL, (pred_pass<PRED_FULL, R>(h, D.gx)));
-    LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART, R>(h, 0)));
+    step_tail<R>(h);
     ++cycles;
     CK(cudaMemcpyAsync(h->h_flags, D.gdone, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1777,22 +1866,190 @@ static grte_status step_once(grte_t h) {
     }
   }
   h->stats.krylov_cycles += cycles;
-  // correction substep 1 (per-cell Newton); T now holds T^{n+1}
-  if (D.use_guess || D.log_samples)
-    LAUNCH(GRTE_K_NEWTON, k_newton_feat<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
-  if (D.use_guess) {
-    cudaError_t e = mlp_guess_launch(h->mlp, D.feat, nc, D.guess, st);
-    if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("mlp guess: ") + cudaGetErrorString(e));
-    ++h->launches;
+  return step_epilogue<R>(h);
+}
+
+// ----------------------------------------------------------------------------- graph
+// Device-side control of the captured step.  k_cond_active sets an IF node's
+// condition to "some instance is still iterating"; k_cond_cycle counts restart
+// cycles and sets the WHILE node's condition to "some instance is not done and the
+// cycle limit is not reached" (flagging the instances left undone at the limit);
+// k_step_stats accumulates the step's Krylov iterations and cycles.
+__global__ void k_cond_active(cudaGraphConditionalHandle hnd, const int* __restrict__ gactive, int n, long long* acc) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (gactive[i]) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    acc[3] += 1;            // condition kernels run
+    if (any) acc[2] += 1;   // Krylov iterations run
+    cudaGraphSetConditional(hnd, any ? 1u : 0u);
   }
-  LAUNCH(GRTE_K_NEWTON, k_newton<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
-  // correction substep 2 + projection at T^{n+1}
-  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc, 1));
-  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_corr<<<cgrid, cb, 0, st>>>(D, ni, h->d_cell_start, nc));
-  LAUNCH(GRTE_K_CORR, corr_pass<R>(h, 0));
-  LAUNCH(GRTE_K_PROJECT, k_project_U<<<cgrid, cb, 0, st>>>(D, nc));
-  if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<R><<<ni, kTriThreads, 0, st>>>(D, 1));
+}
+
+__global__ void k_cond_cycle(cudaGraphConditionalHandle hnd, const int* __restrict__ gdone, int* status, int n,
+                             int* cycles, int maxcycles, int count) {
+  __shared__ int undone;
+  if (threadIdx.x == 0) undone = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!gdone[i]) undone = 1;
+  __syncthreads();
+  const int c = *cycles + count;   // every thread reads before thread 0 writes
+  __syncthreads();
+  bool go = undone != 0;
+  if (go && c >= maxcycles) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (!gdone[i]) atomicOr(status + i, 1 << GRTE_ENONCONV);
+    go = false;
+  }
+  if (threadIdx.x == 0) {
+    *cycles = c;
+    cudaGraphSetConditional(hnd, go ? 1u : 0u);
+  }
+}
+
+__global__ void k_step_stats(const int* __restrict__ gits, int n, const int* __restrict__ cycles,
+                             long long* acc) {
+  long long t = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += gits[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __shared__ long long red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    acc[0] += s;
+    acc[1] += *cycles;
+  }
+}
+
+// Add a conditional node at the current end of the capture on stream st and return
+// its body graph; further captures on st depend on the node.
+static cudaError_t capture_conditional(cudaStream_t st, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
+                                       cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorIllegalState;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, ed, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static cudaError_t capture_graph_of(cudaStream_t st, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs;
+  return cudaStreamGetCaptureInfo(st, &cs, nullptr, g, nullptr, nullptr, nullptr);
+}
+
+// Capture the Krylov iterations j..m-1 as nested IF nodes on stream st:
+//   cond_active(h_j); IF(h_j) { iteration j; cond_active(h_j+1); IF(h_j+1) { ... } }
+template <typename R>
+static grte_status capture_iterations(grte_t h, cudaStream_t st, int j, std::vector<cudaStream_t>& aux) {
+  Dev& D = h->D;
+  cudaGraph_t g = nullptr;
+  CK(capture_graph_of(st, &g));
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, g, 0, 0));
+  k_cond_active<<<1, 256, 0, st>>>(hc, D.gactive, h->n_inst, h->d_acc);
   CK(cudaGetLastError());
+  cudaGraph_t body = nullptr;
+  CK(capture_conditional(st, hc, cudaGraphCondTypeIf, &body));
+  cudaStream_t sb = aux[j];
+  CK(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaStream_t keep = h->stream;
+  h->stream = sb;
+  step_iteration<R>(h, j);
+  grte_status s = GRTE_OK;
+  if (j + 1 < D.m) s = capture_iterations<R>(h, sb, j + 1, aux);
+  h->stream = keep;
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(sb, &out);
+  if (s != GRTE_OK) return s;
+  CK(e);
+  return GRTE_OK;
+}
+
+// Build the executable graph of one step (after the line solves are tuned).
+template <typename R>
+static grte_status build_step_graph(grte_t h) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  std::vector<cudaStream_t> aux(D.m + 1, nullptr);
+  for (auto& a : aux) CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+  auto drop = [&]() { for (auto& a : aux) if (a) cudaStreamDestroy(a); };
+  const bool prof = h->prof_mask != 0;
+  if (prof) { drop(); return fail(h, GRTE_ESTATE, "graph capture while profiling"); }
+  grte_status s = GRTE_OK;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) { drop(); return fail(h, GRTE_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e)); }
+  const int64_t l0 = h->launches;
+  int64_t fixed = 0;
+  do {
+    s = step_prologue<R>(h, false);
+    if (s != GRTE_OK) break;
+    fixed += h->launches - l0;
+    cudaGraph_t g = nullptr;
+    if ((e = capture_graph_of(st, &g)) != cudaSuccess) break;
+    cudaGraphConditionalHandle hw;
+    if ((e = cudaGraphConditionalHandleCreate(&hw, g, 0, 0)) != cudaSuccess) break;
+    k_cond_cycle<<<1, 256, 0, st>>>(hw, D.gdone, D.status, h->n_inst, h->d_cycles, h->opt.krylov_maxcycles, 0);
+    cudaGraph_t wbody = nullptr;
+    if ((e = capture_conditional(st, hw, cudaGraphCondTypeWhile, &wbody)) != cudaSuccess) break;
+    cudaStream_t sw = aux[D.m];
+    if ((e = cudaStreamBeginCaptureToGraph(sw, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) break;
+    h->stream = sw;
+    s = capture_iterations<R>(h, sw, 0, aux);
+    if (s == GRTE_OK) {
+      step_tail<R>(h);
+      k_cond_cycle<<<1, 256, 0, sw>>>(hw, D.gdone, D.status, h->n_inst, h->d_cycles, h->opt.krylov_maxcycles, 1);
+    }
+    h->stream = st;
+    cudaGraph_t wout = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(sw, &wout);
+    if (s != GRTE_OK) break;
+    if ((e = e2) != cudaSuccess) break;
+    const int64_t l1 = h->launches;
+    s = step_epilogue<R>(h);
+    if (s != GRTE_OK) break;
+    fixed += h->launches - l1 + 2;   // + the first cycle condition and the statistics
+    k_step_stats<<<1, 256, 0, st>>>(D.gits, h->n_inst, h->d_cycles, h->d_acc);
+  } while (0);
+  h->launches = l0;
+  h->graph_fixed_launches = fixed;
+  h->stream = st;
+  cudaError_t e3 = cudaStreamEndCapture(st, &graph);
+  drop();
+  if (s != GRTE_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+  if (e == cudaSuccess) e = e3;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(h, GRTE_ECUDA, std::string("step graph capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(h, GRTE_ECUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e));
+  }
+  h->graph = graph;
+  h->graph_exec = ex;
   return GRTE_OK;
 }
 
@@ -1805,17 +2062,43 @@ grte_status grte_step(grte_t h, int64_t nsteps) {
   h->stats.krylov_cycles = 0;
   h->stats.krylov_iters = 0;
   h->launches = 0;
-  int64_t its = 0;
+  const bool mixed = h->opt.precision == GRTE_MIXED;
+  int64_t its = 0, cyc = 0, ngraph = 0;
   std::vector<int> hits(h->n_inst);
+  CK(cudaMemsetAsync(h->d_acc, 0, 4 * sizeof(long long), h->stream));
   for (int64_t n = 0; n < nsteps; ++n) {
-    grte_status s = h->opt.precision == GRTE_MIXED ? step_once<float>(h) : step_once<double>(h);
-    if (s != GRTE_OK) return s;
-    CK(cudaMemcpyAsync(hits.data(), h->D.gits, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    for (int v : hits) its += v;
+    // graph path: after the first (tuning) step, when not profiling
+    const bool use_graph = h->opt.use_graph && h->nt != 0 && h->prof_mask == 0;
+    if (use_graph) {
+      if (!h->graph_exec) {
+        grte_status s = mixed ? build_step_graph<float>(h) : build_step_graph<double>(h);
+        if (s != GRTE_OK) return s;
+      }
+      CK(cudaGraphLaunch(h->graph_exec, h->stream));
+      ++ngraph;
+    } else {
+      const int64_t c0 = h->stats.krylov_cycles;
+      grte_status s = mixed ? step_once<float>(h) : step_once<double>(h);
+      if (s != GRTE_OK) return s;
+      cyc += h->stats.krylov_cycles - c0;
+      CK(cudaMemcpyAsync(hits.data(), h->D.gits, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int v : hits) its += v;
+    }
     h->stats.steps += 1;
   }
+  if (ngraph > 0) {
+    long long acc[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    its += acc[0];
+    cyc += acc[1];
+    // kernels run by the graph steps: the fixed ones, per cycle the tail (4) and its
+    // condition kernel, every condition kernel of the iterations, 3 per iteration run
+    h->launches += ngraph * h->graph_fixed_launches + acc[1] * 5 + acc[3] + acc[2] * 3;
+  }
   h->stats.krylov_iters = its;
+  h->stats.krylov_cycles = cyc;
   return GRTE_OK;
 }
 
@@ -2024,6 +2307,7 @@ static grte_status ensure_feat(grte_t h) {
 
 grte_status grte_set_guess(grte_t h, grte_mlp_t m) {
   if (!h) return GRTE_EINVAL;
+  drop_step_graph(h);
   CK(cudaStreamSynchronize(h->stream));
   if (m) {
     grte_status s = ensure_feat(h);
@@ -2037,6 +2321,7 @@ grte_status grte_set_guess(grte_t h, grte_mlp_t m) {
 
 grte_status grte_set_newton_start(grte_t h, int mode) {
   if (!h) return GRTE_EINVAL;
+  drop_step_graph(h);
   if (mode != GRTE_START_BOUND && mode != GRTE_START_PREVIOUS && mode != GRTE_START_LEARNED)
     return fail(h, GRTE_EINVAL, "bad start mode");
   if (mode == GRTE_START_LEARNED && !h->mlp) return fail(h, GRTE_ESTATE, "no network set (grte_set_guess)");
@@ -2048,6 +2333,7 @@ grte_status grte_set_newton_start(grte_t h, int mode) {
 
 grte_status grte_set_sample_logging(grte_t h, int on) {
   if (!h) return GRTE_EINVAL;
+  drop_step_graph(h);
   CK(cudaStreamSynchronize(h->stream));
   if (on) {
     grte_status s = ensure_feat(h);

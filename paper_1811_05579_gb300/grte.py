@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("energy_every", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -225,7 +225,8 @@ class Grte:
     """Handle over n independent 1D instances (grte_create_1d)."""
 
     def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
-                 krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None, line_threads=0):
+                 krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None, line_threads=0,
+                 use_graph=True):
         L = lib()
         self._keep = []
         arr = (Instance1D * len(instances))()
@@ -253,6 +254,7 @@ class Grte:
         opt.energy_every = energy_every
         opt.stream = stream
         opt.line_threads = line_threads
+        opt.use_graph = 1 if use_graph else 0
         h = ctypes.c_void_p()
         st = L.grte_create_1d(len(instances), arr, ctypes.byref(opt), ctypes.byref(h))
         self.h = h
