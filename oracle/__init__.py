@@ -9,9 +9,12 @@ Each module follows the paper (Tang, Wang, Zhang, "Accurate front capturing
 asymptotic preserving scheme for nonlinear gray radiative transfer equation",
 arXiv:1811.05579) and cites the section / equation it writes out:
 
-  quadrature  - angular quadrature sets (velocity discretisation of Sec. 4)
+  quadrature  - angular quadrature sets (velocity discretisation of Sec. 4):
+                Gauss-Legendre in 1D, level-symmetric S8 pairs in 2D
   scalar      - the per-cell quartic of the correction step (Eq. Tnp1)
   grte1d      - Algorithm 2 (Sec. 4) and its sigma/T^3 form (Sec. 5) in 1D
+  grte2d      - the same scheme on a 2D grid (direction by direction, Sec. 4; the
+                reading of the 2D discretisation is in that module's header)
   diffusion1d - the three-stage diffusion solver (Sec. 2, Eq. dis-diff) and the
                 fully implicit limit solvers (Sec. 6, Eq. imp_T and diff_solver)
   freestream  - the exact characteristic solution of the sigma = 0 limit
