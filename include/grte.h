@@ -50,7 +50,8 @@ typedef enum {
 enum { GRTE_SIGMA_CONST = 0, /* sigma(x), independent of T (Sec. 4)            */
        GRTE_SIGMA_T3 = 1     /* sigma_0(x) / T^3 (Sec. 5, Eq. marshak00)        */ };
 enum { GRTE_BC_INFLOW = 0,   /* I(0,v) = b_L(v), I(L,-v) = b_R(-v), v > 0 (Eq. BC1d, Eq. bc-pre) */
-       GRTE_BC_REFLECT = 1   /* I(wall, v) = I(wall, -v): odd part zero at the walls             */ };
+       GRTE_BC_REFLECT = 1,  /* I(wall, v) = I(wall, -v): odd part zero at the walls (1D)        */
+       GRTE_BC_PERIODIC = 2  /* 2D only: the axis wraps around                                   */ };
 enum { GRTE_FP64 = 0,        /* every per-element operation in binary64                         */
        GRTE_MIXED = 1        /* angular bulk in binary32; per-cell Newton and sums in binary64   */ };
 
@@ -232,6 +233,66 @@ grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size
  * the same statuses as grte_step + grte_sync (synchronises `stream`). */
 grte_status grte_step1d_noalloc(const grte_instance1d* inst, const grte_options* opt, double* T, double* E,
                                 double* O, int64_t nsteps, void* stream);
+
+/* ----------------------------------------------------------------------------------
+ * 2D instances.  The paper derives the scheme in 1D and extends it direction by
+ * direction (Sec. 4); the 2D form used here: E (and U, T) at the centres of an
+ * nx x ny cell grid, O at its (nx+1) x (ny+1) vertices, for K pairs of directions
+ * (Omega_k, -Omega_k) with Omega_k = (mu_k, eta_k).  The streaming derivative of E
+ * at a vertex is the mean of the two cell differences across it, that of O at a
+ * cell the mean of the two vertex differences along each side; node, cell and U
+ * equations, Newton and correction are those of the 1D scheme (Eq. dis-pre,
+ * Eq. dis-pre-marshak, Eq. Tnp1, Eq. dis-cor, Eq. dis-proj).  Inflow walls use
+ * Eq. bc-pre along the wall normal with E the mean of the two wall cells beside the
+ * vertex; a corner of two inflow walls takes the mean of the two walls' values.
+ *
+ * Linear solves: the prediction by GMRES on (e, rho) (E = rho + e, as in 1D) with the
+ * matrix applied by stencil kernels and an exact per-cell angular block solve as
+ * preconditioner; correction substep 2 by GMRES on the K stacked pair systems
+ * (Jacobi preconditioned).  Both run on unknowns scaled per cell by the cell's own
+ * magnitude, so that the stopping test holds in every cell.  All arithmetic binary64.
+ * -------------------------------------------------------------------------------- */
+typedef struct grte2d_ctx* grte2d_t;
+
+typedef struct {
+  int64_t nx, ny;        /* cells per axis, >= 2 each                                        */
+  int n_pair;            /* K; 0: the built-in level-symmetric S8 set (20 pairs)             */
+  const double* mu;      /* host, K x-cosines (n_pair > 0), nonzero where x is an inflow axis */
+  const double* eta;     /* host, K y-cosines, nonzero where y is an inflow axis              */
+  const double* w;       /* host, K pair weights > 0 (renormalised to sum 1)                  */
+  const double* sigma;   /* host, nx*ny values, row-major [j*nx + i] (j: y index), >= 0       */
+  int sigma_kind;        /* GRTE_SIGMA_CONST or GRTE_SIGMA_T3                                 */
+  int bc_x, bc_y;        /* GRTE_BC_INFLOW or GRTE_BC_PERIODIC per axis                       */
+  double b_x0, b_x1;     /* isotropic inflow intensity on x = 0 and x = lx (INFLOW; 0: vacuum) */
+  double b_y0, b_y1;     /* the same on y = 0 and y = ly                                      */
+  double lx, ly;         /* domain [0, lx] x [0, ly]                                          */
+  double dt, a, c, Cv, eps;
+} grte_instance2d;
+
+/* Create a 2D handle (inputs copied; opt may be NULL: precision must be GRTE_FP64,
+ * krylov_rtol (root mean square over cells of the preconditioned residual relative to
+ * each cell's own magnitude, default 1e-13), krylov_restart (up to 64; 30 if the 1D
+ * default 10 is given),
+ * krylov_maxcycles and newton_maxit apply).  The state is unset until
+ * grte2d_set_state.  Errors: EINVAL, ENOMEM, ECUDA. */
+grte_status grte2d_create(const grte_instance2d* inst, const grte_options* opt, grte2d_t* out);
+/* T: nx*ny; E: nx*ny*K as [cell][k] and O: (nx+1)*(ny+1)*K as [vertex][k] (vertex
+ * index j*(nx+1) + i), or E = O = NULL for the equilibrium I = a c T^4. */
+grte_status grte2d_set_state(grte2d_t h, const double* T, const double* E, const double* O);
+/* Advance n steps (synchronous).  Statuses as grte_step + grte_sync. */
+grte_status grte2d_step(grte2d_t h, int64_t n);
+grte_status grte2d_get_T(grte2d_t h, double* T, size_t len);           /* len = nx*ny          */
+grte_status grte2d_get_E(grte2d_t h, double* E, size_t len);           /* len = nx*ny*K        */
+grte_status grte2d_get_O(grte2d_t h, double* O, size_t len);           /* len = (nx+1)(ny+1)K  */
+/* which: 0 U*, 1 sum_k w_k (D*_k O*_k) (the flux term of Eq. Tnp1), 2 rho*, 3 Newton
+ * iterations; len = nx*ny. */
+grte_status grte2d_get_stage(grte2d_t h, int which, double* out, size_t len);
+grte_status grte2d_get_quadrature(grte2d_t h, double* mu, double* eta, double* w, size_t K);
+/* Total energy sum over cells dx dy (rho/c + Cv T) of the current state. */
+grte_status grte2d_get_energy(grte2d_t h, double* e);
+grte_status grte2d_stats(grte2d_t h, grte_stats_t* st);
+const char* grte2d_last_error(grte2d_t h);
+void grte2d_destroy(grte2d_t h);
 
 #ifdef __cplusplus
 }

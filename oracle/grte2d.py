@@ -32,14 +32,18 @@ Eq. dis-cor-marshak and Eq. dis-proj are taken over unchanged.  Vertex opacity i
 harmonic mean of the four cells, vertex kappa (sigma/T^3) their mean.
 
 Boundaries, per axis: 'periodic' (vertex Nx is vertex 0, cell -1 is cell Nx-1), or
-'inflow' with an isotropic inflow intensity per side (b = 0: vacuum).  An inflow wall
-vertex uses Eq. bc-pre along the wall normal with E taken as the mean of the two
-wall cells beside the vertex: if Omega_k enters the domain there,
-  O = 2/eps (b - E_wall) - O_inner,
-otherwise (-Omega_k enters)
-  O = 2/eps (E_wall - b) - O_inner,
-with O_inner the next vertex inward along the normal.  A corner vertex of two inflow
-walls takes the mean of the two walls' expressions (E_wall = the corner cell).
+'inflow' with an isotropic inflow intensity per side (b = 0: vacuum).  A cell beside
+an inflow wall applies Eq. bc-pre to its own wall side, exactly as the 1D wall cell:
+the mean of O over that side obeys
+  side = 2/eps (b - E_cell) - opposite side      (Omega_k enters the domain there)
+  side = 2/eps (E_cell - b) - opposite side      (-Omega_k enters)
+(div_operator).  An inflow wall vertex itself (needed for the opposite side of a
+corner cell and for the output) uses the same relation along the wall normal with E
+the mean of the two wall cells beside it and the next vertex inward; a corner vertex
+takes the mean of its two walls' values (E_wall = the corner cell).  Applying the
+wall relation per cell rather than per vertex keeps a cell's outflow from depending
+on its neighbours' E along the wall (with the vertex form, a cold wall cell beside a
+hot one was drained by its neighbour's outflow).
 
 Linear solves (sparse LU throughout): the prediction on the unknowns (e, rho) with
 E = rho + e exactly as grte1d.coefficients() (O eliminated by the vertex map
@@ -202,7 +206,7 @@ def grad_matrix(P, k):
 
 
 def div_matrix(P, k):
-    """D*_k: vertices -> cells."""
+    """D*_k: vertices -> cells, without wall rows (the plain 2x2 side averages)."""
     rows, cols, vals = [], [], []
     mu, eta = P.mu[k], P.eta[k]
     for q in range(P.Ny):
@@ -216,6 +220,55 @@ def div_matrix(P, k):
                 cols.append(vidx)
                 vals.append(val)
     return sp.csr_matrix((vals, (rows, cols)), shape=(P.nc, P.nv))
+
+
+def div_operator(P, k):
+    """The streaming derivative of O at the cells as used by the scheme:
+    (D*_k O)_c + ed_c E_c + bt_c.  A cell beside an inflow wall takes its wall side
+    from Eq. bc-pre with its own E, as the 1D wall cell does: for the x = 0 side
+    (mean of its two wall vertices, L) with R the opposite side's mean,
+      L = s 2/eps (b - E_c) - R,  so  mu (R - L)/dx = mu (2 R - s 2/eps (b - E_c))/dx,
+    and likewise on the other walls.  Returns (D (nc x nv), ed (nc,), bt (nc,))."""
+    rows, cols, vals = [], [], []
+    ed = np.zeros(P.nc)
+    bt = np.zeros(P.nc)
+    mu, eta = P.mu[k], P.eta[k]
+    for q in range(P.Ny):
+        for p in range(P.Nx):
+            c = q * P.Nx + p
+            v00, v10, v01, v11 = P.vert(p, q), P.vert(p + 1, q), P.vert(p, q + 1), P.vert(p + 1, q + 1)
+            # side weights (L, R along x; B, T along y) of mu/dx and eta/dy
+            wL, wR, wB, wT = -1.0, 1.0, -1.0, 1.0
+            for axis, comp, h_, side_lo, side_hi in (("x", mu, P.dx, p == 0, p == P.Nx - 1),
+                                                       ("y", eta, P.dy, q == 0, q == P.Ny - 1)):
+                inflow = (P.bcx if axis == "x" else P.bcy) == "inflow"
+                if not inflow:
+                    continue
+                if side_lo:      # low side replaced: comp (2 hi - s 2/eps (b - E))/h
+                    s_, b = _wall(P, k, axis, 0)
+                    if axis == "x":
+                        wL, wR = 0.0, 2.0
+                    else:
+                        wB, wT = 0.0, 2.0
+                    ed[c] += comp * s_ * 2.0 / P.eps / h_
+                    bt[c] -= comp * s_ * 2.0 / P.eps * b / h_
+                if side_hi:      # high side replaced: comp (s 2/eps (b - E) - 2 lo)/h
+                    s_, b = _wall(P, k, axis, 1)
+                    if axis == "x":
+                        wL, wR = (wL if side_lo else -2.0), 0.0
+                    else:
+                        wB, wT = (wB if side_lo else -2.0), 0.0
+                    ed[c] -= comp * s_ * 2.0 / P.eps / h_
+                    bt[c] += comp * s_ * 2.0 / P.eps * b / h_
+            for vidx, val in ((v00, wL * mu / (2 * P.dx)), (v01, wL * mu / (2 * P.dx)),
+                              (v10, wR * mu / (2 * P.dx)), (v11, wR * mu / (2 * P.dx)),
+                              (v00, wB * eta / (2 * P.dy)), (v10, wB * eta / (2 * P.dy)),
+                              (v01, wT * eta / (2 * P.dy)), (v11, wT * eta / (2 * P.dy))):
+                if val != 0.0:
+                    rows.append(c)
+                    cols.append(vidx)
+                    vals.append(val)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(P.nc, P.nv)), ed, bt
 
 
 def _wall(P, k, axis, side):
@@ -284,8 +337,9 @@ def vertex_map(P, k, E_coef, o):
 
 def coefficients(P, T, Oold):
     """Per-cell coefficients at temperature T and, per pair, the eliminated streaming
-    operator G_k = diag(kappa) D*_k Q_k, its data part phi_k = kappa D*_k q_k and the
-    vertex map (Q_k, q_k) (names as grte1d.coefficients)."""
+    operator G_k = diag(kappa) (D*_k Q_k + diag(ed_k)), its data part
+    phi_k = kappa (D*_k q_k + bt_k) (div_operator) and the vertex map (Q_k, q_k)
+    (names as grte1d.coefficients)."""
     eps, c, a, dt, Cv = P.eps, P.c, P.a, P.dt, P.Cv
     kc, theta = _kappa_theta(P, T)
     sc = P.sig.ravel()
@@ -297,12 +351,12 @@ def coefficients(P, T, Oold):
     ops = []
     for k in range(P.K):
         Dk = grad_matrix(P, k)
-        Dsk = div_matrix(P, k)
+        Dsk, ed, bt = div_operator(P, k)
         o = d * eps ** 2 / (c * dt) * Oold[:, k]
         Qk, qk = vertex_map(P, k, sp.diags(d) @ Dk, o)
-        Gk = sp.diags(kc) @ (Dsk @ Qk)
-        phik = kc * (Dsk @ qk)
-        ops.append(dict(G=Gk.tocsr(), phi=phik, Q=Qk, q=qk, Ds=Dsk))
+        Gk = sp.diags(kc) @ (Dsk @ Qk + sp.diags(ed))
+        phik = kc * (Dsk @ qk + bt)
+        ops.append(dict(G=Gk.tocsr(), phi=phik, Q=Qk, q=qk, Ds=Dsk, ed=ed, bt=bt))
     return dict(kc=kc, theta=theta, s=s, gam=gam, d=d, A=kc / (c * dt) + sc / eps ** 2,
                 alpha=kc / (c * dt) + s, ops=ops)
 
@@ -366,11 +420,12 @@ def predict_literal(P, S):
     iO = lambda v, k: nE + k * nv + v
     iU = lambda cc: nE + nO + cc
     for k in range(K):
-        Ds = div_matrix(P, k).tocoo()
+        Dsm, ed, bt = div_operator(P, k)
+        Ds = Dsm.tocoo()
         for cc in range(nc):
-            add(iE(cc, k), iE(cc, k), kc[cc] / (c * dt) + sc[cc] / eps ** 2)
+            add(iE(cc, k), iE(cc, k), kc[cc] / (c * dt) + sc[cc] / eps ** 2 + kc[cc] * ed[cc])
             add(iE(cc, k), iU(cc), -sc[cc] * a * c / eps ** 2)
-            b[iE(cc, k)] = kc[cc] * S.E[cc, k] / (c * dt)
+            b[iE(cc, k)] = kc[cc] * S.E[cc, k] / (c * dt) - kc[cc] * bt[cc]
         for r, v, val in zip(Ds.row, Ds.col, Ds.data):
             add(iE(r, k), iO(v, k), kc[r] * val)
         Dk = grad_matrix(P, k).tocoo()
@@ -421,12 +476,14 @@ def predict_literal(P, S):
     return E, O, U
 
 
-def flux_div(P, O):
-    """sum_k w_k (D*_k O_k) per cell (the angular integral of Eq. Tnp1, divided by the
-    cell width as in grte1d: Fstar/dx)."""
+def flux_div(P, O, E):
+    """sum_k w_k (streaming derivative of O_k) per cell (the angular integral of
+    Eq. Tnp1, divided by the cell width as in grte1d: Fstar/dx); wall cells through
+    div_operator, which needs E."""
     out = np.zeros(P.nc)
     for k in range(P.K):
-        out += P.w[k] * (div_matrix(P, k) @ O[:, k])
+        Ds, ed, bt = div_operator(P, k)
+        out += P.w[k] * (Ds @ O[:, k] + ed * E[:, k] + bt)
     return out
 
 
@@ -470,7 +527,7 @@ def correct_intensity(P, S, Tnew):
 def step(P, S, info=None):
     """One step: prediction, correction substeps 1 and 2, projection."""
     Es, Os, Us, rhos = predict(P, S)
-    Fd = flux_div(P, Os)
+    Fd = flux_div(P, Os, Es)
     Tn, its, rho_n = correction_temperature(P, S, Fd, Us)
     EJ, En, On = correct_intensity(P, S, Tn)
     if info is not None:

@@ -4,7 +4,7 @@ import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
-SOURCES = [os.path.join(_HERE, "csrc", "grte1d.cu"), os.path.join(_HERE, "csrc", "mlp.cu")]
+SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("grte1d.cu", "grte2d.cu", "mlp.cu")]
 LIB = os.path.join(_HERE, "libgrte.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]

@@ -1,0 +1,1117 @@
+// GB300 (sm_103a) implementation of one step of the AP scheme for the gray radiative
+// transfer equation (Tang, Wang, Zhang, arXiv:1811.05579) on a 2D grid: the 1D
+// scheme (Algorithm 2 of Sec. 4, sigma_0/T^3 form of Sec. 5) taken direction by
+// direction, as declared in include/grte.h (grte2d_*).
+//
+// Unknowns: E (pairs k, cells) and O (pairs k, vertices), U and T per cell.  The
+// streaming operators are applied matrix-free by two stencil kernels: a vertex pass
+// (node equation O = o - d D_k E at vertices that carry one, the inflow-wall and
+// corner expressions elsewhere) and a cell pass (kappa D*_k O, a cell beside an
+// inflow wall taking its wall side from Eq. bc-pre with its own E).  The prediction
+// (Eq. dis-pre / Eq. dis-pre-marshak) is solved for (e, rho), E = rho + e, by
+// restarted GMRES with an exact per-cell angular block solve as left preconditioner;
+// the temperature (Eq. Tnp1) by monotone Newton per cell; correction substep 2
+// (Eq. dis-cor) by GMRES on the stacked pair systems; projection (Eq. dis-proj).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grte.h"
+
+namespace grte2 {
+
+constexpr int kMaxPairs = 64;
+constexpr int kMaxRestart2 = 64;
+constexpr int kThreads = 256;
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs: blocks of the first reduction stage
+
+struct G2 {
+  int Nx, Ny, K, bcx, bcy, kind;
+  int64_t nc, nv;
+  double dx, dy, eps, dt, a, c, Cv;
+  double bx0, bx1, by0, by1;
+};
+
+struct D2 {
+  G2 g;
+  const double *mu, *eta, *w, *sig;
+  double *T, *U, *E, *O;                      // state; E [k][cell], O [k][vertex]
+  double *kc, *A, *alpha, *s, *gam;           // per cell at the current temperature
+  double *dv, *odv;                           // per vertex: d and d eps^2/(c dt) (node-equation vertices)
+  double *rho_n, *Us, *Fdiv, *rho_s, *newton_its, *acU;
+  double *wsc, *iwsc;   // per-cell scale of the Krylov unknowns (k2_weights) and its inverse
+  int* status;
+  int newton_maxit;
+};
+
+__device__ __forceinline__ void flag2(int* status, int code) { atomicOr(status, 1 << code); }
+
+__device__ __forceinline__ int cell_of(const G2& g, int p, int q) {
+  if (g.bcx == GRTE_BC_PERIODIC) p = (p + g.Nx) % g.Nx;
+  if (g.bcy == GRTE_BC_PERIODIC) q = (q + g.Ny) % g.Ny;
+  if (p < 0 || p >= g.Nx || q < 0 || q >= g.Ny) return -1;
+  return q * g.Nx + p;
+}
+
+// 0: node equation (inside, or a periodic copy), 2: inflow x wall, 3: inflow y wall, 4: corner
+__device__ __forceinline__ int vkind(const G2& g, int i, int j) {
+  const bool onx = g.bcx == GRTE_BC_INFLOW && (i == 0 || i == g.Nx);
+  const bool ony = g.bcy == GRTE_BC_INFLOW && (j == 0 || j == g.Ny);
+  return onx && ony ? 4 : onx ? 2 : ony ? 3 : 0;
+}
+
+// ----------------------------------------------------------------------------- coefficients
+// Per cell at temperature T (Eq. dis-pre: kappa = 1, theta = T^3; Eq. dis-pre-marshak:
+// kappa = T^3, theta = 1): s, gamma, A = kappa/(c dt) + sig/eps^2, alpha = kappa/(c dt) + s.
+__global__ void k2_coef(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double T = D.T[c], sg = D.sig[c];
+  const double T3 = T * T * T;
+  const double kc = g.kind == GRTE_SIGMA_CONST ? 1.0 : T3;
+  const double th = g.kind == GRTE_SIGMA_CONST ? T3 : 1.0;
+  const double e2 = g.eps * g.eps;
+  const double s = sg * g.Cv / (g.Cv * e2 + 4.0 * sg * th * g.dt * g.a * g.c);
+  D.kc[c] = kc;
+  D.s[c] = s;
+  D.gam[c] = 4.0 * sg * th * g.dt / (e2 * g.Cv);
+  D.A[c] = kc / (g.c * g.dt) + sg / e2;
+  D.alpha[c] = kc / (g.c * g.dt) + s;
+}
+
+// Per vertex with a node equation: kappa = mean of the four cells, sig = their harmonic
+// mean, d = kappa/(kappa eps^2/(c dt) + sig), od = d eps^2/(c dt).  0 at wall vertices.
+__global__ void k2_vcoef(D2 D) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (v >= g.nv) return;
+  const int i = (int)(v % (g.Nx + 1)), j = (int)(v / (g.Nx + 1));
+  double d = 0.0;
+  if (vkind(g, i, j) == 0) {
+    const int cs[4] = {cell_of(g, i - 1, j - 1), cell_of(g, i, j - 1), cell_of(g, i - 1, j), cell_of(g, i, j)};
+    double kv = 0.0, inv = 0.0;
+    bool pos = true;
+    for (int q = 0; q < 4; ++q) {
+      kv += 0.25 * D.kc[cs[q]];
+      const double sg = D.sig[cs[q]];
+      if (sg > 0.0) inv += 1.0 / sg; else pos = false;
+    }
+    const double sv = pos ? 4.0 / inv : 0.0;
+    d = kv > 0.0 ? kv / (kv * g.eps * g.eps / (g.c * g.dt) + sv) : 0.0;
+  }
+  D.dv[v] = d;
+  D.odv[v] = d * g.eps * g.eps / (g.c * g.dt);
+}
+
+__global__ void k2_rho(D2 D, const double* __restrict__ E, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= D.g.nc) return;
+  double r = 0.0;
+  for (int k = 0; k < D.g.K; ++k) r += D.w[k] * E[(int64_t)k * D.g.nc + c];
+  out[c] = r;
+}
+
+__global__ void k2_acU(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= D.g.nc) return;
+  const double t = D.T[c];
+  D.acU[c] = D.g.a * D.g.c * (t * t) * (t * t);
+}
+
+// ----------------------------------------------------------------------------- stencils
+// Per-pair cell field u_k(c) = (uk[k*ks + c] + ub[c]) * sc[c] (any part may be absent).
+struct UField {
+  const double* uk;
+  int64_t ks;
+  const double* ub;
+  const double* sc = nullptr;
+  __device__ __forceinline__ double at(int k, int c) const {
+    double v = 0.0;
+    if (uk) v += uk[(int64_t)k * ks + c];
+    if (ub) v += ub[c];
+    return sc ? v * sc[c] : v;
+  }
+  __device__ __forceinline__ bool any() const { return uk || ub; }
+};
+
+// O at a node-equation vertex: o - d (D_k u)  (o = d eps^2 O^n/(c dt) with data).
+template <bool DATA>
+__device__ double O_node(const D2& D, const UField& u, int k, int i, int j) {
+  const G2& g = D.g;
+  const int64_t v = (int64_t)j * (g.Nx + 1) + i;
+  double r = DATA ? D.odv[v] * D.O[(int64_t)k * g.nv + v] : 0.0;
+  if (u.any()) {
+    const int c00 = cell_of(g, i - 1, j - 1), c10 = cell_of(g, i, j - 1), c01 = cell_of(g, i - 1, j),
+              c11 = cell_of(g, i, j);
+    const double u00 = u.at(k, c00), u10 = u.at(k, c10), u01 = u.at(k, c01), u11 = u.at(k, c11);
+    const double grad = D.mu[k] * ((u10 + u11) - (u00 + u01)) / (2.0 * g.dx) +
+                        D.eta[k] * ((u01 + u11) - (u00 + u10)) / (2.0 * g.dy);
+    r -= D.dv[v] * grad;
+  }
+  return r;
+}
+
+// Wall expression (Eq. bc-pre along the normal of `axis` at vertex (i, j)):
+//   Omega_k enters:  O = 2/eps (b - E_wall) - O_inner;  else  O = 2/eps (E_wall - b) - O_inner.
+template <bool DATA>
+__device__ double O_wall(const D2& D, const UField& u, int k, int i, int j, int axis, double Oinner) {
+  const G2& g = D.g;
+  double comp, b;
+  int side, ca, cb;
+  if (axis == 0) {
+    side = i == 0 ? 0 : 1;
+    comp = D.mu[k];
+    b = side == 0 ? g.bx0 : g.bx1;
+    const int p = side == 0 ? 0 : g.Nx - 1;
+    ca = cell_of(g, p, j - 1);
+    cb = cell_of(g, p, j);
+  } else {
+    side = j == 0 ? 0 : 1;
+    comp = D.eta[k];
+    b = side == 0 ? g.by0 : g.by1;
+    const int q = side == 0 ? 0 : g.Ny - 1;
+    ca = cell_of(g, i - 1, q);
+    cb = cell_of(g, i, q);
+  }
+  const bool enters = side == 0 ? comp > 0.0 : comp < 0.0;
+  const double sgn = enters ? 1.0 : -1.0;
+  double Ew = 0.0;
+  if (u.any()) {
+    int n = 0;
+    if (ca >= 0) { Ew += u.at(k, ca); ++n; }
+    if (cb >= 0) { Ew += u.at(k, cb); ++n; }
+    Ew /= (double)n;
+  }
+  return sgn * 2.0 / g.eps * ((DATA ? b : 0.0) - Ew) - Oinner;
+}
+
+template <bool DATA>
+__device__ double O_at(const D2& D, const UField& u, int k, int i, int j) {
+  const G2& g = D.g;
+  const int kind = vkind(g, i, j);
+  if (kind == 0) return O_node<DATA>(D, u, k, i, j);
+  const int ii = i == 0 ? 1 : g.Nx - 1, jj = j == 0 ? 1 : g.Ny - 1;
+  if (kind == 2) return O_wall<DATA>(D, u, k, i, j, 0, O_node<DATA>(D, u, k, ii, j));
+  if (kind == 3) return O_wall<DATA>(D, u, k, i, j, 1, O_node<DATA>(D, u, k, i, jj));
+  // corner: mean of the two walls; each wall's inner vertex lies on the other wall
+  const double Oin_x = O_wall<DATA>(D, u, k, ii, j, 1, O_node<DATA>(D, u, k, ii, jj));
+  const double Oin_y = O_wall<DATA>(D, u, k, i, jj, 0, O_node<DATA>(D, u, k, ii, jj));
+  return 0.5 * (O_wall<DATA>(D, u, k, i, j, 0, Oin_x) + O_wall<DATA>(D, u, k, i, j, 1, Oin_y));
+}
+
+// V[k][v] = O_k at every vertex for the field u (and the data part with DATA).
+template <bool DATA>
+__global__ void k2_vertex(D2 D, UField u, double* __restrict__ V) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (v >= g.nv) return;
+  const int i = (int)(v % (g.Nx + 1)), j = (int)(v / (g.Nx + 1));
+  for (int k = 0; k < g.K; ++k) V[(int64_t)k * g.nv + v] = O_at<DATA>(D, u, k, i, j);
+}
+
+enum { C_MV_PRED = 0, C_MV_CORR = 1, C_DIVK = 2, C_FDIV = 3 };
+
+// Side weights of cell (p, q) for pair k: the streaming derivative of O at the cell is
+//   mu/(2 dx) [wL (O00 + O01) + wR (O10 + O11)] + eta/(2 dy) [wB (O00 + O10) + wT (O01 + O11)]
+//   + ed E_cell + bt,
+// with (wL, wR, wB, wT) = (-1, 1, -1, 1) inside.  A cell beside an inflow wall applies
+// Eq. bc-pre to its own wall side as the 1D wall cell does: the low x side becomes
+// s 2/eps (b - E_cell) - (high side), i.e. mu (2 R - s 2/eps (b - E_cell))/dx, and
+// likewise for the other sides (s = +1 if Omega_k enters there, else -1).
+struct CellSides {
+  double wL, wR, wB, wT, ed, bt;
+};
+
+__device__ __forceinline__ CellSides cell_sides(const D2& D, int k, int p, int q) {
+  const G2& g = D.g;
+  CellSides cs{-1.0, 1.0, -1.0, 1.0, 0.0, 0.0};
+  const double mu = D.mu[k], eta = D.eta[k], te = 2.0 / g.eps;
+  if (g.bcx == GRTE_BC_INFLOW) {
+    if (p == 0) {
+      const double s = mu > 0.0 ? 1.0 : -1.0;   // Omega_k enters at x = 0 when mu > 0
+      cs.wL = 0.0;
+      cs.wR = 2.0;
+      cs.ed += mu * s * te / g.dx;
+      cs.bt -= mu * s * te * g.bx0 / g.dx;
+    }
+    if (p == g.Nx - 1) {
+      const double s = mu < 0.0 ? 1.0 : -1.0;
+      if (p != 0) cs.wL = -2.0;
+      cs.wR = 0.0;
+      cs.ed -= mu * s * te / g.dx;
+      cs.bt += mu * s * te * g.bx1 / g.dx;
+    }
+  }
+  if (g.bcy == GRTE_BC_INFLOW) {
+    if (q == 0) {
+      const double s = eta > 0.0 ? 1.0 : -1.0;
+      cs.wB = 0.0;
+      cs.wT = 2.0;
+      cs.ed += eta * s * te / g.dy;
+      cs.bt -= eta * s * te * g.by0 / g.dy;
+    }
+    if (q == g.Ny - 1) {
+      const double s = eta < 0.0 ? 1.0 : -1.0;
+      if (q != 0) cs.wB = -2.0;
+      cs.wT = 0.0;
+      cs.ed -= eta * s * te / g.dy;
+      cs.bt += eta * s * te * g.by1 / g.dy;
+    }
+  }
+  return cs;
+}
+
+// Cell pass over the vertex values V (computed from the same field u, with the data
+// part when DATA):
+//   C_MV_PRED: y_k = A z_k + alpha z_rho + kappa S_k,  y_rho = alpha z_rho + sum_k w_k kappa S_k
+//   C_MV_CORR: y_k = A z_k + kappa S_k
+//   C_DIVK:    y_k = kappa S_k
+//   C_FDIV:    y   = sum_k w_k S_k
+// S_k the streaming derivative of O_k at the cell (cell_sides).  z is read scaled by
+// zs[c] when zs is given (the Krylov unknowns are cell-scaled).
+template <int MODE, bool DATA>
+__global__ void k2_cell(D2 D, const double* __restrict__ V, UField u, const double* __restrict__ z,
+                        double* __restrict__ y, const double* __restrict__ zs) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
+  const int64_t v00 = (int64_t)q * (g.Nx + 1) + p, v10 = v00 + 1, v01 = v00 + g.Nx + 1, v11 = v01 + 1;
+  const double kc = D.kc[c];
+  const double f = zs ? zs[c] : 1.0;
+  const double zr = MODE == C_MV_PRED ? f * z[(int64_t)g.K * g.nc + c] : 0.0;
+  const bool wall = (g.bcx == GRTE_BC_INFLOW && (p == 0 || p == g.Nx - 1)) ||
+                    (g.bcy == GRTE_BC_INFLOW && (q == 0 || q == g.Ny - 1));
+  double acc = 0.0;
+  for (int k = 0; k < g.K; ++k) {
+    const double* Vk = V + (int64_t)k * g.nv;
+    double div;
+    if (!wall) {
+      div = D.mu[k] * ((Vk[v10] + Vk[v11]) - (Vk[v00] + Vk[v01])) / (2.0 * g.dx) +
+            D.eta[k] * ((Vk[v01] + Vk[v11]) - (Vk[v00] + Vk[v10])) / (2.0 * g.dy);
+    } else {
+      const CellSides cs = cell_sides(D, k, p, q);
+      div = D.mu[k] / (2.0 * g.dx) * (cs.wL * (Vk[v00] + Vk[v01]) + cs.wR * (Vk[v10] + Vk[v11])) +
+            D.eta[k] / (2.0 * g.dy) * (cs.wB * (Vk[v00] + Vk[v10]) + cs.wT * (Vk[v01] + Vk[v11]));
+      if (u.any()) div += cs.ed * u.at(k, (int)c);
+      if (DATA) div += cs.bt;
+    }
+    const int64_t o = (int64_t)k * g.nc + c;
+    if (MODE == C_MV_PRED) {
+      y[o] = D.A[c] * f * z[o] + D.alpha[c] * zr + kc * div;
+      acc += D.w[k] * kc * div;
+    } else if (MODE == C_MV_CORR) {
+      y[o] = D.A[c] * f * z[o] + kc * div;
+    } else if (MODE == C_DIVK) {
+      y[o] = kc * div;
+    } else {
+      acc += D.w[k] * div;
+    }
+  }
+  if (MODE == C_MV_PRED) y[(int64_t)g.K * g.nc + c] = D.alpha[c] * zr + acc;
+  if (MODE == C_FDIV) y[c] = acc;
+}
+
+// Diagonal of G_k at cell c (for the preconditioner): the node-equation vertices of
+// the cell contribute kappa (side weight) (D* coefficient) (-d) (D_k coefficient), a
+// wall cell its own E term kappa ed; wall vertices of an opposite side (corner cells)
+// are left out.
+__device__ double gdiag(const D2& D, int k, int p, int q) {
+  const G2& g = D.g;
+  const CellSides cs = cell_sides(D, k, p, q);
+  const double mx = D.mu[k] / (2.0 * g.dx), ey = D.eta[k] / (2.0 * g.dy);
+  const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
+  // D* coefficient of vertex t of the cell with the side weights
+  const double cst[4] = {cs.wL * mx + cs.wB * ey, cs.wR * mx + cs.wB * ey, cs.wL * mx + cs.wT * ey,
+                         cs.wR * mx + cs.wT * ey};
+  const double a = mx + ey, b = mx - ey;
+  const double cgr[4] = {a, -b, b, -a};   // D_k coefficient of this cell at vertex t
+  double r = cs.ed;
+  for (int t = 0; t < 4; ++t) {
+    const int i = p + di[t], j = q + dj[t];
+    if (vkind(g, i, j) != 0) continue;
+    const int64_t v = (int64_t)j * (g.Nx + 1) + i;
+    r += cst[t] * (-D.dv[v] * cgr[t]);
+  }
+  return D.kc[q * g.Nx + p] * r;
+}
+
+// Left preconditioner.  Prediction: per cell, the angular block of the matrix with G_k
+// replaced by its diagonal g_k (an arrow matrix), solved exactly:
+//   rho = [r_rho - sum_k w_k g_k r_k/(A+g_k)] / [alpha + sum_k w_k g_k (A - alpha)/(A+g_k)],
+//   e_k = (r_k - (alpha + g_k) rho)/(A + g_k).
+// Correction: z_k = r_k/(A + g_k).  The result is multiplied by the cell's Krylov
+// scale w (the GMRES runs on w-scaled unknowns: D_w P^{-1} M D_w^{-1}).
+template <bool PRED>
+__global__ void k2_prec(D2 D, const double* __restrict__ r, double* __restrict__ z) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
+  const double A = D.A[c], al = D.alpha[c], ws = D.wsc[c];
+  if (!PRED) {
+    for (int k = 0; k < g.K; ++k)
+      z[(int64_t)k * g.nc + c] = ws * r[(int64_t)k * g.nc + c] / (A + gdiag(D, k, p, q));
+    return;
+  }
+  double num = r[(int64_t)g.K * g.nc + c], den = al;
+  double gk[kMaxPairs];
+  for (int k = 0; k < g.K; ++k) {
+    gk[k] = gdiag(D, k, p, q);
+    const double wg = D.w[k] * gk[k];
+    num -= wg * r[(int64_t)k * g.nc + c] / (A + gk[k]);
+    den += wg * (A - al) / (A + gk[k]);
+  }
+  const double rho = num / den;
+  z[(int64_t)g.K * g.nc + c] = ws * rho;
+  for (int k = 0; k < g.K; ++k)
+    z[(int64_t)k * g.nc + c] = ws * (r[(int64_t)k * g.nc + c] - (al + gk[k]) * rho) / (A + gk[k]);
+}
+
+// Krylov scale per cell from a magnitude field src: s = |src| + 1e-13 max|src|,
+// w = f/s (f = 1 in the prediction, eps in the correction, whose unknown E_J enters
+// E as eps E_J).
+__global__ void k2_maxabs(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  __shared__ double red[kThreads / 32];
+  double t = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    t = fmax(t, fabs(x[j]));
+  for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, red[q]);
+    part[blockIdx.x] = m;
+  }
+}
+
+__global__ void k2_weights(D2 D, const double* __restrict__ src, double f, const double* __restrict__ part, int nb) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= D.g.nc) return;
+  double m = 0.0;
+  for (int b = 0; b < nb; ++b) m = fmax(m, part[b]);
+  const double s = fabs(src[c]) + 1e-13 * m + 1e-300;
+  D.wsc[c] = f / s;
+  D.iwsc[c] = s / f;
+}
+
+// magnitude of E^{n+1} per cell for the correction's scale: max(a c U, |rho*|)
+__global__ void k2_corrscale(D2 D, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= D.g.nc) return;
+  out[c] = fmax(D.acU[c], fabs(D.rho_s[c]));
+}
+
+// x[k][c] *= sc[c] over nvec stacked per-cell blocks
+__global__ void k2_cellscale(double* __restrict__ x, const double* __restrict__ sc, int nvec, int64_t nc) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double f = sc[c];
+  for (int k = 0; k < nvec; ++k) x[(int64_t)k * nc + c] *= f;
+}
+
+// ----------------------------------------------------------------------------- right-hand sides
+// Prediction: b_k = kappa E^n_k/(c dt) + s a c U^n - phi_k,
+//             b_rho = kappa rho^n/(c dt) + s a c U^n - sum_k w_k phi_k;
+// initial iterate e_k = E^n_k - rho^n, rho = rho^n.
+__global__ void k2_rhs_pred(D2 D, const double* __restrict__ phi, double* __restrict__ b, double* __restrict__ x) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double cdt = g.c * g.dt, sac = D.s[c] * g.a * g.c * D.U[c], kc = D.kc[c], rn = D.rho_n[c];
+  double ps = 0.0;
+  for (int k = 0; k < g.K; ++k) {
+    const int64_t o = (int64_t)k * g.nc + c;
+    b[o] = kc * D.E[o] / cdt + sac - phi[o];
+    x[o] = D.E[o] - rn;
+    ps += D.w[k] * phi[o];
+  }
+  b[(int64_t)g.K * g.nc + c] = kc * rn / cdt + sac - ps;
+  x[(int64_t)g.K * g.nc + c] = rn;
+}
+
+// E*_k = rho + e_k, U* = (U^n + gamma rho)/(1 + gamma a c), rho* kept.
+__global__ void k2_finish_pred(D2 D, const double* __restrict__ x, double* __restrict__ Es) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double rho = x[(int64_t)g.K * g.nc + c];
+  for (int k = 0; k < g.K; ++k) Es[(int64_t)k * g.nc + c] = rho + x[(int64_t)k * g.nc + c];
+  D.rho_s[c] = rho;
+  D.Us[c] = (D.U[c] + D.gam[c] * rho) / (1.0 + D.gam[c] * g.a * g.c);
+}
+
+// Correction: b_k = [kappa (E^n_k - a c U)/(c dt) - (G_k a c U) - phi_k]/eps, x = 0.
+__global__ void k2_rhs_corr(D2 D, const double* __restrict__ GU, const double* __restrict__ phi,
+                            double* __restrict__ b, double* __restrict__ x) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double cdt = g.c * g.dt, kc = D.kc[c], acU = D.acU[c];
+  for (int k = 0; k < g.K; ++k) {
+    const int64_t o = (int64_t)k * g.nc + c;
+    b[o] = (kc * (D.E[o] - acU) / cdt - GU[o] - phi[o]) / g.eps;
+    x[o] = 0.0;
+  }
+}
+
+// E^{n+1} = a c U + eps E_J (Eq. dis-proj), U = T^4
+__global__ void k2_project(D2 D, const double* __restrict__ EJ) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double acU = D.acU[c];
+  for (int k = 0; k < g.K; ++k) {
+    const int64_t o = (int64_t)k * g.nc + c;
+    D.E[o] = acU + g.eps * EJ[o];
+  }
+  const double t = D.T[c];
+  D.U[c] = (t * t) * (t * t);
+}
+
+// ----------------------------------------------------------------------------- Newton
+// Eq. Tnp1 (sigma_0/T^3: Eq. dis-cor-marshak4 + 5) multiplied by sig:
+//   A T^4 + B T = R,  A = sig a/dt,  B = sig Cv/dt + eps^2 kap Cv/(c dt^2),
+//   R = sig (rho^n/(c dt) - Fdiv) + B T^n,  kap = 1 or max(U*, 0)^{3/4};
+// Newton from T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the root.
+__global__ void k2_newton(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double sg = D.sig[c], Tn = D.T[c];
+  const double kap = g.kind == GRTE_SIGMA_CONST ? 1.0 : pow(fmax(D.Us[c], 0.0), 0.75);
+  const double A = sg * g.a / g.dt;
+  const double B = sg * g.Cv / g.dt + g.eps * g.eps * kap * g.Cv / (g.c * g.dt * g.dt);
+  const double R = sg * (D.rho_n[c] / (g.c * g.dt) - D.Fdiv[c]) + B * Tn;
+  double T = Tn;
+  int its = 0;
+  if (A == 0.0 && B == 0.0) {
+    T = Tn;
+  } else if (!(R > 0.0)) {
+    T = 0.0;
+    flag2(D.status, R <= 0.0 ? GRTE_ENEGATIVE : GRTE_ENAN);
+  } else {
+    double t = A > 0.0 ? sqrt(sqrt(R / A)) : INFINITY;
+    if (B > 0.0) t = fmin(t, R / B);
+    for (its = 1; its <= D.newton_maxit; ++its) {
+      const double t2 = t * t;
+      const double f = A * t2 * t2 + B * t - R;
+      const double fp = 4.0 * A * t2 * t + B;
+      const double tn = t - f / fp;
+      if (!(tn < t)) break;
+      t = tn;
+    }
+    if (its > D.newton_maxit) flag2(D.status, GRTE_ENONCONV);
+    T = t;
+  }
+  D.T[c] = T;
+  D.newton_its[c] = (double)its;
+}
+
+// ----------------------------------------------------------------------------- vector kernels
+// Partial dot products of w with V_0..V_{nvec-1} (stride n): one value per (block, vec),
+// fixed order; k2_reduce sums the block partials (one block per value).
+__global__ void k2_mdot(const double* __restrict__ w, const double* __restrict__ V, int nvec, int64_t n,
+                        double* __restrict__ part) {
+  __shared__ double red[kThreads / 32][kMaxRestart2 + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nvec; i0 += 8) {
+    double acc[8];
+    for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const double wj = w[j];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (i0 + t < nvec) acc[t] += wj * V[(int64_t)(i0 + t) * n + j];
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      double v = acc[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && i0 + t < nvec) red[wid][i0 + t] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][i];
+    part[(int64_t)i * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k2_reduce(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double red[kThreads / 32];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[(int64_t)blockIdx.x * nb + b];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    out[blockIdx.x] = s;
+  }
+}
+
+// w -= sum_i coef[i] V_i
+__global__ void k2_maxpy(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ coef,
+                         int nvec, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double t = w[j];
+    for (int i = 0; i < nvec; ++i) t -= coef[i] * V[(int64_t)i * n + j];
+    w[j] = t;
+  }
+}
+
+// x += sum_i coef[i] V_i
+__global__ void k2_update(double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ coef,
+                          int nvec, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double t = x[j];
+    for (int i = 0; i < nvec; ++i) t += coef[i] * V[(int64_t)i * n + j];
+    x[j] = t;
+  }
+}
+
+__global__ void k2_scale(double* __restrict__ x, double s, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    x[j] *= s;
+}
+
+// y = b - y
+__global__ void k2_bminus(const double* __restrict__ b, double* __restrict__ y, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    y[j] = b[j] - y[j];
+}
+
+__global__ void k2_energy(D2 D, double* __restrict__ part) {
+  __shared__ double red[kThreads / 32];
+  const G2& g = D.g;
+  double t = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.nc; c += (int64_t)gridDim.x * blockDim.x) {
+    double rho = 0.0;
+    for (int k = 0; k < g.K; ++k) rho += D.w[k] * D.E[(int64_t)k * g.nc + c];
+    t += g.dx * g.dy * (rho / g.c + g.Cv * D.T[c]);
+  }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    part[blockIdx.x] = s;
+  }
+}
+
+// Level-symmetric S8 pairs for 2D (80 directions on the sphere: cosine levels
+// mu_i^2 = (1 + 6 i)/21, i = 0..3; per octant the permutations of the level triples
+// (0,0,3), (0,1,2), (1,1,1), three weight classes fixed by the moments sum w = 1,
+// sum w mu^4 = 1/5, sum w mu^6 = 1/7; the 40 directions with a positive third cosine,
+// projected on the plane, form 20 pairs; each pair is represented by its member with
+// mu > 0 and weighs its two members).  Sorted by (mu, eta).
+static void s8_pairs(std::vector<double>& mu, std::vector<double>& eta, std::vector<double>& w) {
+  double m[4], lv[4];
+  for (int i = 0; i < 4; ++i) {
+    m[i] = (1.0 + 6.0 * i) / 21.0;
+    lv[i] = std::sqrt(m[i]);
+  }
+  struct Dir { int a, b, c, cls; };
+  std::vector<Dir> oct;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c)
+        if (a + b + c == 3) {
+          int s[3] = {a, b, c};
+          std::sort(s, s + 3);
+          const int cls = (s[0] == 0 && s[1] == 0) ? 0 : (s[0] == 1 && s[1] == 1) ? 2 : 1;
+          oct.push_back({a, b, c, cls});
+        }
+  double M[3][4] = {{0}};
+  for (const Dir& d : oct) {
+    M[0][d.cls] += 8.0;
+    M[1][d.cls] += 8.0 * m[d.a] * m[d.a];
+    M[2][d.cls] += 8.0 * m[d.a] * m[d.a] * m[d.a];
+  }
+  M[0][3] = 1.0;
+  M[1][3] = 1.0 / 5.0;
+  M[2][3] = 1.0 / 7.0;
+  for (int col = 0; col < 3; ++col) {   // Gauss-Jordan with partial pivoting on 3x3
+    int piv = col;
+    for (int r = col + 1; r < 3; ++r)
+      if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+    for (int cc = 0; cc < 4; ++cc) std::swap(M[col][cc], M[piv][cc]);
+    for (int r = 0; r < 3; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col] / M[col][col];
+      for (int cc = 0; cc < 4; ++cc) M[r][cc] -= f * M[col][cc];
+    }
+  }
+  const double wc[3] = {M[0][3] / M[0][0], M[1][3] / M[1][1], M[2][3] / M[2][2]};
+  struct P { double mu, eta, w; };
+  std::vector<P> ps;
+  double tot = 0.0;
+  // the member with mu > 0 and third cosine > 0 of each pair; the pair's weight is that
+  // of (mu, eta, xi) plus that of (-mu, -eta, xi)
+  for (int sy = 0; sy < 2; ++sy)
+    for (const Dir& d : oct) {
+      const double x = lv[d.a], y = (sy == 0 ? 1.0 : -1.0) * lv[d.b];
+      ps.push_back({x, y, 2.0 * wc[d.cls]});
+      tot += 2.0 * wc[d.cls];
+    }
+  std::sort(ps.begin(), ps.end(), [](const P& l, const P& r) { return l.mu < r.mu || (l.mu == r.mu && l.eta < r.eta); });
+  mu.clear(); eta.clear(); w.clear();
+  for (const P& p : ps) {
+    mu.push_back(p.mu);
+    eta.push_back(p.eta);
+    w.push_back(p.w / tot);
+  }
+}
+
+}  // namespace grte2
+
+// =============================================================================== host
+using namespace grte2;
+
+struct grte2d_ctx {
+  D2 D{};
+  G2 g{};
+  grte_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool state_set = false;
+  std::vector<double> hmu, heta, hw;
+  std::vector<void*> allocs;
+  std::string err;
+  grte_stats_t stats{};
+  int host_flags = 0;   // statuses found on the host (a solve that missed its tolerance)
+  int m = 30;
+  double *V = nullptr, *phi = nullptr, *GU = nullptr, *Es = nullptr;
+  double *b = nullptr, *x = nullptr, *Kr = nullptr, *Kt = nullptr, *Kbasis = nullptr;
+  double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr;
+  double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
+};
+
+static grte_status fail2(grte2d_t h, grte_status s, const std::string& m) {
+  if (h) h->err = m;
+  return s;
+}
+#define CK2(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail2(h, GRTE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+template <typename T>
+static bool alloc2(grte2d_t h, T** p, int64_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, sizeof(T) * (size_t)std::max<int64_t>(n, 1)) != cudaSuccess) return false;
+  cudaMemset(q, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return true;
+}
+
+// dots[i] = <w, V_i>, i < nvec, returned on the host.
+static grte_status mdot(grte2d_t h, const double* w, const double* V, int nvec, int64_t n, double* host) {
+  cudaStream_t st = h->stream;
+  k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, V, nvec, n, h->part);
+  k2_reduce<<<nvec, kThreads, 0, st>>>(h->part, kRedBlocks, h->dots);
+  CK2(cudaGetLastError());
+  CK2(cudaMemcpyAsync(host, h->dots, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
+  CK2(cudaStreamSynchronize(st));
+  return GRTE_OK;
+}
+
+// y = M x (pred: the (e, rho) matrix; corr: the stacked A + G_k), through the vertex
+// and cell passes.  The Krylov unknowns are w-scaled: they are unscaled on the way in.
+static void apply_M(grte2d_t h, bool pred, const double* xin, double* y) {
+  D2& D = h->D;
+  cudaStream_t st = h->stream;
+  UField u{xin, D.g.nc, pred ? xin + (int64_t)D.g.K * D.g.nc : nullptr, D.iwsc};
+  k2_vertex<false><<<grid_of(D.g.nv), kThreads, 0, st>>>(D, u, h->V);
+  if (pred) k2_cell<C_MV_PRED, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc);
+  else k2_cell<C_MV_CORR, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc);
+}
+
+static void apply_P(grte2d_t h, bool pred, const double* r, double* z) {
+  if (pred) k2_prec<true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, r, z);
+  else k2_prec<false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, r, z);
+}
+
+// Restarted GMRES(m) with left preconditioning on M x = b (x holds the initial
+// iterate).  Each restart cycle runs on the cell-scaled unknowns y = D_w x, D_w the
+// diagonal of the per-cell scale w computed from the current iterate (prediction:
+// w = 1/|rho|; correction: w = eps/max(a c U, |rho*|)), a similarity transform
+// D_w P^{-1} M D_w^{-1} that keeps the preconditioned spectrum.  In those units every
+// cell's unknowns are O(1), so the test |D_w P^{-1}(b - M x)|_2 <= rtol sqrt(n_cells)
+// bounds the residual of every cell relative to the cell's own magnitude (RMS).
+static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
+  cudaStream_t st = h->stream;
+  D2& D = h->D;
+  const int nblk = pred ? D.g.K + 1 : D.g.K;
+  const unsigned gc = grid_of(D.g.nc);
+  const int m = h->m;
+  double* V = h->Kbasis;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), yv(m), dd(m + 2);
+  const unsigned vb = kRedBlocks;
+  const double thr = h->opt.krylov_rtol * std::sqrt((double)D.g.nc);
+  grte_status s = GRTE_OK;
+  iters = 0;
+  auto set_scale = [&]() {
+    const double* src = pred ? h->x + (int64_t)D.g.K * D.g.nc : h->cscale;
+    k2_maxabs<<<kRedBlocks, kThreads, 0, st>>>(src, D.g.nc, h->part);
+    k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks);
+  };
+  // the true scaled residual of the unscaled x, into V_0; returns its norm
+  auto residual = [&](double* beta) -> grte_status {
+    set_scale();
+    k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.wsc, nblk, D.g.nc);   // x -> y
+    apply_M(h, pred, h->x, h->Kr);
+    k2_bminus<<<vb, kThreads, 0, st>>>(h->b, h->Kr, n);
+    apply_P(h, pred, h->Kr, V);
+    double b2 = 0.0;
+    grte_status r = mdot(h, V, V, 1, n, &b2);
+    *beta = std::sqrt(b2);
+    return r;
+  };
+  for (int cycle = 0; cycle <= h->opt.krylov_maxcycles; ++cycle) {
+    double beta = 0.0;
+    if ((s = residual(&beta)) != GRTE_OK) return s;
+    if (!std::isfinite(beta)) return fail2(h, GRTE_ENAN, "GMRES: non-finite residual");
+    if (beta <= thr || cycle == h->opt.krylov_maxcycles) {
+      k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);  // y -> x
+      if (!(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
+      return GRTE_OK;
+    }
+    k2_scale<<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kk = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* w = V + (int64_t)(j + 1) * n;
+      apply_M(h, pred, vj, h->Kr);
+      apply_P(h, pred, h->Kr, w);
+      // classical Gram-Schmidt, twice
+      std::vector<double> hc(j + 2, 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((s = mdot(h, w, V, j + 1, n, dd.data())) != GRTE_OK) return s;
+        CK2(cudaMemcpyAsync(h->coef, dd.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+        k2_maxpy<<<vb, kThreads, 0, st>>>(w, V, h->coef, j + 1, n);
+        CK2(cudaStreamSynchronize(st));   // dd is reused by the next pass
+        for (int i = 0; i <= j; ++i) hc[i] += dd[i];
+      }
+      double hn2 = 0.0;
+      if ((s = mdot(h, w, w, 1, n, &hn2)) != GRTE_OK) return s;
+      const double hn = std::sqrt(hn2);
+      hc[j + 1] = hn;
+      ++iters;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+        hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+        hc[i] = t;
+      }
+      const double rr = std::hypot(hc[j], hc[j + 1]);
+      cs[j] = rr > 0.0 ? hc[j] / rr : 1.0;
+      sn[j] = rr > 0.0 ? hc[j + 1] / rr : 0.0;
+      hc[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
+      kk = j + 1;
+      if (hn > 0.0) k2_scale<<<vb, kThreads, 0, st>>>(w, 1.0 / hn, n);
+      if (std::fabs(g[j + 1]) <= 0.5 * thr || hn == 0.0) break;
+    }
+    for (int i = kk - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < kk; ++l) t -= H[(size_t)i * m + l] * yv[l];
+      yv[i] = t / H[(size_t)i * m + i];
+    }
+    CK2(cudaMemcpyAsync(h->coef, yv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
+    k2_update<<<vb, kThreads, 0, st>>>(h->x, V, h->coef, kk, n);
+    k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);    // y -> x
+    CK2(cudaStreamSynchronize(st));
+    CK2(cudaGetLastError());
+  }
+  return GRTE_OK;
+}
+
+static grte_status step2(grte2d_t h) {
+  D2& D = h->D;
+  const G2& g = D.g;
+  cudaStream_t st = h->stream;
+  const unsigned gc = grid_of(g.nc), gv = grid_of(g.nv);
+  const int64_t K = g.K, nc = g.nc;
+  int its = 0;
+  // prediction at T^n
+  k2_coef<<<gc, kThreads, 0, st>>>(D);
+  k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+  k2_rho<<<gc, kThreads, 0, st>>>(D, D.E, D.rho_n);
+  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<C_DIVK, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr);
+  k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
+  CK2(cudaGetLastError());
+  grte_status s = gmres2(h, true, (K + 1) * nc, its);
+  if (s != GRTE_OK) return s;
+  h->stats.krylov_iters += its;
+  k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
+  // O* and the flux term of the temperature equation
+  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{h->Es, nc, nullptr}, h->V);
+  k2_cell<C_FDIV, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{h->Es, nc, nullptr}, nullptr, D.Fdiv, nullptr);
+  k2_newton<<<gc, kThreads, 0, st>>>(D);
+  // correction substep 2 at T^{n+1}
+  k2_coef<<<gc, kThreads, 0, st>>>(D);
+  k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+  k2_acU<<<gc, kThreads, 0, st>>>(D);
+  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<C_DIVK, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr);
+  k2_vertex<false><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, D.acU}, h->V);
+  k2_cell<C_DIVK, false><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr);
+  k2_rhs_corr<<<gc, kThreads, 0, st>>>(D, h->GU, h->phi, h->b, h->x);
+  k2_corrscale<<<gc, kThreads, 0, st>>>(D, h->cscale);
+  CK2(cudaGetLastError());
+  its = 0;
+  s = gmres2(h, false, K * nc, its);
+  if (s != GRTE_OK) return s;
+  h->stats.krylov_iters += its;
+  // projection: E = a c U + eps E_J, O from E (vertex map with the O^n data), U = T^4
+  k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
+  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{D.E, nc, nullptr}, h->V);
+  CK2(cudaMemcpyAsync(D.O, h->V, sizeof(double) * K * g.nv, cudaMemcpyDeviceToDevice, st));
+  CK2(cudaGetLastError());
+  return GRTE_OK;
+}
+
+extern "C" {
+
+void grte2d_destroy(grte2d_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* grte2d_last_error(grte2d_t h) { return h ? h->err.c_str() : "null handle"; }
+
+grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grte2d_t* out) {
+  if (!out) return GRTE_EINVAL;
+  *out = nullptr;
+  if (!p) return GRTE_EINVAL;
+  grte2d_t h = new (std::nothrow) grte2d_ctx();
+  if (!h) return GRTE_ENOMEM;
+  *out = h;
+  grte_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (h->opt.precision != GRTE_FP64) return fail2(h, GRTE_EINVAL, "2D instances run in GRTE_FP64");
+  h->m = h->opt.krylov_restart == 10 ? 30 : h->opt.krylov_restart;
+  if (h->m < 1 || h->m > kMaxRestart2) return fail2(h, GRTE_EINVAL, "krylov_restart out of range [1,64]");
+  if (!(h->opt.krylov_rtol > 0) || h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1)
+    return fail2(h, GRTE_EINVAL, "bad solver options");
+  if (p->nx < 2 || p->ny < 2 || p->nx > 32768 || p->ny > 32768) return fail2(h, GRTE_EINVAL, "nx, ny must be in [2, 32768]");
+  if (!p->sigma) return fail2(h, GRTE_EINVAL, "sigma is NULL");
+  if (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3) return fail2(h, GRTE_EINVAL, "bad sigma_kind");
+  for (int bc : {p->bc_x, p->bc_y})
+    if (bc != GRTE_BC_INFLOW && bc != GRTE_BC_PERIODIC) return fail2(h, GRTE_EINVAL, "bc must be INFLOW or PERIODIC");
+  if (!(p->lx > 0) || !(p->ly > 0) || !(p->dt > 0) || !(p->a > 0) || !(p->c > 0) || !(p->Cv > 0) || !(p->eps > 0))
+    return fail2(h, GRTE_EINVAL, "lx, ly, dt, a, c, Cv, eps must be positive");
+  if (p->n_pair < 0 || p->n_pair > kMaxPairs) return fail2(h, GRTE_EINVAL, "n_pair must be in [0, 64]");
+  if (p->n_pair == 0) {
+    s8_pairs(h->hmu, h->heta, h->hw);
+  } else {
+    if (!p->mu || !p->eta || !p->w) return fail2(h, GRTE_EINVAL, "mu, eta, w required when n_pair > 0");
+    h->hmu.assign(p->mu, p->mu + p->n_pair);
+    h->heta.assign(p->eta, p->eta + p->n_pair);
+    h->hw.assign(p->w, p->w + p->n_pair);
+    double sw = 0.0;
+    for (int k = 0; k < p->n_pair; ++k) {
+      if (!(h->hw[k] > 0.0)) return fail2(h, GRTE_EINVAL, "weights must be positive");
+      if (p->bc_x == GRTE_BC_INFLOW && h->hmu[k] == 0.0) return fail2(h, GRTE_EINVAL, "mu = 0 with an inflow x axis");
+      if (p->bc_y == GRTE_BC_INFLOW && h->heta[k] == 0.0) return fail2(h, GRTE_EINVAL, "eta = 0 with an inflow y axis");
+      sw += h->hw[k];
+    }
+    for (double& v : h->hw) v /= sw;
+  }
+  G2& g = h->g;
+  g.Nx = (int)p->nx;
+  g.Ny = (int)p->ny;
+  g.K = (int)h->hmu.size();
+  g.bcx = p->bc_x;
+  g.bcy = p->bc_y;
+  g.kind = p->sigma_kind;
+  g.nc = p->nx * p->ny;
+  g.nv = (p->nx + 1) * (p->ny + 1);
+  g.dx = p->lx / (double)p->nx;
+  g.dy = p->ly / (double)p->ny;
+  g.eps = p->eps; g.dt = p->dt; g.a = p->a; g.c = p->c; g.Cv = p->Cv;
+  g.bx0 = p->b_x0; g.bx1 = p->b_x1; g.by0 = p->b_y0; g.by1 = p->b_y1;
+  for (int64_t c = 0; c < g.nc; ++c)
+    if (!(p->sigma[c] >= 0.0) || !std::isfinite(p->sigma[c])) return fail2(h, GRTE_EINVAL, "sigma must be finite and >= 0");
+  if (h->opt.stream) {
+    h->stream = (cudaStream_t)h->opt.stream;
+  } else {
+    CK2(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  D2& D = h->D;
+  D.g = g;
+  D.newton_maxit = h->opt.newton_maxit;
+  const int64_t K = g.K, nc = g.nc, nv = g.nv, nz = (K + 1) * nc;
+  bool ok = alloc2(h, &h->dmu, K) && alloc2(h, &h->deta, K) && alloc2(h, &h->dw, K) && alloc2(h, &h->dsig, nc) &&
+            alloc2(h, &D.T, nc) && alloc2(h, &D.U, nc) && alloc2(h, &D.E, K * nc) && alloc2(h, &D.O, K * nv) &&
+            alloc2(h, &D.kc, nc) && alloc2(h, &D.A, nc) && alloc2(h, &D.alpha, nc) && alloc2(h, &D.s, nc) &&
+            alloc2(h, &D.gam, nc) && alloc2(h, &D.dv, nv) && alloc2(h, &D.odv, nv) && alloc2(h, &D.rho_n, nc) &&
+            alloc2(h, &D.Us, nc) && alloc2(h, &D.Fdiv, nc) && alloc2(h, &D.rho_s, nc) &&
+            alloc2(h, &D.newton_its, nc) && alloc2(h, &D.acU, nc) && alloc2(h, &D.status, 1) &&
+            alloc2(h, &D.wsc, nc) && alloc2(h, &D.iwsc, nc) &&
+            alloc2(h, &h->V, K * nv) && alloc2(h, &h->phi, K * nc) && alloc2(h, &h->GU, K * nc) &&
+            alloc2(h, &h->Es, K * nc) && alloc2(h, &h->b, nz) && alloc2(h, &h->x, nz) && alloc2(h, &h->Kr, nz) &&
+            alloc2(h, &h->Kt, nz) && alloc2(h, &h->Kbasis, (int64_t)(h->m + 1) * nz) &&
+            alloc2(h, &h->part, (int64_t)kRedBlocks * (kMaxRestart2 + 1)) && alloc2(h, &h->dots, kMaxRestart2 + 1) &&
+            alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc);
+  if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
+  D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
+  CK2(cudaMemcpy(h->dmu, h->hmu.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(h->deta, h->heta.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(h->dw, h->hw.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(h->dsig, p->sigma, sizeof(double) * nc, cudaMemcpyHostToDevice));
+  return GRTE_OK;
+}
+
+grte_status grte2d_set_state(grte2d_t h, const double* T, const double* E, const double* O) {
+  if (!h) return GRTE_EINVAL;
+  if (!T) return fail2(h, GRTE_EINVAL, "T is NULL");
+  if ((E == nullptr) != (O == nullptr)) return fail2(h, GRTE_EINVAL, "E and O must both be given or both NULL");
+  const G2& g = h->g;
+  const int64_t K = g.K, nc = g.nc, nv = g.nv;
+  std::vector<double> hE(K * nc), hO(K * nv, 0.0), hU(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    if (!(T[c] >= 0.0) || !std::isfinite(T[c])) return fail2(h, GRTE_EINVAL, "T must be finite and >= 0");
+    hU[c] = (T[c] * T[c]) * (T[c] * T[c]);
+  }
+  for (int64_t k = 0; k < K; ++k) {
+    for (int64_t c = 0; c < nc; ++c) hE[k * nc + c] = E ? E[c * K + k] : g.a * g.c * hU[c];
+    if (O)
+      for (int64_t v = 0; v < nv; ++v) hO[k * nv + v] = O[v * K + k];
+  }
+  D2& D = h->D;
+  CK2(cudaStreamSynchronize(h->stream));
+  CK2(cudaMemcpy(D.T, T, sizeof(double) * nc, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(D.U, hU.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(D.E, hE.data(), sizeof(double) * K * nc, cudaMemcpyHostToDevice));
+  CK2(cudaMemcpy(D.O, hO.data(), sizeof(double) * K * nv, cudaMemcpyHostToDevice));
+  CK2(cudaMemset(D.status, 0, sizeof(int)));
+  h->host_flags = 0;
+  h->state_set = true;
+  return GRTE_OK;
+}
+
+static grte_status status2(grte2d_t h) {
+  int s = 0;
+  CK2(cudaStreamSynchronize(h->stream));
+  CK2(cudaMemcpy(&s, h->D.status, sizeof(int), cudaMemcpyDeviceToHost));
+  s |= h->host_flags;
+  h->stats.status_flags = s;
+  for (int code : {GRTE_ENAN, GRTE_ENONCONV, GRTE_ENEGATIVE, GRTE_ETIMEOUT})
+    if (s & (1 << code)) return fail2(h, (grte_status)code, "device reported status " + std::to_string(code));
+  return GRTE_OK;
+}
+
+grte_status grte2d_step(grte2d_t h, int64_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (!h->state_set) return fail2(h, GRTE_ESTATE, "state not set");
+  if (n < 0) return fail2(h, GRTE_EINVAL, "n < 0");
+  h->stats.krylov_iters = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    grte_status s = step2(h);
+    if (s != GRTE_OK) return s;
+    h->stats.steps += 1;
+  }
+  return status2(h);
+}
+
+static grte_status get2(grte2d_t h, const double* src, int64_t count, double* out, size_t len) {
+  if (!out || len != (size_t)count) return fail2(h, GRTE_EINVAL, "bad output length");
+  CK2(cudaStreamSynchronize(h->stream));
+  CK2(cudaMemcpy(out, src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+  return status2(h);
+}
+
+grte_status grte2d_get_T(grte2d_t h, double* T, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  return get2(h, h->D.T, h->g.nc, T, len);
+}
+
+grte_status grte2d_get_E(grte2d_t h, double* E, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  const int64_t K = h->g.K, nc = h->g.nc;
+  if (!E || len != (size_t)(K * nc)) return fail2(h, GRTE_EINVAL, "len must be nx*ny*K");
+  std::vector<double> t(K * nc);
+  grte_status s = get2(h, h->D.E, K * nc, t.data(), t.size());
+  for (int64_t k = 0; k < K; ++k)
+    for (int64_t c = 0; c < nc; ++c) E[c * K + k] = t[k * nc + c];
+  return s;
+}
+
+grte_status grte2d_get_O(grte2d_t h, double* O, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  const int64_t K = h->g.K, nv = h->g.nv;
+  if (!O || len != (size_t)(K * nv)) return fail2(h, GRTE_EINVAL, "len must be (nx+1)*(ny+1)*K");
+  std::vector<double> t(K * nv);
+  grte_status s = get2(h, h->D.O, K * nv, t.data(), t.size());
+  for (int64_t k = 0; k < K; ++k)
+    for (int64_t v = 0; v < nv; ++v) O[v * K + k] = t[k * nv + v];
+  return s;
+}
+
+grte_status grte2d_get_stage(grte2d_t h, int which, double* out, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  const double* src = which == 0 ? h->D.Us : which == 1 ? h->D.Fdiv : which == 2 ? h->D.rho_s
+                    : which == 3 ? h->D.newton_its : nullptr;
+  if (!src) return fail2(h, GRTE_EINVAL, "which must be 0..3");
+  return get2(h, src, h->g.nc, out, len);
+}
+
+grte_status grte2d_get_quadrature(grte2d_t h, double* mu, double* eta, double* w, size_t K) {
+  if (!h) return GRTE_EINVAL;
+  if (!mu || !eta || !w || K != h->hmu.size()) return fail2(h, GRTE_EINVAL, "K must equal the pair count");
+  std::copy(h->hmu.begin(), h->hmu.end(), mu);
+  std::copy(h->heta.begin(), h->heta.end(), eta);
+  std::copy(h->hw.begin(), h->hw.end(), w);
+  return GRTE_OK;
+}
+
+grte_status grte2d_get_energy(grte2d_t h, double* e) {
+  if (!h) return GRTE_EINVAL;
+  if (!e) return fail2(h, GRTE_EINVAL, "e is NULL");
+  k2_energy<<<kRedBlocks, kThreads, 0, h->stream>>>(h->D, h->part);
+  k2_reduce<<<1, kThreads, 0, h->stream>>>(h->part, kRedBlocks, h->dots);
+  CK2(cudaGetLastError());
+  CK2(cudaMemcpyAsync(e, h->dots, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK2(cudaStreamSynchronize(h->stream));
+  return GRTE_OK;
+}
+
+grte_status grte2d_stats(grte2d_t h, grte_stats_t* st) {
+  if (!h || !st) return GRTE_EINVAL;
+  std::vector<double> its(h->g.nc);
+  CK2(cudaStreamSynchronize(h->stream));
+  CK2(cudaMemcpy(its.data(), h->D.newton_its, sizeof(double) * h->g.nc, cudaMemcpyDeviceToHost));
+  double mx = 0.0, sum = 0.0;
+  for (double v : its) { mx = std::max(mx, v); sum += v; }
+  h->stats.newton_iters_max = (int64_t)mx;
+  h->stats.newton_iters_mean = sum / (double)h->g.nc;
+  grte_status s = status2(h);
+  *st = h->stats;
+  return s;
+}
+
+}  // extern "C"

@@ -16,7 +16,7 @@ GRTE_OK = 0
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONCONV", 5: "ENEGATIVE",
                 6: "ENAN", 7: "ETIMEOUT", 8: "ESTATE"}
 SIGMA_CONST, SIGMA_T3 = 0, 1
-BC_INFLOW, BC_REFLECT = 0, 1
+BC_INFLOW, BC_REFLECT, BC_PERIODIC = 0, 1, 2
 FP64, MIXED = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -27,6 +27,15 @@ class Instance1D(ctypes.Structure):
                 ("sigma", _dp), ("sigma_kind", ctypes.c_int), ("bc", ctypes.c_int),
                 ("bL", _dp), ("bR", _dp), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
+                ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class Instance2D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("n_pair", ctypes.c_int), ("mu", _dp),
+                ("eta", _dp), ("w", _dp), ("sigma", _dp), ("sigma_kind", ctypes.c_int), ("bc_x", ctypes.c_int),
+                ("bc_y", ctypes.c_int), ("b_x0", ctypes.c_double), ("b_x1", ctypes.c_double),
+                ("b_y0", ctypes.c_double), ("b_y1", ctypes.c_double), ("lx", ctypes.c_double),
+                ("ly", ctypes.c_double), ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
                 ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
@@ -51,7 +60,9 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_step1d_noalloc", "grte_mlp_create", "grte_mlp_destroy", "grte_mlp_last_error",
             "grte_mlp_set_norm", "grte_mlp_get_params", "grte_mlp_set_params", "grte_mlp_forward",
             "grte_mlp_grad", "grte_mlp_train", "grte_set_guess", "grte_set_sample_logging",
-            "grte_get_newton_samples", "grte_set_newton_start", "grte_get_tuning"]
+            "grte_get_newton_samples", "grte_set_newton_start", "grte_get_tuning", "grte2d_create",
+            "grte2d_set_state", "grte2d_step", "grte2d_get_T", "grte2d_get_E", "grte2d_get_O", "grte2d_get_stage",
+            "grte2d_get_quadrature", "grte2d_get_energy", "grte2d_stats", "grte2d_last_error", "grte2d_destroy"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -103,6 +114,19 @@ def load_library(path=LIB_PATH):
     lib.grte_get_newton_samples.argtypes = [ctypes.c_void_p, ctypes.c_int, _fp, _fp, ctypes.c_size_t]
     lib.grte_step1d_noalloc.argtypes = [ctypes.POINTER(Instance1D), ctypes.POINTER(Options), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    lib.grte2d_create.argtypes = [ctypes.POINTER(Instance2D), ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]
+    lib.grte2d_set_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    lib.grte2d_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    for name in ("grte2d_get_T", "grte2d_get_E", "grte2d_get_O"):
+        getattr(lib, name).argtypes = [ctypes.c_void_p, _dp, ctypes.c_size_t]
+    lib.grte2d_get_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte2d_get_quadrature.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_size_t]
+    lib.grte2d_get_energy.argtypes = [ctypes.c_void_p, _dp]
+    lib.grte2d_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
+    lib.grte2d_last_error.argtypes = [ctypes.c_void_p]
+    lib.grte2d_last_error.restype = ctypes.c_char_p
+    lib.grte2d_destroy.argtypes = [ctypes.c_void_p]
+    lib.grte2d_destroy.restype = None
     return lib
 
 
@@ -375,4 +399,98 @@ class Grte:
     def stats(self, allow=()):
         s = Stats()
         self._check(lib().grte_stats(self.h, ctypes.byref(s)), allow)
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Grte2D:
+    """One 2D instance (grte2d_create): cells nx x ny ([j][i] row-major), vertices
+    (nx+1) x (ny+1), K direction pairs (the built-in S8 set when mu is None)."""
+
+    def __init__(self, nx, ny, sigma, dt, eps, kind=SIGMA_T3, bc_x=BC_INFLOW, bc_y=BC_INFLOW, b_x0=0.0, b_x1=0.0,
+                 b_y0=0.0, b_y1=0.0, mu=None, eta=None, w=None, lx=1.0, ly=1.0, a=1.0, c=1.0, Cv=1.0,
+                 krylov_rtol=1e-13, krylov_restart=30, krylov_maxcycles=30, newton_maxit=60, stream=None):
+        L = lib()
+        sig = _f64(np.broadcast_to(np.asarray(sigma, dtype=np.float64).ravel(), (nx * ny,)))
+        mu, eta, w = _f64(mu), _f64(eta), _f64(w)
+        self._keep = [sig, mu, eta, w]
+        K = 0 if mu is None else mu.size
+        inst = Instance2D(nx, ny, K, _ptr(mu), _ptr(eta), _ptr(w), _ptr(sig), kind, bc_x, bc_y, b_x0, b_x1, b_y0,
+                          b_y1, lx, ly, dt, a, c, Cv, eps)
+        opt = Options()
+        L.grte_default_options(ctypes.byref(opt))
+        opt.krylov_rtol = krylov_rtol
+        opt.krylov_restart = krylov_restart
+        opt.krylov_maxcycles = krylov_maxcycles
+        opt.newton_maxit = newton_maxit
+        opt.stream = stream
+        h = ctypes.c_void_p()
+        st = L.grte2d_create(ctypes.byref(inst), ctypes.byref(opt), ctypes.byref(h))
+        self.h = h
+        if st != GRTE_OK:
+            msg = L.grte2d_last_error(h).decode() if h.value else "create failed"
+            L.grte2d_destroy(h)
+            self.h = None
+            raise GrteError(st, msg)
+        self.nx, self.ny = nx, ny
+        self.nc, self.nv = nx * ny, (nx + 1) * (ny + 1)
+        self.K = K if K else 20
+
+    def _check(self, st, allow=()):
+        if st != GRTE_OK and st not in allow:
+            raise GrteError(st, lib().grte2d_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if self.h is not None:
+            lib().grte2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, T, E=None, O=None):
+        T = _f64(np.ravel(T))
+        E = None if E is None else _f64(E)
+        O = None if O is None else _f64(O)
+        return self._check(lib().grte2d_set_state(self.h, _ptr(T), _ptr(E), _ptr(O)))
+
+    def step(self, n=1, allow=()):
+        return self._check(lib().grte2d_step(self.h, n), allow)
+
+    def T(self, allow=()):
+        out = np.empty(self.nc)
+        self._check(lib().grte2d_get_T(self.h, _ptr(out), out.size), allow)
+        return out
+
+    def E(self, allow=()):
+        out = np.empty((self.nc, self.K))
+        self._check(lib().grte2d_get_E(self.h, _ptr(out), out.size), allow)
+        return out
+
+    def O(self, allow=()):
+        out = np.empty((self.nv, self.K))
+        self._check(lib().grte2d_get_O(self.h, _ptr(out), out.size), allow)
+        return out
+
+    def stage(self, which, allow=()):
+        out = np.empty(self.nc)
+        self._check(lib().grte2d_get_stage(self.h, which, _ptr(out), out.size), allow)
+        return out
+
+    def quadrature(self):
+        mu, eta, w = np.empty(self.K), np.empty(self.K), np.empty(self.K)
+        self._check(lib().grte2d_get_quadrature(self.h, _ptr(mu), _ptr(eta), _ptr(w), self.K))
+        return mu, eta, w
+
+    def energy(self):
+        e = np.zeros(1)
+        self._check(lib().grte2d_get_energy(self.h, _ptr(e)))
+        return float(e[0])
+
+    def stats(self, allow=()):
+        s = Stats()
+        self._check(lib().grte2d_stats(self.h, ctypes.byref(s)), allow)
         return {f: getattr(s, f) for f, _ in Stats._fields_}

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "grte.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(grte_[A-Za-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(grte(?:2d)?_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -43,3 +43,5 @@ def test_null_handle_calls_are_rejected(libpath):
     assert L.grte_step(None, 1) == 1          # EINVAL, no CUDA call made
     assert L.grte_sync(None) == 1
     L.grte_destroy(None)                       # no-op
+    assert L.grte2d_step(None, 1) == 1
+    L.grte2d_destroy(None)
