@@ -38,6 +38,26 @@ HOM_FLOPS_PER_ELEM = 31
 # factor values read (1/den, a, c-hat, c-check, a-check) and the flux contribution
 # written; the line's unknowns stay in shared memory.
 LINE_BYTES_PER_ELEM_F32 = 5 * 4 + 4
+# Bytes a Krylov-kernel launch (k_gmres, one cluster of 8 CTAs per instance) must move
+# per cell: the e/o flux parts of all M angles of the pass before it (bulk type) and
+# four double per-cell vectors (direction or iterate in, result out, two basis reads).
+GMRES_BYTES_PER_CELL = lambda M, es: M * es + 4 * 8
+# DRAM bytes per k_gmres<ARNOLDI> launch measured by ncu --set full (mean of two
+# launches, cold cache) on the 1D slab workload in mixed precision
+GMRES_TRAFFIC_SLAB6_MIXED = 13.19e6
+
+
+def job_throughput(updates_per_step, steps, t_ms, world, dist=None, device="cuda"):
+    """Whole-job throughput of weak-scaled replicas: every rank advanced its own copy of
+    the workload by `steps` steps in t_ms (its own CUDA-event time); the job's time is
+    the maximum over ranks and its work the updates of all ranks.  Returns (updates/s,
+    max time in ms)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return updates_per_step * steps * world / (t_ms * 1e-3), t_ms
 
 
 def workload_instances(name):
@@ -168,7 +188,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256"])
+    ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256", "checker2d"])
+    ap.add_argument("--n2d", type=int, default=128, help="cells per axis of the checker2d workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -178,6 +199,19 @@ def main():
                     help="also time the same instances advanced one handle at a time")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "checker2d":
+        if args.impl == "reference":
+            if int(os.environ.get("RANK", "0")) == 0:
+                cb = cpu_baseline_2d()
+                print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+                                  "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                                  "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                                  "dtype": "f64", "data": "synthetic",
+                                  "config": {"workload": "2d_checkerboard_%dx%d_s8" % (args.n2d, args.n2d)},
+                                  "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT,
+                                                              "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            return
+        return run_2d(args)
     runs, cfg = workload_instances(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg)
@@ -244,12 +278,7 @@ def main():
         h.step(1)
     prof = h.profile_end()
     torch.cuda.synchronize()
-    if dist is not None:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    total_updates = updates_per_step * args.steps * world
-    value = total_updates / (t_ms * 1e-3)
+    value, t_ms = job_throughput(updates_per_step, args.steps, t_ms, world, dist, "cuda")
 
     # end to end through the public API with host buffers: state in (H2D), one step,
     # temperature out (D2H), timed on the host clock with the stream synchronised
@@ -358,6 +387,16 @@ def main():
                 "frac": achieved / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n,
                 "bytes_per_elem": LINE_BYTES_PER_ELEM_F32}
+    elif dom_name == "gmres":
+        es = 8 if prec == G.FP64 else 4
+        M = runs[0].n_dir // 2
+        byts = sum(r.nx for r in runs) * GMRES_BYTES_PER_CELL(M, es)
+        achieved = byts / avg_s / 1e9
+        traffic = GMRES_TRAFFIC_SLAB6_MIXED if (args.workload == "slab6" and prec == G.MIXED) else None
+        roof = {"kernel": "k_gmres (all modes; Arnoldi step dominant)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": traffic,
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n, "bytes_per_cell": GMRES_BYTES_PER_CELL(M, es)}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
@@ -396,6 +435,112 @@ def main():
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def checker2d_inputs(n, blocks=8):
+    """2D checkerboard slab: sigma_0 = 1 on the 'black' and 100 on the 'white' blocks of a
+    blocks x blocks board (block (0, 0) black), times 1/T^3; T_in = 1e-2; eps = 1e-3;
+    inflow a c 1^4 on x = 0, vacuum on the other walls; dt = 0.5 dx; S8 (20 pairs)."""
+    i = np.arange(n) // max(n // blocks, 1)
+    sig = np.where(((i[None, :] + i[:, None]) % 2) == 0, 1.0, 100.0)
+    return sig, np.full(n * n, 1e-2), 0.5 / n, 1e-3
+
+
+def cpu_baseline_2d(n=16, nsteps=1):
+    """The 2D oracle as it stands, one thread, on the same geometry at n x n."""
+    code = f"""
+import os, sys, time, json
+os.environ["OMP_NUM_THREADS"] = "1"; os.environ["OPENBLAS_NUM_THREADS"] = "1"
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import bench
+from oracle import grte2d as o2
+from oracle.quadrature import s8_pairs_2d
+sig, T0, dt, eps = bench.checker2d_inputs({n})
+mu, eta, w = s8_pairs_2d()
+P = o2.Problem2D(Nx={n}, Ny={n}, mu=mu, eta=eta, w=w, sig=sig, eps=eps, dt=dt, kind="t3", bx0=1.0)
+S = o2.equilibrium_state(P, T0)
+t = time.perf_counter()
+for _ in range({nsteps}):
+    S = o2.step(P, S)
+dt_ = time.perf_counter() - t
+print(json.dumps({{"updates": {n} * {n} * 40 * {nsteps}, "seconds": dt_}}))
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d step(s) of the same geometry at %dx%d (sparse LU), %.1f s, 1 thread" % (nsteps, n, n, d["seconds"])}
+
+
+def run_2d(args):
+    """The 2D path (grte2d_*) on the checkerboard workload at n2d x n2d."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    from paper_1811_05579_gb300 import grte as G
+    n = args.n2d
+    sig, T0, dt, eps = checker2d_inputs(n)
+    stream = torch.cuda.current_stream()
+    h = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream)
+    h.set_state(T0)
+    allow = (5,)        # cells reaching R <= 0 at this dt (see the workload's readings)
+    for _ in range(args.warmup):
+        h.step(1, allow=allow)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_ms, its = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.step(1, allow=allow)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        its += h.stats(allow=allow)["krylov_iters"]
+    clk = clocks.stop()
+    upd = n * n * 40
+    value, t_ms = job_throughput(upd, args.steps, t_ms, world, None)
+    T, E, O = h.T(allow), h.E(allow), h.O(allow)
+    ke = min(args.steps, 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        h.set_state(T, E, O)
+        h.step(1, allow=allow)
+        h.T(allow)
+    e2e = upd * ke / (time.perf_counter() - t0)
+    hbm_peak = 6800.0
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    step_s = t_ms * 1e-3 / args.steps
+    ach = upd * 24 / step_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
+            "config": {"workload": "2d_checkerboard_%dx%d_s8" % (n, n), "n": n, "pairs": 20, "eps": eps,
+                       "sigma0": [1, 100], "blocks": 8, "dt": "0.5 dx", "T_in": 1e-2,
+                       "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},
+            "gpu_launches": None,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(T.nbytes + E.nbytes + O.nbytes),
+                    "d2h_bytes_per_step": int(T.nbytes)},
+            "roofline": {"kernel": "2D step (all kernels)", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                         "note": "24 B per cell-angle update over the step time"},
+            "krylov_iters_per_step": its / args.steps, "status_flags": h.stats(allow=allow)["status_flags"],
+            "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_2d()
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
 
 
 if __name__ == "__main__":

@@ -271,8 +271,9 @@ typedef struct {
 
 /* Create a 2D handle (inputs copied; opt may be NULL: precision must be GRTE_FP64,
  * krylov_rtol (root mean square over cells of the preconditioned residual relative to
- * each cell's own magnitude, default 1e-13), krylov_restart (up to 64; 30 if the 1D
- * default 10 is given),
+ * each cell's own magnitude, default 1e-13; a restart cycle that stalls below 1e-9, the
+ * rounding floor of the residual, is accepted too), krylov_restart (up to 64; 30 if
+ * the 1D default 10 is given),
  * krylov_maxcycles and newton_maxit apply).  The state is unset until
  * grte2d_set_state.  Errors: EINVAL, ENOMEM, ECUDA. */
 grte_status grte2d_create(const grte_instance2d* inst, const grte_options* opt, grte2d_t* out);

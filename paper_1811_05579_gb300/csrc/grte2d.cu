@@ -559,6 +559,12 @@ __global__ void k2_reduce(const double* __restrict__ part, int nb, double* __res
   }
 }
 
+// hcol[i] (+)= dots[i], i < n (first pass: assign)
+__global__ void k2_hacc(double* __restrict__ hcol, const double* __restrict__ dots, int n, int assign) {
+  const int i = threadIdx.x;
+  if (i < n) hcol[i] = assign ? dots[i] : hcol[i] + dots[i];
+}
+
 // w -= sum_i coef[i] V_i
 __global__ void k2_maxpy(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ coef,
                          int nvec, int64_t n) {
@@ -693,7 +699,7 @@ struct grte2d_ctx {
   int m = 30;
   double *V = nullptr, *phi = nullptr, *GU = nullptr, *Es = nullptr;
   double *b = nullptr, *x = nullptr, *Kr = nullptr, *Kt = nullptr, *Kbasis = nullptr;
-  double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr;
+  double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr, *hcol = nullptr;
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
 };
 
@@ -760,7 +766,7 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
   const unsigned gc = grid_of(D.g.nc);
   const int m = h->m;
   double* V = h->Kbasis;
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), yv(m), dd(m + 2);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), yv(m);
   const unsigned vb = kRedBlocks;
   const double thr = h->opt.krylov_rtol * std::sqrt((double)D.g.nc);
   grte_status s = GRTE_OK;
@@ -782,11 +788,19 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
     *beta = std::sqrt(b2);
     return r;
   };
+  // a restart cycle that did not reduce the residual 4x while it is below 1e-9 (RMS per
+  // cell) has reached the rounding floor of the residual evaluation (in cold, very
+  // opaque cells the rows are sums of terms far larger than the residual)
+  const double stall = 1e-9 * std::sqrt((double)D.g.nc);
+  double prev = INFINITY;
   for (int cycle = 0; cycle <= h->opt.krylov_maxcycles; ++cycle) {
     double beta = 0.0;
     if ((s = residual(&beta)) != GRTE_OK) return s;
     if (!std::isfinite(beta)) return fail2(h, GRTE_ENAN, "GMRES: non-finite residual");
-    if (beta <= thr || cycle == h->opt.krylov_maxcycles) {
+    const bool floor_reached = beta <= stall && beta >= 0.25 * prev;
+    prev = beta;
+    if (beta <= thr || floor_reached || cycle == h->opt.krylov_maxcycles) {
+      if (floor_reached) beta = 0.0;
       k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);  // y -> x
       if (!(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
       return GRTE_OK;
@@ -800,18 +814,21 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
       double* w = V + (int64_t)(j + 1) * n;
       apply_M(h, pred, vj, h->Kr);
       apply_P(h, pred, h->Kr, w);
-      // classical Gram-Schmidt, twice
+      // classical Gram-Schmidt, twice; the coefficients stay on the device (dots ->
+      // maxpy), the Hessenberg column is accumulated there and read once per iteration
       std::vector<double> hc(j + 2, 0.0);
       for (int pass = 0; pass < 2; ++pass) {
-        if ((s = mdot(h, w, V, j + 1, n, dd.data())) != GRTE_OK) return s;
-        CK2(cudaMemcpyAsync(h->coef, dd.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+        k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, V, j + 1, n, h->part);
+        k2_reduce<<<j + 1, kThreads, 0, st>>>(h->part, kRedBlocks, h->coef);
         k2_maxpy<<<vb, kThreads, 0, st>>>(w, V, h->coef, j + 1, n);
-        CK2(cudaStreamSynchronize(st));   // dd is reused by the next pass
-        for (int i = 0; i <= j; ++i) hc[i] += dd[i];
+        k2_hacc<<<1, kMaxRestart2 + 1, 0, st>>>(h->hcol, h->coef, j + 1, pass == 0);
       }
-      double hn2 = 0.0;
-      if ((s = mdot(h, w, w, 1, n, &hn2)) != GRTE_OK) return s;
-      const double hn = std::sqrt(hn2);
+      k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, w, 1, n, h->part);
+      k2_reduce<<<1, kThreads, 0, st>>>(h->part, kRedBlocks, h->hcol + j + 1);
+      CK2(cudaGetLastError());
+      CK2(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
+      CK2(cudaStreamSynchronize(st));
+      const double hn = std::sqrt(hc[j + 1]);
       hc[j + 1] = hn;
       ++iters;
       for (int i = 0; i < j; ++i) {
@@ -976,7 +993,8 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
             alloc2(h, &h->Es, K * nc) && alloc2(h, &h->b, nz) && alloc2(h, &h->x, nz) && alloc2(h, &h->Kr, nz) &&
             alloc2(h, &h->Kt, nz) && alloc2(h, &h->Kbasis, (int64_t)(h->m + 1) * nz) &&
             alloc2(h, &h->part, (int64_t)kRedBlocks * (kMaxRestart2 + 1)) && alloc2(h, &h->dots, kMaxRestart2 + 1) &&
-            alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc);
+            alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc) &&
+            alloc2(h, &h->hcol, kMaxRestart2 + 2);
   if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
   D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
   CK2(cudaMemcpy(h->dmu, h->hmu.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
