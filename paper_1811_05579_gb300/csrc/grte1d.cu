@@ -250,6 +250,32 @@ __global__ void k_rho(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_s
 // X: type of the input vector (double for the iterate, the bulk type for a Krylov
 // direction).
 template <typename X>
+__device__ __forceinline__ void cellpart_cell(const Dev& D, const Inst& I, int64_t gid, int64_t j,
+                                              const X* __restrict__ x, int full) {
+  const int64_t N = I.N;
+  const double xj = x[j], xl = j > 0 ? (double)x[j - 1] : 0.0, xr = j < N - 1 ? (double)x[j + 1] : 0.0;
+  double p1 = -D.cf.alpha[gid] * xj;
+  if (full) p1 += (D.cf.sac[gid] + D.cf.kcd[gid] * I.a * I.c) * D.U[gid];
+  const double p2 = D.cf.gl[gid] * (xj - xl) + D.cf.gu[gid] * (xj - xr);
+  const double p3 = D.cf.gb[gid] * xj;
+  double fr = I.wv2 * (D.cf.fR[gid] * (xj - xr) + D.cf.fL[gid] * (xj - xl)) + I.wv * D.cf.gbx[gid] * xj;
+  if (full && I.bc == GRTE_BC_INFLOW) {
+    if (j == 0) fr -= I.two_eps * I.bLflux;
+    if (j == N - 1) fr -= I.two_eps * I.bRflux;
+  }
+  D.P1[gid] = p1;
+  D.P2[gid] = p2;
+  D.P3[gid] = p3;
+  D.Frho[gid] = fr;
+  if (D.mixed) {
+    D.fc.P1[gid] = (float)p1;
+    D.fc.P2[gid] = (float)p2;
+    D.fc.P3[gid] = (float)p3;
+    D.fc.Frho[gid] = (float)fr;
+  }
+}
+
+template <typename X>
 __global__ void k_cellpart_pred(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start, int64_t ncell,
                                 const X* __restrict__ xvec, int full) {
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -257,26 +283,7 @@ __global__ void k_cellpart_pred(Dev D, int n_inst, const int64_t* __restrict__ c
   const int ii = inst_of(cell_inst_start, n_inst, gid);
   const Inst I = D.inst[ii];
   if (!full && !D.gactive[ii]) return;
-  const int64_t j = gid - I.cell_off, N = I.N;
-  const X* x = xvec + I.cell_off;
-  const double xj = x[j], xl = j > 0 ? (double)x[j - 1] : 0.0, xr = j < N - 1 ? (double)x[j + 1] : 0.0;
-  double p1 = -D.cf.alpha[gid] * xj;
-  if (full) p1 += (D.cf.sac[gid] + D.cf.kcd[gid] * I.a * I.c) * D.U[gid];
-  D.P1[gid] = p1;
-  D.P2[gid] = D.cf.gl[gid] * (xj - xl) + D.cf.gu[gid] * (xj - xr);
-  D.P3[gid] = D.cf.gb[gid] * xj;
-  double fr = I.wv2 * (D.cf.fR[gid] * (xj - xr) + D.cf.fL[gid] * (xj - xl)) + I.wv * D.cf.gbx[gid] * xj;
-  if (full && I.bc == GRTE_BC_INFLOW) {
-    if (j == 0) fr -= I.two_eps * I.bLflux;
-    if (j == N - 1) fr -= I.two_eps * I.bRflux;
-  }
-  D.Frho[gid] = fr;
-  if (D.mixed) {
-    D.fc.P1[gid] = (float)p1;
-    D.fc.P2[gid] = (float)D.P2[gid];
-    D.fc.P3[gid] = (float)D.P3[gid];
-    D.fc.Frho[gid] = (float)fr;
-  }
+  cellpart_cell<X>(D, I, gid, gid - I.cell_off, xvec + I.cell_off, full);
 }
 
 // Per-cell parts of correction substep 2 at T^{n+1} (U^n still in D.U):
@@ -750,6 +757,8 @@ enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
 template <int MODE, typename R, bool XS>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmres(Dev D, int jcol) {
   using K = typename KryT<R>::type;   // arithmetic of the Krylov vectors
+  // FP64 mode: the per-cell parts of the next pass are formed here (no separate launch)
+  constexpr bool FUSED_PARTS = sizeof(R) == 8;
   __shared__ GmresSmem sm;
   extern __shared__ __align__(16) unsigned char gdsm[];   // the slice's unknowns (XS)
   K* wsm = (K*)gdsm;
@@ -775,6 +784,10 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
 
   if (MODE == G_RESTART_FIRST || MODE == G_RESTART) {
     if (MODE == G_RESTART && D.gdone[ii]) return;        // uniform over the cluster
+    // the previous restart's values, read before any CTA of the cluster can overwrite
+    // them (rank 0 stores the new ones below): every CTA takes the same decision
+    const double beta_prev = D.gbeta[ii];
+    const int cycles_prev = D.gcycles[ii];
     // r = -R(x) from the FULL pass that just ran at x
     double* r = zd;
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) {
@@ -821,7 +834,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     // did not reduce it by 4x while it is below 1e-9 has reached that floor.
     bool conv = !(rinf > D.rtol);   // also true for rinf == 0
     if (MODE == G_RESTART && !conv && rinf <= D.stall &&
-        (rinf >= 0.25 * D.gbeta[ii] || (D.mixed && D.gcycles[ii] >= 1))) conv = true;
+        (rinf >= 0.25 * beta_prev || (D.mixed && cycles_prev >= 1))) conv = true;
     if (rank == 0 && threadIdx.x == 0) {
       if (MODE == G_RESTART) D.gcycles[ii] += 1;
       D.gbeta[ii] = rinf;
@@ -844,6 +857,12 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) v0[j] *= inv;
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
+    // per-cell parts of the first direction pass (V_0 of the neighbouring slices is
+    // complete after the cluster barrier)
+    // (FP64 mode only: in the mixed mode the per-cell kernel runs on all SMs instead,
+    // since this kernel's FP64 rate on one cluster per instance would be the limit)
+    if (FUSED_PARTS && !conv)
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) cellpart_cell<K>(D, I, co + j, j, v0, 0);
     return;
   }
 
@@ -861,6 +880,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
     // classical Gram-Schmidt, twice (CGS2): two cluster reductions instead of j+1
     __shared__ double dots[kMaxRestart + 2];
     __shared__ double hc[kMaxRestart + 2];   // Hessenberg column (thread 0 finishes it)
+    __shared__ int cont_s;                   // 1: another Arnoldi step follows
     if (threadIdx.x <= jcol + 1) hc[threadIdx.x] = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
       // all jcol+1 dot products in one sweep and one CTA reduction
@@ -913,6 +933,11 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       hc[jcol] = rr;
       const double gj = g[jcol];
       const double gnext = -s0g * gj;
+      // GMRES's own (2-norm) estimate; the per-cell test runs on the true residual.
+      // Every CTA takes the same decision (its inputs are cluster-wide values).
+      const bool est = fabs(gnext) <= 0.05 * D.rtol * D.gxn[ii];
+      const bool stop = est || nrm == 0.0 || jcol + 1 >= m;
+      cont_s = stop ? 0 : 1;
       if (rank == 0) {
         cs[jcol] = c0g;
         sn[jcol] = s0g;
@@ -921,15 +946,16 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
         for (int i = 0; i <= jcol; ++i) H[i * kMaxRestart + jcol] = hc[i];
         D.gk[ii] = jcol + 1;
         D.gits[ii] += 1;
-        // GMRES's own (2-norm) estimate; the per-cell test runs on the true residual
-        const bool est = fabs(gnext) <= 0.05 * D.rtol * D.gxn[ii];
         if (est) D.gestconv[ii] = 1;
-        if (est || nrm == 0.0 || jcol + 1 >= m) D.gactive[ii] = 0;
+        if (stop) D.gactive[ii] = 0;
       }
     }
     const K inv = K(nrm > 0.0 ? 1.0 / nrm : 0.0);
     for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) wv[j] *= inv;
     cl.sync();
+    // per-cell parts of the next direction pass (V_{j+1} complete after the barrier)
+    if (FUSED_PARTS && cont_s)
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) cellpart_cell<K>(D, I, co + j, j, wv, 0);
     return;
   }
 
@@ -948,6 +974,11 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       double t = x[j];
       for (int i = 0; i < kk; ++i) t += sm.y[i] * (double)Vi(i)[j];
       x[j] = t;
+    }
+    if (FUSED_PARTS) {
+      cl.sync();
+      // per-cell parts of the data pass at the updated iterate
+      for (int64_t j = c0 + threadIdx.x; j < c0 + n; j += blockDim.x) cellpart_cell<double>(D, I, co + j, j, x, 1);
     }
     return;
   }
@@ -1784,7 +1815,9 @@ static void step_iteration(grte_t h, int j) {
   cudaStream_t st = h->stream;
   const StepGeom G = step_geom(h);
   const K* vj = (const K*)D.gV + (int64_t)j * G.vstride;   // Krylov direction
-  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<K><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, vj, 0));
+  // per-cell parts of the pass: in FP64 k_gmres forms them, in the mixed mode this kernel
+  if (sizeof(R) == 4)
+    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<K><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, vj, 0));
   LAUNCH(GRTE_K_PRED_HOM, (pred_pass<PRED_HOM, R>(h, vj)));
   LAUNCH(GRTE_K_GMRES, (gmres_launch<G_ARNOLDI, R>(h, j)));
 }
@@ -1794,8 +1827,9 @@ static void step_tail(grte_t h) {
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const StepGeom G = step_geom(h);
-  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_UPDATE, R>(h, 0)));
-  LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.gx, 1));
+  LAUNCH(GRTE_K_GMRES, (gmres_launch<G_UPDATE, R>(h, 0)));   // FP64: also the per-cell parts at x
+  if (sizeof(R) == 4)
+    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.gx, 1));
   LAUNCH(GRTE_K_PRED_FULL, (pred_pass<PRED_FULL, R>(h, D.gx)));
   LAUNCH(GRTE_K_GMRES, (gmres_launch<G_RESTART, R>(h, 0)));
 }
@@ -2093,9 +2127,11 @@ grte_status grte_step(grte_t h, int64_t nsteps) {
     CK(cudaStreamSynchronize(h->stream));
     its += acc[0];
     cyc += acc[1];
-    // kernels run by the graph steps: the fixed ones, per cycle the tail (4) and its
-    // condition kernel, every condition kernel of the iterations, 3 per iteration run
-    h->launches += ngraph * h->graph_fixed_launches + acc[1] * 5 + acc[3] + acc[2] * 3;
+    // kernels run by the graph steps: the fixed ones, per cycle the tail (mixed 4, FP64 3)
+    // and its condition kernel, every condition kernel of the iterations, and per
+    // iteration run the direction pass and the Arnoldi step (mixed: also the per-cell parts)
+    const int64_t per_cycle = mixed ? 5 : 4, per_iter = mixed ? 3 : 2;
+    h->launches += ngraph * h->graph_fixed_launches + acc[1] * per_cycle + acc[3] + acc[2] * per_iter;
   }
   h->stats.krylov_iters = its;
   h->stats.krylov_cycles = cyc;
