@@ -34,6 +34,7 @@ struct G2 {
   int64_t nc, nv;
   double dx, dy, eps, dt, a, c, Cv;
   double bx0, bx1, by0, by1;
+  double h2x, h2y, te;   // 1/(2 dx), 1/(2 dy), 2/eps (no divisions in the stencils)
 };
 
 struct D2 {
@@ -44,6 +45,7 @@ struct D2 {
   double *dv, *odv;                           // per vertex: d and d eps^2/(c dt) (node-equation vertices)
   double *rho_n, *Us, *Fdiv, *rho_s, *newton_its, *acU;
   double *wsc, *iwsc;   // per-cell scale of the Krylov unknowns (k2_weights) and its inverse
+  double *gd, *gdi, *pdi;   // [k][cell] diagonal g_k of G_k, 1/(A + g_k); [cell] inverse rho pivot
   int* status;
   int newton_maxit;
 };
@@ -149,8 +151,7 @@ __device__ double O_node(const D2& D, const UField& u, int k, int i, int j) {
     const int c00 = cell_of(g, i - 1, j - 1), c10 = cell_of(g, i, j - 1), c01 = cell_of(g, i - 1, j),
               c11 = cell_of(g, i, j);
     const double u00 = u.at(k, c00), u10 = u.at(k, c10), u01 = u.at(k, c01), u11 = u.at(k, c11);
-    const double grad = D.mu[k] * ((u10 + u11) - (u00 + u01)) / (2.0 * g.dx) +
-                        D.eta[k] * ((u01 + u11) - (u00 + u10)) / (2.0 * g.dy);
+    const double grad = D.mu[k] * ((u10 + u11) - (u00 + u01)) * g.h2x + D.eta[k] * ((u01 + u11) - (u00 + u10)) * g.h2y;
     r -= D.dv[v] * grad;
   }
   return r;
@@ -185,9 +186,9 @@ __device__ double O_wall(const D2& D, const UField& u, int k, int i, int j, int 
     int n = 0;
     if (ca >= 0) { Ew += u.at(k, ca); ++n; }
     if (cb >= 0) { Ew += u.at(k, cb); ++n; }
-    Ew /= (double)n;
+    if (n == 2) Ew *= 0.5;
   }
-  return sgn * 2.0 / g.eps * ((DATA ? b : 0.0) - Ew) - Oinner;
+  return sgn * g.te * ((DATA ? b : 0.0) - Ew) - Oinner;
 }
 
 template <bool DATA>
@@ -204,14 +205,17 @@ __device__ double O_at(const D2& D, const UField& u, int k, int i, int j) {
   return 0.5 * (O_wall<DATA>(D, u, k, i, j, 0, Oin_x) + O_wall<DATA>(D, u, k, i, j, 1, Oin_y));
 }
 
-// V[k][v] = O_k at every vertex for the field u (and the data part with DATA).
+// V[k][v] = O_k at every vertex for the field u (and the data part with DATA); one
+// thread per (pair, vertex), consecutive threads on consecutive vertices.
 template <bool DATA>
 __global__ void k2_vertex(D2 D, UField u, double* __restrict__ V) {
-  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
-  if (v >= g.nv) return;
-  const int i = (int)(v % (g.Nx + 1)), j = (int)(v / (g.Nx + 1));
-  for (int k = 0; k < g.K; ++k) V[(int64_t)k * g.nv + v] = O_at<DATA>(D, u, k, i, j);
+  if (t >= (int64_t)g.K * g.nv) return;
+  const int tt = (int)t, nv = (int)g.nv;   // K nv < 2^31 (checked at creation)
+  const int k = tt / nv, v = tt - k * nv;
+  const int j = v / (g.Nx + 1), i = v - j * (g.Nx + 1);
+  V[t] = O_at<DATA>(D, u, k, i, j);
 }
 
 enum { C_MV_PRED = 0, C_MV_CORR = 1, C_DIVK = 2, C_FDIV = 3 };
@@ -230,21 +234,21 @@ struct CellSides {
 __device__ __forceinline__ CellSides cell_sides(const D2& D, int k, int p, int q) {
   const G2& g = D.g;
   CellSides cs{-1.0, 1.0, -1.0, 1.0, 0.0, 0.0};
-  const double mu = D.mu[k], eta = D.eta[k], te = 2.0 / g.eps;
+  const double mu = D.mu[k], eta = D.eta[k], te = g.te, ix = 2.0 * g.h2x, iy = 2.0 * g.h2y;
   if (g.bcx == GRTE_BC_INFLOW) {
     if (p == 0) {
       const double s = mu > 0.0 ? 1.0 : -1.0;   // Omega_k enters at x = 0 when mu > 0
       cs.wL = 0.0;
       cs.wR = 2.0;
-      cs.ed += mu * s * te / g.dx;
-      cs.bt -= mu * s * te * g.bx0 / g.dx;
+      cs.ed += mu * s * te * ix;
+      cs.bt -= mu * s * te * g.bx0 * ix;
     }
     if (p == g.Nx - 1) {
       const double s = mu < 0.0 ? 1.0 : -1.0;
       if (p != 0) cs.wL = -2.0;
       cs.wR = 0.0;
-      cs.ed -= mu * s * te / g.dx;
-      cs.bt += mu * s * te * g.bx1 / g.dx;
+      cs.ed -= mu * s * te * ix;
+      cs.bt += mu * s * te * g.bx1 * ix;
     }
   }
   if (g.bcy == GRTE_BC_INFLOW) {
@@ -252,69 +256,90 @@ __device__ __forceinline__ CellSides cell_sides(const D2& D, int k, int p, int q
       const double s = eta > 0.0 ? 1.0 : -1.0;
       cs.wB = 0.0;
       cs.wT = 2.0;
-      cs.ed += eta * s * te / g.dy;
-      cs.bt -= eta * s * te * g.by0 / g.dy;
+      cs.ed += eta * s * te * iy;
+      cs.bt -= eta * s * te * g.by0 * iy;
     }
     if (q == g.Ny - 1) {
       const double s = eta < 0.0 ? 1.0 : -1.0;
       if (q != 0) cs.wB = -2.0;
       cs.wT = 0.0;
-      cs.ed -= eta * s * te / g.dy;
-      cs.bt += eta * s * te * g.by1 / g.dy;
+      cs.ed -= eta * s * te * iy;
+      cs.bt += eta * s * te * g.by1 * iy;
     }
   }
   return cs;
 }
 
+// Streaming derivative of O_k at cell c (cell_sides), for pair k.
+template <bool DATA>
+__device__ __forceinline__ double cell_div(const D2& D, const double* __restrict__ V, const UField& u, int k, int64_t c) {
+  const G2& g = D.g;
+  const int ci = (int)c;
+  const int q = ci / g.Nx, p = ci - q * g.Nx;
+  const int64_t v00 = (int64_t)q * (g.Nx + 1) + p, v10 = v00 + 1, v01 = v00 + g.Nx + 1, v11 = v01 + 1;
+  const double* Vk = V + (int64_t)k * g.nv;
+  const bool wall = (g.bcx == GRTE_BC_INFLOW && (p == 0 || p == g.Nx - 1)) ||
+                    (g.bcy == GRTE_BC_INFLOW && (q == 0 || q == g.Ny - 1));
+  if (!wall)
+    return D.mu[k] * ((Vk[v10] + Vk[v11]) - (Vk[v00] + Vk[v01])) * g.h2x +
+           D.eta[k] * ((Vk[v01] + Vk[v11]) - (Vk[v00] + Vk[v10])) * g.h2y;
+  const CellSides cs = cell_sides(D, k, p, q);
+  double div = D.mu[k] * g.h2x * (cs.wL * (Vk[v00] + Vk[v01]) + cs.wR * (Vk[v10] + Vk[v11])) +
+               D.eta[k] * g.h2y * (cs.wB * (Vk[v00] + Vk[v10]) + cs.wT * (Vk[v01] + Vk[v11]));
+  if (u.any()) div += cs.ed * u.at(k, (int)c);
+  if (DATA) div += cs.bt;
+  return div;
+}
+
 // Cell pass over the vertex values V (computed from the same field u, with the data
-// part when DATA):
-//   C_MV_PRED: y_k = A z_k + alpha z_rho + kappa S_k,  y_rho = alpha z_rho + sum_k w_k kappa S_k
+// part when DATA), one thread per (pair, cell):
+//   C_MV_PRED: y_k = A z_k + alpha z_rho + kappa S_k,  t_k = kappa S_k (for the rho row)
 //   C_MV_CORR: y_k = A z_k + kappa S_k
 //   C_DIVK:    y_k = kappa S_k
-//   C_FDIV:    y   = sum_k w_k S_k
+//   C_FDIV:    t_k = S_k
 // S_k the streaming derivative of O_k at the cell (cell_sides).  z is read scaled by
-// zs[c] when zs is given (the Krylov unknowns are cell-scaled).
+// zs[c] when zs is given (the Krylov unknowns are cell-scaled).  The sums over pairs
+// (rho row, C_FDIV) are k2_cellsum.
 template <int MODE, bool DATA>
 __global__ void k2_cell(D2 D, const double* __restrict__ V, UField u, const double* __restrict__ z,
-                        double* __restrict__ y, const double* __restrict__ zs) {
+                        double* __restrict__ y, const double* __restrict__ zs, double* __restrict__ tk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nc) return;
+  const int tt = (int)t, nc = (int)g.nc;
+  const int k = tt / nc;
+  const int64_t c = tt - k * nc;
+  const double div = cell_div<DATA>(D, V, u, k, c);
+  const double kc = D.kc[c];
+  const double f = zs ? zs[c] : 1.0;
+  if (MODE == C_MV_PRED) {
+    y[t] = D.A[c] * f * z[t] + D.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + kc * div;
+    tk[t] = kc * div;
+  } else if (MODE == C_MV_CORR) {
+    y[t] = D.A[c] * f * z[t] + kc * div;
+  } else if (MODE == C_DIVK) {
+    y[t] = kc * div;
+  } else {
+    tk[t] = div;
+  }
+}
+
+// Per-cell sums over pairs (fixed order): C_MV_PRED: y_rho = alpha z_rho + sum_k w_k t_k;
+// C_FDIV: y = sum_k w_k t_k.
+template <int MODE>
+__global__ void k2_cellsum(D2 D, const double* __restrict__ tk, const double* __restrict__ z,
+                           double* __restrict__ y, const double* __restrict__ zs) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
-  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
-  const int64_t v00 = (int64_t)q * (g.Nx + 1) + p, v10 = v00 + 1, v01 = v00 + g.Nx + 1, v11 = v01 + 1;
-  const double kc = D.kc[c];
-  const double f = zs ? zs[c] : 1.0;
-  const double zr = MODE == C_MV_PRED ? f * z[(int64_t)g.K * g.nc + c] : 0.0;
-  const bool wall = (g.bcx == GRTE_BC_INFLOW && (p == 0 || p == g.Nx - 1)) ||
-                    (g.bcy == GRTE_BC_INFLOW && (q == 0 || q == g.Ny - 1));
   double acc = 0.0;
-  for (int k = 0; k < g.K; ++k) {
-    const double* Vk = V + (int64_t)k * g.nv;
-    double div;
-    if (!wall) {
-      div = D.mu[k] * ((Vk[v10] + Vk[v11]) - (Vk[v00] + Vk[v01])) / (2.0 * g.dx) +
-            D.eta[k] * ((Vk[v01] + Vk[v11]) - (Vk[v00] + Vk[v10])) / (2.0 * g.dy);
-    } else {
-      const CellSides cs = cell_sides(D, k, p, q);
-      div = D.mu[k] / (2.0 * g.dx) * (cs.wL * (Vk[v00] + Vk[v01]) + cs.wR * (Vk[v10] + Vk[v11])) +
-            D.eta[k] / (2.0 * g.dy) * (cs.wB * (Vk[v00] + Vk[v10]) + cs.wT * (Vk[v01] + Vk[v11]));
-      if (u.any()) div += cs.ed * u.at(k, (int)c);
-      if (DATA) div += cs.bt;
-    }
-    const int64_t o = (int64_t)k * g.nc + c;
-    if (MODE == C_MV_PRED) {
-      y[o] = D.A[c] * f * z[o] + D.alpha[c] * zr + kc * div;
-      acc += D.w[k] * kc * div;
-    } else if (MODE == C_MV_CORR) {
-      y[o] = D.A[c] * f * z[o] + kc * div;
-    } else if (MODE == C_DIVK) {
-      y[o] = kc * div;
-    } else {
-      acc += D.w[k] * div;
-    }
+  for (int k = 0; k < g.K; ++k) acc += D.w[k] * tk[(int64_t)k * g.nc + c];
+  if (MODE == C_MV_PRED) {
+    const double f = zs ? zs[c] : 1.0;
+    y[(int64_t)g.K * g.nc + c] = D.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + acc;
+  } else {
+    y[c] = acc;
   }
-  if (MODE == C_MV_PRED) y[(int64_t)g.K * g.nc + c] = D.alpha[c] * zr + acc;
-  if (MODE == C_FDIV) y[c] = acc;
 }
 
 // Diagonal of G_k at cell c (for the preconditioner): the node-equation vertices of
@@ -324,7 +349,7 @@ __global__ void k2_cell(D2 D, const double* __restrict__ V, UField u, const doub
 __device__ double gdiag(const D2& D, int k, int p, int q) {
   const G2& g = D.g;
   const CellSides cs = cell_sides(D, k, p, q);
-  const double mx = D.mu[k] / (2.0 * g.dx), ey = D.eta[k] / (2.0 * g.dy);
+  const double mx = D.mu[k] * g.h2x, ey = D.eta[k] * g.h2y;
   const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
   // D* coefficient of vertex t of the cell with the side weights
   const double cst[4] = {cs.wL * mx + cs.wB * ey, cs.wR * mx + cs.wB * ey, cs.wL * mx + cs.wT * ey,
@@ -347,30 +372,49 @@ __device__ double gdiag(const D2& D, int k, int p, int q) {
 //   e_k = (r_k - (alpha + g_k) rho)/(A + g_k).
 // Correction: z_k = r_k/(A + g_k).  The result is multiplied by the cell's Krylov
 // scale w (the GMRES runs on w-scaled unknowns: D_w P^{-1} M D_w^{-1}).
+// (the diagonals g_k and the reciprocals come from k2_gdiag, once per solve)
 template <bool PRED>
 __global__ void k2_prec(D2 D, const double* __restrict__ r, double* __restrict__ z) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
-  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
-  const double A = D.A[c], al = D.alpha[c], ws = D.wsc[c];
+  const double ws = D.wsc[c];
   if (!PRED) {
-    for (int k = 0; k < g.K; ++k)
-      z[(int64_t)k * g.nc + c] = ws * r[(int64_t)k * g.nc + c] / (A + gdiag(D, k, p, q));
+    for (int k = 0; k < g.K; ++k) z[(int64_t)k * g.nc + c] = ws * r[(int64_t)k * g.nc + c] * D.gdi[(int64_t)k * g.nc + c];
     return;
   }
-  double num = r[(int64_t)g.K * g.nc + c], den = al;
-  double gk[kMaxPairs];
+  const double al = D.alpha[c];
+  double num = r[(int64_t)g.K * g.nc + c];
   for (int k = 0; k < g.K; ++k) {
-    gk[k] = gdiag(D, k, p, q);
-    const double wg = D.w[k] * gk[k];
-    num -= wg * r[(int64_t)k * g.nc + c] / (A + gk[k]);
-    den += wg * (A - al) / (A + gk[k]);
+    const int64_t o = (int64_t)k * g.nc + c;
+    num -= D.w[k] * D.gd[o] * r[o] * D.gdi[o];
   }
-  const double rho = num / den;
+  const double rho = num * D.pdi[c];
   z[(int64_t)g.K * g.nc + c] = ws * rho;
-  for (int k = 0; k < g.K; ++k)
-    z[(int64_t)k * g.nc + c] = ws * (r[(int64_t)k * g.nc + c] - (al + gk[k]) * rho) / (A + gk[k]);
+  for (int k = 0; k < g.K; ++k) {
+    const int64_t o = (int64_t)k * g.nc + c;
+    z[o] = ws * (r[o] - (al + D.gd[o]) * rho) * D.gdi[o];
+  }
+}
+
+// gd[k][c] = diagonal of G_k at cell c (for the preconditioner), at the current coefficients
+// and the reciprocals the preconditioner needs: gdi = 1/(A + g_k) and, per cell, the
+// inverse of the arrow block's rho pivot alpha + sum_k w_k g_k (A - alpha)/(A + g_k).
+__global__ void k2_gdiag(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
+  const double A = D.A[c], al = D.alpha[c];
+  double den = al;
+  for (int k = 0; k < g.K; ++k) {
+    const int64_t o = (int64_t)k * g.nc + c;
+    const double gk = gdiag(D, k, p, q), inv = 1.0 / (A + gk);
+    D.gd[o] = gk;
+    D.gdi[o] = inv;
+    den += D.w[k] * gk * (A - al) * inv;
+  }
+  D.pdi[c] = 1.0 / den;
 }
 
 // Krylov scale per cell from a magnitude field src: s = |src| + 1e-13 max|src|,
@@ -700,6 +744,7 @@ struct grte2d_ctx {
   double *V = nullptr, *phi = nullptr, *GU = nullptr, *Es = nullptr;
   double *b = nullptr, *x = nullptr, *Kr = nullptr, *Kt = nullptr, *Kbasis = nullptr;
   double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr, *hcol = nullptr;
+  double* tk = nullptr;   // [k][cell] per-pair cell values summed by k2_cellsum
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
 };
 
@@ -742,9 +787,14 @@ static void apply_M(grte2d_t h, bool pred, const double* xin, double* y) {
   D2& D = h->D;
   cudaStream_t st = h->stream;
   UField u{xin, D.g.nc, pred ? xin + (int64_t)D.g.K * D.g.nc : nullptr, D.iwsc};
-  k2_vertex<false><<<grid_of(D.g.nv), kThreads, 0, st>>>(D, u, h->V);
-  if (pred) k2_cell<C_MV_PRED, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc);
-  else k2_cell<C_MV_CORR, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc);
+  const int64_t K = D.g.K;
+  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, u, h->V);
+  if (pred) {
+    k2_cell<C_MV_PRED, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc, h->tk);
+    k2_cellsum<C_MV_PRED><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->tk, xin, y, D.iwsc);
+  } else {
+    k2_cell<C_MV_CORR, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc, h->tk);
+  }
 }
 
 static void apply_P(grte2d_t h, bool pred, const double* r, double* z) {
@@ -866,34 +916,38 @@ static grte_status step2(grte2d_t h) {
   const G2& g = D.g;
   cudaStream_t st = h->stream;
   const unsigned gc = grid_of(g.nc), gv = grid_of(g.nv);
+  const unsigned gvk = grid_of((int64_t)g.K * g.nv), gck = grid_of((int64_t)g.K * g.nc);
   const int64_t K = g.K, nc = g.nc;
   int its = 0;
   // prediction at T^n
   k2_coef<<<gc, kThreads, 0, st>>>(D);
   k2_vcoef<<<gv, kThreads, 0, st>>>(D);
   k2_rho<<<gc, kThreads, 0, st>>>(D, D.E, D.rho_n);
-  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<C_DIVK, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr);
+  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
   k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
+  k2_gdiag<<<gc, kThreads, 0, st>>>(D);
   CK2(cudaGetLastError());
   grte_status s = gmres2(h, true, (K + 1) * nc, its);
   if (s != GRTE_OK) return s;
   h->stats.krylov_iters += its;
   k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
   // O* and the flux term of the temperature equation
-  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{h->Es, nc, nullptr}, h->V);
-  k2_cell<C_FDIV, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{h->Es, nc, nullptr}, nullptr, D.Fdiv, nullptr);
+  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{h->Es, nc, nullptr}, h->V);
+  k2_cell<C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
+  k2_cellsum<C_FDIV><<<gc, kThreads, 0, st>>>(D, h->tk, nullptr, D.Fdiv, nullptr);
   k2_newton<<<gc, kThreads, 0, st>>>(D);
   // correction substep 2 at T^{n+1}
   k2_coef<<<gc, kThreads, 0, st>>>(D);
   k2_vcoef<<<gv, kThreads, 0, st>>>(D);
   k2_acU<<<gc, kThreads, 0, st>>>(D);
-  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<C_DIVK, true><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr);
-  k2_vertex<false><<<gv, kThreads, 0, st>>>(D, UField{nullptr, 0, D.acU}, h->V);
-  k2_cell<C_DIVK, false><<<gc, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr);
+  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
+  k2_vertex<false><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, D.acU}, h->V);
+  k2_cell<C_DIVK, false><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr, nullptr);
   k2_rhs_corr<<<gc, kThreads, 0, st>>>(D, h->GU, h->phi, h->b, h->x);
   k2_corrscale<<<gc, kThreads, 0, st>>>(D, h->cscale);
+  k2_gdiag<<<gc, kThreads, 0, st>>>(D);
   CK2(cudaGetLastError());
   its = 0;
   s = gmres2(h, false, K * nc, its);
@@ -901,7 +955,7 @@ static grte_status step2(grte2d_t h) {
   h->stats.krylov_iters += its;
   // projection: E = a c U + eps E_J, O from E (vertex map with the O^n data), U = T^4
   k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
-  k2_vertex<true><<<gv, kThreads, 0, st>>>(D, UField{D.E, nc, nullptr}, h->V);
+  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{D.E, nc, nullptr}, h->V);
   CK2(cudaMemcpyAsync(D.O, h->V, sizeof(double) * K * g.nv, cudaMemcpyDeviceToDevice, st));
   CK2(cudaGetLastError());
   return GRTE_OK;
@@ -934,6 +988,8 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
   if (!(h->opt.krylov_rtol > 0) || h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1)
     return fail2(h, GRTE_EINVAL, "bad solver options");
   if (p->nx < 2 || p->ny < 2 || p->nx > 32768 || p->ny > 32768) return fail2(h, GRTE_EINVAL, "nx, ny must be in [2, 32768]");
+  if ((int64_t)std::max(p->n_pair, 20) * (p->nx + 1) * (p->ny + 1) >= (int64_t)1 << 31)
+    return fail2(h, GRTE_EINVAL, "n_pair * (nx+1) * (ny+1) must be below 2^31");
   if (!p->sigma) return fail2(h, GRTE_EINVAL, "sigma is NULL");
   if (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3) return fail2(h, GRTE_EINVAL, "bad sigma_kind");
   for (int bc : {p->bc_x, p->bc_y})
@@ -970,6 +1026,9 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
   g.dy = p->ly / (double)p->ny;
   g.eps = p->eps; g.dt = p->dt; g.a = p->a; g.c = p->c; g.Cv = p->Cv;
   g.bx0 = p->b_x0; g.bx1 = p->b_x1; g.by0 = p->b_y0; g.by1 = p->b_y1;
+  g.h2x = 1.0 / (2.0 * g.dx);
+  g.h2y = 1.0 / (2.0 * g.dy);
+  g.te = 2.0 / g.eps;
   for (int64_t c = 0; c < g.nc; ++c)
     if (!(p->sigma[c] >= 0.0) || !std::isfinite(p->sigma[c])) return fail2(h, GRTE_EINVAL, "sigma must be finite and >= 0");
   if (h->opt.stream) {
@@ -988,13 +1047,13 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
             alloc2(h, &D.gam, nc) && alloc2(h, &D.dv, nv) && alloc2(h, &D.odv, nv) && alloc2(h, &D.rho_n, nc) &&
             alloc2(h, &D.Us, nc) && alloc2(h, &D.Fdiv, nc) && alloc2(h, &D.rho_s, nc) &&
             alloc2(h, &D.newton_its, nc) && alloc2(h, &D.acU, nc) && alloc2(h, &D.status, 1) &&
-            alloc2(h, &D.wsc, nc) && alloc2(h, &D.iwsc, nc) &&
+            alloc2(h, &D.wsc, nc) && alloc2(h, &D.iwsc, nc) && alloc2(h, &D.gd, K * nc) && alloc2(h, &D.gdi, K * nc) && alloc2(h, &D.pdi, nc) &&
             alloc2(h, &h->V, K * nv) && alloc2(h, &h->phi, K * nc) && alloc2(h, &h->GU, K * nc) &&
             alloc2(h, &h->Es, K * nc) && alloc2(h, &h->b, nz) && alloc2(h, &h->x, nz) && alloc2(h, &h->Kr, nz) &&
             alloc2(h, &h->Kt, nz) && alloc2(h, &h->Kbasis, (int64_t)(h->m + 1) * nz) &&
             alloc2(h, &h->part, (int64_t)kRedBlocks * (kMaxRestart2 + 1)) && alloc2(h, &h->dots, kMaxRestart2 + 1) &&
             alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc) &&
-            alloc2(h, &h->hcol, kMaxRestart2 + 2);
+            alloc2(h, &h->hcol, kMaxRestart2 + 2) && alloc2(h, &h->tk, K * nc);
   if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
   D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
   CK2(cudaMemcpy(h->dmu, h->hmu.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
