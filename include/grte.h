@@ -292,6 +292,13 @@ grte_status grte2d_get_quadrature(grte2d_t h, double* mu, double* eta, double* w
 /* Total energy sum over cells dx dy (rho/c + Cv T) of the current state. */
 grte_status grte2d_get_energy(grte2d_t h, double* e);
 grte_status grte2d_stats(grte2d_t h, grte_stats_t* st);
+/* Learned Newton start on a 2D handle, as grte_set_guess / grte_set_newton_start /
+ * grte_set_sample_logging / grte_get_newton_samples (n = nx*ny; the features are the
+ * same six per cell). */
+grte_status grte2d_set_guess(grte2d_t h, grte_mlp_t mlp);
+grte_status grte2d_set_newton_start(grte2d_t h, int mode);
+grte_status grte2d_set_sample_logging(grte2d_t h, int on);
+grte_status grte2d_get_newton_samples(grte2d_t h, float* X, float* y, size_t n);
 const char* grte2d_last_error(grte2d_t h);
 void grte2d_destroy(grte2d_t h);
 

@@ -1,4 +1,5 @@
-"""In-tree build of the CUDA library (nvcc, sm_103a only)."""
+"""In-tree build of the CUDA library (nvcc, sm_103a only): each translation unit is
+compiled in its own nvcc process, in parallel, then linked into one shared library."""
 import os
 import subprocess
 
@@ -6,8 +7,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("grte1d.cu", "grte2d.cu", "mlp.cu")]
 LIB = os.path.join(_HERE, "libgrte.so")
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared"]
+OBJ_DIR = os.path.join(_HERE, "_build")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def nvcc():
@@ -18,7 +20,20 @@ def nvcc():
 
 
 def build_library(verbose=False):
-    cmd = [nvcc()] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", LIB] + SOURCES
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include")]
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
+        cmd = [nvcc()] + NVCC_FLAGS + inc + ["-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    failed = [cmd for cmd, p in procs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

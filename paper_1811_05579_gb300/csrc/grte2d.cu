@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/grte.h"
+#include "mlp.cuh"
 
 namespace grte2 {
 
@@ -48,6 +49,9 @@ struct D2 {
   double *gd, *gdi, *pdi;   // [k][cell] diagonal g_k of G_k, 1/(A + g_k); [cell] inverse rho pivot
   int* status;
   int newton_maxit;
+  // learned Newton start: per-cell features (6 floats), predicted and logged targets
+  float *feat, *guess, *ytrue;
+  int use_guess, log_samples, start_prev;
 };
 
 __device__ __forceinline__ void flag2(int* status, int code) { atomicOr(status, 1 << code); }
@@ -520,10 +524,31 @@ __global__ void k2_project(D2 D, const double* __restrict__ EJ) {
 }
 
 // ----------------------------------------------------------------------------- Newton
+// Features of the learned Newton start per cell (after the prediction), as in 1D:
+// log10 T^n, log10 rho*, log10 sigma_eff, log10 eps, log10 dt, log10 Cv.
+__global__ void k2_newton_feat(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const double Tn = D.T[c], t3 = Tn * Tn * Tn;
+  const double sig_eff = g.kind == GRTE_SIGMA_CONST ? D.sig[c] : D.sig[c] / fmax(t3, 1e-300);
+  auto lg = [](double x) { return (float)log10(fmin(fmax(x, 1e-300), 1e300)); };
+  float* f = D.feat + 6 * c;
+  f[0] = lg(Tn);
+  f[1] = lg(D.rho_s[c]);
+  f[2] = lg(sig_eff);
+  f[3] = lg(g.eps);
+  f[4] = lg(g.dt);
+  f[5] = lg(g.Cv);
+}
+
 // Eq. Tnp1 (sigma_0/T^3: Eq. dis-cor-marshak4 + 5) multiplied by sig:
 //   A T^4 + B T = R,  A = sig a/dt,  B = sig Cv/dt + eps^2 kap Cv/(c dt^2),
 //   R = sig (rho^n/(c dt) - Fdiv) + B T^n,  kap = 1 or max(U*, 0)^{3/4};
-// Newton from T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the root.
+// Newton from T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the root.  With
+// a learned start (network output y = log10(T^{n+1}/T^n), used where |y| > 1e-2) or the
+// previous-T start, one Newton step from the guess lands at or above the root (convex
+// left side); the learned one is clamped to T_hi.
 __global__ void k2_newton(D2 D) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
@@ -543,7 +568,17 @@ __global__ void k2_newton(D2 D) {
   } else {
     double t = A > 0.0 ? sqrt(sqrt(R / A)) : INFINITY;
     if (B > 0.0) t = fmin(t, R / B);
-    for (its = 1; its <= D.newton_maxit; ++its) {
+    const bool learned = D.use_guess && fabs((double)D.guess[c]) > 1e-2;
+    if (learned || D.start_prev) {
+      const double gs = learned ? Tn * exp10((double)D.guess[c]) : Tn;
+      if (isfinite(gs) && gs > 0.0) {
+        const double g2 = gs * gs;
+        const double t1 = gs - (A * g2 * g2 + B * gs - R) / (4.0 * A * g2 * gs + B);
+        if (isfinite(t1) && t1 > 0.0) t = learned ? fmin(t, t1) : t1;
+        ++its;
+      }
+    }
+    for (its = its + 1; its <= D.newton_maxit; ++its) {
       const double t2 = t * t;
       const double f = A * t2 * t2 + B * t - R;
       const double fp = 4.0 * A * t2 * t + B;
@@ -556,6 +591,7 @@ __global__ void k2_newton(D2 D) {
   }
   D.T[c] = T;
   D.newton_its[c] = (double)its;
+  if (D.log_samples) D.ytrue[c] = (T > 0.0 && Tn > 0.0) ? (float)log10(T / Tn) : 0.0f;
 }
 
 // ----------------------------------------------------------------------------- vector kernels
@@ -745,6 +781,7 @@ struct grte2d_ctx {
   double *b = nullptr, *x = nullptr, *Kr = nullptr, *Kt = nullptr, *Kbasis = nullptr;
   double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr, *hcol = nullptr;
   double* tk = nullptr;   // [k][cell] per-pair cell values summed by k2_cellsum
+  grte_mlp_t mlp = nullptr;   // learned Newton start (not owned)
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
 };
 
@@ -936,6 +973,11 @@ static grte_status step2(grte2d_t h) {
   k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{h->Es, nc, nullptr}, h->V);
   k2_cell<C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
   k2_cellsum<C_FDIV><<<gc, kThreads, 0, st>>>(D, h->tk, nullptr, D.Fdiv, nullptr);
+  if (D.use_guess || D.log_samples) k2_newton_feat<<<gc, kThreads, 0, st>>>(D);
+  if (D.use_guess) {
+    cudaError_t e = grte::mlp_guess_launch(h->mlp, D.feat, nc, D.guess, st);
+    if (e != cudaSuccess) return fail2(h, GRTE_ECUDA, std::string("mlp guess: ") + cudaGetErrorString(e));
+  }
   k2_newton<<<gc, kThreads, 0, st>>>(D);
   // correction substep 2 at T^{n+1}
   k2_coef<<<gc, kThreads, 0, st>>>(D);
@@ -1174,6 +1216,61 @@ grte_status grte2d_get_energy(grte2d_t h, double* e) {
   CK2(cudaGetLastError());
   CK2(cudaMemcpyAsync(e, h->dots, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK2(cudaStreamSynchronize(h->stream));
+  return GRTE_OK;
+}
+
+static grte_status ensure_feat2(grte2d_t h) {
+  D2& D = h->D;
+  if (!D.feat) {
+    const int64_t nc = h->g.nc;
+    if (!alloc2(h, &D.feat, 6 * nc) || !alloc2(h, &D.guess, nc) || !alloc2(h, &D.ytrue, nc))
+      return fail2(h, GRTE_ENOMEM, "cudaMalloc features");
+  }
+  return GRTE_OK;
+}
+
+grte_status grte2d_set_guess(grte2d_t h, grte_mlp_t m) {
+  if (!h) return GRTE_EINVAL;
+  CK2(cudaStreamSynchronize(h->stream));
+  if (m) {
+    grte_status s = ensure_feat2(h);
+    if (s != GRTE_OK) return s;
+  }
+  h->mlp = m;
+  h->D.use_guess = m ? 1 : 0;
+  h->D.start_prev = 0;
+  return GRTE_OK;
+}
+
+grte_status grte2d_set_newton_start(grte2d_t h, int mode) {
+  if (!h) return GRTE_EINVAL;
+  if (mode != GRTE_START_BOUND && mode != GRTE_START_PREVIOUS && mode != GRTE_START_LEARNED)
+    return fail2(h, GRTE_EINVAL, "bad start mode");
+  if (mode == GRTE_START_LEARNED && !h->mlp) return fail2(h, GRTE_ESTATE, "no network set (grte2d_set_guess)");
+  CK2(cudaStreamSynchronize(h->stream));
+  h->D.start_prev = mode == GRTE_START_PREVIOUS ? 1 : 0;
+  h->D.use_guess = mode == GRTE_START_LEARNED ? 1 : 0;
+  return GRTE_OK;
+}
+
+grte_status grte2d_set_sample_logging(grte2d_t h, int on) {
+  if (!h) return GRTE_EINVAL;
+  CK2(cudaStreamSynchronize(h->stream));
+  if (on) {
+    grte_status s = ensure_feat2(h);
+    if (s != GRTE_OK) return s;
+  }
+  h->D.log_samples = on ? 1 : 0;
+  return GRTE_OK;
+}
+
+grte_status grte2d_get_newton_samples(grte2d_t h, float* X, float* y, size_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (!X || !y || n != (size_t)h->g.nc) return fail2(h, GRTE_EINVAL, "n must be nx*ny");
+  if (!h->D.log_samples) return fail2(h, GRTE_ESTATE, "sample logging is off");
+  CK2(cudaStreamSynchronize(h->stream));
+  CK2(cudaMemcpy(X, h->D.feat, sizeof(float) * 6 * n, cudaMemcpyDeviceToHost));
+  CK2(cudaMemcpy(y, h->D.ytrue, sizeof(float) * n, cudaMemcpyDeviceToHost));
   return GRTE_OK;
 }
 

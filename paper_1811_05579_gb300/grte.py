@@ -62,7 +62,9 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_mlp_grad", "grte_mlp_train", "grte_set_guess", "grte_set_sample_logging",
             "grte_get_newton_samples", "grte_set_newton_start", "grte_get_tuning", "grte2d_create",
             "grte2d_set_state", "grte2d_step", "grte2d_get_T", "grte2d_get_E", "grte2d_get_O", "grte2d_get_stage",
-            "grte2d_get_quadrature", "grte2d_get_energy", "grte2d_stats", "grte2d_last_error", "grte2d_destroy"]
+            "grte2d_get_quadrature", "grte2d_get_energy", "grte2d_stats", "grte2d_last_error", "grte2d_destroy",
+            "grte2d_set_guess", "grte2d_set_newton_start", "grte2d_set_sample_logging",
+            "grte2d_get_newton_samples"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -127,6 +129,10 @@ def load_library(path=LIB_PATH):
     lib.grte2d_last_error.restype = ctypes.c_char_p
     lib.grte2d_destroy.argtypes = [ctypes.c_void_p]
     lib.grte2d_destroy.restype = None
+    lib.grte2d_set_guess.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.grte2d_set_newton_start.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.grte2d_set_sample_logging.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.grte2d_get_newton_samples.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_size_t]
     return lib
 
 
@@ -489,6 +495,21 @@ class Grte2D:
         e = np.zeros(1)
         self._check(lib().grte2d_get_energy(self.h, _ptr(e)))
         return float(e[0])
+
+    def set_guess(self, mlp):
+        return self._check(lib().grte2d_set_guess(self.h, mlp.h if mlp is not None else None))
+
+    def set_newton_start(self, mode):
+        return self._check(lib().grte2d_set_newton_start(self.h, mode))
+
+    def set_sample_logging(self, on):
+        return self._check(lib().grte2d_set_sample_logging(self.h, 1 if on else 0))
+
+    def newton_samples(self):
+        X = np.empty((self.nc, 6), dtype=np.float32)
+        y = np.empty(self.nc, dtype=np.float32)
+        self._check(lib().grte2d_get_newton_samples(self.h, _fptr(X), _fptr(y), self.nc))
+        return X, y
 
     def stats(self, allow=()):
         s = Stats()

@@ -33,7 +33,15 @@ class SplitMix64:
         """Uniform doubles in [0, 1)."""
         if n is None:
             return (self.next_u64() >> 11) * (1.0 / (1 << 53))
-        return np.array([(self.next_u64() >> 11) * (1.0 / (1 << 53)) for _ in range(n)])
+        # the same stream, n draws at once: state_k = state + k * golden (mod 2^64)
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            z = np.uint64(self.state) + k * np.uint64(_GOLDEN)
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+        self.state = (self.state + n * _GOLDEN) & _MASK
+        return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
 
     def normal(self, n):
         """Standard normals by Box-Muller."""
@@ -162,3 +170,29 @@ def random_state_1d(rng, nx, M, scale_T=(0.05, 1.0)):
     E = (T ** 4)[:, None] * (1.0 + 0.1 * rng.uniform(nx * M).reshape(nx, M))
     O = 0.2 * (rng.uniform((nx + 1) * M).reshape(nx + 1, M) - 0.5)
     return T, E, O
+
+
+# ----------------------------------------------------------------------------- 2D
+
+def checkerboard_sigma_2d(nx, ny=None, blocks=8, lo=1.0, hi=100.0):
+    """sigma_0 per cell ([j][i], row-major) of the 2D checkerboard: lo on the 'black',
+    hi on the 'white' blocks of a blocks x blocks board, block (0, 0) black."""
+    ny = nx if ny is None else ny
+    i = np.arange(nx) // max(nx // blocks, 1)
+    j = np.arange(ny) // max(ny // blocks, 1)
+    return np.where(((i[None, :] + j[:, None]) % 2) == 0, lo, hi).astype(np.float64)
+
+
+def lognormal_sigma_2d(n, seed=BASE_SEED + 5, sd_cells=8.0):
+    """sigma_0 per cell of the random-smooth 2D workload: exp(g), where g is an iid
+    N(0, 1) field on the periodic n x n grid, filtered by a separable Gaussian of
+    standard deviation sd_cells (taps to 4 sd, wrapped), then shifted and scaled to
+    zero mean and unit variance, so that sigma_0 is log-normal with mu = 0, s = 1."""
+    z = SplitMix64(seed).normal(n * n).reshape(n, n)
+    r = int(math.ceil(4 * sd_cells))
+    taps = np.exp(-0.5 * (np.arange(-r, r + 1) / sd_cells) ** 2)
+    taps /= taps.sum()
+    for ax in (0, 1):
+        z = sum(t * np.roll(z, d, axis=ax) for d, t in zip(range(-r, r + 1), taps))
+    g = (z - z.mean()) / z.std()
+    return np.exp(g)
