@@ -190,6 +190,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256", "checker2d"])
     ap.add_argument("--n2d", type=int, default=128, help="cells per axis of the checker2d workload")
+    ap.add_argument("--prec2d", default="block", choices=["block", "multigrid"],
+                    help="2D prediction preconditioner: per-cell block + multigrid on rho, or per-cell block only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -483,7 +485,8 @@ def run_2d(args):
     n = args.n2d
     sig, T0, dt, eps = checker2d_inputs(n)
     stream = torch.cuda.current_stream()
-    h = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream)
+    prec = G.PREC2D_MULTIGRID if args.prec2d == "multigrid" else G.PREC2D_BLOCK
+    h = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream, prec=prec)
     h.set_state(T0)
     allow = (5,)        # cells reaching R <= 0 at this dt (see the workload's readings)
     for _ in range(args.warmup):
@@ -492,7 +495,7 @@ def run_2d(args):
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
-    t_ms, its = 0.0, 0
+    t_ms, its, its_corr, its_mg = 0.0, 0, 0, 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -502,7 +505,10 @@ def run_2d(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t_ms += e0.elapsed_time(e1)
-        its += h.stats(allow=allow)["krylov_iters"]
+        st = h.stats(allow=allow)
+        its += st["krylov_iters"]
+        its_corr += st["krylov_iters_corr"]
+        its_mg += st["krylov_iters_mg"]
     clk = clocks.stop()
     upd = n * n * 40
     value, t_ms = job_throughput(upd, args.steps, t_ms, world, None)
@@ -526,7 +532,7 @@ def run_2d(args):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
             "config": {"workload": "2d_checkerboard_%dx%d_s8" % (n, n), "n": n, "pairs": 20, "eps": eps,
-                       "sigma0": [1, 100], "blocks": 8, "dt": "0.5 dx", "T_in": 1e-2,
+                       "sigma0": [1, 100], "blocks": 8, "dt": "0.5 dx", "T_in": 1e-2, "prec2d": args.prec2d,
                        "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},
             "gpu_launches": None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(T.nbytes + E.nbytes + O.nbytes),
@@ -534,7 +540,9 @@ def run_2d(args):
             "roofline": {"kernel": "2D step (all kernels)", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
                          "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
                          "note": "24 B per cell-angle update over the step time"},
-            "krylov_iters_per_step": its / args.steps, "status_flags": h.stats(allow=allow)["status_flags"],
+            "krylov_iters_per_step": its / args.steps, "krylov_iters_corr_per_step": its_corr / args.steps,
+            "krylov_iters_mg_per_step": its_mg / args.steps,
+            "status_flags": h.stats(allow=allow)["status_flags"],
             "clocks": clk}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_2d()

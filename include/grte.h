@@ -91,6 +91,13 @@ typedef struct {
                             launch (captured once; the Krylov loop runs under device-side
                             conditional nodes, no host round trip inside a step).  Steps
                             taken while per-kernel profiling is on run eagerly.  0: eager    */
+  int prec2d;            /* 2D prediction preconditioner: GRTE_PREC2D_BLOCK (default): the
+                            per-cell angular block (cells uncoupled); GRTE_PREC2D_MULTIGRID:
+                            first a solve preconditioned by block elimination of the (e, rho)
+                            system with the per-cell diagonal of each pair operator and one
+                            multigrid V-cycle on the cells' rho Schur complement (one scale
+                            for all cells), then the per-cell scaled solve with the block
+                            preconditioner.  Ignored by the 1D path                        */
 } grte_options;
 
 /* Statistics of the last grte_step call (summed over its steps and instances). */
@@ -103,6 +110,10 @@ typedef struct {
   int64_t status_flags;      /* OR over instances of (1 << grte_status) seen       */
   int64_t line_threads;      /* threads per line solve in use (0 before the first step) */
   int64_t line_smem;         /* 1: the line unknowns stay in shared memory           */
+  int64_t krylov_iters_corr; /* 2D: the part of krylov_iters spent in the correction
+                                substep (the rest is the prediction); 1D: 0          */
+  int64_t krylov_iters_mg;   /* 2D: the part of the prediction's iterations taken with
+                                the multigrid preconditioner; 1D: 0                  */
 } grte_stats_t;
 
 /* Fill *opt with the defaults. */
@@ -205,7 +216,10 @@ grte_status grte_set_guess(grte_t h, grte_mlp_t m);
 /* Newton's starting point: BOUND (default) min((R/A)^{1/4}, R/B), from which Newton
  * decreases monotonically to the root; PREVIOUS one Newton step from T^n (the textbook
  * start); LEARNED one Newton step from the network's guess, clamped to BOUND (set by
- * grte_set_guess).  All three converge to the same root. */
+ * grte_set_guess), in the cells where the guess lies more than 10^0.05 - 1 (about 12%)
+ * below BOUND (elsewhere BOUND is within the network's error of the root and is kept).
+ * All three converge to the same root. */
+enum { GRTE_PREC2D_BLOCK = 0, GRTE_PREC2D_MULTIGRID = 1 };
 enum { GRTE_START_BOUND = 0, GRTE_START_PREVIOUS = 1, GRTE_START_LEARNED = 2 };
 grte_status grte_set_newton_start(grte_t h, int mode);
 /* 1: record the features and the converged target of every cell at each step (the last

@@ -34,6 +34,7 @@
 namespace grte {
 
 namespace cg = cooperative_groups;
+constexpr double kGuessGate = 1.1220184543019633;   // 10^0.05: learned-start gate (k_newton)
 constexpr int kMaxRestart = 16;
 
 struct Inst {
@@ -1044,17 +1045,19 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
     double t = INFINITY;
     if (A > 0.0) t = sqrt(sqrt(R / A));
     if (B > 0.0) t = fmin(t, R / B);
-    // the learned start is used where the network predicts a change of more than
-    // 10^0.01 - 1 (about 2.3%) in the step (above its prediction noise); elsewhere the
-    // closed-form bound is already within a step of the root and an extra guess step
-    // would only cost one
-    const bool learned = D.use_guess && fabs((double)D.guess[gid]) > 1e-2;
+    // the learned guess gl is used where it lies more than 10^0.05 - 1 (about 12%)
+    // below the closed-form bound: there the bound starts far above the root (a front
+    // cell).  Elsewhere the bound is within the network's few-percent error of the root
+    // (the root lies below both) and is kept, so that noise does not cost the extra
+    // guess step.
+    const double gl = D.use_guess ? Tn * exp10((double)D.guess[gid]) : 0.0;
+    const bool learned = D.use_guess && isfinite(gl) && gl > 0.0 && gl * kGuessGate < t;
     if (learned || D.start_prev) {
       // learned (or previous-T) start: one Newton step from any positive guess lands
       // at or above the root (convex left side).  The learned start is clamped to the
       // closed-form bound, so its residual is never larger than the plain start's; the
       // previous-T start is kept unclamped (the textbook start, for comparison).
-      const double g = learned ? Tn * exp10((double)D.guess[gid]) : Tn;
+      const double g = learned ? gl : Tn;
       if (isfinite(g) && g > 0.0) {
         const double g2 = g * g;
         const double t1 = g - (A * g2 * g2 + B * g - R) / (4.0 * A * g2 * g + B);
@@ -1503,6 +1506,7 @@ void grte_default_options(grte_options* o) {
   o->stream = nullptr;
   o->line_threads = 0;
   o->use_graph = 1;
+  o->prec2d = 0;
 }
 
 const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle"; }

@@ -21,9 +21,13 @@
 #include <vector>
 
 #include "../../include/grte.h"
+#include "mg2d.cuh"
 #include "mlp.cuh"
 
 namespace grte2 {
+
+constexpr double kGuessGate2 = 1.1220184543019633;   // 10^0.05: learned-start gate (k2_newton)
+constexpr int kMgStageCycles = 4;   // restart cycles of the multigrid-preconditioned stage
 
 constexpr int kMaxPairs = 64;
 constexpr int kMaxRestart2 = 64;
@@ -401,6 +405,99 @@ __global__ void k2_prec(D2 D, const double* __restrict__ r, double* __restrict__
   }
 }
 
+// ----------------------------------------------------------------------------- Schur preconditioner
+// Prediction preconditioner with the cells coupled (GRTE_PREC2D_MULTIGRID): block elimination of
+// the (e, rho) system with (A + G_k)^{-1} replaced by its diagonal D_k = 1/(A + g_k),
+//   f   = r_rho - sum_k w_k G_k D_k r_k
+//   rho = S^{-1} f,   S = alpha + sum_k w_k G_k D_k beta   (beta = A - alpha)
+//   e_k = D_k (r_k - alpha rho - G_k rho),
+// with G_k applied exactly (vertex and cell passes) and S^{-1} one multigrid V-cycle
+// (mg2d.cuh).  S is a 3x3 stencil on the cells, recovered once per solve by probing:
+// the cells are coloured so that no two cells of a 3x3 neighbourhood share a colour,
+// and S applied to the indicator of one colour gives, at every cell, the coupling to
+// the one cell of that colour next to it.
+
+// Colour of cell i along an axis of n cells: i mod 3, except on a periodic axis whose
+// length is not a multiple of 3, where the sequence ends with 0 1 2 3 (n = 1 mod 3) or
+// 0 1 2 3 0 1 2 3 (n = 2 mod 3) so that any three cyclically consecutive cells differ
+// (n = 5 needs five colours, n <= 2 one per cell).
+__host__ __device__ inline int axis_colour(int i, int n, int per) {
+  if (!per || n % 3 == 0) return i % 3;
+  if (n <= 2 || n == 5) return i;
+  if (n % 3 == 1) return i < n - 4 ? i % 3 : i - (n - 4);
+  return i < n - 8 ? i % 3 : (i - (n - 8)) % 4;
+}
+__host__ __device__ inline int axis_ncolours(int n, int per) {
+  if (!per || n % 3 == 0) return n < 3 ? n : 3;
+  if (n <= 2 || n == 5) return n;
+  return 4;
+}
+
+// probe input: e_k = D_k beta on the cells of colour (cx, cy), 0 elsewhere
+__global__ void k2_probe_in(D2 D, int cx, int cy, double* __restrict__ e) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nc) return;
+  const int c = (int)(t % g.nc), p = c % g.Nx, q = c / g.Nx;
+  const bool on = axis_colour(p, g.Nx, g.bcx == GRTE_BC_PERIODIC) == cx &&
+                  axis_colour(q, g.Ny, g.bcy == GRTE_BC_PERIODIC) == cy;
+  e[t] = on ? D.gdi[t] * (D.A[c] - D.alpha[c]) : 0.0;
+}
+
+// probe output: sum_k w_k tk (+ alpha on the diagonal) stored at the stencil position of
+// the cell of colour (cx, cy) in the 3x3 neighbourhood (positions tried in the order
+// 0, +1, -1 per axis: on a periodic axis of one or two cells several positions name the
+// same cell and the coupling is stored once)
+__global__ void k2_probe_out(D2 D, int cx, int cy, const double* __restrict__ tk, double* __restrict__ S0) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  const int px = g.bcx == GRTE_BC_PERIODIC, py = g.bcy == GRTE_BC_PERIODIC;
+  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
+  double v = 0.0;
+  for (int k = 0; k < g.K; ++k) v += D.w[k] * tk[(int64_t)k * g.nc + c];
+  const int order[3] = {0, 1, -1};
+  for (int a = 0; a < 3; ++a) {
+    const int dy = order[a], qn = mg::nbr(q, dy, g.Ny, py);
+    if (qn < 0 || axis_colour(qn, g.Ny, py) != cy) continue;
+    for (int b = 0; b < 3; ++b) {
+      const int dx = order[b], pn = mg::nbr(p, dx, g.Nx, px);
+      if (pn < 0 || axis_colour(pn, g.Nx, px) != cx) continue;
+      if (pn == p && qn == q) v += D.alpha[c];
+      S0[(int64_t)((dy + 1) * 3 + dx + 1) * g.nc + c] = v;
+      return;
+    }
+  }
+}
+
+// et_k = D_k r_k
+__global__ void k2_pc_et(D2 D, const double* __restrict__ r, double* __restrict__ et) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)D.g.K * D.g.nc) return;
+  et[t] = D.gdi[t] * r[t];
+}
+
+// f = r_rho - sum_k w_k tk
+__global__ void k2_pc_rhs(D2 D, const double* __restrict__ r, const double* __restrict__ tk, double* __restrict__ f) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (c >= g.nc) return;
+  double s = r[(int64_t)g.K * g.nc + c];
+  for (int k = 0; k < g.K; ++k) s -= D.w[k] * tk[(int64_t)k * g.nc + c];
+  f[c] = s;
+}
+
+// z_k = w D_k (r_k - alpha rho - tk), z_rho = w rho  (tk = G_k rho; w the Krylov scale)
+__global__ void k2_pc_final(D2 D, const double* __restrict__ r, const double* __restrict__ rho,
+                            const double* __restrict__ tk, double* __restrict__ z) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  const int64_t ne = (int64_t)g.K * g.nc;
+  if (t >= ne + g.nc) return;
+  const int64_t c = t % g.nc;
+  z[t] = t < ne ? D.wsc[c] * D.gdi[t] * (r[t] - D.alpha[c] * rho[c] - tk[t]) : D.wsc[c] * rho[c];
+}
+
 // gd[k][c] = diagonal of G_k at cell c (for the preconditioner), at the current coefficients
 // and the reciprocals the preconditioner needs: gdi = 1/(A + g_k) and, per cell, the
 // inverse of the arrow block's rho pivot alpha + sum_k w_k g_k (A - alpha)/(A + g_k).
@@ -421,8 +518,8 @@ __global__ void k2_gdiag(D2 D) {
   D.pdi[c] = 1.0 / den;
 }
 
-// Krylov scale per cell from a magnitude field src: s = |src| + 1e-13 max|src|,
-// w = f/s (f = 1 in the prediction, eps in the correction, whose unknown E_J enters
+// Krylov scale per cell from a magnitude field src: s = |src| + 1e-13 max|src| (or
+// s = max|src| for every cell with uniform), w = f/s (f = 1 in the prediction, eps in the correction, whose unknown E_J enters
 // E as eps E_J).
 __global__ void k2_maxabs(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
   __shared__ double red[kThreads / 32];
@@ -439,12 +536,13 @@ __global__ void k2_maxabs(const double* __restrict__ x, int64_t n, double* __res
   }
 }
 
-__global__ void k2_weights(D2 D, const double* __restrict__ src, double f, const double* __restrict__ part, int nb) {
+__global__ void k2_weights(D2 D, const double* __restrict__ src, double f, const double* __restrict__ part, int nb,
+                           int uniform) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= D.g.nc) return;
   double m = 0.0;
   for (int b = 0; b < nb; ++b) m = fmax(m, part[b]);
-  const double s = fabs(src[c]) + 1e-13 * m + 1e-300;
+  const double s = (uniform ? m : fabs(src[c]) + 1e-13 * m) + 1e-300;
   D.wsc[c] = f / s;
   D.iwsc[c] = s / f;
 }
@@ -546,9 +644,11 @@ __global__ void k2_newton_feat(D2 D) {
 //   A T^4 + B T = R,  A = sig a/dt,  B = sig Cv/dt + eps^2 kap Cv/(c dt^2),
 //   R = sig (rho^n/(c dt) - Fdiv) + B T^n,  kap = 1 or max(U*, 0)^{3/4};
 // Newton from T_hi = min((R/A)^{1/4}, R/B) decreases monotonically to the root.  With
-// a learned start (network output y = log10(T^{n+1}/T^n), used where |y| > 1e-2) or the
-// previous-T start, one Newton step from the guess lands at or above the root (convex
-// left side); the learned one is clamped to T_hi.
+// a learned start (network output y = log10(T^{n+1}/T^n), guess T^n 10^y, used where
+// it lies more than 12% below T_hi: elsewhere T_hi is within the network's error of
+// the root) or the previous-T
+// start, one Newton step from the guess lands at or above the root (convex left
+// side); the learned one is clamped to T_hi.
 __global__ void k2_newton(D2 D) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
@@ -568,9 +668,10 @@ __global__ void k2_newton(D2 D) {
   } else {
     double t = A > 0.0 ? sqrt(sqrt(R / A)) : INFINITY;
     if (B > 0.0) t = fmin(t, R / B);
-    const bool learned = D.use_guess && fabs((double)D.guess[c]) > 1e-2;
+    const double gl = D.use_guess ? Tn * exp10((double)D.guess[c]) : 0.0;
+    const bool learned = D.use_guess && isfinite(gl) && gl > 0.0 && gl * kGuessGate2 < t;
     if (learned || D.start_prev) {
-      const double gs = learned ? Tn * exp10((double)D.guess[c]) : Tn;
+      const double gs = learned ? gl : Tn;
       if (isfinite(gs) && gs > 0.0) {
         const double g2 = gs * gs;
         const double t1 = gs - (A * g2 * g2 + B * gs - R) / (4.0 * A * g2 * gs + B);
@@ -782,6 +883,8 @@ struct grte2d_ctx {
   double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr, *hcol = nullptr;
   double* tk = nullptr;   // [k][cell] per-pair cell values summed by k2_cellsum
   grte_mlp_t mlp = nullptr;   // learned Newton start (not owned)
+  std::vector<mg::Level> mgl;        // multigrid levels of the Schur preconditioner (empty: per-cell block only)
+  double *mg_M = nullptr, *mg_inv = nullptr;   // coarsest level: dense scratch and inverse
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
 };
 
@@ -834,9 +937,88 @@ static void apply_M(grte2d_t h, bool pred, const double* xin, double* y) {
   }
 }
 
-static void apply_P(grte2d_t h, bool pred, const double* r, double* z) {
-  if (pred) k2_prec<true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, r, z);
-  else k2_prec<false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, r, z);
+// One V-cycle on level l (right side in mgl[l].b); returns the buffer holding the result.
+static const double* mg_vcycle(grte2d_t h, size_t l) {
+  cudaStream_t st = h->stream;
+  mg::Level& L = h->mgl[l];
+  const unsigned gb = grid_of(L.n);
+  if (l + 1 == h->mgl.size()) {
+    mg::mg_dense_apply<<<1, mg::kThreadsMg, 0, st>>>(L, h->mg_inv);
+    return L.x;
+  }
+  mg::Level& C = h->mgl[l + 1];
+  const unsigned gcb = grid_of(C.n);
+  mg::mg_jacobi0<<<gb, kThreads, 0, st>>>(L);
+  if (L.ncomp == 1) {
+    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    mg::mg_restrict<1><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
+  } else {
+    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    mg::mg_restrict<2><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
+  }
+  const double* xc = mg_vcycle(h, l + 1);
+  if (L.ncomp == 1) {
+    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
+    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+  } else {
+    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
+    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+  }
+  return L.xt;
+}
+
+// Probe S (3x3 stencil into level 0) at the current coefficients and build the
+// coarse levels; after k2_gdiag.
+static void mg_setup(grte2d_t h) {
+  D2& D = h->D;
+  const G2& g = D.g;
+  cudaStream_t st = h->stream;
+  const int64_t K = g.K, nc = g.nc;
+  mg::Level& L0 = h->mgl[0];
+  cudaMemsetAsync(L0.coef, 0, sizeof(double) * 9 * nc, st);
+  const int px = g.bcx == GRTE_BC_PERIODIC, py = g.bcy == GRTE_BC_PERIODIC;
+  const int ncx = axis_ncolours(g.Nx, px), ncy = axis_ncolours(g.Ny, py);
+  for (int cy = 0; cy < ncy; ++cy)
+    for (int cx = 0; cx < ncx; ++cx) {
+      k2_probe_in<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->Kt);
+      k2_vertex<false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, UField{h->Kt, nc, nullptr}, h->V);
+      k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{h->Kt, nc, nullptr}, nullptr,
+                                                                   h->tk, nullptr, nullptr);
+      k2_probe_out<<<grid_of(nc), kThreads, 0, st>>>(D, cx, cy, h->tk, L0.coef);
+    }
+  mg::mg_idiag0<<<grid_of(nc), kThreads, 0, st>>>(L0);
+  for (size_t l = 0; l + 1 < h->mgl.size(); ++l) {
+    mg::Level &F = h->mgl[l], &C = h->mgl[l + 1];
+    if (F.ncomp == 1) mg::mg_galerkin<1><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
+    else mg::mg_galerkin<2><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
+  }
+  mg::Level& Lc = h->mgl.back();
+  if (Lc.ncomp == 1) mg::mg_dense_inverse<1><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
+  else mg::mg_dense_inverse<2><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
+}
+
+static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double* z) {
+  D2& D = h->D;
+  cudaStream_t st = h->stream;
+  if (!pred) {
+    k2_prec<false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, r, z);
+    return;
+  }
+  if (!use_mg) {
+    k2_prec<true><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, r, z);
+    return;
+  }
+  const int64_t K = D.g.K, nc = D.g.nc;
+  k2_pc_et<<<grid_of(K * nc), kThreads, 0, st>>>(D, r, h->Kt);
+  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, UField{h->Kt, nc, nullptr}, h->V);
+  k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{h->Kt, nc, nullptr}, nullptr, h->tk,
+                                                               nullptr, nullptr);
+  k2_pc_rhs<<<grid_of(nc), kThreads, 0, st>>>(D, r, h->tk, h->mgl[0].b);
+  const double* rho = mg_vcycle(h, 0);
+  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, UField{nullptr, 0, rho}, h->V);
+  k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, rho}, nullptr, h->tk,
+                                                               nullptr, nullptr);
+  k2_pc_final<<<grid_of((K + 1) * nc), kThreads, 0, st>>>(D, r, rho, h->tk, z);
 }
 
 // Restarted GMRES(m) with left preconditioning on M x = b (x holds the initial
@@ -846,7 +1028,17 @@ static void apply_P(grte2d_t h, bool pred, const double* r, double* z) {
 // D_w P^{-1} M D_w^{-1} that keeps the preconditioned spectrum.  In those units every
 // cell's unknowns are O(1), so the test |D_w P^{-1}(b - M x)|_2 <= rtol sqrt(n_cells)
 // bounds the residual of every cell relative to the cell's own magnitude (RMS).
-static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
+//
+// mg_stage (prediction, multigrid preconditioner): the same iteration with one scale
+// for all cells (w = 1/max|rho|).  The multigrid couples the cells, and under per-cell
+// scales its error terms from hot cells into cold ones are multiplied by the ratio of
+// their magnitudes (up to ~1e8 across a front), which stalls the iteration; with one
+// scale it converges in a few iterations to rtol relative to the largest cell.  It
+// ends there, or when a restart no longer gains 4x, or a cycle stops falling (less
+// than 2x over four iterations after a 1e6 reduction), without a verdict: the
+// per-cell scaled solve with the per-cell block preconditioner then runs from its
+// iterate and decides (the cold, opaque cells it still has to fix are nearly local).
+static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& iters) {
   cudaStream_t st = h->stream;
   D2& D = h->D;
   const int nblk = pred ? D.g.K + 1 : D.g.K;
@@ -856,12 +1048,13 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
   std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), yv(m);
   const unsigned vb = kRedBlocks;
   const double thr = h->opt.krylov_rtol * std::sqrt((double)D.g.nc);
+  const int maxcycles = mg_stage ? kMgStageCycles : h->opt.krylov_maxcycles;
   grte_status s = GRTE_OK;
   iters = 0;
   auto set_scale = [&]() {
     const double* src = pred ? h->x + (int64_t)D.g.K * D.g.nc : h->cscale;
     k2_maxabs<<<kRedBlocks, kThreads, 0, st>>>(src, D.g.nc, h->part);
-    k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks);
+    k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks, mg_stage ? 1 : 0);
   };
   // the true scaled residual of the unscaled x, into V_0; returns its norm
   auto residual = [&](double* beta) -> grte_status {
@@ -869,7 +1062,7 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
     k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.wsc, nblk, D.g.nc);   // x -> y
     apply_M(h, pred, h->x, h->Kr);
     k2_bminus<<<vb, kThreads, 0, st>>>(h->b, h->Kr, n);
-    apply_P(h, pred, h->Kr, V);
+    apply_P(h, pred, mg_stage, h->Kr, V);
     double b2 = 0.0;
     grte_status r = mdot(h, V, V, 1, n, &b2);
     *beta = std::sqrt(b2);
@@ -880,16 +1073,16 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
   // opaque cells the rows are sums of terms far larger than the residual)
   const double stall = 1e-9 * std::sqrt((double)D.g.nc);
   double prev = INFINITY;
-  for (int cycle = 0; cycle <= h->opt.krylov_maxcycles; ++cycle) {
+  for (int cycle = 0; cycle <= maxcycles; ++cycle) {
     double beta = 0.0;
     if ((s = residual(&beta)) != GRTE_OK) return s;
     if (!std::isfinite(beta)) return fail2(h, GRTE_ENAN, "GMRES: non-finite residual");
-    const bool floor_reached = beta <= stall && beta >= 0.25 * prev;
+    const bool floor_reached = mg_stage ? beta >= 0.25 * prev : (beta <= stall && beta >= 0.25 * prev);
     prev = beta;
-    if (beta <= thr || floor_reached || cycle == h->opt.krylov_maxcycles) {
+    if (beta <= thr || floor_reached || cycle == maxcycles) {
       if (floor_reached) beta = 0.0;
       k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);  // y -> x
-      if (!(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
+      if (!mg_stage && !(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
       return GRTE_OK;
     }
     k2_scale<<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
@@ -900,7 +1093,7 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
       double* vj = V + (int64_t)j * n;
       double* w = V + (int64_t)(j + 1) * n;
       apply_M(h, pred, vj, h->Kr);
-      apply_P(h, pred, h->Kr, w);
+      apply_P(h, pred, mg_stage, h->Kr, w);
       // classical Gram-Schmidt, twice; the coefficients stay on the device (dots ->
       // maxpy), the Hessenberg column is accumulated there and read once per iteration
       std::vector<double> hc(j + 2, 0.0);
@@ -932,7 +1125,9 @@ static grte_status gmres2(grte2d_t h, bool pred, int64_t n, int& iters) {
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
       kk = j + 1;
       if (hn > 0.0) k2_scale<<<vb, kThreads, 0, st>>>(w, 1.0 / hn, n);
-      if (std::fabs(g[j + 1]) <= 0.5 * thr || hn == 0.0) break;
+      const double gj = std::fabs(g[j + 1]);
+      if (gj <= 0.5 * thr || hn == 0.0) break;
+      if (mg_stage && j >= 4 && gj <= 1e-6 * beta && gj > 0.5 * std::fabs(g[j - 3])) break;
     }
     for (int i = kk - 1; i >= 0; --i) {
       double t = g[i];
@@ -964,8 +1159,16 @@ static grte_status step2(grte2d_t h) {
   k2_cell<C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
   k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
   k2_gdiag<<<gc, kThreads, 0, st>>>(D);
+  if (!h->mgl.empty()) mg_setup(h);
   CK2(cudaGetLastError());
-  grte_status s = gmres2(h, true, (K + 1) * nc, its);
+  grte_status s = GRTE_OK;
+  if (!h->mgl.empty()) {
+    s = gmres2(h, true, true, (K + 1) * nc, its);
+    if (s != GRTE_OK) return s;
+    h->stats.krylov_iters += its;
+    h->stats.krylov_iters_mg += its;
+  }
+  s = gmres2(h, true, false, (K + 1) * nc, its);
   if (s != GRTE_OK) return s;
   h->stats.krylov_iters += its;
   k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
@@ -992,9 +1195,10 @@ static grte_status step2(grte2d_t h) {
   k2_gdiag<<<gc, kThreads, 0, st>>>(D);
   CK2(cudaGetLastError());
   its = 0;
-  s = gmres2(h, false, K * nc, its);
+  s = gmres2(h, false, false, K * nc, its);
   if (s != GRTE_OK) return s;
   h->stats.krylov_iters += its;
+  h->stats.krylov_iters_corr += its;
   // projection: E = a c U + eps E_J, O from E (vertex map with the O^n data), U = T^4
   k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
   k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{D.E, nc, nullptr}, h->V);
@@ -1097,6 +1301,29 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
             alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc) &&
             alloc2(h, &h->hcol, kMaxRestart2 + 2) && alloc2(h, &h->tk, K * nc);
   if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
+  if (h->opt.prec2d == GRTE_PREC2D_MULTIGRID) {
+    // level 0: the cells (one unknown each); then 2x2 aggregation with one unknown per
+    // colour class, until the level has at most mg::kDenseMax unknowns
+    mg::Level L{};
+    L.nx = g.Nx; L.ny = g.Ny; L.ncomp = 1;
+    L.perx = g.bcx == GRTE_BC_PERIODIC; L.pery = g.bcy == GRTE_BC_PERIODIC;
+    for (;;) {
+      L.ncell = (int64_t)L.nx * L.ny;
+      L.n = L.ncell * L.ncomp;
+      if (!alloc2(h, &L.coef, 9 * L.ncomp * L.n) || !alloc2(h, &L.idiag, L.n) || !alloc2(h, &L.x, L.n) ||
+          !alloc2(h, &L.xt, L.n) || !alloc2(h, &L.b, L.n))
+        return fail2(h, GRTE_ENOMEM, "cudaMalloc multigrid");
+      h->mgl.push_back(L);
+      if (L.n <= mg::kDenseMax) break;
+      L.nx = (L.nx + 1) / 2;
+      L.ny = (L.ny + 1) / 2;
+      L.ncomp = 2;
+    }
+    if (!alloc2(h, &h->mg_M, mg::kDenseMax * mg::kDenseMax) || !alloc2(h, &h->mg_inv, mg::kDenseMax * mg::kDenseMax))
+      return fail2(h, GRTE_ENOMEM, "cudaMalloc multigrid");
+  } else if (h->opt.prec2d != GRTE_PREC2D_BLOCK) {
+    return fail2(h, GRTE_EINVAL, "prec2d must be GRTE_PREC2D_MULTIGRID or GRTE_PREC2D_BLOCK");
+  }
   D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
   CK2(cudaMemcpy(h->dmu, h->hmu.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
   CK2(cudaMemcpy(h->deta, h->heta.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
@@ -1149,6 +1376,8 @@ grte_status grte2d_step(grte2d_t h, int64_t n) {
   if (!h->state_set) return fail2(h, GRTE_ESTATE, "state not set");
   if (n < 0) return fail2(h, GRTE_EINVAL, "n < 0");
   h->stats.krylov_iters = 0;
+  h->stats.krylov_iters_corr = 0;
+  h->stats.krylov_iters_mg = 0;
   for (int64_t i = 0; i < n; ++i) {
     grte_status s = step2(h);
     if (s != GRTE_OK) return s;

@@ -43,14 +43,16 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("energy_every", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("prec2d", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("krylov_iters", ctypes.c_int64),
                 ("krylov_cycles", ctypes.c_int64), ("newton_iters_max", ctypes.c_int64),
                 ("newton_iters_mean", ctypes.c_double), ("status_flags", ctypes.c_int64),
-                ("line_threads", ctypes.c_int64), ("line_smem", ctypes.c_int64)]
+                ("line_threads", ctypes.c_int64), ("line_smem", ctypes.c_int64),
+                ("krylov_iters_corr", ctypes.c_int64), ("krylov_iters_mg", ctypes.c_int64)]
 
 
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",
@@ -66,6 +68,7 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte2d_set_guess", "grte2d_set_newton_start", "grte2d_set_sample_logging",
             "grte2d_get_newton_samples"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
+PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
@@ -414,7 +417,8 @@ class Grte2D:
 
     def __init__(self, nx, ny, sigma, dt, eps, kind=SIGMA_T3, bc_x=BC_INFLOW, bc_y=BC_INFLOW, b_x0=0.0, b_x1=0.0,
                  b_y0=0.0, b_y1=0.0, mu=None, eta=None, w=None, lx=1.0, ly=1.0, a=1.0, c=1.0, Cv=1.0,
-                 krylov_rtol=1e-13, krylov_restart=30, krylov_maxcycles=30, newton_maxit=60, stream=None):
+                 krylov_rtol=1e-13, krylov_restart=30, krylov_maxcycles=30, newton_maxit=60, stream=None,
+                 prec=0):
         L = lib()
         sig = _f64(np.broadcast_to(np.asarray(sigma, dtype=np.float64).ravel(), (nx * ny,)))
         mu, eta, w = _f64(mu), _f64(eta), _f64(w)
@@ -429,6 +433,7 @@ class Grte2D:
         opt.krylov_maxcycles = krylov_maxcycles
         opt.newton_maxit = newton_maxit
         opt.stream = stream
+        opt.prec2d = prec
         h = ctypes.c_void_p()
         st = L.grte2d_create(ctypes.byref(inst), ctypes.byref(opt), ctypes.byref(h))
         self.h = h

@@ -78,7 +78,8 @@ def test_checkerboard_marshak_one_step_stages(G):
     h.close()
 
 
-def test_checkerboard_warm_inflow_three_steps(G):
+@pytest.mark.parametrize("prec", ["block", "multigrid"])
+def test_checkerboard_warm_inflow_three_steps(G, prec):
     # a warm slab (T ~ 0.3-0.45) with a moderate inflow: no cell reaches R <= 0
     mu, eta, w = s8_pairs_2d()
     nx, ny = 12, 10
@@ -86,13 +87,13 @@ def test_checkerboard_warm_inflow_three_steps(G):
     T0 = 0.3 * (1.0 + 0.5 * rng.random(nx * ny))
     P = o2.Problem2D(Nx=nx, Ny=ny, mu=mu, eta=eta, w=w, sig=checkerboard(nx, ny, 2), eps=1e-3,
                      dt=0.5 / nx, kind="t3", bx0=0.2)
-    h = _pair(G, P, T0)
+    h = _pair(G, P, T0, prec=G.PREC2D_BLOCK if prec == "block" else G.PREC2D_MULTIGRID)
     S3 = o2.run(P, o2.equilibrium_state(P, T0), 3)
     h.step(3)
     eT = _rel(h.T(), S3.T)
     eE = _rel(h.E(), S3.E)
     eO = float(np.max(np.abs(h.O() - S3.O)) / np.max(np.abs(S3.O)))
-    print("three steps: T %.3e E %.3e O %.3e" % (eT, eE, eO))
+    print("three steps (%s): T %.3e E %.3e O %.3e" % (prec, eT, eE, eO), h.stats())
     assert eT < TOL and eE < TOL and eO < 1e3 * TOL
     h.close()
 
@@ -117,7 +118,8 @@ def test_transport_regime_all_walls_inflow(G):
     h.close()
 
 
-def test_periodic_energy_conserved_on_gpu(G):
+@pytest.mark.parametrize("prec", ["block", "multigrid"])
+def test_periodic_energy_conserved_on_gpu(G, prec):
     mu, eta, w = s8_pairs_2d()
     P = o2.Problem2D(Nx=10, Ny=7, mu=mu, eta=eta, w=w, sig=1.3, eps=1e-2, dt=0.03, kind="const",
                      bcx="periodic", bcy="periodic")
@@ -125,7 +127,7 @@ def test_periodic_energy_conserved_on_gpu(G):
     T0 = 0.4 + 0.6 * rng.random(P.nc)
     E0 = (T0 ** 4)[:, None] * (1.0 + 0.2 * rng.random((P.nc, P.K)))
     O0 = np.zeros((P.nv, P.K))
-    h = _pair(G, P, T0, E0, O0)
+    h = _pair(G, P, T0, E0, O0, prec=G.PREC2D_BLOCK if prec == "block" else G.PREC2D_MULTIGRID)
     e0 = h.energy()
     assert abs(e0 - o2.energy(P, o2.State2D(E=E0, O=O0, U=T0 ** 4, T=T0))) < 1e-14 * e0
     for _ in range(3):
