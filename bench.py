@@ -486,30 +486,46 @@ def run_2d(args):
     sig, T0, dt, eps = checker2d_inputs(n)
     stream = torch.cuda.current_stream()
     prec = G.PREC2D_MULTIGRID if args.prec2d == "multigrid" else G.PREC2D_BLOCK
-    h = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream, prec=prec)
-    h.set_state(T0)
+    precision = G.MIXED if args.precision == "mixed" else G.FP64
     allow = (5,)        # cells reaching R <= 0 at this dt (see the workload's readings)
-    for _ in range(args.warmup):
-        h.step(1, allow=allow)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(local)
-    torch.cuda.synchronize()
-    clocks.start()
-    t_ms, its, its_corr, its_mg = 0.0, 0, 0, 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.step(1, allow=allow)
-        e1.record(stream)
+
+    def timed(precision_, clocks=None):
+        h_ = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream, prec=prec,
+                      precision=precision_)
+        h_.set_state(T0)
+        for _ in range(args.warmup):
+            h_.step(1, allow=allow)
         torch.cuda.synchronize()
-        t_ms += e0.elapsed_time(e1)
-        st = h.stats(allow=allow)
-        its += st["krylov_iters"]
-        its_corr += st["krylov_iters_corr"]
-        its_mg += st["krylov_iters_mg"]
+        if clocks:
+            clocks.start()
+        t, it = 0.0, [0, 0, 0]
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h_.step(1, allow=allow)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1)
+            st = h_.stats(allow=allow)
+            it[0] += st["krylov_iters"]
+            it[1] += st["krylov_iters_corr"]
+            it[2] += st["krylov_iters_mg"]
+        return h_, t, it
+
+    clocks = ClockSampler(local)
+    h, t_ms, (its, its_corr, its_mg) = timed(precision, clocks)
     clk = clocks.stop()
+    vs_fp64 = None
+    if precision == G.MIXED and not args.no_fp64_compare:
+        h64, t64, _ = timed(G.FP64)
+        Tm, T64 = h.T(allow), h64.T(allow)
+        vs_fp64 = {"fp64_ms_per_step": t64 / args.steps, "fp64_value": n * n * 40 * args.steps / (t64 * 1e-3),
+                   "t_max_rel_err_vs_fp64": float(np.max(np.abs(Tm - T64) / np.maximum(np.abs(T64), 1e-300))),
+                   "steps_compared": args.warmup + args.steps}
+        h64.close()
     upd = n * n * 40
     value, t_ms = job_throughput(upd, args.steps, t_ms, world, None)
     T, E, O = h.T(allow), h.E(allow), h.O(allow)
@@ -530,8 +546,10 @@ def run_2d(args):
     ach = upd * 24 / step_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
+            "vs_baseline": None, "dtype": "f32 Krylov cycles / f64 residual, Newton, sums" if precision == G.MIXED else "f64",
+            "data": "synthetic (seeded; no dataset)",
             "config": {"workload": "2d_checkerboard_%dx%d_s8" % (n, n), "n": n, "pairs": 20, "eps": eps,
+                       "precision": args.precision,
                        "sigma0": [1, 100], "blocks": 8, "dt": "0.5 dx", "T_in": 1e-2, "prec2d": args.prec2d,
                        "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},
             "gpu_launches": None,
@@ -541,7 +559,7 @@ def run_2d(args):
                          "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
                          "note": "24 B per cell-angle update over the step time"},
             "krylov_iters_per_step": its / args.steps, "krylov_iters_corr_per_step": its_corr / args.steps,
-            "krylov_iters_mg_per_step": its_mg / args.steps,
+            "krylov_iters_mg_per_step": its_mg / args.steps, "vs_fp64": vs_fp64,
             "status_flags": h.stats(allow=allow)["status_flags"],
             "clocks": clk}
     if not args.no_cpu_baseline:

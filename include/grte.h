@@ -283,13 +283,16 @@ typedef struct {
   double dt, a, c, Cv, eps;
 } grte_instance2d;
 
-/* Create a 2D handle (inputs copied; opt may be NULL: precision must be GRTE_FP64,
- * krylov_rtol (root mean square over cells of the preconditioned residual relative to
- * each cell's own magnitude, default 1e-13; a restart cycle that stalls below 1e-9, the
- * rounding floor of the residual, is accepted too), krylov_restart (up to 64; 30 if
- * the 1D default 10 is given),
- * krylov_maxcycles and newton_maxit apply).  The state is unset until
- * grte2d_set_state.  Errors: EINVAL, ENOMEM, ECUDA. */
+/* Create a 2D handle (inputs copied; opt may be NULL: precision, krylov_rtol (root mean
+ * square over cells of the preconditioned residual relative to each cell's own
+ * magnitude, default 1e-13; a restart cycle that stalls below 1e-9, the rounding floor
+ * of the residual, is accepted too), krylov_restart (up to 64; 30 if the 1D default 10
+ * is given), krylov_maxcycles, newton_maxit, stream and prec2d apply).  GRTE_MIXED: each
+ * restart forms the residual and updates the unknowns in binary64, but the cycle's
+ * Krylov process (basis, matrix, block preconditioner, Gram-Schmidt) runs in binary32
+ * and ends after a 1e5 reduction of the residual (iterative refinement); krylov_rtol is
+ * floored at 1e-9; coefficients, Newton and the energy sums stay binary64.  The state is
+ * unset until grte2d_set_state.  Errors: EINVAL, ENOMEM, ECUDA. */
 grte_status grte2d_create(const grte_instance2d* inst, const grte_options* opt, grte2d_t* out);
 /* T: nx*ny; E: nx*ny*K as [cell][k] and O: (nx+1)*(ny+1)*K as [vertex][k] (vertex
  * index j*(nx+1) + i), or E = O = NULL for the equilibrium I = a c T^4. */

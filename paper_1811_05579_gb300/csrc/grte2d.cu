@@ -28,11 +28,15 @@ namespace grte2 {
 
 constexpr double kGuessGate2 = 1.1220184543019633;   // 10^0.05: learned-start gate (k2_newton)
 constexpr int kMgStageCycles = 4;   // restart cycles of the multigrid-preconditioned stage
+constexpr double kMixedRtol = 1e-9;  // mixed precision: floor of the Krylov tolerance
+constexpr double kInnerReduce = 1e-5; // mixed precision: residual reduction of one binary32 cycle
 
 constexpr int kMaxPairs = 64;
 constexpr int kMaxRestart2 = 64;
 constexpr int kThreads = 256;
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs: blocks of the first reduction stage
+constexpr int kDotBlocks = 608;   // 4 x 152: blocks of the Gram-Schmidt dot products
+constexpr int kAxpyBlocks = 1216; // 8 x 152: blocks of the streaming vector updates
 
 struct G2 {
   int Nx, Ny, K, bcx, bcy, kind;
@@ -134,96 +138,115 @@ __global__ void k2_acU(D2 D) {
 }
 
 // ----------------------------------------------------------------------------- stencils
+// Coefficients the Krylov-loop stencils read, in precision S: binary64 (the D2 arrays)
+// or, in the mixed mode's binary32 Krylov cycles, float copies made once per solve
+// (cell, vertex and preconditioner values) and per restart (the Krylov cell scale).
+template <typename S>
+struct CV {
+  const S *mu, *eta, *w;         // [K]
+  const S *kc, *A, *alpha;       // [cell]
+  const S* dv;                   // [vertex]
+  const S *gd, *gdi, *pdi;       // [k][cell], [k][cell], [cell]
+  const S *wsc, *iwsc;           // [cell]
+  S h2x, h2y, te;
+};
+
 // Per-pair cell field u_k(c) = (uk[k*ks + c] + ub[c]) * sc[c] (any part may be absent).
-struct UField {
-  const double* uk;
+template <typename S>
+struct UFieldT {
+  const S* uk;
   int64_t ks;
-  const double* ub;
-  const double* sc = nullptr;
-  __device__ __forceinline__ double at(int k, int c) const {
-    double v = 0.0;
+  const S* ub;
+  const S* sc = nullptr;
+  __device__ __forceinline__ S at(int k, int c) const {
+    S v = S(0);
     if (uk) v += uk[(int64_t)k * ks + c];
     if (ub) v += ub[c];
     return sc ? v * sc[c] : v;
   }
   __device__ __forceinline__ bool any() const { return uk || ub; }
 };
+using UField = UFieldT<double>;
 
 // O at a node-equation vertex: o - d (D_k u)  (o = d eps^2 O^n/(c dt) with data).
-template <bool DATA>
-__device__ double O_node(const D2& D, const UField& u, int k, int i, int j) {
+template <typename S, bool DATA>
+__device__ S O_node(const D2& D, const CV<S>& cv, const UFieldT<S>& u, int k, int i, int j) {
   const G2& g = D.g;
   const int64_t v = (int64_t)j * (g.Nx + 1) + i;
-  double r = DATA ? D.odv[v] * D.O[(int64_t)k * g.nv + v] : 0.0;
+  S r = S(0);
+  if constexpr (DATA) r = D.odv[v] * D.O[(int64_t)k * g.nv + v];
   if (u.any()) {
     const int c00 = cell_of(g, i - 1, j - 1), c10 = cell_of(g, i, j - 1), c01 = cell_of(g, i - 1, j),
               c11 = cell_of(g, i, j);
-    const double u00 = u.at(k, c00), u10 = u.at(k, c10), u01 = u.at(k, c01), u11 = u.at(k, c11);
-    const double grad = D.mu[k] * ((u10 + u11) - (u00 + u01)) * g.h2x + D.eta[k] * ((u01 + u11) - (u00 + u10)) * g.h2y;
-    r -= D.dv[v] * grad;
+    const S u00 = u.at(k, c00), u10 = u.at(k, c10), u01 = u.at(k, c01), u11 = u.at(k, c11);
+    const S grad = cv.mu[k] * ((u10 + u11) - (u00 + u01)) * cv.h2x + cv.eta[k] * ((u01 + u11) - (u00 + u10)) * cv.h2y;
+    r -= cv.dv[v] * grad;
   }
   return r;
 }
 
 // Wall expression (Eq. bc-pre along the normal of `axis` at vertex (i, j)):
 //   Omega_k enters:  O = 2/eps (b - E_wall) - O_inner;  else  O = 2/eps (E_wall - b) - O_inner.
-template <bool DATA>
-__device__ double O_wall(const D2& D, const UField& u, int k, int i, int j, int axis, double Oinner) {
+template <typename S, bool DATA>
+__device__ S O_wall(const D2& D, const CV<S>& cv, const UFieldT<S>& u, int k, int i, int j, int axis, S Oinner) {
   const G2& g = D.g;
-  double comp, b;
+  S comp;
+  double b;
   int side, ca, cb;
   if (axis == 0) {
     side = i == 0 ? 0 : 1;
-    comp = D.mu[k];
+    comp = cv.mu[k];
     b = side == 0 ? g.bx0 : g.bx1;
     const int p = side == 0 ? 0 : g.Nx - 1;
     ca = cell_of(g, p, j - 1);
     cb = cell_of(g, p, j);
   } else {
     side = j == 0 ? 0 : 1;
-    comp = D.eta[k];
+    comp = cv.eta[k];
     b = side == 0 ? g.by0 : g.by1;
     const int q = side == 0 ? 0 : g.Ny - 1;
     ca = cell_of(g, i - 1, q);
     cb = cell_of(g, i, q);
   }
-  const bool enters = side == 0 ? comp > 0.0 : comp < 0.0;
-  const double sgn = enters ? 1.0 : -1.0;
-  double Ew = 0.0;
+  const bool enters = side == 0 ? comp > S(0) : comp < S(0);
+  const S sgn = enters ? S(1) : S(-1);
+  S Ew = S(0);
   if (u.any()) {
     int n = 0;
     if (ca >= 0) { Ew += u.at(k, ca); ++n; }
     if (cb >= 0) { Ew += u.at(k, cb); ++n; }
-    if (n == 2) Ew *= 0.5;
+    if (n == 2) Ew *= S(0.5);
   }
-  return sgn * g.te * ((DATA ? b : 0.0) - Ew) - Oinner;
+  S bd = S(0);
+  if constexpr (DATA) bd = b;
+  return sgn * cv.te * (bd - Ew) - Oinner;
 }
 
-template <bool DATA>
-__device__ double O_at(const D2& D, const UField& u, int k, int i, int j) {
+template <typename S, bool DATA>
+__device__ S O_at(const D2& D, const CV<S>& cv, const UFieldT<S>& u, int k, int i, int j) {
   const G2& g = D.g;
   const int kind = vkind(g, i, j);
-  if (kind == 0) return O_node<DATA>(D, u, k, i, j);
+  if (kind == 0) return O_node<S, DATA>(D, cv, u, k, i, j);
   const int ii = i == 0 ? 1 : g.Nx - 1, jj = j == 0 ? 1 : g.Ny - 1;
-  if (kind == 2) return O_wall<DATA>(D, u, k, i, j, 0, O_node<DATA>(D, u, k, ii, j));
-  if (kind == 3) return O_wall<DATA>(D, u, k, i, j, 1, O_node<DATA>(D, u, k, i, jj));
+  if (kind == 2) return O_wall<S, DATA>(D, cv, u, k, i, j, 0, O_node<S, DATA>(D, cv, u, k, ii, j));
+  if (kind == 3) return O_wall<S, DATA>(D, cv, u, k, i, j, 1, O_node<S, DATA>(D, cv, u, k, i, jj));
   // corner: mean of the two walls; each wall's inner vertex lies on the other wall
-  const double Oin_x = O_wall<DATA>(D, u, k, ii, j, 1, O_node<DATA>(D, u, k, ii, jj));
-  const double Oin_y = O_wall<DATA>(D, u, k, i, jj, 0, O_node<DATA>(D, u, k, ii, jj));
-  return 0.5 * (O_wall<DATA>(D, u, k, i, j, 0, Oin_x) + O_wall<DATA>(D, u, k, i, j, 1, Oin_y));
+  const S Oin_x = O_wall<S, DATA>(D, cv, u, k, ii, j, 1, O_node<S, DATA>(D, cv, u, k, ii, jj));
+  const S Oin_y = O_wall<S, DATA>(D, cv, u, k, i, jj, 0, O_node<S, DATA>(D, cv, u, k, ii, jj));
+  return S(0.5) * (O_wall<S, DATA>(D, cv, u, k, i, j, 0, Oin_x) + O_wall<S, DATA>(D, cv, u, k, i, j, 1, Oin_y));
 }
 
 // V[k][v] = O_k at every vertex for the field u (and the data part with DATA); one
 // thread per (pair, vertex), consecutive threads on consecutive vertices.
-template <bool DATA>
-__global__ void k2_vertex(D2 D, UField u, double* __restrict__ V) {
+template <typename S, bool DATA>
+__global__ void k2_vertex(D2 D, CV<S> cv, UFieldT<S> u, S* __restrict__ V) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (t >= (int64_t)g.K * g.nv) return;
   const int tt = (int)t, nv = (int)g.nv;   // K nv < 2^31 (checked at creation)
   const int k = tt / nv, v = tt - k * nv;
   const int j = v / (g.Nx + 1), i = v - j * (g.Nx + 1);
-  V[t] = O_at<DATA>(D, u, k, i, j);
+  V[t] = O_at<S, DATA>(D, cv, u, k, i, j);
 }
 
 enum { C_MV_PRED = 0, C_MV_CORR = 1, C_DIVK = 2, C_FDIV = 3 };
@@ -235,67 +258,70 @@ enum { C_MV_PRED = 0, C_MV_CORR = 1, C_DIVK = 2, C_FDIV = 3 };
 // Eq. bc-pre to its own wall side as the 1D wall cell does: the low x side becomes
 // s 2/eps (b - E_cell) - (high side), i.e. mu (2 R - s 2/eps (b - E_cell))/dx, and
 // likewise for the other sides (s = +1 if Omega_k enters there, else -1).
+template <typename S>
 struct CellSides {
-  double wL, wR, wB, wT, ed, bt;
+  S wL, wR, wB, wT, ed, bt;
 };
 
-__device__ __forceinline__ CellSides cell_sides(const D2& D, int k, int p, int q) {
+template <typename S>
+__device__ __forceinline__ CellSides<S> cell_sides(const D2& D, const CV<S>& cv, int k, int p, int q) {
   const G2& g = D.g;
-  CellSides cs{-1.0, 1.0, -1.0, 1.0, 0.0, 0.0};
-  const double mu = D.mu[k], eta = D.eta[k], te = g.te, ix = 2.0 * g.h2x, iy = 2.0 * g.h2y;
+  CellSides<S> cs{S(-1), S(1), S(-1), S(1), S(0), S(0)};
+  const S mu = cv.mu[k], eta = cv.eta[k], te = cv.te, ix = S(2) * cv.h2x, iy = S(2) * cv.h2y;
   if (g.bcx == GRTE_BC_INFLOW) {
     if (p == 0) {
-      const double s = mu > 0.0 ? 1.0 : -1.0;   // Omega_k enters at x = 0 when mu > 0
-      cs.wL = 0.0;
-      cs.wR = 2.0;
+      const S s = mu > S(0) ? S(1) : S(-1);   // Omega_k enters at x = 0 when mu > 0
+      cs.wL = S(0);
+      cs.wR = S(2);
       cs.ed += mu * s * te * ix;
-      cs.bt -= mu * s * te * g.bx0 * ix;
+      cs.bt -= mu * s * te * S(g.bx0) * ix;
     }
     if (p == g.Nx - 1) {
-      const double s = mu < 0.0 ? 1.0 : -1.0;
-      if (p != 0) cs.wL = -2.0;
-      cs.wR = 0.0;
+      const S s = mu < S(0) ? S(1) : S(-1);
+      if (p != 0) cs.wL = S(-2);
+      cs.wR = S(0);
       cs.ed -= mu * s * te * ix;
-      cs.bt += mu * s * te * g.bx1 * ix;
+      cs.bt += mu * s * te * S(g.bx1) * ix;
     }
   }
   if (g.bcy == GRTE_BC_INFLOW) {
     if (q == 0) {
-      const double s = eta > 0.0 ? 1.0 : -1.0;
-      cs.wB = 0.0;
-      cs.wT = 2.0;
+      const S s = eta > S(0) ? S(1) : S(-1);
+      cs.wB = S(0);
+      cs.wT = S(2);
       cs.ed += eta * s * te * iy;
-      cs.bt -= eta * s * te * g.by0 * iy;
+      cs.bt -= eta * s * te * S(g.by0) * iy;
     }
     if (q == g.Ny - 1) {
-      const double s = eta < 0.0 ? 1.0 : -1.0;
-      if (q != 0) cs.wB = -2.0;
-      cs.wT = 0.0;
+      const S s = eta < S(0) ? S(1) : S(-1);
+      if (q != 0) cs.wB = S(-2);
+      cs.wT = S(0);
       cs.ed -= eta * s * te * iy;
-      cs.bt += eta * s * te * g.by1 * iy;
+      cs.bt += eta * s * te * S(g.by1) * iy;
     }
   }
   return cs;
 }
 
 // Streaming derivative of O_k at cell c (cell_sides), for pair k.
-template <bool DATA>
-__device__ __forceinline__ double cell_div(const D2& D, const double* __restrict__ V, const UField& u, int k, int64_t c) {
+template <typename S, bool DATA>
+__device__ __forceinline__ S cell_div(const D2& D, const CV<S>& cv, const S* __restrict__ V, const UFieldT<S>& u,
+                                      int k, int64_t c) {
   const G2& g = D.g;
   const int ci = (int)c;
   const int q = ci / g.Nx, p = ci - q * g.Nx;
   const int64_t v00 = (int64_t)q * (g.Nx + 1) + p, v10 = v00 + 1, v01 = v00 + g.Nx + 1, v11 = v01 + 1;
-  const double* Vk = V + (int64_t)k * g.nv;
+  const S* Vk = V + (int64_t)k * g.nv;
   const bool wall = (g.bcx == GRTE_BC_INFLOW && (p == 0 || p == g.Nx - 1)) ||
                     (g.bcy == GRTE_BC_INFLOW && (q == 0 || q == g.Ny - 1));
   if (!wall)
-    return D.mu[k] * ((Vk[v10] + Vk[v11]) - (Vk[v00] + Vk[v01])) * g.h2x +
-           D.eta[k] * ((Vk[v01] + Vk[v11]) - (Vk[v00] + Vk[v10])) * g.h2y;
-  const CellSides cs = cell_sides(D, k, p, q);
-  double div = D.mu[k] * g.h2x * (cs.wL * (Vk[v00] + Vk[v01]) + cs.wR * (Vk[v10] + Vk[v11])) +
-               D.eta[k] * g.h2y * (cs.wB * (Vk[v00] + Vk[v10]) + cs.wT * (Vk[v01] + Vk[v11]));
+    return cv.mu[k] * ((Vk[v10] + Vk[v11]) - (Vk[v00] + Vk[v01])) * cv.h2x +
+           cv.eta[k] * ((Vk[v01] + Vk[v11]) - (Vk[v00] + Vk[v10])) * cv.h2y;
+  const CellSides<S> cs = cell_sides<S>(D, cv, k, p, q);
+  S div = cv.mu[k] * cv.h2x * (cs.wL * (Vk[v00] + Vk[v01]) + cs.wR * (Vk[v10] + Vk[v11])) +
+          cv.eta[k] * cv.h2y * (cs.wB * (Vk[v00] + Vk[v10]) + cs.wT * (Vk[v01] + Vk[v11]));
   if (u.any()) div += cs.ed * u.at(k, (int)c);
-  if (DATA) div += cs.bt;
+  if constexpr (DATA) div += cs.bt;
   return div;
 }
 
@@ -308,23 +334,23 @@ __device__ __forceinline__ double cell_div(const D2& D, const double* __restrict
 // S_k the streaming derivative of O_k at the cell (cell_sides).  z is read scaled by
 // zs[c] when zs is given (the Krylov unknowns are cell-scaled).  The sums over pairs
 // (rho row, C_FDIV) are k2_cellsum.
-template <int MODE, bool DATA>
-__global__ void k2_cell(D2 D, const double* __restrict__ V, UField u, const double* __restrict__ z,
-                        double* __restrict__ y, const double* __restrict__ zs, double* __restrict__ tk) {
+template <typename S, int MODE, bool DATA>
+__global__ void k2_cell(D2 D, CV<S> cv, const S* __restrict__ V, UFieldT<S> u, const S* __restrict__ z,
+                        S* __restrict__ y, const S* __restrict__ zs, S* __restrict__ tk) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (t >= (int64_t)g.K * g.nc) return;
   const int tt = (int)t, nc = (int)g.nc;
   const int k = tt / nc;
   const int64_t c = tt - k * nc;
-  const double div = cell_div<DATA>(D, V, u, k, c);
-  const double kc = D.kc[c];
-  const double f = zs ? zs[c] : 1.0;
+  const S div = cell_div<S, DATA>(D, cv, V, u, k, c);
+  const S kc = cv.kc[c];
+  const S f = zs ? zs[c] : S(1);
   if (MODE == C_MV_PRED) {
-    y[t] = D.A[c] * f * z[t] + D.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + kc * div;
+    y[t] = cv.A[c] * f * z[t] + cv.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + kc * div;
     tk[t] = kc * div;
   } else if (MODE == C_MV_CORR) {
-    y[t] = D.A[c] * f * z[t] + kc * div;
+    y[t] = cv.A[c] * f * z[t] + kc * div;
   } else if (MODE == C_DIVK) {
     y[t] = kc * div;
   } else {
@@ -334,17 +360,17 @@ __global__ void k2_cell(D2 D, const double* __restrict__ V, UField u, const doub
 
 // Per-cell sums over pairs (fixed order): C_MV_PRED: y_rho = alpha z_rho + sum_k w_k t_k;
 // C_FDIV: y = sum_k w_k t_k.
-template <int MODE>
-__global__ void k2_cellsum(D2 D, const double* __restrict__ tk, const double* __restrict__ z,
-                           double* __restrict__ y, const double* __restrict__ zs) {
+template <typename S, int MODE>
+__global__ void k2_cellsum(D2 D, CV<S> cv, const S* __restrict__ tk, const S* __restrict__ z, S* __restrict__ y,
+                           const S* __restrict__ zs) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
-  double acc = 0.0;
-  for (int k = 0; k < g.K; ++k) acc += D.w[k] * tk[(int64_t)k * g.nc + c];
+  S acc = S(0);
+  for (int k = 0; k < g.K; ++k) acc += cv.w[k] * tk[(int64_t)k * g.nc + c];
   if (MODE == C_MV_PRED) {
-    const double f = zs ? zs[c] : 1.0;
-    y[(int64_t)g.K * g.nc + c] = D.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + acc;
+    const S f = zs ? zs[c] : S(1);
+    y[(int64_t)g.K * g.nc + c] = cv.alpha[c] * f * z[(int64_t)g.K * g.nc + c] + acc;
   } else {
     y[c] = acc;
   }
@@ -354,9 +380,9 @@ __global__ void k2_cellsum(D2 D, const double* __restrict__ tk, const double* __
 // the cell contribute kappa (side weight) (D* coefficient) (-d) (D_k coefficient), a
 // wall cell its own E term kappa ed; wall vertices of an opposite side (corner cells)
 // are left out.
-__device__ double gdiag(const D2& D, int k, int p, int q) {
+__device__ double gdiag(const D2& D, const CV<double>& cv, int k, int p, int q) {
   const G2& g = D.g;
-  const CellSides cs = cell_sides(D, k, p, q);
+  const CellSides<double> cs = cell_sides<double>(D, cv, k, p, q);
   const double mx = D.mu[k] * g.h2x, ey = D.eta[k] * g.h2y;
   const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
   // D* coefficient of vertex t of the cell with the side weights
@@ -381,27 +407,27 @@ __device__ double gdiag(const D2& D, int k, int p, int q) {
 // Correction: z_k = r_k/(A + g_k).  The result is multiplied by the cell's Krylov
 // scale w (the GMRES runs on w-scaled unknowns: D_w P^{-1} M D_w^{-1}).
 // (the diagonals g_k and the reciprocals come from k2_gdiag, once per solve)
-template <bool PRED>
-__global__ void k2_prec(D2 D, const double* __restrict__ r, double* __restrict__ z) {
+template <typename S, bool PRED>
+__global__ void k2_prec(D2 D, CV<S> cv, const S* __restrict__ r, S* __restrict__ z) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
-  const double ws = D.wsc[c];
+  const S ws = cv.wsc[c];
   if (!PRED) {
-    for (int k = 0; k < g.K; ++k) z[(int64_t)k * g.nc + c] = ws * r[(int64_t)k * g.nc + c] * D.gdi[(int64_t)k * g.nc + c];
+    for (int k = 0; k < g.K; ++k) z[(int64_t)k * g.nc + c] = ws * r[(int64_t)k * g.nc + c] * cv.gdi[(int64_t)k * g.nc + c];
     return;
   }
-  const double al = D.alpha[c];
-  double num = r[(int64_t)g.K * g.nc + c];
+  const S al = cv.alpha[c];
+  S num = r[(int64_t)g.K * g.nc + c];
   for (int k = 0; k < g.K; ++k) {
     const int64_t o = (int64_t)k * g.nc + c;
-    num -= D.w[k] * D.gd[o] * r[o] * D.gdi[o];
+    num -= cv.w[k] * cv.gd[o] * r[o] * cv.gdi[o];
   }
-  const double rho = num * D.pdi[c];
+  const S rho = num * cv.pdi[c];
   z[(int64_t)g.K * g.nc + c] = ws * rho;
   for (int k = 0; k < g.K; ++k) {
     const int64_t o = (int64_t)k * g.nc + c;
-    z[o] = ws * (r[o] - (al + D.gd[o]) * rho) * D.gdi[o];
+    z[o] = ws * (r[o] - (al + cv.gd[o]) * rho) * cv.gdi[o];
   }
 }
 
@@ -501,7 +527,7 @@ __global__ void k2_pc_final(D2 D, const double* __restrict__ r, const double* __
 // gd[k][c] = diagonal of G_k at cell c (for the preconditioner), at the current coefficients
 // and the reciprocals the preconditioner needs: gdi = 1/(A + g_k) and, per cell, the
 // inverse of the arrow block's rho pivot alpha + sum_k w_k g_k (A - alpha)/(A + g_k).
-__global__ void k2_gdiag(D2 D) {
+__global__ void k2_gdiag(D2 D, CV<double> cv) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
@@ -510,7 +536,7 @@ __global__ void k2_gdiag(D2 D) {
   double den = al;
   for (int k = 0; k < g.K; ++k) {
     const int64_t o = (int64_t)k * g.nc + c;
-    const double gk = gdiag(D, k, p, q), inv = 1.0 / (A + gk);
+    const double gk = gdiag(D, cv, k, p, q), inv = 1.0 / (A + gk);
     D.gd[o] = gk;
     D.gdi[o] = inv;
     den += D.w[k] * gk * (A - al) * inv;
@@ -697,32 +723,39 @@ __global__ void k2_newton(D2 D) {
 
 // ----------------------------------------------------------------------------- vector kernels
 // Partial dot products of w with V_0..V_{nvec-1} (stride n): one value per (block, vec),
-// fixed order; k2_reduce sums the block partials (one block per value).
-__global__ void k2_mdot(const double* __restrict__ w, const double* __restrict__ V, int nvec, int64_t n,
-                        double* __restrict__ part) {
-  __shared__ double red[kThreads / 32][kMaxRestart2 + 1];
+// fixed order; k2_reduce sums the block partials (one block per value).  The vectors go
+// in chunks of C (w read once per chunk), each thread keeping C sums in the vectors'
+// precision S; the block sums are binary64.
+template <typename S, int C>
+__global__ void __launch_bounds__(kThreads) k2_mdot(const S* __restrict__ w, const S* __restrict__ V, int nvec,
+                                                     int64_t n, double* __restrict__ part) {
+  __shared__ double red[kThreads / 32][C];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i0 = 0; i0 < nvec; i0 += 8) {
-    double acc[8];
-    for (int t = 0; t < 8; ++t) acc[t] = 0.0;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-      const double wj = w[j];
+  for (int i0 = 0; i0 < nvec; i0 += C) {
+    const int nv = min(C, nvec - i0);
+    const S* Vb = V + (int64_t)i0 * n;
+    S acc[C];
 #pragma unroll
-      for (int t = 0; t < 8; ++t)
-        if (i0 + t < nvec) acc[t] += wj * V[(int64_t)(i0 + t) * n + j];
+    for (int t = 0; t < C; ++t) acc[t] = S(0);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const S wj = w[j];
+#pragma unroll
+      for (int t = 0; t < C; ++t)
+        if (t < nv) acc[t] = fma(wj, Vb[(int64_t)t * n + j], acc[t]);
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < C; ++t) {
       double v = acc[t];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && i0 + t < nvec) red[wid][i0 + t] = v;
+      if (lane == 0) red[wid][t] = v;
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][i];
-    part[(int64_t)i * gridDim.x + blockIdx.x] = t;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+      double u = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) u += red[q][t];
+      part[(int64_t)(i0 + t) * gridDim.x + blockIdx.x] = u;
+    }
+    __syncthreads();
   }
 }
 
@@ -746,29 +779,74 @@ __global__ void k2_hacc(double* __restrict__ hcol, const double* __restrict__ do
   if (i < n) hcol[i] = assign ? dots[i] : hcol[i] + dots[i];
 }
 
-// w -= sum_i coef[i] V_i
-__global__ void k2_maxpy(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ coef,
-                         int nvec, int64_t n) {
+// w -= sum_i coef[i] V_i (coefficients staged in shared memory in the vectors' precision,
+// four independent partial sums per element); with NORM also the block partials of
+// |w|^2 of the result (binary64).
+template <typename S, bool NORM>
+__global__ void __launch_bounds__(kThreads) k2_maxpy(S* __restrict__ w, const S* __restrict__ V,
+                                                      const double* __restrict__ coef, int nvec, int64_t n,
+                                                      double* __restrict__ part) {
+  __shared__ S cf[kMaxRestart2 + 1];
+  __shared__ double red[kThreads / 32];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cf[i] = S(coef[i]);
+  __syncthreads();
+  S nrm = S(0);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    double t = w[j];
-    for (int i = 0; i < nvec; ++i) t -= coef[i] * V[(int64_t)i * n + j];
-    w[j] = t;
+    S t0 = w[j], t1 = S(0), t2 = S(0), t3 = S(0);
+    int i = 0;
+    for (; i + 4 <= nvec; i += 4) {
+      t0 = fma(-cf[i], V[(int64_t)i * n + j], t0);
+      t1 = fma(-cf[i + 1], V[(int64_t)(i + 1) * n + j], t1);
+      t2 = fma(-cf[i + 2], V[(int64_t)(i + 2) * n + j], t2);
+      t3 = fma(-cf[i + 3], V[(int64_t)(i + 3) * n + j], t3);
+    }
+    for (; i < nvec; ++i) t0 = fma(-cf[i], V[(int64_t)i * n + j], t0);
+    const S r = (t0 + t1) + (t2 + t3);
+    w[j] = r;
+    if (NORM) nrm = fma(r, r, nrm);
+  }
+  if (NORM) {
+    double v = nrm;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) u += red[q];
+      part[blockIdx.x] = u;
+    }
   }
 }
 
-// x += sum_i coef[i] V_i
-__global__ void k2_update(double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ coef,
-                          int nvec, int64_t n) {
+// x += sum_i coef[i] V_i (x binary64; binary32 basis vectors: the combination is formed
+// in binary32 and added once)
+template <typename S>
+__global__ void k2_update(double* __restrict__ x, const S* __restrict__ V, const double* __restrict__ coef, int nvec,
+                          int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    double t = x[j];
-    for (int i = 0; i < nvec; ++i) t += coef[i] * V[(int64_t)i * n + j];
-    x[j] = t;
+    if constexpr (sizeof(S) == 8) {
+      double t = x[j];
+      for (int i = 0; i < nvec; ++i) t += coef[i] * V[(int64_t)i * n + j];
+      x[j] = t;
+    } else {
+      S t = S(0);
+      for (int i = 0; i < nvec; ++i) t = fma(S(coef[i]), V[(int64_t)i * n + j], t);
+      x[j] += (double)t;
+    }
   }
 }
 
-__global__ void k2_scale(double* __restrict__ x, double s, int64_t n) {
+template <typename S>
+__global__ void k2_scale(S* __restrict__ x, double s, int64_t n) {
+  const S f = S(s);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    x[j] *= s;
+    x[j] *= f;
+}
+
+// binary32 copy dst = src * f
+__global__ void k2_tof(const double* __restrict__ src, float* __restrict__ dst, int64_t n, double f) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = (float)(src[j] * f);
 }
 
 // y = b - y
@@ -883,6 +961,14 @@ struct grte2d_ctx {
   double *part = nullptr, *dots = nullptr, *coef = nullptr, *cscale = nullptr, *hcol = nullptr;
   double* tk = nullptr;   // [k][cell] per-pair cell values summed by k2_cellsum
   grte_mlp_t mlp = nullptr;   // learned Newton start (not owned)
+  CV<double> cv{};            // the binary64 coefficient view of D
+  // mixed precision: binary32 copies of the coefficients (cv32) and the binary32 Krylov
+  // cycle's buffers (basis, matrix-vector product, vertex values, per-pair cell values)
+  bool mixed = false;
+  CV<float> cv32{};
+  float *mu32 = nullptr, *eta32 = nullptr, *w32 = nullptr, *kc32 = nullptr, *A32 = nullptr, *alpha32 = nullptr;
+  float *dv32 = nullptr, *gd32 = nullptr, *gdi32 = nullptr, *pdi32 = nullptr, *wsc32 = nullptr, *iwsc32 = nullptr;
+  float *V32 = nullptr, *Kr32 = nullptr, *Vv32 = nullptr, *tk32 = nullptr;
   std::vector<mg::Level> mgl;        // multigrid levels of the Schur preconditioner (empty: per-cell block only)
   double *mg_M = nullptr, *mg_inv = nullptr;   // coarsest level: dense scratch and inverse
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
@@ -910,11 +996,18 @@ static bool alloc2(grte2d_t h, T** p, int64_t n) {
   return true;
 }
 
+template <typename S>
+static void launch_mdot(const S* w, const S* V, int nvec, int64_t n, double* part, cudaStream_t st) {
+  if (nvec <= 4) k2_mdot<S, 4><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+  else if (nvec <= 8) k2_mdot<S, 8><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+  else k2_mdot<S, 16><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+}
+
 // dots[i] = <w, V_i>, i < nvec, returned on the host.
 static grte_status mdot(grte2d_t h, const double* w, const double* V, int nvec, int64_t n, double* host) {
   cudaStream_t st = h->stream;
-  k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, V, nvec, n, h->part);
-  k2_reduce<<<nvec, kThreads, 0, st>>>(h->part, kRedBlocks, h->dots);
+  launch_mdot<double>(w, V, nvec, n, h->part, st);
+  k2_reduce<<<nvec, kThreads, 0, st>>>(h->part, kDotBlocks, h->dots);
   CK2(cudaGetLastError());
   CK2(cudaMemcpyAsync(host, h->dots, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
   CK2(cudaStreamSynchronize(st));
@@ -928,13 +1021,53 @@ static void apply_M(grte2d_t h, bool pred, const double* xin, double* y) {
   cudaStream_t st = h->stream;
   UField u{xin, D.g.nc, pred ? xin + (int64_t)D.g.K * D.g.nc : nullptr, D.iwsc};
   const int64_t K = D.g.K;
-  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, u, h->V);
+  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, u, h->V);
   if (pred) {
-    k2_cell<C_MV_PRED, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc, h->tk);
-    k2_cellsum<C_MV_PRED><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->tk, xin, y, D.iwsc);
+    k2_cell<double, C_MV_PRED, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
+    k2_cellsum<double, C_MV_PRED><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, h->tk, xin, y, D.iwsc);
   } else {
-    k2_cell<C_MV_CORR, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->V, u, xin, y, D.iwsc, h->tk);
+    k2_cell<double, C_MV_CORR, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
   }
+}
+
+// binary32 matrix and block preconditioner (mixed precision Krylov cycles)
+static void apply_M32(grte2d_t h, bool pred, const float* xin, float* y) {
+  D2& D = h->D;
+  cudaStream_t st = h->stream;
+  const int64_t K = D.g.K, nc = D.g.nc;
+  UFieldT<float> u{xin, nc, pred ? xin + K * nc : nullptr, h->cv32.iwsc};
+  k2_vertex<float, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv32, u, h->Vv32);
+  if (pred) {
+    k2_cell<float, C_MV_PRED, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
+                                                                         h->cv32.iwsc, h->tk32);
+    k2_cellsum<float, C_MV_PRED><<<grid_of(nc), kThreads, 0, st>>>(D, h->cv32, h->tk32, xin, y, h->cv32.iwsc);
+  } else {
+    k2_cell<float, C_MV_CORR, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
+                                                                         h->cv32.iwsc, h->tk32);
+  }
+}
+
+static void apply_P32(grte2d_t h, bool pred, const float* r, float* z) {
+  if (pred) k2_prec<float, true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
+  else k2_prec<float, false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
+}
+
+static void tof(grte2d_t h, const double* src, float* dst, int64_t n) {
+  k2_tof<<<kAxpyBlocks, kThreads, 0, h->stream>>>(src, dst, n, 1.0);
+}
+
+// binary32 copies of the coefficients a solve's Krylov cycles read (after k2_gdiag)
+static void mirror_coefficients(grte2d_t h) {
+  if (!h->mixed) return;
+  const D2& D = h->D;
+  const int64_t K = D.g.K, nc = D.g.nc;
+  tof(h, D.kc, h->kc32, nc);
+  tof(h, D.A, h->A32, nc);
+  tof(h, D.alpha, h->alpha32, nc);
+  tof(h, D.dv, h->dv32, D.g.nv);
+  tof(h, D.gd, h->gd32, K * nc);
+  tof(h, D.gdi, h->gdi32, K * nc);
+  tof(h, D.pdi, h->pdi32, nc);
 }
 
 // One V-cycle on level l (right side in mgl[l].b); returns the buffer holding the result.
@@ -981,8 +1114,8 @@ static void mg_setup(grte2d_t h) {
   for (int cy = 0; cy < ncy; ++cy)
     for (int cx = 0; cx < ncx; ++cx) {
       k2_probe_in<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->Kt);
-      k2_vertex<false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, UField{h->Kt, nc, nullptr}, h->V);
-      k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{h->Kt, nc, nullptr}, nullptr,
+      k2_vertex<double, false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
+      k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr,
                                                                    h->tk, nullptr, nullptr);
       k2_probe_out<<<grid_of(nc), kThreads, 0, st>>>(D, cx, cy, h->tk, L0.coef);
     }
@@ -1001,24 +1134,57 @@ static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double*
   D2& D = h->D;
   cudaStream_t st = h->stream;
   if (!pred) {
-    k2_prec<false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, r, z);
+    k2_prec<double, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
     return;
   }
   if (!use_mg) {
-    k2_prec<true><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, r, z);
+    k2_prec<double, true><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
     return;
   }
   const int64_t K = D.g.K, nc = D.g.nc;
   k2_pc_et<<<grid_of(K * nc), kThreads, 0, st>>>(D, r, h->Kt);
-  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, UField{h->Kt, nc, nullptr}, h->V);
-  k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{h->Kt, nc, nullptr}, nullptr, h->tk,
+  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
+  k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr, h->tk,
                                                                nullptr, nullptr);
   k2_pc_rhs<<<grid_of(nc), kThreads, 0, st>>>(D, r, h->tk, h->mgl[0].b);
   const double* rho = mg_vcycle(h, 0);
-  k2_vertex<false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, UField{nullptr, 0, rho}, h->V);
-  k2_cell<C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, rho}, nullptr, h->tk,
+  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, rho}, h->V);
+  k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, rho}, nullptr, h->tk,
                                                                nullptr, nullptr);
   k2_pc_final<<<grid_of((K + 1) * nc), kThreads, 0, st>>>(D, r, rho, h->tk, z);
+}
+
+// One Arnoldi step in precision S: w = V_{j+1} = D_w P^{-1} M D_w^{-1} V_j (binary32: the
+// binary32 matrix and block preconditioner), orthogonalised against V_0..V_j by classical
+// Gram-Schmidt twice (the coefficients stay on the device; the second pass's update also
+// gives |w|^2); hc receives the Hessenberg column, hc[j+1] = |w|^2 (w not normalised).
+template <typename S>
+static grte_status arnoldi_step(grte2d_t h, bool pred, bool mg_stage, S* V, int j, int64_t n, std::vector<double>& hc) {
+  cudaStream_t st = h->stream;
+  S* vj = V + (int64_t)j * n;
+  S* w = V + (int64_t)(j + 1) * n;
+  if constexpr (sizeof(S) == 8) {
+    apply_M(h, pred, vj, h->Kr);
+    apply_P(h, pred, mg_stage, h->Kr, w);
+  } else {
+    apply_M32(h, pred, vj, h->Kr32);
+    apply_P32(h, pred, h->Kr32, w);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_mdot<S>(w, V, j + 1, n, h->part, st);
+    k2_reduce<<<j + 1, kThreads, 0, st>>>(h->part, kDotBlocks, h->coef);
+    k2_hacc<<<1, kMaxRestart2 + 1, 0, st>>>(h->hcol, h->coef, j + 1, pass == 0);
+    if (pass == 0) {
+      k2_maxpy<S, false><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, nullptr);
+    } else {
+      k2_maxpy<S, true><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, h->part);
+      k2_reduce<<<1, kThreads, 0, st>>>(h->part, kAxpyBlocks, h->hcol + j + 1);
+    }
+  }
+  CK2(cudaGetLastError());
+  CK2(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
+  CK2(cudaStreamSynchronize(st));
+  return GRTE_OK;
 }
 
 // Restarted GMRES(m) with left preconditioning on M x = b (x holds the initial
@@ -1029,15 +1195,22 @@ static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double*
 // cell's unknowns are O(1), so the test |D_w P^{-1}(b - M x)|_2 <= rtol sqrt(n_cells)
 // bounds the residual of every cell relative to the cell's own magnitude (RMS).
 //
-// mg_stage (prediction, multigrid preconditioner): the same iteration with one scale
-// for all cells (w = 1/max|rho|).  The multigrid couples the cells, and under per-cell
-// scales its error terms from hot cells into cold ones are multiplied by the ratio of
-// their magnitudes (up to ~1e8 across a front), which stalls the iteration; with one
-// scale it converges in a few iterations to rtol relative to the largest cell.  It
-// ends there, or when a restart no longer gains 4x, or a cycle stops falling (less
-// than 2x over four iterations after a 1e6 reduction), without a verdict: the
-// per-cell scaled solve with the per-cell block preconditioner then runs from its
-// iterate and decides (the cold, opaque cells it still has to fix are nearly local).
+// Mixed precision: every restart still forms the residual and updates x in binary64,
+// but the cycle's Krylov process (basis, matrix, block preconditioner, Gram-Schmidt)
+// runs in binary32 and ends once it has reduced the residual by kInnerReduce (about
+// the most a binary32 cycle can do reliably): restarted GMRES as iterative refinement,
+// whose accuracy is set by the binary64 residual.  rtol is floored at kMixedRtol.
+//
+// mg_stage (prediction, multigrid preconditioner, binary64): the same iteration with
+// one scale for all cells (w = 1/max|rho|).  The multigrid couples the cells, and
+// under per-cell scales its error terms from hot cells into cold ones are multiplied by
+// the ratio of their magnitudes (up to ~1e8 across a front), which stalls the
+// iteration; with one scale it converges in a few iterations to rtol relative to the
+// largest cell.  It ends there, or when a restart no longer gains 4x, or a cycle stops
+// falling (less than 2x over four iterations after a 1e6 reduction), without a
+// verdict: the per-cell scaled solve with the per-cell block preconditioner then runs
+// from its iterate and decides (the cold, opaque cells it still has to fix are nearly
+// local).
 static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& iters) {
   cudaStream_t st = h->stream;
   D2& D = h->D;
@@ -1045,9 +1218,11 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
   const unsigned gc = grid_of(D.g.nc);
   const int m = h->m;
   double* V = h->Kbasis;
+  const bool f32 = h->mixed && !mg_stage;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), yv(m);
-  const unsigned vb = kRedBlocks;
-  const double thr = h->opt.krylov_rtol * std::sqrt((double)D.g.nc);
+  const unsigned vb = kAxpyBlocks;
+  const double rtol = h->mixed ? std::max(h->opt.krylov_rtol, kMixedRtol) : h->opt.krylov_rtol;
+  const double thr = rtol * std::sqrt((double)D.g.nc);
   const int maxcycles = mg_stage ? kMgStageCycles : h->opt.krylov_maxcycles;
   grte_status s = GRTE_OK;
   iters = 0;
@@ -1055,6 +1230,10 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
     const double* src = pred ? h->x + (int64_t)D.g.K * D.g.nc : h->cscale;
     k2_maxabs<<<kRedBlocks, kThreads, 0, st>>>(src, D.g.nc, h->part);
     k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks, mg_stage ? 1 : 0);
+    if (f32) {
+      tof(h, D.wsc, h->wsc32, D.g.nc);
+      tof(h, D.iwsc, h->iwsc32, D.g.nc);
+    }
   };
   // the true scaled residual of the unscaled x, into V_0; returns its norm
   auto residual = [&](double* beta) -> grte_status {
@@ -1085,29 +1264,16 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
       if (!mg_stage && !(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
       return GRTE_OK;
     }
-    k2_scale<<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
+    if (f32) k2_tof<<<vb, kThreads, 0, st>>>(V, h->V32, n, 1.0 / beta);
+    else k2_scale<double><<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int kk = 0;
     for (int j = 0; j < m; ++j) {
-      double* vj = V + (int64_t)j * n;
-      double* w = V + (int64_t)(j + 1) * n;
-      apply_M(h, pred, vj, h->Kr);
-      apply_P(h, pred, mg_stage, h->Kr, w);
-      // classical Gram-Schmidt, twice; the coefficients stay on the device (dots ->
-      // maxpy), the Hessenberg column is accumulated there and read once per iteration
       std::vector<double> hc(j + 2, 0.0);
-      for (int pass = 0; pass < 2; ++pass) {
-        k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, V, j + 1, n, h->part);
-        k2_reduce<<<j + 1, kThreads, 0, st>>>(h->part, kRedBlocks, h->coef);
-        k2_maxpy<<<vb, kThreads, 0, st>>>(w, V, h->coef, j + 1, n);
-        k2_hacc<<<1, kMaxRestart2 + 1, 0, st>>>(h->hcol, h->coef, j + 1, pass == 0);
-      }
-      k2_mdot<<<kRedBlocks, kThreads, 0, st>>>(w, w, 1, n, h->part);
-      k2_reduce<<<1, kThreads, 0, st>>>(h->part, kRedBlocks, h->hcol + j + 1);
-      CK2(cudaGetLastError());
-      CK2(cudaMemcpyAsync(hc.data(), h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
-      CK2(cudaStreamSynchronize(st));
+      s = f32 ? arnoldi_step<float>(h, pred, mg_stage, h->V32, j, n, hc)
+              : arnoldi_step<double>(h, pred, mg_stage, V, j, n, hc);
+      if (s != GRTE_OK) return s;
       const double hn = std::sqrt(hc[j + 1]);
       hc[j + 1] = hn;
       ++iters;
@@ -1124,9 +1290,13 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
       g[j] = cs[j] * g[j];
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
       kk = j + 1;
-      if (hn > 0.0) k2_scale<<<vb, kThreads, 0, st>>>(w, 1.0 / hn, n);
+      if (hn > 0.0) {
+        if (f32) k2_scale<float><<<vb, kThreads, 0, st>>>(h->V32 + (int64_t)(j + 1) * n, 1.0 / hn, n);
+        else k2_scale<double><<<vb, kThreads, 0, st>>>(V + (int64_t)(j + 1) * n, 1.0 / hn, n);
+      }
       const double gj = std::fabs(g[j + 1]);
       if (gj <= 0.5 * thr || hn == 0.0) break;
+      if (f32 && gj <= kInnerReduce * beta) break;
       if (mg_stage && j >= 4 && gj <= 1e-6 * beta && gj > 0.5 * std::fabs(g[j - 3])) break;
     }
     for (int i = kk - 1; i >= 0; --i) {
@@ -1135,7 +1305,8 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
       yv[i] = t / H[(size_t)i * m + i];
     }
     CK2(cudaMemcpyAsync(h->coef, yv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
-    k2_update<<<vb, kThreads, 0, st>>>(h->x, V, h->coef, kk, n);
+    if (f32) k2_update<float><<<vb, kThreads, 0, st>>>(h->x, h->V32, h->coef, kk, n);
+    else k2_update<double><<<vb, kThreads, 0, st>>>(h->x, V, h->coef, kk, n);
     k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);    // y -> x
     CK2(cudaStreamSynchronize(st));
     CK2(cudaGetLastError());
@@ -1155,10 +1326,11 @@ static grte_status step2(grte2d_t h) {
   k2_coef<<<gc, kThreads, 0, st>>>(D);
   k2_vcoef<<<gv, kThreads, 0, st>>>(D);
   k2_rho<<<gc, kThreads, 0, st>>>(D, D.E, D.rho_n);
-  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
+  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
   k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
-  k2_gdiag<<<gc, kThreads, 0, st>>>(D);
+  k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
+  mirror_coefficients(h);
   if (!h->mgl.empty()) mg_setup(h);
   CK2(cudaGetLastError());
   grte_status s = GRTE_OK;
@@ -1173,9 +1345,9 @@ static grte_status step2(grte2d_t h) {
   h->stats.krylov_iters += its;
   k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
   // O* and the flux term of the temperature equation
-  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{h->Es, nc, nullptr}, h->V);
-  k2_cell<C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
-  k2_cellsum<C_FDIV><<<gc, kThreads, 0, st>>>(D, h->tk, nullptr, D.Fdiv, nullptr);
+  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
+  k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
+  k2_cellsum<double, C_FDIV><<<gc, kThreads, 0, st>>>(D, h->cv, h->tk, nullptr, D.Fdiv, nullptr);
   if (D.use_guess || D.log_samples) k2_newton_feat<<<gc, kThreads, 0, st>>>(D);
   if (D.use_guess) {
     cudaError_t e = grte::mlp_guess_launch(h->mlp, D.feat, nc, D.guess, st);
@@ -1186,13 +1358,14 @@ static grte_status step2(grte2d_t h) {
   k2_coef<<<gc, kThreads, 0, st>>>(D);
   k2_vcoef<<<gv, kThreads, 0, st>>>(D);
   k2_acU<<<gc, kThreads, 0, st>>>(D);
-  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
-  k2_vertex<false><<<gvk, kThreads, 0, st>>>(D, UField{nullptr, 0, D.acU}, h->V);
-  k2_cell<C_DIVK, false><<<gck, kThreads, 0, st>>>(D, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr, nullptr);
+  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
+  k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
+  k2_vertex<double, false><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, D.acU}, h->V);
+  k2_cell<double, C_DIVK, false><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr, nullptr);
   k2_rhs_corr<<<gc, kThreads, 0, st>>>(D, h->GU, h->phi, h->b, h->x);
   k2_corrscale<<<gc, kThreads, 0, st>>>(D, h->cscale);
-  k2_gdiag<<<gc, kThreads, 0, st>>>(D);
+  k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
+  mirror_coefficients(h);
   CK2(cudaGetLastError());
   its = 0;
   s = gmres2(h, false, false, K * nc, its);
@@ -1201,7 +1374,7 @@ static grte_status step2(grte2d_t h) {
   h->stats.krylov_iters_corr += its;
   // projection: E = a c U + eps E_J, O from E (vertex map with the O^n data), U = T^4
   k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
-  k2_vertex<true><<<gvk, kThreads, 0, st>>>(D, UField{D.E, nc, nullptr}, h->V);
+  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{D.E, nc, nullptr}, h->V);
   CK2(cudaMemcpyAsync(D.O, h->V, sizeof(double) * K * g.nv, cudaMemcpyDeviceToDevice, st));
   CK2(cudaGetLastError());
   return GRTE_OK;
@@ -1228,7 +1401,6 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
   *out = h;
   grte_default_options(&h->opt);
   if (opt) h->opt = *opt;
-  if (h->opt.precision != GRTE_FP64) return fail2(h, GRTE_EINVAL, "2D instances run in GRTE_FP64");
   h->m = h->opt.krylov_restart == 10 ? 30 : h->opt.krylov_restart;
   if (h->m < 1 || h->m > kMaxRestart2) return fail2(h, GRTE_EINVAL, "krylov_restart out of range [1,64]");
   if (!(h->opt.krylov_rtol > 0) || h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1)
@@ -1297,7 +1469,7 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
             alloc2(h, &h->V, K * nv) && alloc2(h, &h->phi, K * nc) && alloc2(h, &h->GU, K * nc) &&
             alloc2(h, &h->Es, K * nc) && alloc2(h, &h->b, nz) && alloc2(h, &h->x, nz) && alloc2(h, &h->Kr, nz) &&
             alloc2(h, &h->Kt, nz) && alloc2(h, &h->Kbasis, (int64_t)(h->m + 1) * nz) &&
-            alloc2(h, &h->part, (int64_t)kRedBlocks * (kMaxRestart2 + 1)) && alloc2(h, &h->dots, kMaxRestart2 + 1) &&
+            alloc2(h, &h->part, (int64_t)kAxpyBlocks * (kMaxRestart2 + 1)) && alloc2(h, &h->dots, kMaxRestart2 + 1) &&
             alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc) &&
             alloc2(h, &h->hcol, kMaxRestart2 + 2) && alloc2(h, &h->tk, K * nc);
   if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
@@ -1325,6 +1497,30 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
     return fail2(h, GRTE_EINVAL, "prec2d must be GRTE_PREC2D_MULTIGRID or GRTE_PREC2D_BLOCK");
   }
   D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
+  h->cv = CV<double>{D.mu, D.eta, D.w, D.kc, D.A, D.alpha, D.dv, D.gd, D.gdi, D.pdi, D.wsc, D.iwsc,
+                     g.h2x, g.h2y, g.te};
+  if (h->opt.precision == GRTE_MIXED) {
+    h->mixed = true;
+    const int64_t nvk = K * nv;
+    bool okf = alloc2(h, &h->mu32, K) && alloc2(h, &h->eta32, K) && alloc2(h, &h->w32, K) &&
+               alloc2(h, &h->kc32, nc) && alloc2(h, &h->A32, nc) && alloc2(h, &h->alpha32, nc) &&
+               alloc2(h, &h->dv32, nv) && alloc2(h, &h->gd32, K * nc) && alloc2(h, &h->gdi32, K * nc) &&
+               alloc2(h, &h->pdi32, nc) && alloc2(h, &h->wsc32, nc) && alloc2(h, &h->iwsc32, nc) &&
+               alloc2(h, &h->V32, (int64_t)(h->m + 1) * nz) && alloc2(h, &h->Kr32, nz) &&
+               alloc2(h, &h->Vv32, nvk) && alloc2(h, &h->tk32, K * nc);
+    if (!okf) return fail2(h, GRTE_ENOMEM, "cudaMalloc binary32 buffers");
+    std::vector<float> f(K);
+    for (int64_t k = 0; k < K; ++k) f[k] = (float)h->hmu[k];
+    CK2(cudaMemcpy(h->mu32, f.data(), sizeof(float) * K, cudaMemcpyHostToDevice));
+    for (int64_t k = 0; k < K; ++k) f[k] = (float)h->heta[k];
+    CK2(cudaMemcpy(h->eta32, f.data(), sizeof(float) * K, cudaMemcpyHostToDevice));
+    for (int64_t k = 0; k < K; ++k) f[k] = (float)h->hw[k];
+    CK2(cudaMemcpy(h->w32, f.data(), sizeof(float) * K, cudaMemcpyHostToDevice));
+    h->cv32 = CV<float>{h->mu32, h->eta32, h->w32, h->kc32, h->A32, h->alpha32, h->dv32, h->gd32, h->gdi32,
+                        h->pdi32, h->wsc32, h->iwsc32, (float)g.h2x, (float)g.h2y, (float)g.te};
+  } else if (h->opt.precision != GRTE_FP64) {
+    return fail2(h, GRTE_EINVAL, "precision must be GRTE_FP64 or GRTE_MIXED");
+  }
   CK2(cudaMemcpy(h->dmu, h->hmu.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
   CK2(cudaMemcpy(h->deta, h->heta.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
   CK2(cudaMemcpy(h->dw, h->hw.data(), sizeof(double) * K, cudaMemcpyHostToDevice));

@@ -418,7 +418,7 @@ class Grte2D:
     def __init__(self, nx, ny, sigma, dt, eps, kind=SIGMA_T3, bc_x=BC_INFLOW, bc_y=BC_INFLOW, b_x0=0.0, b_x1=0.0,
                  b_y0=0.0, b_y1=0.0, mu=None, eta=None, w=None, lx=1.0, ly=1.0, a=1.0, c=1.0, Cv=1.0,
                  krylov_rtol=1e-13, krylov_restart=30, krylov_maxcycles=30, newton_maxit=60, stream=None,
-                 prec=0):
+                 prec=0, precision=FP64):
         L = lib()
         sig = _f64(np.broadcast_to(np.asarray(sigma, dtype=np.float64).ravel(), (nx * ny,)))
         mu, eta, w = _f64(mu), _f64(eta), _f64(w)
@@ -434,6 +434,7 @@ class Grte2D:
         opt.newton_maxit = newton_maxit
         opt.stream = stream
         opt.prec2d = prec
+        opt.precision = precision
         h = ctypes.c_void_p()
         st = L.grte2d_create(ctypes.byref(inst), ctypes.byref(opt), ctypes.byref(h))
         self.h = h

@@ -152,3 +152,58 @@ def test_equilibrium_preserved_on_gpu(G):
     print("equilibrium: T %.3e E %.3e" % (eT, eE))
     assert eT < tol and eE < 4 * tol
     h.close()
+
+
+def test_mixed_precision_against_oracle(G):
+    # binary32 Krylov cycles inside binary64 restarts, Krylov tolerance floored at 1e-9:
+    # the mixed tolerance (1e-5 relative in T) with room to spare
+    mu, eta, w = s8_pairs_2d()
+    cases = []
+    nx, ny = 12, 10
+    rng = np.random.default_rng(19)
+    T0 = 0.3 * (1.0 + 0.5 * rng.random(nx * ny))
+    cases.append((o2.Problem2D(Nx=nx, Ny=ny, mu=mu, eta=eta, w=w, sig=checkerboard(nx, ny, 2), eps=1e-3,
+                               dt=0.5 / nx, kind="t3", bx0=0.2), T0, None, None, 3))
+    rng = np.random.default_rng(23)
+    P = o2.Problem2D(Nx=9, Ny=8, mu=mu, eta=eta, w=w, sig=0.2 + rng.random((8, 9)), eps=1.0, dt=0.02,
+                     kind="const", bx0=1.0, bx1=0.3, by0=0.6, by1=0.1)
+    T1 = 0.5 + 0.5 * rng.random(P.nc)
+    cases.append((P, T1, (T1 ** 4)[:, None] * (1.0 + 0.3 * rng.random((P.nc, P.K))),
+                  0.2 * (rng.random((P.nv, P.K)) - 0.5), 2))
+    for P, T0, E0, O0, nsteps in cases:
+        S = o2.equilibrium_state(P, T0) if E0 is None else o2.State2D(E=E0, O=O0, U=T0 ** 4, T=T0)
+        Sn = o2.run(P, S, nsteps)
+        h = _pair(G, P, T0, E0, O0, precision=G.MIXED)
+        h.step(nsteps)
+        eT, eE = _rel(h.T(), Sn.T), _rel(h.E(), Sn.E)
+        eO = float(np.max(np.abs(h.O() - Sn.O)) / np.max(np.abs(Sn.O)))
+        print("mixed %dx%d eps %g: T %.3e E %.3e O %.3e" % (P.Nx, P.Ny, P.eps, eT, eE, eO), h.stats())
+        assert eT < 1e-6 and eE < 1e-6 and eO < 1e-5
+        h.close()
+
+
+def test_mixed_precision_cold_checkerboard_and_energy(G):
+    mu, eta, w = s8_pairs_2d()
+    nx, ny = 12, 10
+    rng = np.random.default_rng(17)
+    T0 = 1e-2 * (1.0 + 0.5 * rng.random(nx * ny))
+    P = o2.Problem2D(Nx=nx, Ny=ny, mu=mu, eta=eta, w=w, sig=checkerboard(nx, ny, 2), eps=1e-3,
+                     dt=0.5 / nx, kind="t3", bx0=1.0)
+    S1 = o2.step(P, o2.equilibrium_state(P, T0))
+    h = _pair(G, P, T0, precision=G.MIXED)
+    h.step(1, allow=(5,))
+    Tg = h.T(allow=(5,))
+    assert np.array_equal(Tg == 0.0, S1.T == 0.0)
+    assert _rel(Tg, S1.T) < 1e-6
+    h.close()
+    # periodic axes: the energy sum is conserved to the Krylov tolerance
+    P = o2.Problem2D(Nx=10, Ny=7, mu=mu, eta=eta, w=w, sig=1.3, eps=1e-2, dt=0.03, kind="const",
+                     bcx="periodic", bcy="periodic")
+    T0 = 0.4 + 0.6 * rng.random(P.nc)
+    E0 = (T0 ** 4)[:, None] * (1.0 + 0.2 * rng.random((P.nc, P.K)))
+    h = _pair(G, P, T0, E0, np.zeros((P.nv, P.K)), precision=G.MIXED)
+    e0 = h.energy()
+    for _ in range(3):
+        h.step(1)
+        assert abs(h.energy() - e0) < 1e-8 * e0
+    h.close()
