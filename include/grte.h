@@ -291,7 +291,7 @@ typedef struct {
  * restart forms the residual and updates the unknowns in binary64, but the cycle's
  * Krylov process (basis, matrix, block preconditioner, Gram-Schmidt) runs in binary32
  * and ends after a 1e5 reduction of the residual (iterative refinement); krylov_rtol is
- * floored at 1e-9; coefficients, Newton and the energy sums stay binary64.  The state is
+ * floored at 1e-11; coefficients, Newton and the energy sums stay binary64.  The state is
  * unset until grte2d_set_state.  Errors: EINVAL, ENOMEM, ECUDA. */
 grte_status grte2d_create(const grte_instance2d* inst, const grte_options* opt, grte2d_t* out);
 /* T: nx*ny; E: nx*ny*K as [cell][k] and O: (nx+1)*(ny+1)*K as [vertex][k] (vertex
