@@ -188,8 +188,18 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="slab6", choices=["slab6", "marshak128", "batched256", "checker2d"])
-    ap.add_argument("--n2d", type=int, default=128, help="cells per axis of the checker2d workload")
+    ap.add_argument("--workload", default="slab6",
+                    choices=["slab6", "marshak128", "batched256", "checker2d", "lognormal2d"])
+    ap.add_argument("--n2d", type=int, default=None,
+                    help="cells per axis of the 2D workloads (checker2d: 128, lognormal2d: 1024)")
+    ap.add_argument("--newton-start", default="bound", choices=["bound", "previous", "learned"],
+                    help="2D: Newton's starting point (learned: a network trained first on small 2D runs)")
+    ap.add_argument("--krylov-restart", type=int, default=None,
+                    help="2D: GMRES restart length (checker2d: 30, lognormal2d: 60)")
+    ap.add_argument("--krylov-maxcycles", type=int, default=None,
+                    help="2D: GMRES restart cycles per solve (checker2d: 30, lognormal2d: 60)")
+    ap.add_argument("--compare-starts", action="store_true",
+                    help="2D: also run the other Newton starts from the same state and report their counts")
     ap.add_argument("--prec2d", default="block", choices=["block", "multigrid"],
                     help="2D prediction preconditioner: per-cell block + multigrid on rho, or per-cell block only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -201,15 +211,21 @@ def main():
                     help="also time the same instances advanced one handle at a time")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.workload == "checker2d":
+    if args.workload in ("checker2d", "lognormal2d"):
+        if args.n2d is None:
+            args.n2d = 128 if args.workload == "checker2d" else 1024
+        if args.krylov_restart is None:
+            args.krylov_restart = 30 if args.workload == "checker2d" else 60
+        if args.krylov_maxcycles is None:
+            args.krylov_maxcycles = 30 if args.workload == "checker2d" else 60
         if args.impl == "reference":
             if int(os.environ.get("RANK", "0")) == 0:
-                cb = cpu_baseline_2d()
+                cb = cpu_baseline_2d(workload=args.workload)
                 print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
                                   "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                                   "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                                   "dtype": "f64", "data": "synthetic",
-                                  "config": {"workload": "2d_checkerboard_%dx%d_s8" % (args.n2d, args.n2d)},
+                                  "config": {"workload": workload_name_2d(args.workload, args.n2d)},
                                   "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT,
                                                               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
             return
@@ -448,7 +464,25 @@ def checker2d_inputs(n, blocks=8):
     return sig, np.full(n * n, 1e-2), 0.5 / n, 1e-3
 
 
-def cpu_baseline_2d(n=16, nsteps=1):
+def lognormal2d_inputs(n):
+    """2D random-smooth slab: sigma_0 = exp(g), g an iid N(0, 1) field smoothed by a
+    Gaussian of standard deviation 8 cells (wrapped, separable) and renormalised to unit
+    variance, times 1/T^3; T_in = 1e-2; eps = 1e-4; inflow a c 1^4 on x = 0, vacuum on
+    the other walls; dt = 0.5 dx; S8 (20 pairs)."""
+    from paper_1811_05579_gb300 import workloads as wl
+    sig = wl.lognormal_sigma_2d(n, seed=wl.BASE_SEED + 5, sd_cells=8.0)
+    return sig, np.full(n * n, 1e-2), 0.5 / n, 1e-4
+
+
+def inputs_2d(workload, n):
+    return checker2d_inputs(n) if workload == "checker2d" else lognormal2d_inputs(n)
+
+
+def workload_name_2d(workload, n):
+    return ("2d_checkerboard_%dx%d_s8" if workload == "checker2d" else "2d_lognormal_%dx%d_s8") % (n, n)
+
+
+def cpu_baseline_2d(n=16, nsteps=8, workload="checker2d"):
     """The 2D oracle as it stands, one thread, on the same geometry at n x n."""
     code = f"""
 import os, sys, time, json
@@ -458,7 +492,7 @@ import numpy as np
 import bench
 from oracle import grte2d as o2
 from oracle.quadrature import s8_pairs_2d
-sig, T0, dt, eps = bench.checker2d_inputs({n})
+sig, T0, dt, eps = bench.inputs_2d({workload!r}, {n})
 mu, eta, w = s8_pairs_2d()
 P = o2.Problem2D(Nx={n}, Ny={n}, mu=mu, eta=eta, w=w, sig=sig, eps=eps, dt=dt, kind="t3", bx0=1.0)
 S = o2.equilibrium_state(P, T0)
@@ -474,8 +508,41 @@ print(json.dumps({{"updates": {n} * {n} * 40 * {nsteps}, "seconds": dt_}}))
             "sample": "%d step(s) of the same geometry at %dx%d (sparse LU), %.1f s, 1 thread" % (nsteps, n, n, d["seconds"])}
 
 
+def train_guess_2d(G, stream):
+    """A network for the learned Newton start, trained on the GPU on the scheme's own
+    (features -> log10 T^{n+1}/T^n) pairs logged by small 2D runs: checkerboards with
+    per-run sigma_0 values (log-uniform in [10^-0.5, 1] and [10, 100]) and log-normal
+    fields of other seeds, 24^2-56^2, eps 1e-3 and 1e-4, 25 steps each."""
+    from paper_1811_05579_gb300 import workloads as wl
+    runs = []
+    for r, n in enumerate((24, 32, 40, 56)):
+        u = wl.SplitMix64(wl.BASE_SEED + 100 + r).uniform(2)
+        runs.append((n, wl.checkerboard_sigma_2d(n, lo=10 ** (-0.5 + 0.5 * u[0]), hi=10 ** (1.0 + u[1])),
+                     1e-3 if r % 2 == 0 else 1e-4, 41 + r))
+    for r, n in enumerate((32, 40)):
+        runs.append((n, wl.lognormal_sigma_2d(n, seed=wl.BASE_SEED + 11 + r, sd_cells=3.0), 1e-4, 51 + r))
+    Xs, Ys = [], []
+    t0 = time.perf_counter()
+    for n, sig, eps, seed in runs:
+        h = G.Grte2D(n, n, sig, 0.5 / n, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream)
+        h.set_state(1e-2 * (1.0 + 0.5 * wl.SplitMix64(seed).uniform(n * n)))
+        h.set_sample_logging(True)
+        for _ in range(25):
+            h.step(1, allow=(5,))
+            X, y = h.newton_samples()
+            keep = np.all(np.isfinite(X), axis=1) & (X[:, 0] > -30) & (np.abs(X[:, 2]) < 30)
+            Xs.append(X[keep])
+            Ys.append(y[keep])
+        h.close()
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    m = G.MLP(seed=1)
+    m.set_norm(X.mean(0), np.maximum(X.std(0), 0.1), float(Y.mean()), float(Y.std() + 1e-6))
+    loss = m.train(X, Y, epochs=30, batch=256, lr=1e-3, seed=3)
+    return m, {"samples": int(X.shape[0]), "standardised_mse": float(loss), "seconds": time.perf_counter() - t0}
+
+
 def run_2d(args):
-    """The 2D path (grte2d_*) on the checkerboard workload at n2d x n2d."""
+    """The 2D path (grte2d_*) on the checkerboard or the random-smooth workload at n2d x n2d."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -483,8 +550,11 @@ def run_2d(args):
     torch.cuda.set_device(local)
     from paper_1811_05579_gb300 import grte as G
     n = args.n2d
-    sig, T0, dt, eps = checker2d_inputs(n)
+    sig, T0, dt, eps = inputs_2d(args.workload, n)
     stream = torch.cuda.current_stream()
+    net, training = None, None
+    if args.newton_start == "learned" or args.compare_starts:
+        net, training = train_guess_2d(G, stream)
     prec = G.PREC2D_MULTIGRID if args.prec2d == "multigrid" else G.PREC2D_BLOCK
     precision = G.MIXED if args.precision == "mixed" else G.FP64
     allow = (5,)        # cells reaching R <= 0 at this dt (see the workload's readings)
@@ -492,9 +562,14 @@ def run_2d(args):
 
     snap = {}
 
-    def timed(precision_, clocks=None):
+    def timed(precision_, clocks=None, start=args.newton_start):
         h_ = G.Grte2D(n, n, sig, dt, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream, prec=prec,
-                      precision=precision_)
+                      precision=precision_, krylov_restart=args.krylov_restart,
+                      krylov_maxcycles=args.krylov_maxcycles)
+        if start == "learned":
+            h_.set_guess(net)
+        elif start == "previous":
+            h_.set_newton_start(G.START_PREVIOUS)
         h_.set_state(T0)
         for _ in range(args.warmup):
             h_.step(1, allow=allow)
@@ -503,7 +578,7 @@ def run_2d(args):
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-        t, it = 0.0, [0, 0, 0]
+        t, it = 0.0, [0, 0, 0, 0.0]
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -517,11 +592,22 @@ def run_2d(args):
             it[0] += st["krylov_iters"]
             it[1] += st["krylov_iters_corr"]
             it[2] += st["krylov_iters_mg"]
+            it[3] += st["newton_iters_mean"] / args.steps
         return h_, t, it
 
     clocks = ClockSampler(local)
-    h, t_ms, (its, its_corr, its_mg) = timed(precision, clocks)
+    h, t_ms, (its, its_corr, its_mg, newton_mean) = timed(precision, clocks)
     clk = clocks.stop()
+    starts = None
+    if args.compare_starts:
+        starts = {args.newton_start: {"ms_per_step": t_ms / args.steps, "newton_iters_per_cell": newton_mean}}
+        for other in ("bound", "previous", "learned"):
+            if other != args.newton_start:
+                h2, t2, it2 = timed(precision, start=other)
+                starts[other] = {"ms_per_step": t2 / args.steps, "newton_iters_per_cell": it2[3],
+                                 "t_max_rel_diff": float(np.max(np.abs(h2.T(allow) - h.T(allow)) /
+                                                                np.maximum(np.abs(h.T(allow)), 1e-300)))}
+                h2.close()
     vs_fp64 = None
     if precision == G.MIXED and not args.no_fp64_compare:
         h64, t64, _ = timed(G.FP64)
@@ -555,9 +641,12 @@ def run_2d(args):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 Krylov cycles / f64 residual, Newton, sums" if precision == G.MIXED else "f64",
             "data": "synthetic (seeded; no dataset)",
-            "config": {"workload": "2d_checkerboard_%dx%d_s8" % (n, n), "n": n, "pairs": 20, "eps": eps,
+            "config": {"workload": workload_name_2d(args.workload, n), "n": n, "pairs": 20, "eps": eps,
                        "precision": args.precision,
-                       "sigma0": [1, 100], "blocks": 8, "dt": "0.5 dx", "T_in": 1e-2, "prec2d": args.prec2d,
+                       "sigma0": [1, 100] if args.workload == "checker2d" else "exp(N(0,1) smoothed 8 cells)",
+                       "dt": "0.5 dx", "T_in": 1e-2, "prec2d": args.prec2d,
+                       "newton_start": args.newton_start, "krylov_restart": args.krylov_restart,
+                       "krylov_maxcycles": args.krylov_maxcycles,
                        "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},
             "gpu_launches": None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(T.nbytes + E.nbytes + O.nbytes),
@@ -568,13 +657,16 @@ def run_2d(args):
                          "note": "24 B per cell-angle update over the step time"},
             "krylov_iters_per_step": its / args.steps, "krylov_iters_corr_per_step": its_corr / args.steps,
             "krylov_iters_mg_per_step": its_mg / args.steps, "vs_fp64": vs_fp64,
+            "newton_iters_per_cell": newton_mean, "newton_starts": starts, "guess_training": training,
             "status_flags": h.stats(allow=allow)["status_flags"],
             "clocks": clk}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_2d()
+        line["cpu_baseline"] = cpu_baseline_2d(workload=args.workload)
     if rank == 0:
         print(json.dumps(line))
     h.close()
+    if net is not None:
+        net.close()
 
 
 if __name__ == "__main__":
