@@ -1172,8 +1172,8 @@ static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double*
 
 // One Arnoldi step in precision S: w = V_{j+1} = D_w P^{-1} M D_w^{-1} V_j (binary32: the
 // binary32 matrix and block preconditioner), orthogonalised against V_0..V_j by classical
-// Gram-Schmidt twice (the coefficients stay on the device; the second pass's update also
-// gives |w|^2); hc receives the Hessenberg column, hc[j+1] = |w|^2 (w not normalised).
+// Gram-Schmidt (the coefficients stay on the device; the last pass's update also gives
+// |w|^2); hc receives the Hessenberg column, hc[j+1] = |w|^2 (w not normalised).
 template <typename S>
 static grte_status arnoldi_step(grte2d_t h, bool pred, bool mg_stage, S* V, int j, int64_t n, std::vector<double>& hc) {
   cudaStream_t st = h->stream;
@@ -1186,10 +1186,13 @@ static grte_status arnoldi_step(grte2d_t h, bool pred, bool mg_stage, S* V, int 
     apply_M32(h, pred, vj, h->Kr32);
     apply_P32(h, pred, h->Kr32, w);
   }
-  for (int pass = 0; pass < 2; ++pass) {
+  // binary32 cycles: one pass (a cycle only has to gain 1e5 and the binary64 restart
+  // corrects what the basis's loss of orthogonality costs); binary64: two passes
+  const int passes = sizeof(S) == 4 ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
     launch_mdot<S>(w, V, j + 1, n, h->part, st);
     k2_reduce_h<<<j + 1, kThreads, 0, st>>>(h->part, kDotBlocks, h->coef, h->hcol, pass == 0);
-    if (pass == 0) {
+    if (pass + 1 < passes) {
       k2_maxpy<S, false><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, nullptr);
     } else {
       k2_maxpy<S, true><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, h->part);
