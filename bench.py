@@ -580,7 +580,7 @@ def run_2d(args):
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-        t, it = 0.0, [0, 0, 0, 0.0]
+        t, it = 0.0, [0, 0, 0, 0.0, 0]
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -595,10 +595,11 @@ def run_2d(args):
             it[1] += st["krylov_iters_corr"]
             it[2] += st["krylov_iters_mg"]
             it[3] += st["newton_iters_mean"] / args.steps
+            it[4] += st["launches"]
         return h_, t, it
 
     clocks = ClockSampler(local)
-    h, t_ms, (its, its_corr, its_mg, newton_mean) = timed(precision, clocks)
+    h, t_ms, (its, its_corr, its_mg, newton_mean, launches) = timed(precision, clocks)
     clk = clocks.stop()
     starts = None
     if args.compare_starts:
@@ -650,7 +651,7 @@ def run_2d(args):
                        "newton_start": args.newton_start, "krylov_restart": args.krylov_restart,
                        "krylov_maxcycles": args.krylov_maxcycles,
                        "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(T.nbytes + E.nbytes + O.nbytes),
                     "d2h_bytes_per_step": int(T.nbytes + E.nbytes + O.nbytes),
                     "note": "replays the timed steps from the same state; L2 not flushed"},

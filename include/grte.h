@@ -114,6 +114,8 @@ typedef struct {
                                 substep (the rest is the prediction); 1D: 0          */
   int64_t krylov_iters_mg;   /* 2D: the part of the prediction's iterations taken with
                                 the multigrid preconditioner; 1D: 0                  */
+  int64_t launches;          /* 2D: kernels launched by the last grte2d_step call (1D:
+                                0; see grte_last_launches)                           */
 } grte_stats_t;
 
 /* Fill *opt with the defaults. */

@@ -959,6 +959,10 @@ static void s8_pairs(std::vector<double>& mu, std::vector<double>& eta, std::vec
 // =============================================================================== host
 using namespace grte2;
 
+// Kernel launches made by this thread (every launch site increments it); grte2d_step
+// reports the difference over the call in grte_stats_t.launches.
+static thread_local int64_t tl_launches = 0;
+
 struct grte2d_ctx {
   D2 D{};
   G2 g{};
@@ -1014,16 +1018,16 @@ static bool alloc2(grte2d_t h, T** p, int64_t n) {
 
 template <typename S>
 static void launch_mdot(const S* w, const S* V, int nvec, int64_t n, double* part, cudaStream_t st) {
-  if (nvec <= 4) k2_mdot<S, 4><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
-  else if (nvec <= 8) k2_mdot<S, 8><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
-  else k2_mdot<S, 16><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+  if (nvec <= 4) tl_launches++, k2_mdot<S, 4><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+  else if (nvec <= 8) tl_launches++, k2_mdot<S, 8><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
+  else tl_launches++, k2_mdot<S, 16><<<kDotBlocks, kThreads, 0, st>>>(w, V, nvec, n, part);
 }
 
 // dots[i] = <w, V_i>, i < nvec, returned on the host.
 static grte_status mdot(grte2d_t h, const double* w, const double* V, int nvec, int64_t n, double* host) {
   cudaStream_t st = h->stream;
   launch_mdot<double>(w, V, nvec, n, h->part, st);
-  k2_reduce<<<nvec, kThreads, 0, st>>>(h->part, kDotBlocks, h->dots);
+  tl_launches++, k2_reduce<<<nvec, kThreads, 0, st>>>(h->part, kDotBlocks, h->dots);
   CK2(cudaGetLastError());
   CK2(cudaMemcpyAsync(host, h->dots, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
   CK2(cudaStreamSynchronize(st));
@@ -1037,12 +1041,12 @@ static void apply_M(grte2d_t h, bool pred, const double* xin, double* y) {
   cudaStream_t st = h->stream;
   UField u{xin, D.g.nc, pred ? xin + (int64_t)D.g.K * D.g.nc : nullptr, D.iwsc};
   const int64_t K = D.g.K;
-  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, u, h->V);
+  tl_launches++, k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, u, h->V);
   if (pred) {
-    k2_cell<double, C_MV_PRED, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
-    k2_cellsum<double, C_MV_PRED><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, h->tk, xin, y, D.iwsc);
+    tl_launches++, k2_cell<double, C_MV_PRED, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
+    tl_launches++, k2_cellsum<double, C_MV_PRED><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, h->tk, xin, y, D.iwsc);
   } else {
-    k2_cell<double, C_MV_CORR, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
+    tl_launches++, k2_cell<double, C_MV_CORR, false><<<grid_of(K * D.g.nc), kThreads, 0, st>>>(D, h->cv, h->V, u, xin, y, D.iwsc, h->tk);
   }
 }
 
@@ -1052,24 +1056,24 @@ static void apply_M32(grte2d_t h, bool pred, const float* xin, float* y) {
   cudaStream_t st = h->stream;
   const int64_t K = D.g.K, nc = D.g.nc;
   UFieldT<float> u{xin, nc, pred ? xin + K * nc : nullptr, h->cv32.iwsc};
-  k2_vertex<float, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv32, u, h->Vv32);
+  tl_launches++, k2_vertex<float, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv32, u, h->Vv32);
   if (pred) {
-    k2_cell<float, C_MV_PRED, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
+    tl_launches++, k2_cell<float, C_MV_PRED, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
                                                                          h->cv32.iwsc, h->tk32);
-    k2_cellsum<float, C_MV_PRED><<<grid_of(nc), kThreads, 0, st>>>(D, h->cv32, h->tk32, xin, y, h->cv32.iwsc);
+    tl_launches++, k2_cellsum<float, C_MV_PRED><<<grid_of(nc), kThreads, 0, st>>>(D, h->cv32, h->tk32, xin, y, h->cv32.iwsc);
   } else {
-    k2_cell<float, C_MV_CORR, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
+    tl_launches++, k2_cell<float, C_MV_CORR, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv32, h->Vv32, u, xin, y,
                                                                          h->cv32.iwsc, h->tk32);
   }
 }
 
 static void apply_P32(grte2d_t h, bool pred, const float* r, float* z) {
-  if (pred) k2_prec<float, true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
-  else k2_prec<float, false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
+  if (pred) tl_launches++, k2_prec<float, true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
+  else tl_launches++, k2_prec<float, false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
 }
 
 static void tof(grte2d_t h, const double* src, float* dst, int64_t n) {
-  k2_tof<<<kAxpyBlocks, kThreads, 0, h->stream>>>(src, dst, n, 1.0);
+  tl_launches++, k2_tof<<<kAxpyBlocks, kThreads, 0, h->stream>>>(src, dst, n, 1.0);
 }
 
 // binary32 copies of the coefficients a solve's Krylov cycles read (after k2_gdiag)
@@ -1092,26 +1096,26 @@ static const double* mg_vcycle(grte2d_t h, size_t l) {
   mg::Level& L = h->mgl[l];
   const unsigned gb = grid_of(L.n);
   if (l + 1 == h->mgl.size()) {
-    mg::mg_dense_apply<<<1, mg::kThreadsMg, 0, st>>>(L, h->mg_inv);
+    tl_launches++, mg::mg_dense_apply<<<1, mg::kThreadsMg, 0, st>>>(L, h->mg_inv);
     return L.x;
   }
   mg::Level& C = h->mgl[l + 1];
   const unsigned gcb = grid_of(C.n);
-  mg::mg_jacobi0<<<gb, kThreads, 0, st>>>(L);
+  tl_launches++, mg::mg_jacobi0<<<gb, kThreads, 0, st>>>(L);
   if (L.ncomp == 1) {
-    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
-    mg::mg_restrict<1><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
+    tl_launches++, mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    tl_launches++, mg::mg_restrict<1><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
   } else {
-    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
-    mg::mg_restrict<2><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
+    tl_launches++, mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    tl_launches++, mg::mg_restrict<2><<<gcb, kThreads, 0, st>>>(L, L.xt, C);
   }
   const double* xc = mg_vcycle(h, l + 1);
   if (L.ncomp == 1) {
-    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
-    mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    tl_launches++, mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
+    tl_launches++, mg::mg_jacobi<1><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
   } else {
-    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
-    mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
+    tl_launches++, mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.xt, L.x, xc, C);
+    tl_launches++, mg::mg_jacobi<2><<<gb, kThreads, 0, st>>>(L, L.x, L.xt, nullptr, C);
   }
   return L.xt;
 }
@@ -1129,45 +1133,45 @@ static void mg_setup(grte2d_t h) {
   const int ncx = axis_ncolours(g.Nx, px), ncy = axis_ncolours(g.Ny, py);
   for (int cy = 0; cy < ncy; ++cy)
     for (int cx = 0; cx < ncx; ++cx) {
-      k2_probe_in<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->Kt);
-      k2_vertex<double, false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
-      k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr,
+      tl_launches++, k2_probe_in<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->Kt);
+      tl_launches++, k2_vertex<double, false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
+      tl_launches++, k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr,
                                                                    h->tk, nullptr, nullptr);
-      k2_probe_out<<<grid_of(nc), kThreads, 0, st>>>(D, cx, cy, h->tk, L0.coef);
+      tl_launches++, k2_probe_out<<<grid_of(nc), kThreads, 0, st>>>(D, cx, cy, h->tk, L0.coef);
     }
-  mg::mg_idiag0<<<grid_of(nc), kThreads, 0, st>>>(L0);
+  tl_launches++, mg::mg_idiag0<<<grid_of(nc), kThreads, 0, st>>>(L0);
   for (size_t l = 0; l + 1 < h->mgl.size(); ++l) {
     mg::Level &F = h->mgl[l], &C = h->mgl[l + 1];
-    if (F.ncomp == 1) mg::mg_galerkin<1><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
-    else mg::mg_galerkin<2><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
+    if (F.ncomp == 1) tl_launches++, mg::mg_galerkin<1><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
+    else tl_launches++, mg::mg_galerkin<2><<<grid_of(C.n), kThreads, 0, st>>>(F, C);
   }
   mg::Level& Lc = h->mgl.back();
-  if (Lc.ncomp == 1) mg::mg_dense_inverse<1><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
-  else mg::mg_dense_inverse<2><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
+  if (Lc.ncomp == 1) tl_launches++, mg::mg_dense_inverse<1><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
+  else tl_launches++, mg::mg_dense_inverse<2><<<1, mg::kThreadsMg, 0, st>>>(Lc, h->mg_M, h->mg_inv);
 }
 
 static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double* z) {
   D2& D = h->D;
   cudaStream_t st = h->stream;
   if (!pred) {
-    k2_prec<double, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
+    tl_launches++, k2_prec<double, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
     return;
   }
   if (!use_mg) {
-    k2_prec<double, true><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
+    tl_launches++, k2_prec<double, true><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
     return;
   }
   const int64_t K = D.g.K, nc = D.g.nc;
-  k2_pc_et<<<grid_of(K * nc), kThreads, 0, st>>>(D, r, h->Kt);
-  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
-  k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr, h->tk,
+  tl_launches++, k2_pc_et<<<grid_of(K * nc), kThreads, 0, st>>>(D, r, h->Kt);
+  tl_launches++, k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->Kt, nc, nullptr}, h->V);
+  tl_launches++, k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Kt, nc, nullptr}, nullptr, h->tk,
                                                                nullptr, nullptr);
-  k2_pc_rhs<<<grid_of(nc), kThreads, 0, st>>>(D, r, h->tk, h->mgl[0].b);
+  tl_launches++, k2_pc_rhs<<<grid_of(nc), kThreads, 0, st>>>(D, r, h->tk, h->mgl[0].b);
   const double* rho = mg_vcycle(h, 0);
-  k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, rho}, h->V);
-  k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, rho}, nullptr, h->tk,
+  tl_launches++, k2_vertex<double, false><<<grid_of(K * D.g.nv), kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, rho}, h->V);
+  tl_launches++, k2_cell<double, C_DIVK, false><<<grid_of(K * nc), kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, rho}, nullptr, h->tk,
                                                                nullptr, nullptr);
-  k2_pc_final<<<grid_of((K + 1) * nc), kThreads, 0, st>>>(D, r, rho, h->tk, z);
+  tl_launches++, k2_pc_final<<<grid_of((K + 1) * nc), kThreads, 0, st>>>(D, r, rho, h->tk, z);
 }
 
 // One Arnoldi step in precision S: w = V_{j+1} = D_w P^{-1} M D_w^{-1} V_j (binary32: the
@@ -1191,12 +1195,12 @@ static grte_status arnoldi_step(grte2d_t h, bool pred, bool mg_stage, S* V, int 
   const int passes = sizeof(S) == 4 ? 1 : 2;
   for (int pass = 0; pass < passes; ++pass) {
     launch_mdot<S>(w, V, j + 1, n, h->part, st);
-    k2_reduce_h<<<j + 1, kThreads, 0, st>>>(h->part, kDotBlocks, h->coef, h->hcol, pass == 0);
+    tl_launches++, k2_reduce_h<<<j + 1, kThreads, 0, st>>>(h->part, kDotBlocks, h->coef, h->hcol, pass == 0);
     if (pass + 1 < passes) {
-      k2_maxpy<S, false><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, nullptr);
+      tl_launches++, k2_maxpy<S, false><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, nullptr);
     } else {
-      k2_maxpy<S, true><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, h->part);
-      k2_reduce<<<1, kThreads, 0, st>>>(h->part, kAxpyBlocks, h->hcol + j + 1);
+      tl_launches++, k2_maxpy<S, true><<<kAxpyBlocks, kThreads, 0, st>>>(w, V, h->coef, j + 1, n, h->part);
+      tl_launches++, k2_reduce<<<1, kThreads, 0, st>>>(h->part, kAxpyBlocks, h->hcol + j + 1);
     }
   }
   CK2(cudaGetLastError());
@@ -1247,8 +1251,8 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
   iters = 0;
   auto set_scale = [&]() {
     const double* src = pred ? h->x + (int64_t)D.g.K * D.g.nc : h->cscale;
-    k2_maxabs<<<kRedBlocks, kThreads, 0, st>>>(src, D.g.nc, h->part);
-    k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks, mg_stage ? 1 : 0);
+    tl_launches++, k2_maxabs<<<kRedBlocks, kThreads, 0, st>>>(src, D.g.nc, h->part);
+    tl_launches++, k2_weights<<<gc, kThreads, 0, st>>>(D, src, pred ? 1.0 : D.g.eps, h->part, kRedBlocks, mg_stage ? 1 : 0);
     if (f32) {
       tof(h, D.wsc, h->wsc32, D.g.nc);
       tof(h, D.iwsc, h->iwsc32, D.g.nc);
@@ -1257,9 +1261,9 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
   // the true scaled residual of the unscaled x, into V_0; returns its norm
   auto residual = [&](double* beta) -> grte_status {
     set_scale();
-    k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.wsc, nblk, D.g.nc);   // x -> y
+    tl_launches++, k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.wsc, nblk, D.g.nc);   // x -> y
     apply_M(h, pred, h->x, h->Kr);
-    k2_bminus<<<vb, kThreads, 0, st>>>(h->b, h->Kr, n);
+    tl_launches++, k2_bminus<<<vb, kThreads, 0, st>>>(h->b, h->Kr, n);
     apply_P(h, pred, mg_stage, h->Kr, V);
     double b2 = 0.0;
     grte_status r = mdot(h, V, V, 1, n, &b2);
@@ -1279,12 +1283,12 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
     prev = beta;
     if (beta <= thr || floor_reached || cycle == maxcycles) {
       if (floor_reached) beta = 0.0;
-      k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);  // y -> x
+      tl_launches++, k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);  // y -> x
       if (!mg_stage && !(beta <= thr)) h->host_flags |= 1 << GRTE_ENONCONV;
       return GRTE_OK;
     }
-    if (f32) k2_tof<<<vb, kThreads, 0, st>>>(V, h->V32, n, 1.0 / beta);
-    else k2_scale<double><<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
+    if (f32) tl_launches++, k2_tof<<<vb, kThreads, 0, st>>>(V, h->V32, n, 1.0 / beta);
+    else tl_launches++, k2_scale<double><<<vb, kThreads, 0, st>>>(V, 1.0 / beta, n);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int kk = 0;
@@ -1310,8 +1314,8 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
       kk = j + 1;
       if (hn > 0.0) {
-        if (f32) k2_scale<float><<<vb, kThreads, 0, st>>>(h->V32 + (int64_t)(j + 1) * n, 1.0 / hn, n);
-        else k2_scale<double><<<vb, kThreads, 0, st>>>(V + (int64_t)(j + 1) * n, 1.0 / hn, n);
+        if (f32) tl_launches++, k2_scale<float><<<vb, kThreads, 0, st>>>(h->V32 + (int64_t)(j + 1) * n, 1.0 / hn, n);
+        else tl_launches++, k2_scale<double><<<vb, kThreads, 0, st>>>(V + (int64_t)(j + 1) * n, 1.0 / hn, n);
       }
       const double gj = std::fabs(g[j + 1]);
       if (gj <= 0.5 * thr || hn == 0.0) break;
@@ -1324,9 +1328,9 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
       yv[i] = t / H[(size_t)i * m + i];
     }
     CK2(cudaMemcpyAsync(h->coef, yv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
-    if (f32) k2_update<float><<<vb, kThreads, 0, st>>>(h->x, h->V32, h->coef, kk, n);
-    else k2_update<double><<<vb, kThreads, 0, st>>>(h->x, V, h->coef, kk, n);
-    k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);    // y -> x
+    if (f32) tl_launches++, k2_update<float><<<vb, kThreads, 0, st>>>(h->x, h->V32, h->coef, kk, n);
+    else tl_launches++, k2_update<double><<<vb, kThreads, 0, st>>>(h->x, V, h->coef, kk, n);
+    tl_launches++, k2_cellscale<<<gc, kThreads, 0, st>>>(h->x, D.iwsc, nblk, D.g.nc);    // y -> x
     CK2(cudaStreamSynchronize(st));
     CK2(cudaGetLastError());
   }
@@ -1342,13 +1346,13 @@ static grte_status step2(grte2d_t h) {
   const int64_t K = g.K, nc = g.nc;
   int its = 0;
   // prediction at T^n
-  k2_coef<<<gc, kThreads, 0, st>>>(D);
-  k2_vcoef<<<gv, kThreads, 0, st>>>(D);
-  k2_rho<<<gc, kThreads, 0, st>>>(D, D.E, D.rho_n);
-  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
-  k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
-  k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
+  tl_launches++, k2_coef<<<gc, kThreads, 0, st>>>(D);
+  tl_launches++, k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+  tl_launches++, k2_rho<<<gc, kThreads, 0, st>>>(D, D.E, D.rho_n);
+  tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
+  tl_launches++, k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
+  tl_launches++, k2_rhs_pred<<<gc, kThreads, 0, st>>>(D, h->phi, h->b, h->x);
+  tl_launches++, k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
   mirror_coefficients(h);
   if (!h->mgl.empty()) mg_setup(h);
   CK2(cudaGetLastError());
@@ -1362,28 +1366,29 @@ static grte_status step2(grte2d_t h) {
   s = gmres2(h, true, false, (K + 1) * nc, its);
   if (s != GRTE_OK) return s;
   h->stats.krylov_iters += its;
-  k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
+  tl_launches++, k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
   // O* and the flux term of the temperature equation
-  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
-  k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
-  k2_cellsum<double, C_FDIV><<<gc, kThreads, 0, st>>>(D, h->cv, h->tk, nullptr, D.Fdiv, nullptr);
-  if (D.use_guess || D.log_samples) k2_newton_feat<<<gc, kThreads, 0, st>>>(D);
+  tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
+  tl_launches++, k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
+  tl_launches++, k2_cellsum<double, C_FDIV><<<gc, kThreads, 0, st>>>(D, h->cv, h->tk, nullptr, D.Fdiv, nullptr);
+  if (D.use_guess || D.log_samples) tl_launches++, k2_newton_feat<<<gc, kThreads, 0, st>>>(D);
   if (D.use_guess) {
+    tl_launches++;   // the network's guess: one kernel
     cudaError_t e = grte::mlp_guess_launch(h->mlp, D.feat, nc, D.guess, st);
     if (e != cudaSuccess) return fail2(h, GRTE_ECUDA, std::string("mlp guess: ") + cudaGetErrorString(e));
   }
-  k2_newton<<<gc, kThreads, 0, st>>>(D);
+  tl_launches++, k2_newton<<<gc, kThreads, 0, st>>>(D);
   // correction substep 2 at T^{n+1}
-  k2_coef<<<gc, kThreads, 0, st>>>(D);
-  k2_vcoef<<<gv, kThreads, 0, st>>>(D);
-  k2_acU<<<gc, kThreads, 0, st>>>(D);
-  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
-  k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
-  k2_vertex<double, false><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, D.acU}, h->V);
-  k2_cell<double, C_DIVK, false><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr, nullptr);
-  k2_rhs_corr<<<gc, kThreads, 0, st>>>(D, h->GU, h->phi, h->b, h->x);
-  k2_corrscale<<<gc, kThreads, 0, st>>>(D, h->cscale);
-  k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
+  tl_launches++, k2_coef<<<gc, kThreads, 0, st>>>(D);
+  tl_launches++, k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+  tl_launches++, k2_acU<<<gc, kThreads, 0, st>>>(D);
+  tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, nullptr}, h->V);
+  tl_launches++, k2_cell<double, C_DIVK, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, nullptr}, nullptr, h->phi, nullptr, nullptr);
+  tl_launches++, k2_vertex<double, false><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{nullptr, 0, D.acU}, h->V);
+  tl_launches++, k2_cell<double, C_DIVK, false><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{nullptr, 0, D.acU}, nullptr, h->GU, nullptr, nullptr);
+  tl_launches++, k2_rhs_corr<<<gc, kThreads, 0, st>>>(D, h->GU, h->phi, h->b, h->x);
+  tl_launches++, k2_corrscale<<<gc, kThreads, 0, st>>>(D, h->cscale);
+  tl_launches++, k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
   mirror_coefficients(h);
   CK2(cudaGetLastError());
   its = 0;
@@ -1392,8 +1397,8 @@ static grte_status step2(grte2d_t h) {
   h->stats.krylov_iters += its;
   h->stats.krylov_iters_corr += its;
   // projection: E = a c U + eps E_J, O from E (vertex map with the O^n data), U = T^4
-  k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
-  k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{D.E, nc, nullptr}, h->V);
+  tl_launches++, k2_project<<<gc, kThreads, 0, st>>>(D, h->x);
+  tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{D.E, nc, nullptr}, h->V);
   CK2(cudaMemcpyAsync(D.O, h->V, sizeof(double) * K * g.nv, cudaMemcpyDeviceToDevice, st));
   CK2(cudaGetLastError());
   return GRTE_OK;
@@ -1593,8 +1598,10 @@ grte_status grte2d_step(grte2d_t h, int64_t n) {
   h->stats.krylov_iters = 0;
   h->stats.krylov_iters_corr = 0;
   h->stats.krylov_iters_mg = 0;
+  const int64_t l0 = tl_launches;
   for (int64_t i = 0; i < n; ++i) {
     grte_status s = step2(h);
+    h->stats.launches = tl_launches - l0;
     if (s != GRTE_OK) return s;
     h->stats.steps += 1;
   }
@@ -1655,8 +1662,8 @@ grte_status grte2d_get_quadrature(grte2d_t h, double* mu, double* eta, double* w
 grte_status grte2d_get_energy(grte2d_t h, double* e) {
   if (!h) return GRTE_EINVAL;
   if (!e) return fail2(h, GRTE_EINVAL, "e is NULL");
-  k2_energy<<<kRedBlocks, kThreads, 0, h->stream>>>(h->D, h->part);
-  k2_reduce<<<1, kThreads, 0, h->stream>>>(h->part, kRedBlocks, h->dots);
+  tl_launches++, k2_energy<<<kRedBlocks, kThreads, 0, h->stream>>>(h->D, h->part);
+  tl_launches++, k2_reduce<<<1, kThreads, 0, h->stream>>>(h->part, kRedBlocks, h->dots);
   CK2(cudaGetLastError());
   CK2(cudaMemcpyAsync(e, h->dots, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK2(cudaStreamSynchronize(h->stream));

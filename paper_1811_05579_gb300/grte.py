@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("krylov_cycles", ctypes.c_int64), ("newton_iters_max", ctypes.c_int64),
                 ("newton_iters_mean", ctypes.c_double), ("status_flags", ctypes.c_int64),
                 ("line_threads", ctypes.c_int64), ("line_smem", ctypes.c_int64),
-                ("krylov_iters_corr", ctypes.c_int64), ("krylov_iters_mg", ctypes.c_int64)]
+                ("krylov_iters_corr", ctypes.c_int64), ("krylov_iters_mg", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
 
 
 EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_step", "grte_sync",

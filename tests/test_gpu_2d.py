@@ -111,6 +111,7 @@ def test_transport_regime_all_walls_inflow(G):
     h = _pair(G, P, T0, E0, O0)
     S2 = o2.run(P, S, 2)
     h.step(2)
+    assert h.stats()["launches"] > 2 * 20   # every stage of both steps is a kernel of the library
     eT, eE = _rel(h.T(), S2.T), _rel(h.E(), S2.E)
     eO = float(np.max(np.abs(h.O() - S2.O)) / np.max(np.abs(S2.O)))
     print("transport: T %.3e E %.3e O %.3e" % (eT, eE, eO))
