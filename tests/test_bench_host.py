@@ -1,0 +1,46 @@
+"""Host logic of bench.py that needs no GPU: the 2D workload inputs and the reference arm
+(the oracle timed on the host), whose JSON line the driver reads."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_checkerboard_inputs():
+    sig, T0, dt, eps = bench.inputs_2d("checker2d", 64)
+    assert sig.shape == (64, 64) and T0.shape == (64 * 64,)
+    assert set(np.unique(sig)) == {1.0, 100.0}
+    assert sig[0, 0] == 1.0 and sig[0, 8] == 100.0 and sig[8, 8] == 1.0   # 8 x 8 board, block (0, 0) black
+    assert np.all(T0 == 1e-2) and dt == 0.5 / 64 and eps == 1e-3
+    assert bench.workload_name_2d("checker2d", 64) == "2d_checkerboard_64x64_s8"
+
+
+def test_random_smooth_inputs():
+    sig, T0, dt, eps = bench.inputs_2d("lognormal2d", 96)
+    g = np.log(sig)
+    assert sig.shape == (96, 96) and np.all(sig > 0)
+    assert abs(g.mean()) < 1e-12 and abs(g.std() - 1.0) < 1e-12
+    assert np.all(T0 == 1e-2) and dt == 0.5 / 96 and eps == 1e-4
+    # seeded: the same field every time
+    assert np.array_equal(sig, bench.inputs_2d("lognormal2d", 96)[0])
+    assert bench.workload_name_2d("lognormal2d", 96) == "2d_lognormal_96x96_s8"
+
+
+def test_reference_arm_line_for_the_random_smooth_workload():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "lognormal2d", "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "2d_lognormal_512x512_s8"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
