@@ -1230,10 +1230,10 @@ static grte_status arnoldi_step(grte2d_t h, bool pred, bool mg_stage, S* V, int 
 // the ratio of their magnitudes (up to ~1e8 across a front), which stalls the
 // iteration; with one scale it converges in a few iterations to rtol relative to the
 // largest cell.  It ends there, or when a restart no longer gains 4x, or a cycle stops
-// falling (less than 2x over four iterations after a 1e6 reduction), without a
-// verdict: the per-cell scaled solve with the per-cell block preconditioner then runs
-// from its iterate and decides (the cold, opaque cells it still has to fix are nearly
-// local).
+// falling (less than 2x over four iterations after a 1e6 reduction), and never flags
+// ENONCONV: the per-cell scaled solve with the per-cell block preconditioner then runs
+// from its iterate and decides convergence (the cold, opaque cells it still has to fix
+// are nearly local).
 static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& iters) {
   cudaStream_t st = h->stream;
   D2& D = h->D;
