@@ -553,6 +553,10 @@ def run_2d(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:   # weak-scaled replicas: each rank its own copy, max time over ranks
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     from paper_1811_05579_gb300 import grte as G
     n = args.n2d
     sig, T0, dt, eps = inputs_2d(args.workload, n)
@@ -580,6 +584,8 @@ def run_2d(args):
             h_.step(1, allow=allow)
         if clocks:   # the state the timed steps start from (for the end-to-end replay)
             snap["state"] = (h_.T(allow), h_.E(allow), h_.O(allow))
+        if clocks and dist is not None:
+            dist.barrier()
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
@@ -599,6 +605,9 @@ def run_2d(args):
             it[2] += st["krylov_iters_mg"]
             it[3] += st["newton_iters_mean"] / args.steps
             it[4] += st["launches"]
+        if clocks and dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
         return h_, t, it
 
     clocks = ClockSampler(local)
@@ -623,7 +632,7 @@ def run_2d(args):
                    "steps_compared": args.warmup + args.steps}
         h64.close()
     upd = n * n * 40
-    value, t_ms = job_throughput(upd, args.steps, t_ms, world, None)
+    value, t_ms = job_throughput(upd, args.steps, t_ms, world, dist)
     # end to end through the public API with host buffers: the same K steps from the same
     # state, each one copying the whole state (T, E, O) in, stepping and copying it out
     T, E, O = snap["state"]
@@ -673,6 +682,8 @@ def run_2d(args):
     h.close()
     if net is not None:
         net.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
