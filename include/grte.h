@@ -258,15 +258,19 @@ grte_status grte_step1d_noalloc(const grte_instance1d* inst, const grte_options*
  * at a vertex is the mean of the two cell differences across it, that of O at a
  * cell the mean of the two vertex differences along each side; node, cell and U
  * equations, Newton and correction are those of the 1D scheme (Eq. dis-pre,
- * Eq. dis-pre-marshak, Eq. Tnp1, Eq. dis-cor, Eq. dis-proj).  Inflow walls use
- * Eq. bc-pre along the wall normal with E the mean of the two wall cells beside the
- * vertex; a corner of two inflow walls takes the mean of the two walls' values.
+ * Eq. dis-pre-marshak, Eq. Tnp1, Eq. dis-cor, Eq. dis-proj).  A cell beside an inflow
+ * wall applies Eq. bc-pre to its own wall side, as the 1D wall cell does (side =
+ * s 2/eps (b - E_cell) - opposite side); a wall vertex itself uses the same relation
+ * along the normal with E the mean of the two wall cells beside it, and a corner of two
+ * inflow walls takes the mean of the two walls' values.
  *
  * Linear solves: the prediction by GMRES on (e, rho) (E = rho + e, as in 1D) with the
  * matrix applied by stencil kernels and an exact per-cell angular block solve as
- * preconditioner; correction substep 2 by GMRES on the K stacked pair systems
- * (Jacobi preconditioned).  Both run on unknowns scaled per cell by the cell's own
- * magnitude, so that the stopping test holds in every cell.  All arithmetic binary64.
+ * preconditioner (optionally preceded by a multigrid-preconditioned stage, prec2d);
+ * correction substep 2 by GMRES on the K stacked pair systems (Jacobi preconditioned).
+ * Both run on unknowns scaled per cell by the cell's own magnitude, so that the stopping
+ * test holds in every cell.  GRTE_FP64: binary64 throughout; GRTE_MIXED: binary32
+ * Krylov cycles inside binary64 restarts (grte2d_create).
  * -------------------------------------------------------------------------------- */
 typedef struct grte2d_ctx* grte2d_t;
 
