@@ -1,6 +1,7 @@
 """Pins of the 2D oracle (oracle/grte2d.py) against what the paper and the mathematics
 fix: the 1D scheme it must reduce to, equilibrium, conservation, the literal system,
-and the S8 moment conditions."""
+the S8 moment conditions, and the exactness of the directional differences on
+polynomials (which the 1D reduction cannot see: the mixed mu-eta terms)."""
 import numpy as np
 import pytest
 
@@ -126,3 +127,36 @@ def test_eliminated_prediction_matches_literal_system(eps):
     assert np.max(np.abs(E - El)) < 1e-12 * np.max(np.abs(El))
     assert np.max(np.abs(O - Ol)) < 1e-11 * np.max(np.abs(Ol))
     assert np.max(np.abs(U - Ul) / Ul) < 1e-12
+
+
+def _centres_and_vertices(P):
+    xc, yc = np.meshgrid((np.arange(P.Nx) + 0.5) * P.dx, (np.arange(P.Ny) + 0.5) * P.dy)
+    xv, yv = np.meshgrid(np.arange(P.Nx + 1) * P.dx, np.arange(P.Ny + 1) * P.dy)
+    return xc.ravel(), yc.ravel(), xv.ravel(), yv.ravel()
+
+
+def test_directional_differences_exact_on_polynomials():
+    # The vertex gradient D_k and the cell divergence D*_k are the directional derivative
+    # Omega_k . grad, exact on linear fields; through both, quadratics give the second
+    # directional derivative exactly: mu^2 f_xx + 2 mu eta f_xy + eta^2 f_yy.  xy pins the
+    # sign of the cross terms and which cosine goes with which axis; dx != dy pins the
+    # spacings.
+    mu, eta, w = s8_pairs_2d()
+    P = o2.Problem2D(Nx=7, Ny=5, mu=mu, eta=eta, w=w, sig=1.0, Lx=1.3, Ly=0.7)
+    xc, yc, xv, yv = _centres_and_vertices(P)
+    vi, vj = np.arange(P.nv) % (P.Nx + 1), np.arange(P.nv) // (P.Nx + 1)
+    node = (vi > 0) & (vi < P.Nx) & (vj > 0) & (vj < P.Ny)          # vertices with a node equation
+    cp, cq = np.arange(P.nc) % P.Nx, np.arange(P.nc) // P.Nx
+    inner = (cp > 0) & (cp < P.Nx - 1) & (cq > 0) & (cq < P.Ny - 1)   # cells whose 4 vertices are nodes
+    for k in range(P.K):
+        Dk, Ds = o2.grad_matrix(P, k), o2.div_matrix(P, k)
+        m, e = mu[k], eta[k]
+        for a, b in ((1.0, 0.0), (0.0, 1.0), (0.7, -1.9)):
+            g = Dk @ (a * xc + b * yc + 0.3)
+            assert np.allclose(g[node], m * a + e * b, rtol=0, atol=1e-12)
+            assert np.all(g[~node] == 0.0)
+            d = Ds @ (a * xv + b * yv - 0.2)
+            assert np.allclose(d, m * a + e * b, rtol=0, atol=1e-12)
+        for f, want in ((xc ** 2, 2 * m * m), (xc * yc, 2 * m * e), (yc ** 2, 2 * e * e)):
+            second = Ds @ (Dk @ f)
+            assert np.allclose(second[inner], want, rtol=0, atol=1e-11), (k, want)
