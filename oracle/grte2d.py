@@ -45,6 +45,10 @@ wall relation per cell rather than per vertex keeps a cell's outflow from depend
 on its neighbours' E along the wall (with the vertex form, a cold wall cell beside a
 hot one was drained by its neighbour's outflow).
 
+Parity unpinned: the value of O at the four corner vertices of a grid with two inflow
+walls (the corner mean above).  No cell's update reads it, so it reaches only the
+reported O there, and no invariant or limit fixes it.
+
 Linear solves (sparse LU throughout): the prediction on the unknowns (e, rho) with
 E = rho + e exactly as grte1d.coefficients() (O eliminated by the vertex map
 O_k = Q_k E_k + q_k, U* by Eq. dis-pre3); predict_literal() assembles the unknowns

@@ -160,3 +160,28 @@ def test_directional_differences_exact_on_polynomials():
         for f, want in ((xc ** 2, 2 * m * m), (xc * yc, 2 * m * e), (yc ** 2, 2 * e * e)):
             second = Ds @ (Dk @ f)
             assert np.allclose(second[inner], want, rtol=0, atol=1e-11), (k, want)
+
+
+@pytest.mark.parametrize("kind", ["const", "t3"])
+def test_reflection_and_transpose_symmetry(kind):
+    # The S8 pair set is symmetric under x -> -x and under x <-> y, so a problem with
+    # data symmetric under the reflection x -> Lx - x (or, on a square grid, under the
+    # transpose) keeps that symmetry step by step; a wall treatment that favours one
+    # side or one axis breaks it.
+    mu, eta, w = s8_pairs_2d()
+    n = 6
+    rng = np.random.default_rng(41)
+    base = 0.5 + rng.random((n, n))
+    sig = base + base[:, ::-1] + base.T + base.T[:, ::-1]          # symmetric both ways
+    sig = sig + sig[::-1, :]
+    T = 0.3 + 0.2 * rng.random((n, n))
+    T = T + T[:, ::-1] + T.T + T.T[:, ::-1]
+    T = 0.25 * (T + T[::-1, :]) / 2.0
+    P = o2.Problem2D(Nx=n, Ny=n, mu=mu, eta=eta, w=w, sig=sig, eps=1e-2, dt=0.02, kind=kind,
+                     bx0=0.8, bx1=0.8, by0=0.8, by1=0.8)
+    S = o2.equilibrium_state(P, T.ravel())
+    for _ in range(2):
+        S = o2.step(P, S)
+        Tn = S.T.reshape(n, n)
+        assert np.max(np.abs(Tn - Tn[:, ::-1])) < 1e-12 * np.max(Tn)      # x -> Lx - x
+        assert np.max(np.abs(Tn - Tn.T)) < 1e-12 * np.max(Tn)             # x <-> y
