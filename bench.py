@@ -163,10 +163,11 @@ def cpu_baseline(nsteps=3):
     out = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, nsteps=nsteps)],
                          capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(), "kind": "oracle",
                 "sample": "failed: " + out.stderr.strip()[-200:]}
     d = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
+            "kind": "oracle",
             "sample": "%d steps of one run (sigma0=1, eps=1e-2, 8192 cells x 64 dirs), %.1f s, 1 thread"
                       % (d["steps"], d["seconds"])}
 
@@ -509,7 +510,8 @@ print(json.dumps({{"updates": {n} * {n} * 40 * {nsteps}, "seconds": dt_}}))
 """
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": d["updates"] / d["seconds"], "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(),
+            "kind": "oracle",
             "sample": "%d step(s) of the same geometry at %dx%d (sparse LU), %.1f s, 1 thread" % (nsteps, n, n, d["seconds"])}
 
 

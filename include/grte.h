@@ -239,7 +239,7 @@ grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size
  *   E  device, nx*M doubles, line-major E[k*nx + j] (the device layout of grte.h);
  *   O  device, (nx+1)*M doubles, line-major O[k*(nx+1) + i].
  * No cudaMalloc, cudaFree or other allocating call is made: every work buffer is
- * carved from one static device array of about 9.2 MB that every GPU loading this
+ * carved from one static device array of 10,575,872 bytes (about 10.6 MB) that every GPU loading this
  * library holds until the process exits.  Limits: nx <= 4096, n_angle <= 32,
  * nx*n_angle <= 65536; larger sizes return GRTE_EINVAL.  The first call on a device
  * looks up the device address of that array (cudaGetSymbolAddress, with the device

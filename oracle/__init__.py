@@ -17,7 +17,8 @@ arXiv:1811.05579) and cites the section / equation it writes out:
                 reading of the 2D discretisation is in that module's header)
   diffusion1d - the three-stage diffusion solver (Sec. 2, Eq. dis-diff) and the
                 fully implicit limit solvers (Sec. 6, Eq. imp_T and diff_solver)
-  freestream  - the exact characteristic solution of the sigma = 0 limit
+  mlp         - the network of the learned Newton start, in FP64 with BF16-rounded
+                weights (forward and gradient)
 
 The linear systems are solved exactly by direct elimination (block-tridiagonal
 Gaussian elimination, sparse LU); iterative solvers are not used anywhere here.

@@ -869,6 +869,10 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
 
   if (MODE == G_ARNOLDI) {
     if (!D.gactive[ii]) return;                           // uniform over the cluster
+    // g[jcol] is rotated by rank 0 at the end of this step: read it now, before the
+    // cluster barriers below, so that no CTA can see the rotated value and every CTA
+    // takes the same continue/stop decision
+    const double g_jcol = g[jcol];
     // C v_j = alpha v_j + kappa/dx * sum_k S_k  (the HOM pass just ran on v_j)
     const K* vj = Vi(jcol);
     K* cv = zk;
@@ -932,7 +936,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       const double rr = hypot(a0, b0);
       const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
       hc[jcol] = rr;
-      const double gj = g[jcol];
+      const double gj = g_jcol;
       const double gnext = -s0g * gj;
       // GMRES's own (2-norm) estimate; the per-cell test runs on the true residual.
       // Every CTA takes the same decision (its inputs are cluster-wide values).
@@ -1862,6 +1866,12 @@ static grte_status step_epilogue(grte_t h) {
   return GRTE_OK;
 }
 
+// ENONCONV for every instance whose prediction solve is not done (restart limit).
+__global__ void k_flag_undone(const int* __restrict__ gdone, int* status, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!gdone[i]) atomicOr(status + i, 1 << GRTE_ENONCONV);
+}
+
 // Eager step: the host reads the solver flags between launches.
 template <typename R>
 static grte_status step_once(grte_t h) {
@@ -1892,14 +1902,9 @@ static grte_status step_once(grte_t h) {
     for (int i = 0; i < ni; ++i) all = all && h->h_flags[i];
     if (all) break;
     if (cycles >= h->opt.krylov_maxcycles) {
-      // flag the instances that did not converge
-      for (int i = 0; i < ni; ++i) {
-        if (h->h_flags[i]) continue;
-        int si = 0;
-        CK(cudaMemcpy(&si, D.status + i, sizeof(int), cudaMemcpyDeviceToHost));
-        si |= 1 << GRTE_ENONCONV;
-        CK(cudaMemcpy(D.status + i, &si, sizeof(int), cudaMemcpyHostToDevice));
-      }
+      // flag the instances that did not converge (on the handle's stream)
+      k_flag_undone<<<1, 256, 0, st>>>(D.gdone, D.status, ni);
+      CK(cudaGetLastError());
       break;
     }
   }
@@ -2427,8 +2432,11 @@ constexpr int64_t kNaBytes =
     na_round(4 * 16) + na_round(sizeof(Inst)) + na_round(sizeof(Line) * kNaMaxAngles) + na_round(8);
 }  // namespace grte
 
-// Work memory of grte_step1d_noalloc: kNaBytes (about 8.5 MB), held by every GPU that
-// loads the library until the process exits.  Calls share it (see include/grte.h).
+// Work memory of grte_step1d_noalloc: kNaBytes = 10,575,872 bytes (about 10.6 MB),
+// held by every GPU that loads the library until the process exits.  Calls share it
+// (see include/grte.h, which states the same figure; the assertion keeps the two in
+// step when the layout changes).
+static_assert(grte::kNaBytes == 10575872, "no-alloc work memory size changed: update the documented figure");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[grte::kNaBytes];
 static void* g_noalloc_base[64];   // device address of g_noalloc_scratch, per device
 

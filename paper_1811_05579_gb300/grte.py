@@ -179,12 +179,20 @@ def instance_struct(p, keep):
                       p.get("Cv", 1.0), p["eps"])
 
 
-def step1d_noalloc(spec, T_ptr, E_ptr, O_ptr, nsteps, stream=None):
+def step1d_noalloc(spec, T_ptr, E_ptr, O_ptr, nsteps, stream=None, options=None):
     """grte_step1d_noalloc on caller-owned device buffers (device addresses as ints):
-    T (nx), E (nx*M, line-major) and O ((nx+1)*M, line-major), updated in place."""
+    T (nx), E (nx*M, line-major) and O ((nx+1)*M, line-major), updated in place.
+    options: None (the library's defaults) or a dict of grte_options fields."""
     keep = []
     inst = instance_struct(spec, keep)
-    return lib().grte_step1d_noalloc(ctypes.byref(inst), None, T_ptr, E_ptr, O_ptr, nsteps, stream)
+    opt = None
+    if options is not None:
+        opt = Options()
+        lib().grte_default_options(ctypes.byref(opt))
+        for k, v in options.items():
+            setattr(opt, k, v)
+        opt = ctypes.byref(opt)
+    return lib().grte_step1d_noalloc(ctypes.byref(inst), opt, T_ptr, E_ptr, O_ptr, nsteps, stream)
 
 
 def _f32(a):
