@@ -98,7 +98,14 @@ typedef struct {
                             multigrid V-cycle on the cells' rho Schur complement (one scale
                             for all cells), then the per-cell scaled solve with the block
                             preconditioner.  Ignored by the 1D path                        */
+  int solver1d;          /* 1D prediction solve: GRTE_SOLVER_AUTO (default): in GRTE_MIXED, when
+                            every instance has 64 <= nx <= 8192 and n_angle <= 32, the whole
+                            solve of an instance runs in one persistent kernel on a cluster of
+                            up to 16 CTAs (the angular unknowns of each 512-cell slice held in
+                            shared memory), else the line kernels; GRTE_SOLVER_LINES: always
+                            the line kernels (one launch per line pass and Krylov step)      */
 } grte_options;
+enum { GRTE_SOLVER_AUTO = 0, GRTE_SOLVER_LINES = 1 };
 
 /* Statistics of the last grte_step call (summed over its steps and instances). */
 typedef struct {
@@ -169,7 +176,7 @@ grte_status grte_get_tuning(grte_t h, int* line_threads, double* ms, size_t n);
 /* Kernel ids for per-kernel timing. */
 enum { GRTE_K_CELL_COEF = 0, GRTE_K_RHO = 1, GRTE_K_PRED_FACTOR = 2, GRTE_K_PRED_HOM = 3,
        GRTE_K_PRED_FULL = 4, GRTE_K_GMRES = 5, GRTE_K_NEWTON = 6, GRTE_K_CORR = 7,
-       GRTE_K_PROJECT = 8, GRTE_K_ENERGY = 9, GRTE_NKERNELS = 10 };
+       GRTE_K_PROJECT = 8, GRTE_K_ENERGY = 9, GRTE_K_PRED_SOLVE = 10, GRTE_NKERNELS = 11 };
 /* Start recording a CUDA event pair around every launch of the kernels whose bit
  * (1 << id) is set in kernel_mask, on the handle's stream (device-side timing). */
 grte_status grte_profile_begin(grte_t h, uint32_t kernel_mask);

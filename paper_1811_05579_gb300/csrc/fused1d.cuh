@@ -1,0 +1,956 @@
+// fused1d.cuh - the prediction solve of one 1D time step as one persistent kernel per
+// instance (GB300, sm_103a).  Included by grte1d.cu inside namespace grte.
+//
+// What it computes is what the line-kernel path computes: the prediction of Algorithm 2
+// (Eq. dis-pre, Eq. dis-pre-marshak, wall rows Eq. bc-pre) written on (rho, e), E = rho + e,
+//   e-equation     (A + G_k) e_k = h_k - alpha rho - G_k rho        (tridiagonal per angle)
+//   conservation   R(rho) = alpha rho - kappa rho^n/(c dt) - s a c U^n + kappa/dx F(rho) = 0,
+//                  F_j = sum_k w_k v_k (O_{j+1,k} - O_{j,k}),
+// solved for rho by restarted GMRES left-preconditioned by the single-effective-angle Schur
+// operator P = alpha + Gbar (A + Gbar)^{-1} beta (Gbar = sum_k w_k G_k, beta = A - alpha).
+// Its outputs are the converged rho* (D.gx) and F* (D.Fs), read by the Newton kernel.
+//
+// How it runs: one thread-block cluster of Q CTAs per instance (Q in {1,2,4,8,16}), CTA q
+// owning the 512-cell slice [512 q, 512 q + 512) (cells past nx are decoupled identity rows).
+// The cluster runs every restart cycle, Arnoldi step, line pass and preconditioner
+// application of the solve without leaving the kernel; control decisions are taken from
+// cluster-wide sums reduced in a fixed rank order, so every CTA takes the same branch.
+//   - A line pass (the product behind one GMRES matrix-vector product) keeps the unknowns of
+//     all angles of the slice in shared memory: warp w owns cells [32 w, 32 w + 32), lane k
+//     the angle v_k (M <= 32).  Each thread eliminates its 32-cell chunk with the tridiagonal
+//     coefficients recomputed from per-cell arrays held in shared memory (binary32), so a pass
+//     reads no per-element data besides the state (data passes only).  The chunks' end rows
+//     form a 32-row tridiagonal system per angle, solved by parallel cyclic reduction (PCR)
+//     together with its two unit spikes; the slices' 2x2 Schur complements then form a
+//     2Q-row interface system per angle, gathered through distributed shared memory and
+//     solved by PCR in every CTA; each thread finally back-substitutes its chunk.
+//   - The angular sums of the flux are reduced per cell in shared memory in a fixed order.
+//   - The Krylov vectors (binary64) live in global memory, one slice per CTA; dot products
+//     are block sums then cluster sums in rank order (bit-reproducible).
+//   - The preconditioner is one tridiagonal solve per instance in binary64, run by warp 0 of
+//     every CTA on its slice with the same chunk / PCR / interface construction.
+// Mixed precision only (binary32 line passes, binary64 per-cell parts, Krylov vectors,
+// preconditioner, the two inflow wall rows and the true residual's angular sums).
+
+namespace grte {
+
+constexpr int kFL = 32;           // cells per chunk (one thread's serial sweep)
+constexpr int kFW = 16;           // chunks (warps) per slice
+constexpr int kFS = kFL * kFW;    // cells per slice (one CTA)
+constexpr int kFT = 32 * kFW;     // threads per CTA
+constexpr int kFQ = 16;           // largest cluster: nx <= kFQ * kFS
+constexpr int kFR = 2 * kFW;      // reduced rows per angle and slice
+constexpr int kFX = 33;           // padded row length of the slice's unknowns
+constexpr int kFPL = kFS / 32;    // cells per lane of the preconditioner's warp (16)
+
+struct FSmem {
+  float x[kFS][kFX];                                   // unknowns of the slice, [cell][angle]
+  // per-cell binary32 arrays of the slice with one halo cell each side (index j - c0 + 1)
+  float A[kFS + 2], gl[kFS + 2], gu[kFS + 2], gb[kFS + 2], od[kFS + 2], dlx[kFS + 2], kcd[kFS + 2],
+      kdx[kFS + 2];
+  float P1[kFS], P2[kFS], P3[kFS];                      // per-cell parts of the pass
+  // reduced systems: [row][angle]
+  float ra[kFR][32], rb[kFR][32], rc[kFR][32], rr[kFR][32], rg[kFR][32], rh[kFR][32];
+  float ends[2][4][32];                                 // published: S11 S12 S21 S22 (double-buffered)
+  float endr[2][2][32];                                 // published: r'_F, r'_L
+  float coup[2][2][32];                                 // published: a at the first cell, c at the last
+  float xlr[2][32];                                     // e at c0 - 1 and at c0 + kFS, per angle
+  float vk[32], v2k[32], wvk[32];                       // per-angle constants (0 past M)
+  double vkd[32], wvkd[32];
+  double fl[kFS];                                       // flux sums of the last pass
+  double fdat[kFS];                                     // data part of the flux (data passes)
+  double pu[kFS];                                       // preconditioner solution (slice)
+  double pxr[kFPL][32], pch[kFPL][32], pah[kFPL][32];  // its chunk sweeps, [u][lane]
+  double wgt[kFS];                                      // stopping-test weights
+  double wall[2][32];                                   // wall-row right-hand sides (double)
+  double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
+  double part[2][kMaxRestart + 2];                      // cluster partials (double-buffered)
+  double sums[kMaxRestart + 2];
+  // binary64 preconditioner: reduced rows of the 32 lane chunks (64 rows), interface
+  double pe[2][6];                                      // published: S11 S12 S21 S22 r'F r'L
+  double pcoup[2][2];
+  double pxl[2];
+  // GMRES state (identical in every CTA)
+  double H[(kMaxRestart + 1) * kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart],
+      y[kMaxRestart];
+};
+
+// Per-CTA geometry.
+struct FGeo {
+  int ii, q, Q;         // instance, slice, slices in the cluster
+  int64_t c0, co;       // first cell of the slice (instance-local), instance cell offset
+  int N, M;
+};
+
+// Sums of nv values per thread over the CTA (fixed order), result in sm.sums[0..nv-1] for
+// every thread.  nv <= kMaxRestart + 2.
+__device__ void f_block_sums(FSmem& sm, double* v, int nv) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    double t = v[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sm.red[wid][i] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int w = 0; w < kFW; ++w) t += sm.red[w][threadIdx.x];
+    sm.sums[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+__device__ double f_block_max(FSmem& sm, double v) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sm.red[wid][0] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kFW; ++w) t = fmax(t, sm.red[w][0]);
+  __syncthreads();
+  return t;
+}
+
+// Cluster sums (is_max = 0) or maxima of the nv values in sm.sums (rank order); result in
+// sm.sums for every thread.  par selects the half of the double buffer.
+__device__ void f_cluster_reduce(FSmem& sm, cg::cluster_group& cl, int& par, int nv, bool is_max) {
+  if (threadIdx.x < nv) sm.part[par][threadIdx.x] = sm.sums[threadIdx.x];
+  cl.sync();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    const int Q = (int)cl.num_blocks();
+    for (int r = 0; r < Q; ++r) {
+      const double v = cl.map_shared_rank(&sm.part[par][0], r)[threadIdx.x];
+      t = is_max ? fmax(t, v) : t + v;
+    }
+    sm.sums[threadIdx.x] = t;
+  }
+  par ^= 1;
+  __syncthreads();
+}
+
+// Tridiagonal coefficients of line k at the slice-local cell jl (halo index):
+//   a = -v^2 gl, b = A + v^2 (gl + gu) + v gb, c = -v^2 gu   (LineCoef).
+__device__ __forceinline__ void f_coef(const FSmem& sm, int jl, float v, float v2, float& a, float& b, float& c) {
+  const float l = sm.gl[jl], u = sm.gu[jl];
+  a = -v2 * l;
+  c = -v2 * u;
+  b = fmaf(v, sm.gb[jl], fmaf(v2, l + u, sm.A[jl]));
+}
+
+// PCR on n <= kFR rows per lane of (ra, rb, rc) with nr right-hand sides (rr, rg, rh), in
+// place; on return rr (rg, rh) hold the solutions.  Every thread takes part.
+template <int NR>
+__device__ void f_pcr(FSmem& sm, int n) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = threadIdx.x >> 5;   // rows r0 and r0 + kFW
+  for (int st = 1; st < n; st <<= 1) {
+    float na[2], nb[2], nc[2], nrr[2][NR];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int i = r0 + p * kFW;
+      if (i >= n) continue;
+      const bool hl = i - st >= 0, hr = i + st < n;
+      const float k1 = hl ? sm.ra[i][lane] / sm.rb[i - st][lane] : 0.0f;
+      const float k2 = hr ? sm.rc[i][lane] / sm.rb[i + st][lane] : 0.0f;
+      na[p] = hl ? -sm.ra[i - st][lane] * k1 : 0.0f;
+      nc[p] = hr ? -sm.rc[i + st][lane] * k2 : 0.0f;
+      float b = sm.rb[i][lane];
+      if (hl) b -= sm.rc[i - st][lane] * k1;
+      if (hr) b -= sm.ra[i + st][lane] * k2;
+      nb[p] = b;
+      float* R[3] = {&sm.rr[0][0], &sm.rg[0][0], &sm.rh[0][0]};
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        float r = R[q][i * 32 + lane];
+        if (hl) r -= R[q][(i - st) * 32 + lane] * k1;
+        if (hr) r -= R[q][(i + st) * 32 + lane] * k2;
+        nrr[p][q] = r;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int i = r0 + p * kFW;
+      if (i >= n) continue;
+      sm.ra[i][lane] = na[p];
+      sm.rb[i][lane] = nb[p];
+      sm.rc[i][lane] = nc[p];
+      float* R[3] = {&sm.rr[0][0], &sm.rg[0][0], &sm.rh[0][0]};
+#pragma unroll
+      for (int q = 0; q < NR; ++q) R[q][i * 32 + lane] = nrr[p][q];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int i = r0 + p * kFW;
+    if (i >= n) continue;
+    const float ib = 1.0f / sm.rb[i][lane];
+    sm.rr[i][lane] *= ib;
+    if (NR > 1) sm.rg[i][lane] *= ib;
+    if (NR > 2) sm.rh[i][lane] *= ib;
+  }
+  __syncthreads();
+}
+
+// Solve the M line systems (A + G_k) e_k = x_k of the instance for the right-hand sides in
+// sm.x (this CTA's slice), in place.  sm.xlr receives e at the neighbouring cells c0 - 1
+// and c0 + kFS.  All threads of all CTAs of the cluster take part.
+__device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, int& par) {
+  const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float v = sm.vk[k], v2 = sm.v2k[k];
+  const int row0 = w * kFL;
+  float ch[kFL - 2], ah[kFL - 2];
+  float rhp = 0.0f;
+  // down sweep over the chunk's interior: x_u = rh_u - ch_u x_{u+1} - ah_u x_s
+#pragma unroll
+  for (int u = 1; u <= kFL - 2; ++u) {
+    float a, b, c;
+    f_coef(sm, row0 + u + 1, v, v2, a, b, c);
+    const float r = sm.x[row0 + u][k];
+    float den, ahv, num;
+    if (u == 1) {
+      den = b;
+      ahv = a;
+      num = r;
+    } else {
+      den = fmaf(-a, ch[u - 2], b);
+      ahv = -a * ah[u - 2];
+      num = fmaf(-a, rhp, r);
+    }
+    const float inv = 1.0f / den;
+    ch[u - 1] = c * inv;
+    ah[u - 1] = ahv * inv;
+    rhp = num * inv;
+    sm.x[row0 + u][k] = rhp;
+  }
+  // up chain: x_1 = rc - cc x_e - ac x_s
+  float rc = rhp, cc = ch[kFL - 3], ac = ah[kFL - 3];
+#pragma unroll
+  for (int u = kFL - 3; u >= 1; --u) {
+    const float chu = ch[u - 1];
+    rc = fmaf(-chu, rc, sm.x[row0 + u][k]);
+    cc = -chu * cc;
+    ac = fmaf(-chu, ac, ah[u - 1]);
+  }
+  {
+    float as, bs, cs, ae, be, ce;
+    f_coef(sm, row0 + 1, v, v2, as, bs, cs);
+    f_coef(sm, row0 + kFL, v, v2, ae, be, ce);
+    const float rs = sm.x[row0][k], re = sm.x[row0 + kFL - 1][k];
+    sm.ra[2 * w][k] = (w == 0) ? 0.0f : as;
+    sm.rb[2 * w][k] = fmaf(-cs, ac, bs);
+    sm.rc[2 * w][k] = -cs * cc;
+    sm.rr[2 * w][k] = fmaf(-cs, rc, rs);
+    sm.ra[2 * w + 1][k] = -ae * ah[kFL - 3];
+    sm.rb[2 * w + 1][k] = fmaf(-ae, ch[kFL - 3], be);
+    sm.rc[2 * w + 1][k] = (w == kFW - 1) ? 0.0f : ce;
+    sm.rr[2 * w + 1][k] = fmaf(-ae, rhp, re);
+    sm.rg[2 * w][k] = (w == 0) ? 1.0f : 0.0f;          // unit spikes of the slice's reduced system
+    sm.rg[2 * w + 1][k] = 0.0f;
+    sm.rh[2 * w][k] = 0.0f;
+    sm.rh[2 * w + 1][k] = (w == kFW - 1) ? 1.0f : 0.0f;
+    if (w == 0) sm.coup[par][0][k] = as;               // a at the slice's first cell
+    if (w == kFW - 1) sm.coup[par][1][k] = ce;         // c at its last cell
+  }
+  __syncthreads();
+  f_pcr<3>(sm, kFR);
+  // the slice's 2x2 Schur complement on (first, last): S = Z^{-1}, Z = [[g0, h0], [g1, h1]]
+  if (w == 0) {
+    const float z00 = sm.rg[0][k], z0n = sm.rh[0][k], zn0 = sm.rg[kFR - 1][k], znn = sm.rh[kFR - 1][k];
+    const float det = z00 * znn - z0n * zn0;
+    const float id = 1.0f / det;
+    const float S11 = znn * id, S12 = -z0n * id, S21 = -zn0 * id, S22 = z00 * id;
+    const float y0 = sm.rr[0][k], y1 = sm.rr[kFR - 1][k];
+    sm.ends[par][0][k] = S11;
+    sm.ends[par][1][k] = S12;
+    sm.ends[par][2][k] = S21;
+    sm.ends[par][3][k] = S22;
+    sm.endr[par][0][k] = S11 * y0 + S12 * y1;
+    sm.endr[par][1][k] = S21 * y0 + S22 * y1;
+  }
+  cl.sync();
+  // interface system of all slices, rows [F_0, L_0, F_1, L_1, ...] per angle:
+  //   a_q L_{q-1} + S11 F_q + S12 L_q = r'_F,   S21 F_q + S22 L_q + c_q F_{q+1} = r'_L
+  // (built in every CTA from the gathered values into ra..rr; the slice's own y, g, h
+  // are kept in rr/rg/rh until then)
+  const int Q = G.Q, n2 = 2 * Q;
+  float yk[2] = {0.0f, 0.0f}, gk[2] = {0.0f, 0.0f}, hk[2] = {0.0f, 0.0f};
+  {
+    const int r0 = threadIdx.x >> 5;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int i = r0 + p * kFW;
+      yk[p] = sm.rr[i][k];
+      gk[p] = sm.rg[i][k];
+      hk[p] = sm.rh[i][k];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n2 * 32; idx += kFT) {
+    const int i = idx >> 5, kk = idx & 31, qq = i >> 1, side = i & 1;
+    const float* e = cl.map_shared_rank(&sm.ends[par][0][0], qq);
+    const float* er = cl.map_shared_rank(&sm.endr[par][0][0], qq);
+    const float* cp = cl.map_shared_rank(&sm.coup[par][0][0], qq);
+    if (side == 0) {
+      sm.ra[i][kk] = (qq > 0) ? cp[kk] : 0.0f;
+      sm.rb[i][kk] = e[0 * 32 + kk];
+      sm.rc[i][kk] = e[1 * 32 + kk];
+      sm.rr[i][kk] = er[0 * 32 + kk];
+    } else {
+      sm.ra[i][kk] = e[2 * 32 + kk];
+      sm.rb[i][kk] = e[3 * 32 + kk];
+      sm.rc[i][kk] = (qq < Q - 1) ? cp[32 + kk] : 0.0f;
+      sm.rr[i][kk] = er[1 * 32 + kk];
+    }
+  }
+  __syncthreads();
+  // this CTA's couplings (read before the interface solve reuses the arrays)
+  const float a_first = sm.coup[par][0][k], c_last = sm.coup[par][1][k];
+  f_pcr<1>(sm, n2);
+  const float Lp = (G.q > 0) ? sm.rr[2 * G.q - 1][k] : 0.0f;
+  const float Fn = (G.q < Q - 1) ? sm.rr[2 * G.q + 2][k] : 0.0f;
+  __syncthreads();
+  if (w == 0) {
+    sm.xlr[0][k] = Lp;
+    sm.xlr[1][k] = Fn;
+  }
+  // the slice's reduced solution: y - L_{q-1} a g - F_{q+1} c h
+  {
+    const int r0 = threadIdx.x >> 5;
+    const float la = Lp * a_first, fc = Fn * c_last;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int i = r0 + p * kFW;
+      sm.rr[i][k] = yk[p] - la * gk[p] - fc * hk[p];
+    }
+  }
+  par ^= 1;
+  __syncthreads();
+  // back substitution of the chunk
+  const float xs = sm.rr[2 * w][k], xe = sm.rr[2 * w + 1][k];
+  sm.x[row0][k] = xs;
+  sm.x[row0 + kFL - 1][k] = xe;
+  float xn = xe;
+#pragma unroll
+  for (int u = kFL - 2; u >= 1; --u) {
+    xn = fmaf(-ch[u - 1], xn, fmaf(-ah[u - 1], xs, sm.x[row0 + u][k]));
+    sm.x[row0 + u][k] = xn;
+  }
+  __syncthreads();
+}
+
+// Load the slice's per-cell binary32 arrays (with halos) and the angle constants.
+__device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G) {
+  for (int t = threadIdx.x; t < kFS + 2; t += kFT) {
+    const int64_t j = G.c0 + t - 1;
+    const bool in = j >= 0 && j < G.N;
+    const int64_t g = G.co + j;
+    sm.A[t] = in ? D.fc.A[g] : 1.0f;
+    sm.gl[t] = in ? D.fc.gl[g] : 0.0f;
+    sm.gu[t] = in ? D.fc.gu[g] : 0.0f;
+    sm.gb[t] = in ? D.fc.gb[g] : 0.0f;
+    sm.od[t] = in ? D.fc.od[g] : 0.0f;
+    sm.dlx[t] = in ? D.fc.dlx[g] : 0.0f;
+    sm.kcd[t] = in ? D.fc.kcd[g] : 0.0f;
+    sm.kdx[t] = in ? D.fc.kdx[g] : 0.0f;
+  }
+  if (threadIdx.x < 32) {
+    const int k = threadIdx.x;
+    const bool ka = k < G.M;
+    const double v = ka ? D.v[I.ang_off + k] : 0.0, w = ka ? D.w[I.ang_off + k] : 0.0;
+    sm.vk[k] = (float)v;
+    sm.v2k[k] = (float)(v * v);
+    sm.wvk[k] = (float)(w * v);
+    sm.vkd[k] = v;
+    sm.wvkd[k] = w * v;
+  }
+  __syncthreads();
+}
+
+// Per-cell parts of a pass at the per-cell vector xg (instance-local, global, complete):
+//   P1 = -alpha x (+ (s a c + kappa a c/(c dt)) U^n on data passes), P2 = Gint x, P3 = gb x,
+//   fl = Frho = wv2 [fR (x_j - x_{j+1}) + fL (x_j - x_{j-1})] + wv gbx x_j
+//        (data passes: minus 2/eps sum_k w_k v_k b at the inflow walls).
+template <bool FULL>
+__device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const double* xg) {
+  const int t = threadIdx.x;
+  const int64_t j = G.c0 + t;
+  if (j < G.N) {
+    const int64_t g = G.co + j, N = G.N;
+    const double xj = xg[j], xl = j > 0 ? xg[j - 1] : 0.0, xr = j < N - 1 ? xg[j + 1] : 0.0;
+    double p1 = -D.cf.alpha[g] * xj;
+    if (FULL) p1 += (D.cf.sac[g] + D.cf.kcd[g] * I.a * I.c) * D.U[g];
+    const double p2 = D.cf.gl[g] * (xj - xl) + D.cf.gu[g] * (xj - xr);
+    const double p3 = D.cf.gb[g] * xj;
+    double fr = I.wv2 * (D.cf.fR[g] * (xj - xr) + D.cf.fL[g] * (xj - xl)) + I.wv * D.cf.gbx[g] * xj;
+    if (FULL && I.bc == GRTE_BC_INFLOW) {
+      if (j == 0) fr -= I.two_eps * I.bLflux;
+      if (j == N - 1) fr -= I.two_eps * I.bRflux;
+    }
+    sm.P1[t] = (float)p1;
+    sm.P2[t] = (float)p2;
+    sm.P3[t] = (float)p3;
+    sm.fl[t] = FULL ? fr : (double)(float)fr;
+  } else {
+    sm.P1[t] = 0.0f;
+    sm.P2[t] = 0.0f;
+    sm.P3[t] = 0.0f;
+    sm.fl[t] = 0.0;
+  }
+  sm.fdat[t] = 0.0;
+}
+
+// Data part of a data pass: the right-hand side terms kappa/(c dt) Eh^n - kappa v/dx (o_{j+1} - o_j)
+// (o_i = d_i eps^2 O^n_i/(c dt) at interior nodes, 0 at the walls) into sm.x, and the data
+// part of the flux sum_k w_k v_k (o_{j+1,k} - o_{j,k}) into sm.fdat (not at inflow wall cells).
+// Warp w loads the 32 cells of its chunk for one angle at a time (coalesced rows of the
+// angle-major state) and writes them transposed.
+__device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t N = G.N, j = G.c0 + w * kFL + lane;
+  const int jl = w * kFL + lane + 1;
+  const float* Eh = (const float*)D.Eh + I.elem_off;
+  const float* On = (const float*)D.O + I.nelem_off;
+  const bool real = j < N;
+  const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
+  const float kcd = sm.kcd[jl], kdx = sm.kdx[jl], odj = sm.od[jl], odr = sm.od[jl + 1];
+  double fd = 0.0;
+  for (int kk = 0; kk < G.M; ++kk) {
+    const float* Ek = Eh + (int64_t)kk * N;
+    const float* Ok = On + (int64_t)kk * (N + 1);
+    const float e = real ? Ek[j] : 0.0f;
+    const float oj = (j >= 1 && j <= N - 1) ? odj * Ok[j] : 0.0f;
+    float or_ = __shfl_down_sync(0xffffffffu, oj, 1);
+    if (lane == 31) or_ = (j + 1 >= 1 && j + 1 <= N - 1) ? odr * Ok[j + 1] : 0.0f;
+    const float Dj = or_ - oj;
+    sm.x[w * kFL + lane][kk] = real ? fmaf(kcd, e, -kdx * sm.vk[kk] * Dj) : 0.0f;
+    if (real && !wallc) fd += sm.wvkd[kk] * (double)Dj;
+  }
+  for (int kk = G.M; kk < 32; ++kk) sm.x[w * kFL + lane][kk] = 0.0f;
+  sm.fdat[w * kFL + lane] = fd;
+  __syncwarp();
+}
+
+// Right-hand side of the inflow wall row j (0 or N-1) for angle k in binary64:
+//   P1 - v^2 P2 + kappa v (2/eps)(b - x)/dx  [+ kappa/(c dt) Eh^n - kappa v o/dx on data passes,
+//   o = 2 o_1 (left) or -2 o_{N-1} (right)] (the O(eps) difference is formed in double).
+template <bool FULL>
+__device__ double f_wall_rhs(const Dev& D, const Inst& I, const FGeo& G, const double* xg, int64_t j, int k) {
+  const int64_t N = G.N, g = G.co + j;
+  const double v = D.v[I.ang_off + k], v2 = v * v;
+  const double xj = xg[j], xl = j > 0 ? xg[j - 1] : 0.0, xr = j < N - 1 ? xg[j + 1] : 0.0;
+  double p1 = -D.cf.alpha[g] * xj;
+  if (FULL) p1 += (D.cf.sac[g] + D.cf.kcd[g] * I.a * I.c) * D.U[g];
+  const double p2 = D.cf.gl[g] * (xj - xl) + D.cf.gu[g] * (xj - xr);
+  const double b = FULL ? ((j == 0) ? D.bL[I.ang_off + k] : D.bR[I.ang_off + k]) : 0.0;
+  double r = p1 - v2 * p2 + D.cf.kdx[g] * v * I.two_eps * (b - xj);
+  if (FULL) {
+    const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (N + 1);
+    const float* Ek = (const float*)D.Eh + I.elem_off + (int64_t)k * N;
+    const int64_t ni = (j == 0) ? 1 : N - 1;
+    const double on = (double)(D.fc.od[G.co + ni] * Ok[ni]);
+    const double o = (j == 0) ? 2.0 * on : -2.0 * on;
+    r += D.cf.kcd[g] * (double)Ek[j] - D.cf.kdx[g] * v * o;
+  }
+  return r;
+}
+
+// One line pass at the per-cell vector xg (FULL: the iterate, with the data terms; HOM: a
+// Krylov direction).  On return sm.fl[t] holds F_j for the slice's cells (double; HOM:
+// the binary32 sum widened).  xg must be complete in global memory (a cluster barrier
+// precedes the call inside).
+template <bool FULL>
+__device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
+                       const double* xg, int& par) {
+  cl.sync();   // xg complete on every slice (halo reads)
+  const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t N = G.N;
+  f_cellparts<FULL>(sm, D, I, G, xg);
+  if (FULL) f_stage_data(sm, D, I, G);
+  __syncthreads();
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  const float v = sm.vk[k], v2 = sm.v2k[k];
+  // right-hand sides r = P1 - v^2 P2 - v P3 (+ data) of the chunk
+#pragma unroll 4
+  for (int u = 0; u < kFL; ++u) {
+    const int t = w * kFL + u;
+    float r = fmaf(-v, sm.P3[t], fmaf(-v2, sm.P2[t], sm.P1[t]));
+    if (FULL) r += sm.x[t][k];
+    sm.x[t][k] = (k < G.M) ? r : 0.0f;
+  }
+  // inflow wall rows in double
+  if (inflow && k < G.M) {
+    for (int side = 0; side < 2; ++side) {
+      const int64_t jw = side == 0 ? 0 : N - 1;
+      const int64_t tl = jw - G.c0;
+      if (tl >= 0 && tl < kFS && (int)(tl / kFL) == w) {
+        const double r = f_wall_rhs<FULL>(D, I, G, xg, jw, k);
+        sm.wall[side][k] = r;
+        sm.x[tl][k] = (float)r;
+      }
+    }
+  }
+  __syncthreads();
+  f_line_solve(sm, cl, G, par);
+  // inflow walls: e re-solved in double from the neighbour; e/o wall flux in double
+  if (inflow && w == 0) {
+    for (int side = 0; side < 2; ++side) {
+      const int64_t jw = side == 0 ? 0 : N - 1;
+      const int64_t tl = jw - G.c0;
+      if (!(tl >= 0 && tl < kFS)) continue;
+      double sw = 0.0;
+      if (k < G.M) {
+        const double vd = sm.vkd[k], v2d = vd * vd;
+        const int64_t g = G.co + jw;
+        const double bw = D.cf.A[g] + v2d * (D.cf.gl[g] + D.cf.gu[g]) + vd * D.cf.gb[g];
+        // neighbour value (float solution) and the node term next to the wall
+        const int64_t jn = side == 0 ? 1 : N - 2;
+        const int64_t tn = jn - G.c0;
+        const double en = (tn >= 0) ? (double)sm.x[tn][k] : (double)sm.xlr[0][k];
+        const double ew = side == 0 ? (sm.wall[0][k] + v2d * D.cf.gu[g] * en) / bw
+                                    : (sm.wall[1][k] + v2d * D.cf.gl[g] * en) / bw;
+        const int64_t ni = side == 0 ? 1 : N - 1;
+        double on = 0.0;
+        if (FULL) {
+          const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (N + 1);
+          on = (double)(D.fc.od[G.co + ni] * Ok[ni]);
+        }
+        const double dl = D.cf.dlx[G.co + ni];
+        if (side == 0) {
+          const double O1 = on - dl * vd * (en - ew);
+          sw = sm.wvkd[k] * (2.0 * O1 + I.two_eps * ew);
+        } else {
+          const double ON1 = on - dl * vd * (ew - en);
+          sw = sm.wvkd[k] * (I.two_eps * ew - 2.0 * ON1);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
+      if (k == 0) sm.fl[tl] += sw;
+    }
+  }
+  // e/o flux w_k v_k (O_{j+1} - O_j) of every interior cell without the data part:
+  //   -w_k v_k^2 [dlx_{j+1} (e_{j+1} - e_j) - dlx_j (e_j - e_{j-1})]  (node terms at 1..N-1)
+  float val[kFL];
+  {
+    const float wv = sm.wvk[k];
+#pragma unroll
+    for (int u = 0; u < kFL; ++u) {
+      const int t = w * kFL + u;
+      const int64_t j = G.c0 + t;
+      const float ej = sm.x[t][k];
+      const float el = (t > 0) ? sm.x[t - 1][k] : sm.xlr[0][k];
+      const float er = (t < kFS - 1) ? sm.x[t + 1][k] : sm.xlr[1][k];
+      const float OR = (j + 1 <= N - 1) ? sm.dlx[t + 2] * (er - ej) : 0.0f;
+      const float OL = (j >= 1) ? sm.dlx[t + 1] * (ej - el) : 0.0f;
+      const bool wallc = inflow && (j == 0 || j == N - 1);
+      val[u] = (j < N && !wallc) ? -wv * v * (OR - OL) : 0.0f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kFL; ++u) sm.x[w * kFL + u][k] = val[u];
+  __syncthreads();
+  {
+    const int t = threadIdx.x;
+    const int64_t j = G.c0 + t;
+    if (j < N && !(inflow && (j == 0 || j == N - 1))) {
+      if (FULL) {
+        double s = 0.0;
+        for (int kk = 0; kk < G.M; ++kk) s += (double)sm.x[t][kk];
+        sm.fl[t] += sm.fdat[t] + s;
+      } else {
+        float s = 0.0f;
+        for (int kk = 0; kk < G.M; ++kk) s += sm.x[t][kk];
+        sm.fl[t] = (double)((float)sm.fl[t] + s);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// PCR step on rows held two per lane (row 2 lane + p) of a 64-row system, by shuffles.
+__device__ __forceinline__ double f_pick(double a0, double a1, int p) { return p ? a1 : a0; }
+
+// z = P^{-1} rin on the slice (binary64), P the single-effective-angle Schur operator:
+//   u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) rin,  z = (rin - Gbar u)/alpha.
+// Warp 0 of every CTA solves the slice's rows (32 lanes x 16 cells, reduced 64 rows by
+// PCR in registers, 2x2 Schur complements to the interface, PCR over the 2Q interface rows
+// per CTA); the other warps wait.  rin and z: instance-local global vectors (own slice).
+__device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
+                       const double* rin, double* z, int& par) {
+  const int64_t N = G.N, co = G.co;
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
+  const double wv = I.wv, wv2 = I.wv2;
+  auto coef = [&](int64_t j, double& a, double& b, double& c) {
+    if (j >= N) { a = 0.0; b = 1.0; c = 0.0; return; }
+    const int64_t g = co + j;
+    const double f = D.cf.A[g] * D.cf.ralpha[g];
+    const double l = D.cf.gl[g], u = D.cf.gu[g];
+    a = j > 0 ? -f * wv2 * l : 0.0;
+    c = j < N - 1 ? -f * wv2 * u : 0.0;
+    b = D.cf.A[g] + f * (wv2 * (l + u) + wv * D.cf.gb[g]);
+  };
+  const int64_t s = G.c0 + lane * kFPL;   // this lane's chunk (warp 0)
+  double (*xr)[32] = sm.pxr;
+  double (*ch)[32] = sm.pch;
+  double (*ah)[32] = sm.pah;
+  double ra0 = 0, ra1 = 0, rb0 = 1, rb1 = 1, rc0 = 0, rc1 = 0, rr0 = 0, rr1 = 0, rg0 = 0, rg1 = 0, rh0 = 0, rh1 = 0;
+  double af = 0.0, cl_ = 0.0, rhp = 0.0;
+  if (w0) {
+#pragma unroll
+    for (int u = 0; u < kFPL; ++u) {
+      const int64_t j = s + u;
+      xr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
+      ch[u][lane] = 0.0;
+      ah[u][lane] = 0.0;
+    }
+    // down sweep over the interior, up chain, reduced rows (as f_line_solve, in double)
+#pragma unroll
+    for (int u = 1; u <= kFPL - 2; ++u) {
+      double a, b, c;
+      coef(s + u, a, b, c);
+      double den, ahv, num;
+      if (u == 1) { den = b; ahv = a; num = xr[u][lane]; }
+      else { den = b - a * ch[u - 1][lane]; ahv = -a * ah[u - 1][lane]; num = xr[u][lane] - a * rhp; }
+      const double inv = 1.0 / den;
+      ch[u][lane] = c * inv;
+      ah[u][lane] = ahv * inv;
+      rhp = num * inv;
+      xr[u][lane] = rhp;
+    }
+    double rc = rhp, cc = ch[kFPL - 2][lane], ac = ah[kFPL - 2][lane];
+#pragma unroll
+    for (int u = kFPL - 3; u >= 1; --u) {
+      rc = xr[u][lane] - ch[u][lane] * rc;
+      cc = -ch[u][lane] * cc;
+      ac = ah[u][lane] - ch[u][lane] * ac;
+    }
+    double as, bs, cs, ae, be, ce;
+    coef(s, as, bs, cs);
+    coef(s + kFPL - 1, ae, be, ce);
+    ra0 = (lane == 0) ? 0.0 : as;
+    rb0 = bs - cs * ac;
+    rc0 = -cs * cc;
+    rr0 = xr[0][lane] - cs * rc;
+    ra1 = -ae * ah[kFPL - 2][lane];
+    rb1 = be - ae * ch[kFPL - 2][lane];
+    rc1 = (lane == 31) ? 0.0 : ce;
+    rr1 = xr[kFPL - 1][lane] - ae * rhp;
+    rg0 = (lane == 0) ? 1.0 : 0.0;
+    rh1 = (lane == 31) ? 1.0 : 0.0;
+    af = __shfl_sync(0xffffffffu, as, 0);
+    cl_ = __shfl_sync(0xffffffffu, ce, 31);
+    // PCR over the 64 rows (rows 2 lane and 2 lane + 1 on this lane), 6 levels
+    for (int st = 1; st < 64; st <<= 1) {
+      double na[2], nb[2], nc[2], n_r[2], n_g[2], n_h[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int i = 2 * lane + p, il = i - st, ir = i + st;
+        const bool hl = il >= 0, hr = ir < 64;
+        const int sl = (hl ? il : 0) >> 1, pl = (hl ? il : 0) & 1;
+        const int sr = (hr ? ir : 63) >> 1, pr = (hr ? ir : 63) & 1;
+        const double Lb = f_pick(__shfl_sync(0xffffffffu, rb0, sl), __shfl_sync(0xffffffffu, rb1, sl), pl);
+        const double La = f_pick(__shfl_sync(0xffffffffu, ra0, sl), __shfl_sync(0xffffffffu, ra1, sl), pl);
+        const double Lc = f_pick(__shfl_sync(0xffffffffu, rc0, sl), __shfl_sync(0xffffffffu, rc1, sl), pl);
+        const double Lr = f_pick(__shfl_sync(0xffffffffu, rr0, sl), __shfl_sync(0xffffffffu, rr1, sl), pl);
+        const double Lg = f_pick(__shfl_sync(0xffffffffu, rg0, sl), __shfl_sync(0xffffffffu, rg1, sl), pl);
+        const double Lh = f_pick(__shfl_sync(0xffffffffu, rh0, sl), __shfl_sync(0xffffffffu, rh1, sl), pl);
+        const double Rb = f_pick(__shfl_sync(0xffffffffu, rb0, sr), __shfl_sync(0xffffffffu, rb1, sr), pr);
+        const double Ra = f_pick(__shfl_sync(0xffffffffu, ra0, sr), __shfl_sync(0xffffffffu, ra1, sr), pr);
+        const double Rc = f_pick(__shfl_sync(0xffffffffu, rc0, sr), __shfl_sync(0xffffffffu, rc1, sr), pr);
+        const double Rr = f_pick(__shfl_sync(0xffffffffu, rr0, sr), __shfl_sync(0xffffffffu, rr1, sr), pr);
+        const double Rg = f_pick(__shfl_sync(0xffffffffu, rg0, sr), __shfl_sync(0xffffffffu, rg1, sr), pr);
+        const double Rh = f_pick(__shfl_sync(0xffffffffu, rh0, sr), __shfl_sync(0xffffffffu, rh1, sr), pr);
+        const double a = p ? ra1 : ra0, b = p ? rb1 : rb0, c = p ? rc1 : rc0;
+        const double r = p ? rr1 : rr0, gg = p ? rg1 : rg0, hh = p ? rh1 : rh0;
+        const double k1 = hl ? a / Lb : 0.0;
+        const double k2 = hr ? c / Rb : 0.0;
+        na[p] = hl ? -La * k1 : 0.0;
+        nc[p] = hr ? -Rc * k2 : 0.0;
+        nb[p] = b - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
+        n_r[p] = r - (hl ? Lr * k1 : 0.0) - (hr ? Rr * k2 : 0.0);
+        n_g[p] = gg - (hl ? Lg * k1 : 0.0) - (hr ? Rg * k2 : 0.0);
+        n_h[p] = hh - (hl ? Lh * k1 : 0.0) - (hr ? Rh * k2 : 0.0);
+      }
+      ra0 = na[0]; ra1 = na[1]; rb0 = nb[0]; rb1 = nb[1]; rc0 = nc[0]; rc1 = nc[1];
+      rr0 = n_r[0]; rr1 = n_r[1]; rg0 = n_g[0]; rg1 = n_g[1]; rh0 = n_h[0]; rh1 = n_h[1];
+    }
+    {
+      const double i0 = 1.0 / rb0, i1 = 1.0 / rb1;
+      rr0 *= i0; rg0 *= i0; rh0 *= i0;
+      rr1 *= i1; rg1 *= i1; rh1 *= i1;
+    }
+    // the slice's 2x2 Schur complement on (first, last), published by lane 0
+    const double z00 = __shfl_sync(0xffffffffu, rg0, 0), z0n = __shfl_sync(0xffffffffu, rh0, 0);
+    const double zn0 = __shfl_sync(0xffffffffu, rg1, 31), znn = __shfl_sync(0xffffffffu, rh1, 31);
+    const double y0 = __shfl_sync(0xffffffffu, rr0, 0), y1 = __shfl_sync(0xffffffffu, rr1, 31);
+    if (lane == 0) {
+      const double id = 1.0 / (z00 * znn - z0n * zn0);
+      const double S11 = znn * id, S12 = -z0n * id, S21 = -zn0 * id, S22 = z00 * id;
+      sm.pe[par][0] = S11;
+      sm.pe[par][1] = S12;
+      sm.pe[par][2] = S21;
+      sm.pe[par][3] = S22;
+      sm.pe[par][4] = S11 * y0 + S12 * y1;
+      sm.pe[par][5] = S21 * y0 + S22 * y1;
+      sm.pcoup[par][0] = af;
+      sm.pcoup[par][1] = cl_;
+    }
+  }
+  cl.sync();   // every slice's Schur complement published
+  if (w0) {
+    // interface rows [F_0, L_0, F_1, L_1, ...] (2Q <= 32): lane i holds row i; PCR by shuffles
+    const int Q = G.Q, n2 = 2 * Q;
+    double ia = 0.0, ib = 1.0, ic = 0.0, ir = 0.0;
+    if (lane < n2) {
+      const int qq = lane >> 1;
+      const double* pe = cl.map_shared_rank(&sm.pe[par][0], qq);
+      const double* pc = cl.map_shared_rank(&sm.pcoup[par][0], qq);
+      if ((lane & 1) == 0) {
+        ia = qq > 0 ? pc[0] : 0.0;
+        ib = pe[0];
+        ic = pe[1];
+        ir = pe[4];
+      } else {
+        ia = pe[2];
+        ib = pe[3];
+        ic = qq < Q - 1 ? pc[1] : 0.0;
+        ir = pe[5];
+      }
+    }
+    for (int st = 1; st < n2; st <<= 1) {
+      const int il = lane - st, irr = lane + st;
+      const int sl = il >= 0 ? il : 0, sr = irr < n2 ? irr : 0;
+      const double Lb = __shfl_sync(0xffffffffu, ib, sl), La = __shfl_sync(0xffffffffu, ia, sl);
+      const double Lc = __shfl_sync(0xffffffffu, ic, sl), Lr = __shfl_sync(0xffffffffu, ir, sl);
+      const double Rb = __shfl_sync(0xffffffffu, ib, sr), Ra = __shfl_sync(0xffffffffu, ia, sr);
+      const double Rc = __shfl_sync(0xffffffffu, ic, sr), Rr = __shfl_sync(0xffffffffu, ir, sr);
+      if (lane < n2) {
+        const bool hl = il >= 0, hr = irr < n2;
+        const double k1 = hl ? ia / Lb : 0.0, k2 = hr ? ic / Rb : 0.0;
+        const double na = hl ? -La * k1 : 0.0, nc = hr ? -Rc * k2 : 0.0;
+        const double nb = ib - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
+        const double nr = ir - (hl ? Lr * k1 : 0.0) - (hr ? Rr * k2 : 0.0);
+        ia = na;
+        ib = nb;
+        ic = nc;
+        ir = nr;
+      }
+    }
+    const double X = (lane < n2) ? ir / ib : 0.0;
+    const int sLp = G.q > 0 ? 2 * G.q - 1 : 0, sFn = G.q < Q - 1 ? 2 * G.q + 2 : 0;
+    const double XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
+    const double Lp = G.q > 0 ? XL : 0.0, Fn = G.q < Q - 1 ? XF : 0.0;
+    const double la = Lp * af, fc = Fn * cl_;
+    const double xs = rr0 - la * rg0 - fc * rh0;
+    const double xe = rr1 - la * rg1 - fc * rh1;
+    // back substitution of the lane's chunk
+    sm.pu[lane * kFPL] = xs;
+    sm.pu[lane * kFPL + kFPL - 1] = xe;
+    double xn = xe;
+#pragma unroll
+    for (int u = kFPL - 2; u >= 1; --u) {
+      xn = xr[u][lane] - ch[u][lane] * xn - ah[u][lane] * xs;
+      sm.pu[lane * kFPL + u] = xn;
+    }
+    if (lane == 0) {
+      sm.pxl[0] = Lp;
+      sm.pxl[1] = Fn;
+    }
+  }
+  par ^= 1;
+  __syncthreads();
+  // z = (r - Gbar u)/alpha, Gbar u = wv2 [gl (u_j - u_{j-1}) + gu (u_j - u_{j+1})] + wv gb u_j
+  {
+    const int t = threadIdx.x;
+    const int64_t j = G.c0 + t;
+    if (j < N) {
+      const int64_t g = co + j;
+      const double uj = sm.pu[t];
+      const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
+      const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
+      const double Gu = wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + wv * D.cf.gb[g] * uj;
+      z[j] = (rin[j] - Gu) * D.cf.ralpha[g];
+    }
+  }
+  __syncthreads();
+}
+
+// The whole prediction solve of one instance per cluster.  blockIdx.x / Q indexes
+// D.finst (the instances of this launch's cluster size).
+__global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restrict__ finst) {
+  extern __shared__ __align__(16) unsigned char fdsm[];
+  FSmem& sm = *reinterpret_cast<FSmem*>(fdsm);
+  cg::cluster_group cl = cg::this_cluster();
+  FGeo G;
+  G.Q = (int)cl.num_blocks();
+  G.q = (int)cl.block_rank();
+  G.ii = finst[blockIdx.x / G.Q];
+  const Inst I = D.inst[G.ii];
+  G.N = I.N;
+  G.M = I.M;
+  G.c0 = (int64_t)G.q * kFS;
+  G.co = I.cell_off;
+  const int ii = G.ii;
+  const int64_t N = G.N, co = G.co;
+  const int t = threadIdx.x;
+  const int64_t j = G.c0 + t;
+  const bool real = j < N;
+  const int m = D.m;
+  const int64_t vstride = D.gz - D.gx;
+  double* x = D.gx + co;
+  double* z = D.gz + co;
+  auto Vi = [&](int i) { return D.gV + (int64_t)i * vstride + co; };
+  int par = 0;
+  f_load_cells(sm, D, I, G);
+  int cycles = 0, its = 0;
+  double beta_prev = 0.0;
+  bool first = true;
+  for (;;) {
+    // ---- restart: true residual at x, preconditioned, stopping test --------------------
+    f_pass<true>(sm, cl, D, I, G, x, par);
+    if (real) {
+      const int64_t g = co + j;
+      const double fl = sm.fl[t];
+      const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
+      z[j] = -R;
+      D.Fs[g] = fl;
+    }
+    {
+      const double xm = f_block_max(sm, real ? fabs(x[j]) : 0.0);
+      if (t == 0) sm.sums[0] = xm;
+      __syncthreads();
+      f_cluster_reduce(sm, cl, par, 1, true);
+    }
+    const double xmax = sm.sums[0];
+    sm.wgt[t] = real ? 1.0 / (fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0;
+    __syncthreads();
+    double* v0 = Vi(0);
+    f_prec(sm, cl, D, I, G, z, v0, par);
+    {
+      double loc[2] = {0.0, 0.0};
+      if (real) {
+        const double vj = v0[j];
+        loc[0] = vj * vj;
+        loc[1] = x[j] * x[j];
+      }
+      f_block_sums(sm, loc, 2);
+      f_cluster_reduce(sm, cl, par, 2, false);
+      const double nrm = sqrt(sm.sums[0]), xn = sqrt(sm.sums[1]);
+      __syncthreads();
+      const double bm = f_block_max(sm, real ? fabs(v0[j]) * sm.wgt[t] : 0.0);
+      if (t == 0) sm.sums[0] = bm;
+      __syncthreads();
+      f_cluster_reduce(sm, cl, par, 1, true);
+      const double rinf_c = sm.sums[0];
+      __syncthreads();
+      bool conv = !(rinf_c > D.rtol);
+      if (!first && !conv && rinf_c <= D.stall && (rinf_c >= 0.25 * beta_prev || (D.mixed && cycles >= 2)))
+        conv = true;
+      beta_prev = rinf_c;
+      if (!isfinite(nrm)) {
+        if (G.q == 0 && t == 0) flag(D.status, ii, GRTE_ENAN);
+        conv = true;
+      }
+      if (conv) break;
+      if (cycles >= D.maxcycles) {
+        if (G.q == 0 && t == 0) flag(D.status, ii, GRTE_ENONCONV);
+        break;
+      }
+      ++cycles;
+      first = false;
+      // ---- restart cycle: Arnoldi with CGS2 ---------------------------------------------
+      if (t == 0) {
+        sm.g[0] = nrm;
+        for (int i = 1; i <= m; ++i) sm.g[i] = 0.0;
+      }
+      if (real) v0[j] *= 1.0 / nrm;
+      __syncthreads();
+      int kk = 0;
+      for (int jc = 0; jc < m; ++jc) {
+        const double* vj = Vi(jc);
+        f_pass<false>(sm, cl, D, I, G, vj, par);
+        // C v_j = alpha v_j + kappa/dx F(v_j), preconditioned into V_{j+1}
+        if (real) {
+          const int64_t g = co + j;
+          z[j] = D.cf.alpha[g] * vj[j] + D.cf.kdx[g] * sm.fl[t];
+        }
+        __syncthreads();
+        double* wv = Vi(jc + 1);
+        f_prec(sm, cl, D, I, G, z, wv, par);
+        double hcol[kMaxRestart + 2];
+        for (int i = 0; i <= jc + 1; ++i) hcol[i] = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          double loc[kMaxRestart + 1];
+          const double wj = real ? wv[j] : 0.0;
+          for (int i = 0; i <= jc; ++i) loc[i] = real ? wj * Vi(i)[j] : 0.0;
+          f_block_sums(sm, loc, jc + 1);
+          f_cluster_reduce(sm, cl, par, jc + 1, false);
+          if (real) {
+            double tt = wv[j];
+            for (int i = 0; i <= jc; ++i) tt -= sm.sums[i] * Vi(i)[j];
+            wv[j] = tt;
+          }
+          for (int i = 0; i <= jc; ++i) hcol[i] += sm.sums[i];
+          __syncthreads();
+        }
+        double l1[1] = {real ? wv[j] * wv[j] : 0.0};
+        f_block_sums(sm, l1, 1);
+        f_cluster_reduce(sm, cl, par, 1, false);
+        const double nrmw = sqrt(sm.sums[0]);
+        hcol[jc + 1] = nrmw;
+        // Givens rotations (every thread, identical values)
+        for (int i = 0; i < jc; ++i) {
+          const double tq = sm.cs[i] * hcol[i] + sm.sn[i] * hcol[i + 1];
+          hcol[i + 1] = -sm.sn[i] * hcol[i] + sm.cs[i] * hcol[i + 1];
+          hcol[i] = tq;
+        }
+        const double a0 = hcol[jc], b0 = hcol[jc + 1];
+        const double rr = hypot(a0, b0);
+        const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
+        hcol[jc] = rr;
+        const double gj = sm.g[jc];
+        const double gnext = -s0g * gj;
+        __syncthreads();
+        if (t == 0) {
+          sm.cs[jc] = c0g;
+          sm.sn[jc] = s0g;
+          sm.g[jc + 1] = gnext;
+          sm.g[jc] = c0g * gj;
+          for (int i = 0; i <= jc; ++i) sm.H[i * kMaxRestart + jc] = hcol[i];
+        }
+        if (real) wv[j] *= (nrmw > 0.0 ? 1.0 / nrmw : 0.0);
+        __syncthreads();
+        ++its;
+        kk = jc + 1;
+        const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
+        if (est || nrmw == 0.0 || jc + 1 >= m) break;
+      }
+      // x += V y, H y = g (upper triangular, kk columns)
+      if (t == 0) {
+        for (int i = kk - 1; i >= 0; --i) {
+          double tq = sm.g[i];
+          for (int l = i + 1; l < kk; ++l) tq -= sm.H[i * kMaxRestart + l] * sm.y[l];
+          sm.y[i] = tq / sm.H[i * kMaxRestart + i];
+        }
+      }
+      __syncthreads();
+      if (real) {
+        double tq = x[j];
+        for (int i = 0; i < kk; ++i) tq += sm.y[i] * Vi(i)[j];
+        x[j] = tq;
+      }
+      __syncthreads();
+    }
+  }
+  if (G.q == 0 && t == 0) {
+    D.gits[ii] = its;
+    D.gcycles[ii] = cycles;
+  }
+  cl.sync();   // no CTA leaves while another may read its shared memory
+}
+
+}  // namespace grte

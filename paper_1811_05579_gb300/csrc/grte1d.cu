@@ -112,6 +112,7 @@ struct Dev {
   int use_guess, log_samples;
   int start_prev;   // 1: Newton starts one step from T^n instead of the closed-form bound
   int m;  // restart length
+  int maxcycles;  // restart cycles per step before ENONCONV
   double rtol, stall, wfloor;
   int mixed;
   int newton_maxit;
@@ -1214,6 +1215,8 @@ __global__ void k_project_U(Dev D, int64_t ncell) {
 
 }  // namespace grte
 
+#include "fused1d.cuh"
+
 // =============================================================================== host
 using namespace grte;
 
@@ -1257,6 +1260,10 @@ struct grte_ctx {
   long long* d_acc = nullptr;       // Krylov iterations, cycles, iterations run, condition kernels run
   int64_t graph_fixed_launches = 0;
   double tune_ms[3] = {-1.0, -1.0, -1.0};
+  // fused prediction solve: instances grouped by cluster size 1, 2, 4, 8, 16
+  bool fused = false;
+  int* d_finst = nullptr;
+  int fcnt[5] = {0, 0, 0, 0, 0}, foff[5] = {0, 0, 0, 0, 0};
 };
 
 // The captured step depends on values passed by value to its kernels (the device
@@ -1422,6 +1429,77 @@ static void corr_pass(grte_ctx* h, int dry) {
   }
 }
 
+// ----------------------------------------------------------------------------- fused launches
+// Cluster size of an instance in the fused prediction solve: one 512-cell slice per CTA,
+// rounded up to a power of two (class index 0..4 for 1, 2, 4, 8, 16 CTAs).
+static int fused_class(int64_t nx) {
+  const int64_t q = (nx + kFS - 1) / kFS;
+  int c = 0;
+  while ((1 << c) < q) ++c;
+  return c;
+}
+
+static bool fused_fits(const Inst& I) { return I.N >= 64 && I.N <= (int64_t)kFQ * kFS && I.M <= 32; }
+
+// Kernel attributes of the fused solve (once per device): its shared memory and the
+// non-portable cluster size 16.
+static cudaError_t fused_attrs() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute((const void*)k_pred_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FSmem));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_pred_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+static void fused_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int Qc, int nclusters, cudaStream_t st) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3((unsigned)(nclusters * Qc), 1, 1);
+  cfg.blockDim = dim3(kFT, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(FSmem);
+  cfg.stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)Qc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+}
+
+// 1 if a cluster of Qc CTAs of the fused kernel can be resident on this device.
+static cudaError_t fused_schedulable(int Qc, bool* ok) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  fused_config(cfg, at, Qc, 1, nullptr);
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)k_pred_fused, &cfg);
+  *ok = e == cudaSuccess && n >= 1;
+  return e;
+}
+
+static cudaError_t fused_launch(grte_ctx* h, int c) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  fused_config(cfg, at, 1 << c, h->fcnt[c], h->stream);
+  return cudaLaunchKernelEx(&cfg, k_pred_fused, h->D, (const int*)(h->d_finst + h->foff[c]));
+}
+
+// Krylov iterations and restart cycles of the fused solve, accumulated over graph replays.
+__global__ void k_fused_stats(const int* __restrict__ gits, const int* __restrict__ gcycles, int n, long long* acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long a = 0, b = 0;
+    for (int i = 0; i < n; ++i) {
+      a += gits[i];
+      b += gcycles[i];
+    }
+    acc[0] += a;
+    acc[1] += b;
+  }
+}
+
 // Autotuner of the line solves: times, for 256, 512 and 1024 threads per line (those
 // whose shared memory fits), one factor pass, four solve passes and one correction
 // pass (dry: the state is not touched) on this handle's own instances, twice, and
@@ -1511,6 +1589,7 @@ void grte_default_options(grte_options* o) {
   o->line_threads = 0;
   o->use_graph = 1;
   o->prec2d = 0;
+  o->solver1d = GRTE_SOLVER_AUTO;
 }
 
 const char* grte_last_error(grte_t h) { return h ? h->err.c_str() : "null handle"; }
@@ -1640,6 +1719,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   Dev& D = h->D;
   const int m = h->opt.krylov_restart;
   D.m = m;
+  D.maxcycles = h->opt.krylov_maxcycles;
   // binary32 line solves and Krylov vectors leave noise in the residual of cells far
   // below the maximum: the mixed mode floors the tolerance at 1e-9, measures cells
   // below 1e-6 of the maximum against that floor, and accepts a second restart below
@@ -1733,6 +1813,32 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   h->gxs = (tri_xs_len(h->max_slice) * 8 + 15) / 16 * 16 <= g_gmres_dyn;
   if (h->opt.line_threads != 0) h->nt = (h->xs && line_fits(h, h->opt.line_threads)) ? h->opt.line_threads : 256;
   else if (!h->xs) h->nt = 256;   // nothing to tune: the global-memory variant runs at 256
+  // fused prediction solve: mixed precision, every instance within the slice limits, and a
+  // device that can hold the clusters
+  if (mixed && h->opt.solver1d == GRTE_SOLVER_AUTO) {
+    bool ok = std::all_of(h->inst.begin(), h->inst.end(), [](const Inst& I) { return fused_fits(I); });
+    if (ok) CK(fused_attrs());
+    std::vector<std::vector<int>> cls(5);
+    if (ok)
+      for (int i = 0; i < n_inst; ++i) cls[fused_class(h->inst[i].N)].push_back(i);
+    for (int c = 0; c < 5 && ok; ++c) {
+      if (cls[c].empty()) continue;
+      bool sched = false;
+      CK(fused_schedulable(1 << c, &sched));
+      ok = sched;
+    }
+    if (ok) {
+      std::vector<int> order;
+      for (int c = 0; c < 5; ++c) {
+        h->foff[c] = (int)order.size();
+        h->fcnt[c] = (int)cls[c].size();
+        order.insert(order.end(), cls[c].begin(), cls[c].end());
+      }
+      if (dalloc(h, &h->d_finst, n_inst) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc finst");
+      CK(cudaMemcpy(h->d_finst, order.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice));
+      h->fused = true;
+    }
+  }
   return GRTE_OK;
 }
 
@@ -1863,6 +1969,62 @@ static grte_status step_epilogue(grte_t h) {
   LAUNCH(GRTE_K_PROJECT, k_project_U<<<G.cgrid, G.cb, 0, st>>>(D, G.nc));
   if (h->opt.energy_every > 0) LAUNCH(GRTE_K_ENERGY, k_energy<R><<<G.ni, kTriThreads, 0, st>>>(D, 1));
   CK(cudaGetLastError());
+  return GRTE_OK;
+}
+
+// One step with the fused prediction solve: coefficients and rho^n, one persistent launch
+// per cluster size for the whole GMRES solve, then Newton, correction and projection.
+template <typename R>
+static grte_status step_fused(grte_t h, bool allow_tune) {
+  Dev& D = h->D;
+  cudaStream_t st = h->stream;
+  const StepGeom G = step_geom(h);
+  LAUNCH(GRTE_K_CELL_COEF, k_cell_coef<<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, 0));
+  LAUNCH(GRTE_K_RHO, k_rho<R><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.rho_n));
+  CK(cudaMemcpyAsync(D.gx, D.rho_n, sizeof(double) * G.nc, cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < 5; ++c) {
+    if (!h->fcnt[c]) continue;
+    cudaError_t e = cudaSuccess;
+    LAUNCH(GRTE_K_PRED_SOLVE, e = fused_launch(h, c));
+    CK(e);
+  }
+  if (h->nt == 0) {
+    if (!allow_tune) return fail(h, GRTE_ESTATE, "line solves not tuned");
+    // the correction's line solves are tuned on this step's per-cell parts
+    LAUNCH(GRTE_K_CELL_COEF, k_cellpart_pred<double><<<G.cgrid, G.cb, 0, st>>>(D, G.ni, h->d_cell_start, G.nc, D.gx, 1));
+    cudaError_t e = autotune_lines<R>(h);
+    if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("line autotune: ") + cudaGetErrorString(e));
+  }
+  return step_epilogue<R>(h);
+}
+
+template <typename R>
+static grte_status build_fused_graph(grte_t h) {
+  cudaStream_t st = h->stream;
+  if (h->prof_mask != 0) return fail(h, GRTE_ESTATE, "graph capture while profiling");
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(h, GRTE_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  const int64_t l0 = h->launches;
+  grte_status s = step_fused<R>(h, false);
+  if (s == GRTE_OK) k_fused_stats<<<1, 32, 0, st>>>(h->D.gits, h->D.gcycles, h->n_inst, h->d_acc);
+  h->graph_fixed_launches = h->launches - l0 + 1;
+  h->launches = l0;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+  if (s != GRTE_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+  if (e2 == cudaSuccess) e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(h, GRTE_ECUDA, std::string("fused step capture: ") + cudaGetErrorString(e2));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e2 = cudaGraphInstantiate(&ex, graph, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(h, GRTE_ECUDA, std::string("fused step instantiate: ") + cudaGetErrorString(e2));
+  }
+  h->graph = graph;
+  h->graph_exec = ex;
   return GRTE_OK;
 }
 
@@ -2109,6 +2271,40 @@ grte_status grte_step(grte_t h, int64_t nsteps) {
   int64_t its = 0, cyc = 0, ngraph = 0;
   std::vector<int> hits(h->n_inst);
   CK(cudaMemsetAsync(h->d_acc, 0, 4 * sizeof(long long), h->stream));
+  if (h->fused) {
+    std::vector<int> hcyc(h->n_inst);
+    for (int64_t n = 0; n < nsteps; ++n) {
+      const bool use_graph = h->opt.use_graph && h->nt != 0 && h->prof_mask == 0;
+      if (use_graph) {
+        if (!h->graph_exec) {
+          grte_status s = build_fused_graph<float>(h);
+          if (s != GRTE_OK) return s;
+        }
+        CK(cudaGraphLaunch(h->graph_exec, h->stream));
+        ++ngraph;
+      } else {
+        grte_status s = step_fused<float>(h, true);
+        if (s != GRTE_OK) return s;
+        CK(cudaMemcpyAsync(hits.data(), h->D.gits, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hcyc.data(), h->D.gcycles, sizeof(int) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int v : hits) its += v;
+        for (int v : hcyc) cyc += v;
+      }
+      h->stats.steps += 1;
+    }
+    if (ngraph > 0) {
+      long long acc[4] = {0, 0, 0, 0};
+      CK(cudaMemcpyAsync(acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      its += acc[0];
+      cyc += acc[1];
+      h->launches += ngraph * h->graph_fixed_launches;
+    }
+    h->stats.krylov_iters = its;
+    h->stats.krylov_cycles = cyc;
+    return GRTE_OK;
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
     // graph path: after the first (tuning) step, when not profiling
     const bool use_graph = h->opt.use_graph && h->nt != 0 && h->prof_mask == 0;
@@ -2596,6 +2792,7 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   D.inst = d_inst;
   D.lines = d_lines;
   D.m = o.krylov_restart;
+  D.maxcycles = o.krylov_maxcycles;
   D.rtol = o.krylov_rtol;
   D.stall = 1e-9;
   D.wfloor = 1e-13;

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("energy_every", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("line_threads", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("prec2d", ctypes.c_int)]
+                ("prec2d", ctypes.c_int), ("solver1d", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +73,8 @@ PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
-           "project", "energy"]
+           "project", "energy", "pred_solve"]
+SOLVER_AUTO, SOLVER_LINES = 0, 1
 
 
 def load_library(path=LIB_PATH):
@@ -268,7 +269,7 @@ class Grte:
 
     def __init__(self, instances, precision=FP64, krylov_rtol=1e-13, krylov_restart=10,
                  krylov_maxcycles=30, newton_maxit=60, energy_every=0, stream=None, line_threads=0,
-                 use_graph=True):
+                 use_graph=True, solver1d=SOLVER_AUTO):
         L = lib()
         self._keep = []
         arr = (Instance1D * len(instances))()
@@ -297,6 +298,7 @@ class Grte:
         opt.stream = stream
         opt.line_threads = line_threads
         opt.use_graph = 1 if use_graph else 0
+        opt.solver1d = solver1d
         h = ctypes.c_void_p()
         st = L.grte_create_1d(len(instances), arr, ctypes.byref(opt), ctypes.byref(h))
         self.h = h

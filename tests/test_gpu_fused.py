@@ -1,0 +1,165 @@
+"""The fused prediction solve (one persistent cluster kernel per instance, mixed precision)
+against the CPU oracle and against the line-kernel path.
+
+Sizes span one slice (nx <= 512, one CTA), several slices with a ragged last slice
+(nx = 600, 1500), clusters with idle slices (nx = 5000 on 16 CTAs) and the full 8192
+cells; angle counts 2..32 (lanes past M idle); inflow and reflecting walls; both opacity
+forms; eps from 1 to 1e-4.  Tolerance: 1e-5 relative in T against the FP64 oracle (the
+tolerance stated for reduced precision), the same as the line kernels' mixed mode."""
+import numpy as np
+import pytest
+
+from oracle import grte1d as og
+from oracle.quadrature import gauss_legendre_half
+from paper_1811_05579_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+MIXED_TOL = 1e-5
+KIND = {"const": 0, "t3": 1}
+BC = {"inflow": 0, "reflect": 1}
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_05579_gb300 import grte
+    return grte
+
+
+def make(N, nv, eps, kind="t3", bc="inflow", sig=1.0, bL=1.0, bR=0.0, cfl=0.5):
+    v, w = gauss_legendre_half(nv)
+    sig = np.broadcast_to(np.asarray(sig, dtype=np.float64), (N,)).copy()
+    P = og.Problem(N=N, v=v, w=w, sig=sig, eps=eps, dt=cfl / N, kind=kind, bc=bc,
+                   bL=np.full(v.size, bL), bR=np.full(v.size, bR))
+    spec = dict(nx=N, n_angle=v.size, v=v, w=w, sigma=sig, kind=KIND[kind], bc=BC[bc],
+                bL=P.bL, bR=P.bR, dt=P.dt, eps=eps)
+    return P, spec
+
+
+def state(P, seed, lo=0.05, hi=1.0):
+    rng = wl.SplitMix64(2000 + seed)
+    T, E, O = wl.random_state_1d(rng, P.N, P.M, (lo, hi))
+    if P.bc == "reflect":
+        O[0] = O[-1] = 0.0
+    return og.State(E=E, O=O, U=T ** 4, T=T)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def fused_ran(G, h, n=1):
+    """Step h by n with per-kernel timing on and return the fused kernel's launch count."""
+    h.profile_begin(["pred_solve", "gmres"])
+    h.step(n)
+    prof = h.profile_end()
+    return prof.get("pred_solve", (0.0, 0))[1], prof.get("gmres", (0.0, 0))[1]
+
+
+CASES = [
+    # N, n_dir, eps, kind, bc
+    (64, 4, 1.0, "t3", "inflow"),
+    (300, 16, 1e-2, "const", "inflow"),
+    (512, 32, 1e-4, "t3", "reflect"),
+    (600, 8, 1e-2, "t3", "inflow"),        # two slices, ragged second
+    (1500, 64, 1.0, "const", "reflect"),   # four slices, 32 angles
+    (1500, 2, 1e-3, "t3", "inflow"),       # one angle pair: 31 idle lanes
+]
+
+
+@pytest.mark.parametrize("N,nv,eps,kind,bc", CASES)
+def test_fused_vs_oracle(G, N, nv, eps, kind, bc):
+    P, spec = make(N, nv, eps, kind, bc, sig=np.linspace(0.5, 4.0, N))
+    S = state(P, N + nv)
+    h = G.Grte([spec], precision=G.MIXED)
+    h.set_state(0, S.T, S.E, S.O)
+    nf, ng = fused_ran(G, h, 1)
+    assert nf == 1 and ng == 0, (nf, ng)
+    h.step(1)
+    S2 = og.run(P, S, 2)
+    err = rel(h.T(0, allow=(5,)), S2.T)
+    print("fused N=%d M=%d eps=%g %s %s: T vs oracle %.2e" % (N, P.M, eps, kind, bc, err))
+    assert err < MIXED_TOL
+    Oc = 0.5 * (S2.O[:-1] + S2.O[1:])
+    E = h.E(0, allow=(5,))
+    errE = float(np.max(np.abs(E - S2.E) / (np.abs(S2.E) + np.abs(P.eps * Oc))[:, :]))
+    assert errE < 1e-4, errE
+    h.close()
+
+
+@pytest.mark.parametrize("N,nv", [(5000, 16), (8192, 64), (2049, 32)])
+def test_fused_vs_line_kernels_and_fp64(G, N, nv):
+    """Clusters with idle slices (5000 cells on 16 CTAs), the full 8192 x 32 angles, and a
+    one-cell ragged slice (2049 = 4 x 512 + 1): 5 steps of the fused and the line-kernel
+    mixed paths against the FP64 path."""
+    P, spec = make(N, nv, 1e-2, "t3", "inflow", sig=1.0 + 9.0 * (np.arange(N) % 7 == 0))
+    rng = wl.SplitMix64(31 + N)
+    T0 = wl.smoothed_log_uniform_T(rng, N, 1e-3, 1e-2, width=65)
+    hs = {"fused": G.Grte([spec], precision=G.MIXED),
+          "lines": G.Grte([spec], precision=G.MIXED, solver1d=G.SOLVER_LINES),
+          "fp64": G.Grte([spec])}
+    for h in hs.values():
+        h.set_state(0, T0)
+        h.step(5)
+    Tf, Tl, Td = (hs[k].T(0, allow=(5,)) for k in ("fused", "lines", "fp64"))
+    ef, el = rel(Tf, Td), rel(Tl, Td)
+    print("N=%d M=%d: fused vs FP64 %.2e, lines vs FP64 %.2e" % (N, P.M, ef, el))
+    assert ef < MIXED_TOL and el < MIXED_TOL
+    for h in hs.values():
+        h.close()
+
+
+def test_fused_uneven_batch_vs_oracle(G):
+    """One handle with instances of every cluster size class (1, 2, 4, 8 slices), uneven
+    angle counts and eps, each compared with the oracle after 2 steps."""
+    insts = [(200, 8, 1e-5), (700, 16, 1e-2), (1800, 32, 1.0), (3000, 4, 1e-3), (64, 64, 1e-1)]
+    rng = wl.SplitMix64(5150)
+    specs, probs, states = [], [], []
+    for i, (N, nv, eps) in enumerate(insts):
+        sig = 0.5 + 20 * rng.uniform(N)
+        P, spec = make(N, nv, eps, "t3", "inflow", sig=sig, bL=0.8, bR=0.05)
+        specs.append(spec)
+        probs.append(P)
+        states.append(state(P, 40 + i, lo=0.02, hi=0.5))
+    h = G.Grte(specs, precision=G.MIXED)
+    for i, S in enumerate(states):
+        h.set_state(i, S.T, S.E, S.O)
+    nf, ng = fused_ran(G, h, 1)
+    assert nf == 4 and ng == 0, (nf, ng)    # one launch per cluster-size class present
+    h.step(1)
+    for i, (P, S) in enumerate(zip(probs, states)):
+        S2 = og.run(P, S, 2)
+        err = rel(h.T(i, allow=(5,)), S2.T)
+        print("batch inst %d N=%d M=%d: %.2e" % (i, P.N, P.M, err))
+        assert err < MIXED_TOL, i
+    h.close()
+
+
+def test_fused_graph_equals_eager_bitwise(G):
+    """Steps replayed from the captured graph give the same state, bit for bit, as eager
+    steps (the fused kernel's reductions run in a fixed order)."""
+    P, spec = make(3000, 32, 1e-3, "t3", "inflow", sig=2.0)
+    S = state(P, 9)
+    hg = G.Grte([spec], precision=G.MIXED)
+    he = G.Grte([spec], precision=G.MIXED, use_graph=False)
+    for h in (hg, he):
+        h.set_state(0, S.T, S.E, S.O)
+        h.step(4)
+    assert np.array_equal(hg.T(0, allow=(5,)), he.T(0, allow=(5,)))
+    assert np.array_equal(hg.E(0, allow=(5,)), he.E(0, allow=(5,)))
+    assert np.array_equal(hg.O(0, allow=(5,)), he.O(0, allow=(5,)))
+    hg.close()
+    he.close()
+
+
+def test_fused_reports_krylov_counts(G):
+    P, spec = make(1024, 16, 1e-2, "t3", "inflow")
+    S = state(P, 3)
+    h = G.Grte([spec], precision=G.MIXED)
+    h.set_state(0, S.T, S.E, S.O)
+    h.step(3)
+    st = h.stats(allow=(5,))
+    assert st["krylov_iters"] > 0 and st["krylov_cycles"] > 0
+    h.close()
