@@ -392,7 +392,11 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     sm.P1[t] = (float)p1;
     sm.P2[t] = (float)p2;
     sm.P3[t] = (float)p3;
-    sm.fl[t] = FULL ? fr : (double)(float)fr;
+    // Krylov directions sum the interior fluxes in binary32; the inflow wall cells keep
+    // their rho part in double: it cancels against the e/o wall sum to O(eps), both
+    // carrying the factor 2/eps
+    const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
+    sm.fl[t] = (FULL || wallc) ? fr : (double)(float)fr;
   } else {
     sm.P1[t] = 0.0f;
     sm.P2[t] = 0.0f;
