@@ -60,7 +60,13 @@ struct FSmem {
   double fl[kFS];                                       // flux sums of the last pass
   double fdat[kFS];                                     // data part of the flux (data passes)
   double pu[kFS];                                       // preconditioner solution (slice)
-  double pxr[kFPL][32], pch[kFPL][32], pah[kFPL][32];  // its chunk sweeps, [u][lane]
+  // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
+  // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
+  double pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
+  double pcs[32], pae[32];
+  double pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
+  double ik1[5][32], ik2[5][32], iib[32];
+  double pS[4], paf, pcl;
   double wgt[kFS];                                      // stopping-test weights
   double wall[2][32];                                   // wall-row right-hand sides (double)
   double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
@@ -84,9 +90,12 @@ struct FGeo {
 
 // Sums of nv values per thread over the CTA (fixed order), result in sm.sums[0..nv-1] for
 // every thread.  nv <= kMaxRestart + 2.
-__device__ void f_block_sums(FSmem& sm, double* v, int nv) {
+template <int NV>
+__device__ void f_block_sums(FSmem& sm, const double* v, int nv) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i >= nv) break;
     double t = v[i];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) sm.red[wid][i] = t;
@@ -117,12 +126,13 @@ __device__ void f_cluster_reduce(FSmem& sm, cg::cluster_group& cl, int& par, int
   if (threadIdx.x < nv) sm.part[par][threadIdx.x] = sm.sums[threadIdx.x];
   cl.sync();
   if (threadIdx.x < nv) {
-    double t = 0.0;
     const int Q = (int)cl.num_blocks();
-    for (int r = 0; r < Q; ++r) {
-      const double v = cl.map_shared_rank(&sm.part[par][0], r)[threadIdx.x];
-      t = is_max ? fmax(t, v) : t + v;
-    }
+    double v[kFQ];
+#pragma unroll
+    for (int r = 0; r < kFQ; ++r) v[r] = r < Q ? cl.map_shared_rank(&sm.part[par][0], r)[threadIdx.x] : 0.0;
+    double t = 0.0;
+#pragma unroll
+    for (int r = 0; r < kFQ; ++r) t = is_max ? fmax(t, v[r]) : t + v[r];
     sm.sums[threadIdx.x] = t;
   }
   par ^= 1;
@@ -403,16 +413,24 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     sm.P3[t] = 0.0f;
     sm.fl[t] = 0.0;
   }
-  sm.fdat[t] = 0.0;
 }
 
 // Data part of a data pass: the right-hand side terms kappa/(c dt) Eh^n - kappa v/dx (o_{j+1} - o_j)
 // (o_i = d_i eps^2 O^n_i/(c dt) at interior nodes, 0 at the walls) into sm.x, and the data
 // part of the flux sum_k w_k v_k (o_{j+1,k} - o_{j,k}) into sm.fdat (not at inflow wall cells).
-// Warp w loads the 32 cells of its chunk for one angle at a time (coalesced rows of the
-// angle-major state) and writes them transposed.
-__device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G) {
+// The data do not change within a step: the first data pass of a solve (stage = true) reads
+// the angle-major state (warp w loads the 32 cells of its chunk for 8 angles at a time,
+// coalesced rows, written transposed), keeps fdat in shared memory and the transposed terms
+// in D.fdata; the later data passes read them back with lane = angle (coalesced).
+__device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, bool stage) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* fd = D.fdata + I.fd_off + (G.c0 + w * kFL) * 32;
+  if (!stage) {
+#pragma unroll 8
+    for (int u = 0; u < kFL; ++u) sm.x[w * kFL + u][lane] = fd[u * 32 + lane];
+    __syncwarp();
+    return;
+  }
   const int64_t N = G.N, j = G.c0 + w * kFL + lane;
   const int jl = w * kFL + lane + 1;
   const float* Eh = (const float*)D.Eh + I.elem_off;
@@ -420,20 +438,37 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
   const bool real = j < N;
   const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
   const float kcd = sm.kcd[jl], kdx = sm.kdx[jl], odj = sm.od[jl], odr = sm.od[jl + 1];
-  double fd = 0.0;
-  for (int kk = 0; kk < G.M; ++kk) {
-    const float* Ek = Eh + (int64_t)kk * N;
-    const float* Ok = On + (int64_t)kk * (N + 1);
-    const float e = real ? Ek[j] : 0.0f;
-    const float oj = (j >= 1 && j <= N - 1) ? odj * Ok[j] : 0.0f;
-    float or_ = __shfl_down_sync(0xffffffffu, oj, 1);
-    if (lane == 31) or_ = (j + 1 >= 1 && j + 1 <= N - 1) ? odr * Ok[j + 1] : 0.0f;
-    const float Dj = or_ - oj;
-    sm.x[w * kFL + lane][kk] = real ? fmaf(kcd, e, -kdx * sm.vk[kk] * Dj) : 0.0f;
-    if (real && !wallc) fd += sm.wvkd[kk] * (double)Dj;
+  const bool nj = j >= 1 && j <= N - 1, nr = j + 1 >= 1 && j + 1 <= N - 1;
+  double fsum = 0.0;
+  constexpr int B = 8;
+  for (int k0 = 0; k0 < 32; k0 += B) {
+    float e[B], oj[B], orr[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int kk = k0 + q;
+      const bool ka = kk < G.M;
+      const float* Ek = Eh + (int64_t)kk * N;
+      const float* Ok = On + (int64_t)kk * (N + 1);
+      e[q] = (ka && real) ? Ek[j] : 0.0f;
+      oj[q] = (ka && nj) ? Ok[j] : 0.0f;
+      orr[q] = (ka && lane == 31 && nr) ? Ok[j + 1] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int kk = k0 + q;
+      const float o0 = odj * oj[q];
+      float o1 = __shfl_down_sync(0xffffffffu, o0, 1);
+      if (lane == 31) o1 = odr * orr[q];
+      const float Dj = o1 - o0;
+      const float d = real ? fmaf(kcd, e[q], -kdx * sm.vk[kk] * Dj) : 0.0f;
+      sm.x[w * kFL + lane][kk] = d;
+      if (real && !wallc) fsum += sm.wvkd[kk] * (double)Dj;
+    }
   }
-  for (int kk = G.M; kk < 32; ++kk) sm.x[w * kFL + lane][kk] = 0.0f;
-  sm.fdat[w * kFL + lane] = fd;
+  sm.fdat[w * kFL + lane] = fsum;
+  __syncwarp();
+#pragma unroll 8
+  for (int u = 0; u < kFL; ++u) fd[u * 32 + lane] = sm.x[w * kFL + u][lane];
   __syncwarp();
 }
 
@@ -467,12 +502,12 @@ __device__ double f_wall_rhs(const Dev& D, const Inst& I, const FGeo& G, const d
 // precedes the call inside).
 template <bool FULL>
 __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
-                       const double* xg, int& par) {
+                       const double* xg, int& par, bool stage = false) {
   cl.sync();   // xg complete on every slice (halo reads)
   const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t N = G.N;
   f_cellparts<FULL>(sm, D, I, G, xg);
-  if (FULL) f_stage_data(sm, D, I, G);
+  if (FULL) f_stage_data(sm, D, I, G, stage);
   __syncthreads();
   const bool inflow = I.bc == GRTE_BC_INFLOW;
   const float v = sm.vk[k], v2 = sm.v2k[k];
@@ -561,9 +596,17 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     const int64_t j = G.c0 + t;
     if (j < N && !(inflow && (j == 0 || j == N - 1))) {
       if (FULL) {
-        double s = 0.0;
-        for (int kk = 0; kk < G.M; ++kk) s += (double)sm.x[t][kk];
-        sm.fl[t] += sm.fdat[t] + s;
+        // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
+        // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
+        float hi = 0.0f, lo = 0.0f;
+        for (int kk = 0; kk < G.M; ++kk) {
+          const float a = sm.x[t][kk];
+          const float sN = hi + a;
+          const float bb = sN - hi;
+          lo += (hi - (sN - bb)) + (a - bb);
+          hi = sN;
+        }
+        sm.fl[t] += sm.fdat[t] + ((double)hi + (double)lo);
       } else {
         float s = 0.0f;
         for (int kk = 0; kk < G.M; ++kk) s += sm.x[t][kk];
@@ -574,141 +617,123 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   __syncthreads();
 }
 
-// PCR step on rows held two per lane (row 2 lane + p) of a 64-row system, by shuffles.
-__device__ __forceinline__ double f_pick(double a0, double a1, int p) { return p ? a1 : a0; }
+// Right-hand side of row il (and row ir) of a 64-row system held two rows per lane of
+// warp 0 (rows 2 lane, 2 lane + 1 in v0, v1).
+__device__ __forceinline__ double f_row(double v0, double v1, int i) {
+  const int src = (i < 0 ? 0 : (i > 63 ? 63 : i));
+  const double a = __shfl_sync(0xffffffffu, v0, src >> 1), b = __shfl_sync(0xffffffffu, v1, src >> 1);
+  return (src & 1) ? b : a;
+}
 
-// z = P^{-1} rin on the slice (binary64), P the single-effective-angle Schur operator:
-//   u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) rin,  z = (rin - Gbar u)/alpha.
-// Warp 0 of every CTA solves the slice's rows (32 lanes x 16 cells, reduced 64 rows by
-// PCR in registers, 2x2 Schur complements to the interface, PCR over the 2Q interface rows
-// per CTA); the other warps wait.  rin and z: instance-local global vectors (own slice).
-__device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
-                       const double* rin, double* z, int& par) {
-  const int64_t N = G.N, co = G.co;
+// The single-effective-angle Schur operator of the preconditioner (binary64):
+//   P = alpha + Gbar (A + Gbar)^{-1} beta, applied as  u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) r,
+//   z = (r - Gbar u)/alpha,  Gbar = sum_k w_k G_k, beta = A - alpha.
+// The tridiagonal matrix T = A + (A/alpha) Gbar is the same for every application of a solve:
+// f_prec_factor eliminates it once (warp 0 of each CTA, 32 lanes x 16 cells: chunk sweeps,
+// PCR of the 64 chunk-end rows with its two unit spikes, the slice's 2x2 Schur complement,
+// and in every CTA the PCR multipliers of the 2Q-row interface system); f_prec_apply then
+// solves with the stored factors, without divisions.
+__device__ void f_prec_coef(const Dev& D, const Inst& I, const FGeo& G, int64_t j, double& a, double& b,
+                            double& c) {
+  if (j >= G.N) { a = 0.0; b = 1.0; c = 0.0; return; }
+  const int64_t g = G.co + j;
+  const double f = D.cf.A[g] * D.cf.ralpha[g];
+  const double l = D.cf.gl[g], u = D.cf.gu[g];
+  a = j > 0 ? -f * I.wv2 * l : 0.0;
+  c = j < G.N - 1 ? -f * I.wv2 * u : 0.0;
+  b = D.cf.A[g] + f * (I.wv2 * (l + u) + I.wv * D.cf.gb[g]);
+}
+
+__device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
+                              int& par) {
   const int lane = threadIdx.x & 31;
   const bool w0 = threadIdx.x < 32;
-  const double wv = I.wv, wv2 = I.wv2;
-  auto coef = [&](int64_t j, double& a, double& b, double& c) {
-    if (j >= N) { a = 0.0; b = 1.0; c = 0.0; return; }
-    const int64_t g = co + j;
-    const double f = D.cf.A[g] * D.cf.ralpha[g];
-    const double l = D.cf.gl[g], u = D.cf.gu[g];
-    a = j > 0 ? -f * wv2 * l : 0.0;
-    c = j < N - 1 ? -f * wv2 * u : 0.0;
-    b = D.cf.A[g] + f * (wv2 * (l + u) + wv * D.cf.gb[g]);
-  };
-  const int64_t s = G.c0 + lane * kFPL;   // this lane's chunk (warp 0)
-  double (*xr)[32] = sm.pxr;
-  double (*ch)[32] = sm.pch;
-  double (*ah)[32] = sm.pah;
-  double ra0 = 0, ra1 = 0, rb0 = 1, rb1 = 1, rc0 = 0, rc1 = 0, rr0 = 0, rr1 = 0, rg0 = 0, rg1 = 0, rh0 = 0, rh1 = 0;
-  double af = 0.0, cl_ = 0.0, rhp = 0.0;
   if (w0) {
-#pragma unroll
-    for (int u = 0; u < kFPL; ++u) {
-      const int64_t j = s + u;
-      xr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
-      ch[u][lane] = 0.0;
-      ah[u][lane] = 0.0;
-    }
-    // down sweep over the interior, up chain, reduced rows (as f_line_solve, in double)
+    const int64_t s = G.c0 + lane * kFPL;
+    double chp = 0.0, ahp = 0.0;
 #pragma unroll
     for (int u = 1; u <= kFPL - 2; ++u) {
       double a, b, c;
-      coef(s + u, a, b, c);
-      double den, ahv, num;
-      if (u == 1) { den = b; ahv = a; num = xr[u][lane]; }
-      else { den = b - a * ch[u - 1][lane]; ahv = -a * ah[u - 1][lane]; num = xr[u][lane] - a * rhp; }
+      f_prec_coef(D, I, G, s + u, a, b, c);
+      const double den = (u == 1) ? b : b - a * chp;
       const double inv = 1.0 / den;
-      ch[u][lane] = c * inv;
-      ah[u][lane] = ahv * inv;
-      rhp = num * inv;
-      xr[u][lane] = rhp;
+      ahp = ((u == 1) ? a : -a * ahp) * inv;
+      chp = c * inv;
+      sm.pinv[u][lane] = inv;
+      sm.pa[u][lane] = a;
+      sm.pch[u][lane] = chp;
+      sm.pah[u][lane] = ahp;
     }
-    double rc = rhp, cc = ch[kFPL - 2][lane], ac = ah[kFPL - 2][lane];
+    double cc = sm.pch[kFPL - 2][lane], ac = sm.pah[kFPL - 2][lane];
 #pragma unroll
     for (int u = kFPL - 3; u >= 1; --u) {
-      rc = xr[u][lane] - ch[u][lane] * rc;
-      cc = -ch[u][lane] * cc;
-      ac = ah[u][lane] - ch[u][lane] * ac;
+      const double chu = sm.pch[u][lane];
+      cc = -chu * cc;
+      ac = sm.pah[u][lane] - chu * ac;
     }
     double as, bs, cs, ae, be, ce;
-    coef(s, as, bs, cs);
-    coef(s + kFPL - 1, ae, be, ce);
-    ra0 = (lane == 0) ? 0.0 : as;
-    rb0 = bs - cs * ac;
-    rc0 = -cs * cc;
-    rr0 = xr[0][lane] - cs * rc;
-    ra1 = -ae * ah[kFPL - 2][lane];
-    rb1 = be - ae * ch[kFPL - 2][lane];
-    rc1 = (lane == 31) ? 0.0 : ce;
-    rr1 = xr[kFPL - 1][lane] - ae * rhp;
-    rg0 = (lane == 0) ? 1.0 : 0.0;
-    rh1 = (lane == 31) ? 1.0 : 0.0;
-    af = __shfl_sync(0xffffffffu, as, 0);
-    cl_ = __shfl_sync(0xffffffffu, ce, 31);
-    // PCR over the 64 rows (rows 2 lane and 2 lane + 1 on this lane), 6 levels
-    for (int st = 1; st < 64; st <<= 1) {
-      double na[2], nb[2], nc[2], n_r[2], n_g[2], n_h[2];
+    f_prec_coef(D, I, G, s, as, bs, cs);
+    f_prec_coef(D, I, G, s + kFPL - 1, ae, be, ce);
+    sm.pcs[lane] = cs;
+    sm.pae[lane] = ae;
+    double ra0 = (lane == 0) ? 0.0 : as, rb0 = bs - cs * ac, rc0 = -cs * cc;
+    double ra1 = -ae * sm.pah[kFPL - 2][lane], rb1 = be - ae * sm.pch[kFPL - 2][lane];
+    double rc1 = (lane == 31) ? 0.0 : ce;
+    double g0 = (lane == 0) ? 1.0 : 0.0, g1 = 0.0, h0 = 0.0, h1 = (lane == 31) ? 1.0 : 0.0;
+    const double af = __shfl_sync(0xffffffffu, as, 0), cl_ = __shfl_sync(0xffffffffu, ce, 31);
+    for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
+      double na[2], nb[2], nc[2], ng[2], nh[2];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int i = 2 * lane + p, il = i - st, ir = i + st;
         const bool hl = il >= 0, hr = ir < 64;
-        const int sl = (hl ? il : 0) >> 1, pl = (hl ? il : 0) & 1;
-        const int sr = (hr ? ir : 63) >> 1, pr = (hr ? ir : 63) & 1;
-        const double Lb = f_pick(__shfl_sync(0xffffffffu, rb0, sl), __shfl_sync(0xffffffffu, rb1, sl), pl);
-        const double La = f_pick(__shfl_sync(0xffffffffu, ra0, sl), __shfl_sync(0xffffffffu, ra1, sl), pl);
-        const double Lc = f_pick(__shfl_sync(0xffffffffu, rc0, sl), __shfl_sync(0xffffffffu, rc1, sl), pl);
-        const double Lr = f_pick(__shfl_sync(0xffffffffu, rr0, sl), __shfl_sync(0xffffffffu, rr1, sl), pl);
-        const double Lg = f_pick(__shfl_sync(0xffffffffu, rg0, sl), __shfl_sync(0xffffffffu, rg1, sl), pl);
-        const double Lh = f_pick(__shfl_sync(0xffffffffu, rh0, sl), __shfl_sync(0xffffffffu, rh1, sl), pl);
-        const double Rb = f_pick(__shfl_sync(0xffffffffu, rb0, sr), __shfl_sync(0xffffffffu, rb1, sr), pr);
-        const double Ra = f_pick(__shfl_sync(0xffffffffu, ra0, sr), __shfl_sync(0xffffffffu, ra1, sr), pr);
-        const double Rc = f_pick(__shfl_sync(0xffffffffu, rc0, sr), __shfl_sync(0xffffffffu, rc1, sr), pr);
-        const double Rr = f_pick(__shfl_sync(0xffffffffu, rr0, sr), __shfl_sync(0xffffffffu, rr1, sr), pr);
-        const double Rg = f_pick(__shfl_sync(0xffffffffu, rg0, sr), __shfl_sync(0xffffffffu, rg1, sr), pr);
-        const double Rh = f_pick(__shfl_sync(0xffffffffu, rh0, sr), __shfl_sync(0xffffffffu, rh1, sr), pr);
+        const double Lb = f_row(rb0, rb1, il), La = f_row(ra0, ra1, il), Lc = f_row(rc0, rc1, il);
+        const double Lg = f_row(g0, g1, il), Lh = f_row(h0, h1, il);
+        const double Rb = f_row(rb0, rb1, ir), Ra = f_row(ra0, ra1, ir), Rc = f_row(rc0, rc1, ir);
+        const double Rg = f_row(g0, g1, ir), Rh = f_row(h0, h1, ir);
         const double a = p ? ra1 : ra0, b = p ? rb1 : rb0, c = p ? rc1 : rc0;
-        const double r = p ? rr1 : rr0, gg = p ? rg1 : rg0, hh = p ? rh1 : rh0;
-        const double k1 = hl ? a / Lb : 0.0;
-        const double k2 = hr ? c / Rb : 0.0;
+        const double k1 = hl ? a / Lb : 0.0, k2 = hr ? c / Rb : 0.0;
+        sm.pk1[l][i] = k1;
+        sm.pk2[l][i] = k2;
         na[p] = hl ? -La * k1 : 0.0;
         nc[p] = hr ? -Rc * k2 : 0.0;
         nb[p] = b - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
-        n_r[p] = r - (hl ? Lr * k1 : 0.0) - (hr ? Rr * k2 : 0.0);
-        n_g[p] = gg - (hl ? Lg * k1 : 0.0) - (hr ? Rg * k2 : 0.0);
-        n_h[p] = hh - (hl ? Lh * k1 : 0.0) - (hr ? Rh * k2 : 0.0);
+        ng[p] = (p ? g1 : g0) - (hl ? Lg * k1 : 0.0) - (hr ? Rg * k2 : 0.0);
+        nh[p] = (p ? h1 : h0) - (hl ? Lh * k1 : 0.0) - (hr ? Rh * k2 : 0.0);
       }
       ra0 = na[0]; ra1 = na[1]; rb0 = nb[0]; rb1 = nb[1]; rc0 = nc[0]; rc1 = nc[1];
-      rr0 = n_r[0]; rr1 = n_r[1]; rg0 = n_g[0]; rg1 = n_g[1]; rh0 = n_h[0]; rh1 = n_h[1];
+      g0 = ng[0]; g1 = ng[1]; h0 = nh[0]; h1 = nh[1];
     }
-    {
-      const double i0 = 1.0 / rb0, i1 = 1.0 / rb1;
-      rr0 *= i0; rg0 *= i0; rh0 *= i0;
-      rr1 *= i1; rg1 *= i1; rh1 *= i1;
-    }
-    // the slice's 2x2 Schur complement on (first, last), published by lane 0
-    const double z00 = __shfl_sync(0xffffffffu, rg0, 0), z0n = __shfl_sync(0xffffffffu, rh0, 0);
-    const double zn0 = __shfl_sync(0xffffffffu, rg1, 31), znn = __shfl_sync(0xffffffffu, rh1, 31);
-    const double y0 = __shfl_sync(0xffffffffu, rr0, 0), y1 = __shfl_sync(0xffffffffu, rr1, 31);
+    const double i0 = 1.0 / rb0, i1 = 1.0 / rb1;
+    sm.pib[2 * lane] = i0;
+    sm.pib[2 * lane + 1] = i1;
+    g0 *= i0; h0 *= i0; g1 *= i1; h1 *= i1;
+    sm.pgv[2 * lane] = g0;
+    sm.pgv[2 * lane + 1] = g1;
+    sm.phv[2 * lane] = h0;
+    sm.phv[2 * lane + 1] = h1;
+    // the slice's 2x2 Schur complement on (first, last): S = Z^{-1}, Z = [[g0, h0], [g63, h63]]
+    const double z00 = __shfl_sync(0xffffffffu, g0, 0), z0n = __shfl_sync(0xffffffffu, h0, 0);
+    const double zn0 = __shfl_sync(0xffffffffu, g1, 31), znn = __shfl_sync(0xffffffffu, h1, 31);
     if (lane == 0) {
       const double id = 1.0 / (z00 * znn - z0n * zn0);
-      const double S11 = znn * id, S12 = -z0n * id, S21 = -zn0 * id, S22 = z00 * id;
-      sm.pe[par][0] = S11;
-      sm.pe[par][1] = S12;
-      sm.pe[par][2] = S21;
-      sm.pe[par][3] = S22;
-      sm.pe[par][4] = S11 * y0 + S12 * y1;
-      sm.pe[par][5] = S21 * y0 + S22 * y1;
+      sm.pS[0] = znn * id;
+      sm.pS[1] = -z0n * id;
+      sm.pS[2] = -zn0 * id;
+      sm.pS[3] = z00 * id;
+      sm.paf = af;
+      sm.pcl = cl_;
+      for (int q = 0; q < 4; ++q) sm.pe[par][q] = sm.pS[q];
       sm.pcoup[par][0] = af;
       sm.pcoup[par][1] = cl_;
     }
   }
-  cl.sync();   // every slice's Schur complement published
+  cl.sync();
   if (w0) {
-    // interface rows [F_0, L_0, F_1, L_1, ...] (2Q <= 32): lane i holds row i; PCR by shuffles
+    // interface rows [F_0, L_0, F_1, L_1, ...]: a_q L_{q-1} + S11 F_q + S12 L_q (F rows),
+    // S21 F_q + S22 L_q + c_q F_{q+1} (L rows); PCR multipliers stored per level
     const int Q = G.Q, n2 = 2 * Q;
-    double ia = 0.0, ib = 1.0, ic = 0.0, ir = 0.0;
+    double ia = 0.0, ib = 1.0, ic = 0.0;
     if (lane < n2) {
       const int qq = lane >> 1;
       const double* pe = cl.map_shared_rank(&sm.pe[par][0], qq);
@@ -717,47 +742,107 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
         ia = qq > 0 ? pc[0] : 0.0;
         ib = pe[0];
         ic = pe[1];
-        ir = pe[4];
       } else {
         ia = pe[2];
         ib = pe[3];
         ic = qq < Q - 1 ? pc[1] : 0.0;
-        ir = pe[5];
       }
     }
-    for (int st = 1; st < n2; st <<= 1) {
+    for (int l = 0, st = 1; st < n2; ++l, st <<= 1) {
       const int il = lane - st, irr = lane + st;
       const int sl = il >= 0 ? il : 0, sr = irr < n2 ? irr : 0;
       const double Lb = __shfl_sync(0xffffffffu, ib, sl), La = __shfl_sync(0xffffffffu, ia, sl);
-      const double Lc = __shfl_sync(0xffffffffu, ic, sl), Lr = __shfl_sync(0xffffffffu, ir, sl);
+      const double Lc = __shfl_sync(0xffffffffu, ic, sl);
       const double Rb = __shfl_sync(0xffffffffu, ib, sr), Ra = __shfl_sync(0xffffffffu, ia, sr);
-      const double Rc = __shfl_sync(0xffffffffu, ic, sr), Rr = __shfl_sync(0xffffffffu, ir, sr);
+      const double Rc = __shfl_sync(0xffffffffu, ic, sr);
+      const bool hl = il >= 0, hr = irr < n2;
+      const double k1 = hl ? ia / Lb : 0.0, k2 = hr ? ic / Rb : 0.0;
       if (lane < n2) {
-        const bool hl = il >= 0, hr = irr < n2;
-        const double k1 = hl ? ia / Lb : 0.0, k2 = hr ? ic / Rb : 0.0;
+        sm.ik1[l][lane] = k1;
+        sm.ik2[l][lane] = k2;
         const double na = hl ? -La * k1 : 0.0, nc = hr ? -Rc * k2 : 0.0;
         const double nb = ib - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
-        const double nr = ir - (hl ? Lr * k1 : 0.0) - (hr ? Rr * k2 : 0.0);
         ia = na;
         ib = nb;
         ic = nc;
-        ir = nr;
       }
     }
-    const double X = (lane < n2) ? ir / ib : 0.0;
+    sm.iib[lane] = (lane < n2) ? 1.0 / ib : 0.0;
+  }
+  par ^= 1;
+  __syncthreads();
+}
+
+// z = P^{-1} rin on the slice with the factors of f_prec_factor (binary64).  rin and z:
+// instance-local global vectors (own slice).
+__device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
+                       const double* rin, double* z, int& par) {
+  const int64_t N = G.N, co = G.co;
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
+  double y0 = 0.0, y1 = 0.0, rh14 = 0.0;
+  if (w0) {
+    const int64_t s = G.c0 + lane * kFPL;
+    double xv[kFPL];
+#pragma unroll
+    for (int u = 0; u < kFPL; ++u) {
+      const int64_t j = s + u;
+      xv[u] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
+    }
+    double rh = 0.0;
+#pragma unroll
+    for (int u = 1; u <= kFPL - 2; ++u) {
+      rh = (u == 1 ? xv[u] : xv[u] - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
+      sm.pxr[u][lane] = rh;
+    }
+    rh14 = rh;
+    double rc = rh;
+#pragma unroll
+    for (int u = kFPL - 3; u >= 1; --u) rc = sm.pxr[u][lane] - sm.pch[u][lane] * rc;
+    double r0 = xv[0] - sm.pcs[lane] * rc, r1 = xv[kFPL - 1] - sm.pae[lane] * rh14;
+    for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
+      double nr[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int i = 2 * lane + p;
+        const double Lr = f_row(r0, r1, i - st), Rr = f_row(r0, r1, i + st);
+        nr[p] = (p ? r1 : r0) - sm.pk1[l][i] * Lr - sm.pk2[l][i] * Rr;
+      }
+      r0 = nr[0];
+      r1 = nr[1];
+    }
+    y0 = r0 * sm.pib[2 * lane];
+    y1 = r1 * sm.pib[2 * lane + 1];
+    const double ya = __shfl_sync(0xffffffffu, y0, 0), yb = __shfl_sync(0xffffffffu, y1, 31);
+    if (lane == 0) {
+      sm.pe[par][4] = sm.pS[0] * ya + sm.pS[1] * yb;
+      sm.pe[par][5] = sm.pS[2] * ya + sm.pS[3] * yb;
+    }
+  }
+  cl.sync();   // every slice's reduced right-hand side published
+  if (w0) {
+    const int Q = G.Q, n2 = 2 * Q;
+    double ir = 0.0;
+    if (lane < n2) ir = cl.map_shared_rank(&sm.pe[par][0], lane >> 1)[4 + (lane & 1)];
+    for (int l = 0, st = 1; st < n2; ++l, st <<= 1) {
+      const int il = lane - st, irr = lane + st;
+      const double Lr = __shfl_sync(0xffffffffu, ir, il >= 0 ? il : 0);
+      const double Rr = __shfl_sync(0xffffffffu, ir, irr < n2 ? irr : 0);
+      if (lane < n2) ir = ir - sm.ik1[l][lane] * Lr - sm.ik2[l][lane] * Rr;
+    }
+    const double X = ir * sm.iib[lane];
     const int sLp = G.q > 0 ? 2 * G.q - 1 : 0, sFn = G.q < Q - 1 ? 2 * G.q + 2 : 0;
     const double XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
     const double Lp = G.q > 0 ? XL : 0.0, Fn = G.q < Q - 1 ? XF : 0.0;
-    const double la = Lp * af, fc = Fn * cl_;
-    const double xs = rr0 - la * rg0 - fc * rh0;
-    const double xe = rr1 - la * rg1 - fc * rh1;
-    // back substitution of the lane's chunk
+    const double la = Lp * sm.paf, fc = Fn * sm.pcl;
+    const double xs = y0 - la * sm.pgv[2 * lane] - fc * sm.phv[2 * lane];
+    const double xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
     sm.pu[lane * kFPL] = xs;
     sm.pu[lane * kFPL + kFPL - 1] = xe;
     double xn = xe;
 #pragma unroll
     for (int u = kFPL - 2; u >= 1; --u) {
-      xn = xr[u][lane] - ch[u][lane] * xn - ah[u][lane] * xs;
+      xn = sm.pxr[u][lane] - sm.pch[u][lane] * xn - sm.pah[u][lane] * xs;
       sm.pu[lane * kFPL + u] = xn;
     }
     if (lane == 0) {
@@ -776,7 +861,7 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const double uj = sm.pu[t];
       const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
       const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
-      const double Gu = wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + wv * D.cf.gb[g] * uj;
+      const double Gu = I.wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + I.wv * D.cf.gb[g] * uj;
       z[j] = (rin[j] - Gu) * D.cf.ralpha[g];
     }
   }
@@ -810,12 +895,13 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   auto Vi = [&](int i) { return D.gV + (int64_t)i * vstride + co; };
   int par = 0;
   f_load_cells(sm, D, I, G);
+  f_prec_factor(sm, cl, D, I, G, par);
   int cycles = 0, its = 0;
   double beta_prev = 0.0;
   bool first = true;
   for (;;) {
     // ---- restart: true residual at x, preconditioned, stopping test --------------------
-    f_pass<true>(sm, cl, D, I, G, x, par);
+    f_pass<true>(sm, cl, D, I, G, x, par, first);
     if (real) {
       const int64_t g = co + j;
       const double fl = sm.fl[t];
@@ -841,7 +927,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         loc[0] = vj * vj;
         loc[1] = x[j] * x[j];
       }
-      f_block_sums(sm, loc, 2);
+      f_block_sums<2>(sm, loc, 2);
       f_cluster_reduce(sm, cl, par, 2, false);
       const double nrm = sqrt(sm.sums[0]), xn = sqrt(sm.sums[1]);
       __syncthreads();
@@ -887,22 +973,28 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         f_prec(sm, cl, D, I, G, z, wv, par);
         double hcol[kMaxRestart + 2];
         for (int i = 0; i <= jc + 1; ++i) hcol[i] = 0.0;
+        // this thread's cell of V_0..V_jc, loaded together (predicated, unrolled)
+        double vv[kMaxRestart];
+#pragma unroll
+        for (int i = 0; i < kMaxRestart; ++i) vv[i] = (real && i <= jc) ? Vi(i)[j] : 0.0;
+        double wj = real ? wv[j] : 0.0;
         for (int pass = 0; pass < 2; ++pass) {
-          double loc[kMaxRestart + 1];
-          const double wj = real ? wv[j] : 0.0;
-          for (int i = 0; i <= jc; ++i) loc[i] = real ? wj * Vi(i)[j] : 0.0;
-          f_block_sums(sm, loc, jc + 1);
+          double loc[kMaxRestart];
+#pragma unroll
+          for (int i = 0; i < kMaxRestart; ++i) loc[i] = wj * vv[i];
+          f_block_sums<kMaxRestart>(sm, loc, jc + 1);
           f_cluster_reduce(sm, cl, par, jc + 1, false);
-          if (real) {
-            double tt = wv[j];
-            for (int i = 0; i <= jc; ++i) tt -= sm.sums[i] * Vi(i)[j];
-            wv[j] = tt;
-          }
-          for (int i = 0; i <= jc; ++i) hcol[i] += sm.sums[i];
+#pragma unroll
+          for (int i = 0; i < kMaxRestart; ++i)
+            if (i <= jc) {
+              wj -= sm.sums[i] * vv[i];
+              hcol[i] += sm.sums[i];
+            }
           __syncthreads();
         }
-        double l1[1] = {real ? wv[j] * wv[j] : 0.0};
-        f_block_sums(sm, l1, 1);
+        if (real) wv[j] = wj;
+        double l1[1] = {wj * wj};
+        f_block_sums<1>(sm, l1, 1);
         f_cluster_reduce(sm, cl, par, 1, false);
         const double nrmw = sqrt(sm.sums[0]);
         hcol[jc + 1] = nrmw;
@@ -926,7 +1018,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           sm.g[jc] = c0g * gj;
           for (int i = 0; i <= jc; ++i) sm.H[i * kMaxRestart + jc] = hcol[i];
         }
-        if (real) wv[j] *= (nrmw > 0.0 ? 1.0 / nrmw : 0.0);
+        if (real) wv[j] = wj * (nrmw > 0.0 ? 1.0 / nrmw : 0.0);
         __syncthreads();
         ++its;
         kk = jc + 1;
@@ -943,8 +1035,13 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       }
       __syncthreads();
       if (real) {
+        double vv[kMaxRestart];
+#pragma unroll
+        for (int i = 0; i < kMaxRestart; ++i) vv[i] = i < kk ? Vi(i)[j] : 0.0;
         double tq = x[j];
-        for (int i = 0; i < kk; ++i) tq += sm.y[i] * Vi(i)[j];
+#pragma unroll
+        for (int i = 0; i < kMaxRestart; ++i)
+          if (i < kk) tq += sm.y[i] * vv[i];
         x[j] = tq;
       }
       __syncthreads();

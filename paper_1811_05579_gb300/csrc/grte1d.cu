@@ -49,6 +49,7 @@ struct Inst {
   int64_t red_off;         // reduced-system storage of the preconditioner
   int ang_off;             // v, w, bL, bR
   int line_off;            // first line of this instance
+  int64_t fd_off;          // fused solve: the instance's staged data terms (floats)
 };
 
 struct Line {
@@ -109,6 +110,7 @@ struct Dev {
   double* energy;   // 3 per instance
   // learned Newton guess: per-cell features (6 floats), predicted and logged targets
   float *feat, *guess, *ytrue;
+  float* fdata;     // fused solve: data terms of the prediction, [slice cell][32 angles]
   int use_guess, log_samples;
   int start_prev;   // 1: Newton starts one step from T^n instead of the closed-form bound
   int m;  // restart length
@@ -1834,8 +1836,15 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
         h->fcnt[c] = (int)cls[c].size();
         order.insert(order.end(), cls[c].begin(), cls[c].end());
       }
+      int64_t fd = 0;
+      for (int i = 0; i < n_inst; ++i) {
+        h->inst[i].fd_off = fd;
+        fd += (int64_t)(1 << fused_class(h->inst[i].N)) * kFS * 32;
+      }
       if (dalloc(h, &h->d_finst, n_inst) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc finst");
+      if (dalloc(h, &D.fdata, fd) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc fdata");
       CK(cudaMemcpy(h->d_finst, order.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_inst, h->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice));
       h->fused = true;
     }
   }
