@@ -78,7 +78,8 @@ struct FSmem {
   double pxl[2];
   // GMRES state (identical in every CTA)
   double H[(kMaxRestart + 1) * kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart],
-      y[kMaxRestart];
+      y[kMaxRestart], hc[kMaxRestart + 2];
+  int stop;
 };
 
 // Per-CTA geometry.
@@ -91,7 +92,7 @@ struct FGeo {
 // Sums of nv values per thread over the CTA (fixed order), result in sm.sums[0..nv-1] for
 // every thread.  nv <= kMaxRestart + 2.
 template <int NV>
-__device__ void f_block_sums(FSmem& sm, const double* v, int nv) {
+__device__ __forceinline__ void f_block_sums(FSmem& sm, const double* v, int nv) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
@@ -109,7 +110,7 @@ __device__ void f_block_sums(FSmem& sm, const double* v, int nv) {
   __syncthreads();
 }
 
-__device__ double f_block_max(FSmem& sm, double v) {
+__device__ __forceinline__ double f_block_max(FSmem& sm, double v) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (lane == 0) sm.red[wid][0] = v;
@@ -148,35 +149,29 @@ __device__ __forceinline__ void f_coef(const FSmem& sm, int jl, float v, float v
   b = fmaf(v, sm.gb[jl], fmaf(v2, l + u, sm.A[jl]));
 }
 
-// PCR on n <= kFR rows per lane of (ra, rb, rc) with nr right-hand sides (rr, rg, rh), in
+// PCR on n <= kFR rows per lane of (ra, rb, rc) with NR right-hand sides (rr; rg, rh), in
 // place; on return rr (rg, rh) hold the solutions.  Every thread takes part.
 template <int NR>
-__device__ void f_pcr(FSmem& sm, int n) {
+__device__ __forceinline__ void f_pcr(FSmem& sm, int n) {
   const int lane = threadIdx.x & 31;
   const int r0 = threadIdx.x >> 5;   // rows r0 and r0 + kFW
   for (int st = 1; st < n; st <<= 1) {
-    float na[2], nb[2], nc[2], nrr[2][NR];
+    float na[2], nb[2], nc[2], n1[2], n2[2], n3[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int i = r0 + p * kFW;
+      na[p] = nb[p] = nc[p] = n1[p] = n2[p] = n3[p] = 0.0f;
       if (i >= n) continue;
+      const int il = i - st >= 0 ? i - st : i, ir = i + st < n ? i + st : i;
       const bool hl = i - st >= 0, hr = i + st < n;
-      const float k1 = hl ? sm.ra[i][lane] / sm.rb[i - st][lane] : 0.0f;
-      const float k2 = hr ? sm.rc[i][lane] / sm.rb[i + st][lane] : 0.0f;
-      na[p] = hl ? -sm.ra[i - st][lane] * k1 : 0.0f;
-      nc[p] = hr ? -sm.rc[i + st][lane] * k2 : 0.0f;
-      float b = sm.rb[i][lane];
-      if (hl) b -= sm.rc[i - st][lane] * k1;
-      if (hr) b -= sm.ra[i + st][lane] * k2;
-      nb[p] = b;
-      float* R[3] = {&sm.rr[0][0], &sm.rg[0][0], &sm.rh[0][0]};
-#pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        float r = R[q][i * 32 + lane];
-        if (hl) r -= R[q][(i - st) * 32 + lane] * k1;
-        if (hr) r -= R[q][(i + st) * 32 + lane] * k2;
-        nrr[p][q] = r;
-      }
+      const float k1 = hl ? sm.ra[i][lane] / sm.rb[il][lane] : 0.0f;
+      const float k2 = hr ? sm.rc[i][lane] / sm.rb[ir][lane] : 0.0f;
+      na[p] = -sm.ra[il][lane] * k1;
+      nc[p] = -sm.rc[ir][lane] * k2;
+      nb[p] = sm.rb[i][lane] - sm.rc[il][lane] * k1 - sm.ra[ir][lane] * k2;
+      n1[p] = sm.rr[i][lane] - sm.rr[il][lane] * k1 - sm.rr[ir][lane] * k2;
+      if (NR > 1) n2[p] = sm.rg[i][lane] - sm.rg[il][lane] * k1 - sm.rg[ir][lane] * k2;
+      if (NR > 2) n3[p] = sm.rh[i][lane] - sm.rh[il][lane] * k1 - sm.rh[ir][lane] * k2;
     }
     __syncthreads();
 #pragma unroll
@@ -186,9 +181,9 @@ __device__ void f_pcr(FSmem& sm, int n) {
       sm.ra[i][lane] = na[p];
       sm.rb[i][lane] = nb[p];
       sm.rc[i][lane] = nc[p];
-      float* R[3] = {&sm.rr[0][0], &sm.rg[0][0], &sm.rh[0][0]};
-#pragma unroll
-      for (int q = 0; q < NR; ++q) R[q][i * 32 + lane] = nrr[p][q];
+      sm.rr[i][lane] = n1[p];
+      if (NR > 1) sm.rg[i][lane] = n2[p];
+      if (NR > 2) sm.rh[i][lane] = n3[p];
     }
     __syncthreads();
   }
@@ -211,9 +206,31 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
   const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float v = sm.vk[k], v2 = sm.v2k[k];
   const int row0 = w * kFL;
-  float ch[kFL - 2], ah[kFL - 2];
-  float rhp = 0.0f;
-  // down sweep over the chunk's interior: x_u = rh_u - ch_u x_{u+1} - ah_u x_s
+  // (1) backward elimination of the chunk's interior from its last cell:
+  //     x_u = rt_u - at_u x_{u-1} - ct_u x_e, down to u = 1 (the S row's partner)
+  float rt = 0.0f, at = 0.0f, ct = 0.0f;
+#pragma unroll
+  for (int u = kFL - 2; u >= 1; --u) {
+    float a, b, c;
+    f_coef(sm, row0 + u + 1, v, v2, a, b, c);
+    const float r = sm.x[row0 + u][k];
+    float den, num, ctv;
+    if (u == kFL - 2) {
+      den = b;
+      num = r;
+      ctv = c;
+    } else {
+      den = fmaf(-c, at, b);
+      num = fmaf(-c, rt, r);
+      ctv = -c * ct;
+    }
+    const float inv = 1.0f / den;
+    rt = num * inv;
+    at = a * inv;
+    ct = ctv * inv;
+  }
+  // (2) forward elimination: x_u = rh_u - ch_u x_{u+1} - ah_u x_s (rh_u kept in sm.x)
+  float rhp = 0.0f, chp = 0.0f, ahp = 0.0f;
 #pragma unroll
   for (int u = 1; u <= kFL - 2; ++u) {
     float a, b, c;
@@ -225,36 +242,29 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       ahv = a;
       num = r;
     } else {
-      den = fmaf(-a, ch[u - 2], b);
-      ahv = -a * ah[u - 2];
+      den = fmaf(-a, chp, b);
+      ahv = -a * ahp;
       num = fmaf(-a, rhp, r);
     }
     const float inv = 1.0f / den;
-    ch[u - 1] = c * inv;
-    ah[u - 1] = ahv * inv;
+    chp = c * inv;
+    ahp = ahv * inv;
     rhp = num * inv;
     sm.x[row0 + u][k] = rhp;
-  }
-  // up chain: x_1 = rc - cc x_e - ac x_s
-  float rc = rhp, cc = ch[kFL - 3], ac = ah[kFL - 3];
-#pragma unroll
-  for (int u = kFL - 3; u >= 1; --u) {
-    const float chu = ch[u - 1];
-    rc = fmaf(-chu, rc, sm.x[row0 + u][k]);
-    cc = -chu * cc;
-    ac = fmaf(-chu, ac, ah[u - 1]);
   }
   {
     float as, bs, cs, ae, be, ce;
     f_coef(sm, row0 + 1, v, v2, as, bs, cs);
     f_coef(sm, row0 + kFL, v, v2, ae, be, ce);
     const float rs = sm.x[row0][k], re = sm.x[row0 + kFL - 1][k];
+    // S row: a_s x_{s-1} + b_s x_s + c_s x_1, x_1 = rt - at x_s - ct x_e
     sm.ra[2 * w][k] = (w == 0) ? 0.0f : as;
-    sm.rb[2 * w][k] = fmaf(-cs, ac, bs);
-    sm.rc[2 * w][k] = -cs * cc;
-    sm.rr[2 * w][k] = fmaf(-cs, rc, rs);
-    sm.ra[2 * w + 1][k] = -ae * ah[kFL - 3];
-    sm.rb[2 * w + 1][k] = fmaf(-ae, ch[kFL - 3], be);
+    sm.rb[2 * w][k] = fmaf(-cs, at, bs);
+    sm.rc[2 * w][k] = -cs * ct;
+    sm.rr[2 * w][k] = fmaf(-cs, rt, rs);
+    // E row: a_e x_{e-1} + b_e x_e + c_e x_{e+1}, x_{e-1} = rh - ch x_e - ah x_s
+    sm.ra[2 * w + 1][k] = -ae * ahp;
+    sm.rb[2 * w + 1][k] = fmaf(-ae, chp, be);
     sm.rc[2 * w + 1][k] = (w == kFW - 1) ? 0.0f : ce;
     sm.rr[2 * w + 1][k] = fmaf(-ae, rhp, re);
     sm.rg[2 * w][k] = (w == 0) ? 1.0f : 0.0f;          // unit spikes of the slice's reduced system
@@ -338,8 +348,24 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
   }
   par ^= 1;
   __syncthreads();
-  // back substitution of the chunk
+  // back substitution of the chunk: the forward factors ch, ah (matrix only) recomputed
+  // into registers, then x_u = rh_u - ch_u x_{u+1} - ah_u x_s from the last cell down
   const float xs = sm.rr[2 * w][k], xe = sm.rr[2 * w + 1][k];
+  float ch[kFL - 2], ah[kFL - 2];
+  {
+    float chv = 0.0f, ahv = 0.0f;
+#pragma unroll
+    for (int u = 1; u <= kFL - 2; ++u) {
+      float a, b, c;
+      f_coef(sm, row0 + u + 1, v, v2, a, b, c);
+      const float den = (u == 1) ? b : fmaf(-a, chv, b);
+      const float inv = 1.0f / den;
+      ahv = ((u == 1) ? a : -a * ahv) * inv;
+      chv = c * inv;
+      ch[u - 1] = chv;
+      ah[u - 1] = ahv;
+    }
+  }
   sm.x[row0][k] = xs;
   sm.x[row0 + kFL - 1][k] = xe;
   float xn = xe;
@@ -569,38 +595,24 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       if (k == 0) sm.fl[tl] += sw;
     }
   }
-  // e/o flux w_k v_k (O_{j+1} - O_j) of every interior cell without the data part:
-  //   -w_k v_k^2 [dlx_{j+1} (e_{j+1} - e_j) - dlx_j (e_j - e_{j-1})]  (node terms at 1..N-1)
-  float val[kFL];
-  {
-    const float wv = sm.wvk[k];
-#pragma unroll
-    for (int u = 0; u < kFL; ++u) {
-      const int t = w * kFL + u;
-      const int64_t j = G.c0 + t;
-      const float ej = sm.x[t][k];
-      const float el = (t > 0) ? sm.x[t - 1][k] : sm.xlr[0][k];
-      const float er = (t < kFS - 1) ? sm.x[t + 1][k] : sm.xlr[1][k];
-      const float OR = (j + 1 <= N - 1) ? sm.dlx[t + 2] * (er - ej) : 0.0f;
-      const float OL = (j >= 1) ? sm.dlx[t + 1] * (ej - el) : 0.0f;
-      const bool wallc = inflow && (j == 0 || j == N - 1);
-      val[u] = (j < N && !wallc) ? -wv * v * (OR - OL) : 0.0f;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < kFL; ++u) sm.x[w * kFL + u][k] = val[u];
-  __syncthreads();
+  // e/o flux of every interior cell without the data part, summed over the angles by the
+  // cell's own thread (reads its row and the two neighbouring rows of sm.x):
+  //   sum_k -w_k v_k^2 [dlx_{j+1} (e_{j+1} - e_j) - dlx_j (e_j - e_{j-1})]  (nodes 1..N-1)
   {
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
     if (j < N && !(inflow && (j == 0 || j == N - 1))) {
+      const float dR = (j + 1 <= N - 1) ? sm.dlx[t + 2] : 0.0f;
+      const float dL = (j >= 1) ? sm.dlx[t + 1] : 0.0f;
+      const float* xl = (t > 0) ? &sm.x[t - 1][0] : &sm.xlr[0][0];
+      const float* xr = (t < kFS - 1) ? &sm.x[t + 1][0] : &sm.xlr[1][0];
       if (FULL) {
         // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
         // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
         float hi = 0.0f, lo = 0.0f;
         for (int kk = 0; kk < G.M; ++kk) {
-          const float a = sm.x[t][kk];
+          const float ej = sm.x[t][kk];
+          const float a = -sm.wvk[kk] * sm.vk[kk] * (dR * (xr[kk] - ej) - dL * (ej - xl[kk]));
           const float sN = hi + a;
           const float bb = sN - hi;
           lo += (hi - (sN - bb)) + (a - bb);
@@ -608,9 +620,12 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
         }
         sm.fl[t] += sm.fdat[t] + ((double)hi + (double)lo);
       } else {
-        float s = 0.0f;
-        for (int kk = 0; kk < G.M; ++kk) s += sm.x[t][kk];
-        sm.fl[t] = (double)((float)sm.fl[t] + s);
+        float acc = (float)sm.fl[t];
+        for (int kk = 0; kk < G.M; ++kk) {
+          const float ej = sm.x[t][kk];
+          acc += -sm.wvk[kk] * sm.vk[kk] * (dR * (xr[kk] - ej) - dL * (ej - xl[kk]));
+        }
+        sm.fl[t] = (double)acc;
       }
     }
   }
@@ -783,23 +798,23 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   double y0 = 0.0, y1 = 0.0, rh14 = 0.0;
   if (w0) {
     const int64_t s = G.c0 + lane * kFPL;
-    double xv[kFPL];
 #pragma unroll
     for (int u = 0; u < kFPL; ++u) {
       const int64_t j = s + u;
-      xv[u] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
+      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
     }
     double rh = 0.0;
 #pragma unroll
     for (int u = 1; u <= kFPL - 2; ++u) {
-      rh = (u == 1 ? xv[u] : xv[u] - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
+      const double xu = sm.pxr[u][lane];
+      rh = (u == 1 ? xu : xu - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
       sm.pxr[u][lane] = rh;
     }
     rh14 = rh;
     double rc = rh;
 #pragma unroll
     for (int u = kFPL - 3; u >= 1; --u) rc = sm.pxr[u][lane] - sm.pch[u][lane] * rc;
-    double r0 = xv[0] - sm.pcs[lane] * rc, r1 = xv[kFPL - 1] - sm.pae[lane] * rh14;
+    double r0 = sm.pxr[0][lane] - sm.pcs[lane] * rc, r1 = sm.pxr[kFPL - 1][lane] - sm.pae[lane] * rh14;
     for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
       double nr[2];
 #pragma unroll
@@ -971,59 +986,70 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         __syncthreads();
         double* wv = Vi(jc + 1);
         f_prec(sm, cl, D, I, G, z, wv, par);
-        double hcol[kMaxRestart + 2];
-        for (int i = 0; i <= jc + 1; ++i) hcol[i] = 0.0;
-        // this thread's cell of V_0..V_jc, loaded together (predicated, unrolled)
-        double vv[kMaxRestart];
-#pragma unroll
-        for (int i = 0; i < kMaxRestart; ++i) vv[i] = (real && i <= jc) ? Vi(i)[j] : 0.0;
+        // classical Gram-Schmidt, twice (CGS2): per pass one block sum of the jc + 1 dot
+        // products w.V_i (each thread's terms reduced by shuffles as they are formed) and one
+        // cluster sum; the Hessenberg column accumulates in shared memory
         double wj = real ? wv[j] : 0.0;
+        if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
-          double loc[kMaxRestart];
+          const int lane = t & 31, wid = t >> 5;
 #pragma unroll
-          for (int i = 0; i < kMaxRestart; ++i) loc[i] = wj * vv[i];
-          f_block_sums<kMaxRestart>(sm, loc, jc + 1);
+          for (int i = 0; i < kMaxRestart; ++i) {
+            if (i > jc) break;
+            double p = (real ? Vi(i)[j] : 0.0) * wj;
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == 0) sm.red[wid][i] = p;
+          }
+          __syncthreads();
+          if (t <= jc) {
+            double tq = 0.0;
+            for (int w2 = 0; w2 < kFW; ++w2) tq += sm.red[w2][t];
+            sm.sums[t] = tq;
+          }
+          __syncthreads();
           f_cluster_reduce(sm, cl, par, jc + 1, false);
 #pragma unroll
-          for (int i = 0; i < kMaxRestart; ++i)
-            if (i <= jc) {
-              wj -= sm.sums[i] * vv[i];
-              hcol[i] += sm.sums[i];
-            }
+          for (int i = 0; i < kMaxRestart; ++i) {
+            if (i > jc) break;
+            if (real) wj -= sm.sums[i] * Vi(i)[j];
+          }
+          if (t <= jc) sm.hc[t] += sm.sums[t];
           __syncthreads();
         }
-        if (real) wv[j] = wj;
-        double l1[1] = {wj * wj};
-        f_block_sums<1>(sm, l1, 1);
+        {
+          double l1[1] = {wj * wj};
+          f_block_sums<1>(sm, l1, 1);
+        }
         f_cluster_reduce(sm, cl, par, 1, false);
         const double nrmw = sqrt(sm.sums[0]);
-        hcol[jc + 1] = nrmw;
-        // Givens rotations (every thread, identical values)
-        for (int i = 0; i < jc; ++i) {
-          const double tq = sm.cs[i] * hcol[i] + sm.sn[i] * hcol[i + 1];
-          hcol[i + 1] = -sm.sn[i] * hcol[i] + sm.cs[i] * hcol[i + 1];
-          hcol[i] = tq;
-        }
-        const double a0 = hcol[jc], b0 = hcol[jc + 1];
-        const double rr = hypot(a0, b0);
-        const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
-        hcol[jc] = rr;
-        const double gj = sm.g[jc];
-        const double gnext = -s0g * gj;
-        __syncthreads();
+        // Givens rotations and the GMRES residual estimate (thread 0; shared with all)
         if (t == 0) {
+          double* hc = sm.hc;
+          hc[jc + 1] = nrmw;
+          for (int i = 0; i < jc; ++i) {
+            const double tq = sm.cs[i] * hc[i] + sm.sn[i] * hc[i + 1];
+            hc[i + 1] = -sm.sn[i] * hc[i] + sm.cs[i] * hc[i + 1];
+            hc[i] = tq;
+          }
+          const double a0 = hc[jc], b0 = hc[jc + 1];
+          const double rr = hypot(a0, b0);
+          const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
+          hc[jc] = rr;
+          const double gj = sm.g[jc];
+          const double gnext = -s0g * gj;
           sm.cs[jc] = c0g;
           sm.sn[jc] = s0g;
           sm.g[jc + 1] = gnext;
           sm.g[jc] = c0g * gj;
-          for (int i = 0; i <= jc; ++i) sm.H[i * kMaxRestart + jc] = hcol[i];
+          for (int i = 0; i <= jc; ++i) sm.H[i * kMaxRestart + jc] = hc[i];
+          const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
+          sm.stop = (est || nrmw == 0.0 || jc + 1 >= m) ? 1 : 0;
         }
         if (real) wv[j] = wj * (nrmw > 0.0 ? 1.0 / nrmw : 0.0);
         __syncthreads();
         ++its;
         kk = jc + 1;
-        const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
-        if (est || nrmw == 0.0 || jc + 1 >= m) break;
+        if (sm.stop) break;
       }
       // x += V y, H y = g (upper triangular, kk columns)
       if (t == 0) {
@@ -1035,13 +1061,12 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       }
       __syncthreads();
       if (real) {
-        double vv[kMaxRestart];
-#pragma unroll
-        for (int i = 0; i < kMaxRestart; ++i) vv[i] = i < kk ? Vi(i)[j] : 0.0;
         double tq = x[j];
 #pragma unroll
-        for (int i = 0; i < kMaxRestart; ++i)
-          if (i < kk) tq += sm.y[i] * vv[i];
+        for (int i = 0; i < kMaxRestart; ++i) {
+          if (i >= kk) break;
+          tq += sm.y[i] * Vi(i)[j];
+        }
         x[j] = tq;
       }
       __syncthreads();
