@@ -67,7 +67,9 @@ struct FSmem {
   double pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
   double ik1[5][32], ik2[5][32], iib[32];
   double pS[4], paf, pcl;
-  double wgt[kFS];                                      // stopping-test weights
+  float wgt[kFS];                                       // stopping-test weights
+  double wvec[kFS];                                     // the Arnoldi vector being orthogonalised
+  double sc[4];                                         // scalars computed once (thread 0)
   double wall[2][32];                                   // wall-row right-hand sides (double)
   double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
   double part[2][kMaxRestart + 2];                      // cluster partials (double-buffered)
@@ -89,36 +91,35 @@ struct FGeo {
   int N, M;
 };
 
-// Sums of nv values per thread over the CTA (fixed order), result in sm.sums[0..nv-1] for
-// every thread.  nv <= kMaxRestart + 2.
-template <int NV>
-__device__ __forceinline__ void f_block_sums(FSmem& sm, const double* v, int nv) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Block sums over the slice of nv <= NV per-cell terms term(i, t) (t the slice cell): 64
+// threads each accumulate 8 cells, then one shuffle tree per value in two warps (binary64
+// additions are the scarce resource: 8x fewer than a tree over 512 threads).  Result in
+// sm.sums[0..nv-1]; every thread takes part in the barriers.
+constexpr int kGT = 64;
+template <int NV, bool MAX, class F>
+__device__ __forceinline__ void f_slice_sums(FSmem& sm, int nv, F term) {
+  const int t = threadIdx.x;
+  if (t < kGT) {
+    const int lane = t & 31, wid = t >> 5;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i >= nv) break;
-    double t = v[i];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sm.red[wid][i] = t;
+    for (int i = 0; i < NV; ++i) {
+      if (i >= nv) break;
+      double a = 0.0;
+#pragma unroll
+      for (int c = 0; c < kFS / kGT; ++c) {
+        const double v = term(i, t + c * kGT);
+        a = MAX ? fmax(a, v) : a + v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double b = __shfl_xor_sync(0xffffffffu, a, o);
+        a = MAX ? fmax(a, b) : a + b;
+      }
+      if (lane == 0) sm.red[wid][i] = a;
+    }
   }
   __syncthreads();
-  if (threadIdx.x < nv) {
-    double t = 0.0;
-    for (int w = 0; w < kFW; ++w) t += sm.red[w][threadIdx.x];
-    sm.sums[threadIdx.x] = t;
-  }
+  if (t < nv) sm.sums[t] = MAX ? fmax(sm.red[0][t], sm.red[1][t]) : sm.red[0][t] + sm.red[1][t];
   __syncthreads();
-}
-
-__device__ __forceinline__ double f_block_max(FSmem& sm, double v) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) sm.red[wid][0] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kFW; ++w) t = fmax(t, sm.red[w][0]);
-  __syncthreads();
-  return t;
 }
 
 // Cluster sums (is_max = 0) or maxima of the nv values in sm.sums (rank order); result in
@@ -164,8 +165,8 @@ __device__ __forceinline__ void f_pcr(FSmem& sm, int n) {
       if (i >= n) continue;
       const int il = i - st >= 0 ? i - st : i, ir = i + st < n ? i + st : i;
       const bool hl = i - st >= 0, hr = i + st < n;
-      const float k1 = hl ? sm.ra[i][lane] / sm.rb[il][lane] : 0.0f;
-      const float k2 = hr ? sm.rc[i][lane] / sm.rb[ir][lane] : 0.0f;
+      const float k1 = hl ? __fdividef(sm.ra[i][lane], sm.rb[il][lane]) : 0.0f;
+      const float k2 = hr ? __fdividef(sm.rc[i][lane], sm.rb[ir][lane]) : 0.0f;
       na[p] = -sm.ra[il][lane] * k1;
       nc[p] = -sm.rc[ir][lane] * k2;
       nb[p] = sm.rb[i][lane] - sm.rc[il][lane] * k1 - sm.ra[ir][lane] * k2;
@@ -191,7 +192,7 @@ __device__ __forceinline__ void f_pcr(FSmem& sm, int n) {
   for (int p = 0; p < 2; ++p) {
     const int i = r0 + p * kFW;
     if (i >= n) continue;
-    const float ib = 1.0f / sm.rb[i][lane];
+    const float ib = __frcp_rn(sm.rb[i][lane]);
     sm.rr[i][lane] *= ib;
     if (NR > 1) sm.rg[i][lane] *= ib;
     if (NR > 2) sm.rh[i][lane] *= ib;
@@ -224,7 +225,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       num = fmaf(-c, rt, r);
       ctv = -c * ct;
     }
-    const float inv = 1.0f / den;
+    const float inv = __frcp_rn(den);
     rt = num * inv;
     at = a * inv;
     ct = ctv * inv;
@@ -246,7 +247,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       ahv = -a * ahp;
       num = fmaf(-a, rhp, r);
     }
-    const float inv = 1.0f / den;
+    const float inv = __frcp_rn(den);
     chp = c * inv;
     ahp = ahv * inv;
     rhp = num * inv;
@@ -280,7 +281,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
   if (w == 0) {
     const float z00 = sm.rg[0][k], z0n = sm.rh[0][k], zn0 = sm.rg[kFR - 1][k], znn = sm.rh[kFR - 1][k];
     const float det = z00 * znn - z0n * zn0;
-    const float id = 1.0f / det;
+    const float id = __frcp_rn(det);
     const float S11 = znn * id, S12 = -z0n * id, S21 = -zn0 * id, S22 = z00 * id;
     const float y0 = sm.rr[0][k], y1 = sm.rr[kFR - 1][k];
     sm.ends[par][0][k] = S11;
@@ -359,7 +360,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       float a, b, c;
       f_coef(sm, row0 + u + 1, v, v2, a, b, c);
       const float den = (u == 1) ? b : fmaf(-a, chv, b);
-      const float inv = 1.0f / den;
+      const float inv = __frcp_rn(den);
       ahv = ((u == 1) ? a : -a * ahv) * inv;
       chv = c * inv;
       ch[u - 1] = chv;
@@ -413,6 +414,20 @@ template <bool FULL>
 __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const double* xg) {
   const int t = threadIdx.x;
   const int64_t j = G.c0 + t;
+  const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == G.N - 1);
+  if (!FULL && j < G.N && !wallc) {
+    // a Krylov direction's parts are used in binary32: formed in binary32 (the binary64
+    // pipe is the scarce one) from the direction and the binary32 coefficient copies
+    const int64_t g = G.co + j, N = G.N;
+    const float xj = (float)xg[j], xl = j > 0 ? (float)xg[j - 1] : 0.0f, xr = j < N - 1 ? (float)xg[j + 1] : 0.0f;
+    const float gl = sm.gl[t + 1], gu = sm.gu[t + 1];
+    sm.P1[t] = -D.fc.alpha[g] * xj;
+    sm.P2[t] = gl * (xj - xl) + gu * (xj - xr);
+    sm.P3[t] = sm.gb[t + 1] * xj;
+    sm.fl[t] = (double)((float)I.wv2 * (D.fc.fR[g] * (xj - xr) + D.fc.fL[g] * (xj - xl)) +
+                        (float)I.wv * D.fc.gbx[g] * xj);
+    return;
+  }
   if (j < G.N) {
     const int64_t g = G.co + j, N = G.N;
     const double xj = xg[j], xl = j > 0 ? xg[j - 1] : 0.0, xr = j < N - 1 ? xg[j + 1] : 0.0;
@@ -428,11 +443,9 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     sm.P1[t] = (float)p1;
     sm.P2[t] = (float)p2;
     sm.P3[t] = (float)p3;
-    // Krylov directions sum the interior fluxes in binary32; the inflow wall cells keep
-    // their rho part in double: it cancels against the e/o wall sum to O(eps), both
-    // carrying the factor 2/eps
-    const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
-    sm.fl[t] = (FULL || wallc) ? fr : (double)(float)fr;
+    // (here: data passes, and the inflow wall cells of Krylov passes, whose rho part
+    // cancels against the e/o wall sum to O(eps), both carrying the factor 2/eps)
+    sm.fl[t] = fr;
   } else {
     sm.P1[t] = 0.0f;
     sm.P2[t] = 0.0f;
@@ -924,31 +937,30 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       z[j] = -R;
       D.Fs[g] = fl;
     }
-    {
-      const double xm = f_block_max(sm, real ? fabs(x[j]) : 0.0);
-      if (t == 0) sm.sums[0] = xm;
-      __syncthreads();
-      f_cluster_reduce(sm, cl, par, 1, true);
-    }
+    f_slice_sums<1, true>(sm, 1, [&](int, int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
+    f_cluster_reduce(sm, cl, par, 1, true);
     const double xmax = sm.sums[0];
-    sm.wgt[t] = real ? 1.0 / (fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0;
+    sm.wgt[t] = real ? 1.0f / (float)(fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0f;
     __syncthreads();
     double* v0 = Vi(0);
     f_prec(sm, cl, D, I, G, z, v0, par);
     {
-      double loc[2] = {0.0, 0.0};
-      if (real) {
-        const double vj = v0[j];
-        loc[0] = vj * vj;
-        loc[1] = x[j] * x[j];
-      }
-      f_block_sums<2>(sm, loc, 2);
+      f_slice_sums<2, false>(sm, 2, [&](int i, int c) {
+        if (G.c0 + c >= N) return 0.0;
+        const double a = i == 0 ? v0[G.c0 + c] : x[G.c0 + c];
+        return a * a;
+      });
       f_cluster_reduce(sm, cl, par, 2, false);
-      const double nrm = sqrt(sm.sums[0]), xn = sqrt(sm.sums[1]);
+      if (t == 0) {
+        sm.sc[0] = sqrt(sm.sums[0]);
+        sm.sc[1] = sqrt(sm.sums[1]);
+        sm.sc[2] = 1.0 / sm.sc[0];
+      }
       __syncthreads();
-      const double bm = f_block_max(sm, real ? fabs(v0[j]) * sm.wgt[t] : 0.0);
-      if (t == 0) sm.sums[0] = bm;
-      __syncthreads();
+      const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2];
+      f_slice_sums<1, true>(sm, 1, [&](int, int c) {
+        return G.c0 + c < N ? fabs(v0[G.c0 + c]) * (double)sm.wgt[c] : 0.0;
+      });
       f_cluster_reduce(sm, cl, par, 1, true);
       const double rinf_c = sm.sums[0];
       __syncthreads();
@@ -972,7 +984,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         sm.g[0] = nrm;
         for (int i = 1; i <= m; ++i) sm.g[i] = 0.0;
       }
-      if (real) v0[j] *= 1.0 / nrm;
+      if (real) v0[j] *= inv_nrm;
       __syncthreads();
       int kk = 0;
       for (int jc = 0; jc < m; ++jc) {
@@ -987,41 +999,36 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         double* wv = Vi(jc + 1);
         f_prec(sm, cl, D, I, G, z, wv, par);
         // classical Gram-Schmidt, twice (CGS2): per pass one block sum of the jc + 1 dot
-        // products w.V_i (each thread's terms reduced by shuffles as they are formed) and one
-        // cluster sum; the Hessenberg column accumulates in shared memory
-        double wj = real ? wv[j] : 0.0;
+        // products w.V_i and one cluster sum; the Hessenberg column accumulates in shared
+        // memory, the vector being orthogonalised stays in shared memory
+        sm.wvec[t] = real ? wv[j] : 0.0;
         if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
+        __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-          const int lane = t & 31, wid = t >> 5;
-#pragma unroll
-          for (int i = 0; i < kMaxRestart; ++i) {
-            if (i > jc) break;
-            double p = (real ? Vi(i)[j] : 0.0) * wj;
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == 0) sm.red[wid][i] = p;
-          }
-          __syncthreads();
-          if (t <= jc) {
-            double tq = 0.0;
-            for (int w2 = 0; w2 < kFW; ++w2) tq += sm.red[w2][t];
-            sm.sums[t] = tq;
-          }
-          __syncthreads();
+          f_slice_sums<kMaxRestart, false>(sm, jc + 1, [&](int i, int c) {
+            return G.c0 + c < N ? sm.wvec[c] * Vi(i)[G.c0 + c] : 0.0;
+          });
           f_cluster_reduce(sm, cl, par, jc + 1, false);
+          if (real) {
+            double wj = sm.wvec[t];
 #pragma unroll
-          for (int i = 0; i < kMaxRestart; ++i) {
-            if (i > jc) break;
-            if (real) wj -= sm.sums[i] * Vi(i)[j];
+            for (int i = 0; i < kMaxRestart; ++i) {
+              if (i > jc) break;
+              wj -= sm.sums[i] * Vi(i)[j];
+            }
+            sm.wvec[t] = wj;
           }
           if (t <= jc) sm.hc[t] += sm.sums[t];
           __syncthreads();
         }
-        {
-          double l1[1] = {wj * wj};
-          f_block_sums<1>(sm, l1, 1);
-        }
+        f_slice_sums<1, false>(sm, 1, [&](int, int c) { return sm.wvec[c] * sm.wvec[c]; });
         f_cluster_reduce(sm, cl, par, 1, false);
-        const double nrmw = sqrt(sm.sums[0]);
+        if (t == 0) {
+          sm.sc[0] = sqrt(sm.sums[0]);
+          sm.sc[1] = sm.sc[0] > 0.0 ? 1.0 / sm.sc[0] : 0.0;
+        }
+        __syncthreads();
+        const double nrmw = sm.sc[0];
         // Givens rotations and the GMRES residual estimate (thread 0; shared with all)
         if (t == 0) {
           double* hc = sm.hc;
@@ -1045,7 +1052,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
           sm.stop = (est || nrmw == 0.0 || jc + 1 >= m) ? 1 : 0;
         }
-        if (real) wv[j] = wj * (nrmw > 0.0 ? 1.0 / nrmw : 0.0);
+        if (real) wv[j] = sm.wvec[t] * sm.sc[1];
         __syncthreads();
         ++its;
         kk = jc + 1;

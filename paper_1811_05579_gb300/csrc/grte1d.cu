@@ -79,6 +79,7 @@ struct CellCoef {
 struct CellF {
   float *A, *gl, *gu, *gb, *od, *dlx, *kcd, *kdx, *ratio, *ralpha, *alpha;
   float *kcde, *kdxe, *dlxe;    // kcd/eps, kdx/eps, dlx*eps (correction substep 2)
+  float *fR, *fL, *gbx;         // rho-part flux coefficients (fused Krylov passes)
   float *P1, *P2, *P3, *Frho;   // per-cell parts of a prediction pass
   float *Q1, *Q2, *gU;          // per-cell parts of correction substep 2
 };
@@ -218,6 +219,9 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
     f.kcde[gid] = (float)(D.cf.kcd[gid] * I.inv_eps);
     f.kdxe[gid] = (float)(D.cf.kdx[gid] * I.inv_eps);
     f.dlxe[gid] = (float)(D.cf.dlx[gid] * I.eps);
+    f.fR[gid] = (float)D.cf.fR[gid];
+    f.fL[gid] = (float)D.cf.fL[gid];
+    f.gbx[gid] = (float)D.cf.gbx[gid];
   }
 }
 
@@ -1755,7 +1759,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     AL(f.A, nc); AL(f.gl, nc); AL(f.gu, nc); AL(f.gb, nc); AL(f.od, nc); AL(f.dlx, nc); AL(f.kcd, nc);
     AL(f.kdx, nc); AL(f.ratio, nc); AL(f.ralpha, nc); AL(f.alpha, nc); AL(f.kcde, nc); AL(f.kdxe, nc);
     AL(f.dlxe, nc); AL(f.P1, nc); AL(f.P2, nc); AL(f.P3, nc); AL(f.Frho, nc); AL(f.Q1, nc); AL(f.Q2, nc);
-    AL(f.gU, nc);
+    AL(f.gU, nc); AL(f.fR, nc); AL(f.fL, nc); AL(f.gbx, nc);
   }
   {
     char* p_;
