@@ -68,7 +68,7 @@ struct FSmem {
   double ik1[5][32], ik2[5][32], iib[32];
   double pS[4], paf, pcl;
   float wgt[kFS];                                       // stopping-test weights
-  double wvec[kFS];                                     // the Arnoldi vector being orthogonalised
+  double zv[kFS];                                       // preconditioner input (slice)
   double sc[4];                                         // scalars computed once (thread 0)
   double wall[2][32];                                   // wall-row right-hand sides (double)
   double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
@@ -410,8 +410,23 @@ __device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
 //   P1 = -alpha x (+ (s a c + kappa a c/(c dt)) U^n on data passes), P2 = Gint x, P3 = gb x,
 //   fl = Frho = wv2 [fR (x_j - x_{j+1}) + fL (x_j - x_{j-1})] + wv gbx x_j
 //        (data passes: minus 2/eps sum_k w_k v_k b at the inflow walls).
+// X: the per-cell vector.  Data passes: the iterate, an instance-local global vector.
+// Krylov passes: a direction, slice-local in shared memory, whose values at the two
+// neighbouring cells are read from the neighbouring CTAs (distributed shared memory).
+struct FVec {
+  const double* p;   // FULL: instance-local global; HOM: slice-local shared
+  double left, right;   // HOM: the values at c0 - 1 and c0 + kFS
+};
+
 template <bool FULL>
-__device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const double* xg) {
+__device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
+  if (FULL) return X.p[j];
+  const int64_t t = j - G.c0;
+  return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
+}
+
+template <bool FULL>
+__device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const FVec& X) {
   const int t = threadIdx.x;
   const int64_t j = G.c0 + t;
   const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == G.N - 1);
@@ -419,7 +434,8 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     // a Krylov direction's parts are used in binary32: formed in binary32 (the binary64
     // pipe is the scarce one) from the direction and the binary32 coefficient copies
     const int64_t g = G.co + j, N = G.N;
-    const float xj = (float)xg[j], xl = j > 0 ? (float)xg[j - 1] : 0.0f, xr = j < N - 1 ? (float)xg[j + 1] : 0.0f;
+    const float xj = (float)f_x<FULL>(X, G, j), xl = j > 0 ? (float)f_x<FULL>(X, G, j - 1) : 0.0f,
+                xr = j < N - 1 ? (float)f_x<FULL>(X, G, j + 1) : 0.0f;
     const float gl = sm.gl[t + 1], gu = sm.gu[t + 1];
     sm.P1[t] = -D.fc.alpha[g] * xj;
     sm.P2[t] = gl * (xj - xl) + gu * (xj - xr);
@@ -430,7 +446,8 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
   }
   if (j < G.N) {
     const int64_t g = G.co + j, N = G.N;
-    const double xj = xg[j], xl = j > 0 ? xg[j - 1] : 0.0, xr = j < N - 1 ? xg[j + 1] : 0.0;
+    const double xj = f_x<FULL>(X, G, j), xl = j > 0 ? f_x<FULL>(X, G, j - 1) : 0.0,
+                 xr = j < N - 1 ? f_x<FULL>(X, G, j + 1) : 0.0;
     double p1 = -D.cf.alpha[g] * xj;
     if (FULL) p1 += (D.cf.sac[g] + D.cf.kcd[g] * I.a * I.c) * D.U[g];
     const double p2 = D.cf.gl[g] * (xj - xl) + D.cf.gu[g] * (xj - xr);
@@ -515,10 +532,11 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
 //   P1 - v^2 P2 + kappa v (2/eps)(b - x)/dx  [+ kappa/(c dt) Eh^n - kappa v o/dx on data passes,
 //   o = 2 o_1 (left) or -2 o_{N-1} (right)] (the O(eps) difference is formed in double).
 template <bool FULL>
-__device__ double f_wall_rhs(const Dev& D, const Inst& I, const FGeo& G, const double* xg, int64_t j, int k) {
+__device__ double f_wall_rhs(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t j, int k) {
   const int64_t N = G.N, g = G.co + j;
   const double v = D.v[I.ang_off + k], v2 = v * v;
-  const double xj = xg[j], xl = j > 0 ? xg[j - 1] : 0.0, xr = j < N - 1 ? xg[j + 1] : 0.0;
+  const double xj = f_x<FULL>(X, G, j), xl = j > 0 ? f_x<FULL>(X, G, j - 1) : 0.0,
+               xr = j < N - 1 ? f_x<FULL>(X, G, j + 1) : 0.0;
   double p1 = -D.cf.alpha[g] * xj;
   if (FULL) p1 += (D.cf.sac[g] + D.cf.kcd[g] * I.a * I.c) * D.U[g];
   const double p2 = D.cf.gl[g] * (xj - xl) + D.cf.gu[g] * (xj - xr);
@@ -543,9 +561,15 @@ template <bool FULL>
 __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
                        const double* xg, int& par, bool stage = false) {
   cl.sync();   // xg complete on every slice (halo reads)
+  FVec X{xg, 0.0, 0.0};
+  if (!FULL) {
+    // the direction's values next to the slice, from the neighbouring CTAs' shared memory
+    if (G.q > 0) X.left = cl.map_shared_rank(const_cast<double*>(xg), G.q - 1)[kFS - 1];
+    if (G.q < G.Q - 1) X.right = cl.map_shared_rank(const_cast<double*>(xg), G.q + 1)[0];
+  }
   const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t N = G.N;
-  f_cellparts<FULL>(sm, D, I, G, xg);
+  f_cellparts<FULL>(sm, D, I, G, X);
   if (FULL) f_stage_data(sm, D, I, G, stage);
   __syncthreads();
   const bool inflow = I.bc == GRTE_BC_INFLOW;
@@ -564,7 +588,7 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const int64_t jw = side == 0 ? 0 : N - 1;
       const int64_t tl = jw - G.c0;
       if (tl >= 0 && tl < kFS && (int)(tl / kFL) == w) {
-        const double r = f_wall_rhs<FULL>(D, I, G, xg, jw, k);
+        const double r = f_wall_rhs<FULL>(D, I, G, X, jw, k);
         sm.wall[side][k] = r;
         sm.x[tl][k] = (float)r;
       }
@@ -802,7 +826,7 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
 }
 
 // z = P^{-1} rin on the slice with the factors of f_prec_factor (binary64).  rin and z:
-// instance-local global vectors (own slice).
+// slice-local vectors in shared memory (cell c0 + t at index t).
 __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
                        const double* rin, double* z, int& par) {
   const int64_t N = G.N, co = G.co;
@@ -814,7 +838,7 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
 #pragma unroll
     for (int u = 0; u < kFPL; ++u) {
       const int64_t j = s + u;
-      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[j] : 0.0;
+      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[lane * kFPL + u] : 0.0;
     }
     double rh = 0.0;
 #pragma unroll
@@ -890,7 +914,9 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
       const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
       const double Gu = I.wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + I.wv * D.cf.gb[g] * uj;
-      z[j] = (rin[j] - Gu) * D.cf.ralpha[g];
+      z[t] = (rin[t] - Gu) * D.cf.ralpha[g];
+    } else {
+      z[t] = 0.0;
     }
   }
   __syncthreads();
@@ -917,10 +943,11 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   const int64_t j = G.c0 + t;
   const bool real = j < N;
   const int m = D.m;
-  const int64_t vstride = D.gz - D.gx;
   double* x = D.gx + co;
-  double* z = D.gz + co;
-  auto Vi = [&](int i) { return D.gV + (int64_t)i * vstride + co; };
+  // the slice's Krylov basis V_0..V_m in shared memory after the struct (cell c0 + t at t)
+  double* Vs = reinterpret_cast<double*>(fdsm + sizeof(FSmem));
+  auto Vi = [&](int i) { return Vs + (int64_t)i * kFS; };
+  double* zv = sm.zv;
   int par = 0;
   f_load_cells(sm, D, I, G);
   f_prec_factor(sm, cl, D, I, G, par);
@@ -934,8 +961,10 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       const int64_t g = co + j;
       const double fl = sm.fl[t];
       const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
-      z[j] = -R;
+      zv[t] = -R;
       D.Fs[g] = fl;
+    } else {
+      zv[t] = 0.0;
     }
     f_slice_sums<1, true>(sm, 1, [&](int, int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
     f_cluster_reduce(sm, cl, par, 1, true);
@@ -943,11 +972,11 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
     sm.wgt[t] = real ? 1.0f / (float)(fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0f;
     __syncthreads();
     double* v0 = Vi(0);
-    f_prec(sm, cl, D, I, G, z, v0, par);
+    f_prec(sm, cl, D, I, G, zv, v0, par);
     {
       f_slice_sums<2, false>(sm, 2, [&](int i, int c) {
         if (G.c0 + c >= N) return 0.0;
-        const double a = i == 0 ? v0[G.c0 + c] : x[G.c0 + c];
+        const double a = i == 0 ? v0[c] : x[G.c0 + c];
         return a * a;
       });
       f_cluster_reduce(sm, cl, par, 2, false);
@@ -958,9 +987,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       }
       __syncthreads();
       const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2];
-      f_slice_sums<1, true>(sm, 1, [&](int, int c) {
-        return G.c0 + c < N ? fabs(v0[G.c0 + c]) * (double)sm.wgt[c] : 0.0;
-      });
+      f_slice_sums<1, true>(sm, 1, [&](int, int c) { return fabs(v0[c]) * (double)sm.wgt[c]; });
       f_cluster_reduce(sm, cl, par, 1, true);
       const double rinf_c = sm.sums[0];
       __syncthreads();
@@ -984,7 +1011,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         sm.g[0] = nrm;
         for (int i = 1; i <= m; ++i) sm.g[i] = 0.0;
       }
-      if (real) v0[j] *= inv_nrm;
+      v0[t] *= inv_nrm;
       __syncthreads();
       int kk = 0;
       for (int jc = 0; jc < m; ++jc) {
@@ -993,35 +1020,34 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         // C v_j = alpha v_j + kappa/dx F(v_j), preconditioned into V_{j+1}
         if (real) {
           const int64_t g = co + j;
-          z[j] = D.cf.alpha[g] * vj[j] + D.cf.kdx[g] * sm.fl[t];
+          zv[t] = D.cf.alpha[g] * vj[t] + D.cf.kdx[g] * sm.fl[t];
+        } else {
+          zv[t] = 0.0;
         }
         __syncthreads();
         double* wv = Vi(jc + 1);
-        f_prec(sm, cl, D, I, G, z, wv, par);
+        f_prec(sm, cl, D, I, G, zv, wv, par);
         // classical Gram-Schmidt, twice (CGS2): per pass one block sum of the jc + 1 dot
         // products w.V_i and one cluster sum; the Hessenberg column accumulates in shared
-        // memory, the vector being orthogonalised stays in shared memory
-        sm.wvec[t] = real ? wv[j] : 0.0;
+        // memory
         if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-          f_slice_sums<kMaxRestart, false>(sm, jc + 1, [&](int i, int c) {
-            return G.c0 + c < N ? sm.wvec[c] * Vi(i)[G.c0 + c] : 0.0;
-          });
+          f_slice_sums<kMaxRestart, false>(sm, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; });
           f_cluster_reduce(sm, cl, par, jc + 1, false);
-          if (real) {
-            double wj = sm.wvec[t];
+          {
+            double wj = wv[t];
 #pragma unroll
             for (int i = 0; i < kMaxRestart; ++i) {
               if (i > jc) break;
-              wj -= sm.sums[i] * Vi(i)[j];
+              wj -= sm.sums[i] * Vi(i)[t];
             }
-            sm.wvec[t] = wj;
+            wv[t] = wj;
           }
           if (t <= jc) sm.hc[t] += sm.sums[t];
           __syncthreads();
         }
-        f_slice_sums<1, false>(sm, 1, [&](int, int c) { return sm.wvec[c] * sm.wvec[c]; });
+        f_slice_sums<1, false>(sm, 1, [&](int, int c) { return wv[c] * wv[c]; });
         f_cluster_reduce(sm, cl, par, 1, false);
         if (t == 0) {
           sm.sc[0] = sqrt(sm.sums[0]);
@@ -1052,7 +1078,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
           sm.stop = (est || nrmw == 0.0 || jc + 1 >= m) ? 1 : 0;
         }
-        if (real) wv[j] = sm.wvec[t] * sm.sc[1];
+        wv[t] *= sm.sc[1];
         __syncthreads();
         ++its;
         kk = jc + 1;
@@ -1072,7 +1098,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
 #pragma unroll
         for (int i = 0; i < kMaxRestart; ++i) {
           if (i >= kk) break;
-          tq += sm.y[i] * Vi(i)[j];
+          tq += sm.y[i] * Vi(i)[t];
         }
         x[j] = tq;
       }

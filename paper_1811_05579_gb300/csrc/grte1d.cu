@@ -1449,23 +1449,32 @@ static bool fused_fits(const Inst& I) { return I.N >= 64 && I.N <= (int64_t)kFQ 
 
 // Kernel attributes of the fused solve (once per device): its shared memory and the
 // non-portable cluster size 16.
+// Dynamic shared memory of the fused kernel: the struct and the slice's Krylov basis
+// V_0..V_m (m = restart length).
+static size_t fused_smem(int m) { return sizeof(FSmem) + (size_t)(m + 1) * kFS * sizeof(double); }
+static int g_fused_optin = 0;   // the device's opt-in shared memory per block
+
 static cudaError_t fused_attrs() {
   static bool done[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute((const void*)k_pred_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FSmem));
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_pred_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_pred_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) g_fused_optin = optin;
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
 
-static void fused_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int Qc, int nclusters, cudaStream_t st) {
+static void fused_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int Qc, int nclusters, int m,
+                         cudaStream_t st) {
   cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3((unsigned)(nclusters * Qc), 1, 1);
   cfg.blockDim = dim3(kFT, 1, 1);
-  cfg.dynamicSmemBytes = sizeof(FSmem);
+  cfg.dynamicSmemBytes = fused_smem(m);
   cfg.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = (unsigned)Qc;
@@ -1476,10 +1485,10 @@ static void fused_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int Q
 }
 
 // 1 if a cluster of Qc CTAs of the fused kernel can be resident on this device.
-static cudaError_t fused_schedulable(int Qc, bool* ok) {
+static cudaError_t fused_schedulable(int Qc, int m, bool* ok) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];
-  fused_config(cfg, at, Qc, 1, nullptr);
+  fused_config(cfg, at, Qc, 1, m, nullptr);
   int n = 0;
   cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)k_pred_fused, &cfg);
   *ok = e == cudaSuccess && n >= 1;
@@ -1489,7 +1498,7 @@ static cudaError_t fused_schedulable(int Qc, bool* ok) {
 static cudaError_t fused_launch(grte_ctx* h, int c) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];
-  fused_config(cfg, at, 1 << c, h->fcnt[c], h->stream);
+  fused_config(cfg, at, 1 << c, h->fcnt[c], h->D.m, h->stream);
   return cudaLaunchKernelEx(&cfg, k_pred_fused, h->D, (const int*)(h->d_finst + h->foff[c]));
 }
 
@@ -1824,13 +1833,14 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   if (mixed && h->opt.solver1d == GRTE_SOLVER_AUTO) {
     bool ok = std::all_of(h->inst.begin(), h->inst.end(), [](const Inst& I) { return fused_fits(I); });
     if (ok) CK(fused_attrs());
+    ok = ok && fused_smem(m) <= (size_t)g_fused_optin;
     std::vector<std::vector<int>> cls(5);
     if (ok)
       for (int i = 0; i < n_inst; ++i) cls[fused_class(h->inst[i].N)].push_back(i);
     for (int c = 0; c < 5 && ok; ++c) {
       if (cls[c].empty()) continue;
       bool sched = false;
-      CK(fused_schedulable(1 << c, &sched));
+      CK(fused_schedulable(1 << c, m, &sched));
       ok = sched;
     }
     if (ok) {
