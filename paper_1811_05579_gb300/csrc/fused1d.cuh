@@ -59,25 +59,25 @@ struct FSmem {
   double vkd[32], wvkd[32];
   double fl[kFS];                                       // flux sums of the last pass
   double fdat[kFS];                                     // data part of the flux (data passes)
-  float pu[kFS];                                        // preconditioner solution (slice)
+  double pu[kFS];                                       // preconditioner solution (slice)
   // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
   // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
-  float pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
-  float pcs[32], pae[32];
-  float pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
-  float ik1[5][32], ik2[5][32], iib[32];
-  float pS[4], paf, pcl;
+  double pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
+  double pcs[32], pae[32];
+  double pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
+  double ik1[5][32], ik2[5][32], iib[32];
+  double pS[4], paf, pcl;
   float wgt[kFS];                                       // stopping-test weights
-  float zv[kFS];                                        // preconditioner input (slice)
+  double zv[kFS];                                       // preconditioner input (slice)
   double sc[4];                                         // scalars computed once (thread 0)
   double wall[2][32];                                   // wall-row right-hand sides (double)
   double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
   double part[2][kMaxRestart + 2];                      // cluster partials (double-buffered)
   double sums[kMaxRestart + 2];
   // binary64 preconditioner: reduced rows of the 32 lane chunks (64 rows), interface
-  float pe[2][6];                                       // published: S11 S12 S21 S22 r'F r'L
-  float pcoup[2][2];
-  float pxl[2];
+  double pe[2][6];                                      // published: S11 S12 S21 S22 r'F r'L
+  double pcoup[2][2];
+  double pxl[2];
   // GMRES state (identical in every CTA)
   double H[(kMaxRestart + 1) * kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart],
       y[kMaxRestart], hc[kMaxRestart + 2];
@@ -96,7 +96,7 @@ struct FGeo {
 // additions are the scarce resource: 8x fewer than a tree over 512 threads).  Result in
 // sm.sums[0..nv-1]; every thread takes part in the barriers.
 constexpr int kGT = 64;
-template <int NV, bool MAX, typename T = double, class F>
+template <int NV, bool MAX, class F>
 __device__ __forceinline__ void f_slice_sums(FSmem& sm, int nv, F term) {
   const int t = threadIdx.x;
   if (t < kGT) {
@@ -104,17 +104,17 @@ __device__ __forceinline__ void f_slice_sums(FSmem& sm, int nv, F term) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       if (i >= nv) break;
-      T a = T(0);
+      double a = 0.0;
 #pragma unroll
       for (int c = 0; c < kFS / kGT; ++c) {
-        const T v = term(i, t + c * kGT);
+        const double v = term(i, t + c * kGT);
         a = MAX ? fmax(a, v) : a + v;
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const T b = __shfl_xor_sync(0xffffffffu, a, o);
+        const double b = __shfl_xor_sync(0xffffffffu, a, o);
         a = MAX ? fmax(a, b) : a + b;
       }
-      if (lane == 0) sm.red[wid][i] = (double)a;
+      if (lane == 0) sm.red[wid][i] = a;
     }
   }
   __syncthreads();
@@ -414,16 +414,15 @@ __device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
 // Krylov passes: a direction, slice-local in shared memory, whose values at the two
 // neighbouring cells are read from the neighbouring CTAs (distributed shared memory).
 struct FVec {
-  const double* p;      // FULL: the iterate, instance-local global (binary64)
-  const float* pf;      // HOM: the direction, slice-local shared (binary32)
-  float left, right;    // HOM: the direction's values at c0 - 1 and c0 + kFS
+  const double* p;   // FULL: instance-local global; HOM: slice-local shared
+  double left, right;   // HOM: the values at c0 - 1 and c0 + kFS
 };
 
 template <bool FULL>
 __device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
   if (FULL) return X.p[j];
   const int64_t t = j - G.c0;
-  return (double)(t < 0 ? X.left : (t >= kFS ? X.right : X.pf[t]));
+  return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
 }
 
 template <bool FULL>
@@ -560,13 +559,13 @@ __device__ double f_wall_rhs(const Dev& D, const Inst& I, const FGeo& G, const F
 // precedes the call inside).
 template <bool FULL>
 __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
-                       const double* xg, const float* vg, int& par, bool stage = false) {
-  cl.sync();   // the vector complete on every slice (halo reads)
-  FVec X{xg, vg, 0.0f, 0.0f};
+                       const double* xg, int& par, bool stage = false) {
+  cl.sync();   // xg complete on every slice (halo reads)
+  FVec X{xg, 0.0, 0.0};
   if (!FULL) {
     // the direction's values next to the slice, from the neighbouring CTAs' shared memory
-    if (G.q > 0) X.left = cl.map_shared_rank(const_cast<float*>(vg), G.q - 1)[kFS - 1];
-    if (G.q < G.Q - 1) X.right = cl.map_shared_rank(const_cast<float*>(vg), G.q + 1)[0];
+    if (G.q > 0) X.left = cl.map_shared_rank(const_cast<double*>(xg), G.q - 1)[kFS - 1];
+    if (G.q < G.Q - 1) X.right = cl.map_shared_rank(const_cast<double*>(xg), G.q + 1)[0];
   }
   const int k = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t N = G.N;
@@ -670,33 +669,31 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   __syncthreads();
 }
 
-// Right-hand side of row i of a 64-row system held two rows per lane of warp 0 (rows
-// 2 lane and 2 lane + 1 in v0, v1).
-__device__ __forceinline__ float f_row(float v0, float v1, int i) {
+// Right-hand side of row il (and row ir) of a 64-row system held two rows per lane of
+// warp 0 (rows 2 lane, 2 lane + 1 in v0, v1).
+__device__ __forceinline__ double f_row(double v0, double v1, int i) {
   const int src = (i < 0 ? 0 : (i > 63 ? 63 : i));
-  const float a = __shfl_sync(0xffffffffu, v0, src >> 1), b = __shfl_sync(0xffffffffu, v1, src >> 1);
+  const double a = __shfl_sync(0xffffffffu, v0, src >> 1), b = __shfl_sync(0xffffffffu, v1, src >> 1);
   return (src & 1) ? b : a;
 }
 
-// The single-effective-angle Schur operator of the preconditioner:
+// The single-effective-angle Schur operator of the preconditioner (binary64):
 //   P = alpha + Gbar (A + Gbar)^{-1} beta, applied as  u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) r,
-//   z = (r - Gbar u)/alpha,  Gbar = sum_k w_k G_k, beta = A - alpha,
-// in binary32 (it belongs to the Krylov cycle, whose accuracy the binary64 restarts set).
+//   z = (r - Gbar u)/alpha,  Gbar = sum_k w_k G_k, beta = A - alpha.
 // The tridiagonal matrix T = A + (A/alpha) Gbar is the same for every application of a solve:
 // f_prec_factor eliminates it once (warp 0 of each CTA, 32 lanes x 16 cells: chunk sweeps,
 // PCR of the 64 chunk-end rows with its two unit spikes, the slice's 2x2 Schur complement,
-// and in every CTA the PCR multipliers of the 2Q-row interface system); f_prec then
+// and in every CTA the PCR multipliers of the 2Q-row interface system); f_prec_apply then
 // solves with the stored factors, without divisions.
-__device__ __forceinline__ void f_prec_coef(const Dev& D, const Inst& I, const FGeo& G, int64_t j, float& a,
-                                            float& b, float& c) {
-  if (j >= G.N) { a = 0.0f; b = 1.0f; c = 0.0f; return; }
+__device__ void f_prec_coef(const Dev& D, const Inst& I, const FGeo& G, int64_t j, double& a, double& b,
+                            double& c) {
+  if (j >= G.N) { a = 0.0; b = 1.0; c = 0.0; return; }
   const int64_t g = G.co + j;
-  const float f = D.fc.A[g] * D.fc.ralpha[g];
-  const float l = D.fc.gl[g], u = D.fc.gu[g];
-  const float wv = (float)I.wv, wv2 = (float)I.wv2;
-  a = j > 0 ? -f * wv2 * l : 0.0f;
-  c = j < G.N - 1 ? -f * wv2 * u : 0.0f;
-  b = D.fc.A[g] + f * (wv2 * (l + u) + wv * D.fc.gb[g]);
+  const double f = D.cf.A[g] * D.cf.ralpha[g];
+  const double l = D.cf.gl[g], u = D.cf.gu[g];
+  a = j > 0 ? -f * I.wv2 * l : 0.0;
+  c = j < G.N - 1 ? -f * I.wv2 * u : 0.0;
+  b = D.cf.A[g] + f * (I.wv2 * (l + u) + I.wv * D.cf.gb[g]);
 }
 
 __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
@@ -705,13 +702,13 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
   const bool w0 = threadIdx.x < 32;
   if (w0) {
     const int64_t s = G.c0 + lane * kFPL;
-    float chp = 0.0f, ahp = 0.0f;
+    double chp = 0.0, ahp = 0.0;
 #pragma unroll
     for (int u = 1; u <= kFPL - 2; ++u) {
-      float a, b, c;
+      double a, b, c;
       f_prec_coef(D, I, G, s + u, a, b, c);
-      const float den = (u == 1) ? b : fmaf(-a, chp, b);
-      const float inv = 1.0f / den;
+      const double den = (u == 1) ? b : b - a * chp;
+      const double inv = 1.0 / den;
       ahp = ((u == 1) ? a : -a * ahp) * inv;
       chp = c * inv;
       sm.pinv[u][lane] = inv;
@@ -719,47 +716,47 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
       sm.pch[u][lane] = chp;
       sm.pah[u][lane] = ahp;
     }
-    float cc = sm.pch[kFPL - 2][lane], ac = sm.pah[kFPL - 2][lane];
+    double cc = sm.pch[kFPL - 2][lane], ac = sm.pah[kFPL - 2][lane];
 #pragma unroll
     for (int u = kFPL - 3; u >= 1; --u) {
-      const float chu = sm.pch[u][lane];
+      const double chu = sm.pch[u][lane];
       cc = -chu * cc;
-      ac = fmaf(-chu, ac, sm.pah[u][lane]);
+      ac = sm.pah[u][lane] - chu * ac;
     }
-    float as, bs, cs, ae, be, ce;
+    double as, bs, cs, ae, be, ce;
     f_prec_coef(D, I, G, s, as, bs, cs);
     f_prec_coef(D, I, G, s + kFPL - 1, ae, be, ce);
     sm.pcs[lane] = cs;
     sm.pae[lane] = ae;
-    float ra0 = (lane == 0) ? 0.0f : as, rb0 = fmaf(-cs, ac, bs), rc0 = -cs * cc;
-    float ra1 = -ae * sm.pah[kFPL - 2][lane], rb1 = fmaf(-ae, sm.pch[kFPL - 2][lane], be);
-    float rc1 = (lane == 31) ? 0.0f : ce;
-    float g0 = (lane == 0) ? 1.0f : 0.0f, g1 = 0.0f, h0 = 0.0f, h1 = (lane == 31) ? 1.0f : 0.0f;
-    const float af = __shfl_sync(0xffffffffu, as, 0), cl_ = __shfl_sync(0xffffffffu, ce, 31);
+    double ra0 = (lane == 0) ? 0.0 : as, rb0 = bs - cs * ac, rc0 = -cs * cc;
+    double ra1 = -ae * sm.pah[kFPL - 2][lane], rb1 = be - ae * sm.pch[kFPL - 2][lane];
+    double rc1 = (lane == 31) ? 0.0 : ce;
+    double g0 = (lane == 0) ? 1.0 : 0.0, g1 = 0.0, h0 = 0.0, h1 = (lane == 31) ? 1.0 : 0.0;
+    const double af = __shfl_sync(0xffffffffu, as, 0), cl_ = __shfl_sync(0xffffffffu, ce, 31);
     for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
-      float na[2], nb[2], nc[2], ng[2], nh[2];
+      double na[2], nb[2], nc[2], ng[2], nh[2];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int i = 2 * lane + p, il = i - st, ir = i + st;
         const bool hl = il >= 0, hr = ir < 64;
-        const float Lb = f_row(rb0, rb1, il), La = f_row(ra0, ra1, il), Lc = f_row(rc0, rc1, il);
-        const float Lg = f_row(g0, g1, il), Lh = f_row(h0, h1, il);
-        const float Rb = f_row(rb0, rb1, ir), Ra = f_row(ra0, ra1, ir), Rc = f_row(rc0, rc1, ir);
-        const float Rg = f_row(g0, g1, ir), Rh = f_row(h0, h1, ir);
-        const float a = p ? ra1 : ra0, b = p ? rb1 : rb0, c = p ? rc1 : rc0;
-        const float k1 = hl ? a / Lb : 0.0f, k2 = hr ? c / Rb : 0.0f;
+        const double Lb = f_row(rb0, rb1, il), La = f_row(ra0, ra1, il), Lc = f_row(rc0, rc1, il);
+        const double Lg = f_row(g0, g1, il), Lh = f_row(h0, h1, il);
+        const double Rb = f_row(rb0, rb1, ir), Ra = f_row(ra0, ra1, ir), Rc = f_row(rc0, rc1, ir);
+        const double Rg = f_row(g0, g1, ir), Rh = f_row(h0, h1, ir);
+        const double a = p ? ra1 : ra0, b = p ? rb1 : rb0, c = p ? rc1 : rc0;
+        const double k1 = hl ? a / Lb : 0.0, k2 = hr ? c / Rb : 0.0;
         sm.pk1[l][i] = k1;
         sm.pk2[l][i] = k2;
-        na[p] = hl ? -La * k1 : 0.0f;
-        nc[p] = hr ? -Rc * k2 : 0.0f;
-        nb[p] = b - (hl ? Lc * k1 : 0.0f) - (hr ? Ra * k2 : 0.0f);
-        ng[p] = (p ? g1 : g0) - (hl ? Lg * k1 : 0.0f) - (hr ? Rg * k2 : 0.0f);
-        nh[p] = (p ? h1 : h0) - (hl ? Lh * k1 : 0.0f) - (hr ? Rh * k2 : 0.0f);
+        na[p] = hl ? -La * k1 : 0.0;
+        nc[p] = hr ? -Rc * k2 : 0.0;
+        nb[p] = b - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
+        ng[p] = (p ? g1 : g0) - (hl ? Lg * k1 : 0.0) - (hr ? Rg * k2 : 0.0);
+        nh[p] = (p ? h1 : h0) - (hl ? Lh * k1 : 0.0) - (hr ? Rh * k2 : 0.0);
       }
       ra0 = na[0]; ra1 = na[1]; rb0 = nb[0]; rb1 = nb[1]; rc0 = nc[0]; rc1 = nc[1];
       g0 = ng[0]; g1 = ng[1]; h0 = nh[0]; h1 = nh[1];
     }
-    const float i0 = 1.0f / rb0, i1 = 1.0f / rb1;
+    const double i0 = 1.0 / rb0, i1 = 1.0 / rb1;
     sm.pib[2 * lane] = i0;
     sm.pib[2 * lane + 1] = i1;
     g0 *= i0; h0 *= i0; g1 *= i1; h1 *= i1;
@@ -768,10 +765,10 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
     sm.phv[2 * lane] = h0;
     sm.phv[2 * lane + 1] = h1;
     // the slice's 2x2 Schur complement on (first, last): S = Z^{-1}, Z = [[g0, h0], [g63, h63]]
-    const float z00 = __shfl_sync(0xffffffffu, g0, 0), z0n = __shfl_sync(0xffffffffu, h0, 0);
-    const float zn0 = __shfl_sync(0xffffffffu, g1, 31), znn = __shfl_sync(0xffffffffu, h1, 31);
+    const double z00 = __shfl_sync(0xffffffffu, g0, 0), z0n = __shfl_sync(0xffffffffu, h0, 0);
+    const double zn0 = __shfl_sync(0xffffffffu, g1, 31), znn = __shfl_sync(0xffffffffu, h1, 31);
     if (lane == 0) {
-      const float id = 1.0f / (z00 * znn - z0n * zn0);
+      const double id = 1.0 / (z00 * znn - z0n * zn0);
       sm.pS[0] = znn * id;
       sm.pS[1] = -z0n * id;
       sm.pS[2] = -zn0 * id;
@@ -788,79 +785,79 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
     // interface rows [F_0, L_0, F_1, L_1, ...]: a_q L_{q-1} + S11 F_q + S12 L_q (F rows),
     // S21 F_q + S22 L_q + c_q F_{q+1} (L rows); PCR multipliers stored per level
     const int Q = G.Q, n2 = 2 * Q;
-    float ia = 0.0f, ib = 1.0f, ic = 0.0f;
+    double ia = 0.0, ib = 1.0, ic = 0.0;
     if (lane < n2) {
       const int qq = lane >> 1;
-      const float* pe = cl.map_shared_rank(&sm.pe[par][0], qq);
-      const float* pc = cl.map_shared_rank(&sm.pcoup[par][0], qq);
+      const double* pe = cl.map_shared_rank(&sm.pe[par][0], qq);
+      const double* pc = cl.map_shared_rank(&sm.pcoup[par][0], qq);
       if ((lane & 1) == 0) {
-        ia = qq > 0 ? pc[0] : 0.0f;
+        ia = qq > 0 ? pc[0] : 0.0;
         ib = pe[0];
         ic = pe[1];
       } else {
         ia = pe[2];
         ib = pe[3];
-        ic = qq < Q - 1 ? pc[1] : 0.0f;
+        ic = qq < Q - 1 ? pc[1] : 0.0;
       }
     }
     for (int l = 0, st = 1; st < n2; ++l, st <<= 1) {
       const int il = lane - st, irr = lane + st;
       const int sl = il >= 0 ? il : 0, sr = irr < n2 ? irr : 0;
-      const float Lb = __shfl_sync(0xffffffffu, ib, sl), La = __shfl_sync(0xffffffffu, ia, sl);
-      const float Lc = __shfl_sync(0xffffffffu, ic, sl);
-      const float Rb = __shfl_sync(0xffffffffu, ib, sr), Ra = __shfl_sync(0xffffffffu, ia, sr);
-      const float Rc = __shfl_sync(0xffffffffu, ic, sr);
+      const double Lb = __shfl_sync(0xffffffffu, ib, sl), La = __shfl_sync(0xffffffffu, ia, sl);
+      const double Lc = __shfl_sync(0xffffffffu, ic, sl);
+      const double Rb = __shfl_sync(0xffffffffu, ib, sr), Ra = __shfl_sync(0xffffffffu, ia, sr);
+      const double Rc = __shfl_sync(0xffffffffu, ic, sr);
       const bool hl = il >= 0, hr = irr < n2;
-      const float k1 = hl ? ia / Lb : 0.0f, k2 = hr ? ic / Rb : 0.0f;
+      const double k1 = hl ? ia / Lb : 0.0, k2 = hr ? ic / Rb : 0.0;
       if (lane < n2) {
         sm.ik1[l][lane] = k1;
         sm.ik2[l][lane] = k2;
-        const float na = hl ? -La * k1 : 0.0f, nc = hr ? -Rc * k2 : 0.0f;
-        const float nb = ib - (hl ? Lc * k1 : 0.0f) - (hr ? Ra * k2 : 0.0f);
+        const double na = hl ? -La * k1 : 0.0, nc = hr ? -Rc * k2 : 0.0;
+        const double nb = ib - (hl ? Lc * k1 : 0.0) - (hr ? Ra * k2 : 0.0);
         ia = na;
         ib = nb;
         ic = nc;
       }
     }
-    sm.iib[lane] = (lane < n2) ? 1.0f / ib : 0.0f;
+    sm.iib[lane] = (lane < n2) ? 1.0 / ib : 0.0;
   }
   par ^= 1;
   __syncthreads();
 }
 
-// z = P^{-1} rin on the slice with the factors of f_prec_factor.  rin and z: slice-local
-// binary32 vectors in shared memory (cell c0 + t at index t).
+// z = P^{-1} rin on the slice with the factors of f_prec_factor (binary64).  rin and z:
+// slice-local vectors in shared memory (cell c0 + t at index t).
 __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
-                       const float* rin, float* z, int& par) {
+                       const double* rin, double* z, int& par) {
   const int64_t N = G.N, co = G.co;
   const int lane = threadIdx.x & 31;
   const bool w0 = threadIdx.x < 32;
-  float y0 = 0.0f, y1 = 0.0f;
+  double y0 = 0.0, y1 = 0.0, rh14 = 0.0;
   if (w0) {
     const int64_t s = G.c0 + lane * kFPL;
 #pragma unroll
     for (int u = 0; u < kFPL; ++u) {
       const int64_t j = s + u;
-      sm.pxr[u][lane] = (j < N) ? D.fc.ratio[co + j] * rin[lane * kFPL + u] : 0.0f;
+      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[lane * kFPL + u] : 0.0;
     }
-    float rh = 0.0f;
+    double rh = 0.0;
 #pragma unroll
     for (int u = 1; u <= kFPL - 2; ++u) {
-      const float xu = sm.pxr[u][lane];
-      rh = (u == 1 ? xu : fmaf(-sm.pa[u][lane], rh, xu)) * sm.pinv[u][lane];
+      const double xu = sm.pxr[u][lane];
+      rh = (u == 1 ? xu : xu - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
       sm.pxr[u][lane] = rh;
     }
-    const float rh14 = rh;
-    float rc = rh;
+    rh14 = rh;
+    double rc = rh;
 #pragma unroll
-    for (int u = kFPL - 3; u >= 1; --u) rc = fmaf(-sm.pch[u][lane], rc, sm.pxr[u][lane]);
-    float r0 = fmaf(-sm.pcs[lane], rc, sm.pxr[0][lane]), r1 = fmaf(-sm.pae[lane], rh14, sm.pxr[kFPL - 1][lane]);
+    for (int u = kFPL - 3; u >= 1; --u) rc = sm.pxr[u][lane] - sm.pch[u][lane] * rc;
+    double r0 = sm.pxr[0][lane] - sm.pcs[lane] * rc, r1 = sm.pxr[kFPL - 1][lane] - sm.pae[lane] * rh14;
     for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
-      float nr[2];
+      double nr[2];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int i = 2 * lane + p;
-        const float Lr = f_row(r0, r1, i - st), Rr = f_row(r0, r1, i + st);
+        const double Lr = f_row(r0, r1, i - st), Rr = f_row(r0, r1, i + st);
         nr[p] = (p ? r1 : r0) - sm.pk1[l][i] * Lr - sm.pk2[l][i] * Rr;
       }
       r0 = nr[0];
@@ -868,7 +865,7 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     }
     y0 = r0 * sm.pib[2 * lane];
     y1 = r1 * sm.pib[2 * lane + 1];
-    const float ya = __shfl_sync(0xffffffffu, y0, 0), yb = __shfl_sync(0xffffffffu, y1, 31);
+    const double ya = __shfl_sync(0xffffffffu, y0, 0), yb = __shfl_sync(0xffffffffu, y1, 31);
     if (lane == 0) {
       sm.pe[par][4] = sm.pS[0] * ya + sm.pS[1] * yb;
       sm.pe[par][5] = sm.pS[2] * ya + sm.pS[3] * yb;
@@ -877,24 +874,24 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   cl.sync();   // every slice's reduced right-hand side published
   if (w0) {
     const int Q = G.Q, n2 = 2 * Q;
-    float ir = 0.0f;
+    double ir = 0.0;
     if (lane < n2) ir = cl.map_shared_rank(&sm.pe[par][0], lane >> 1)[4 + (lane & 1)];
     for (int l = 0, st = 1; st < n2; ++l, st <<= 1) {
       const int il = lane - st, irr = lane + st;
-      const float Lr = __shfl_sync(0xffffffffu, ir, il >= 0 ? il : 0);
-      const float Rr = __shfl_sync(0xffffffffu, ir, irr < n2 ? irr : 0);
+      const double Lr = __shfl_sync(0xffffffffu, ir, il >= 0 ? il : 0);
+      const double Rr = __shfl_sync(0xffffffffu, ir, irr < n2 ? irr : 0);
       if (lane < n2) ir = ir - sm.ik1[l][lane] * Lr - sm.ik2[l][lane] * Rr;
     }
-    const float X = ir * sm.iib[lane];
+    const double X = ir * sm.iib[lane];
     const int sLp = G.q > 0 ? 2 * G.q - 1 : 0, sFn = G.q < Q - 1 ? 2 * G.q + 2 : 0;
-    const float XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
-    const float Lp = G.q > 0 ? XL : 0.0f, Fn = G.q < Q - 1 ? XF : 0.0f;
-    const float la = Lp * sm.paf, fc = Fn * sm.pcl;
-    const float xs = y0 - la * sm.pgv[2 * lane] - fc * sm.phv[2 * lane];
-    const float xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
+    const double XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
+    const double Lp = G.q > 0 ? XL : 0.0, Fn = G.q < Q - 1 ? XF : 0.0;
+    const double la = Lp * sm.paf, fc = Fn * sm.pcl;
+    const double xs = y0 - la * sm.pgv[2 * lane] - fc * sm.phv[2 * lane];
+    const double xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
     sm.pu[lane * kFPL] = xs;
     sm.pu[lane * kFPL + kFPL - 1] = xe;
-    float xn = xe;
+    double xn = xe;
 #pragma unroll
     for (int u = kFPL - 2; u >= 1; --u) {
       xn = sm.pxr[u][lane] - sm.pch[u][lane] * xn - sm.pah[u][lane] * xs;
@@ -913,14 +910,13 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     const int64_t j = G.c0 + t;
     if (j < N) {
       const int64_t g = co + j;
-      const float uj = sm.pu[t];
-      const float uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0f;
-      const float uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0f;
-      const float Gu = (float)I.wv2 * (sm.gl[t + 1] * (uj - uL) + sm.gu[t + 1] * (uj - uR)) +
-                       (float)I.wv * sm.gb[t + 1] * uj;
-      z[t] = (rin[t] - Gu) * D.fc.ralpha[g];
+      const double uj = sm.pu[t];
+      const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
+      const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
+      const double Gu = I.wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + I.wv * D.cf.gb[g] * uj;
+      z[t] = (rin[t] - Gu) * D.cf.ralpha[g];
     } else {
-      z[t] = 0.0f;
+      z[t] = 0.0;
     }
   }
   __syncthreads();
@@ -948,11 +944,10 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   const bool real = j < N;
   const int m = D.m;
   double* x = D.gx + co;
-  // the slice's Krylov basis V_0..V_m (binary32) in shared memory after the struct (cell
-  // c0 + t at index t)
-  float* Vs = reinterpret_cast<float*>(fdsm + sizeof(FSmem));
+  // the slice's Krylov basis V_0..V_m in shared memory after the struct (cell c0 + t at t)
+  double* Vs = reinterpret_cast<double*>(fdsm + sizeof(FSmem));
   auto Vi = [&](int i) { return Vs + (int64_t)i * kFS; };
-  float* zv = sm.zv;
+  double* zv = sm.zv;
   int par = 0;
   f_load_cells(sm, D, I, G);
   f_prec_factor(sm, cl, D, I, G, par);
@@ -961,27 +956,27 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   bool first = true;
   for (;;) {
     // ---- restart: true residual at x, preconditioned, stopping test --------------------
-    f_pass<true>(sm, cl, D, I, G, x, nullptr, par, first);
+    f_pass<true>(sm, cl, D, I, G, x, par, first);
     if (real) {
       const int64_t g = co + j;
       const double fl = sm.fl[t];
       const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
-      zv[t] = (float)(-R);
+      zv[t] = -R;
       D.Fs[g] = fl;
     } else {
-      zv[t] = 0.0f;
+      zv[t] = 0.0;
     }
     f_slice_sums<1, true>(sm, 1, [&](int, int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
     f_cluster_reduce(sm, cl, par, 1, true);
     const double xmax = sm.sums[0];
     sm.wgt[t] = real ? 1.0f / (float)(fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0f;
     __syncthreads();
-    float* v0 = Vi(0);
+    double* v0 = Vi(0);
     f_prec(sm, cl, D, I, G, zv, v0, par);
     {
       f_slice_sums<2, false>(sm, 2, [&](int i, int c) {
         if (G.c0 + c >= N) return 0.0;
-        const double a = i == 0 ? (double)v0[c] : x[G.c0 + c];
+        const double a = i == 0 ? v0[c] : x[G.c0 + c];
         return a * a;
       });
       f_cluster_reduce(sm, cl, par, 2, false);
@@ -992,7 +987,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       }
       __syncthreads();
       const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2];
-      f_slice_sums<1, true, float>(sm, 1, [&](int, int c) { return fabsf(v0[c]) * sm.wgt[c]; });
+      f_slice_sums<1, true>(sm, 1, [&](int, int c) { return fabs(v0[c]) * (double)sm.wgt[c]; });
       f_cluster_reduce(sm, cl, par, 1, true);
       const double rinf_c = sm.sums[0];
       __syncthreads();
@@ -1016,21 +1011,21 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         sm.g[0] = nrm;
         for (int i = 1; i <= m; ++i) sm.g[i] = 0.0;
       }
-      v0[t] *= (float)inv_nrm;
+      v0[t] *= inv_nrm;
       __syncthreads();
       int kk = 0;
       for (int jc = 0; jc < m; ++jc) {
-        const float* vj = Vi(jc);
-        f_pass<false>(sm, cl, D, I, G, nullptr, vj, par);
+        const double* vj = Vi(jc);
+        f_pass<false>(sm, cl, D, I, G, vj, par);
         // C v_j = alpha v_j + kappa/dx F(v_j), preconditioned into V_{j+1}
         if (real) {
           const int64_t g = co + j;
-          zv[t] = D.fc.alpha[g] * vj[t] + D.fc.kdx[g] * (float)sm.fl[t];
+          zv[t] = D.cf.alpha[g] * vj[t] + D.cf.kdx[g] * sm.fl[t];
         } else {
-          zv[t] = 0.0f;
+          zv[t] = 0.0;
         }
         __syncthreads();
-        float* wv = Vi(jc + 1);
+        double* wv = Vi(jc + 1);
         f_prec(sm, cl, D, I, G, zv, wv, par);
         // classical Gram-Schmidt, twice (CGS2): per pass one block sum of the jc + 1 dot
         // products w.V_i and one cluster sum; the Hessenberg column accumulates in shared
@@ -1038,21 +1033,21 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-          f_slice_sums<kMaxRestart, false, float>(sm, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; });
+          f_slice_sums<kMaxRestart, false>(sm, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; });
           f_cluster_reduce(sm, cl, par, jc + 1, false);
           {
-            float wj = wv[t];
+            double wj = wv[t];
 #pragma unroll
             for (int i = 0; i < kMaxRestart; ++i) {
               if (i > jc) break;
-              wj = fmaf(-(float)sm.sums[i], Vi(i)[t], wj);
+              wj -= sm.sums[i] * Vi(i)[t];
             }
             wv[t] = wj;
           }
           if (t <= jc) sm.hc[t] += sm.sums[t];
           __syncthreads();
         }
-        f_slice_sums<1, false, float>(sm, 1, [&](int, int c) { return wv[c] * wv[c]; });
+        f_slice_sums<1, false>(sm, 1, [&](int, int c) { return wv[c] * wv[c]; });
         f_cluster_reduce(sm, cl, par, 1, false);
         if (t == 0) {
           sm.sc[0] = sqrt(sm.sums[0]);
@@ -1083,7 +1078,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           const bool est = fabs(gnext) <= 0.05 * D.rtol * xn;
           sm.stop = (est || nrmw == 0.0 || jc + 1 >= m) ? 1 : 0;
         }
-        wv[t] *= (float)sm.sc[1];
+        wv[t] *= sm.sc[1];
         __syncthreads();
         ++its;
         kk = jc + 1;
@@ -1103,7 +1098,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
 #pragma unroll
         for (int i = 0; i < kMaxRestart; ++i) {
           if (i >= kk) break;
-          tq += sm.y[i] * (double)Vi(i)[t];
+          tq += sm.y[i] * Vi(i)[t];
         }
         x[j] = tq;
       }

@@ -1449,9 +1449,9 @@ static bool fused_fits(const Inst& I) { return I.N >= 64 && I.N <= (int64_t)kFQ 
 
 // Kernel attributes of the fused solve (once per device): its shared memory and the
 // non-portable cluster size 16.
-// Dynamic shared memory of the fused kernel: the struct and the slice's binary32 Krylov
-// basis V_0..V_m (m = restart length).
-static size_t fused_smem(int m) { return sizeof(FSmem) + (size_t)(m + 1) * kFS * sizeof(float); }
+// Dynamic shared memory of the fused kernel: the struct and the slice's Krylov basis
+// V_0..V_m (m = restart length).
+static size_t fused_smem(int m) { return sizeof(FSmem) + (size_t)(m + 1) * kFS * sizeof(double); }
 static int g_fused_optin = 0;   // the device's opt-in shared memory per block
 
 static cudaError_t fused_attrs() {
