@@ -47,6 +47,10 @@ GMRES_BYTES_PER_CELL = lambda M, es: M * es + 4 * 8
 # changed since (restart decision read before the CTAs' barriers); until the counters
 # are taken again the line reports traffic as null and gives this figure as context.
 GMRES_TRAFFIC_SLAB6_MIXED_EARLIER = 13.19e6
+# Per-cell bytes the fused prediction solve must move besides the state: the binary64
+# inputs it reads once (T^n, U^n, rho^n and the 16 coefficient arrays of the cell) and
+# the outputs rho* and F* (20 x 8 B).
+FUSED_BYTES_PER_CELL = 160
 
 
 def job_throughput(updates_per_step, steps, t_ms, world, dist=None, device="cuda"):
@@ -410,6 +414,19 @@ def main():
                 "frac": achieved / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n,
                 "bytes_per_elem": LINE_BYTES_PER_ELEM_F32}
+    elif dom_name == "pred_solve":
+        # the fused prediction solve (one persistent cluster per instance): the bytes it
+        # must move are the state read once (E, O in the bulk type) and per cell the
+        # coefficient and vector traffic of the solve's inputs and outputs
+        es = 8 if prec == G.FP64 else 4
+        byts = sum(r.nx * (r.n_dir // 2) * 2 * es + r.nx * FUSED_BYTES_PER_CELL for r in runs)
+        achieved = byts / avg_s / 1e9
+        roof = {"kernel": "k_pred_fused (whole prediction solve per instance cluster)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
+                "bytes_model": "state read once (2 x %d B per line element) + %d B per cell" % (es, FUSED_BYTES_PER_CELL),
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n,
+                "note": "latency-bound: barrier and binary64 dependency chains of ~7 Krylov steps per launch"}
     elif dom_name == "gmres":
         es = 8 if prec == G.FP64 else 4
         M = runs[0].n_dir // 2
@@ -427,6 +444,9 @@ def main():
                 "avg_launch_us": avg_s * 1e6, "launches": dom_n}
     step_s = t_ms * 1e-3 / args.steps
     bpu = 24 if prec == G.FP64 else 12
+    h_mode = ("one CUDA graph launch per step: the prediction solve is one persistent cluster kernel per "
+              "instance" if "pred_solve" in prof else
+              "one CUDA graph launch per step (Krylov loop under device-side conditional nodes)")
     hbm_alg = updates_per_step * bpu / step_s / 1e9    # state read twice, written once per update
 
     if rank == 0:
@@ -442,7 +462,7 @@ def main():
                 "roofline": roof,
                 "step_hbm_roofline": {"algorithmic_bytes_per_update": bpu, "achieved_gbs": hbm_alg,
                                       "peak_gbs": hbm_peak, "frac": hbm_alg / hbm_peak},
-                "step_mode": "one CUDA graph launch per step (Krylov loop under device-side conditional nodes)",
+                "step_mode": h_mode,
                 "kernel_share": {k: round(v[0] / tot_prof, 4) for k, v in sorted(prof.items())},
                 "kernel_profile": "event pairs around every launch over %d further eager steps of the same workload" % kp,
                 "krylov_iters_per_step": kry_its / args.steps / len(runs),
