@@ -72,6 +72,10 @@ def workload_instances(name):
         runs = wl.slab_1d_runs(steps=1)
         cfg = {"workload": "1d_slab_8192x64_sigma0_over_T3_6runs", "nx": 8192, "n_dir": 64,
                "runs": 6, "sigma0": [1, 10], "eps": [1, 1e-2, 1e-4], "dt": "0.5 dx"}
+    elif name == "slab1":
+        runs = [wl.slab_1d_runs(steps=1)[1]]
+        cfg = {"workload": "1d_slab_8192x64_sigma0_1_eps_1e-2", "nx": 8192, "n_dir": 64, "runs": 1,
+               "sigma0": 1, "eps": 1e-2, "dt": "0.5 dx"}
     elif name == "marshak128":
         runs = [wl.marshak_1d()]
         cfg = {"workload": "1d_marshak_128x16", "nx": 128, "n_dir": 16, "runs": 1}
@@ -196,7 +200,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slab6",
-                    choices=["slab6", "marshak128", "batched256", "checker2d", "lognormal2d"])
+                    choices=["slab6", "slab1", "marshak128", "batched256", "checker2d", "lognormal2d"])
     ap.add_argument("--n2d", type=int, default=None,
                     help="cells per axis of the 2D workloads (checker2d: 128, lognormal2d: 512)")
     ap.add_argument("--newton-start", default="bound", choices=["bound", "previous", "learned"],
