@@ -116,3 +116,69 @@ def implicit_T4_step(T, sig, dx, dt, a=1.0, c=1.0, Cv=1.0, Dd=3.0, tol=1e-14, ma
         if np.max(np.abs(dx_)) <= tol * max(1.0, np.max(np.abs(x))):
             break
     return x
+
+
+def implicit_T7_step(T, sig0, dx, dt, a=1.0, c=1.0, Cv=1.0, TL=None, TR=None, tol=1e-13, maxit=200):
+    """One step of the fully implicit limit solver for sigma = sigma_0/T^3 (Sec. 6.5,
+    Eq. diff_solver):
+
+      (T^4 - T_n^4)/dt + (Cv/a)(T - T_n)/dt
+          = 4c/(21 dx^2) [ k_{i+1/2} (T_{i+1}^7 - T_i^7) - k_{i-1/2} (T_i^7 - T_{i-1}^7) ],
+
+    k_{i+1/2} = (1/sigma_0)_{i+1/2}, the mean of 1/sigma_0 of the two cells (the
+    displayed average).  Walls (the paper does not print them): TL / TR given - the
+    Dirichlet values T(0) = TL, T(L) = TR of the Marshak problem - enter through the
+    half cell between the wall and the first cell centre, with k of that cell;
+    None - zero flux.  Newton's method on the global system in the unknown u = T^4
+    (its accumulation term keeps the Jacobian regular where the diffusion degenerates,
+    T -> 0), tridiagonal Jacobian, iterates kept non-negative."""
+    N = T.size
+    Tn = np.asarray(T, dtype=np.float64)
+    un = Tn ** 4
+    inv = 1.0 / np.asarray(sig0, dtype=np.float64) * np.ones(N)
+    kf = 0.5 * (inv[:-1] + inv[1:])                  # interior faces 1..N-1
+    coef = 4.0 * c / (21.0 * dx ** 2)
+    kL = 2.0 * inv[0] if TL is not None else 0.0     # half-cell distance at the walls
+    kR = 2.0 * inv[-1] if TR is not None else 0.0
+    bL = TL ** 7 if TL is not None else 0.0
+    bR = TR ** 7 if TR is not None else 0.0
+    u = un.copy()
+    for _ in range(maxit):
+        V = u ** 1.75                                  # T^7
+        flux = np.zeros(N)
+        fi = kf * (V[1:] - V[:-1])
+        flux[:-1] += fi
+        flux[1:] -= fi
+        flux[0] += kL * (bL - V[0])
+        flux[-1] += kR * (bR - V[-1])
+        F = (u - un) / dt + Cv / a * (u ** 0.25 - Tn) / dt - coef * flux
+        dV = 1.75 * u ** 0.75
+        di = 1.0 / dt + Cv / a * 0.25 * np.maximum(u, 1e-300) ** -0.75 / dt
+        di[:-1] += coef * kf * dV[:-1]
+        di[1:] += coef * kf * dV[1:]
+        di[0] += coef * kL * dV[0]
+        di[-1] += coef * kR * dV[-1]
+        ab = np.zeros((3, N))
+        ab[0, 1:] = -coef * kf * dV[1:]
+        ab[2, :-1] = -coef * kf * dV[:-1]
+        ab[1] = di
+        d = solve_banded((1, 1), ab, -F)
+        unew = np.maximum(u + d, 0.0)
+        step = np.max(np.abs(unew - u))
+        u = unew
+        if step <= tol * max(1.0, np.max(np.abs(u))):
+            break
+    return u ** 0.25
+
+
+def front_position(T, dx, level=0.5):
+    """x_f = the largest cell centre with T >= level (Sec. 6.5: where the wave stands);
+    linear interpolation between that cell and the next."""
+    i = np.nonzero(T >= level)[0]
+    if i.size == 0:
+        return 0.0
+    j = i[-1]
+    xc = (j + 0.5) * dx
+    if j + 1 < T.size and T[j] != T[j + 1]:
+        xc += dx * (T[j] - level) / (T[j] - T[j + 1])
+    return xc

@@ -386,7 +386,8 @@ def predict_literal(P, S):
 
 
 def correction_temperature(P, S, Fstar, Ustar):
-    """Correction substep 1: per-cell scalar equation for T^{n+1}.
+    """Correction substep 1: per-cell scalar equation for T^{n+1}; Fstar is the flux of
+    correction_flux().
 
     sigma(x): Eq. Tnp1,
       1/(c dt) [a c T^4 + eps^2 Cv/(sig dt) (T - T^n)] + Cv/dt (T - T^n)
@@ -487,18 +488,53 @@ def correct_intensity(P, S, Tnew):
     return EJ, OJ
 
 
+def correction_flux(P, S, Es, Os, Us):
+    """The flux sum_k w_k v_k (O_{J,j+1} - O_{J,j}) that the temperature equation of the
+    correction takes from the predicted state.
+
+    sigma(x): O_J^{n+1*} = O^{n+1*}, the prediction's own O (stated after Eq. Tnp1).
+    sigma/T^3: Eq. dis-cor-marshak1 evaluated with the predicted data, i.e. the node
+    flux with the multiplier V* = (U*)^{3/4} (node values the mean of the two cells,
+    U* < 0 read as 0) in place of the prediction's K^n = (T^n)^3:
+        O~_i = d*_i [eps^2 O^n_i/(c dt) - v (E*_i - E*_{i-1})/dx],
+        d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i)   (interior nodes),
+    walls Eq. bc-pre with E*.  This is the reading under which the correction's diffusion
+    limit carries (T^{n+1*})^3 as the remark closing Sec. 5 states (with K^n frozen at
+    T^n the two coincide only for sigma(x)); it is also the one that reproduces the
+    Marshak front of Sec. 6.5 at eps = 1e-5."""
+    if P.kind == SIGMA_CONST:
+        return flux_div(P, Os)
+    N, M = P.N, P.M
+    eps, c, dt, dx = P.eps, P.c, P.dt, P.dx
+    V = np.maximum(Us, 0.0) ** 0.75
+    Vn = np.zeros(N + 1)
+    Vn[1:-1] = 0.5 * (V[:-1] + V[1:])
+    sn = P.node_sig()
+    d = np.zeros(N + 1)
+    den = Vn[1:-1] * eps ** 2 / (c * dt) + sn[1:-1]
+    d[1:-1] = np.where(den > 0, Vn[1:-1] / np.where(den > 0, den, 1.0), 0.0)
+    O = np.zeros((N + 1, M))
+    O[1:-1] = d[1:-1, None] * (eps ** 2 * S.O[1:-1] / (c * dt) - P.v[None, :] * (Es[1:] - Es[:-1]) / dx)
+    if P.bc == "inflow":
+        O[0] = 2.0 / eps * (P.bL - Es[0]) - O[1]
+        O[N] = 2.0 / eps * (Es[N - 1] - P.bR) - O[N - 1]
+    return flux_div(P, O)
+
+
 def step(P, S, info=None):
     """One step of Algorithm 2: prediction, correction (substeps 1 and 2), projection
     (Eq. dis-proj).  Returns the new State; fills `info` if given."""
     Es, Os, Us, _ = predict(P, S)
     Fs = flux_div(P, Os)
-    Tn, its, nneg, rho_n = correction_temperature(P, S, Fs, Us)
+    Fc = correction_flux(P, S, Es, Os, Us)
+    Tn, its, nneg, rho_n = correction_temperature(P, S, Fc, Us)
     EJ, OJ = correct_intensity(P, S, Tn)
     U = Tn ** 4                                   # Eq. dis-proj1
     E = P.a * P.c * U[:, None] + P.eps * EJ       # Eq. dis-proj3
     O = OJ                                        # Eq. dis-proj2 and its boundary rows
     if info is not None:
         info.Estar, info.Ostar, info.Ustar, info.Fstar = Es, Os, Us, Fs
+        info.extra["Fcorr"] = Fc
         info.rho_n, info.T_new, info.newton_its, info.EJ = rho_n, Tn, its, EJ
         info.negative_R = nneg
     return State(E=E, O=O, U=U, T=Tn, t=S.t + P.dt, step=S.step + 1)

@@ -491,6 +491,27 @@ def flux_div(P, O, E):
     return out
 
 
+def correction_flux(P, S, Es, Os, Us):
+    """The flux the temperature equation of the correction takes from the predicted
+    state (see grte1d.correction_flux): sigma(x) the prediction's own O*; sigma/T^3 the
+    vertex map rebuilt with the multiplier V* = (U*)^{3/4} (vertex values the mean of
+    the four cells) in place of the prediction's K^n, applied to the predicted E*."""
+    if P.kind == SIGMA_CONST:
+        return flux_div(P, Os, Es)
+    eps, c, dt = P.eps, P.c, P.dt
+    V = np.maximum(Us, 0.0) ** 0.75
+    kv, sv = _vertex_coef(P, V)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(kv > 0, kv / (kv * eps ** 2 / (c * dt) + sv), 0.0)
+    Oc = np.zeros((P.nv, P.K))
+    for k in range(P.K):
+        Dk = grad_matrix(P, k)
+        o = d * eps ** 2 / (c * dt) * S.O[:, k]
+        Qk, qk = vertex_map(P, k, sp.diags(d) @ Dk, o)
+        Oc[:, k] = Qk @ Es[:, k] + qk
+    return flux_div(P, Oc, Es)
+
+
 def correction_temperature(P, S, Fdiv, Ustar):
     """Eq. Tnp1 (sigma/T^3: Eq. dis-cor-marshak4 + 5) multiplied by sig:
     A T^4 + B T = R with R = sig (rho^n/(c dt) - Fdiv) + B T^n (see grte1d)."""
@@ -532,10 +553,11 @@ def step(P, S, info=None):
     """One step: prediction, correction substeps 1 and 2, projection."""
     Es, Os, Us, rhos = predict(P, S)
     Fd = flux_div(P, Os, Es)
-    Tn, its, rho_n = correction_temperature(P, S, Fd, Us)
+    Fc = correction_flux(P, S, Es, Os, Us)
+    Tn, its, rho_n = correction_temperature(P, S, Fc, Us)
     EJ, En, On = correct_intensity(P, S, Tn)
     if info is not None:
-        info.update(Estar=Es, Ostar=Os, Ustar=Us, rho_star=rhos, Fdiv=Fd, rho_n=rho_n, T_new=Tn,
+        info.update(Estar=Es, Ostar=Os, Ustar=Us, rho_star=rhos, Fdiv=Fd, Fcorr=Fc, rho_n=rho_n, T_new=Tn,
                     newton_its=its, EJ=EJ)
     return State2D(E=En, O=On, U=Tn ** 4, T=Tn)
 
