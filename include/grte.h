@@ -248,7 +248,7 @@ grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size
  *   E  device, nx*M doubles, line-major E[k*nx + j] (the device layout of grte.h);
  *   O  device, (nx+1)*M doubles, line-major O[k*(nx+1) + i].
  * No cudaMalloc, cudaFree or other allocating call is made: every work buffer is
- * carved from one static device array of 10,575,872 bytes (about 10.6 MB) that every GPU loading this
+ * carved from one static device array of 11,198,976 bytes (about 11.2 MB) that every GPU loading this
  * library holds until the process exits.  Limits: nx <= 4096, n_angle <= 32,
  * nx*n_angle <= 65536; larger sizes return GRTE_EINVAL.  The first call on a device
  * looks up the device address of that array (cudaGetSymbolAddress, with the device
@@ -317,7 +317,9 @@ grte_status grte2d_step(grte2d_t h, int64_t n);
 grte_status grte2d_get_T(grte2d_t h, double* T, size_t len);           /* len = nx*ny          */
 grte_status grte2d_get_E(grte2d_t h, double* E, size_t len);           /* len = nx*ny*K        */
 grte_status grte2d_get_O(grte2d_t h, double* O, size_t len);           /* len = (nx+1)(ny+1)K  */
-/* which: 0 U*, 1 sum_k w_k (D*_k O*_k) (the flux term of Eq. Tnp1), 2 rho*, 3 Newton
+/* which: 0 U*, 1 the flux term of the temperature equation (Eq. Tnp1): sum_k w_k (D*_k O_k)
+ * with O from the predicted E* by the vertex map of the prediction (sigma(x)) or of the
+ * multiplier V* = (U*)^{3/4} (sigma_0/T^3, Eq. dis-cor-marshak1), 2 rho*, 3 Newton
  * iterations; len = nx*ny. */
 grte_status grte2d_get_stage(grte2d_t h, int which, double* out, size_t len);
 grte_status grte2d_get_quadrature(grte2d_t h, double* mu, double* eta, double* w, size_t K);

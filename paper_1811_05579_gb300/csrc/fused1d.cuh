@@ -59,6 +59,9 @@ struct FSmem {
   double vkd[32], wvkd[32];
   double fl[kFS];                                       // flux sums of the last pass
   double fdat[kFS];                                     // data part of the flux (data passes)
+  // the correction's flux (sigma_0/T^3): node coefficients d* of V* = (U*)^{3/4} at the
+  // nodes c0 + t (t = 0..kFS), the node moments Om = sum_k w_k v_k O^n, the flux per cell
+  double dsd[kFS + 1], Om[kFS + 1], flc[kFS];
   double pu[kFS];                                       // preconditioner solution (slice)
   // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
   // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
@@ -425,6 +428,24 @@ __device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
   return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
 }
 
+// Node coefficient of the correction's flux (sigma_0/T^3, Eq. dis-cor-marshak1 with the
+// predicted data) at interior node i, for the iterate rho = X:
+//   d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i),  V*_i = (V*_{i-1/2} + V*_{i+1/2})/2,
+//   V* = max(U*, 0)^{3/4},  U* = (U^n + gam rho)/(1 + gam a c)  (Eq. dis-pre3),
+// sig_i the harmonic node mean; 0 at the wall nodes and past the grid.
+__device__ double f_dstar(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t i) {
+  if (i < 1 || i > G.N - 1) return 0.0;
+  const int64_t gl = G.co + i - 1, gr = G.co + i;
+  const double ac = I.a * I.c;
+  const double ul = (D.U[gl] + D.cf.gam[gl] * f_x<true>(X, G, i - 1)) / (1.0 + D.cf.gam[gl] * ac);
+  const double ur = (D.U[gr] + D.cf.gam[gr] * f_x<true>(X, G, i)) / (1.0 + D.cf.gam[gr] * ac);
+  const double vn = 0.5 * (pow(fmax(ul, 0.0), 0.75) + pow(fmax(ur, 0.0), 0.75));
+  const double sl = D.sig[gl], sr = D.sig[gr];
+  const double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
+  const double den = vn * I.eps * I.eps / (I.c * I.dt) + sn;
+  return den > 0.0 ? vn / den : 0.0;
+}
+
 template <bool FULL>
 __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const FVec& X) {
   const int t = threadIdx.x;
@@ -463,11 +484,20 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     // (here: data passes, and the inflow wall cells of Krylov passes, whose rho part
     // cancels against the e/o wall sum to O(eps), both carrying the factor 2/eps)
     sm.fl[t] = fr;
+    if (FULL && I.kind == GRTE_SIGMA_T3) {
+      // d* at this cell's left node (and, for the last thread, at the slice's right end)
+      sm.dsd[t] = f_dstar(D, I, G, X, j);
+      if (t == kFS - 1) sm.dsd[kFS] = f_dstar(D, I, G, X, j + 1);
+    }
   } else {
     sm.P1[t] = 0.0f;
     sm.P2[t] = 0.0f;
     sm.P3[t] = 0.0f;
     sm.fl[t] = 0.0;
+    if (FULL) {
+      sm.dsd[t] = 0.0;
+      if (t == kFS - 1) sm.dsd[kFS] = 0.0;
+    }
   }
 }
 
@@ -495,7 +525,7 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
   const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
   const float kcd = sm.kcd[jl], kdx = sm.kdx[jl], odj = sm.od[jl], odr = sm.od[jl + 1];
   const bool nj = j >= 1 && j <= N - 1, nr = j + 1 >= 1 && j + 1 <= N - 1;
-  double fsum = 0.0;
+  double fsum = 0.0, om = 0.0, omr = 0.0;
   constexpr int B = 8;
   for (int k0 = 0; k0 < 32; k0 += B) {
     float e[B], oj[B], orr[B];
@@ -519,9 +549,13 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
       const float d = real ? fmaf(kcd, e[q], -kdx * sm.vk[kk] * Dj) : 0.0f;
       sm.x[w * kFL + lane][kk] = d;
       if (real && !wallc) fsum += sm.wvkd[kk] * (double)Dj;
+      om += sm.wvkd[kk] * (double)oj[q];
+      omr += sm.wvkd[kk] * (double)orr[q];
     }
   }
   sm.fdat[w * kFL + lane] = fsum;
+  sm.Om[w * kFL + lane] = om;            // node c0 + t (interior nodes; 0 elsewhere)
+  if (w == kFW - 1 && lane == 31) sm.Om[kFS] = omr;
   __syncwarp();
 #pragma unroll 8
   for (int u = 0; u < kFL; ++u) fd[u * 32 + lane] = sm.x[w * kFL + u][lane];
@@ -596,13 +630,36 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   }
   __syncthreads();
   f_line_solve(sm, cl, G, par);
+  const bool corr = FULL && I.kind == GRTE_SIGMA_T3;
+  if (corr) {
+    // the correction's flux (see f_dstar): its rho part, and the data part of the cells
+    // that are not inflow wall cells (those take theirs in the wall block below)
+    const int t = threadIdx.x;
+    const int64_t j = G.c0 + t;
+    if (j < N) {
+      const int64_t g = G.co + j;
+      const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
+                   xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
+      const double dL = sm.dsd[t], dR = sm.dsd[t + 1];
+      const bool wl = inflow && j == 0, wr = inflow && j == N - 1;
+      const double mR = wl ? 2.0 : 1.0, mL = wr ? 2.0 : 1.0;
+      double fc = I.wv2 * (mR * dR * (xj - xr) + mL * dL * (xj - xl)) / I.dx + I.wv * D.cf.gbx[g] * xj;
+      if (wl) fc -= I.two_eps * I.bLflux;
+      if (wr) fc -= I.two_eps * I.bRflux;
+      if (!wl && !wr) fc += I.eps * I.eps / (I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
+      sm.flc[t] = fc;
+    } else {
+      sm.flc[t] = 0.0;
+    }
+    __syncthreads();
+  }
   // inflow walls: e re-solved in double from the neighbour; e/o wall flux in double
   if (inflow && w == 0) {
     for (int side = 0; side < 2; ++side) {
       const int64_t jw = side == 0 ? 0 : N - 1;
       const int64_t tl = jw - G.c0;
       if (!(tl >= 0 && tl < kFS)) continue;
-      double sw = 0.0;
+      double sw = 0.0, swc = 0.0;
       if (k < G.M) {
         const double vd = sm.vkd[k], v2d = vd * vd;
         const int64_t g = G.co + jw;
@@ -627,9 +684,29 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
           const double ON1 = on - dl * vd * (ew - en);
           sw = sm.wvkd[k] * (I.two_eps * ew - 2.0 * ON1);
         }
+        if (corr) {
+          // the same wall row with the correction's node coefficient d*
+          const double ds = sm.dsd[ni - G.c0];
+          double onc = 0.0;
+          {
+            const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (N + 1);
+            onc = ds * I.eps * I.eps / (I.c * I.dt) * (double)Ok[ni];
+          }
+          if (side == 0) {
+            const double O1 = onc - ds / I.dx * vd * (en - ew);
+            swc = sm.wvkd[k] * (2.0 * O1 + I.two_eps * ew);
+          } else {
+            const double ON1 = onc - ds / I.dx * vd * (ew - en);
+            swc = sm.wvkd[k] * (I.two_eps * ew - 2.0 * ON1);
+          }
+        }
       }
       for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
       if (k == 0) sm.fl[tl] += sw;
+      if (corr) {
+        for (int o = 16; o > 0; o >>= 1) swc += __shfl_xor_sync(0xffffffffu, swc, o);
+        if (k == 0) sm.flc[tl] += swc;
+      }
     }
   }
   // e/o flux of every interior cell without the data part, summed over the angles by the
@@ -646,16 +723,30 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       if (FULL) {
         // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
         // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
-        float hi = 0.0f, lo = 0.0f;
+        float hi = 0.0f, lo = 0.0f, hc = 0.0f, lc = 0.0f;
+        const float dRc = corr ? (float)(sm.dsd[t + 1] / I.dx) : 0.0f;
+        const float dLc = corr ? (float)(sm.dsd[t] / I.dx) : 0.0f;
         for (int kk = 0; kk < G.M; ++kk) {
           const float ej = sm.x[t][kk];
-          const float a = -sm.wvk[kk] * sm.vk[kk] * (dR * (xr[kk] - ej) - dL * (ej - xl[kk]));
-          const float sN = hi + a;
-          const float bb = sN - hi;
-          lo += (hi - (sN - bb)) + (a - bb);
-          hi = sN;
+          const float wv2k = -sm.wvk[kk] * sm.vk[kk];
+          const float gr = xr[kk] - ej, gl_ = ej - xl[kk];
+          {
+            const float a = wv2k * (dR * gr - dL * gl_);
+            const float sN = hi + a;
+            const float bb = sN - hi;
+            lo += (hi - (sN - bb)) + (a - bb);
+            hi = sN;
+          }
+          if (corr) {
+            const float a = wv2k * (dRc * gr - dLc * gl_);
+            const float sN = hc + a;
+            const float bb = sN - hc;
+            lc += (hc - (sN - bb)) + (a - bb);
+            hc = sN;
+          }
         }
         sm.fl[t] += sm.fdat[t] + ((double)hi + (double)lo);
+        if (corr) sm.flc[t] += (double)hc + (double)lc;
       } else {
         float acc = (float)sm.fl[t];
         for (int kk = 0; kk < G.M; ++kk) {
@@ -963,6 +1054,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
       zv[t] = -R;
       D.Fs[g] = fl;
+      D.Fc[g] = (I.kind == GRTE_SIGMA_T3) ? sm.flc[t] : fl;
     } else {
       zv[t] = 0.0;
     }

@@ -71,6 +71,10 @@ struct CellCoef {
   double *ratio;   // (A_j - alpha_j)/alpha_j = beta/alpha
   double *fR, *fL; // m^R d_{j+1}/dx, m^L d_j/dx (streaming flux of a per-cell field, unscaled by kappa)
   double *gbx;     // 2/eps in the inflow wall cells, else 0
+  // the correction's flux (sigma_0/T^3) at the iterate of the last data pass: at the
+  // left node of each cell d*/dx and d* eps^2/(c dt), d* the node coefficient of
+  // V* = (U*)^{3/4} (Eq. dis-cor-marshak1 with the predicted data)
+  double *dsx, *ods;
 };
 
 // Binary32 copies of the per-cell values that the line and Krylov kernels use per
@@ -80,6 +84,7 @@ struct CellF {
   float *A, *gl, *gu, *gb, *od, *dlx, *kcd, *kdx, *ratio, *ralpha, *alpha;
   float *kcde, *kdxe, *dlxe;    // kcd/eps, kdx/eps, dlx*eps (correction substep 2)
   float *fR, *fL, *gbx;         // rho-part flux coefficients (fused Krylov passes)
+  float *dsx, *ods;             // binary32 copies of cf.dsx, cf.ods
   float *P1, *P2, *P3, *Frho;   // per-cell parts of a prediction pass
   float *Q1, *Q2, *gU;          // per-cell parts of correction substep 2
 };
@@ -94,6 +99,7 @@ struct Dev {
   double *T, *U, *sig;
   // per-cell
   double *rho_n, *rho_s, *Fs, *Us, *newton_its;
+  double* Fc;      // the correction's flux (sigma_0/T^3: with V* = (U*)^{3/4}; sigma(x): = Fs)
   // per-cell parts of a line pass, computed once per cell in double
   double *P1, *P2, *P3, *Frho, *gU, *Q1, *Q2;
   double *gwork;   // per-cell double work vector of the Krylov kernels
@@ -102,6 +108,8 @@ struct Dev {
   CellF fc;
   // per-element work (bulk type)
   void *xb, *S, *F, *Rd, *onode;
+  void* S2;        // per element: the correction's e/o flux part (sigma_0/T^3 data passes)
+  double* Swall2;  // its two inflow-wall contributions per (instance, angle), in double
   // preconditioner factors
   double *pF, *pRd, *pG, *pH, *gw, *pInv;
   // GMRES
@@ -281,6 +289,28 @@ __device__ __forceinline__ void cellpart_cell(const Dev& D, const Inst& I, int64
     D.fc.P3[gid] = (float)p3;
     D.fc.Frho[gid] = (float)fr;
   }
+  if (full && I.kind == GRTE_SIGMA_T3) {
+    // node coefficient of the correction's flux at this cell's left node (interior
+    // nodes): d* = V*/(V* eps^2/(c dt) + sig), V* = mean over the two cells of
+    // max(U*, 0)^{3/4}, U* = (U^n + gam x)/(1 + gam a c)
+    double ds = 0.0;
+    if (j >= 1) {
+      const double ac = I.a * I.c;
+      const double ul = (D.U[gid - 1] + D.cf.gam[gid - 1] * xl) / (1.0 + D.cf.gam[gid - 1] * ac);
+      const double ur = (D.U[gid] + D.cf.gam[gid] * xj) / (1.0 + D.cf.gam[gid] * ac);
+      const double vn = 0.5 * (pow(fmax(ul, 0.0), 0.75) + pow(fmax(ur, 0.0), 0.75));
+      const double sl = D.sig[gid - 1], sr = D.sig[gid];
+      const double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
+      const double den = vn * I.eps * I.eps / (I.c * I.dt) + sn;
+      ds = den > 0.0 ? vn / den : 0.0;
+    }
+    D.cf.dsx[gid] = ds / I.dx;
+    D.cf.ods[gid] = ds * I.eps * I.eps / (I.c * I.dt);
+    if (D.mixed) {
+      D.fc.dsx[gid] = (float)(ds / I.dx);
+      D.fc.ods[gid] = (float)(ds * I.eps * I.eps / (I.c * I.dt));
+    }
+  }
 }
 
 template <typename X>
@@ -433,6 +463,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const void* 
   //   j = N-1: (2/eps) e_{N-1} - 2 O^eo_{N-1}
   R* Sk = (R*)D.S + eo;
   const R wvr = R(w * v);
+  // the correction's flux (sigma_0/T^3 data passes): the same with the node coefficient
+  // d* of V* = (U*)^{3/4} (cf.dsx = d*/dx, cf.ods = d* eps^2/(c dt), from the per-cell parts)
+  const bool corr = MODE != PRED_HOM && I.kind == GRTE_SIGMA_T3;
   if (inflow && threadIdx.x == 0) {   // wall cells: e/o flux in double, kept in Swall
     const double eL = ew[0], eR = ew[1];
     const double e1 = (N > 2) ? (double)xb[1] : eR, eN2 = (N > 2) ? (double)xb[N - 2] : eL;
@@ -440,6 +473,29 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const void* 
     const double ON1 = (double)onode(N - 1) - dlx[N - 1] * v * (eR - eN2);
     D.Swall[2 * (I.ang_off + k) + 0] = w * v * (2.0 * O1 + two_eps * eL);
     D.Swall[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1);
+    if (corr) {
+      const double *dsx = D.cf.dsx + co, *ods = D.cf.ods + co;
+      const double O1c = ods[1] * (double)On[1] - dsx[1] * v * (e1 - eL);
+      const double ON1c = ods[N - 1] * (double)On[N - 1] - dsx[N - 1] * v * (eR - eN2);
+      D.Swall2[2 * (I.ang_off + k) + 0] = w * v * (2.0 * O1c + two_eps * eL);
+      D.Swall2[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1c);
+    }
+  }
+  if (corr) {
+    R* S2k = (R*)D.S2 + eo;
+    const R *dsxr = pick<R>(D.cf.dsx, D.fc.dsx) + co, *odsr = pick<R>(D.cf.ods, D.fc.ods) + co;
+    for (int64_t j = threadIdx.x; j < N; j += NT) {
+      auto Oc = [&](int64_t i) -> R { return odsr[i] * On[i] - dsxr[i] * vr * (xb[i] - xb[i - 1]); };
+      R val;
+      if (inflow && (j == 0 || j == N - 1)) {
+        val = R(0);                       // in Swall2
+      } else {
+        const R OR = (j + 1 <= N - 1) ? Oc(j + 1) : R(0);
+        const R OL = (j >= 1) ? Oc(j) : R(0);
+        val = OR - OL;
+      }
+      S2k[j] = wvr * val;
+    }
   }
 #pragma unroll 4
   for (int64_t j = threadIdx.x; j < N; j += NT) {
@@ -755,6 +811,32 @@ __device__ __forceinline__ R flux_sum_k(const Dev& D, const Inst& I, int64_t j) 
   return pick<R>(D.Frho, D.fc.Frho)[I.cell_off + j] + eo_sum<R>(D, I, j);
 }
 
+// The correction's flux at cell j (sigma_0/T^3, the node coefficients d* of the data pass
+// that just ran at the iterate x): its rho part
+//   wv2 [mR d*_{j+1} (x_j - x_{j+1}) + mL d*_j (x_j - x_{j-1})]/dx + wv gbx x_j
+//   (minus 2/eps sum_k w_k v_k b at the inflow walls; m = 2 on the inflow wall sides)
+// plus the per-angle e/o parts S2 (in double), or at the inflow walls the Swall2 sums.
+template <typename R>
+__device__ __forceinline__ double corr_flux_sum(const Dev& D, const Inst& I, int64_t j, const double* x) {
+  const int64_t N = I.N, co = I.cell_off;
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  const double xj = x[j], xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
+  const double dR = j < N - 1 ? D.cf.dsx[co + j + 1] : 0.0, dL = D.cf.dsx[co + j];
+  const double mR = (inflow && j == 0) ? 2.0 : 1.0, mL = (inflow && j == N - 1) ? 2.0 : 1.0;
+  double f = I.wv2 * (mR * dR * (xj - xr) + mL * dL * (xj - xl)) + I.wv * D.cf.gbx[co + j] * xj;
+  if (inflow && j == 0) f -= I.two_eps * I.bLflux;
+  if (inflow && j == N - 1) f -= I.two_eps * I.bRflux;
+  if (wall_cell(I, j)) {
+    const int side = (j == 0) ? 0 : 1;
+    for (int k = 0; k < I.M; ++k) f += D.Swall2[2 * (I.ang_off + k) + side];
+    return f;
+  }
+  const R* S = (const R*)D.S2 + I.elem_off + j;
+  double acc = 0.0;
+  for (int k = 0; k < I.M; ++k) acc += (double)S[(int64_t)k * N];
+  return f + acc;
+}
+
 enum { G_RESTART_FIRST = 0, G_RESTART = 1, G_ARNOLDI = 2, G_UPDATE = 3 };
 
 
@@ -803,6 +885,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       const double Rj = alpha[j] * x[j] - kcd[j] * D.rho_n[co + j] - sac[j] * D.U[co + j] + kdx[j] * fl;
       r[j] = -Rj;
       D.Fs[co + j] = fl;                    // F* of the current iterate (final at convergence)
+      D.Fc[co + j] = (I.kind == GRTE_SIGMA_T3) ? corr_flux_sum<R>(D, I, j, x) : fl;
     }
     // per-cell weights of the stopping test: the preconditioned residual relative to
     // |x_j| (floor wfloor max|x|: 1e-13 in FP64, 1e-8 with binary32 line solves), so
@@ -1044,7 +1127,8 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
   const double A = sig * I.a / dt;
   const double B = sig * I.Cv / dt + I.eps * I.eps * kap * I.Cv / (I.c * dt * dt);
   const double Tn = D.T[gid];
-  const double R = sig * (D.rho_n[gid] / (I.c * dt) - D.Fs[gid] / I.dx) + B * Tn;
+  // the correction's flux (sigma_0/T^3: with V* = (U*)^{3/4}; sigma(x): the prediction's F*)
+  const double R = sig * (D.rho_n[gid] / (I.c * dt) - D.Fc[gid] / I.dx) + B * Tn;
   double T;
   int its = 0;
   if (A == 0.0 && B == 0.0) {
@@ -1758,22 +1842,25 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.P1, nc); AL(D.P2, nc); AL(D.P3, nc); AL(D.Frho, nc); AL(D.gU, nc); AL(D.Q1, nc); AL(D.Q2, nc);
   AL(D.gwork, nc);
   AL(D.Swall, 2 * na);
-  AL(D.rho_n, nc); AL(D.rho_s, nc); AL(D.Fs, nc); AL(D.Us, nc); AL(D.newton_its, nc);
+  AL(D.rho_n, nc); AL(D.rho_s, nc); AL(D.Fs, nc); AL(D.Us, nc); AL(D.newton_its, nc); AL(D.Fc, nc);
   AL(D.cf.kc, nc); AL(D.cf.s, nc); AL(D.cf.alpha, nc); AL(D.cf.A, nc); AL(D.cf.gam, nc);
   AL(D.cf.gl, nc); AL(D.cf.gu, nc); AL(D.cf.gb, nc); AL(D.cf.dl, nc);
   AL(D.cf.od, nc); AL(D.cf.dlx, nc); AL(D.cf.kcd, nc); AL(D.cf.kdx, nc); AL(D.cf.sac, nc);
   AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc); AL(D.cf.fR, nc); AL(D.cf.fL, nc); AL(D.cf.gbx, nc);
+  AL(D.cf.dsx, nc); AL(D.cf.ods, nc);
+  AL(D.Swall2, 2 * na);
   if (mixed) {
     CellF& f = D.fc;
     AL(f.A, nc); AL(f.gl, nc); AL(f.gu, nc); AL(f.gb, nc); AL(f.od, nc); AL(f.dlx, nc); AL(f.kcd, nc);
     AL(f.kdx, nc); AL(f.ratio, nc); AL(f.ralpha, nc); AL(f.alpha, nc); AL(f.kcde, nc); AL(f.kdxe, nc);
     AL(f.dlxe, nc); AL(f.P1, nc); AL(f.P2, nc); AL(f.P3, nc); AL(f.Frho, nc); AL(f.Q1, nc); AL(f.Q2, nc);
-    AL(f.gU, nc); AL(f.fR, nc); AL(f.fL, nc); AL(f.gbx, nc);
+    AL(f.gU, nc); AL(f.fR, nc); AL(f.fL, nc); AL(f.gbx, nc); AL(f.dsx, nc); AL(f.ods, nc);
   }
   {
     char* p_;
     if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc xb"); D.xb = p_;
     if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S"); D.S = p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S2"); D.S2 = p_;
     if (dalloc(h, &p_, es * foff) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc F"); D.F = p_;
     if (dalloc(h, &p_, es * h->nred) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Rd"); D.Rd = p_;
     if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc onode"); D.onode = p_;
@@ -2630,7 +2717,7 @@ constexpr int64_t kNaMaxCells = 4096;
 constexpr int kNaMaxAngles = 32;
 constexpr int64_t kNaMaxElems = 65536;                      // nx * n_angle
 constexpr int64_t kNaMaxNodeElems = kNaMaxElems + kNaMaxAngles;
-constexpr int64_t kNaCellArrays = 39;                       // per-cell double arrays (37 + the x/z pair)
+constexpr int64_t kNaCellArrays = 42;                       // per-cell double arrays (40 + the x/z pair)
 constexpr int64_t kNaAlign = 256;
 __host__ __device__ constexpr int64_t na_round(int64_t b) { return (b + kNaAlign - 1) / kNaAlign * kNaAlign; }
 // line solves run at kTriThreads threads here: per line at most 2 kTriThreads reduced
@@ -2642,20 +2729,20 @@ constexpr int64_t kNaBytes =
     na_round(8 * 5 * (kNaMaxCells + kCL * kTriThreads)) +           // preconditioner factors
     na_round(8 * kCL * kNaRedLine) +                                // preconditioner reduced systems
     na_round(8 * (kMaxRestart + 1) * kNaMaxCells) +                 // Krylov basis
-    na_round(8 * kNaMaxElems) * 3 +                                 // Eh, xb, S
+    na_round(8 * kNaMaxElems) * 4 +                                 // Eh, xb, S, S2
     na_round(8 * (5 * kNaMaxElems + kNaMaxAngles * kNaFacLine)) +   // line factors
     na_round(8 * kNaMaxNodeElems) +                                 // node scratch
     na_round(8 * kNaMaxAngles * kNaRedLine) +                        // line reduced systems
-    na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) + // v, w, bL, bR; Swall
+    na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) * 2 + // v, w, bL, bR; Swall, Swall2
     na_round(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL)) +
     na_round(4 * 16) + na_round(sizeof(Inst)) + na_round(sizeof(Line) * kNaMaxAngles) + na_round(8);
 }  // namespace grte
 
-// Work memory of grte_step1d_noalloc: kNaBytes = 10,575,872 bytes (about 10.6 MB),
+// Work memory of grte_step1d_noalloc: kNaBytes = 11,198,976 bytes (about 11.2 MB),
 // held by every GPU that loads the library until the process exits.  Calls share it
 // (see include/grte.h, which states the same figure; the assertion keeps the two in
 // step when the layout changes).
-static_assert(grte::kNaBytes == 10575872, "no-alloc work memory size changed: update the documented figure");
+static_assert(grte::kNaBytes == 11198976, "no-alloc work memory size changed: update the documented figure");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[grte::kNaBytes];
 static void* g_noalloc_base[64];   // device address of g_noalloc_scratch, per device
 
@@ -2776,7 +2863,8 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
                                    &D.P3, &D.Frho, &D.gU, &D.Q1, &D.Q2, &D.gwork, &D.cf.kc, &D.cf.s,
                                    &D.cf.alpha, &D.cf.A, &D.cf.gam, &D.cf.gl, &D.cf.gu, &D.cf.gb, &D.cf.dl,
                                    &D.cf.od, &D.cf.dlx, &D.cf.kcd, &D.cf.kdx, &D.cf.sac, &D.cf.ralpha,
-                                   &D.cf.ratio, &D.cf.fR, &D.cf.fL, &D.cf.gbx, &D.pG, &D.pH, &D.gw};
+                                   &D.cf.ratio, &D.cf.fR, &D.cf.fL, &D.cf.gbx, &D.pG, &D.pH, &D.gw,
+                                   &D.cf.dsx, &D.cf.ods, &D.Fc};
   for (int i = 0; i < kNaCellArrays - 2; ++i) *cells[i] = (double*)take(8 * kNaMaxCells);
   // x and z of the Krylov kernels are adjacent: the kernels take the cell stride of
   // the basis as gz - gx, here kNaMaxCells
@@ -2788,12 +2876,14 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   D.Eh = take(8 * kNaMaxElems);
   D.xb = take(8 * kNaMaxElems);
   D.S = take(8 * kNaMaxElems);
+  D.S2 = take(8 * kNaMaxElems);
   D.F = take(8 * (5 * kNaMaxElems + kNaMaxAngles * kNaFacLine));
   D.onode = take(8 * kNaMaxNodeElems);
   D.Rd = take(8 * kNaMaxAngles * kNaRedLine);
   double* vw = (double*)take(8 * 4 * kNaMaxAngles);
   D.v = vw; D.w = vw + kNaMaxAngles; D.bL = vw + 2 * kNaMaxAngles; D.bR = vw + 3 * kNaMaxAngles;
   D.Swall = (double*)take(8 * 2 * kNaMaxAngles);
+  D.Swall2 = (double*)take(8 * 2 * kNaMaxAngles);
   double* small = (double*)take(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL));
   D.gH = small;
   D.gg = D.gH + (kMaxRestart + 1) * kMaxRestart;

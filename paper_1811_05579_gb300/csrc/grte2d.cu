@@ -608,6 +608,15 @@ __global__ void k2_rhs_pred(D2 D, const double* __restrict__ phi, double* __rest
   x[(int64_t)g.K * g.nc + c] = rn;
 }
 
+// The correction's flux (sigma_0/T^3): the vertex coefficients of Eq. dis-cor-marshak1 take
+// the multiplier V* = max(U*, 0)^{3/4} in place of the prediction's kappa = (T^n)^3;
+// kc is set to V* here for k2_vcoef, and k2_coef restores it at T^{n+1} for substep 2.
+__global__ void k2_vstar(D2 D) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= D.g.nc) return;
+  D.kc[c] = pow(fmax(D.Us[c], 0.0), 0.75);
+}
+
 // E*_k = rho + e_k, U* = (U^n + gamma rho)/(1 + gamma a c), rho* kept.
 __global__ void k2_finish_pred(D2 D, const double* __restrict__ x, double* __restrict__ Es) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1367,7 +1376,12 @@ static grte_status step2(grte2d_t h) {
   if (s != GRTE_OK) return s;
   h->stats.krylov_iters += its;
   tl_launches++, k2_finish_pred<<<gc, kThreads, 0, st>>>(D, h->x, h->Es);
-  // O* and the flux term of the temperature equation
+  // the flux term of the temperature equation: O from E* by the vertex map, with the
+  // prediction's coefficients (sigma(x)) or those of V* = (U*)^{3/4} (sigma_0/T^3)
+  if (g.kind == GRTE_SIGMA_T3) {
+    tl_launches++, k2_vstar<<<gc, kThreads, 0, st>>>(D);
+    tl_launches++, k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+  }
   tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
   tl_launches++, k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
   tl_launches++, k2_cellsum<double, C_FDIV><<<gc, kThreads, 0, st>>>(D, h->cv, h->tk, nullptr, D.Fdiv, nullptr);

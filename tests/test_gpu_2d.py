@@ -66,7 +66,7 @@ def test_checkerboard_marshak_one_step_stages(G):
     a = (5,)
     errs = {"U*": _rel(h.stage(0, a), info["Ustar"]), "rho*": _rel(h.stage(2, a), info["rho_star"]),
             "T": _rel(h.T(a), S1.T)}
-    Fd = info["Fdiv"]
+    Fd = info["Fcorr"]          # the flux of the temperature equation (see correction_flux)
     errs["Fdiv"] = float(np.max(np.abs(h.stage(1, a) - Fd)) / np.max(np.abs(Fd)))
     print("one step:", errs, "krylov iterations", h.stats(a)["krylov_iters"])
     # at dt = 0.5 dx and eps = 1e-3 (the edge of the paper's stable range for this
