@@ -155,7 +155,9 @@ grte_status grte_get_O(grte_t h, int inst, double* O, size_t len);           /* 
 /* Cell-centre intensities I(+v_k) = E + eps (O_j + O_{j+1})/2 and I(-v_k) = E - eps(...), [j][k]. */
 grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t len);
 /* Intermediate per-cell results of the last step: which = 0 U*, 1 F* =
- * sum_k w_k v_k (O*_{j+1,k} - O*_{j,k}), 2 rho*, 3 Newton iterations (as double). */
+ * sum_k w_k v_k (O*_{j+1,k} - O*_{j,k}), 2 rho*, 3 Newton iterations (as double),
+ * 4 the flux that correction substep 1 takes (sigma(x): F*; sigma_0/T^3: the flux of
+ * Eq. dis-cor-marshak1 at the predicted data with V* = max(U*,0)^{3/4}). */
 grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t len);
 /* Energy diagnostics of instance `inst` (FP64 sums on the device; Eq. energybalance and
  * Eq. semiconservative of Sec. 3, 1D): out[0] = sum_j dx (rho_j/c + Cv T_j) now;
@@ -248,7 +250,7 @@ grte_status grte_get_newton_samples(grte_t h, int inst, float* X, float* y, size
  *   E  device, nx*M doubles, line-major E[k*nx + j] (the device layout of grte.h);
  *   O  device, (nx+1)*M doubles, line-major O[k*(nx+1) + i].
  * No cudaMalloc, cudaFree or other allocating call is made: every work buffer is
- * carved from one static device array of 11,198,976 bytes (about 11.2 MB) that every GPU loading this
+ * carved from one static device array of 11,198,464 bytes (about 11.2 MB) that every GPU loading this
  * library holds until the process exits.  Limits: nx <= 4096, n_angle <= 32,
  * nx*n_angle <= 65536; larger sizes return GRTE_EINVAL.  The first call on a device
  * looks up the device address of that array (cudaGetSymbolAddress, with the device

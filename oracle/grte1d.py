@@ -497,11 +497,19 @@ def correction_flux(P, S, Es, Os, Us):
     flux with the multiplier V* = (U*)^{3/4} (node values the mean of the two cells,
     U* < 0 read as 0) in place of the prediction's K^n = (T^n)^3:
         O~_i = d*_i [eps^2 O^n_i/(c dt) - v (E*_i - E*_{i-1})/dx],
-        d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i)   (interior nodes),
-    walls Eq. bc-pre with E*.  This is the reading under which the correction's diffusion
-    limit carries (T^{n+1*})^3 as the remark closing Sec. 5 states (with K^n frozen at
-    T^n the two coincide only for sigma(x)); it is also the one that reproduces the
-    Marshak front of Sec. 6.5 at eps = 1e-5."""
+        d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i)   (interior nodes).
+    This is the reading under which the correction's diffusion limit carries
+    (T^{n+1*})^3 as the remark closing Sec. 5 states (with K^n frozen at T^n the two
+    coincide only for sigma(x)); it is also the one that reproduces the Marshak front of
+    Sec. 6.5 at eps = 1e-5.
+    Inflow walls (the paper gives Eq. dis-cor-marshak1 for the interior nodes only): the
+    wall node takes the prediction's wall value shifted by the change at the adjacent
+    node, O~_0 = O*_0 + (O~_1 - O*_1) (likewise at x = 1), so that the wall cell keeps the
+    prediction's net flux and the wall supplies what the corrected interior node draws.
+    Eq. bc-pre applied to O~ with the frozen E* would tie the wall inflow to O~_1 with
+    the opposite sign (the inflow falls as the interior draws more), which empties a
+    cold wall cell or freezes a hot one at the configured dt = dx/2 of the 128-cell
+    Marshak slab."""
     if P.kind == SIGMA_CONST:
         return flux_div(P, Os)
     N, M = P.N, P.M
@@ -516,8 +524,8 @@ def correction_flux(P, S, Es, Os, Us):
     O = np.zeros((N + 1, M))
     O[1:-1] = d[1:-1, None] * (eps ** 2 * S.O[1:-1] / (c * dt) - P.v[None, :] * (Es[1:] - Es[:-1]) / dx)
     if P.bc == "inflow":
-        O[0] = 2.0 / eps * (P.bL - Es[0]) - O[1]
-        O[N] = 2.0 / eps * (Es[N - 1] - P.bR) - O[N - 1]
+        O[0] = Os[0] + (O[1] - Os[1])
+        O[N] = Os[N] + (O[N - 1] - Os[N - 1])
     return flux_div(P, O)
 
 

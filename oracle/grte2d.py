@@ -495,7 +495,9 @@ def correction_flux(P, S, Es, Os, Us):
     """The flux the temperature equation of the correction takes from the predicted
     state (see grte1d.correction_flux): sigma(x) the prediction's own O*; sigma/T^3 the
     vertex map rebuilt with the multiplier V* = (U*)^{3/4} (vertex values the mean of
-    the four cells) in place of the prediction's K^n, applied to the predicted E*."""
+    the four cells) in place of the prediction's K^n, applied to the predicted E*; at
+    the inflow-wall vertices the prediction's value plus the change at the inner vertex
+    (the reading of grte1d.correction_flux for the walls)."""
     if P.kind == SIGMA_CONST:
         return flux_div(P, Os, Es)
     eps, c, dt = P.eps, P.c, P.dt
@@ -509,7 +511,50 @@ def correction_flux(P, S, Es, Os, Us):
         o = d * eps ** 2 / (c * dt) * S.O[:, k]
         Qk, qk = vertex_map(P, k, sp.diags(d) @ Dk, o)
         Oc[:, k] = Qk @ Es[:, k] + qk
-    return flux_div(P, Oc, Es)
+    # inflow-wall vertices: the prediction's value shifted by the change at the inner
+    # vertex (the indices clamped into the interior along the inflow axes), as in 1D
+    for j in range(P.Ny + 1):
+        for i in range(P.Nx + 1):
+            if _vertex_kind(P, i, j) not in ("x", "y", "corner"):
+                continue
+            ii = min(max(i, 1), P.Nx - 1) if P.bcx == "inflow" else i
+            jj = min(max(j, 1), P.Ny - 1) if P.bcy == "inflow" else j
+            v, vin = P.vert(i, j), P.vert(ii, jj)
+            Oc[v] = Os[v] + (Oc[vin] - Os[vin])
+    # a cell beside an inflow wall takes the part of its flux along that wall's normal
+    # from the prediction's O* (its wall side is Eq. bc-pre of its own E*, so with the
+    # wall value shifted as above the normal part equals the prediction's, as the 1D wall
+    # cell's flux does); the part along the wall reads O~
+    F = flux_div(P, Oc, Es)
+    for k in range(P.K):
+        F += P.w[k] * (_wall_normal_operator(P, k) @ (Os[:, k] - Oc[:, k]))
+    return F
+
+
+def _wall_normal_operator(P, k):
+    """The vertex terms of div_operator along the normal of each inflow wall, in the
+    cells beside that wall (nc x nv); zero elsewhere."""
+    rows, cols, vals = [], [], []
+    for q in range(P.Ny):
+        for p in range(P.Nx):
+            c = q * P.Nx + p
+            v00, v10, v01, v11 = P.vert(p, q), P.vert(p + 1, q), P.vert(p, q + 1), P.vert(p + 1, q + 1)
+            for axis, comp, h_, lo, hi in (("x", P.mu[k], P.dx, p == 0, p == P.Nx - 1),
+                                           ("y", P.eta[k], P.dy, q == 0, q == P.Ny - 1)):
+                if (P.bcx if axis == "x" else P.bcy) != "inflow" or not (lo or hi):
+                    continue
+                wlo = 0.0 if lo else -2.0
+                whi = 0.0 if hi else 2.0
+                if axis == "x":
+                    terms = ((v00, wlo), (v01, wlo), (v10, whi), (v11, whi))
+                else:
+                    terms = ((v00, wlo), (v10, wlo), (v01, whi), (v11, whi))
+                for vidx, wgt in terms:
+                    if wgt != 0.0:
+                        rows.append(c)
+                        cols.append(vidx)
+                        vals.append(wgt * comp / (2.0 * h_))
+    return sp.csr_matrix((vals, (rows, cols)), shape=(P.nc, P.nv))
 
 
 def correction_temperature(P, S, Fdiv, Ustar):

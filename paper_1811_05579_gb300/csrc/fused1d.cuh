@@ -632,22 +632,17 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   f_line_solve(sm, cl, G, par);
   const bool corr = FULL && I.kind == GRTE_SIGMA_T3;
   if (corr) {
-    // the correction's flux (see f_dstar): its rho part, and the data part of the cells
-    // that are not inflow wall cells (those take theirs in the wall block below)
+    // the correction's flux (see f_dstar) of the cells that are not inflow wall cells
+    // (those keep the prediction's flux: the wall node takes the prediction's value
+    // shifted by the change at the adjacent node): its rho and data parts
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
-    if (j < N) {
-      const int64_t g = G.co + j;
+    if (j < N && !(inflow && (j == 0 || j == N - 1))) {
       const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
                    xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
       const double dL = sm.dsd[t], dR = sm.dsd[t + 1];
-      const bool wl = inflow && j == 0, wr = inflow && j == N - 1;
-      const double mR = wl ? 2.0 : 1.0, mL = wr ? 2.0 : 1.0;
-      double fc = I.wv2 * (mR * dR * (xj - xr) + mL * dL * (xj - xl)) / I.dx + I.wv * D.cf.gbx[g] * xj;
-      if (wl) fc -= I.two_eps * I.bLflux;
-      if (wr) fc -= I.two_eps * I.bRflux;
-      if (!wl && !wr) fc += I.eps * I.eps / (I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
-      sm.flc[t] = fc;
+      sm.flc[t] = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) / I.dx +
+                  I.eps * I.eps / (I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
     } else {
       sm.flc[t] = 0.0;
     }
@@ -659,7 +654,7 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const int64_t jw = side == 0 ? 0 : N - 1;
       const int64_t tl = jw - G.c0;
       if (!(tl >= 0 && tl < kFS)) continue;
-      double sw = 0.0, swc = 0.0;
+      double sw = 0.0;
       if (k < G.M) {
         const double vd = sm.vkd[k], v2d = vd * vd;
         const int64_t g = G.co + jw;
@@ -684,29 +679,9 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
           const double ON1 = on - dl * vd * (ew - en);
           sw = sm.wvkd[k] * (I.two_eps * ew - 2.0 * ON1);
         }
-        if (corr) {
-          // the same wall row with the correction's node coefficient d*
-          const double ds = sm.dsd[ni - G.c0];
-          double onc = 0.0;
-          {
-            const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (N + 1);
-            onc = ds * I.eps * I.eps / (I.c * I.dt) * (double)Ok[ni];
-          }
-          if (side == 0) {
-            const double O1 = onc - ds / I.dx * vd * (en - ew);
-            swc = sm.wvkd[k] * (2.0 * O1 + I.two_eps * ew);
-          } else {
-            const double ON1 = onc - ds / I.dx * vd * (ew - en);
-            swc = sm.wvkd[k] * (I.two_eps * ew - 2.0 * ON1);
-          }
-        }
       }
       for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
       if (k == 0) sm.fl[tl] += sw;
-      if (corr) {
-        for (int o = 16; o > 0; o >>= 1) swc += __shfl_xor_sync(0xffffffffu, swc, o);
-        if (k == 0) sm.flc[tl] += swc;
-      }
     }
   }
   // e/o flux of every interior cell without the data part, summed over the angles by the
@@ -1054,7 +1029,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
       zv[t] = -R;
       D.Fs[g] = fl;
-      D.Fc[g] = (I.kind == GRTE_SIGMA_T3) ? sm.flc[t] : fl;
+      D.Fc[g] = (I.kind == GRTE_SIGMA_T3 && !(I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1))) ? sm.flc[t] : fl;
     } else {
       zv[t] = 0.0;
     }

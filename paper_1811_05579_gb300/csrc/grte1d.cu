@@ -109,7 +109,6 @@ struct Dev {
   // per-element work (bulk type)
   void *xb, *S, *F, *Rd, *onode;
   void* S2;        // per element: the correction's e/o flux part (sigma_0/T^3 data passes)
-  double* Swall2;  // its two inflow-wall contributions per (instance, angle), in double
   // preconditioner factors
   double *pF, *pRd, *pG, *pH, *gw, *pInv;
   // GMRES
@@ -473,28 +472,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_pred_line(Dev D, const void* 
     const double ON1 = (double)onode(N - 1) - dlx[N - 1] * v * (eR - eN2);
     D.Swall[2 * (I.ang_off + k) + 0] = w * v * (2.0 * O1 + two_eps * eL);
     D.Swall[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1);
-    if (corr) {
-      const double *dsx = D.cf.dsx + co, *ods = D.cf.ods + co;
-      const double O1c = ods[1] * (double)On[1] - dsx[1] * v * (e1 - eL);
-      const double ON1c = ods[N - 1] * (double)On[N - 1] - dsx[N - 1] * v * (eR - eN2);
-      D.Swall2[2 * (I.ang_off + k) + 0] = w * v * (2.0 * O1c + two_eps * eL);
-      D.Swall2[2 * (I.ang_off + k) + 1] = w * v * (two_eps * eR - 2.0 * ON1c);
-    }
   }
   if (corr) {
     R* S2k = (R*)D.S2 + eo;
     const R *dsxr = pick<R>(D.cf.dsx, D.fc.dsx) + co, *odsr = pick<R>(D.cf.ods, D.fc.ods) + co;
     for (int64_t j = threadIdx.x; j < N; j += NT) {
       auto Oc = [&](int64_t i) -> R { return odsr[i] * On[i] - dsxr[i] * vr * (xb[i] - xb[i - 1]); };
-      R val;
-      if (inflow && (j == 0 || j == N - 1)) {
-        val = R(0);                       // in Swall2
-      } else {
-        const R OR = (j + 1 <= N - 1) ? Oc(j + 1) : R(0);
-        const R OL = (j >= 1) ? Oc(j) : R(0);
-        val = OR - OL;
-      }
-      S2k[j] = wvr * val;
+      // (the inflow wall cells keep the prediction's flux: not read there)
+      const R OR = (j + 1 <= N - 1) ? Oc(j + 1) : R(0);
+      const R OL = (j >= 1) ? Oc(j) : R(0);
+      S2k[j] = wvr * (OR - OL);
     }
   }
 #pragma unroll 4
@@ -811,26 +798,18 @@ __device__ __forceinline__ R flux_sum_k(const Dev& D, const Inst& I, int64_t j) 
   return pick<R>(D.Frho, D.fc.Frho)[I.cell_off + j] + eo_sum<R>(D, I, j);
 }
 
-// The correction's flux at cell j (sigma_0/T^3, the node coefficients d* of the data pass
-// that just ran at the iterate x): its rho part
-//   wv2 [mR d*_{j+1} (x_j - x_{j+1}) + mL d*_j (x_j - x_{j-1})]/dx + wv gbx x_j
-//   (minus 2/eps sum_k w_k v_k b at the inflow walls; m = 2 on the inflow wall sides)
-// plus the per-angle e/o parts S2 (in double), or at the inflow walls the Swall2 sums.
+// The correction's flux at a cell j that is not an inflow wall cell (sigma_0/T^3, the
+// node coefficients d* of the data pass that just ran at the iterate x): its rho part
+//   wv2 [d*_{j+1} (x_j - x_{j+1}) + d*_j (x_j - x_{j-1})]/dx
+// plus the per-angle e/o parts S2 (in double).  The inflow wall cells keep the
+// prediction's flux (the wall node takes the prediction's value shifted by the change at
+// the adjacent node).
 template <typename R>
 __device__ __forceinline__ double corr_flux_sum(const Dev& D, const Inst& I, int64_t j, const double* x) {
   const int64_t N = I.N, co = I.cell_off;
-  const bool inflow = I.bc == GRTE_BC_INFLOW;
   const double xj = x[j], xl = j > 0 ? x[j - 1] : 0.0, xr = j < N - 1 ? x[j + 1] : 0.0;
   const double dR = j < N - 1 ? D.cf.dsx[co + j + 1] : 0.0, dL = D.cf.dsx[co + j];
-  const double mR = (inflow && j == 0) ? 2.0 : 1.0, mL = (inflow && j == N - 1) ? 2.0 : 1.0;
-  double f = I.wv2 * (mR * dR * (xj - xr) + mL * dL * (xj - xl)) + I.wv * D.cf.gbx[co + j] * xj;
-  if (inflow && j == 0) f -= I.two_eps * I.bLflux;
-  if (inflow && j == N - 1) f -= I.two_eps * I.bRflux;
-  if (wall_cell(I, j)) {
-    const int side = (j == 0) ? 0 : 1;
-    for (int k = 0; k < I.M; ++k) f += D.Swall2[2 * (I.ang_off + k) + side];
-    return f;
-  }
+  const double f = I.wv2 * (dR * (xj - xr) + dL * (xj - xl));
   const R* S = (const R*)D.S2 + I.elem_off + j;
   double acc = 0.0;
   for (int k = 0; k < I.M; ++k) acc += (double)S[(int64_t)k * N];
@@ -885,7 +864,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kTriThreads) k_gmr
       const double Rj = alpha[j] * x[j] - kcd[j] * D.rho_n[co + j] - sac[j] * D.U[co + j] + kdx[j] * fl;
       r[j] = -Rj;
       D.Fs[co + j] = fl;                    // F* of the current iterate (final at convergence)
-      D.Fc[co + j] = (I.kind == GRTE_SIGMA_T3) ? corr_flux_sum<R>(D, I, j, x) : fl;
+      D.Fc[co + j] = (I.kind == GRTE_SIGMA_T3 && !wall_cell(I, j)) ? corr_flux_sum<R>(D, I, j, x) : fl;
     }
     // per-cell weights of the stopping test: the preconditioned residual relative to
     // |x_j| (floor wfloor max|x|: 1e-13 in FP64, 1e-8 with binary32 line solves), so
@@ -1848,7 +1827,6 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   AL(D.cf.od, nc); AL(D.cf.dlx, nc); AL(D.cf.kcd, nc); AL(D.cf.kdx, nc); AL(D.cf.sac, nc);
   AL(D.cf.ralpha, nc); AL(D.cf.ratio, nc); AL(D.cf.fR, nc); AL(D.cf.fL, nc); AL(D.cf.gbx, nc);
   AL(D.cf.dsx, nc); AL(D.cf.ods, nc);
-  AL(D.Swall2, 2 * na);
   if (mixed) {
     CellF& f = D.fc;
     AL(f.A, nc); AL(f.gl, nc); AL(f.gu, nc); AL(f.gb, nc); AL(f.od, nc); AL(f.dlx, nc); AL(f.kcd, nc);
@@ -2488,8 +2466,8 @@ grte_status grte_get_T(grte_t h, int inst, double* T, size_t len) {
 grte_status grte_get_stage(grte_t h, int inst, int which, double* out, size_t len) {
   if (!h) return GRTE_EINVAL;
   const double* src = which == 0 ? h->D.Us : which == 1 ? h->D.Fs : which == 2 ? h->D.rho_s
-                    : which == 3 ? h->D.newton_its : nullptr;
-  if (!src) return fail(h, GRTE_EINVAL, "which must be 0..3");
+                    : which == 3 ? h->D.newton_its : which == 4 ? h->D.Fc : nullptr;
+  if (!src) return fail(h, GRTE_EINVAL, "which must be 0..4");
   return get_cells(h, inst, src, out, len);
 }
 
@@ -2733,16 +2711,16 @@ constexpr int64_t kNaBytes =
     na_round(8 * (5 * kNaMaxElems + kNaMaxAngles * kNaFacLine)) +   // line factors
     na_round(8 * kNaMaxNodeElems) +                                 // node scratch
     na_round(8 * kNaMaxAngles * kNaRedLine) +                        // line reduced systems
-    na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) * 2 + // v, w, bL, bR; Swall, Swall2
+    na_round(8 * 4 * kNaMaxAngles) + na_round(8 * 2 * kNaMaxAngles) +   // v, w, bL, bR; Swall
     na_round(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL)) +
     na_round(4 * 16) + na_round(sizeof(Inst)) + na_round(sizeof(Line) * kNaMaxAngles) + na_round(8);
 }  // namespace grte
 
-// Work memory of grte_step1d_noalloc: kNaBytes = 11,198,976 bytes (about 11.2 MB),
+// Work memory of grte_step1d_noalloc: kNaBytes = 11,198,464 bytes (about 11.2 MB),
 // held by every GPU that loads the library until the process exits.  Calls share it
 // (see include/grte.h, which states the same figure; the assertion keeps the two in
 // step when the layout changes).
-static_assert(grte::kNaBytes == 11198976, "no-alloc work memory size changed: update the documented figure");
+static_assert(grte::kNaBytes == 11198464, "no-alloc work memory size changed: update the documented figure");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[grte::kNaBytes];
 static void* g_noalloc_base[64];   // device address of g_noalloc_scratch, per device
 
@@ -2883,7 +2861,6 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   double* vw = (double*)take(8 * 4 * kNaMaxAngles);
   D.v = vw; D.w = vw + kNaMaxAngles; D.bL = vw + 2 * kNaMaxAngles; D.bR = vw + 3 * kNaMaxAngles;
   D.Swall = (double*)take(8 * 2 * kNaMaxAngles);
-  D.Swall2 = (double*)take(8 * 2 * kNaMaxAngles);
   double* small = (double*)take(8 * ((kMaxRestart + 1) * kMaxRestart + 3 * kMaxRestart + 8 + kCL * 2 * 2 * kCL));
   D.gH = small;
   D.gg = D.gH + (kMaxRestart + 1) * kMaxRestart;

@@ -249,6 +249,23 @@ __global__ void k2_vertex(D2 D, CV<S> cv, UFieldT<S> u, S* __restrict__ V) {
   V[t] = O_at<S, DATA>(D, cv, u, k, i, j);
 }
 
+// The correction's flux (sigma_0/T^3) at the inflow walls: each inflow-wall vertex takes
+// the prediction's value shifted by the change at its inner vertex (the indices clamped
+// into the interior along the inflow axes), V = Vp + (V_in - Vp_in); Vp holds the
+// prediction's vertex values.  Inner vertices are never wall vertices (Nx, Ny >= 2).
+__global__ void k2_wallshift(D2 D, double* __restrict__ V, const double* __restrict__ Vp) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nv) return;
+  const int64_t k = t / g.nv, v = t - k * g.nv;
+  const int j = (int)(v / (g.Nx + 1)), i = (int)(v - (int64_t)j * (g.Nx + 1));
+  if (vkind(g, i, j) == 0) return;
+  const int ii = g.bcx == GRTE_BC_INFLOW ? min(max(i, 1), g.Nx - 1) : i;
+  const int jj = g.bcy == GRTE_BC_INFLOW ? min(max(j, 1), g.Ny - 1) : j;
+  const int64_t vin = k * g.nv + (int64_t)jj * (g.Nx + 1) + ii;
+  V[t] = Vp[t] + (V[vin] - Vp[vin]);
+}
+
 enum { C_MV_PRED = 0, C_MV_CORR = 1, C_DIVK = 2, C_FDIV = 3 };
 
 // Side weights of cell (p, q) for pair k: the streaming derivative of O at the cell is
@@ -323,6 +340,33 @@ __device__ __forceinline__ S cell_div(const D2& D, const CV<S>& cv, const S* __r
   if (u.any()) div += cs.ed * u.at(k, (int)c);
   if constexpr (DATA) div += cs.bt;
   return div;
+}
+
+// The correction's flux per pair at cell c (sigma_0/T^3): cell_div over V, except that a
+// cell beside an inflow wall takes the part along that wall's normal from the
+// prediction's vertex values Vn (so that, as in 1D, its flux across the wall and the
+// opposite side is the prediction's; the part along the wall reads V).
+__global__ void k2_fdiv_corr(D2 D, CV<double> cv, const double* __restrict__ V, const double* __restrict__ Vn,
+                             UField u, double* __restrict__ tk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nc) return;
+  const int tt = (int)t, nc = (int)g.nc;
+  const int k = tt / nc, ci = tt - k * nc;
+  const int q = ci / g.Nx, p = ci - q * g.Nx;
+  const bool xw = g.bcx == GRTE_BC_INFLOW && (p == 0 || p == g.Nx - 1);
+  const bool yw = g.bcy == GRTE_BC_INFLOW && (q == 0 || q == g.Ny - 1);
+  if (!xw && !yw) {
+    tk[t] = cell_div<double, true>(D, cv, V, u, k, ci);
+    return;
+  }
+  const int64_t v00 = (int64_t)q * (g.Nx + 1) + p, v10 = v00 + 1, v01 = v00 + g.Nx + 1, v11 = v01 + 1;
+  const double* Vx = (xw ? Vn : V) + (int64_t)k * g.nv;
+  const double* Vy = (yw ? Vn : V) + (int64_t)k * g.nv;
+  const CellSides<double> cs = cell_sides<double>(D, cv, k, p, q);
+  tk[t] = cv.mu[k] * cv.h2x * (cs.wL * (Vx[v00] + Vx[v01]) + cs.wR * (Vx[v10] + Vx[v11])) +
+          cv.eta[k] * cv.h2y * (cs.wB * (Vy[v00] + Vy[v10]) + cs.wT * (Vy[v01] + Vy[v11])) +
+          cs.ed * u.at(k, ci) + cs.bt;
 }
 
 // Cell pass over the vertex values V (computed from the same field u, with the data
@@ -1379,11 +1423,21 @@ static grte_status step2(grte2d_t h) {
   // the flux term of the temperature equation: O from E* by the vertex map, with the
   // prediction's coefficients (sigma(x)) or those of V* = (U*)^{3/4} (sigma_0/T^3)
   if (g.kind == GRTE_SIGMA_T3) {
+    // the prediction's vertex values (the Krylov basis is free until the correction's
+    // solve: it holds (m+1)(K+1) nc >= K nv values), then those of V*; the inflow walls
+    // shifted (k2_wallshift) and the wall-normal parts of the wall cells taken from the
+    // prediction's (k2_fdiv_corr)
+    double* Vp = h->Kbasis;
+    tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, Vp);
     tl_launches++, k2_vstar<<<gc, kThreads, 0, st>>>(D);
     tl_launches++, k2_vcoef<<<gv, kThreads, 0, st>>>(D);
+    tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
+    tl_launches++, k2_wallshift<<<gvk, kThreads, 0, st>>>(D, h->V, Vp);
+    tl_launches++, k2_fdiv_corr<<<gck, kThreads, 0, st>>>(D, h->cv, h->V, Vp, UField{h->Es, nc, nullptr}, h->tk);
+  } else {
+    tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
+    tl_launches++, k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
   }
-  tl_launches++, k2_vertex<double, true><<<gvk, kThreads, 0, st>>>(D, h->cv, UField{h->Es, nc, nullptr}, h->V);
-  tl_launches++, k2_cell<double, C_FDIV, true><<<gck, kThreads, 0, st>>>(D, h->cv, h->V, UField{h->Es, nc, nullptr}, nullptr, nullptr, nullptr, h->tk);
   tl_launches++, k2_cellsum<double, C_FDIV><<<gc, kThreads, 0, st>>>(D, h->cv, h->tk, nullptr, D.Fdiv, nullptr);
   if (D.use_guess || D.log_samples) tl_launches++, k2_newton_feat<<<gc, kThreads, 0, st>>>(D);
   if (D.use_guess) {
