@@ -193,6 +193,13 @@ def run_reference(args, cfg):
     print(json.dumps(line))
 
 
+# statuses a 1D step may end with and still be measured: 5 (cells whose correction
+# right-hand side reached R <= 0) and 4 (a prediction solve that ran its restart cycles
+# without meeting the tolerance; the slab runs with sigma_0 = 1, eps <= 1e-2 are unstable
+# at dt = dx/2 and their mixed-precision solves can end so)
+ALLOW1D = (4, 5)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -270,7 +277,7 @@ def main():
 
     for _ in range(args.warmup):
         h.step(1)
-    h.sync(allow=(5,))
+    h.sync(allow=ALLOW1D)
     tune = h.tuning()
 
     def barrier():
@@ -292,7 +299,7 @@ def main():
         h.step(1)                     # one CUDA graph launch per step (after the first step)
         ends[k].record(stream)
         launches += h.last_launches()
-        st = h.stats(allow=(5,))
+        st = h.stats(allow=ALLOW1D)
         kry_its += st["krylov_iters"]
         kry_cycles += st["krylov_cycles"]
     barrier()
@@ -315,7 +322,7 @@ def main():
     # temperature out (D2H), timed on the host clock with the stream synchronised
     host_state = []
     for i, r in enumerate(runs):
-        host_state.append((h.T(i, allow=(5,)), h.E(i, allow=(5,)), h.O(i, allow=(5,))))
+        host_state.append((h.T(i, allow=ALLOW1D), h.E(i, allow=ALLOW1D), h.O(i, allow=ALLOW1D)))
     h2d = sum(T.nbytes + E.nbytes + O.nbytes for T, E, O in host_state)
     d2h = sum(T.nbytes for T, _, _ in host_state)
     ke = min(args.steps, 5)
@@ -326,7 +333,7 @@ def main():
             h.set_state(i, T, E, O)
         h.step(1)
         for i in range(len(runs)):
-            h.T(i, allow=(5,))
+            h.T(i, allow=ALLOW1D)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     e2e_val = updates_per_step * ke / te
@@ -357,11 +364,29 @@ def main():
             t64 += e0.elapsed_time(e1)
         errs = []
         for i in range(len(runs)):
-            a_ = hm.T(i, allow=(5,))
-            b_ = hd.T(i, allow=(5,))
+            a_ = hm.T(i, allow=ALLOW1D)
+            b_ = hd.T(i, allow=ALLOW1D)
             errs.append(float(np.max(np.abs(a_ - b_) / np.maximum(np.abs(b_), 1e-300))))
+        # one step of each form from the FP64 state reached: the error of the precision
+        # itself (over a trajectory an unstable run amplifies it step by step)
+        snap = [(hd.T(i, allow=ALLOW1D), hd.E(i, allow=ALLOW1D), hd.O(i, allow=ALLOW1D)) for i in range(len(runs))]
+        h1 = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
+        h2 = G.Grte(specs, precision=G.FP64, stream=stream.cuda_stream)
+        for i, (T_, E_, O_) in enumerate(snap):
+            h1.set_state(i, T_, E_, O_)
+            h2.set_state(i, T_, E_, O_)
+        h1.step(1)
+        h2.step(1)
+        errs1 = []
+        for i in range(len(runs)):
+            a_ = h1.T(i, allow=ALLOW1D)
+            b_ = h2.T(i, allow=ALLOW1D)
+            errs1.append(float(np.max(np.abs(a_ - b_) / np.maximum(np.abs(b_), 1e-300))))
+        h1.close()
+        h2.close()
         cmp = {"fp64_value": updates_per_step * args.steps / (t64 * 1e-3), "fp64_ms_per_step": t64 / args.steps,
-               "t_max_rel_err_vs_fp64": max(errs), "t_rel_err_per_run": errs,
+               "t_max_rel_err_one_step": max(errs1), "t_rel_err_one_step_per_run": errs1,
+               "t_max_rel_err_trajectory": max(errs), "t_rel_err_trajectory_per_run": errs,
                "steps_compared": args.warmup + args.steps}
         hd.close()
         hm.close()
@@ -471,7 +496,9 @@ def main():
                 "kernel_profile": "event pairs around every launch over %d further eager steps of the same workload" % kp,
                 "krylov_iters_per_step": kry_its / args.steps / len(runs),
                 "krylov_cycles_per_step": kry_cycles / args.steps,
-                "line_tuning": {"threads": tune[0], "candidates_ms": tune[1], "smem": bool(h.stats(allow=(5,))["line_smem"])},
+                "line_tuning": {"threads": tune[0], "candidates_ms": tune[1], "smem": bool(h.stats(allow=ALLOW1D)["line_smem"])},
+                "statuses_seen": [n_ for b_, n_ in ((4, "ENONCONV"), (5, "R<=0 cells"))
+                                  if h.stats(allow=ALLOW1D)["status_flags"] & (1 << b_)],
                 "clocks": clk}
         if cmp is not None:
             line["vs_fp64"] = cmp

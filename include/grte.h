@@ -78,7 +78,11 @@ typedef struct {
                             is <= rtol |rho_j| (1e-13), or when a restart cycle stalls below
                             1e-9 (the rounding floor of the residual).  MIXED: rtol is
                             floored at 1e-9, cells below 1e-6 max|rho| are measured against
-                            that floor, and a second restart below 1e-4 ends the solve       */
+                            that floor, and a second restart below 1e-4 ends the solve; in
+                            the one-kernel solve (solver1d) two restart cycles in a row that
+                            each reduce the residual by less than 10% above that level end
+                            it with GRTE_ENONCONV (the binary32 rounding floor lies above the
+                            tolerance there)                                                   */
   int krylov_restart;    /* GMRES restart length (10)                                        */
   int krylov_maxcycles;  /* GMRES restart cycles per step before GRTE_ENONCONV (30)           */
   int newton_maxit;      /* per-cell Newton iterations before GRTE_ENONCONV (60)             */

