@@ -14,7 +14,11 @@
   wall temperature (Sec. 6.5: "captures the correct propagation front").
 - Uniform first-order self-convergence (Sec. 6.2, Eq. IC000 and Eq. error): sigma = 1,
   t = 0.1, dt = 0.1 dx, eps in {1, 1e-3, 1e-5}, dx = 1/25 .. 1/100 against the grid of
-  half the spacing."""
+  half the spacing.
+- The two readings of the correction's flux for sigma/T^3: the flux of Eq.
+  dis-cor-marshak1 with V* (the front pin fails with the prediction's own flux, planted),
+  and its inflow-wall nodes (the 128-cell Marshak slab stays bounded after its start
+  transient; Eq. bc-pre applied to the corrected wall nodes, planted, does not)."""
 import math
 
 import numpy as np
@@ -157,3 +161,54 @@ def test_front_pin_catches_the_frozen_K_flux(monkeypatch):
     Td = _limit(N, 0.1, 0.02 / N, 1e-4)
     xf, xd = dif.front_position(S.T, 0.01), dif.front_position(Td, 0.01)
     assert abs(xf - xd) > 10 * 0.01 or S.T.max() > 1.5
+
+
+def _bcpre_wall_flux(P, S, Es, Os, Us):
+    """A copy of the correction's flux with the inflow-wall nodes from Eq. bc-pre applied
+    to the corrected flux and the predicted E* (the wall reading the oracle does not
+    take)."""
+    N = P.N
+    eps, c, dt, dx = P.eps, P.c, P.dt, P.dx
+    V = np.maximum(Us, 0.0) ** 0.75
+    Vn = 0.5 * (V[:-1] + V[1:])
+    sn = P.node_sig()[1:-1]
+    d = Vn / (Vn * eps ** 2 / (c * dt) + sn)
+    O = np.zeros((N + 1, P.M))
+    O[1:-1] = d[:, None] * (eps ** 2 * S.O[1:-1] / (c * dt) - P.v[None, :] * (Es[1:] - Es[:-1]) / dx)
+    O[0] = 2.0 / eps * (P.bL - Es[0]) - O[1]
+    O[N] = 2.0 / eps * (Es[N - 1] - P.bR) - O[N - 1]
+    return g.flux_div(P, O)
+
+
+def _marshak128(monkeypatch=None):
+    """The 128-cell Marshak slab at its configured dt = dx/2: eps = 1e-3, sigma = 1/T^3,
+    T_in = 1e-2, inflow 1 on the left, vacuum on the right, t = 0.5 (128 steps)."""
+    N = 128
+    v, w = gauss_legendre_half(16)
+    P = g.Problem(N=N, v=v, w=w, sig=1.0, eps=1e-3, dt=0.5 / N, kind="t3", bL=np.ones(v.size), bR=np.zeros(v.size))
+    S = g.equilibrium_state(P, np.full(N, 1e-2))
+    worst, zeros = 0.0, 0
+    for n in range(128):
+        S = g.step(P, S)
+        if n >= 30:                         # after the start transient at the hot wall
+            worst = max(worst, S.T.max())
+            zeros = max(zeros, int(np.sum(S.T == 0.0)))
+    return S, worst, zeros
+
+
+def test_corrected_flux_wall_reading_keeps_the_marshak_slab_bounded(monkeypatch):
+    """The wall reading of the correction's flux (the wall node shifted by the change at
+    the adjacent node, so the wall cell keeps F*): on the 128-cell Marshak slab at its
+    dt = dx/2, once the start transient at the hot wall has passed (~25 steps; T reaches
+    4.7 in the first step) the temperature stays below the wall temperature 1 (maximum
+    principle of the limit equation), no cell empties, and the profile behind the front
+    decreases monotonically.  The same scheme with Eq. bc-pre
+    applied to the corrected wall nodes, planted through a copy of the flux, empties the
+    wall cell and overshoots to ~4.7 (the behaviour that decided the reading)."""
+    S, worst, zeros = _marshak128()
+    assert worst <= 1.0 and zeros == 0, (worst, zeros)
+    front = int(dif.front_position(S.T, 1.0 / S.T.size) * S.T.size)
+    assert np.all(np.diff(S.T[: front - 1]) <= 1e-12)
+    monkeypatch.setattr(g, "correction_flux", _bcpre_wall_flux)
+    S2, worst2, zeros2 = _marshak128()
+    assert worst2 > 2.0 or zeros2 > 0, (worst2, zeros2)

@@ -65,9 +65,14 @@ def test_noalloc_step_matches_handle_step_twice(nx, nv, eps, bcname, nsteps, opt
         Tn = Td.cpu().numpy()
         En = Ed.cpu().numpy().T
         On = Od.cpu().numpy().T
-        errT = np.max(np.abs(Tn - Th) / np.maximum(Th, 1e-300))
+        # per-cell tolerance of the parity tests: 1e-12, in the two wall cells 1e-12 + 4e-15/eps
+        # (there the wall rows turn a rounding difference into one of O that grows like 1/eps)
+        tol = np.full(N, 1e-12)
+        if bcname == "inflow":
+            tol[0] = tol[-1] = 1e-12 + 4e-15 / eps
+        errT = np.max(np.abs(Tn - Th) / np.maximum(Th, 1e-300) / tol) * 1e-12
         # E = a c U + Eh: rounding relative to |E| + a c U (E can be a small difference)
-        errE = np.max(np.abs(En - Eh) / np.maximum(np.abs(Eh) + (Th ** 4)[:, None], 1e-300))
+        errE = np.max(np.abs(En - Eh) / np.maximum(np.abs(Eh) + (Th ** 4)[:, None], 1e-300) / tol[:, None]) * 1e-12
         print("noalloc nx=%d M=%d %s call %d: T %.2e E %.2e" % (N, M, bcname, call, errT, errE))
         assert errT < 1e-12, call
         assert errE < 1e-12, call
