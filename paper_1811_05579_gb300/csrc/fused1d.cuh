@@ -8,7 +8,10 @@
 //                  F_j = sum_k w_k v_k (O_{j+1,k} - O_{j,k}),
 // solved for rho by restarted GMRES left-preconditioned by the single-effective-angle Schur
 // operator P = alpha + Gbar (A + Gbar)^{-1} beta (Gbar = sum_k w_k G_k, beta = A - alpha).
-// Its outputs are the converged rho* (D.gx) and F* (D.Fs), read by the Newton kernel.
+// Its outputs are the converged rho* (D.gx), F* (D.Fs) and the flux the temperature
+// equation takes (D.Fc: for sigma_0/T^3 the flux of Eq. dis-cor-marshak1 with the node
+// coefficients of V* = max(U*, 0)^{3/4} at the converged iterate, the inflow wall cells
+// keeping F*; for sigma(x) F* itself), read by the Newton kernel.
 //
 // How it runs: one thread-block cluster of Q CTAs per instance (Q in {1,2,4,8,16}), CTA q
 // owning the 512-cell slice [512 q, 512 q + 512) (cells past nx are decoupled identity rows).
