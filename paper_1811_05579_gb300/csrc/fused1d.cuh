@@ -60,11 +60,12 @@ struct FSmem {
   float xlr[2][32];                                     // e at c0 - 1 and at c0 + kFS, per angle
   float vk[32], v2k[32], wvk[32];                       // per-angle constants (0 past M)
   double vkd[32], wvkd[32];
+  double wib[2][32], wgn[2][32], won[2][32], wdl[2];   // inflow wall rows (f_load_cells)
   double fl[kFS];                                       // flux sums of the last pass
   double fdat[kFS];                                     // data part of the flux (data passes)
   // the correction's flux (sigma_0/T^3): node coefficients d* of V* = (U*)^{3/4} at the
   // nodes c0 + t (t = 0..kFS), the node moments Om = sum_k w_k v_k O^n, the flux per cell
-  double dsd[kFS + 1], Om[kFS + 1], flc[kFS];
+  double Om[kFS + 1], flc[kFS];
   double pu[kFS];                                       // preconditioner solution (slice)
   // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
   // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
@@ -408,6 +409,22 @@ __device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
     sm.wvk[k] = (float)(w * v);
     sm.vkd[k] = v;
     sm.wvkd[k] = w * v;
+    // inflow wall rows of this slice (per angle, fixed for the solve): 1/b of the wall
+    // row, its neighbour coefficient over b, and o^n at the node next to the wall
+    if (I.bc == GRTE_BC_INFLOW) {
+      for (int side = 0; side < 2; ++side) {
+        const int64_t jw = side == 0 ? 0 : G.N - 1;
+        if (!(jw >= G.c0 && jw < G.c0 + kFS)) continue;
+        const int64_t g = G.co + jw, ni = side == 0 ? 1 : G.N - 1;
+        const double v2 = v * v;
+        const double bw = D.cf.A[g] + v2 * (D.cf.gl[g] + D.cf.gu[g]) + v * D.cf.gb[g];
+        sm.wib[side][k] = ka ? 1.0 / bw : 0.0;
+        sm.wgn[side][k] = ka ? v2 * (side == 0 ? D.cf.gu[g] : D.cf.gl[g]) / bw : 0.0;
+        const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (G.N + 1);
+        sm.won[side][k] = ka ? (double)(D.fc.od[G.co + ni] * Ok[ni]) : 0.0;
+        if (k == 0) sm.wdl[side] = D.cf.dlx[G.co + ni];
+      }
+    }
   }
   __syncthreads();
 }
@@ -431,22 +448,27 @@ __device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
   return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
 }
 
-// Node coefficient of the correction's flux (sigma_0/T^3, Eq. dis-cor-marshak1 with the
-// predicted data) at interior node i, for the iterate rho = X:
-//   d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i),  V*_i = (V*_{i-1/2} + V*_{i+1/2})/2,
-//   V* = max(U*, 0)^{3/4},  U* = (U^n + gam rho)/(1 + gam a c)  (Eq. dis-pre3),
-// sig_i the harmonic node mean; 0 at the wall nodes and past the grid.
-__device__ double f_dstar(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t i) {
-  if (i < 1 || i > G.N - 1) return 0.0;
-  const int64_t gl = G.co + i - 1, gr = G.co + i;
-  const double ac = I.a * I.c;
-  const double ul = (D.U[gl] + D.cf.gam[gl] * f_x<true>(X, G, i - 1)) / (1.0 + D.cf.gam[gl] * ac);
-  const double ur = (D.U[gr] + D.cf.gam[gr] * f_x<true>(X, G, i)) / (1.0 + D.cf.gam[gr] * ac);
-  const double vn = 0.5 * (pow(fmax(ul, 0.0), 0.75) + pow(fmax(ur, 0.0), 0.75));
-  const double sl = D.sig[gl], sr = D.sig[gr];
-  const double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
-  const double den = vn * I.eps * I.eps / (I.c * I.dt) + sn;
-  return den > 0.0 ? vn / den : 0.0;
+// The multiplier of the correction's flux (sigma_0/T^3, Eq. dis-cor-marshak1 with the
+// predicted data) in cell i for the iterate rho = X:
+//   V* = max(U*, 0)^{3/4} = sqrt(u sqrt(u)),  U* = (U^n + gam rho)/(1 + gam a c)  (Eq. dis-pre3),
+// in binary32 (it scales binary32 flux parts; one per cell and full pass).
+__device__ __forceinline__ float f_vstar(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t i) {
+  const int64_t g = G.co + i;
+  const float gam = (float)D.cf.gam[g];
+  const float u = fmaxf(((float)D.U[g] + gam * (float)f_x<true>(X, G, i)) * __frcp_rn(1.0f + gam * (float)(I.a * I.c)), 0.0f);
+  return sqrtf(u * sqrtf(u));
+}
+
+// Node coefficient of the correction's flux at node i from the multipliers of its two
+// cells: d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i), V*_i the mean of the two cells, sig_i
+// their harmonic mean; 0 at the wall nodes and past the grid.
+__device__ __forceinline__ float f_dnode(const Dev& D, const Inst& I, const FGeo& G, int64_t i, float vl, float vr) {
+  if (i < 1 || i > G.N - 1) return 0.0f;
+  const float sl = (float)D.sig[G.co + i - 1], sr = (float)D.sig[G.co + i];
+  const float sn = (sl > 0.0f && sr > 0.0f) ? 2.0f * sl * sr * __frcp_rn(sl + sr) : 0.0f;
+  const float vn = 0.5f * (vl + vr);
+  const float den = vn * (float)(I.eps * I.eps / (I.c * I.dt)) + sn;
+  return den > 0.0f ? vn * __frcp_rn(den) : 0.0f;
 }
 
 template <bool FULL>
@@ -487,20 +509,11 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     // (here: data passes, and the inflow wall cells of Krylov passes, whose rho part
     // cancels against the e/o wall sum to O(eps), both carrying the factor 2/eps)
     sm.fl[t] = fr;
-    if (FULL && I.kind == GRTE_SIGMA_T3) {
-      // d* at this cell's left node (and, for the last thread, at the slice's right end)
-      sm.dsd[t] = f_dstar(D, I, G, X, j);
-      if (t == kFS - 1) sm.dsd[kFS] = f_dstar(D, I, G, X, j + 1);
-    }
   } else {
     sm.P1[t] = 0.0f;
     sm.P2[t] = 0.0f;
     sm.P3[t] = 0.0f;
     sm.fl[t] = 0.0;
-    if (FULL) {
-      sm.dsd[t] = 0.0;
-      if (t == kFS - 1) sm.dsd[kFS] = 0.0;
-    }
   }
 }
 
@@ -634,16 +647,28 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   __syncthreads();
   f_line_solve(sm, cl, G, par);
   const bool corr = FULL && I.kind == GRTE_SIGMA_T3;
+  float* const vst = &sm.ra[0][0];   // kFS + 2 cell values
+  float* const dsd = &sm.rb[0][0];   // kFS + 1 node values
   if (corr) {
-    // the correction's flux (see f_dstar) of the cells that are not inflow wall cells
-    // (those keep the prediction's flux: the wall node takes the prediction's value
-    // shifted by the change at the adjacent node): its rho and data parts
+    // the correction's flux (f_vstar, f_dnode) of the cells that are not inflow wall
+    // cells (those keep the prediction's flux: the wall node takes the prediction's value
+    // shifted by the change at the adjacent node): node coefficients, then its rho and
+    // data parts
+    // (V* and d* live in the reduced-system arrays, dead after the line solve until the
+    // next pass)
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
+    vst[t + 1] = j < N ? f_vstar(D, I, G, X, j) : 0.0f;
+    if (t == 0) vst[0] = (j > 0 && j <= N) ? f_vstar(D, I, G, X, j - 1) : 0.0f;
+    if (t == kFS - 1) vst[kFS + 1] = j + 1 < N ? f_vstar(D, I, G, X, j + 1) : 0.0f;
+    __syncthreads();
+    dsd[t] = f_dnode(D, I, G, j, vst[t], vst[t + 1]);
+    if (t == kFS - 1) dsd[kFS] = f_dnode(D, I, G, j + 1, vst[kFS], vst[kFS + 1]);
+    __syncthreads();
     if (j < N && !(inflow && (j == 0 || j == N - 1))) {
       const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
                    xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
-      const double dL = sm.dsd[t], dR = sm.dsd[t + 1];
+      const double dL = dsd[t], dR = dsd[t + 1];
       sm.flc[t] = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) / I.dx +
                   I.eps * I.eps / (I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
     } else {
@@ -659,22 +684,14 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       if (!(tl >= 0 && tl < kFS)) continue;
       double sw = 0.0;
       if (k < G.M) {
-        const double vd = sm.vkd[k], v2d = vd * vd;
-        const int64_t g = G.co + jw;
-        const double bw = D.cf.A[g] + v2d * (D.cf.gl[g] + D.cf.gu[g]) + vd * D.cf.gb[g];
+        const double vd = sm.vkd[k];
         // neighbour value (float solution) and the node term next to the wall
         const int64_t jn = side == 0 ? 1 : N - 2;
         const int64_t tn = jn - G.c0;
         const double en = (tn >= 0) ? (double)sm.x[tn][k] : (double)sm.xlr[0][k];
-        const double ew = side == 0 ? (sm.wall[0][k] + v2d * D.cf.gu[g] * en) / bw
-                                    : (sm.wall[1][k] + v2d * D.cf.gl[g] * en) / bw;
-        const int64_t ni = side == 0 ? 1 : N - 1;
-        double on = 0.0;
-        if (FULL) {
-          const float* Ok = (const float*)D.O + I.nelem_off + (int64_t)k * (N + 1);
-          on = (double)(D.fc.od[G.co + ni] * Ok[ni]);
-        }
-        const double dl = D.cf.dlx[G.co + ni];
+        const double ew = sm.wall[side][k] * sm.wib[side][k] + sm.wgn[side][k] * en;
+        const double on = FULL ? sm.won[side][k] : 0.0;
+        const double dl = sm.wdl[side];
         if (side == 0) {
           const double O1 = on - dl * vd * (en - ew);
           sw = sm.wvkd[k] * (2.0 * O1 + I.two_eps * ew);
@@ -702,8 +719,8 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
         // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
         // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
         float hi = 0.0f, lo = 0.0f, hc = 0.0f, lc = 0.0f;
-        const float dRc = corr ? (float)(sm.dsd[t + 1] / I.dx) : 0.0f;
-        const float dLc = corr ? (float)(sm.dsd[t] / I.dx) : 0.0f;
+        const float dRc = corr ? dsd[t + 1] * (float)(1.0 / I.dx) : 0.0f;
+        const float dLc = corr ? dsd[t] * (float)(1.0 / I.dx) : 0.0f;
         for (int kk = 0; kk < G.M; ++kk) {
           const float ej = sm.x[t][kk];
           const float wv2k = -sm.wvk[kk] * sm.vk[kk];
