@@ -90,6 +90,13 @@ struct FSmem {
       y[kMaxRestart], hc[kMaxRestart + 2];
   int stop;
 };
+// V* and d* of the correction's flux (f_pass) are kept as binary64 over the reduced-system
+// arrays after the line solve: ra..rb and rc..rr must be adjacent and 8-byte aligned
+static_assert(offsetof(FSmem, ra) % 8 == 0 && offsetof(FSmem, rc) % 8 == 0, "alignment");
+static_assert(offsetof(FSmem, rb) == offsetof(FSmem, ra) + sizeof(FSmem::ra) &&
+              offsetof(FSmem, rc) == offsetof(FSmem, rb) + sizeof(FSmem::rb) &&
+              offsetof(FSmem, rr) == offsetof(FSmem, rc) + sizeof(FSmem::rc), "layout");
+static_assert(2 * sizeof(FSmem::ra) >= (kFS + 2) * sizeof(double), "room for V*");
 
 // Per-CTA geometry.
 struct FGeo {
@@ -448,27 +455,42 @@ __device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
   return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
 }
 
+// a / b in binary64 from a binary32 reciprocal and one residual correction (relative
+// error ~1e-14; the binary64 divide is a long FP64 sequence on this part)
+__device__ __forceinline__ double f_div(double a, double b) {
+  if (!(fabs(b) > 1e-30 && fabs(b) < 1e30)) return a / b;   // outside the binary32 range
+  const double r = (double)__frcp_rn((float)b);
+  const double q = a * r;
+  return q + (a - q * b) * r;
+}
+
 // The multiplier of the correction's flux (sigma_0/T^3, Eq. dis-cor-marshak1 with the
 // predicted data) in cell i for the iterate rho = X:
-//   V* = max(U*, 0)^{3/4} = sqrt(u sqrt(u)),  U* = (U^n + gam rho)/(1 + gam a c)  (Eq. dis-pre3),
-// in binary32 (it scales binary32 flux parts; one per cell and full pass).
-__device__ __forceinline__ float f_vstar(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t i) {
+//   V* = max(U*, 0)^{3/4},  U* = (U^n + gam rho)/(1 + gam a c)  (Eq. dis-pre3);
+// y = u^{3/4} from binary32, then one Newton step on y^4 = u^3 in binary64.
+__device__ __forceinline__ double f_vstar(const Dev& D, const Inst& I, const FGeo& G, const FVec& X, int64_t i) {
   const int64_t g = G.co + i;
-  const float gam = (float)D.cf.gam[g];
-  const float u = fmaxf(((float)D.U[g] + gam * (float)f_x<true>(X, G, i)) * __frcp_rn(1.0f + gam * (float)(I.a * I.c)), 0.0f);
-  return sqrtf(u * sqrtf(u));
+  const double gam = D.cf.gam[g];
+  const double u = fmax(f_div(D.U[g] + gam * f_x<true>(X, G, i), 1.0 + gam * (I.a * I.c)), 0.0);
+  if (u == 0.0) return 0.0;
+  if (!(u > 1e-25 && u < 1e25)) return pow(u, 0.75);   // outside the binary32 seed's range
+  const float uf = (float)u;
+  const double y = (double)sqrtf(uf * sqrtf(uf));
+  const double y2 = y * y, u2 = u * u;
+  return y - (y2 * y2 - u2 * u) * (double)__frcp_rn((float)(4.0 * y2 * y));
 }
 
 // Node coefficient of the correction's flux at node i from the multipliers of its two
 // cells: d*_i = V*_i/(V*_i eps^2/(c dt) + sig_i), V*_i the mean of the two cells, sig_i
 // their harmonic mean; 0 at the wall nodes and past the grid.
-__device__ __forceinline__ float f_dnode(const Dev& D, const Inst& I, const FGeo& G, int64_t i, float vl, float vr) {
-  if (i < 1 || i > G.N - 1) return 0.0f;
-  const float sl = (float)D.sig[G.co + i - 1], sr = (float)D.sig[G.co + i];
-  const float sn = (sl > 0.0f && sr > 0.0f) ? 2.0f * sl * sr * __frcp_rn(sl + sr) : 0.0f;
-  const float vn = 0.5f * (vl + vr);
-  const float den = vn * (float)(I.eps * I.eps / (I.c * I.dt)) + sn;
-  return den > 0.0f ? vn * __frcp_rn(den) : 0.0f;
+__device__ __forceinline__ double f_dnode(const Dev& D, const Inst& I, const FGeo& G, int64_t i, double vl,
+                                          double vr) {
+  if (i < 1 || i > G.N - 1) return 0.0;
+  const double sl = D.sig[G.co + i - 1], sr = D.sig[G.co + i];
+  const double sn = (sl > 0.0 && sr > 0.0) ? f_div(2.0 * sl * sr, sl + sr) : 0.0;
+  const double vn = 0.5 * (vl + vr);
+  const double den = vn * f_div(I.eps * I.eps, I.c * I.dt) + sn;
+  return den > 0.0 ? f_div(vn, den) : 0.0;
 }
 
 template <bool FULL>
@@ -647,8 +669,8 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   __syncthreads();
   f_line_solve(sm, cl, G, par);
   const bool corr = FULL && I.kind == GRTE_SIGMA_T3;
-  float* const vst = &sm.ra[0][0];   // kFS + 2 cell values
-  float* const dsd = &sm.rb[0][0];   // kFS + 1 node values
+  double* const vst = reinterpret_cast<double*>(&sm.ra[0][0]);   // kFS + 2 cell values (ra, rb)
+  double* const dsd = reinterpret_cast<double*>(&sm.rc[0][0]);   // kFS + 1 node values (rc, rr)
   if (corr) {
     // the correction's flux (f_vstar, f_dnode) of the cells that are not inflow wall
     // cells (those keep the prediction's flux: the wall node takes the prediction's value
@@ -658,9 +680,9 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     // next pass)
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
-    vst[t + 1] = j < N ? f_vstar(D, I, G, X, j) : 0.0f;
-    if (t == 0) vst[0] = (j > 0 && j <= N) ? f_vstar(D, I, G, X, j - 1) : 0.0f;
-    if (t == kFS - 1) vst[kFS + 1] = j + 1 < N ? f_vstar(D, I, G, X, j + 1) : 0.0f;
+    vst[t + 1] = j < N ? f_vstar(D, I, G, X, j) : 0.0;
+    if (t == 0) vst[0] = (j > 0 && j <= N) ? f_vstar(D, I, G, X, j - 1) : 0.0;
+    if (t == kFS - 1) vst[kFS + 1] = j + 1 < N ? f_vstar(D, I, G, X, j + 1) : 0.0;
     __syncthreads();
     dsd[t] = f_dnode(D, I, G, j, vst[t], vst[t + 1]);
     if (t == kFS - 1) dsd[kFS] = f_dnode(D, I, G, j + 1, vst[kFS], vst[kFS + 1]);
@@ -669,8 +691,8 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
                    xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
       const double dL = dsd[t], dR = dsd[t + 1];
-      sm.flc[t] = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) / I.dx +
-                  I.eps * I.eps / (I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
+      sm.flc[t] = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) * f_div(1.0, I.dx) +
+                  f_div(I.eps * I.eps, I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
     } else {
       sm.flc[t] = 0.0;
     }
@@ -719,8 +741,9 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
         // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
         // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
         float hi = 0.0f, lo = 0.0f, hc = 0.0f, lc = 0.0f;
-        const float dRc = corr ? dsd[t + 1] * (float)(1.0 / I.dx) : 0.0f;
-        const float dLc = corr ? dsd[t] * (float)(1.0 / I.dx) : 0.0f;
+        const float idxf = __frcp_rn((float)I.dx);
+        const float dRc = corr ? (float)dsd[t + 1] * idxf : 0.0f;
+        const float dLc = corr ? (float)dsd[t] * idxf : 0.0f;
         for (int kk = 0; kk < G.M; ++kk) {
           const float ej = sm.x[t][kk];
           const float wv2k = -sm.wvk[kk] * sm.vk[kk];
@@ -1056,7 +1079,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
     f_slice_sums<1, true>(sm, 1, [&](int, int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
     f_cluster_reduce(sm, cl, par, 1, true);
     const double xmax = sm.sums[0];
-    sm.wgt[t] = real ? 1.0f / (float)(fabs(x[j]) + D.wfloor * xmax + 1e-300) : 0.0f;
+    sm.wgt[t] = real ? __frcp_rn((float)(fabs(x[j]) + D.wfloor * xmax + 1e-300)) : 0.0f;
     __syncthreads();
     double* v0 = Vi(0);
     f_prec(sm, cl, D, I, G, zv, v0, par);
