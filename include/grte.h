@@ -17,7 +17,8 @@
  *  - Steps are launched asynchronously on the handle's stream.  Problems found on
  *    the device (non-converged Krylov or Newton solve, negative right-hand side of
  *    the temperature equation, NaN) are recorded per instance and reported, sticky,
- *    by grte_sync() and the grte_get_* calls, which synchronise the stream.
+ *    by the grte_get_* calls and grte_sync(), which synchronise the stream;
+ *    grte_sync() clears them once reported.
  *  - Layout of the angular unknowns in device memory: per instance, angle-major
  *    lines, E[k][j] (k = 0..M-1 positive angles, j = 0..nx-1 cells) and
  *    O[k][i] (i = 0..nx nodes).  Host copies returned by grte_get_E/O use the
@@ -145,10 +146,31 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* inst, const grte_o
  * I = a c T^4 (E = a c T^4, O = 0).  U is set to T^4 (Algorithm 2 input). */
 grte_status grte_set_state(grte_t h, int inst, const double* T, const double* E, const double* O);
 
+/* Checkpoint / restore.  grte_get_state writes an opaque blob of the handle's whole
+ * state: the raw device arrays T, U (binary64) and E - a c U, O (in the handle's bulk
+ * type), the energy sums of grte_get_energy and the step count, behind a header with
+ * the precision and every instance's (nx, n_angle).  buf: host, *len bytes; with
+ * buf = NULL only *len is set to the size needed.  grte_restore_state loads such a blob
+ * into a handle created with the same instances and precision; steps taken after a
+ * restore are bit-identical to the steps the saved handle would have taken (the blob
+ * holds every value a step reads).  Errors: EINVAL (size, header, precision or
+ * instance sizes differ; *len too small), ESTATE (state unset). */
+grte_status grte_get_state(grte_t h, void* buf, size_t* len);
+grte_status grte_restore_state(grte_t h, const void* buf, size_t len);
+
+/* T of instance `inst` (nx values, binary64) copied into the caller's device buffer
+ * dptr (device) on the caller's CUDA stream (NULL: the handle's stream), after the
+ * handle's queued steps (the caller's stream waits for them); asynchronous, no host
+ * round trip (zero-copy hand-off to frameworks holding the device memory).  Errors:
+ * EINVAL (bad instance, NULL dptr, len != nx). */
+grte_status grte_get_T_device(grte_t h, int inst, double* dptr, size_t len, void* stream);
+
 /* Advance every instance by nsteps steps of Algorithm 2 (asynchronous). */
 grte_status grte_step(grte_t h, int64_t nsteps);
 
-/* Wait for the stream; return the first device-side status (sticky). */
+/* Wait for the stream; return the first device-side status (ENAN, ENONCONV, ENEGATIVE in
+ * that order) recorded by the steps since the last grte_sync, then clear it: a status is
+ * sticky (every grte_get_* call reports it too) until grte_sync has returned it. */
 grte_status grte_sync(grte_t h);
 
 /* Copy results of instance `inst` to host arrays (synchronises).  len = element count. */
@@ -195,6 +217,11 @@ grte_status grte_profile_end(grte_t h, double* ms, int64_t* launches, size_t n);
 int64_t grte_last_launches(grte_t h);
 const char* grte_last_error(grte_t h);
 void grte_destroy(grte_t h);   /* NULL is a no-op */
+
+/* Testing hook: the (n+1)-th device allocation of the 1D handle calls from now on fails
+ * as if the device were out of memory (grte_create_1d then returns GRTE_ENOMEM, with the
+ * handle in *out for grte_last_error and grte_destroy); n < 0 switches it off. */
+void grte_test_fail_alloc_after(int n);
 
 /* ---- Learned initial guess of the per-cell Newton solve --------------------------------
  * The paper solves the per-cell quartic of Eq. Tnp1 with "standard iterative solvers";

@@ -18,6 +18,7 @@
 // (Eq. dis-proj) is fused into that kernel's epilogue.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,6 +29,15 @@
 #include <vector>
 
 #include "../../include/grte.h"
+
+// NVTX range over a host-side stage of a step (shown by Nsight Systems and other NVTX
+// tools; free when none is attached)
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 #include "mlp.cuh"
 #include "tridiag.cuh"
 
@@ -1333,6 +1343,7 @@ struct grte_ctx {
   bool fused = false;
   int* d_finst = nullptr;
   int fcnt[5] = {0, 0, 0, 0, 0}, foff[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev_state = nullptr;   // grte_get_T_device: the caller's stream waits on it
 };
 
 // The captured step depends on values passed by value to its kernels (the device
@@ -1375,9 +1386,16 @@ static grte_status fail(grte_t h, grte_status s, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(h, GRTE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+static int g_fail_alloc_after = -1;   // < 0: off (grte_test_fail_alloc_after)
+
 template <typename T>
 static cudaError_t dalloc(grte_t h, T** p, int64_t n) {
   void* q = nullptr;
+  // test hook (grte_test_fail_alloc_after): the allocation after the given count fails
+  if (g_fail_alloc_after >= 0 && g_fail_alloc_after-- == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   cudaError_t e = cudaMalloc(&q, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
   if (e == cudaSuccess) {
     h->allocs.push_back(q);
@@ -1679,9 +1697,12 @@ void grte_destroy(grte_t h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_state) cudaEventDestroy(h->ev_state);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
+
+void grte_test_fail_alloc_after(int n) { g_fail_alloc_after = n < 0 ? -1 : n; }
 
 grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_options* opt, grte_t* out) {
   if (!out) return GRTE_EINVAL;
@@ -1692,6 +1713,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   grte_default_options(&h->opt);
   if (opt) h->opt = *opt;
   auto bad = [&](const std::string& m) { grte_status s = fail(h, GRTE_EINVAL, m); *out = h; return s; };
+  auto nomem = [&](const std::string& m) { grte_status s = fail(h, GRTE_ENOMEM, m); *out = h; return s; };
   if (h->opt.precision != GRTE_FP64 && h->opt.precision != GRTE_MIXED) return bad("precision must be GRTE_FP64 or GRTE_MIXED");
   if (h->opt.krylov_restart < 1 || h->opt.krylov_restart > kMaxRestart) return bad("krylov_restart out of range [1,16]");
   if (h->opt.krylov_maxcycles < 1 || h->opt.newton_maxit < 1 || !(h->opt.krylov_rtol > 0)) return bad("bad solver options");
@@ -1794,6 +1816,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
   }
+  CK(cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming));
   Dev& D = h->D;
   const int m = h->opt.krylov_restart;
   D.m = m;
@@ -1810,13 +1833,13 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   const int64_t es = mixed ? 4 : 8;   // bytes per bulk element
   D.newton_maxit = h->opt.newton_maxit;
   const int64_t nc = h->ncell, ne = h->nelem, nn = h->nnelem, na = aoff;
-#define AL(ptr, n) do { if (dalloc(h, &(ptr), (n)) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc failed for " #ptr); } while (0)
+#define AL(ptr, n) do { if (dalloc(h, &(ptr), (n)) != cudaSuccess) return nomem("cudaMalloc failed for " #ptr); } while (0)
   AL(h->d_inst, n_inst);
   AL(h->d_lines, (int64_t)h->lines.size());
   AL(h->d_cell_start, n_inst);
   AL(D.v, na); AL(D.w, na); AL(D.bL, na); AL(D.bR, na);
-  { char* p_; if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Eh"); D.Eh = p_; }
-  { char* p_; if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc O"); D.O = p_; }
+  { char* p_; if (dalloc(h, &p_, es * ne) != cudaSuccess) return nomem("cudaMalloc Eh"); D.Eh = p_; }
+  { char* p_; if (dalloc(h, &p_, es * nn) != cudaSuccess) return nomem("cudaMalloc O"); D.O = p_; }
   AL(D.T, nc); AL(D.U, nc); AL(D.sig, nc);
   AL(D.P1, nc); AL(D.P2, nc); AL(D.P3, nc); AL(D.Frho, nc); AL(D.gU, nc); AL(D.Q1, nc); AL(D.Q2, nc);
   AL(D.gwork, nc);
@@ -1836,12 +1859,12 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
   }
   {
     char* p_;
-    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc xb"); D.xb = p_;
-    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S"); D.S = p_;
-    if (dalloc(h, &p_, es * ne) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc S2"); D.S2 = p_;
-    if (dalloc(h, &p_, es * foff) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc F"); D.F = p_;
-    if (dalloc(h, &p_, es * h->nred) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc Rd"); D.Rd = p_;
-    if (dalloc(h, &p_, es * nn) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc onode"); D.onode = p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return nomem("cudaMalloc xb"); D.xb = p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return nomem("cudaMalloc S"); D.S = p_;
+    if (dalloc(h, &p_, es * ne) != cudaSuccess) return nomem("cudaMalloc S2"); D.S2 = p_;
+    if (dalloc(h, &p_, es * foff) != cudaSuccess) return nomem("cudaMalloc F"); D.F = p_;
+    if (dalloc(h, &p_, es * h->nred) != cudaSuccess) return nomem("cudaMalloc Rd"); D.Rd = p_;
+    if (dalloc(h, &p_, es * nn) != cudaSuccess) return nomem("cudaMalloc onode"); D.onode = p_;
   }
   AL(D.pF, 5 * (nc + (int64_t)n_inst * kCL * kTriThreads)); AL(D.pRd, h->npred); AL(D.pG, nc); AL(D.pH, nc); AL(D.gw, nc);
   AL(D.pInv, (int64_t)n_inst * kCL * 2 * (2 * kCL));
@@ -1920,8 +1943,8 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
         h->inst[i].fd_off = fd;
         fd += (int64_t)(1 << fused_class(h->inst[i].N)) * kFS * 32;
       }
-      if (dalloc(h, &h->d_finst, n_inst) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc finst");
-      if (dalloc(h, &D.fdata, fd) != cudaSuccess) return fail(h, GRTE_ENOMEM, "cudaMalloc fdata");
+      if (dalloc(h, &h->d_finst, n_inst) != cudaSuccess) return nomem("cudaMalloc finst");
+      if (dalloc(h, &D.fdata, fd) != cudaSuccess) return nomem("cudaMalloc fdata");
       CK(cudaMemcpy(h->d_finst, order.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(h->d_inst, h->inst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice));
       h->fused = true;
@@ -1990,6 +2013,7 @@ static StepGeom step_geom(grte_t h) {
 
 template <typename R>
 static grte_status step_prologue(grte_t h, bool allow_tune) {
+  NvtxRange nv_("grte: prologue (coefficients, rho^n, factor pass, first restart)");
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const StepGeom G = step_geom(h);
@@ -2038,6 +2062,7 @@ static void step_tail(grte_t h) {
 
 template <typename R>
 static grte_status step_epilogue(grte_t h) {
+  NvtxRange nv_("grte: Newton, correction, projection");
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const StepGeom G = step_geom(h);
@@ -2064,6 +2089,7 @@ static grte_status step_epilogue(grte_t h) {
 // per cluster size for the whole GMRES solve, then Newton, correction and projection.
 template <typename R>
 static grte_status step_fused(grte_t h, bool allow_tune) {
+  NvtxRange nv_("grte: step (one-kernel prediction solve)");
   Dev& D = h->D;
   cudaStream_t st = h->stream;
   const StepGeom G = step_geom(h);
@@ -2349,6 +2375,7 @@ static grte_status build_step_graph(grte_t h) {
 extern "C" {
 
 grte_status grte_step(grte_t h, int64_t nsteps) {
+  NvtxRange nv_("grte_step");
   if (!h) return GRTE_EINVAL;
   if (!h->state_set) return fail(h, GRTE_ESTATE, "state not set for every instance");
   if (nsteps < 0) return fail(h, GRTE_EINVAL, "nsteps < 0");
@@ -2445,7 +2472,10 @@ static grte_status device_status(grte_t h) {
 
 grte_status grte_sync(grte_t h) {
   if (!h) return GRTE_EINVAL;
-  return device_status(h);
+  const grte_status s = device_status(h);
+  // reported once: the per-instance flags are cleared for the steps that follow
+  if (s != GRTE_OK && s != GRTE_ECUDA) CK(cudaMemset(h->D.status, 0, sizeof(int) * h->n_inst));
+  return s;
 }
 
 static grte_status get_cells(grte_t h, int inst, const double* src, double* out, size_t len) {
@@ -2544,6 +2574,119 @@ grte_status grte_get_I(grte_t h, int inst, double* Ipos, double* Ineg, size_t le
       Ineg[j * I.M + k] = E[j * I.M + k] - I.eps * oc;
     }
   return s;
+}
+
+// Checkpoint blob: a header, the per-instance sizes, the energy sums and the raw device
+// state (T, U in binary64; Eh = E - a c U and O in the handle's bulk type), so that a
+// restored handle continues bit for bit.
+namespace {
+struct BlobHead {
+  char magic[8];
+  uint32_t version, dim, precision, n_inst;
+  int64_t steps;
+};
+constexpr char kBlobMagic[8] = {'G', 'R', 'T', 'E', 'S', 'T', '1', 'D'};
+}  // namespace
+
+static size_t blob_size(grte_t h) {
+  const size_t es = h->opt.precision == GRTE_MIXED ? 4 : 8;
+  size_t n = sizeof(BlobHead) + sizeof(int64_t) * 2 * h->n_inst + sizeof(double) * 3 * h->n_inst;
+  for (const Inst& I : h->inst) n += sizeof(double) * 2 * I.N + es * (I.N * I.M + (I.N + 1) * I.M);
+  return n;
+}
+
+grte_status grte_get_state(grte_t h, void* buf, size_t* len) {
+  if (!h || !len) return GRTE_EINVAL;
+  const size_t need = blob_size(h);
+  if (!buf) {
+    *len = need;
+    return GRTE_OK;
+  }
+  if (*len < need) return fail(h, GRTE_EINVAL, "buffer smaller than the state (query the size with buf = NULL)");
+  if (!h->state_set) return fail(h, GRTE_ESTATE, "state not set");
+  CK(cudaStreamSynchronize(h->stream));
+  unsigned char* p = (unsigned char*)buf;
+  BlobHead hd{};
+  memcpy(hd.magic, kBlobMagic, 8);
+  hd.version = 1;
+  hd.dim = 1;
+  hd.precision = (uint32_t)h->opt.precision;
+  hd.n_inst = (uint32_t)h->n_inst;
+  hd.steps = h->stats.steps;
+  memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  for (const Inst& I : h->inst) {
+    const int64_t nm[2] = {I.N, I.M};
+    memcpy(p, nm, sizeof nm);
+    p += sizeof nm;
+  }
+  CK(cudaMemcpy(p, h->D.energy, sizeof(double) * 3 * h->n_inst, cudaMemcpyDeviceToHost));
+  p += sizeof(double) * 3 * h->n_inst;
+  const size_t es = h->opt.precision == GRTE_MIXED ? 4 : 8;
+  for (const Inst& I : h->inst) {
+    CK(cudaMemcpy(p, h->D.T + I.cell_off, sizeof(double) * I.N, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * I.N;
+    CK(cudaMemcpy(p, h->D.U + I.cell_off, sizeof(double) * I.N, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * I.N;
+    CK(cudaMemcpy(p, (const char*)h->D.Eh + es * I.elem_off, es * I.N * I.M, cudaMemcpyDeviceToHost));
+    p += es * I.N * I.M;
+    CK(cudaMemcpy(p, (const char*)h->D.O + es * I.nelem_off, es * (I.N + 1) * I.M, cudaMemcpyDeviceToHost));
+    p += es * (I.N + 1) * I.M;
+  }
+  *len = need;
+  return device_status(h);
+}
+
+grte_status grte_restore_state(grte_t h, const void* buf, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (!buf || len != blob_size(h)) return fail(h, GRTE_EINVAL, "blob size does not match this handle");
+  const unsigned char* p = (const unsigned char*)buf;
+  BlobHead hd;
+  memcpy(&hd, p, sizeof hd);
+  p += sizeof hd;
+  if (memcmp(hd.magic, kBlobMagic, 8) != 0 || hd.version != 1 || hd.dim != 1)
+    return fail(h, GRTE_EINVAL, "not a 1D state blob of this library");
+  if (hd.precision != (uint32_t)h->opt.precision || hd.n_inst != (uint32_t)h->n_inst)
+    return fail(h, GRTE_EINVAL, "blob precision or instance count differs from this handle");
+  for (const Inst& I : h->inst) {
+    int64_t nm[2];
+    memcpy(nm, p, sizeof nm);
+    p += sizeof nm;
+    if (nm[0] != I.N || nm[1] != I.M) return fail(h, GRTE_EINVAL, "blob instance sizes differ from this handle");
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->D.energy, p, sizeof(double) * 3 * h->n_inst, cudaMemcpyHostToDevice));
+  p += sizeof(double) * 3 * h->n_inst;
+  const size_t es = h->opt.precision == GRTE_MIXED ? 4 : 8;
+  for (const Inst& I : h->inst) {
+    CK(cudaMemcpy(h->D.T + I.cell_off, p, sizeof(double) * I.N, cudaMemcpyHostToDevice));
+    p += sizeof(double) * I.N;
+    CK(cudaMemcpy(h->D.U + I.cell_off, p, sizeof(double) * I.N, cudaMemcpyHostToDevice));
+    p += sizeof(double) * I.N;
+    CK(cudaMemcpy((char*)h->D.Eh + es * I.elem_off, p, es * I.N * I.M, cudaMemcpyHostToDevice));
+    p += es * I.N * I.M;
+    CK(cudaMemcpy((char*)h->D.O + es * I.nelem_off, p, es * (I.N + 1) * I.M, cudaMemcpyHostToDevice));
+    p += es * (I.N + 1) * I.M;
+  }
+  h->stats.steps = hd.steps;
+  std::fill(h->inst_set.begin(), h->inst_set.end(), (char)1);
+  h->state_set = true;
+  return GRTE_OK;
+}
+
+grte_status grte_get_T_device(grte_t h, int inst, double* dptr, size_t len, void* stream) {
+  if (!h) return GRTE_EINVAL;
+  if (inst < 0 || inst >= h->n_inst || !dptr) return fail(h, GRTE_EINVAL, "bad instance or NULL output");
+  const Inst& I = h->inst[inst];
+  if (len != (size_t)I.N) return fail(h, GRTE_EINVAL, "len must equal nx");
+  cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+  if (st != h->stream) {
+    // the copy waits for the handle's queued steps, on the caller's stream
+    CK(cudaEventRecord(h->ev_state, h->stream));
+    CK(cudaStreamWaitEvent(st, h->ev_state, 0));
+  }
+  CK(cudaMemcpyAsync(dptr, h->D.T + I.cell_off, sizeof(double) * I.N, cudaMemcpyDeviceToDevice, st));
+  return GRTE_OK;
 }
 
 grte_status grte_get_energy(grte_t h, int inst, double* out, size_t n) {

@@ -13,6 +13,7 @@
 // the temperature (Eq. Tnp1) by monotone Newton per cell; correction substep 2
 // (Eq. dis-cor) by GMRES on the stacked pair systems; projection (Eq. dis-proj).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +22,15 @@
 #include <vector>
 
 #include "../../include/grte.h"
+
+// NVTX range over a host-side stage of a step (shown by Nsight Systems and other NVTX
+// tools; free when none is attached)
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 #include "mg2d.cuh"
 #include "mlp.cuh"
 
@@ -1391,6 +1401,7 @@ static grte_status gmres2(grte2d_t h, bool pred, bool mg_stage, int64_t n, int& 
 }
 
 static grte_status step2(grte2d_t h) {
+  NvtxRange nv_("grte2d: step");
   D2& D = h->D;
   const G2& g = D.g;
   cudaStream_t st = h->stream;
@@ -1660,6 +1671,7 @@ static grte_status status2(grte2d_t h) {
 }
 
 grte_status grte2d_step(grte2d_t h, int64_t n) {
+  NvtxRange nv_("grte2d_step");
   if (!h) return GRTE_EINVAL;
   if (!h->state_set) return fail2(h, GRTE_ESTATE, "state not set");
   if (n < 0) return fail2(h, GRTE_EINVAL, "n < 0");

@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgrte.so")
 
 GRTE_OK = 0
+GRTE_EINVAL, GRTE_ENOMEM, GRTE_ECUDA, GRTE_ENONCONV, GRTE_ENEGATIVE, GRTE_ENAN, GRTE_ETIMEOUT, GRTE_ESTATE = range(1, 9)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONCONV", 5: "ENEGATIVE",
                 6: "ENAN", 7: "ETIMEOUT", 8: "ESTATE"}
 SIGMA_CONST, SIGMA_T3 = 0, 1
@@ -67,7 +68,8 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte2d_set_state", "grte2d_step", "grte2d_get_T", "grte2d_get_E", "grte2d_get_O", "grte2d_get_stage",
             "grte2d_get_quadrature", "grte2d_get_energy", "grte2d_stats", "grte2d_last_error", "grte2d_destroy",
             "grte2d_set_guess", "grte2d_set_newton_start", "grte2d_set_sample_logging",
-            "grte2d_get_newton_samples"]
+            "grte2d_get_newton_samples", "grte_get_state", "grte_restore_state", "grte_get_T_device",
+            "grte_test_fail_alloc_after"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
@@ -103,6 +105,12 @@ def load_library(path=LIB_PATH):
     lib.grte_last_launches.argtypes = [ctypes.c_void_p]
     lib.grte_last_launches.restype = ctypes.c_int64
     lib.grte_get_energy.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_get_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    lib.grte_restore_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    lib.grte_get_T_device.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]
+    lib.grte_test_fail_alloc_after.argtypes = [ctypes.c_int]
+    lib.grte_test_fail_alloc_after.restype = None
     lib.grte_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
     lib.grte_mlp_destroy.argtypes = [ctypes.c_void_p]
     lib.grte_mlp_destroy.restype = None
@@ -348,6 +356,23 @@ class Grte:
     def E(self, inst, allow=()):
         s = self.specs[inst]
         return self._get(lib().grte_get_E, inst, (s["nx"], s["M"]), allow)
+
+    def get_state(self, allow=()):
+        """The opaque checkpoint blob of the whole handle (bytes)."""
+        n = ctypes.c_size_t(0)
+        self._check(lib().grte_get_state(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(lib().grte_get_state(self.h, buf, ctypes.byref(n)), allow)
+        return buf.raw[:n.value]
+
+    def restore_state(self, blob):
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        return self._check(lib().grte_restore_state(self.h, buf, len(blob)))
+
+    def T_device(self, inst, dptr, n, stream=None):
+        """Copy T of `inst` into the device buffer at address dptr (n doubles) on `stream`."""
+        return self._check(lib().grte_get_T_device(self.h, inst, ctypes.c_void_p(dptr), n,
+                                                   ctypes.c_void_p(stream) if stream else None))
 
     def O(self, inst, allow=()):
         s = self.specs[inst]
