@@ -369,6 +369,59 @@ grte_status grte2d_get_newton_samples(grte2d_t h, float* X, float* y, size_t n);
 const char* grte2d_last_error(grte2d_t h);
 void grte2d_destroy(grte2d_t h);
 
+/* ----------------------------------------------------------------------------------
+ * One create call for both dimensions: the problem of Eq. radiative_transport on a
+ * uniform grid in 1D (Sec. 4) or 2D, described by grid, quadrature, opacity, the
+ * constants a, c, C_v, eps and the boundary conditions.  It builds a 1D handle with one
+ * instance (grte_create_1d) or a 2D handle (grte2d_create) and returns it in a
+ * grte_handle; the dimension-specific calls stay available on h1 / h2.
+ * -------------------------------------------------------------------------------- */
+typedef struct {
+  int dim;                 /* 1 or 2                                                         */
+  int64_t nx, ny;          /* cells per axis (ny ignored in 1D)                              */
+  double x0, x1;           /* domain along x (1D: the slab; 2D: x0 must be 0)                */
+  double y0, y1;           /* domain along y (2D; y0 must be 0)                              */
+  double dt;               /* time step                                                      */
+} grte_grid;
+typedef struct {
+  int n_dir;               /* directions: 1D 2M (+-v_k), 2D 2K (+-Omega_k), or 0 for the
+                              default (1D: 16 Gauss-Legendre; 2D: S8, 40)                     */
+  const double* mu;        /* host or NULL (built-in): 1D the M positive cosines v_k; 2D the K
+                              x-cosines of the pairs                                          */
+  const double* eta;       /* host, 2D: the K y-cosines (NULL with mu NULL)                   */
+  const double* w;         /* host, M or K weights (NULL with mu NULL)                        */
+} grte_quadrature;
+typedef struct {
+  int kind;                /* GRTE_SIGMA_CONST or GRTE_SIGMA_T3                              */
+  const double* sigma0;    /* host, one value per cell (2D row-major [j*nx + i]), or NULL     */
+  double sigma0_scalar;    /* used when sigma0 is NULL                                       */
+} grte_opacity;
+typedef struct {
+  int kind[4];             /* edges x0, x1, y0, y1: GRTE_BC_INFLOW, GRTE_BC_REFLECT (1D, both
+                              walls), GRTE_BC_PERIODIC (2D, both edges of an axis)            */
+  double b_iso[4];         /* isotropic inflow intensity per edge (0: vacuum)                */
+  const double* b[4];      /* host, 1D only: per positive angle values on x0 / x1 (M each), or
+                              NULL for b_iso                                                  */
+} grte_bc;
+typedef struct {
+  int dim;
+  int64_t ncell;           /* nx (1D) or nx*ny (2D)                                          */
+  grte_t h1;               /* dim 1: a one-instance 1D handle                                */
+  grte2d_t h2;             /* dim 2                                                          */
+} grte_handle;
+
+/* Errors: EINVAL (bad description, as grte_create_1d / grte2d_create), ENOMEM, ECUDA; on
+ * failure out holds no handle (the partial one is destroyed; the message is lost). */
+grte_status grte_create(const grte_grid* grid, const grte_quadrature* quad, const grte_opacity* opac,
+                        double a, double c, double Cv, double eps, const grte_bc* bc,
+                        const grte_options* opt, grte_handle* out);
+/* Initial state: the equilibrium I = a c T^4 for the given T (nx or nx*ny values, host). */
+grte_status grte_handle_set_initial(grte_handle* h, const double* T, size_t len);
+grte_status grte_handle_step(grte_handle* h, int64_t n);
+grte_status grte_handle_sync(grte_handle* h);
+grte_status grte_handle_get_T(grte_handle* h, double* T, size_t len);   /* nx or nx*ny, host */
+void grte_handle_destroy(grte_handle* h);                              /* NULL is a no-op */
+
 #ifdef __cplusplus
 }
 #endif

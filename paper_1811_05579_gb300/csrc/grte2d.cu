@@ -1819,4 +1819,140 @@ grte_status grte2d_stats(grte2d_t h, grte_stats_t* st) {
   return s;
 }
 
+// ----------------------------------------------------------------------------- one create
+grte_status grte_create(const grte_grid* grid, const grte_quadrature* quad, const grte_opacity* opac,
+                        double a, double c, double Cv, double eps, const grte_bc* bc,
+                        const grte_options* opt, grte_handle* out) {
+  if (!out) return GRTE_EINVAL;
+  out->dim = 0;
+  out->ncell = 0;
+  out->h1 = nullptr;
+  out->h2 = nullptr;
+  if (!grid || !opac || !bc) return GRTE_EINVAL;
+  const bool custom = quad && quad->mu;
+  if (grid->dim == 1) {
+    const int64_t nx = grid->nx;
+    if (nx < 2) return GRTE_EINVAL;
+    const int n_dir = (quad && quad->n_dir) ? quad->n_dir : 16;
+    if (n_dir < 2 || n_dir % 2) return GRTE_EINVAL;
+    const int M = n_dir / 2;
+    if (custom && !quad->w) return GRTE_EINVAL;
+    if (bc->kind[0] != bc->kind[1] || (bc->kind[0] != GRTE_BC_INFLOW && bc->kind[0] != GRTE_BC_REFLECT))
+      return GRTE_EINVAL;
+    std::vector<double> sig(nx), bL(M), bR(M);
+    for (int64_t j = 0; j < nx; ++j) sig[j] = opac->sigma0 ? opac->sigma0[j] : opac->sigma0_scalar;
+    for (int k = 0; k < M; ++k) {
+      bL[k] = bc->b[0] ? bc->b[0][k] : bc->b_iso[0];
+      bR[k] = bc->b[1] ? bc->b[1][k] : bc->b_iso[1];
+    }
+    grte_instance1d p{};
+    p.nx = nx;
+    p.n_angle = M;
+    p.v = custom ? quad->mu : nullptr;
+    p.w = custom ? quad->w : nullptr;
+    p.sigma = sig.data();
+    p.sigma_kind = opac->kind;
+    p.bc = bc->kind[0];
+    p.bL = bL.data();
+    p.bR = bR.data();
+    p.x0 = grid->x0;
+    p.x1 = grid->x1;
+    p.dt = grid->dt;
+    p.a = a;
+    p.c = c;
+    p.Cv = Cv;
+    p.eps = eps;
+    grte_t h = nullptr;
+    const grte_status s = grte_create_1d(1, &p, opt, &h);
+    if (s != GRTE_OK) {
+      grte_destroy(h);
+      return s;
+    }
+    out->dim = 1;
+    out->ncell = nx;
+    out->h1 = h;
+    return GRTE_OK;
+  }
+  if (grid->dim != 2) return GRTE_EINVAL;
+  if (grid->x0 != 0.0 || grid->y0 != 0.0) return GRTE_EINVAL;
+  if (bc->kind[0] != bc->kind[1] || bc->kind[2] != bc->kind[3]) return GRTE_EINVAL;
+  const int n_dir = (quad && quad->n_dir) ? quad->n_dir : 40;
+  if (!custom && n_dir != 40) return GRTE_EINVAL;
+  if (custom && (!quad->eta || !quad->w || n_dir < 2 || n_dir % 2)) return GRTE_EINVAL;
+  const int64_t nc = grid->nx * grid->ny;
+  if (grid->nx < 2 || grid->ny < 2) return GRTE_EINVAL;
+  std::vector<double> sig(nc);
+  for (int64_t q = 0; q < nc; ++q) sig[q] = opac->sigma0 ? opac->sigma0[q] : opac->sigma0_scalar;
+  grte_instance2d p{};
+  p.nx = grid->nx;
+  p.ny = grid->ny;
+  p.n_pair = custom ? n_dir / 2 : 0;
+  p.mu = custom ? quad->mu : nullptr;
+  p.eta = custom ? quad->eta : nullptr;
+  p.w = custom ? quad->w : nullptr;
+  p.sigma = sig.data();
+  p.sigma_kind = opac->kind;
+  p.bc_x = bc->kind[0];
+  p.bc_y = bc->kind[2];
+  p.b_x0 = bc->b_iso[0];
+  p.b_x1 = bc->b_iso[1];
+  p.b_y0 = bc->b_iso[2];
+  p.b_y1 = bc->b_iso[3];
+  p.lx = grid->x1;
+  p.ly = grid->y1;
+  p.dt = grid->dt;
+  p.a = a;
+  p.c = c;
+  p.Cv = Cv;
+  p.eps = eps;
+  grte2d_t h = nullptr;
+  const grte_status s = grte2d_create(&p, opt, &h);
+  if (s != GRTE_OK) {
+    grte2d_destroy(h);
+    return s;
+  }
+  out->dim = 2;
+  out->ncell = nc;
+  out->h2 = h;
+  return GRTE_OK;
+}
+
+grte_status grte_handle_set_initial(grte_handle* h, const double* T, size_t len) {
+  if (!h || !T || len != (size_t)h->ncell) return GRTE_EINVAL;
+  if (h->dim == 1) return grte_set_state(h->h1, 0, T, nullptr, nullptr);
+  if (h->dim == 2) return grte2d_set_state(h->h2, T, nullptr, nullptr);
+  return GRTE_EINVAL;
+}
+
+grte_status grte_handle_step(grte_handle* h, int64_t n) {
+  if (!h) return GRTE_EINVAL;
+  if (h->dim == 1) return grte_step(h->h1, n);
+  if (h->dim == 2) return grte2d_step(h->h2, n);
+  return GRTE_EINVAL;
+}
+
+grte_status grte_handle_sync(grte_handle* h) {
+  if (!h) return GRTE_EINVAL;
+  if (h->dim == 1) return grte_sync(h->h1);
+  if (h->dim == 2) return GRTE_OK;   // 2D steps are synchronous and report their status
+  return GRTE_EINVAL;
+}
+
+grte_status grte_handle_get_T(grte_handle* h, double* T, size_t len) {
+  if (!h) return GRTE_EINVAL;
+  if (h->dim == 1) return grte_get_T(h->h1, 0, T, len);
+  if (h->dim == 2) return grte2d_get_T(h->h2, T, len);
+  return GRTE_EINVAL;
+}
+
+void grte_handle_destroy(grte_handle* h) {
+  if (!h) return;
+  if (h->h1) grte_destroy(h->h1);
+  if (h->h2) grte2d_destroy(h->h2);
+  h->h1 = nullptr;
+  h->h2 = nullptr;
+  h->dim = 0;
+  h->ncell = 0;
+}
+
 }  // extern "C"

@@ -40,6 +40,27 @@ class Instance2D(ctypes.Structure):
                 ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+class GridS(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class QuadS(ctypes.Structure):
+    _fields_ = [("n_dir", ctypes.c_int), ("mu", _dp), ("eta", _dp), ("w", _dp)]
+
+
+class OpacS(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma0", _dp), ("sigma0_scalar", ctypes.c_double)]
+
+
+class BcS(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 4), ("b_iso", ctypes.c_double * 4), ("b", _dp * 4)]
+
+
+class HandleS(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ncell", ctypes.c_int64), ("h1", ctypes.c_void_p), ("h2", ctypes.c_void_p)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
@@ -69,7 +90,8 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte2d_get_quadrature", "grte2d_get_energy", "grte2d_stats", "grte2d_last_error", "grte2d_destroy",
             "grte2d_set_guess", "grte2d_set_newton_start", "grte2d_set_sample_logging",
             "grte2d_get_newton_samples", "grte_get_state", "grte_restore_state", "grte_get_T_device",
-            "grte_test_fail_alloc_after"]
+            "grte_test_fail_alloc_after", "grte_create", "grte_handle_set_initial", "grte_handle_step",
+            "grte_handle_sync", "grte_handle_get_T", "grte_handle_destroy"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
@@ -111,6 +133,15 @@ def load_library(path=LIB_PATH):
                                       ctypes.c_void_p]
     lib.grte_test_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.grte_test_fail_alloc_after.restype = None
+    lib.grte_create.argtypes = [ctypes.POINTER(GridS), ctypes.POINTER(QuadS), ctypes.POINTER(OpacS), ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(BcS),
+                                ctypes.POINTER(Options), ctypes.POINTER(HandleS)]
+    lib.grte_handle_set_initial.argtypes = [ctypes.POINTER(HandleS), _dp, ctypes.c_size_t]
+    lib.grte_handle_step.argtypes = [ctypes.POINTER(HandleS), ctypes.c_int64]
+    lib.grte_handle_sync.argtypes = [ctypes.POINTER(HandleS)]
+    lib.grte_handle_get_T.argtypes = [ctypes.POINTER(HandleS), _dp, ctypes.c_size_t]
+    lib.grte_handle_destroy.argtypes = [ctypes.POINTER(HandleS)]
+    lib.grte_handle_destroy.restype = None
     lib.grte_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
     lib.grte_mlp_destroy.argtypes = [ctypes.c_void_p]
     lib.grte_mlp_destroy.restype = None
@@ -557,3 +588,60 @@ class Grte2D:
         s = Stats()
         self._check(lib().grte2d_stats(self.h, ctypes.byref(s)), allow)
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Problem:
+    """grte_create: one problem of either dimension (grid dim 1 or 2), driven through the
+    dimension-independent grte_handle_* calls."""
+
+    def __init__(self, dim, nx, dt, eps, sigma0, kind=SIGMA_T3, ny=0, x0=0.0, x1=1.0, y1=1.0, n_dir=0,
+                 mu=None, eta=None, w=None, bc_kind=(BC_INFLOW,) * 4, b_iso=(0.0,) * 4, a=1.0, c=1.0, Cv=1.0,
+                 precision=FP64):
+        L = lib()
+        self._keep = []
+        sig = np.asarray(sigma0, dtype=np.float64)
+        scalar = sig.ndim == 0
+        sig = None if scalar else np.ascontiguousarray(sig.ravel())
+        arrs = [None if x is None else _f64(x) for x in (mu, eta, w)]
+        self._keep += [sig] + arrs
+        grid = GridS(dim, nx, ny, x0, x1, 0.0, y1, dt)
+        quad = QuadS(n_dir, *[_ptr(x) for x in arrs])
+        opac = OpacS(kind, _ptr(sig), float(sigma0) if scalar else 0.0)
+        bc = BcS((ctypes.c_int * 4)(*bc_kind), (ctypes.c_double * 4)(*b_iso), (_dp * 4)(None, None, None, None))
+        opt = Options()
+        L.grte_default_options(ctypes.byref(opt))
+        opt.precision = precision
+        self.hs = HandleS()
+        st = L.grte_create(ctypes.byref(grid), ctypes.byref(quad), ctypes.byref(opac), a, c, Cv, eps,
+                           ctypes.byref(bc), ctypes.byref(opt), ctypes.byref(self.hs))
+        if st != GRTE_OK:
+            raise GrteError(st, "grte_create failed")
+
+    def set_initial(self, T):
+        T = _f64(T)
+        st = lib().grte_handle_set_initial(ctypes.byref(self.hs), _ptr(T), T.size)
+        if st != GRTE_OK:
+            raise GrteError(st, "grte_handle_set_initial failed")
+
+    def step(self, n=1):
+        return lib().grte_handle_step(ctypes.byref(self.hs), n)
+
+    def sync(self):
+        return lib().grte_handle_sync(ctypes.byref(self.hs))
+
+    def T(self, allow=()):
+        out = np.empty(self.hs.ncell)
+        st = lib().grte_handle_get_T(ctypes.byref(self.hs), _ptr(out), out.size)
+        if st != GRTE_OK and st not in allow:
+            raise GrteError(st, "grte_handle_get_T failed")
+        return out
+
+    def close(self):
+        if self.hs.dim:
+            lib().grte_handle_destroy(ctypes.byref(self.hs))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -4,6 +4,7 @@
   line kernels, mixed one-kernel solve, mixed line kernels); blobs of another precision,
   other sizes or truncated are refused (EINVAL).
 - grte_get_T_device: T copied into a caller's CUDA buffer on the caller's stream.
+- grte_create: one call for 1D and 2D problems, the same handles as the per-dimension calls.
 - Status paths, each caused on the host: NaN in the state (injected through a blob,
   since grte_set_state refuses non-finite T with EINVAL) -> ENAN; newton_maxit = 1 and
   krylov_maxcycles = 1 -> ENONCONV, reported by every grte_get_* call until grte_sync
@@ -176,3 +177,38 @@ def test_injected_allocation_failure_is_enomem(G):
     h.step(1)
     assert h.sync(allow=(5,)) in (G.GRTE_OK, 5)
     h.close()
+
+
+def test_one_create_call_for_both_dimensions(G):
+    """grte_create builds the same 1D and 2D handles as grte_create_1d and grte2d_create
+    (steps bit-identical); an unknown dimension or mismatched edge kinds are EINVAL."""
+    N = 256
+    v, w = gauss_legendre_half(16)
+    p1 = G.Problem(1, N, 0.5 / N, 1e-2, 2.0, n_dir=16, mu=v, w=w, b_iso=(1.0, 0.0, 0.0, 0.0))
+    ref = G.Grte([spec(N)])
+    T = T0(N)
+    p1.set_initial(T)
+    ref.set_state(0, T)
+    p1.step(3)
+    ref.step(3)
+    assert np.array_equal(p1.T(allow=(5,)), ref.T(0, allow=(5,)))
+    p1.close()
+    ref.close()
+    n = 24
+    sig = 1.0 + 9.0 * ((np.arange(n)[:, None] // 8 + np.arange(n)[None, :] // 8) % 2)
+    T2 = 1e-2 * (1.0 + 0.5 * wl.SplitMix64(5).uniform(n * n))
+    p2 = G.Problem(2, n, 0.5 / n, 1e-3, sig, ny=n, b_iso=(1.0, 0.0, 0.0, 0.0))
+    r2 = G.Grte2D(n, n, sig, 0.5 / n, 1e-3, b_x0=1.0, krylov_restart=10)
+    p2.set_initial(T2)
+    r2.set_state(T2)
+    p2.step(2)
+    r2.step(2, allow=(5,))
+    assert np.array_equal(p2.T(allow=(5,)), r2.T(allow=(5,)))
+    p2.close()
+    r2.close()
+    with pytest.raises(G.GrteError) as e:
+        G.Problem(3, N, 0.5 / N, 1e-2, 2.0)
+    assert e.value.status == G.GRTE_EINVAL
+    with pytest.raises(G.GrteError) as e:
+        G.Problem(1, N, 0.5 / N, 1e-2, 2.0, bc_kind=(G.BC_INFLOW, G.BC_REFLECT, 0, 0))
+    assert e.value.status == G.GRTE_EINVAL
