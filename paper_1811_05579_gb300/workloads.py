@@ -79,6 +79,7 @@ class Instance1D:
     Cv: float = 1.0
     steps: int = 1
     name: str = ""
+    length: float = 1.0        # slab [0, length]
 
 
 def marshak_1d(nx=128, n_dir=16, eps=1e-3, sigma0=1.0, T_in=1e-2, cfl=0.5, t_end=0.5):
@@ -91,6 +92,23 @@ def marshak_1d(nx=128, n_dir=16, eps=1e-3, sigma0=1.0, T_in=1e-2, cfl=0.5, t_end
     return Instance1D(nx=nx, n_dir=n_dir, eps=eps, dt=dt, sigma=np.full(nx, sigma0),
                       T0=np.full(nx, T_in), kind=SIGMA_T3, bc=BC_INFLOW, bL=1.0, bR=0.0,
                       steps=int(round(t_end / dt)), name="marshak1d_nx%d_nv%d" % (nx, n_dir))
+
+
+def marshak_dimensional(dt_s, nx=50, t_end_ns=0.02, n_dir=16):
+    """The Marshak wave with units of the last example of Sec. 6: c = 29.98 cm/ns,
+    a = 0.01372 GJ/(cm^3 keV^4), C_v = 0.3 GJ/(cm^3 keV), sigma = 300/T^3 cm^-1 (eps = 1),
+    slab [0, 0.02] cm, T(0, t) = 1 keV (isotropic inflow a c 1^4), vacuum on the right,
+    T(x, 0) = (1 - tanh(1000 (x - 0.0024)))/2 keV with I = a c T^4; time in ns, dt_s in
+    seconds.  The paper gives neither dx nor the final time: nx = 50 (dx = 4e-4 cm) is a
+    grid on which the oracle is stable at all three of its time steps."""
+    L = 0.02
+    a, c, Cv = 0.01372, 29.98, 0.3
+    x = (np.arange(nx) + 0.5) * L / nx
+    T0 = 0.5 * (1.0 - np.tanh((x - 0.0024) * 1000.0))
+    dt = dt_s * 1e9
+    return Instance1D(nx=nx, n_dir=n_dir, eps=1.0, dt=dt, sigma=np.full(nx, 300.0), T0=T0, kind=SIGMA_T3,
+                      bc=BC_INFLOW, bL=a * c, bR=0.0, a=a, c=c, Cv=Cv, steps=int(round(t_end_ns / dt)),
+                      name="marshak_dim_dt%.1e" % dt_s, length=L)
 
 
 def smoothed_log_uniform_T(rng, nx, lo=1e-3, hi=1e-2, width=65, passes=3):
