@@ -422,6 +422,37 @@ grte_status grte_handle_sync(grte_handle* h);
 grte_status grte_handle_get_T(grte_handle* h, double* T, size_t len);   /* nx or nx*ny, host */
 void grte_handle_destroy(grte_handle* h);                              /* NULL is a no-op */
 
+/* ----------------------------------------------------------------------------------
+ * The three-stage diffusion solver of Sec. 2 (Eq. limit_U_dis1 - Eq. limit_UT_dis3, fully
+ * discrete as Eq. dis-diff; for sigma_0/T^3 the fully discrete form after Eq.
+ * marshak-diff2) for the limit equation a dT^4/dt + C_v dT/dt = div(a c/(D sigma) grad T^4)
+ * (Eq. limit_T; sigma_0/T^3: a c T^3/(D sigma_0)), batched over independent 1D instances,
+ * FP64: per step one tridiagonal solve per instance for U* (prediction), the per-cell
+ * quartic for T^{n+1} by monotone Newton (correction; the flux with the node mean of
+ * (U*)^{3/4} for sigma_0/T^3) and U = T^4 (projection).  Zero-flux walls.
+ * -------------------------------------------------------------------------------- */
+typedef struct grte_diff_ctx* grte_diff_t;
+typedef struct {
+  int64_t nx;              /* cells, >= 2                                                    */
+  const double* sigma;     /* host, nx values of sigma (CONST) or sigma_0 (T3), > 0          */
+  int sigma_kind;          /* GRTE_SIGMA_CONST or GRTE_SIGMA_T3                              */
+  double x0, x1, dt, a, c, Cv;
+  double dd;               /* D_d of Eq. limit_T (0: 3, the 1D value)                        */
+} grte_diffusion1d;
+
+/* Errors: EINVAL, ENOMEM, ECUDA (the handle is returned in *out for grte_diff_last_error
+ * and grte_diff_destroy).  stream: a cudaStream_t or NULL (own stream). */
+grte_status grte_diff_create(int n_inst, const grte_diffusion1d* inst, void* stream, grte_diff_t* out);
+grte_status grte_diff_set_T(grte_diff_t h, int inst, const double* T, size_t len);   /* host, nx */
+grte_status grte_diff_step(grte_diff_t h, int64_t nsteps);                            /* async */
+/* Statuses of the steps since the last grte_diff_sync (ENAN, ENONCONV, ENEGATIVE: a cell
+ * whose right-hand side reached R <= 0, set to T = 0), then cleared. */
+grte_status grte_diff_sync(grte_diff_t h);
+grte_status grte_diff_get_T(grte_diff_t h, int inst, double* T, size_t len);         /* host, nx */
+grte_status grte_diff_get_Ustar(grte_diff_t h, int inst, double* U, size_t len);     /* last U* */
+const char* grte_diff_last_error(grte_diff_t h);
+void grte_diff_destroy(grte_diff_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,7 +5,7 @@ import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
-SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("grte1d.cu", "grte2d.cu", "mlp.cu")]
+SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("grte1d.cu", "grte2d.cu", "mlp.cu", "diff1d.cu")]
 LIB = os.path.join(_HERE, "libgrte.so")
 OBJ_DIR = os.path.join(_HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

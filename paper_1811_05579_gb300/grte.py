@@ -61,6 +61,12 @@ class HandleS(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("ncell", ctypes.c_int64), ("h1", ctypes.c_void_p), ("h2", ctypes.c_void_p)]
 
 
+class Diffusion1D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("sigma", _dp), ("sigma_kind", ctypes.c_int), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
+                ("Cv", ctypes.c_double), ("dd", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxcycles", ctypes.c_int),
@@ -91,7 +97,9 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte2d_set_guess", "grte2d_set_newton_start", "grte2d_set_sample_logging",
             "grte2d_get_newton_samples", "grte_get_state", "grte_restore_state", "grte_get_T_device",
             "grte_test_fail_alloc_after", "grte_create", "grte_handle_set_initial", "grte_handle_step",
-            "grte_handle_sync", "grte_handle_get_T", "grte_handle_destroy"]
+            "grte_handle_sync", "grte_handle_get_T", "grte_handle_destroy", "grte_diff_create", "grte_diff_set_T",
+            "grte_diff_step", "grte_diff_sync", "grte_diff_get_T", "grte_diff_get_Ustar", "grte_diff_last_error",
+            "grte_diff_destroy"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
@@ -142,6 +150,17 @@ def load_library(path=LIB_PATH):
     lib.grte_handle_get_T.argtypes = [ctypes.POINTER(HandleS), _dp, ctypes.c_size_t]
     lib.grte_handle_destroy.argtypes = [ctypes.POINTER(HandleS)]
     lib.grte_handle_destroy.restype = None
+    lib.grte_diff_create.argtypes = [ctypes.c_int, ctypes.POINTER(Diffusion1D), ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    lib.grte_diff_set_T.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_diff_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    lib.grte_diff_sync.argtypes = [ctypes.c_void_p]
+    lib.grte_diff_get_T.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_diff_get_Ustar.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_size_t]
+    lib.grte_diff_last_error.argtypes = [ctypes.c_void_p]
+    lib.grte_diff_last_error.restype = ctypes.c_char_p
+    lib.grte_diff_destroy.argtypes = [ctypes.c_void_p]
+    lib.grte_diff_destroy.restype = None
     lib.grte_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
     lib.grte_mlp_destroy.argtypes = [ctypes.c_void_p]
     lib.grte_mlp_destroy.restype = None
@@ -639,6 +658,67 @@ class Problem:
     def close(self):
         if self.hs.dim:
             lib().grte_handle_destroy(ctypes.byref(self.hs))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Diffusion:
+    """The three-stage diffusion solver of Sec. 2 (grte_diff_*): instances are dicts with
+    nx, sigma, kind (SIGMA_CONST / SIGMA_T3), dt and optionally x0, x1, a, c, Cv, dd."""
+
+    def __init__(self, instances, stream=None):
+        L = lib()
+        arr = (Diffusion1D * len(instances))()
+        self._keep = []
+        self.nx = []
+        for i, p in enumerate(instances):
+            sig = _f64(np.broadcast_to(p["sigma"], (p["nx"],)))
+            self._keep.append(sig)
+            arr[i] = Diffusion1D(p["nx"], _ptr(sig), p.get("kind", SIGMA_CONST), p.get("x0", 0.0), p.get("x1", 1.0),
+                                 p["dt"], p.get("a", 1.0), p.get("c", 1.0), p.get("Cv", 1.0), p.get("dd", 0.0))
+            self.nx.append(int(p["nx"]))
+        h = ctypes.c_void_p()
+        st = L.grte_diff_create(len(instances), arr, stream, ctypes.byref(h))
+        self.h = h
+        if st != GRTE_OK:
+            msg = L.grte_diff_last_error(h).decode() if h.value else "create failed"
+            L.grte_diff_destroy(h)
+            self.h = None
+            raise GrteError(st, msg)
+
+    def _check(self, st, allow=()):
+        if st != GRTE_OK and st not in allow:
+            raise GrteError(st, lib().grte_diff_last_error(self.h).decode())
+        return st
+
+    def set_T(self, inst, T):
+        T = _f64(T)
+        return self._check(lib().grte_diff_set_T(self.h, inst, _ptr(T), T.size))
+
+    def step(self, n=1):
+        return self._check(lib().grte_diff_step(self.h, n))
+
+    def sync(self, allow=()):
+        return self._check(lib().grte_diff_sync(self.h), allow)
+
+    def T(self, inst, allow=()):
+        out = np.empty(self.nx[inst])
+        self._check(lib().grte_diff_get_T(self.h, inst, _ptr(out), out.size), allow)
+        return out
+
+    def Ustar(self, inst, allow=()):
+        out = np.empty(self.nx[inst])
+        self._check(lib().grte_diff_get_Ustar(self.h, inst, _ptr(out), out.size), allow)
+        return out
+
+    def close(self):
+        if self.h is not None:
+            lib().grte_diff_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
