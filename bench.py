@@ -98,6 +98,135 @@ def specs_of(runs):
     return out
 
 
+def roofline_of(prof, runs, prec, hbm_peak, workload):
+    """Roofline block of the dominant kernel (largest share of the profiled device time):
+    algorithmic bytes (or flops) per launch over its average event-timed launch."""
+    from paper_1811_05579_gb300 import grte as G
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    tot_prof = sum(v[0] for v in prof.values())
+    nelem = sum(r.nx * (r.n_dir // 2) for r in runs)
+    roof = None
+    avg_s = dom_ms / dom_n * 1e-3
+    if prec == G.FP64 and dom_name in ("pred_hom", "pred_full"):
+        flops = HOM_FLOPS_PER_ELEM * nelem
+        achieved = flops / avg_s / 1e9
+        roof = {"kernel": "k_pred_line<%s,double>" % dom_name[5:].upper(), "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)", "frac": achieved / FP64_PEAK_GFLOPS,
+                "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s)",
+                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n}
+    elif dom_name in ("pred_hom", "pred_full", "pred_factor", "corr"):
+        # binary32 line pass: bytes it must move per line element with stored factors
+        # (4 factors + right-hand side/solution buffer write and read + flux out, 4 B each)
+        byts = LINE_BYTES_PER_ELEM_F32 * nelem
+        achieved = byts / avg_s / 1e9
+        roof = {"kernel": "k_pred_line<%s,float>" % dom_name[5:].upper() if dom_name.startswith("pred") else "k_corr_line<float>",
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n,
+                "bytes_per_elem": LINE_BYTES_PER_ELEM_F32}
+    elif dom_name == "pred_solve":
+        # the fused prediction solve (one persistent cluster per instance): the bytes it
+        # must move are the state read once (E, O in the bulk type) and per cell the
+        # coefficient and vector traffic of the solve's inputs and outputs
+        es = 8 if prec == G.FP64 else 4
+        byts = sum(r.nx * (r.n_dir // 2) * 2 * es + r.nx * FUSED_BYTES_PER_CELL for r in runs)
+        achieved = byts / avg_s / 1e9
+        roof = {"kernel": "k_pred_fused (whole prediction solve per instance cluster)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
+                "bytes_model": "state read once (2 x %d B per line element) + %d B per cell" % (es, FUSED_BYTES_PER_CELL),
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n,
+                "note": "latency-bound: barrier and binary64 dependency chains of ~7 Krylov steps per launch"}
+    elif dom_name == "gmres":
+        es = 8 if prec == G.FP64 else 4
+        M = runs[0].n_dir // 2
+        byts = sum(r.nx for r in runs) * GMRES_BYTES_PER_CELL(M, es)
+        achieved = byts / avg_s / 1e9
+        earlier = GMRES_TRAFFIC_SLAB6_MIXED_EARLIER if (workload == "slab6" and prec == G.MIXED) else None
+        roof = {"kernel": "k_gmres (all modes; Arnoldi step dominant)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
+                "traffic_before_last_kernel_change": earlier,
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n, "bytes_per_cell": GMRES_BYTES_PER_CELL(M, es)}
+    else:
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n}
+    return roof, dom_name
+
+
+def sub_result(name, steps, warmup, sequential=False):
+    """A further workload on the same GPU: the mixed form (the library's default solve)
+    and the plain FP64 form, each timed with CUDA events over `steps` steps after
+    `warmup`, the T error of the mixed form against FP64 after the same steps, and one
+    step of each from the FP64 state reached; with `sequential`, the instances also
+    advanced one handle each, one after the other."""
+    import torch
+    from paper_1811_05579_gb300 import grte as G
+    runs, cfg = workload_instances(name)
+    specs = specs_of(runs)
+    ups = sum(r.nx * r.n_dir for r in runs)
+    stream = torch.cuda.current_stream()
+    out = {"config": cfg, "steps": steps, "warmup": warmup}
+    hs = {}
+    for key, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+        h = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
+        for i, r in enumerate(runs):
+            h.set_state(i, r.T0)
+        for _ in range(warmup):
+            h.step(1)
+        h.sync(allow=ALLOW1D)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[key] = {"value": ups / (ms * 1e-3), "ms_per_step": ms}
+        hs[key] = h
+    errs = []
+    for i in range(len(runs)):
+        a_, b_ = hs["mixed"].T(i, allow=ALLOW1D), hs["fp64"].T(i, allow=ALLOW1D)
+        errs.append(float(np.max(np.abs(a_ - b_) / np.maximum(np.abs(b_), 1e-300))))
+    out["t_max_rel_err_trajectory"] = max(errs)
+    snap = [(hs["fp64"].T(i, allow=ALLOW1D), hs["fp64"].E(i, allow=ALLOW1D), hs["fp64"].O(i, allow=ALLOW1D))
+            for i in range(len(runs))]
+    one = {}
+    for key, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+        h = G.Grte(specs, precision=prec, stream=stream.cuda_stream)
+        for i, (T_, E_, O_) in enumerate(snap):
+            h.set_state(i, T_, E_, O_)
+        h.step(1)
+        one[key] = [h.T(i, allow=ALLOW1D) for i in range(len(runs))]
+        h.close()
+    out["t_max_rel_err_one_step"] = max(float(np.max(np.abs(a_ - b_) / np.maximum(np.abs(b_), 1e-300)))
+                                        for a_, b_ in zip(one["mixed"], one["fp64"]))
+    for h in hs.values():
+        h.close()
+    if sequential:
+        hl = [G.Grte([sp], precision=G.MIXED, stream=stream.cuda_stream) for sp in specs]
+        for hh, r in zip(hl, runs):
+            hh.set_state(0, r.T0)
+            hh.step(1)
+        ks = 2
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ks):
+            for hh in hl:
+                hh.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / ks
+        out["sequential_mixed"] = {"value": ups / (ms * 1e-3), "ms_per_step": ms, "handles": len(hl), "steps": ks}
+        for hh in hl:
+            hh.close()
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -227,6 +356,8 @@ def main():
                     help="threads per line solve (0: the library's autotuner)")
     ap.add_argument("--sequential-compare", action="store_true",
                     help="also time the same instances advanced one handle at a time")
+    ap.add_argument("--no-sub-results", action="store_true",
+                    help="slab workload: skip the batched 256-instance and 128-cell Marshak sub-results")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload in ("checker2d", "lognormal2d"):
@@ -388,6 +519,21 @@ def main():
                "t_max_rel_err_one_step": max(errs1), "t_rel_err_one_step_per_run": errs1,
                "t_max_rel_err_trajectory": max(errs), "t_rel_err_trajectory_per_run": errs,
                "steps_compared": args.warmup + args.steps}
+        # the FP64 form's own roofline: per-kernel event pairs over a few eager steps
+        hd.profile_begin(G.KERNELS)
+        for _ in range(min(args.steps, 3)):
+            flush.zero_()
+            hd.step(1)
+        prof64 = hd.profile_end()
+        torch.cuda.synchronize()
+        peak = 6800.0
+        try:
+            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except Exception:
+            pass
+        cmp["fp64_roofline"] = roofline_of(prof64, runs, G.FP64, peak, args.workload)[0]
+        cmp["fp64_kernel_share"] = {k: round(v[0] / sum(x[0] for x in prof64.values()), 4)
+                                    for k, v in sorted(prof64.items())}
         hd.close()
         hm.close()
 
@@ -419,58 +565,8 @@ def main():
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except Exception:
         pass
-    # dominant kernel (largest share of device time in the timed region)
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
+    roof, dom_name = roofline_of(prof, runs, prec, hbm_peak, args.workload)
     tot_prof = sum(v[0] for v in prof.values())
-    nelem = sum(r.nx * (r.n_dir // 2) for r in runs)
-    roof = None
-    avg_s = dom_ms / dom_n * 1e-3
-    if prec == G.FP64 and dom_name in ("pred_hom", "pred_full"):
-        flops = HOM_FLOPS_PER_ELEM * nelem
-        achieved = flops / avg_s / 1e9
-        roof = {"kernel": "k_pred_line<%s,double>" % dom_name[5:].upper(), "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s)",
-                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n}
-    elif dom_name in ("pred_hom", "pred_full", "pred_factor", "corr"):
-        # binary32 line pass: bytes it must move per line element with stored factors
-        # (4 factors + right-hand side/solution buffer write and read + flux out, 4 B each)
-        byts = LINE_BYTES_PER_ELEM_F32 * nelem
-        achieved = byts / avg_s / 1e9
-        roof = {"kernel": "k_pred_line<%s,float>" % dom_name[5:].upper() if dom_name.startswith("pred") else "k_corr_line<float>",
-                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom_n,
-                "bytes_per_elem": LINE_BYTES_PER_ELEM_F32}
-    elif dom_name == "pred_solve":
-        # the fused prediction solve (one persistent cluster per instance): the bytes it
-        # must move are the state read once (E, O in the bulk type) and per cell the
-        # coefficient and vector traffic of the solve's inputs and outputs
-        es = 8 if prec == G.FP64 else 4
-        byts = sum(r.nx * (r.n_dir // 2) * 2 * es + r.nx * FUSED_BYTES_PER_CELL for r in runs)
-        achieved = byts / avg_s / 1e9
-        roof = {"kernel": "k_pred_fused (whole prediction solve per instance cluster)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
-                "bytes_model": "state read once (2 x %d B per line element) + %d B per cell" % (es, FUSED_BYTES_PER_CELL),
-                "avg_launch_us": avg_s * 1e6, "launches": dom_n,
-                "note": "latency-bound: barrier and binary64 dependency chains of ~7 Krylov steps per launch"}
-    elif dom_name == "gmres":
-        es = 8 if prec == G.FP64 else 4
-        M = runs[0].n_dir // 2
-        byts = sum(r.nx for r in runs) * GMRES_BYTES_PER_CELL(M, es)
-        achieved = byts / avg_s / 1e9
-        earlier = GMRES_TRAFFIC_SLAB6_MIXED_EARLIER if (args.workload == "slab6" and prec == G.MIXED) else None
-        roof = {"kernel": "k_gmres (all modes; Arnoldi step dominant)", "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
-                "traffic_before_last_kernel_change": earlier,
-                "avg_launch_us": avg_s * 1e6, "launches": dom_n, "bytes_per_cell": GMRES_BYTES_PER_CELL(M, es)}
-    else:
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
-                "avg_launch_us": avg_s * 1e6, "launches": dom_n}
     step_s = t_ms * 1e-3 / args.steps
     bpu = 24 if prec == G.FP64 else 12
     h_mode = ("one CUDA graph launch per step: the prediction solve is one persistent cluster kernel per "
@@ -502,6 +598,9 @@ def main():
                 "clocks": clk}
         if cmp is not None:
             line["vs_fp64"] = cmp
+        if args.workload == "slab6" and prec == G.MIXED and not args.no_sub_results and world == 1:
+            line["sub_results"] = {"batched256": sub_result("batched256", 5, 3, sequential=True),
+                                   "marshak128": sub_result("marshak128", 125, 3)}
         if seq is not None:
             line["sequential"] = seq
         if not args.no_cpu_baseline:
