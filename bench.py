@@ -51,6 +51,10 @@ GMRES_TRAFFIC_SLAB6_MIXED_EARLIER = 13.19e6
 # inputs it reads once (T^n, U^n, rho^n and the 16 coefficient arrays of the cell) and
 # the outputs rho* and F* (20 x 8 B).
 FUSED_BYTES_PER_CELL = 160
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_pred_fused launch on one 8192-cell,
+# 64-direction slab run (ncu --set full; profiles/ncu_pred_fused_slab1.md), taken with the
+# kernel as it stands; a slab launch carries one such instance per run
+FUSED_DRAM_BYTES_SLAB_INSTANCE = 4.030208e6
 
 
 def job_throughput(updates_per_step, steps, t_ms, world, dist=None, device="cuda"):
@@ -134,7 +138,11 @@ def roofline_of(prof, runs, prec, hbm_peak, workload):
         achieved = byts / avg_s / 1e9
         roof = {"kernel": "k_pred_fused (whole prediction solve per instance cluster)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "traffic": (FUSED_DRAM_BYTES_SLAB_INSTANCE * len(runs)
+                            if workload in ("slab6", "slab1") and prec == G.MIXED else None),
+                "traffic_source": "ncu dram bytes of one slab-run launch, times the runs in a launch",
+                "algorithmic_bytes_per_launch": byts,
                 "bytes_model": "state read once (2 x %d B per line element) + %d B per cell" % (es, FUSED_BYTES_PER_CELL),
                 "avg_launch_us": avg_s * 1e6, "launches": dom_n,
                 "note": "latency-bound: barrier and binary64 dependency chains of ~7 Krylov steps per launch"}
