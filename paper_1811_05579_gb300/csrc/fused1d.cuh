@@ -65,7 +65,7 @@ struct FSmem {
   double fdat[kFS];                                     // data part of the flux (data passes)
   // the correction's flux (sigma_0/T^3): node coefficients d* of V* = (U*)^{3/4} at the
   // nodes c0 + t (t = 0..kFS), the node moments Om = sum_k w_k v_k O^n, the flux per cell
-  double Om[kFS + 1], flc[kFS];
+  double Om[kFS + 1];                                  // node moments of O^n (sigma_0/T^3 data)
   double pu[kFS];                                       // preconditioner solution (slice)
   // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
   // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
@@ -668,36 +668,6 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   }
   __syncthreads();
   f_line_solve(sm, cl, G, par);
-  const bool corr = FULL && I.kind == GRTE_SIGMA_T3;
-  double* const vst = reinterpret_cast<double*>(&sm.ra[0][0]);   // kFS + 2 cell values (ra, rb)
-  double* const dsd = reinterpret_cast<double*>(&sm.rc[0][0]);   // kFS + 1 node values (rc, rr)
-  if (corr) {
-    // the correction's flux (f_vstar, f_dnode) of the cells that are not inflow wall
-    // cells (those keep the prediction's flux: the wall node takes the prediction's value
-    // shifted by the change at the adjacent node): node coefficients, then its rho and
-    // data parts
-    // (V* and d* live in the reduced-system arrays, dead after the line solve until the
-    // next pass)
-    const int t = threadIdx.x;
-    const int64_t j = G.c0 + t;
-    vst[t + 1] = j < N ? f_vstar(D, I, G, X, j) : 0.0;
-    if (t == 0) vst[0] = (j > 0 && j <= N) ? f_vstar(D, I, G, X, j - 1) : 0.0;
-    if (t == kFS - 1) vst[kFS + 1] = j + 1 < N ? f_vstar(D, I, G, X, j + 1) : 0.0;
-    __syncthreads();
-    dsd[t] = f_dnode(D, I, G, j, vst[t], vst[t + 1]);
-    if (t == kFS - 1) dsd[kFS] = f_dnode(D, I, G, j + 1, vst[kFS], vst[kFS + 1]);
-    __syncthreads();
-    if (j < N && !(inflow && (j == 0 || j == N - 1))) {
-      const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
-                   xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
-      const double dL = dsd[t], dR = dsd[t + 1];
-      sm.flc[t] = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) * f_div(1.0, I.dx) +
-                  f_div(I.eps * I.eps, I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
-    } else {
-      sm.flc[t] = 0.0;
-    }
-    __syncthreads();
-  }
   // inflow walls: e re-solved in double from the neighbour; e/o wall flux in double
   if (inflow && w == 0) {
     for (int side = 0; side < 2; ++side) {
@@ -740,31 +710,17 @@ __device__ void f_pass(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       if (FULL) {
         // compensated binary32 sum (Knuth's two-sum): the rounding error of every addition
         // is carried in lo, so hi + lo holds the sum to about 2^-48 relative
-        float hi = 0.0f, lo = 0.0f, hc = 0.0f, lc = 0.0f;
-        const float idxf = __frcp_rn((float)I.dx);
-        const float dRc = corr ? (float)dsd[t + 1] * idxf : 0.0f;
-        const float dLc = corr ? (float)dsd[t] * idxf : 0.0f;
+        float hi = 0.0f, lo = 0.0f;
         for (int kk = 0; kk < G.M; ++kk) {
           const float ej = sm.x[t][kk];
           const float wv2k = -sm.wvk[kk] * sm.vk[kk];
-          const float gr = xr[kk] - ej, gl_ = ej - xl[kk];
-          {
-            const float a = wv2k * (dR * gr - dL * gl_);
-            const float sN = hi + a;
-            const float bb = sN - hi;
-            lo += (hi - (sN - bb)) + (a - bb);
-            hi = sN;
-          }
-          if (corr) {
-            const float a = wv2k * (dRc * gr - dLc * gl_);
-            const float sN = hc + a;
-            const float bb = sN - hc;
-            lc += (hc - (sN - bb)) + (a - bb);
-            hc = sN;
-          }
+          const float a = wv2k * (dR * (xr[kk] - ej) - dL * (ej - xl[kk]));
+          const float sN = hi + a;
+          const float bb = sN - hi;
+          lo += (hi - (sN - bb)) + (a - bb);
+          hi = sN;
         }
         sm.fl[t] += sm.fdat[t] + ((double)hi + (double)lo);
-        if (corr) sm.flc[t] += (double)hc + (double)lc;
       } else {
         float acc = (float)sm.fl[t];
         for (int kk = 0; kk < G.M; ++kk) {
@@ -1031,6 +987,55 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   __syncthreads();
 }
 
+// The flux the temperature equation of the sigma_0/T^3 correction takes (Eq. dis-cor-marshak1
+// with the predicted data; f_vstar, f_dnode), written to D.Fc for the slice's cells that
+// are not inflow wall cells (those keep F*, written with it).  Called once, after the
+// solve: the last data pass ran at the converged iterate X, and its angular unknowns
+// (E* - rho*) are still in sm.x with the neighbours' edge values in sm.xlr.  Node
+// coefficients in binary64 (the rho part needs them so); the e/o part as a compensated
+// binary32 sum like the prediction's.  V* and d* live in the reduced-system arrays,
+// free after the line solves.
+__device__ void f_corr_flux(FSmem& sm, const Dev& D, const Inst& I, const FGeo& G, const FVec& X) {
+  const int64_t N = G.N;
+  const bool inflow = I.bc == GRTE_BC_INFLOW;
+  double* const vst = reinterpret_cast<double*>(&sm.ra[0][0]);   // kFS + 2 cell values (ra, rb)
+  double* const dsd = reinterpret_cast<double*>(&sm.rc[0][0]);   // kFS + 1 node values (rc, rr)
+  const int t = threadIdx.x;
+  const int64_t j = G.c0 + t;
+  __syncthreads();
+  vst[t + 1] = j < N ? f_vstar(D, I, G, X, j) : 0.0;
+  if (t == 0) vst[0] = (j > 0 && j <= N) ? f_vstar(D, I, G, X, j - 1) : 0.0;
+  if (t == kFS - 1) vst[kFS + 1] = j + 1 < N ? f_vstar(D, I, G, X, j + 1) : 0.0;
+  __syncthreads();
+  dsd[t] = f_dnode(D, I, G, j, vst[t], vst[t + 1]);
+  if (t == kFS - 1) dsd[kFS] = f_dnode(D, I, G, j + 1, vst[kFS], vst[kFS + 1]);
+  __syncthreads();
+  if (j < N && !(inflow && (j == 0 || j == N - 1))) {
+    const double xj = f_x<true>(X, G, j), xl = j > 0 ? f_x<true>(X, G, j - 1) : 0.0,
+                 xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
+    const double dL = dsd[t], dR = dsd[t + 1];
+    // rho and data parts
+    double fc = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) * f_div(1.0, I.dx) +
+                f_div(I.eps * I.eps, I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
+    // e/o part: sum_k -w_k v_k^2 [d*_{j+1}(e_{j+1} - e_j) - d*_j (e_j - e_{j-1})]/dx
+    const float idxf = __frcp_rn((float)I.dx);
+    const float dRc = (float)dR * idxf, dLc = (float)dL * idxf;
+    const float* xlw = (t > 0) ? &sm.x[t - 1][0] : &sm.xlr[0][0];
+    const float* xrw = (t < kFS - 1) ? &sm.x[t + 1][0] : &sm.xlr[1][0];
+    float hc = 0.0f, lc = 0.0f;
+    for (int kk = 0; kk < G.M; ++kk) {
+      const float ej = sm.x[t][kk];
+      const float a = -sm.wvk[kk] * sm.vk[kk] * (dRc * (xrw[kk] - ej) - dLc * (ej - xlw[kk]));
+      const float sN = hc + a;
+      const float bb = sN - hc;
+      lc += (hc - (sN - bb)) + (a - bb);
+      hc = sN;
+    }
+    D.Fc[G.co + j] = fc + ((double)hc + (double)lc);
+  }
+  __syncthreads();
+}
+
 // The whole prediction solve of one instance per cluster.  blockIdx.x / Q indexes
 // D.finst (the instances of this launch's cluster size).
 __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restrict__ finst) {
@@ -1072,7 +1077,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       const double R = D.cf.alpha[g] * x[j] - D.cf.kcd[g] * D.rho_n[g] - D.cf.sac[g] * D.U[g] + D.cf.kdx[g] * fl;
       zv[t] = -R;
       D.Fs[g] = fl;
-      D.Fc[g] = (I.kind == GRTE_SIGMA_T3 && !(I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1))) ? sm.flc[t] : fl;
+      D.Fc[g] = fl;   // sigma_0/T^3: replaced after the solve (f_corr_flux) except at inflow walls
     } else {
       zv[t] = 0.0;
     }
@@ -1223,6 +1228,8 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
       __syncthreads();
     }
   }
+  // the correction's flux at the converged iterate (sigma_0/T^3)
+  if (I.kind == GRTE_SIGMA_T3) f_corr_flux(sm, D, I, G, FVec{x, 0.0, 0.0});
   if (G.q == 0 && t == 0) {
     D.gits[ii] = its;
     D.gcycles[ii] = cycles;
