@@ -43,119 +43,252 @@ __device__ __forceinline__ float gelu_d(float z) {
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * c * z * z);
 }
 
-// Forward pass of one sample with weights in shared memory (BF16) and activations in
-// a per-thread shared-memory row; returns the standardised output.  z1..z3 keep the
-// pre-activations when `keep` is set (for the backward pass).
-__device__ float mlp_forward(const __nv_bfloat16* __restrict__ w, const float* __restrict__ xin, float* z1,
-                             float* z2, float* z3, float* h1, float* h2, float* h3) {
-  for (int j = 0; j < kH; ++j) {
-    float acc = __bfloat162float(w[oB1 + j]);
-#pragma unroll
-    for (int i = 0; i < kIn; ++i) acc += __bfloat162float(w[oW1 + j * kIn + i]) * xin[i];
-    z1[j] = acc;
-    h1[j] = gelu(acc);
-  }
-  for (int j = 0; j < kH; ++j) {
-    float acc = __bfloat162float(w[oB2 + j]);
-    for (int i = 0; i < kH; ++i) acc += __bfloat162float(w[oW2 + j * kH + i]) * h1[i];
-    z2[j] = acc;
-    h2[j] = gelu(acc);
-  }
-  for (int j = 0; j < kH; ++j) {
-    float acc = __bfloat162float(w[oB3 + j]);
-    for (int i = 0; i < kH; ++i) acc += __bfloat162float(w[oW3 + j * kH + i]) * h2[i];
-    z3[j] = acc;
-    h3[j] = gelu(acc);
-  }
-  float out = __bfloat162float(w[oB4]);
-  for (int i = 0; i < kH; ++i) out += __bfloat162float(w[oW4 + i]) * h3[i];
-  return out;
+// ----------------------------------------------------------------------------- tensor cores
+// The 64-wide layers, their backward deltas and the weight gradients run on the tensor
+// cores: mma.sync m16n8k16, BF16 operands, FP32 accumulation.  The network is "BF16 in,
+// FP32 accumulate": the operands of every matrix product are BF16 (the weights, the
+// standardised inputs, the activations h1, h2 and the deltas of layers 3, 2, 1 at the
+// points where they enter a product); pre-activations, GELU, the output layer, the
+// bias gradients and the loss stay FP32.
+constexpr int kMlpSamples = 64;            // samples per block
+constexpr int kMlpThreads = 128;           // 4 warps, 16 samples each
+constexpr int kLd = kH + 8;                // padded row of a BF16 activation tile
+constexpr int kLdX = 16 + 8;               // padded row of the input tile (6 used, K = 16)
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-constexpr int kMlpThreads = 64;   // samples per block (activations live in shared memory)
+// D = A B + D for one 16x16 (A, row-major) x 16x8 (B, column-major) tile
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
 
-struct MlpScratch {
-  float z1[kH], z2[kH], z3[kH], h1[kH], h2[kH], h3[kH], x[kIn];
+// Fragments of the m16n8k16 shape from element accessors A(row, k) and B(k, col)
+// (lane = 4 g + q: A rows g, g + 8 and k = 2q, 2q + 1, 2q + 8, 2q + 9; B k the same,
+// column g; C rows g, g + 8 and columns 2q, 2q + 1).
+template <class FA>
+__device__ __forceinline__ void frag_a(uint32_t a[4], int lane, FA A) {
+  const int g = lane >> 2, q = lane & 3;
+  a[0] = pack2(A(g, 2 * q), A(g, 2 * q + 1));
+  a[1] = pack2(A(g + 8, 2 * q), A(g + 8, 2 * q + 1));
+  a[2] = pack2(A(g, 2 * q + 8), A(g, 2 * q + 9));
+  a[3] = pack2(A(g + 8, 2 * q + 8), A(g + 8, 2 * q + 9));
+}
+template <class FB>
+__device__ __forceinline__ void frag_b(uint32_t b[2], int lane, FB B) {
+  const int g = lane >> 2, q = lane & 3;
+  b[0] = pack2(B(2 * q, g), B(2 * q + 1, g));
+  b[1] = pack2(B(2 * q + 8, g), B(2 * q + 9, g));
+}
+
+struct MlpTile {   // shared memory of one block
+  __nv_bfloat16 w[((kNP + 7) / 8) * 8];    // the BF16 parameter vector
+  __nv_bfloat16 w1p[kH][16];               // W1 with K padded 6 -> 16
+  __nv_bfloat16 xs[kMlpSamples][kLdX];      // standardised inputs (BF16)
+  __nv_bfloat16 h1[kMlpSamples][kLd], h2[kMlpSamples][kLd];
+  __nv_bfloat16 d3[kMlpSamples][kLd], d2[kMlpSamples][kLd], d1[kMlpSamples][kLd];
+  float z1[kMlpSamples][kH], z2[kMlpSamples][kH], z3[kMlpSamples][kH];   // pre-activations, then deltas
+  float d4[kMlpSamples], err2[kMlpSamples];
+  float g[kNP];                             // block gradient (MODE 1)
 };
 
-__device__ __forceinline__ float warp_sum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Forward and (MODE 1) backward of a batch: per-block partial gradients (sum over the
-// block's samples of d(loss)/d(param), loss = mean of squared standardised errors)
-// are written to part[blockIdx.x][kNP]; MODE 0 writes predictions.  Every lane runs
-// the same loops (lanes past n contribute zero), so each gradient contribution is
-// summed over the warp by shuffles before one shared-memory atomic per warp.
+// Forward and (MODE 1) backward of 64 samples per block: MODE 0 writes predictions;
+// MODE 1 writes the block's gradient (sum over its samples of d(loss)/d(param), loss =
+// mean of squared standardised errors, `scale` = 1/n) to part[blockIdx.x][kNP] and its
+// summed squared error to loss_part.  Samples past n enter with zero inputs and zero
+// output gradient.
 template <int MODE>
 __global__ void __launch_bounds__(kMlpThreads) k_mlp(const __nv_bfloat16* __restrict__ wts, const float* __restrict__ X,
                                                      const float* __restrict__ Y, int64_t n, const float* __restrict__ norm,
                                                      float* __restrict__ out, float* __restrict__ part,
                                                      float* __restrict__ loss_part, float scale) {
-  extern __shared__ unsigned char smem_raw[];
-  __nv_bfloat16* w = (__nv_bfloat16*)smem_raw;
-  float* g = (float*)(smem_raw + ((kNP * 2 + 15) / 16) * 16);
-  MlpScratch* scr = (MlpScratch*)(g + (MODE == 1 ? kNP : 0));
-  __shared__ float lsum[kMlpThreads];
-  for (int i = threadIdx.x; i < kNP; i += blockDim.x) {
-    w[i] = wts[i];
-    if (MODE == 1) g[i] = 0.0f;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpTile& S = *reinterpret_cast<MlpTile*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int g8 = lane >> 2, q = lane & 3;
+  const int64_t s0 = (int64_t)blockIdx.x * kMlpSamples;
+  for (int i = tid; i < kNP; i += kMlpThreads) {
+    S.w[i] = wts[i];
+    if (MODE == 1) S.g[i] = 0.0f;
+  }
+  for (int i = tid; i < kH * 16; i += kMlpThreads) {
+    const int j = i / 16, k = i % 16;
+    S.w1p[j][k] = k < kIn ? wts[oW1 + j * kIn + k] : __float2bfloat16(0.0f);
+  }
+  for (int i = tid; i < kMlpSamples * 16; i += kMlpThreads) {
+    const int r = i / 16, k = i % 16;
+    const int64_t s = s0 + r;
+    float v = 0.0f;
+    if (k < kIn && s < n) v = (X[s * kIn + k] - norm[k]) / norm[kIn + k];
+    S.xs[r][k] = __float2bfloat16(v);
   }
   __syncthreads();
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool valid = s < n;
-  const int lane = threadIdx.x & 31;
-  MlpScratch& S = scr[threadIdx.x];
-  for (int i = 0; i < kIn; ++i) S.x[i] = valid ? (X[s * kIn + i] - norm[i]) / norm[kIn + i] : 0.0f;
-  const float o = mlp_forward(w, S.x, S.z1, S.z2, S.z3, S.h1, S.h2, S.h3);
+  const __nv_bfloat16* W = S.w;
+  const int r0 = wp * 16;   // this warp's samples
+  auto bias = [&](int off, int col) { return __bfloat162float(W[off + col]); };
+  // ---- layer 1: Z1 = X W1^T + b1 (K = 16, inputs padded)
+  {
+    uint32_t a[4];
+    frag_a(a, lane, [&](int r, int k) { return S.xs[r0 + r][k]; });
+    for (int nt = 0; nt < kH / 8; ++nt) {
+      const int c0 = nt * 8 + 2 * q;
+      float c[4] = {bias(oB1, c0), bias(oB1, c0 + 1), bias(oB1, c0), bias(oB1, c0 + 1)};
+      uint32_t b[2];
+      frag_b(b, lane, [&](int k, int col) { return S.w1p[nt * 8 + col][k]; });
+      mma16816(c, a, b);
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + g8 + (e >> 1) * 8, col = c0 + (e & 1);
+        S.z1[r][col] = c[e];
+        S.h1[r][col] = __float2bfloat16(gelu(c[e]));
+      }
+    }
+  }
+  __syncwarp();
+  // ---- layers 2 and 3: Z = H W^T + b (K = 64)
+  auto dense = [&](const __nv_bfloat16 (*H)[kLd], int oW, int oB, float (*Z)[kH], __nv_bfloat16 (*Hn)[kLd],
+                   float h3[kH / 8][4]) {
+    uint32_t a[4][4];
+    for (int kt = 0; kt < 4; ++kt) frag_a(a[kt], lane, [&](int r, int k) { return H[r0 + r][kt * 16 + k]; });
+    for (int nt = 0; nt < kH / 8; ++nt) {
+      const int c0 = nt * 8 + 2 * q;
+      float c[4] = {bias(oB, c0), bias(oB, c0 + 1), bias(oB, c0), bias(oB, c0 + 1)};
+      for (int kt = 0; kt < 4; ++kt) {
+        uint32_t b[2];
+        frag_b(b, lane, [&](int k, int col) { return W[oW + (nt * 8 + col) * kH + kt * 16 + k]; });
+        mma16816(c, a[kt], b);
+      }
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + g8 + (e >> 1) * 8, col = c0 + (e & 1);
+        Z[r][col] = c[e];
+        const float hv = gelu(c[e]);
+        if (Hn) Hn[r][col] = __float2bfloat16(hv);
+        if (h3) h3[nt][e] = hv;
+      }
+    }
+    __syncwarp();
+  };
+  float h3[kH / 8][4];
+  dense(S.h1, oW2, oB2, S.z2, S.h2, nullptr);
+  dense(S.h2, oW3, oB3, S.z3, nullptr, h3);
+  // ---- output: W4 . h3 + b4 (FP32), rows g and g + 8 of the warp's tile
+  float o[2] = {0.0f, 0.0f};
+  for (int nt = 0; nt < kH / 8; ++nt)
+    for (int e = 0; e < 4; ++e) o[e >> 1] += __bfloat162float(W[oW4 + nt * 8 + 2 * q + (e & 1)]) * h3[nt][e];
+  for (int hh = 0; hh < 2; ++hh) {
+    o[hh] += __shfl_xor_sync(0xffffffffu, o[hh], 1);
+    o[hh] += __shfl_xor_sync(0xffffffffu, o[hh], 2);
+    o[hh] += __bfloat162float(W[oB4]);
+  }
   if (MODE == 0) {
-    if (valid) out[s] = o * norm[2 * kIn + 1] + norm[2 * kIn];   // un-standardised prediction
+    if (q == 0)
+      for (int hh = 0; hh < 2; ++hh) {
+        const int64_t s = s0 + r0 + g8 + hh * 8;
+        if (s < n) out[s] = o[hh] * norm[2 * kIn + 1] + norm[2 * kIn];   // un-standardised prediction
+      }
     return;
   }
-  const float t = valid ? (Y[s] - norm[2 * kIn]) / norm[2 * kIn + 1] : 0.0f;
-  const float d4 = valid ? 2.0f * (o - t) * scale : 0.0f;      // d loss / d out
-  const float err2 = valid ? (o - t) * (o - t) : 0.0f;
-  auto acc = [&](int idx, float c) {
-    c = warp_sum(c);
-    if (lane == 0) atomicAdd(&g[idx], c);
-  };
-  acc(oB4, d4);
-  for (int i = 0; i < kH; ++i) {
-    acc(oW4 + i, d4 * S.h3[i]);
-    S.z3[i] = d4 * __bfloat162float(w[oW4 + i]) * gelu_d(S.z3[i]);   // delta3
+  // ---- backward
+  float d4r[2];
+  for (int hh = 0; hh < 2; ++hh) {
+    const int r = r0 + g8 + hh * 8;
+    const int64_t s = s0 + r;
+    const bool valid = s < n;
+    const float t = valid ? (Y[s] - norm[2 * kIn]) / norm[2 * kIn + 1] : 0.0f;
+    d4r[hh] = valid ? 2.0f * (o[hh] - t) * scale : 0.0f;      // d loss / d out
+    if (q == 0) {
+      S.d4[r] = d4r[hh];
+      S.err2[r] = valid ? (o[hh] - t) * (o[hh] - t) : 0.0f;
+    }
   }
-  for (int j = 0; j < kH; ++j) {
-    const float d3 = S.z3[j];
-    acc(oB3 + j, d3);
-    for (int i = 0; i < kH; ++i) acc(oW3 + j * kH + i, d3 * S.h2[i]);
-  }
-  for (int i = 0; i < kH; ++i) {
-    float a = 0.0f;
-    for (int j = 0; j < kH; ++j) a += __bfloat162float(w[oW3 + j * kH + i]) * S.z3[j];
-    S.h3[i] = a * gelu_d(S.z2[i]);                                    // delta2
-  }
-  for (int j = 0; j < kH; ++j) {
-    const float d2 = S.h3[j];
-    acc(oB2 + j, d2);
-    for (int i = 0; i < kH; ++i) acc(oW2 + j * kH + i, d2 * S.h1[i]);
-  }
-  for (int i = 0; i < kH; ++i) {
-    float a = 0.0f;
-    for (int j = 0; j < kH; ++j) a += __bfloat162float(w[oW2 + j * kH + i]) * S.h3[j];
-    S.z2[i] = a * gelu_d(S.z1[i]);                                    // delta1
-  }
-  for (int j = 0; j < kH; ++j) {
-    const float d1 = S.z2[j];
-    acc(oB1 + j, d1);
-    for (int i = 0; i < kIn; ++i) acc(oW1 + j * kIn + i, d1 * S.x[i]);
-  }
-  lsum[threadIdx.x] = err2;
+  // dW4 = sum_s d4 h3 (FP32), delta3 = d4 W4 gelu'(z3)
+  for (int nt = 0; nt < kH / 8; ++nt)
+    for (int cc = 0; cc < 2; ++cc) {
+      const int col = nt * 8 + 2 * q + cc;
+      float v = d4r[0] * h3[nt][cc] + d4r[1] * h3[nt][2 + cc];
+      for (int off = 4; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (g8 == 0) atomicAdd(&S.g[oW4 + col], v);
+      const float w4 = __bfloat162float(W[oW4 + col]);
+      for (int hh = 0; hh < 2; ++hh) {
+        const int r = r0 + g8 + hh * 8;
+        const float dv = d4r[hh] * w4 * gelu_d(S.z3[r][col]);
+        S.z3[r][col] = dv;                              // delta3 (FP32)
+        S.d3[r][col] = __float2bfloat16(dv);            // its BF16 operand copy
+      }
+    }
   __syncthreads();
-  for (int i = threadIdx.x; i < kNP; i += blockDim.x) part[(int64_t)blockIdx.x * kNP + i] = g[i];
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
+    float t = 0.0f;
+    for (int r = 0; r < kMlpSamples; ++r) t += S.d4[r];
+    S.g[oB4] = t;
+  }
+  // dW = delta^T H over the block's 64 samples (K = 64): warp wp owns output rows
+  // j = 16 wp .. 16 wp + 15 and all 64 (or the 6 input) columns
+  auto wgrad = [&](const __nv_bfloat16 (*Dl)[kLd], const __nv_bfloat16* Hin, int ldh, int ncols, int oW) {
+    const int ntiles = (ncols + 7) / 8;
+    float acc[kH / 8][4];
+    for (int nt = 0; nt < ntiles; ++nt)
+      for (int e = 0; e < 4; ++e) acc[nt][e] = 0.0f;
+    for (int kt = 0; kt < kMlpSamples / 16; ++kt) {
+      uint32_t a[4];
+      frag_a(a, lane, [&](int r, int k) { return Dl[kt * 16 + k][r0 + r]; });
+      for (int nt = 0; nt < ntiles; ++nt) {
+        uint32_t b[2];
+        frag_b(b, lane, [&](int k, int col) { return Hin[(kt * 16 + k) * ldh + nt * 8 + col]; });
+        mma16816(acc[nt], a, b);
+      }
+    }
+    for (int nt = 0; nt < ntiles; ++nt)
+      for (int e = 0; e < 4; ++e) {
+        const int j = r0 + g8 + (e >> 1) * 8, i = nt * 8 + 2 * q + (e & 1);
+        if (i < ncols) S.g[oW + j * ncols + i] = acc[nt][e];
+      }
+  };
+  // delta_prev = (delta W) gelu'(z_prev) for the warp's 16 samples (K = 64)
+  auto dprop = [&](const __nv_bfloat16 (*Dl)[kLd], int oW, float (*Z)[kH], __nv_bfloat16 (*Dn)[kLd]) {
+    uint32_t a[4][4];
+    for (int kt = 0; kt < 4; ++kt) frag_a(a[kt], lane, [&](int r, int k) { return Dl[r0 + r][kt * 16 + k]; });
+    for (int nt = 0; nt < kH / 8; ++nt) {
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int kt = 0; kt < 4; ++kt) {
+        uint32_t b[2];
+        frag_b(b, lane, [&](int k, int col) { return W[oW + (kt * 16 + k) * kH + nt * 8 + col]; });
+        mma16816(c, a[kt], b);
+      }
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + g8 + (e >> 1) * 8, col = nt * 8 + 2 * q + (e & 1);
+        const float dv = c[e] * gelu_d(Z[r][col]);
+        Z[r][col] = dv;
+        Dn[r][col] = __float2bfloat16(dv);
+      }
+    }
+  };
+  auto bgrad = [&](float (*Dz)[kH], int oB) {   // bias gradient: column sums of the FP32 deltas
+    if (tid < kH) {
+      float t = 0.0f;
+      for (int r = 0; r < kMlpSamples; ++r) t += Dz[r][tid];
+      S.g[oB + tid] = t;
+    }
+  };
+  wgrad(S.d3, &S.h2[0][0], kLd, kH, oW3);
+  bgrad(S.z3, oB3);
+  dprop(S.d3, oW3, S.z2, S.d2);
+  __syncthreads();
+  wgrad(S.d2, &S.h1[0][0], kLd, kH, oW2);
+  bgrad(S.z2, oB2);
+  dprop(S.d2, oW2, S.z1, S.d1);
+  __syncthreads();
+  wgrad(S.d1, &S.xs[0][0], kLdX, kIn, oW1);
+  bgrad(S.z1, oB1);
+  __syncthreads();
+  for (int i = tid; i < kNP; i += kMlpThreads) part[(int64_t)blockIdx.x * kNP + i] = S.g[i];
+  if (tid == 0) {
     float tt = 0.0f;
-    for (int i = 0; i < kMlpThreads; ++i) tt += lsum[i];
+    for (int i = 0; i < kMlpSamples; ++i) tt += S.err2[i];
     loss_part[blockIdx.x] = tt;
   }
 }
@@ -190,9 +323,7 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
   if (i < kNP) wb[i] = __float2bfloat16(p[i]);
 }
 
-size_t mlp_smem_bytes(int mode) {
-  return ((kNP * 2 + 15) / 16) * 16 + (mode == 1 ? kNP * sizeof(float) : 0) + kMlpThreads * sizeof(MlpScratch);
-}
+size_t mlp_smem_bytes(int) { return sizeof(MlpTile); }
 
 }  // namespace grte
 
@@ -223,7 +354,7 @@ static grte_status mfail(grte_mlp_t h, grte_status s, const std::string& m) {
 namespace grte {
 cudaError_t mlp_guess_launch(grte_mlp_t h, const float* feat, int64_t n, float* y, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  const int nb = (int)((n + kMlpThreads - 1) / kMlpThreads);
+  const int nb = (int)((n + kMlpSamples - 1) / kMlpSamples);
   k_mlp<0><<<nb, kMlpThreads, mlp_smem_bytes(0), stream>>>(h->wb, feat, nullptr, n, h->norm, y, nullptr, nullptr,
                                                             0.0f);
   return cudaGetLastError();
@@ -317,7 +448,7 @@ grte_status grte_mlp_forward(grte_mlp_t h, const float* X, int64_t n, float* y) 
   MCK(cudaMalloc(&dX, sizeof(float) * n * kIn));
   MCK(cudaMalloc(&dY, sizeof(float) * n));
   MCK(cudaMemcpy(dX, X, sizeof(float) * n * kIn, cudaMemcpyHostToDevice));
-  const int nb = (int)((n + kMlpThreads - 1) / kMlpThreads);
+  const int nb = (int)((n + kMlpSamples - 1) / kMlpSamples);
   k_mlp<0><<<nb, kMlpThreads, mlp_smem_bytes(0)>>>(h->wb, dX, nullptr, n, h->norm, dY, nullptr, nullptr, 0.0f);
   MCK(cudaGetLastError());
   MCK(cudaMemcpy(y, dY, sizeof(float) * n, cudaMemcpyDeviceToHost));
@@ -328,7 +459,7 @@ grte_status grte_mlp_forward(grte_mlp_t h, const float* X, int64_t n, float* y) 
 
 static grte_status grad_batch(grte_mlp_t h, const float* dX, const float* dY, int64_t n, float* dpart,
                               float* dlpart, float* loss) {
-  const int nb = (int)((n + kMlpThreads - 1) / kMlpThreads);
+  const int nb = (int)((n + kMlpSamples - 1) / kMlpSamples);
   k_mlp<1><<<nb, kMlpThreads, mlp_smem_bytes(1)>>>(h->wb, dX, dY, n, h->norm, nullptr, dpart, dlpart,
                                                     1.0f / (float)n);
   MCK(cudaGetLastError());
@@ -350,7 +481,7 @@ grte_status grte_mlp_grad(grte_mlp_t h, const float* X, const float* Y, int64_t 
                           float* loss) {
   if (!h || !X || !Y || !grad || n <= 0 || ng != (size_t)kNP) return GRTE_EINVAL;
   float *dX, *dY, *dpart, *dl;
-  const int nb = (int)((n + kMlpThreads - 1) / kMlpThreads);
+  const int nb = (int)((n + kMlpSamples - 1) / kMlpSamples);
   MCK(cudaMalloc(&dX, sizeof(float) * n * kIn));
   MCK(cudaMalloc(&dY, sizeof(float) * n));
   MCK(cudaMalloc(&dpart, sizeof(float) * (size_t)nb * kNP));
@@ -374,7 +505,7 @@ grte_status grte_mlp_train(grte_mlp_t h, const float* X, const float* Y, int64_t
   std::vector<int64_t> idx(n);
   for (int64_t i = 0; i < n; ++i) idx[i] = i;
   float *dX, *dY, *dpart, *dl;
-  const int nbmax = (batch + kMlpThreads - 1) / kMlpThreads;
+  const int nbmax = (batch + kMlpSamples - 1) / kMlpSamples;
   MCK(cudaMalloc(&dX, sizeof(float) * n * kIn));
   MCK(cudaMalloc(&dY, sizeof(float) * n));
   MCK(cudaMalloc(&dpart, sizeof(float) * (size_t)nbmax * kNP));

@@ -34,15 +34,22 @@ def test_mlp_forward_and_gradient_match_oracle(G):
     Y = rng.standard_normal(301).astype(np.float32)
     p = m.params()
     xs = _norm_inputs(X, mi, si).astype(np.float64)
-    out, _ = om.forward(om.unpack(om.to_bf16(p)), xs)
+    # the network's BF16 form: every product's operands in bfloat16 (tensor cores), FP32
+    # accumulation.  The kernel rounds FP32 values to bfloat16 where the oracle rounds
+    # FP64 ones, so an operand can land one bfloat16 step (2^-8 relative) apart where the
+    # two sit at a rounding tie: the bound is that of a few such steps, 2e-3
+    out, _ = om.forward(om.unpack(om.to_bf16(p)), xs, act16=True)
     y_gpu = m.forward(X)
-    assert np.max(np.abs(y_gpu - (out * 2.0 + 0.1))) < 1e-4 * max(1.0, np.max(np.abs(out * 2.0)))
+    assert np.max(np.abs(y_gpu - (out * 2.0 + 0.1))) < 2e-3 * max(1.0, np.max(np.abs(out * 2.0)))
     loss_g, g_gpu = m.grad(X, Y)
     t = (Y.astype(np.float64) - 0.1) / 2.0
     loss_o, g_o = om.loss_and_grad(p, xs, t, bf16=True)
-    assert abs(loss_g - loss_o) < 1e-4 * max(loss_o, 1e-12)
+    assert abs(loss_g - loss_o) < 2e-3 * max(loss_o, 1e-12)
     scale = np.max(np.abs(g_o))
-    assert np.max(np.abs(g_gpu - g_o)) < 1e-4 * scale, np.max(np.abs(g_gpu - g_o)) / scale
+    err = np.abs(g_gpu - g_o) / scale
+    print("forward %.2e, loss %.2e, gradient max %.2e (median %.2e)"
+          % (np.max(np.abs(y_gpu - (out * 2.0 + 0.1))), abs(loss_g - loss_o) / loss_o, err.max(), np.median(err)))
+    assert err.max() < 2e-3 and np.median(err) < 1e-5
     m.close()
 
 
