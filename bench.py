@@ -164,6 +164,41 @@ def roofline_of(prof, runs, prec, hbm_peak, workload):
     return roof, dom_name
 
 
+def mlp_throughput(n_inf=1 << 20, n_train=1 << 17, epochs=3, batch=4096):
+    """The learned guess's network on the tensor cores: inference samples/s on device
+    arrays (CUDA events over 10 calls after 3) and training samples/s (grte_mlp_train:
+    forward, backward, Adam per batch; wall clock over `epochs` epochs, the host shuffle
+    and the per-epoch upload included)."""
+    import torch
+    from paper_1811_05579_gb300 import grte as G
+    m = G.MLP(seed=1)
+    rng = np.random.default_rng(7)
+    X = torch.tensor(rng.standard_normal((n_inf, 6)), dtype=torch.float32, device="cuda")
+    y = torch.empty(n_inf, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        m.forward_device(X.data_ptr(), n_inf, y.data_ptr(), stream.cuda_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        m.forward_device(X.data_ptr(), n_inf, y.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    inf = 10 * n_inf / (e0.elapsed_time(e1) * 1e-3)
+    Xt = rng.standard_normal((n_train, 6)).astype(np.float32)
+    Yt = rng.standard_normal(n_train).astype(np.float32)
+    m.train(Xt, Yt, epochs=1, batch=batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.train(Xt, Yt, epochs=epochs, batch=batch)
+    tr = n_train * epochs / (time.perf_counter() - t0)
+    m.close()
+    return {"inference_samples_per_s": inf, "inference_batch": n_inf,
+            "training_samples_per_s": tr, "training_batch": batch, "training_samples": n_train,
+            "kernels": "mma.sync m16n8k16 BF16 -> FP32 (forward, backward deltas, weight gradients)"}
+
+
 def sub_result(name, steps, warmup, sequential=False):
     """A further workload on the same GPU: the mixed form (the library's default solve)
     and the plain FP64 form, each timed with CUDA events over `steps` steps after
@@ -608,7 +643,8 @@ def main():
             line["vs_fp64"] = cmp
         if args.workload == "slab6" and prec == G.MIXED and not args.no_sub_results and world == 1:
             line["sub_results"] = {"batched256": sub_result("batched256", 5, 3, sequential=True),
-                                   "marshak128": sub_result("marshak128", 125, 3)}
+                                   "marshak128": sub_result("marshak128", 125, 3),
+                                   "learned_guess_mlp": mlp_throughput()}
         if seq is not None:
             line["sequential"] = seq
         if not args.no_cpu_baseline:

@@ -247,6 +247,9 @@ grte_status grte_mlp_get_params(grte_mlp_t m, float* p, size_t n);
 grte_status grte_mlp_set_params(grte_mlp_t m, const float* p, size_t n);
 /* y[i] (un-standardised) for n raw feature rows X[i*6 .. i*6+5] (host arrays). */
 grte_status grte_mlp_forward(grte_mlp_t m, const float* X, int64_t n, float* y);
+/* The same on device arrays X (n x 6) and y (n) on a CUDA stream (NULL: the default
+ * stream); asynchronous (the inference the Newton kernels use). */
+grte_status grte_mlp_forward_device(grte_mlp_t m, const float* X, int64_t n, float* y, void* stream);
 /* Gradient (n_grad = GRTE_MLP_NPARAMS) of the mean squared standardised error at the current
  * BF16 weights, and that loss (host arrays). */
 grte_status grte_mlp_grad(grte_mlp_t m, const float* X, const float* y, int64_t n, float* grad, size_t n_grad,

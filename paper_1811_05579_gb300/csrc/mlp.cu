@@ -441,6 +441,14 @@ grte_status grte_mlp_set_params(grte_mlp_t h, const float* p, size_t n) {
   return GRTE_OK;
 }
 
+// Predictions y (un-standardised) of n raw feature rows X, both device arrays, on
+// `stream` (NULL: the legacy default stream); asynchronous.
+grte_status grte_mlp_forward_device(grte_mlp_t h, const float* X, int64_t n, float* y, void* stream) {
+  if (!h || !X || !y || n <= 0) return GRTE_EINVAL;
+  MCK(mlp_guess_launch(h, X, n, y, (cudaStream_t)stream));
+  return GRTE_OK;
+}
+
 // Predictions y (un-standardised) of n raw feature rows X (host arrays).
 grte_status grte_mlp_forward(grte_mlp_t h, const float* X, int64_t n, float* y) {
   if (!h || !X || !y || n <= 0) return GRTE_EINVAL;

@@ -99,7 +99,7 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_test_fail_alloc_after", "grte_create", "grte_handle_set_initial", "grte_handle_step",
             "grte_handle_sync", "grte_handle_get_T", "grte_handle_destroy", "grte_diff_create", "grte_diff_set_T",
             "grte_diff_step", "grte_diff_sync", "grte_diff_get_T", "grte_diff_get_Ustar", "grte_diff_last_error",
-            "grte_diff_destroy"]
+            "grte_diff_destroy", "grte_mlp_forward_device"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
 PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
 MLP_NPARAMS = 8833
@@ -170,6 +170,8 @@ def load_library(path=LIB_PATH):
     lib.grte_mlp_get_params.argtypes = [ctypes.c_void_p, _fp, ctypes.c_size_t]
     lib.grte_mlp_set_params.argtypes = [ctypes.c_void_p, _fp, ctypes.c_size_t]
     lib.grte_mlp_forward.argtypes = [ctypes.c_void_p, _fp, ctypes.c_int64, _fp]
+    lib.grte_mlp_forward_device.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p]
     lib.grte_mlp_grad.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, _fp, ctypes.c_size_t, _fp]
     lib.grte_mlp_train.argtypes = [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_float, ctypes.c_uint64, _fp]
@@ -305,6 +307,11 @@ class MLP:
         y = np.empty(X.shape[0], dtype=np.float32)
         self._check(lib().grte_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(y)))
         return y
+
+    def forward_device(self, x_ptr, n, y_ptr, stream=None):
+        """Inference on device arrays (addresses as ints) on `stream` (asynchronous)."""
+        self._check(lib().grte_mlp_forward_device(self.h, ctypes.c_void_p(x_ptr), n, ctypes.c_void_p(y_ptr),
+                                                  ctypes.c_void_p(stream) if stream else None))
 
     def grad(self, X, Y):
         X, Y = _f32(X), _f32(Y)
