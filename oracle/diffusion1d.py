@@ -118,12 +118,15 @@ def implicit_T4_step(T, sig, dx, dt, a=1.0, c=1.0, Cv=1.0, Dd=3.0, tol=1e-14, ma
     return x
 
 
-def implicit_T7_step(T, sig0, dx, dt, a=1.0, c=1.0, Cv=1.0, TL=None, TR=None, tol=1e-13, maxit=200):
+def implicit_T7_step(T, sig0, dx, dt, a=1.0, c=1.0, Cv=1.0, TL=None, TR=None, tol=1e-13, maxit=200, p=3.0):
     """One step of the fully implicit limit solver for sigma = sigma_0/T^3 (Sec. 6.5,
     Eq. diff_solver):
 
       (T^4 - T_n^4)/dt + (Cv/a)(T - T_n)/dt
           = 4c/(21 dx^2) [ k_{i+1/2} (T_{i+1}^7 - T_i^7) - k_{i-1/2} (T_i^7 - T_{i-1}^7) ],
+
+    and for sigma_0/T^p (p given) the same with T^7 -> T^{p+4} and 21 -> 3 (p + 4): the
+    limit flux a c T^p/(3 sigma_0) d(T^4)/dx = 4 a c/(3 (p + 4) sigma_0) d(T^{p+4})/dx.
 
     k_{i+1/2} = (1/sigma_0)_{i+1/2}, the mean of 1/sigma_0 of the two cells (the
     displayed average).  Walls (the paper does not print them): TL / TR given - the
@@ -137,14 +140,15 @@ def implicit_T7_step(T, sig0, dx, dt, a=1.0, c=1.0, Cv=1.0, TL=None, TR=None, to
     un = Tn ** 4
     inv = 1.0 / np.asarray(sig0, dtype=np.float64) * np.ones(N)
     kf = 0.5 * (inv[:-1] + inv[1:])                  # interior faces 1..N-1
-    coef = 4.0 * c / (21.0 * dx ** 2)
+    m = p + 4.0
+    coef = 4.0 * c / (3.0 * m * dx ** 2)
     kL = 2.0 * inv[0] if TL is not None else 0.0     # half-cell distance at the walls
     kR = 2.0 * inv[-1] if TR is not None else 0.0
-    bL = TL ** 7 if TL is not None else 0.0
-    bR = TR ** 7 if TR is not None else 0.0
+    bL = TL ** m if TL is not None else 0.0
+    bR = TR ** m if TR is not None else 0.0
     u = un.copy()
     for _ in range(maxit):
-        V = u ** 1.75                                  # T^7
+        V = u ** (m / 4.0)                             # T^{p+4}
         flux = np.zeros(N)
         fi = kf * (V[1:] - V[:-1])
         flux[:-1] += fi
@@ -152,7 +156,7 @@ def implicit_T7_step(T, sig0, dx, dt, a=1.0, c=1.0, Cv=1.0, TL=None, TR=None, to
         flux[0] += kL * (bL - V[0])
         flux[-1] += kR * (bR - V[-1])
         F = (u - un) / dt + Cv / a * (u ** 0.25 - Tn) / dt - coef * flux
-        dV = 1.75 * u ** 0.75
+        dV = (m / 4.0) * u ** (m / 4.0 - 1.0)
         di = 1.0 / dt + Cv / a * 0.25 * np.maximum(u, 1e-300) ** -0.75 / dt
         di[:-1] += coef * kf * dV[:-1]
         di[1:] += coef * kf * dV[1:]

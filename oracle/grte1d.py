@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY - see oracle/__init__.py.
 
 Follows Algorithm 2 (Sec. 4) for a temperature-independent opacity sigma(x) and its
-sigma/T^3 form (Sec. 5).  Notation (0-based):
+sigma/T^3 form (Sec. 5), the latter for a general exponent sigma_0/T^p (Problem.p, 3 by
+default; the paper treats p = 3 and names other nonlinearities as extensions, Sec. 1 and
+Sec. 5).  Notation (0-based):
 
   cells  j = 0..N-1 at x_{j+1/2}: E[j, k], U[j], T[j]          (Eq. E000)
   nodes  i = 0..N   at x_i = i dx: O[i, k]                      (Eq. O000)
@@ -15,10 +17,13 @@ O = (I(v) - I(-v))/(2 eps) (Eq. EO), so I(+v) = E + eps O and I(-v) = E - eps O.
 Both opacity forms are written with two per-cell multipliers:
 
   kappa  multiplies the time-derivative and streaming terms: 1 for sigma(x);
-         K = T^3 for sigma/T^3 (Eq. dis-pre-marshak, "multiplied to the left hand
+         K = T^p for sigma/T^p (Eq. dis-pre-marshak, "multiplied to the left hand
          side"), with node values K_i = (K_{i-1/2} + K_{i+1/2})/2.
-  theta  multiplies sigma in the U equation: T^3 for sigma(x) (Eq. dis-pre3), 1 for
-         sigma/T^3 (third line of Eq. dis-pre-marshak).
+  theta  multiplies sigma in the U equation: T^3 for sigma(x) (Eq. dis-pre3), T^{3-p}
+         for sigma/T^p (1 at p = 3: third line of Eq. dis-pre-marshak; the factor
+         4 T^3 of dU = 4 T^3 dT over the T^p the equation was multiplied by).
+  In the correction, V* = max(U*, 0)^{p/4} (= (T^{n+1*})^p) takes the place of
+  (U*)^{3/4}.  p = 0 gives back the sigma(x) scheme exactly; 0 <= p <= 3.
 
 and "sig" is sigma(x) (or sigma_0(x) of sigma_0/T^3), given per cell.  Node values
 of sig are the harmonic mean of the two neighbouring cells (the paper evaluates
@@ -46,7 +51,7 @@ import scipy.sparse.linalg as spla
 from .scalar import quartic_root
 
 SIGMA_CONST = "const"   # sigma(x), independent of T
-SIGMA_T3 = "t3"         # sigma_0(x) / T^3
+SIGMA_T3 = "t3"         # sigma_0(x) / T^p (p = 3 unless Problem.p says otherwise)
 
 
 @dataclass
@@ -67,6 +72,7 @@ class Problem:
     bR: np.ndarray = None    # (M,) inflow I(L, -v_k)
     x0: float = 0.0
     x1: float = 1.0
+    p: float = 3.0           # the exponent of sigma_0/T^p (kind 't3')
 
     def __post_init__(self):
         self.v = np.asarray(self.v, dtype=np.float64)
@@ -157,11 +163,11 @@ def _multipliers(P, T):
         kn = np.ones(N + 1)
         theta = T ** 3
     elif P.kind == SIGMA_T3:
-        K = T ** 3
+        K = T ** P.p
         kc = K
         kn = np.zeros(N + 1)
         kn[1:-1] = 0.5 * (K[:-1] + K[1:])
-        theta = np.ones(N)
+        theta = T ** (3.0 - P.p)
     else:
         raise ValueError(P.kind)
     return kc, kn, theta
@@ -405,7 +411,7 @@ def correction_temperature(P, S, Fstar, Ustar):
     if P.kind == SIGMA_CONST:
         kap = np.ones(P.N)
     else:
-        kap = np.maximum(Ustar, 0.0) ** 0.75
+        kap = np.maximum(Ustar, 0.0) ** (P.p / 4.0)
     A = sig * a / dt
     B = sig * Cv / dt + eps ** 2 * kap * Cv / (c * dt ** 2)
     R = sig * (rho_n / (c * dt) - Fstar / dx) + B * S.T
@@ -429,7 +435,7 @@ def correct_intensity(P, S, Tnew):
         kc = np.ones(N)
         kn = np.ones(N + 1)
     else:
-        K = Tnew ** 3
+        K = Tnew ** P.p
         kc = K
         kn = np.zeros(N + 1)
         kn[1:-1] = 0.5 * (K[:-1] + K[1:])
@@ -514,7 +520,7 @@ def correction_flux(P, S, Es, Os, Us):
         return flux_div(P, Os)
     N, M = P.N, P.M
     eps, c, dt, dx = P.eps, P.c, P.dt, P.dx
-    V = np.maximum(Us, 0.0) ** 0.75
+    V = np.maximum(Us, 0.0) ** (P.p / 4.0)
     Vn = np.zeros(N + 1)
     Vn[1:-1] = 0.5 * (V[:-1] + V[1:])
     sn = P.node_sig()

@@ -88,6 +88,7 @@ class Problem2D:
     by1: float = 0.0
     Lx: float = 1.0
     Ly: float = 1.0
+    p: float = 3.0           # the exponent of sigma_0/T^p (kind 't3'; see grte1d)
 
     def __post_init__(self):
         self.mu = np.asarray(self.mu, dtype=np.float64)
@@ -151,7 +152,7 @@ def rho_of(P, E):
 def _kappa_theta(P, T):
     if P.kind == SIGMA_CONST:
         return np.ones(P.nc), T ** 3
-    return T ** 3, np.ones(P.nc)
+    return T ** P.p, T ** (3.0 - P.p)
 
 
 def _vertex_kind(P, i, j):
@@ -501,7 +502,7 @@ def correction_flux(P, S, Es, Os, Us):
     if P.kind == SIGMA_CONST:
         return flux_div(P, Os, Es)
     eps, c, dt = P.eps, P.c, P.dt
-    V = np.maximum(Us, 0.0) ** 0.75
+    V = np.maximum(Us, 0.0) ** (P.p / 4.0)
     kv, sv = _vertex_coef(P, V)
     with np.errstate(divide="ignore", invalid="ignore"):
         d = np.where(kv > 0, kv / (kv * eps ** 2 / (c * dt) + sv), 0.0)
@@ -563,7 +564,7 @@ def correction_temperature(P, S, Fdiv, Ustar):
     eps, c, a, dt, Cv = P.eps, P.c, P.a, P.dt, P.Cv
     sig = P.sig.ravel()
     rho_n = rho_of(P, S.E)
-    kap = np.ones(P.nc) if P.kind == SIGMA_CONST else np.maximum(Ustar, 0.0) ** 0.75
+    kap = np.ones(P.nc) if P.kind == SIGMA_CONST else np.maximum(Ustar, 0.0) ** (P.p / 4.0)
     A = sig * a / dt
     B = sig * Cv / dt + eps ** 2 * kap * Cv / (c * dt ** 2)
     R = sig * (rho_n / (c * dt) - Fdiv) + B * S.T
