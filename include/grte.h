@@ -49,7 +49,10 @@ typedef enum {
 } grte_status;
 
 enum { GRTE_SIGMA_CONST = 0, /* sigma(x), independent of T (Sec. 4)            */
-       GRTE_SIGMA_T3 = 1     /* sigma_0(x) / T^3 (Sec. 5, Eq. marshak00)        */ };
+       GRTE_SIGMA_T3 = 1,    /* sigma_0(x) / T^3 (Sec. 5, Eq. marshak00)        */
+       GRTE_SIGMA_POW = 2    /* sigma_0(x) / T^p, 0 <= p <= 3 (sigma_p): the Sec. 5 form with
+                                kappa = T^p, theta = T^{3-p}, V* = (U*)^{p/4} in the
+                                correction (p = 3: GRTE_SIGMA_T3; p = 0: GRTE_SIGMA_CONST) */ };
 enum { GRTE_BC_INFLOW = 0,   /* I(0,v) = b_L(v), I(L,-v) = b_R(-v), v > 0 (Eq. BC1d, Eq. bc-pre) */
        GRTE_BC_REFLECT = 1,  /* I(wall, v) = I(wall, -v): odd part zero at the walls (1D)        */
        GRTE_BC_PERIODIC = 2  /* 2D only: the axis wraps around                                   */ };
@@ -71,6 +74,7 @@ typedef struct {
   double dt;             /* time step > 0                                                    */
   double a, c, Cv;       /* radiation constant, light speed, heat capacity (> 0)            */
   double eps;            /* scaled mean free path epsilon > 0                                */
+  double sigma_p;        /* the exponent p of GRTE_SIGMA_POW (ignored otherwise)              */
 } grte_instance1d;
 
 typedef struct {
@@ -332,6 +336,7 @@ typedef struct {
   double b_y0, b_y1;     /* the same on y = 0 and y = ly                                      */
   double lx, ly;         /* domain [0, lx] x [0, ly]                                          */
   double dt, a, c, Cv, eps;
+  double sigma_p;        /* the exponent p of GRTE_SIGMA_POW (ignored otherwise)              */
 } grte_instance2d;
 
 /* Create a 2D handle (inputs copied; opt may be NULL: precision, krylov_rtol (root mean
@@ -395,9 +400,10 @@ typedef struct {
   const double* w;         /* host, M or K weights (NULL with mu NULL)                        */
 } grte_quadrature;
 typedef struct {
-  int kind;                /* GRTE_SIGMA_CONST or GRTE_SIGMA_T3                              */
+  int kind;                /* GRTE_SIGMA_CONST, GRTE_SIGMA_T3 or GRTE_SIGMA_POW              */
   const double* sigma0;    /* host, one value per cell (2D row-major [j*nx + i]), or NULL     */
   double sigma0_scalar;    /* used when sigma0 is NULL                                       */
+  double sigma_p;          /* the exponent p of GRTE_SIGMA_POW                              */
 } grte_opacity;
 typedef struct {
   int kind[4];             /* edges x0, x1, y0, y1: GRTE_BC_INFLOW, GRTE_BC_REFLECT (1D, both

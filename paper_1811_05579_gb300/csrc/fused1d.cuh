@@ -473,6 +473,7 @@ __device__ __forceinline__ double f_vstar(const Dev& D, const Inst& I, const FGe
   const double gam = D.cf.gam[g];
   const double u = fmax(f_div(D.U[g] + gam * f_x<true>(X, G, i), 1.0 + gam * (I.a * I.c)), 0.0);
   if (u == 0.0) return 0.0;
+  if (I.p != 3.0) return pow(u, 0.25 * I.p);          // sigma_0/T^p, p != 3: V* = u^{p/4}
   if (!(u > 1e-25 && u < 1e25)) return pow(u, 0.75);   // outside the binary32 seed's range
   const float uf = (float)u;
   const double y = (double)sqrtf(uf * sqrtf(uf));

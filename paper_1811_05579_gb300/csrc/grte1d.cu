@@ -48,7 +48,8 @@ constexpr double kGuessGate = 1.1220184543019633;   // 10^0.05: learned-start ga
 constexpr int kMaxRestart = 16;
 
 struct Inst {
-  int N, M, kind, bc;
+  int N, M, kind, bc;      // kind: GRTE_SIGMA_CONST or GRTE_SIGMA_T3 (sigma_0/T^p, p below)
+  double p;                // the exponent of sigma_0/T^p (3 for GRTE_SIGMA_T3)
   double eps, dt, dx, a, c, Cv;
   double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
   double two_eps, inv_eps; // 2/eps, 1/eps
@@ -178,7 +179,7 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
   auto kap = [&](int64_t jj) -> double {
     if (I.kind == GRTE_SIGMA_CONST) return 1.0;
     double t = T[I.cell_off + jj];
-    return t * t * t;
+    return I.p == 3.0 ? t * t * t : pow(t, I.p);
   };
   auto sig = [&](int64_t jj) -> double { return D.sig[I.cell_off + jj]; };
   const double eps2 = I.eps * I.eps;
@@ -192,7 +193,8 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
   const double kc = kap(j);
   const double sj = sig(j);
   const double Tj = T[gid];
-  const double theta = (I.kind == GRTE_SIGMA_CONST) ? Tj * Tj * Tj : 1.0;
+  // theta: T^3 (sigma(x)); T^{3-p} for sigma_0/T^p (1 at p = 3)
+  const double theta = (I.kind == GRTE_SIGMA_CONST) ? Tj * Tj * Tj : (I.p == 3.0 ? 1.0 : pow(Tj, 3.0 - I.p));
   const double s = sj * I.Cv / (I.Cv * eps2 + 4.0 * sj * theta * I.dt * I.a * I.c);
   const double dx2 = I.dx * I.dx;
   const bool inflow = I.bc == GRTE_BC_INFLOW;
@@ -307,7 +309,8 @@ __device__ __forceinline__ void cellpart_cell(const Dev& D, const Inst& I, int64
       const double ac = I.a * I.c;
       const double ul = (D.U[gid - 1] + D.cf.gam[gid - 1] * xl) / (1.0 + D.cf.gam[gid - 1] * ac);
       const double ur = (D.U[gid] + D.cf.gam[gid] * xj) / (1.0 + D.cf.gam[gid] * ac);
-      const double vn = 0.5 * (pow(fmax(ul, 0.0), 0.75) + pow(fmax(ur, 0.0), 0.75));
+      const double e4 = 0.25 * I.p;   // V* = max(U*, 0)^{p/4}
+      const double vn = 0.5 * (pow(fmax(ul, 0.0), e4) + pow(fmax(ur, 0.0), e4));
       const double sl = D.sig[gid - 1], sr = D.sig[gid];
       const double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
       const double den = vn * I.eps * I.eps / (I.c * I.dt) + sn;
@@ -1084,7 +1087,9 @@ __global__ void k_newton_feat(Dev D, int n_inst, const int64_t* __restrict__ cel
   const double Tn = D.T[gid];
   const double rho = D.gx[gid];
   const double t3 = Tn * Tn * Tn;
-  const double sig_eff = (I.kind == GRTE_SIGMA_CONST) ? D.sig[gid] : D.sig[gid] / fmax(t3, 1e-300);
+  const double sig_eff = (I.kind == GRTE_SIGMA_CONST)
+                            ? D.sig[gid]
+                            : D.sig[gid] / fmax(I.p == 3.0 ? t3 : pow(Tn, I.p), 1e-300);
   auto lg = [](double x) { return (float)log10(fmin(fmax(x, 1e-300), 1e300)); };
   float* f = D.feat + 6 * gid;
   f[0] = lg(Tn);
@@ -1111,7 +1116,7 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
   D.Us[gid] = Us;
   D.rho_s[gid] = rho;
   const double sig = D.sig[gid];
-  const double kap = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : pow(fmax(Us, 0.0), 0.75);
+  const double kap = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : pow(fmax(Us, 0.0), 0.25 * I.p);
   const double dt = I.dt;
   const double A = sig * I.a / dt;
   const double B = sig * I.Cv / dt + I.eps * I.eps * kap * I.Cv / (I.c * dt * dt);
@@ -1728,7 +1733,10 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     if (p.nx < 2 || p.nx > (1 << 24)) return bad("nx must be in [2, 2^24]");
     if (p.n_angle < 1 || p.n_angle > 4096) return bad("n_angle must be in [1, 4096]");
     if (!p.sigma) return bad("sigma is NULL");
-    if (p.sigma_kind != GRTE_SIGMA_CONST && p.sigma_kind != GRTE_SIGMA_T3) return bad("bad sigma_kind");
+    if (p.sigma_kind != GRTE_SIGMA_CONST && p.sigma_kind != GRTE_SIGMA_T3 && p.sigma_kind != GRTE_SIGMA_POW)
+      return bad("bad sigma_kind");
+    if (p.sigma_kind == GRTE_SIGMA_POW && !(p.sigma_p >= 0.0 && p.sigma_p <= 3.0))
+      return bad("sigma_p must be in [0, 3]");
     if (p.bc != GRTE_BC_INFLOW && p.bc != GRTE_BC_REFLECT) return bad("bad bc");
     if (!(p.x1 > p.x0) || !(p.dt > 0) || !(p.a > 0) || !(p.c > 0) || !(p.Cv > 0) || !(p.eps > 0))
       return bad("x1 > x0, dt, a, c, Cv, eps must be positive");
@@ -1751,7 +1759,8 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     Inst I{};
     I.N = (int)p.nx;
     I.M = p.n_angle;
-    I.kind = p.sigma_kind;
+    I.kind = p.sigma_kind == GRTE_SIGMA_CONST ? GRTE_SIGMA_CONST : GRTE_SIGMA_T3;
+    I.p = p.sigma_kind == GRTE_SIGMA_POW ? p.sigma_p : 3.0;
     I.bc = p.bc;
     I.eps = p.eps;
     I.dt = p.dt;
@@ -2931,7 +2940,8 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   const int M = p->n_angle;
   // size limits of the static work memory
   if (N < 2 || N > kNaMaxCells || M < 1 || M > kNaMaxAngles || N * M > kNaMaxElems) return GRTE_EINVAL;
-  if (!p->sigma || (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3) ||
+  if (!p->sigma || (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3 &&
+                    !(p->sigma_kind == GRTE_SIGMA_POW && p->sigma_p >= 0.0 && p->sigma_p <= 3.0)) ||
       (p->bc != GRTE_BC_INFLOW && p->bc != GRTE_BC_REFLECT))
     return GRTE_EINVAL;
   if (!(p->x1 > p->x0) || !(p->dt > 0) || !(p->a > 0) || !(p->c > 0) || !(p->Cv > 0) || !(p->eps > 0))
@@ -2952,7 +2962,9 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
   for (int64_t j = 0; j < N; ++j)
     if (!(p->sigma[j] >= 0.0) || !std::isfinite(p->sigma[j])) return GRTE_EINVAL;
   Inst I{};
-  I.N = (int)N; I.M = M; I.kind = p->sigma_kind; I.bc = p->bc; I.eps = p->eps; I.dt = p->dt;
+  I.N = (int)N; I.M = M; I.bc = p->bc; I.eps = p->eps; I.dt = p->dt;
+  I.kind = p->sigma_kind == GRTE_SIGMA_CONST ? GRTE_SIGMA_CONST : GRTE_SIGMA_T3;
+  I.p = p->sigma_kind == GRTE_SIGMA_POW ? p->sigma_p : 3.0;
   I.dx = (p->x1 - p->x0) / (double)N; I.a = p->a; I.c = p->c; I.Cv = p->Cv;
   double wv = 0, wv2 = 0, fl = 0, fr = 0;
   for (int k = 0; k < M; ++k) {

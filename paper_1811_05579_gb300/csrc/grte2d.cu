@@ -49,7 +49,8 @@ constexpr int kDotBlocks = 304;   // 2 x 152: blocks of the Gram-Schmidt dot pro
 constexpr int kAxpyBlocks = 1216; // 8 x 152: blocks of the streaming vector updates
 
 struct G2 {
-  int Nx, Ny, K, bcx, bcy, kind;
+  int Nx, Ny, K, bcx, bcy, kind;   // kind: GRTE_SIGMA_CONST or GRTE_SIGMA_T3 (sigma_0/T^p)
+  double p;                        // the exponent of sigma_0/T^p (3 for GRTE_SIGMA_T3)
   int64_t nc, nv;
   double dx, dy, eps, dt, a, c, Cv;
   double bx0, bx1, by0, by1;
@@ -90,15 +91,16 @@ __device__ __forceinline__ int vkind(const G2& g, int i, int j) {
 
 // ----------------------------------------------------------------------------- coefficients
 // Per cell at temperature T (Eq. dis-pre: kappa = 1, theta = T^3; Eq. dis-pre-marshak:
-// kappa = T^3, theta = 1): s, gamma, A = kappa/(c dt) + sig/eps^2, alpha = kappa/(c dt) + s.
+// kappa = T^3, theta = 1; sigma_0/T^p: kappa = T^p, theta = T^{3-p}): s, gamma,
+// A = kappa/(c dt) + sig/eps^2, alpha = kappa/(c dt) + s.
 __global__ void k2_coef(D2 D) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const G2& g = D.g;
   if (c >= g.nc) return;
   const double T = D.T[c], sg = D.sig[c];
   const double T3 = T * T * T;
-  const double kc = g.kind == GRTE_SIGMA_CONST ? 1.0 : T3;
-  const double th = g.kind == GRTE_SIGMA_CONST ? T3 : 1.0;
+  const double kc = g.kind == GRTE_SIGMA_CONST ? 1.0 : (g.p == 3.0 ? T3 : pow(T, g.p));
+  const double th = g.kind == GRTE_SIGMA_CONST ? T3 : (g.p == 3.0 ? 1.0 : pow(T, 3.0 - g.p));
   const double e2 = g.eps * g.eps;
   const double s = sg * g.Cv / (g.Cv * e2 + 4.0 * sg * th * g.dt * g.a * g.c);
   D.kc[c] = kc;
@@ -668,7 +670,7 @@ __global__ void k2_rhs_pred(D2 D, const double* __restrict__ phi, double* __rest
 __global__ void k2_vstar(D2 D) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= D.g.nc) return;
-  D.kc[c] = pow(fmax(D.Us[c], 0.0), 0.75);
+  D.kc[c] = pow(fmax(D.Us[c], 0.0), 0.25 * D.g.p);
 }
 
 // E*_k = rho + e_k, U* = (U^n + gamma rho)/(1 + gamma a c), rho* kept.
@@ -718,7 +720,8 @@ __global__ void k2_newton_feat(D2 D) {
   const G2& g = D.g;
   if (c >= g.nc) return;
   const double Tn = D.T[c], t3 = Tn * Tn * Tn;
-  const double sig_eff = g.kind == GRTE_SIGMA_CONST ? D.sig[c] : D.sig[c] / fmax(t3, 1e-300);
+  const double sig_eff = g.kind == GRTE_SIGMA_CONST ? D.sig[c]
+                                                    : D.sig[c] / fmax(g.p == 3.0 ? t3 : pow(Tn, g.p), 1e-300);
   auto lg = [](double x) { return (float)log10(fmin(fmax(x, 1e-300), 1e300)); };
   float* f = D.feat + 6 * c;
   f[0] = lg(Tn);
@@ -743,7 +746,7 @@ __global__ void k2_newton(D2 D) {
   const G2& g = D.g;
   if (c >= g.nc) return;
   const double sg = D.sig[c], Tn = D.T[c];
-  const double kap = g.kind == GRTE_SIGMA_CONST ? 1.0 : pow(fmax(D.Us[c], 0.0), 0.75);
+  const double kap = g.kind == GRTE_SIGMA_CONST ? 1.0 : pow(fmax(D.Us[c], 0.0), 0.25 * g.p);
   const double A = sg * g.a / g.dt;
   const double B = sg * g.Cv / g.dt + g.eps * g.eps * kap * g.Cv / (g.c * g.dt * g.dt);
   const double R = sg * (D.rho_n[c] / (g.c * g.dt) - D.Fdiv[c]) + B * Tn;
@@ -1512,7 +1515,10 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
   if ((int64_t)std::max(p->n_pair, 20) * (p->nx + 1) * (p->ny + 1) >= (int64_t)1 << 31)
     return fail2(h, GRTE_EINVAL, "n_pair * (nx+1) * (ny+1) must be below 2^31");
   if (!p->sigma) return fail2(h, GRTE_EINVAL, "sigma is NULL");
-  if (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3) return fail2(h, GRTE_EINVAL, "bad sigma_kind");
+  if (p->sigma_kind != GRTE_SIGMA_CONST && p->sigma_kind != GRTE_SIGMA_T3 && p->sigma_kind != GRTE_SIGMA_POW)
+    return fail2(h, GRTE_EINVAL, "bad sigma_kind");
+  if (p->sigma_kind == GRTE_SIGMA_POW && !(p->sigma_p >= 0.0 && p->sigma_p <= 3.0))
+    return fail2(h, GRTE_EINVAL, "sigma_p must be in [0, 3]");
   for (int bc : {p->bc_x, p->bc_y})
     if (bc != GRTE_BC_INFLOW && bc != GRTE_BC_PERIODIC) return fail2(h, GRTE_EINVAL, "bc must be INFLOW or PERIODIC");
   if (!(p->lx > 0) || !(p->ly > 0) || !(p->dt > 0) || !(p->a > 0) || !(p->c > 0) || !(p->Cv > 0) || !(p->eps > 0))
@@ -1540,7 +1546,8 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
   g.K = (int)h->hmu.size();
   g.bcx = p->bc_x;
   g.bcy = p->bc_y;
-  g.kind = p->sigma_kind;
+  g.kind = p->sigma_kind == GRTE_SIGMA_CONST ? GRTE_SIGMA_CONST : GRTE_SIGMA_T3;
+  g.p = p->sigma_kind == GRTE_SIGMA_POW ? p->sigma_p : 3.0;
   g.nc = p->nx * p->ny;
   g.nv = (p->nx + 1) * (p->ny + 1);
   g.dx = p->lx / (double)p->nx;
@@ -1852,6 +1859,7 @@ grte_status grte_create(const grte_grid* grid, const grte_quadrature* quad, cons
     p.w = custom ? quad->w : nullptr;
     p.sigma = sig.data();
     p.sigma_kind = opac->kind;
+    p.sigma_p = opac->sigma_p;
     p.bc = bc->kind[0];
     p.bL = bL.data();
     p.bR = bR.data();
@@ -1892,6 +1900,7 @@ grte_status grte_create(const grte_grid* grid, const grte_quadrature* quad, cons
   p.w = custom ? quad->w : nullptr;
   p.sigma = sig.data();
   p.sigma_kind = opac->kind;
+  p.sigma_p = opac->sigma_p;
   p.bc_x = bc->kind[0];
   p.bc_y = bc->kind[2];
   p.b_x0 = bc->b_iso[0];

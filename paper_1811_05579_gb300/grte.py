@@ -16,7 +16,7 @@ GRTE_OK = 0
 GRTE_EINVAL, GRTE_ENOMEM, GRTE_ECUDA, GRTE_ENONCONV, GRTE_ENEGATIVE, GRTE_ENAN, GRTE_ETIMEOUT, GRTE_ESTATE = range(1, 9)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONCONV", 5: "ENEGATIVE",
                 6: "ENAN", 7: "ETIMEOUT", 8: "ESTATE"}
-SIGMA_CONST, SIGMA_T3 = 0, 1
+SIGMA_CONST, SIGMA_T3, SIGMA_POW = 0, 1, 2
 BC_INFLOW, BC_REFLECT, BC_PERIODIC = 0, 1, 2
 FP64, MIXED = 0, 1
 
@@ -28,7 +28,7 @@ class Instance1D(ctypes.Structure):
                 ("sigma", _dp), ("sigma_kind", ctypes.c_int), ("bc", ctypes.c_int),
                 ("bL", _dp), ("bR", _dp), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
-                ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("Cv", ctypes.c_double), ("eps", ctypes.c_double), ("sigma_p", ctypes.c_double)]
 
 
 class Instance2D(ctypes.Structure):
@@ -37,7 +37,7 @@ class Instance2D(ctypes.Structure):
                 ("bc_y", ctypes.c_int), ("b_x0", ctypes.c_double), ("b_x1", ctypes.c_double),
                 ("b_y0", ctypes.c_double), ("b_y1", ctypes.c_double), ("lx", ctypes.c_double),
                 ("ly", ctypes.c_double), ("dt", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
-                ("Cv", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("Cv", ctypes.c_double), ("eps", ctypes.c_double), ("sigma_p", ctypes.c_double)]
 
 
 class GridS(ctypes.Structure):
@@ -50,7 +50,8 @@ class QuadS(ctypes.Structure):
 
 
 class OpacS(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("sigma0", _dp), ("sigma0_scalar", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("sigma0", _dp), ("sigma0_scalar", ctypes.c_double),
+                ("sigma_p", ctypes.c_double)]
 
 
 class BcS(ctypes.Structure):
@@ -237,7 +238,7 @@ def instance_struct(p, keep):
     return Instance1D(p["nx"], M, _ptr(v), _ptr(w), _ptr(sig), p.get("kind", SIGMA_T3),
                       p.get("bc", BC_INFLOW), _ptr(bL), _ptr(bR), p.get("x0", 0.0),
                       p.get("x1", 1.0), p["dt"], p.get("a", 1.0), p.get("c", 1.0),
-                      p.get("Cv", 1.0), p["eps"])
+                      p.get("Cv", 1.0), p["eps"], p.get("p", 3.0))
 
 
 def step1d_noalloc(spec, T_ptr, E_ptr, O_ptr, nsteps, stream=None, options=None):
@@ -350,7 +351,7 @@ class Grte:
             arr[i] = Instance1D(p["nx"], M, _ptr(v), _ptr(w), _ptr(sig), p.get("kind", SIGMA_T3),
                                 p.get("bc", BC_INFLOW), _ptr(bL), _ptr(bR), p.get("x0", 0.0),
                                 p.get("x1", 1.0), p["dt"], p.get("a", 1.0), p.get("c", 1.0),
-                                p.get("Cv", 1.0), p["eps"])
+                                p.get("Cv", 1.0), p["eps"], p.get("p", 3.0))
             self.specs.append(dict(nx=int(p["nx"]), M=int(M), eps=float(p["eps"])))
         opt = Options()
         L.grte_default_options(ctypes.byref(opt))
@@ -511,14 +512,14 @@ class Grte2D:
     def __init__(self, nx, ny, sigma, dt, eps, kind=SIGMA_T3, bc_x=BC_INFLOW, bc_y=BC_INFLOW, b_x0=0.0, b_x1=0.0,
                  b_y0=0.0, b_y1=0.0, mu=None, eta=None, w=None, lx=1.0, ly=1.0, a=1.0, c=1.0, Cv=1.0,
                  krylov_rtol=1e-13, krylov_restart=30, krylov_maxcycles=30, newton_maxit=60, stream=None,
-                 prec=0, precision=FP64):
+                 prec=0, precision=FP64, p=3.0):
         L = lib()
         sig = _f64(np.broadcast_to(np.asarray(sigma, dtype=np.float64).ravel(), (nx * ny,)))
         mu, eta, w = _f64(mu), _f64(eta), _f64(w)
         self._keep = [sig, mu, eta, w]
         K = 0 if mu is None else mu.size
         inst = Instance2D(nx, ny, K, _ptr(mu), _ptr(eta), _ptr(w), _ptr(sig), kind, bc_x, bc_y, b_x0, b_x1, b_y0,
-                          b_y1, lx, ly, dt, a, c, Cv, eps)
+                          b_y1, lx, ly, dt, a, c, Cv, eps, p)
         opt = Options()
         L.grte_default_options(ctypes.byref(opt))
         opt.krylov_rtol = krylov_rtol
@@ -622,7 +623,7 @@ class Problem:
 
     def __init__(self, dim, nx, dt, eps, sigma0, kind=SIGMA_T3, ny=0, x0=0.0, x1=1.0, y1=1.0, n_dir=0,
                  mu=None, eta=None, w=None, bc_kind=(BC_INFLOW,) * 4, b_iso=(0.0,) * 4, a=1.0, c=1.0, Cv=1.0,
-                 precision=FP64):
+                 precision=FP64, p=3.0):
         L = lib()
         self._keep = []
         sig = np.asarray(sigma0, dtype=np.float64)
@@ -632,7 +633,7 @@ class Problem:
         self._keep += [sig] + arrs
         grid = GridS(dim, nx, ny, x0, x1, 0.0, y1, dt)
         quad = QuadS(n_dir, *[_ptr(x) for x in arrs])
-        opac = OpacS(kind, _ptr(sig), float(sigma0) if scalar else 0.0)
+        opac = OpacS(kind, _ptr(sig), float(sigma0) if scalar else 0.0, float(p))
         bc = BcS((ctypes.c_int * 4)(*bc_kind), (ctypes.c_double * 4)(*b_iso), (_dp * 4)(None, None, None, None))
         opt = Options()
         L.grte_default_options(ctypes.byref(opt))
