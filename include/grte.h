@@ -109,7 +109,7 @@ typedef struct {
                             preconditioner.  Ignored by the 1D path                        */
   int solver1d;          /* 1D prediction solve: GRTE_SOLVER_AUTO (default): in GRTE_MIXED, when
                             every instance has 64 <= nx <= 8192 and n_angle <= 32 and the
-                            restart length is at most 16 (its Krylov basis is held in shared
+                            restart length is at most 11 (its Krylov basis is held in shared
                             memory), the whole
                             solve of an instance runs in one persistent kernel on a cluster of
                             up to 16 CTAs (the angular unknowns of each 512-cell slice held in

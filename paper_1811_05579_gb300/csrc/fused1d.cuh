@@ -66,15 +66,14 @@ struct FSmem {
   // the correction's flux (sigma_0/T^3): node coefficients d* of V* = (U*)^{3/4} at the
   // nodes c0 + t (t = 0..kFS), the node moments Om = sum_k w_k v_k O^n, the flux per cell
   double Om[kFS + 1];                                  // node moments of O^n (sigma_0/T^3 data)
-  float pu[kFS];                                        // preconditioner solution (slice)
-  // the preconditioner, factored once per solve in binary64 and kept (and applied) in
-  // binary32: chunk sweeps [u][lane] (u = 1..kFPL-2), the reduced 64-row system's PCR
-  // multipliers and unit spikes, the interface's multipliers
-  float pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
-  float pcs[32], pae[32];
-  float pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
-  float ik1[5][32], ik2[5][32], iib[32];
-  float pS[4], paf, pcl;
+  double pu[kFS];                                       // preconditioner solution (slice)
+  // binary64 preconditioner, factored once per solve: chunk sweeps [u][lane] (u = 1..kFPL-2),
+  // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
+  double pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
+  double pcs[32], pae[32];
+  double pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
+  double ik1[5][32], ik2[5][32], iib[32];
+  double pS[4], paf, pcl;
   float wgt[kFS];                                       // stopping-test weights
   double zv[kFS];                                       // preconditioner input (slice)
   double sc[4];                                         // scalars computed once (thread 0)
@@ -85,7 +84,7 @@ struct FSmem {
   // binary64 preconditioner: reduced rows of the 32 lane chunks (64 rows), interface
   double pe[2][6];                                      // published: S11 S12 S21 S22 r'F r'L
   double pcoup[2][2];
-  float pxl[2];
+  double pxl[2];
   // GMRES state (identical in every CTA)
   double H[(kMaxRestart + 1) * kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart],
       y[kMaxRestart], hc[kMaxRestart + 2];
@@ -894,49 +893,37 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
 
 // z = P^{-1} rin on the slice with the factors of f_prec_factor (binary64).  rin and z:
 // slice-local vectors in shared memory (cell c0 + t at index t).
-__device__ __forceinline__ float f_rowf(float v0, float v1, int i) {
-  const int src = (i < 0 ? 0 : (i > 63 ? 63 : i));
-  const float a = __shfl_sync(0xffffffffu, v0, src >> 1), b = __shfl_sync(0xffffffffu, v1, src >> 1);
-  return (src & 1) ? b : a;
-}
-
-// z = P^{-1} rin for the slice (rin, z binary64 Krylov vectors): the tridiagonal solve of
-// the factored preconditioner in binary32 by warp 0 of every CTA (chunk sweeps, the
-// 64-row reduced system by PCR, the 2Q-row interface through distributed shared memory),
-// then z = (rin - Gbar u)/alpha with Gbar u from the binary32 coefficient copies.  The
-// preconditioner only steers the Krylov iteration: the residual that decides convergence
-// is formed in binary64 at each restart.
 __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
                        const double* rin, double* z, int& par) {
   const int64_t N = G.N, co = G.co;
   const int lane = threadIdx.x & 31;
   const bool w0 = threadIdx.x < 32;
-  float y0 = 0.0f, y1 = 0.0f;
+  double y0 = 0.0, y1 = 0.0, rh14 = 0.0;
   if (w0) {
     const int64_t s = G.c0 + lane * kFPL;
 #pragma unroll
     for (int u = 0; u < kFPL; ++u) {
       const int64_t j = s + u;
-      sm.pxr[u][lane] = (j < N) ? D.fc.ratio[co + j] * (float)rin[lane * kFPL + u] : 0.0f;
+      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[lane * kFPL + u] : 0.0;
     }
-    float rh = 0.0f;
+    double rh = 0.0;
 #pragma unroll
     for (int u = 1; u <= kFPL - 2; ++u) {
-      const float xu = sm.pxr[u][lane];
+      const double xu = sm.pxr[u][lane];
       rh = (u == 1 ? xu : xu - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
       sm.pxr[u][lane] = rh;
     }
-    const float rh14 = rh;
-    float rc = rh;
+    rh14 = rh;
+    double rc = rh;
 #pragma unroll
     for (int u = kFPL - 3; u >= 1; --u) rc = sm.pxr[u][lane] - sm.pch[u][lane] * rc;
-    float r0 = sm.pxr[0][lane] - sm.pcs[lane] * rc, r1 = sm.pxr[kFPL - 1][lane] - sm.pae[lane] * rh14;
+    double r0 = sm.pxr[0][lane] - sm.pcs[lane] * rc, r1 = sm.pxr[kFPL - 1][lane] - sm.pae[lane] * rh14;
     for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
-      float nr[2];
+      double nr[2];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int i = 2 * lane + p;
-        const float Lr = f_rowf(r0, r1, i - st), Rr = f_rowf(r0, r1, i + st);
+        const double Lr = f_row(r0, r1, i - st), Rr = f_row(r0, r1, i + st);
         nr[p] = (p ? r1 : r0) - sm.pk1[l][i] * Lr - sm.pk2[l][i] * Rr;
       }
       r0 = nr[0];
@@ -944,7 +931,7 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     }
     y0 = r0 * sm.pib[2 * lane];
     y1 = r1 * sm.pib[2 * lane + 1];
-    const float ya = __shfl_sync(0xffffffffu, y0, 0), yb = __shfl_sync(0xffffffffu, y1, 31);
+    const double ya = __shfl_sync(0xffffffffu, y0, 0), yb = __shfl_sync(0xffffffffu, y1, 31);
     if (lane == 0) {
       sm.pe[par][4] = sm.pS[0] * ya + sm.pS[1] * yb;
       sm.pe[par][5] = sm.pS[2] * ya + sm.pS[3] * yb;
@@ -953,24 +940,24 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   cl.sync();   // every slice's reduced right-hand side published
   if (w0) {
     const int Q = G.Q, n2 = 2 * Q;
-    float ir = 0.0f;
-    if (lane < n2) ir = (float)cl.map_shared_rank(&sm.pe[par][0], lane >> 1)[4 + (lane & 1)];
+    double ir = 0.0;
+    if (lane < n2) ir = cl.map_shared_rank(&sm.pe[par][0], lane >> 1)[4 + (lane & 1)];
     for (int l = 0, st = 1; st < n2; ++l, st <<= 1) {
       const int il = lane - st, irr = lane + st;
-      const float Lr = __shfl_sync(0xffffffffu, ir, il >= 0 ? il : 0);
-      const float Rr = __shfl_sync(0xffffffffu, ir, irr < n2 ? irr : 0);
+      const double Lr = __shfl_sync(0xffffffffu, ir, il >= 0 ? il : 0);
+      const double Rr = __shfl_sync(0xffffffffu, ir, irr < n2 ? irr : 0);
       if (lane < n2) ir = ir - sm.ik1[l][lane] * Lr - sm.ik2[l][lane] * Rr;
     }
-    const float X = ir * sm.iib[lane];
+    const double X = ir * sm.iib[lane];
     const int sLp = G.q > 0 ? 2 * G.q - 1 : 0, sFn = G.q < Q - 1 ? 2 * G.q + 2 : 0;
-    const float XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
-    const float Lp = G.q > 0 ? XL : 0.0f, Fn = G.q < Q - 1 ? XF : 0.0f;
-    const float la = Lp * sm.paf, fc = Fn * sm.pcl;
-    const float xs = y0 - la * sm.pgv[2 * lane] - fc * sm.phv[2 * lane];
-    const float xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
+    const double XL = __shfl_sync(0xffffffffu, X, sLp), XF = __shfl_sync(0xffffffffu, X, sFn);
+    const double Lp = G.q > 0 ? XL : 0.0, Fn = G.q < Q - 1 ? XF : 0.0;
+    const double la = Lp * sm.paf, fc = Fn * sm.pcl;
+    const double xs = y0 - la * sm.pgv[2 * lane] - fc * sm.phv[2 * lane];
+    const double xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
     sm.pu[lane * kFPL] = xs;
     sm.pu[lane * kFPL + kFPL - 1] = xe;
-    float xn = xe;
+    double xn = xe;
 #pragma unroll
     for (int u = kFPL - 2; u >= 1; --u) {
       xn = sm.pxr[u][lane] - sm.pch[u][lane] * xn - sm.pah[u][lane] * xs;
@@ -988,12 +975,12 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
     if (j < N) {
-      const float uj = sm.pu[t];
-      const float uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0f;
-      const float uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0f;
-      const float Gu = (float)I.wv2 * (sm.gl[t + 1] * (uj - uL) + sm.gu[t + 1] * (uj - uR)) +
-                       (float)I.wv * sm.gb[t + 1] * uj;
-      z[t] = (rin[t] - (double)Gu) * (double)D.fc.ralpha[co + j];
+      const int64_t g = co + j;
+      const double uj = sm.pu[t];
+      const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
+      const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
+      const double Gu = I.wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + I.wv * D.cf.gb[g] * uj;
+      z[t] = (rin[t] - Gu) * D.cf.ralpha[g];
     } else {
       z[t] = 0.0;
     }
