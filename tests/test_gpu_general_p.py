@@ -73,8 +73,11 @@ def test_p0_equals_sigma_x_on_gpu(G):
 
 
 def test_mixed_one_kernel_solve_p2(G):
+    """One step of the one-kernel mixed solve from a smooth state (a cell-by-cell random
+    state makes single cells' T ill-conditioned: some nearly empty in the step)."""
     P, spec = make(G, 1500, 16, 1e-2, 2.0)
-    S = state(P, 7)
+    T0 = wl.smoothed_log_uniform_T(wl.SplitMix64(77), P.N, 0.1, 1.0, width=9)
+    S = og.equilibrium_state(P, T0)
     h = G.Grte([spec], precision=G.MIXED)
     h.set_state(0, S.T, S.E, S.O)
     h.profile_begin(["pred_solve", "gmres"])
