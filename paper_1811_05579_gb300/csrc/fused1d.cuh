@@ -53,7 +53,7 @@ struct FSmem {
       kdx[kFS + 2];
   float P1[kFS], P2[kFS], P3[kFS];                      // per-cell parts of the pass
   // reduced systems: [row][angle]
-  float ra[kFR][32], rb[kFR][32], rc[kFR][32], rr[kFR][32], rg[kFR][32], rh[kFR][32];
+  float ra[kFR][33], rb[kFR][33], rc[kFR][33], rr[kFR][33], rg[kFR][33], rh[kFR][33];
   float ends[2][4][32];                                 // published: S11 S12 S21 S22 (double-buffered)
   float endr[2][2][32];                                 // published: r'_F, r'_L
   float coup[2][2][32];                                 // published: a at the first cell, c at the last
@@ -164,52 +164,63 @@ __device__ __forceinline__ void f_coef(const FSmem& sm, int jl, float v, float v
   b = fmaf(v, sm.gb[jl], fmaf(v2, l + u, sm.A[jl]));
 }
 
-// PCR on n <= kFR rows per lane of (ra, rb, rc) with NR right-hand sides (rr; rg, rh), in
-// place; on return rr (rg, rh) hold the solutions.  Every thread takes part.
+// PCR on n <= kFR rows of (ra, rb, rc) with NR right-hand sides (rr; rg, rh) for every
+// angle, in place: on return rr (rg, rh) hold the solutions.  Warp w takes the angles w and
+// w + kFW with lane = row; the rows are kept scaled to a unit diagonal, so a level takes the
+// neighbours' (a, c, r) by shuffles and one reciprocal.  The arrays are padded to 33
+// columns, so that a warp's column reads hit 32 banks.  Every thread takes part.
 template <int NR>
 __device__ __forceinline__ void f_pcr(FSmem& sm, int n) {
-  const int lane = threadIdx.x & 31;
-  const int r0 = threadIdx.x >> 5;   // rows r0 and r0 + kFW
-  for (int st = 1; st < n; st <<= 1) {
-    float na[2], nb[2], nc[2], n1[2], n2[2], n3[2];
+  static_assert(2 * kFW == 32, "two angles per warp");
+  const int i = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool live = i < n;
+  float a[2], c[2], r[2][NR];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int i = r0 + p * kFW;
-      na[p] = nb[p] = nc[p] = n1[p] = n2[p] = n3[p] = 0.0f;
-      if (i >= n) continue;
-      const int il = i - st >= 0 ? i - st : i, ir = i + st < n ? i + st : i;
-      const bool hl = i - st >= 0, hr = i + st < n;
-      const float k1 = hl ? __fdividef(sm.ra[i][lane], sm.rb[il][lane]) : 0.0f;
-      const float k2 = hr ? __fdividef(sm.rc[i][lane], sm.rb[ir][lane]) : 0.0f;
-      na[p] = -sm.ra[il][lane] * k1;
-      nc[p] = -sm.rc[ir][lane] * k2;
-      nb[p] = sm.rb[i][lane] - sm.rc[il][lane] * k1 - sm.ra[ir][lane] * k2;
-      n1[p] = sm.rr[i][lane] - sm.rr[il][lane] * k1 - sm.rr[ir][lane] * k2;
-      if (NR > 1) n2[p] = sm.rg[i][lane] - sm.rg[il][lane] * k1 - sm.rg[ir][lane] * k2;
-      if (NR > 2) n3[p] = sm.rh[i][lane] - sm.rh[il][lane] * k1 - sm.rh[ir][lane] * k2;
-    }
-    __syncthreads();
+  for (int h = 0; h < 2; ++h) {
+    const int k = w + h * kFW;
+    if (live) {
+      const float ib = __frcp_rn(sm.rb[i][k]);
+      a[h] = sm.ra[i][k] * ib;
+      c[h] = sm.rc[i][k] * ib;
+      r[h][0] = sm.rr[i][k] * ib;
+      if (NR > 1) r[h][1] = sm.rg[i][k] * ib;
+      if (NR > 2) r[h][2] = sm.rh[i][k] * ib;
+    } else {
+      a[h] = c[h] = 0.0f;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int i = r0 + p * kFW;
-      if (i >= n) continue;
-      sm.ra[i][lane] = na[p];
-      sm.rb[i][lane] = nb[p];
-      sm.rc[i][lane] = nc[p];
-      sm.rr[i][lane] = n1[p];
-      if (NR > 1) sm.rg[i][lane] = n2[p];
-      if (NR > 2) sm.rh[i][lane] = n3[p];
+      for (int j = 0; j < NR; ++j) r[h][j] = 0.0f;
     }
-    __syncthreads();
   }
+  for (int st = 1; st < n; st <<= 1) {
+    const bool hl = i >= st, hr = i + st < n;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const int i = r0 + p * kFW;
-    if (i >= n) continue;
-    const float ib = __frcp_rn(sm.rb[i][lane]);
-    sm.rr[i][lane] *= ib;
-    if (NR > 1) sm.rg[i][lane] *= ib;
-    if (NR > 2) sm.rh[i][lane] *= ib;
+    for (int h = 0; h < 2; ++h) {
+      float al = __shfl_up_sync(0xffffffffu, a[h], st), cl = __shfl_up_sync(0xffffffffu, c[h], st);
+      float ar = __shfl_down_sync(0xffffffffu, a[h], st), cr = __shfl_down_sync(0xffffffffu, c[h], st);
+      float rl[NR], rr[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        rl[j] = __shfl_up_sync(0xffffffffu, r[h][j], st);
+        rr[j] = __shfl_down_sync(0xffffffffu, r[h][j], st);
+      }
+      // row i - a_i row_{i-st} - c_i row_{i+st} (unit diagonals), then rescaled
+      const float k1 = hl ? a[h] : 0.0f, k2 = hr ? c[h] : 0.0f;
+      const float nb = 1.0f - k1 * cl - k2 * ar;
+      const float ib = __frcp_rn(nb);
+      a[h] = -k1 * al * ib;
+      c[h] = -k2 * cr * ib;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) r[h][j] = (r[h][j] - k1 * rl[j] - k2 * rr[j]) * ib;
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = w + h * kFW;
+      sm.rr[i][k] = r[h][0];
+      if (NR > 1) sm.rg[i][k] = r[h][1];
+      if (NR > 2) sm.rh[i][k] = r[h][2];
+    }
   }
   __syncthreads();
 }
