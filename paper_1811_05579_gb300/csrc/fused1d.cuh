@@ -49,8 +49,9 @@ constexpr int kFPL = kFS / 32;    // cells per lane of the preconditioner's warp
 struct FSmem {
   float x[kFS][kFX];                                   // unknowns of the slice, [cell][angle]
   // per-cell binary32 arrays of the slice with one halo cell each side (index j - c0 + 1)
-  float A[kFS + 2], gl[kFS + 2], gu[kFS + 2], gb[kFS + 2], od[kFS + 2], dlx[kFS + 2], kcd[kFS + 2],
-      kdx[kFS + 2];
+  // the line coefficients packed (x: A, y: gl, z: gu, w: gb), one load per sweep step
+  float4 lc[kFS + 2];
+  float od[kFS + 2], dlx[kFS + 2], kcd[kFS + 2], kdx[kFS + 2];
   float P1[kFS], P2[kFS], P3[kFS];                      // per-cell parts of the pass
   // reduced systems: [row][angle]
   float ra[kFR][33], rb[kFR][33], rc[kFR][33], rr[kFR][33], rg[kFR][33], rh[kFR][33];
@@ -105,63 +106,134 @@ struct FGeo {
   int N, M;
 };
 
-// Block sums over the slice of nv <= NV per-cell terms term(i, t) (t the slice cell): 64
-// threads each accumulate 8 cells, then one shuffle tree per value in two warps (binary64
-// additions are the scarce resource: 8x fewer than a tree over 512 threads).  Result in
-// sm.sums[0..nv-1]; every thread takes part in the barriers.
-constexpr int kGT = 64;
-template <int NV, bool MAX, class F>
-__device__ __forceinline__ void f_slice_sums(FSmem& sm, int nv, F term) {
-  const int t = threadIdx.x;
-  if (t < kGT) {
-    const int lane = t & 31, wid = t >> 5;
+// Cluster reductions.  The binary64 pipe is the scarce resource (one warp instruction
+// holds a sub-partition's pipe for many cycles), so the slice part runs on warps 0..3, one
+// per sub-partition, each thread accumulating 4 cells; a warp then reduces its S values
+// with a reduce-scatter butterfly (S - 1 + 5 - log2 S additions per lane instead of 5 S),
+// and the 16 ranks' partials are combined by a 16-lane butterfly per value.  Maxima are of
+// non-negative terms (or NaN), taken as integer maxima of the binary64 bit patterns (order
+// preserving for x >= 0; a NaN wins), off the binary64 pipe.  The order of the additions
+// is fixed, so every CTA of the cluster gets the same bits.
+constexpr int kGW = 4;                 // warps of the slice part
+constexpr int kGC = kFS / (32 * kGW);  // cells per thread (4)
+
+// In-warp reduce-scatter of S (a power of two <= 16) values per lane: on return a[0] holds
+// the warp sum of value vi, and the lanes whose low 5 - log2 S bits are 0 hold distinct vi.
+template <int S>
+__device__ __forceinline__ double f_warp_rs(double (&a)[S], int lane, int& vi) {
+  int base = 0, o = 16;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (i >= nv) break;
-      double a = 0.0;
+  for (int h = S / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
 #pragma unroll
-      for (int c = 0; c < kFS / kGT; ++c) {
-        const double v = term(i, t + c * kGT);
-        a = MAX ? fmax(a, v) : a + v;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double b = __shfl_xor_sync(0xffffffffu, a, o);
-        a = MAX ? fmax(a, b) : a + b;
-      }
-      if (lane == 0) sm.red[wid][i] = a;
+    for (int s2 = 0; s2 < h; ++s2) {
+      const double send = up ? a[s2] : a[s2 + h];
+      const double keep = up ? a[s2 + h] : a[s2];
+      a[s2] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (up) base += h;
+  }
+  for (; o >= 1; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  vi = base;
+  return a[0];
+}
+
+// Warp part of the slice sums for S slots (ns <= S live): writes sm.red[wid][0..ns-1].
+template <int S, class FS>
+__device__ __forceinline__ void f_slice_rs(FSmem& sm, int ns, FS sterm) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  double a[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    a[i] = 0.0;
+    if (i < ns) {
+#pragma unroll
+      for (int c = 0; c < kGC; ++c) a[i] += sterm(i, t + c * 32 * kGW);
+    }
+  }
+  int vi;
+  const double r = f_warp_rs<S>(a, lane, vi);
+  constexpr int lowbits = 32 / S - 1;
+  if ((lane & lowbits) == 0 && vi < ns) sm.red[wid][vi] = r;
+}
+
+// ns <= NS sums of sterm(i, c) (i < ns) and, if MX, the maximum of mterm(c) >= 0 over the
+// cluster's cells (c the slice cell); results in sm.sums[0..ns-1] and sm.sums[ns] for every
+// thread.  Every thread takes part; par selects the half of the double buffer.
+template <int NS, bool MX, class FS, class FM>
+__device__ void f_reduce(FSmem& sm, cg::cluster_group& cl, int& par, int ns, FS sterm, FM mterm) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (wid < kGW) {
+    if (NS > 0 && ns > 0) {
+      if (NS <= 1 || ns <= 1) f_slice_rs<1>(sm, ns, sterm);
+      else if (NS <= 2 || ns <= 2) f_slice_rs<(NS < 2 ? 1 : 2)>(sm, ns, sterm);
+      else if (NS <= 4 || ns <= 4) f_slice_rs<(NS < 4 ? 1 : 4)>(sm, ns, sterm);
+      else if (NS <= 8 || ns <= 8) f_slice_rs<(NS < 8 ? 1 : 8)>(sm, ns, sterm);
+      else f_slice_rs<(NS < 16 ? 1 : 16)>(sm, ns, sterm);
+    }
+    if (MX) {
+      long long m = 0;
+#pragma unroll
+      for (int c = 0; c < kGC; ++c) m = max(m, __double_as_longlong(mterm(t + c * 32 * kGW)));
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) sm.red[wid][ns] = __longlong_as_double(m);
     }
   }
   __syncthreads();
-  if (t < nv) sm.sums[t] = MAX ? fmax(sm.red[0][t], sm.red[1][t]) : sm.red[0][t] + sm.red[1][t];
-  __syncthreads();
-}
-
-// Cluster sums (is_max = 0) or maxima of the nv values in sm.sums (rank order); result in
-// sm.sums for every thread.  par selects the half of the double buffer.
-__device__ void f_cluster_reduce(FSmem& sm, cg::cluster_group& cl, int& par, int nv, bool is_max) {
-  if (threadIdx.x < nv) sm.part[par][threadIdx.x] = sm.sums[threadIdx.x];
+  const int nv = ns + (MX ? 1 : 0);
+  if (t < nv) {
+    double v;
+    if (MX && t == ns) {
+      long long m = __double_as_longlong(sm.red[0][t]);
+#pragma unroll
+      for (int w2 = 1; w2 < kGW; ++w2) m = max(m, __double_as_longlong(sm.red[w2][t]));
+      v = __longlong_as_double(m);
+    } else {
+      v = (sm.red[0][t] + sm.red[1][t]) + (sm.red[2][t] + sm.red[3][t]);
+    }
+    sm.part[par][t] = v;
+  }
   cl.sync();
-  if (threadIdx.x < nv) {
+  // 16 lanes per value, lane r reading rank r's partial
+  if (wid < (nv + 1) / 2) {
+    const int i = t >> 4, r = t & 15;
+    const unsigned hm = (lane < 16) ? 0x0000ffffu : 0xffff0000u;   // this lane's 16-lane group
     const int Q = (int)cl.num_blocks();
-    double v[kFQ];
+    const double* src = cl.map_shared_rank(&sm.part[par][0], r < Q ? r : 0);
+    const bool live = i < nv && r < Q;
+    const double pv = live ? src[i] : 0.0;
+    if (MX && i == ns) {
+      long long m = __double_as_longlong(pv);
 #pragma unroll
-    for (int r = 0; r < kFQ; ++r) v[r] = r < Q ? cl.map_shared_rank(&sm.part[par][0], r)[threadIdx.x] : 0.0;
-    double t = 0.0;
+      for (int o = 8; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(hm, m, o));
+      if (r == 0) sm.sums[i] = __longlong_as_double(m);
+    } else {
+      double a = pv;
 #pragma unroll
-    for (int r = 0; r < kFQ; ++r) t = is_max ? fmax(t, v[r]) : t + v[r];
-    sm.sums[threadIdx.x] = t;
+      for (int o = 8; o >= 1; o >>= 1) a += __shfl_xor_sync(hm, a, o);
+      if (r == 0 && i < nv) sm.sums[i] = a;
+    }
   }
   par ^= 1;
   __syncthreads();
 }
 
+// Approximate binary32 reciprocal (rcp.approx.ftz: within 1 ulp) for the chunk sweeps,
+// whose pivots are O(1) and positive.
+__device__ __forceinline__ float f_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Tridiagonal coefficients of line k at the slice-local cell jl (halo index):
 //   a = -v^2 gl, b = A + v^2 (gl + gu) + v gb, c = -v^2 gu   (LineCoef).
 __device__ __forceinline__ void f_coef(const FSmem& sm, int jl, float v, float v2, float& a, float& b, float& c) {
-  const float l = sm.gl[jl], u = sm.gu[jl];
-  a = -v2 * l;
-  c = -v2 * u;
-  b = fmaf(v, sm.gb[jl], fmaf(v2, l + u, sm.A[jl]));
+  const float4 q = sm.lc[jl];
+  a = -v2 * q.y;
+  c = -v2 * q.z;
+  b = fmaf(v, q.w, fmaf(v2, q.y + q.z, q.x));
 }
 
 // PCR on n <= kFR rows of (ra, rb, rc) with NR right-hand sides (rr; rg, rh) for every
@@ -250,7 +322,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       num = fmaf(-c, rt, r);
       ctv = -c * ct;
     }
-    const float inv = __frcp_rn(den);
+    const float inv = f_rcp(den);
     rt = num * inv;
     at = a * inv;
     ct = ctv * inv;
@@ -272,7 +344,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       ahv = -a * ahp;
       num = fmaf(-a, rhp, r);
     }
-    const float inv = __frcp_rn(den);
+    const float inv = f_rcp(den);
     chp = c * inv;
     ahp = ahv * inv;
     rhp = num * inv;
@@ -385,7 +457,7 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
       float a, b, c;
       f_coef(sm, row0 + u + 1, v, v2, a, b, c);
       const float den = (u == 1) ? b : fmaf(-a, chv, b);
-      const float inv = __frcp_rn(den);
+      const float inv = f_rcp(den);
       ahv = ((u == 1) ? a : -a * ahv) * inv;
       chv = c * inv;
       ch[u - 1] = chv;
@@ -409,10 +481,7 @@ __device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
     const int64_t j = G.c0 + t - 1;
     const bool in = j >= 0 && j < G.N;
     const int64_t g = G.co + j;
-    sm.A[t] = in ? D.fc.A[g] : 1.0f;
-    sm.gl[t] = in ? D.fc.gl[g] : 0.0f;
-    sm.gu[t] = in ? D.fc.gu[g] : 0.0f;
-    sm.gb[t] = in ? D.fc.gb[g] : 0.0f;
+    sm.lc[t] = in ? make_float4(D.fc.A[g], D.fc.gl[g], D.fc.gu[g], D.fc.gb[g]) : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     sm.od[t] = in ? D.fc.od[g] : 0.0f;
     sm.dlx[t] = in ? D.fc.dlx[g] : 0.0f;
     sm.kcd[t] = in ? D.fc.kcd[g] : 0.0f;
@@ -516,10 +585,11 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
     const int64_t g = G.co + j, N = G.N;
     const float xj = (float)f_x<FULL>(X, G, j), xl = j > 0 ? (float)f_x<FULL>(X, G, j - 1) : 0.0f,
                 xr = j < N - 1 ? (float)f_x<FULL>(X, G, j + 1) : 0.0f;
-    const float gl = sm.gl[t + 1], gu = sm.gu[t + 1];
+    const float4 q = sm.lc[t + 1];
+    const float gl = q.y, gu = q.z;
     sm.P1[t] = -D.fc.alpha[g] * xj;
     sm.P2[t] = gl * (xj - xl) + gu * (xj - xr);
-    sm.P3[t] = sm.gb[t + 1] * xj;
+    sm.P3[t] = q.w * xj;
     sm.fl[t] = (double)((float)I.wv2 * (D.fc.fR[g] * (xj - xr) + D.fc.fL[g] * (xj - xl)) +
                         (float)I.wv * D.fc.gbx[g] * xj);
     return;
@@ -1093,31 +1163,31 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
     } else {
       zv[t] = 0.0;
     }
-    f_slice_sums<1, true>(sm, 1, [&](int, int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
-    f_cluster_reduce(sm, cl, par, 1, true);
+    f_reduce<0, true>(sm, cl, par, 0, [](int, int) { return 0.0; },
+                      [&](int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
     const double xmax = sm.sums[0];
     sm.wgt[t] = real ? __frcp_rn((float)(fabs(x[j]) + D.wfloor * xmax + 1e-300)) : 0.0f;
     __syncthreads();
     double* v0 = Vi(0);
     f_prec(sm, cl, D, I, G, zv, v0, par);
     {
-      f_slice_sums<2, false>(sm, 2, [&](int i, int c) {
-        if (G.c0 + c >= N) return 0.0;
-        const double a = i == 0 ? v0[c] : x[G.c0 + c];
-        return a * a;
-      });
-      f_cluster_reduce(sm, cl, par, 2, false);
+      // |v0|^2 and |x|^2, and the weighted maximum of v0 (the stopping test), in one pass
+      f_reduce<2, true>(
+          sm, cl, par, 2,
+          [&](int i, int c) {
+            if (G.c0 + c >= N) return 0.0;
+            const double a = i == 0 ? v0[c] : x[G.c0 + c];
+            return a * a;
+          },
+          [&](int c) { return fabs(v0[c]) * (double)sm.wgt[c]; });
       if (t == 0) {
         sm.sc[0] = sqrt(sm.sums[0]);
         sm.sc[1] = sqrt(sm.sums[1]);
         sm.sc[2] = 1.0 / sm.sc[0];
+        sm.sc[3] = sm.sums[2];
       }
       __syncthreads();
-      const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2];
-      f_slice_sums<1, true>(sm, 1, [&](int, int c) { return fabs(v0[c]) * (double)sm.wgt[c]; });
-      f_cluster_reduce(sm, cl, par, 1, true);
-      const double rinf_c = sm.sums[0];
-      __syncthreads();
+      const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2], rinf_c = sm.sc[3];
       bool conv = !(rinf_c > D.rtol);
       if (!first && !conv && rinf_c <= D.stall && (rinf_c >= 0.25 * beta_prev || (D.mixed && cycles >= 2)))
         conv = true;
@@ -1168,8 +1238,8 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-          f_slice_sums<kMaxRestart, false>(sm, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; });
-          f_cluster_reduce(sm, cl, par, jc + 1, false);
+          f_reduce<kMaxRestart, false>(sm, cl, par, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; },
+                                       [](int) { return 0.0; });
           {
             double wj = wv[t];
 #pragma unroll
@@ -1182,8 +1252,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           if (t <= jc) sm.hc[t] += sm.sums[t];
           __syncthreads();
         }
-        f_slice_sums<1, false>(sm, 1, [&](int, int c) { return wv[c] * wv[c]; });
-        f_cluster_reduce(sm, cl, par, 1, false);
+        f_reduce<1, false>(sm, cl, par, 1, [&](int, int c) { return wv[c] * wv[c]; }, [](int) { return 0.0; });
         if (t == 0) {
           sm.sc[0] = sqrt(sm.sums[0]);
           sm.sc[1] = sm.sc[0] > 0.0 ? 1.0 / sm.sc[0] : 0.0;
