@@ -45,6 +45,8 @@ constexpr int kFQ = 16;           // largest cluster: nx <= kFQ * kFS
 constexpr int kFR = 2 * kFW;      // reduced rows per angle and slice
 constexpr int kFX = 33;           // padded row length of the slice's unknowns
 constexpr int kFPL = kFS / 32;    // cells per lane of the preconditioner's warp (16)
+constexpr int kPW = 4;            // preconditioner sub-chunk warps (4 cells each per lane)
+static_assert(kFPL == 4 * kPW, "the preconditioner's two levels assume 16 = 4 x 4 cells per lane");
 
 struct FSmem {
   float x[kFS][kFX];                                   // unknowns of the slice, [cell][angle]
@@ -59,7 +61,8 @@ struct FSmem {
   float endr[2][2][32];                                 // published: r'_F, r'_L
   float coup[2][2][32];                                 // published: a at the first cell, c at the last
   float xlr[2][32];                                     // e at c0 - 1 and at c0 + kFS, per angle
-  float vk[32], v2k[32], wvk[32];                       // per-angle constants (0 past M)
+  float vk[32], v2k[32], wvk[32], wvkl[32];            // per-angle constants (0 past M); wvkl:
+                                                        // w v - wvk (binary32 low part)
   double vkd[32], wvkd[32];
   double wib[2][32], wgn[2][32], won[2][32], wdl[2];   // inflow wall rows (f_load_cells)
   double fl[kFS];                                       // flux sums of the last pass
@@ -72,6 +75,7 @@ struct FSmem {
   // the reduced 64-row system's PCR multipliers and unit spikes, the interface's multipliers
   double pxr[kFPL][32], pinv[kFPL][32], pa[kFPL][32], pch[kFPL][32], pah[kFPL][32];
   double pcs[32], pae[32];
+  double pc0[kPW][32], pa3[kPW][32];                  // level A: c at a sub-chunk's first cell, a at its last
   double pk1[6][64], pk2[6][64], pib[64], pgv[64], phv[64];
   double ik1[5][32], ik2[5][32], iib[32];
   double pS[4], paf, pcl;
@@ -494,6 +498,7 @@ __device__ void f_load_cells(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
     sm.vk[k] = (float)v;
     sm.v2k[k] = (float)(v * v);
     sm.wvk[k] = (float)(w * v);
+    sm.wvkl[k] = (float)(w * v - (double)(float)(w * v));
     sm.vkd[k] = v;
     sm.wvkd[k] = w * v;
     // inflow wall rows of this slice (per angle, fixed for the solve): 1/b of the wall
@@ -570,7 +575,7 @@ __device__ __forceinline__ double f_dnode(const Dev& D, const Inst& I, const FGe
   const double sl = D.sig[G.co + i - 1], sr = D.sig[G.co + i];
   const double sn = (sl > 0.0 && sr > 0.0) ? f_div(2.0 * sl * sr, sl + sr) : 0.0;
   const double vn = 0.5 * (vl + vr);
-  const double den = vn * f_div(I.eps * I.eps, I.c * I.dt) + sn;
+  const double den = vn * I.e2cdt + sn;
   return den > 0.0 ? f_div(vn, den) : 0.0;
 }
 
@@ -621,6 +626,18 @@ __device__ void f_cellparts(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
   }
 }
 
+// hi + lo += (wh + wl) d in binary32 pairs: the product's rounding error from an fma, the
+// weight's low part, and the addition's error (Knuth's two-sum) carried in lo; the pair holds
+// the sum to about 2^-44 of the terms' magnitudes without the binary64 pipe.
+__device__ __forceinline__ void f_acc2(float& hi, float& lo, float wh, float wl, float d) {
+  const float p = __fmul_rn(wh, d);
+  const float e = fmaf(wl, d, fmaf(wh, d, -p));
+  const float sN = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(sN, hi);
+  lo += (__fsub_rn(hi, __fsub_rn(sN, bb)) + __fsub_rn(p, bb)) + e;
+  hi = sN;
+}
+
 // Data part of a data pass: the right-hand side terms kappa/(c dt) Eh^n - kappa v/dx (o_{j+1} - o_j)
 // (o_i = d_i eps^2 O^n_i/(c dt) at interior nodes, 0 at the walls) into sm.x, and the data
 // part of the flux sum_k w_k v_k (o_{j+1,k} - o_{j,k}) into sm.fdat (not at inflow wall cells).
@@ -645,7 +662,7 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
   const bool wallc = I.bc == GRTE_BC_INFLOW && (j == 0 || j == N - 1);
   const float kcd = sm.kcd[jl], kdx = sm.kdx[jl], odj = sm.od[jl], odr = sm.od[jl + 1];
   const bool nj = j >= 1 && j <= N - 1, nr = j + 1 >= 1 && j + 1 <= N - 1;
-  double fsum = 0.0, om = 0.0, omr = 0.0;
+  float fh = 0.0f, fo = 0.0f, oh = 0.0f, oo = 0.0f, rh = 0.0f, ro = 0.0f;   // (hi, lo) sums
   constexpr int B = 8;
   for (int k0 = 0; k0 < 32; k0 += B) {
     float e[B], oj[B], orr[B];
@@ -668,14 +685,15 @@ __device__ void f_stage_data(FSmem& sm, const Dev& D, const Inst& I, const FGeo&
       const float Dj = o1 - o0;
       const float d = real ? fmaf(kcd, e[q], -kdx * sm.vk[kk] * Dj) : 0.0f;
       sm.x[w * kFL + lane][kk] = d;
-      if (real && !wallc) fsum += sm.wvkd[kk] * (double)Dj;
-      om += sm.wvkd[kk] * (double)oj[q];
-      omr += sm.wvkd[kk] * (double)orr[q];
+      const float wh = sm.wvk[kk], wl = sm.wvkl[kk];
+      if (real && !wallc) f_acc2(fh, fo, wh, wl, Dj);
+      f_acc2(oh, oo, wh, wl, oj[q]);
+      if (lane == 31) f_acc2(rh, ro, wh, wl, orr[q]);
     }
   }
-  sm.fdat[w * kFL + lane] = fsum;
-  sm.Om[w * kFL + lane] = om;            // node c0 + t (interior nodes; 0 elsewhere)
-  if (w == kFW - 1 && lane == 31) sm.Om[kFS] = omr;
+  sm.fdat[w * kFL + lane] = (double)fh + (double)fo;
+  sm.Om[w * kFL + lane] = (double)oh + (double)oo;   // node c0 + t (interior nodes; 0 elsewhere)
+  if (w == kFW - 1 && lane == 31) sm.Om[kFS] = (double)rh + (double)ro;
   __syncwarp();
 #pragma unroll 8
   for (int u = 0; u < kFL; ++u) fd[u * 32 + lane] = sm.x[w * kFL + u][lane];
@@ -824,14 +842,21 @@ __device__ __forceinline__ double f_row(double v0, double v1, int i) {
   return (src & 1) ? b : a;
 }
 
+// Cell slot (within a lane's 16-cell chunk) of row i of the preconditioner's level-B
+// system: the end cells 0, 3, 4, 7, ..., 15 of the four sub-chunks.
+__device__ __forceinline__ int f_pcb(int i) { return 4 * (i >> 1) + 3 * (i & 1); }
+
 // The single-effective-angle Schur operator of the preconditioner (binary64):
 //   P = alpha + Gbar (A + Gbar)^{-1} beta, applied as  u = (A + (A/alpha) Gbar)^{-1} (beta/alpha) r,
 //   z = (r - Gbar u)/alpha,  Gbar = sum_k w_k G_k, beta = A - alpha.
 // The tridiagonal matrix T = A + (A/alpha) Gbar is the same for every application of a solve:
-// f_prec_factor eliminates it once (warp 0 of each CTA, 32 lanes x 16 cells: chunk sweeps,
-// PCR of the 64 chunk-end rows with its two unit spikes, the slice's 2x2 Schur complement,
-// and in every CTA the PCR multipliers of the 2Q-row interface system); f_prec_apply then
-// solves with the stored factors, without divisions.
+// f_prec_factor eliminates it once and f_prec then solves with the stored factors, without
+// divisions.  A slice's 512 cells are 32 chunks of 16 (one per lane), each of four 4-cell
+// sub-chunks.  Level A (warps 0..3, one per sub-partition: the binary64 pipe is the scarce
+// resource) eliminates each sub-chunk's two interior cells, leaving an 8-row system per
+// chunk; level B (warp 0) eliminates its six interior rows, leaving the 64 chunk-end rows,
+// solved by PCR with two unit spikes; then the slice's 2x2 Schur complement and, in every
+// CTA, the 2Q-row interface system of the cluster (PCR multipliers stored per level).
 __device__ void f_prec_coef(const Dev& D, const Inst& I, const FGeo& G, int64_t j, double& a, double& b,
                             double& c) {
   if (j >= G.N) { a = 0.0; b = 1.0; c = 0.0; return; }
@@ -845,38 +870,81 @@ __device__ void f_prec_coef(const Dev& D, const Inst& I, const FGeo& G, int64_t 
 
 __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
                               int& par) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool w0 = threadIdx.x < 32;
+  // level A (warps 0..3, one per sub-partition): sub-chunk w (cells 4w..4w+3) of lane l's
+  // 16-cell chunk; its two interior cells eliminated, its end rows become rows 2w, 2w+1 of
+  // the chunk's 8-row level-B system, kept as (a, b, c) in the free reduced-system arrays
+  double* const lb = reinterpret_cast<double*>(&sm.ra[0][0]);   // [3][8][32]
+  if (w < kPW) {
+    const int u0 = 4 * w;
+    const int64_t s = G.c0 + lane * kFPL + u0;
+    double a0, b0, c0, a1, b1, c1, a2, b2, c2, a3, b3, c3;
+    f_prec_coef(D, I, G, s, a0, b0, c0);
+    f_prec_coef(D, I, G, s + 1, a1, b1, c1);
+    f_prec_coef(D, I, G, s + 2, a2, b2, c2);
+    f_prec_coef(D, I, G, s + 3, a3, b3, c3);
+    const double i1 = 1.0 / b1;
+    const double ah1 = a1 * i1, ch1 = c1 * i1;
+    const double i2 = 1.0 / (b2 - a2 * ch1);
+    const double ah2 = -a2 * ah1 * i2, ch2 = c2 * i2;
+    sm.pinv[u0 + 1][lane] = i1;
+    sm.pa[u0 + 1][lane] = a1;
+    sm.pch[u0 + 1][lane] = ch1;
+    sm.pah[u0 + 1][lane] = ah1;
+    sm.pinv[u0 + 2][lane] = i2;
+    sm.pa[u0 + 2][lane] = a2;
+    sm.pch[u0 + 2][lane] = ch2;
+    sm.pah[u0 + 2][lane] = ah2;
+    sm.pc0[w][lane] = c0;
+    sm.pa3[w][lane] = a3;
+    // x_1 = rc - cc x_e - ac x_s
+    const double cc = -ch1 * ch2, ac = ah1 - ch1 * ah2;
+    lb[(0 * 8 + 2 * w) * 32 + lane] = a0;
+    lb[(1 * 8 + 2 * w) * 32 + lane] = b0 - c0 * ac;
+    lb[(2 * 8 + 2 * w) * 32 + lane] = -c0 * cc;
+    lb[(0 * 8 + 2 * w + 1) * 32 + lane] = -a3 * ah2;
+    lb[(1 * 8 + 2 * w + 1) * 32 + lane] = b3 - a3 * ch2;
+    lb[(2 * 8 + 2 * w + 1) * 32 + lane] = c3;
+  }
+  __syncthreads();
   if (w0) {
-    const int64_t s = G.c0 + lane * kFPL;
+    // level B (warp 0): the 8 rows' interior (rows 1..6, cells f_pcb(1..6)) eliminated;
+    // factors stored at those cells' slots
+    double a[8], b[8], c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      a[i] = lb[(0 * 8 + i) * 32 + lane];
+      b[i] = lb[(1 * 8 + i) * 32 + lane];
+      c[i] = lb[(2 * 8 + i) * 32 + lane];
+    }
+    double chv[8], ahv[8];
     double chp = 0.0, ahp = 0.0;
 #pragma unroll
-    for (int u = 1; u <= kFPL - 2; ++u) {
-      double a, b, c;
-      f_prec_coef(D, I, G, s + u, a, b, c);
-      const double den = (u == 1) ? b : b - a * chp;
+    for (int i = 1; i <= 6; ++i) {
+      const double den = (i == 1) ? b[i] : b[i] - a[i] * chp;
       const double inv = 1.0 / den;
-      ahp = ((u == 1) ? a : -a * ahp) * inv;
-      chp = c * inv;
+      ahp = ((i == 1) ? a[i] : -a[i] * ahp) * inv;
+      chp = c[i] * inv;
+      const int u = f_pcb(i);
       sm.pinv[u][lane] = inv;
-      sm.pa[u][lane] = a;
+      sm.pa[u][lane] = a[i];
       sm.pch[u][lane] = chp;
       sm.pah[u][lane] = ahp;
+      chv[i] = chp;
+      ahv[i] = ahp;
     }
-    double cc = sm.pch[kFPL - 2][lane], ac = sm.pah[kFPL - 2][lane];
+    double cc = chv[6], ac = ahv[6];
 #pragma unroll
-    for (int u = kFPL - 3; u >= 1; --u) {
-      const double chu = sm.pch[u][lane];
-      cc = -chu * cc;
-      ac = sm.pah[u][lane] - chu * ac;
+    for (int i = 5; i >= 1; --i) {
+      cc = -chv[i] * cc;
+      ac = ahv[i] - chv[i] * ac;
     }
-    double as, bs, cs, ae, be, ce;
-    f_prec_coef(D, I, G, s, as, bs, cs);
-    f_prec_coef(D, I, G, s + kFPL - 1, ae, be, ce);
+    const double as = a[0], bs = b[0], cs = c[0], ae = a[7], be = b[7], ce = c[7];
     sm.pcs[lane] = cs;
     sm.pae[lane] = ae;
     double ra0 = (lane == 0) ? 0.0 : as, rb0 = bs - cs * ac, rc0 = -cs * cc;
-    double ra1 = -ae * sm.pah[kFPL - 2][lane], rb1 = be - ae * sm.pch[kFPL - 2][lane];
+    double ra1 = -ae * ahv[6], rb1 = be - ae * chv[6];
     double rc1 = (lane == 31) ? 0.0 : ce;
     double g0 = (lane == 0) ? 1.0 : 0.0, g1 = 0.0, h0 = 0.0, h1 = (lane == 31) ? 1.0 : 0.0;
     const double af = __shfl_sync(0xffffffffu, as, 0), cl_ = __shfl_sync(0xffffffffu, ce, 31);
@@ -977,28 +1045,44 @@ __device__ void f_prec_factor(FSmem& sm, cg::cluster_group& cl, const Dev& D, co
 __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Inst& I, const FGeo& G,
                        const double* rin, double* z, int& par) {
   const int64_t N = G.N, co = G.co;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool w0 = threadIdx.x < 32;
-  double y0 = 0.0, y1 = 0.0, rh14 = 0.0;
-  if (w0) {
-    const int64_t s = G.c0 + lane * kFPL;
+  double y0 = 0.0, y1 = 0.0;
+  // level A (warps 0..3): the sub-chunk's scaled right-hand side, its forward sweep (rh at
+  // the interior slots) and its two level-B right-hand sides (at the end slots)
+  if (w < kPW) {
+    const int u0 = 4 * w, tl = lane * kFPL + u0;
+    const int64_t s = G.c0 + tl;
+    double r[4];
 #pragma unroll
-    for (int u = 0; u < kFPL; ++u) {
-      const int64_t j = s + u;
-      sm.pxr[u][lane] = (j < N) ? D.cf.ratio[co + j] * rin[lane * kFPL + u] : 0.0;
-    }
+    for (int v = 0; v < 4; ++v) r[v] = (s + v < N) ? D.cf.ratio[co + s + v] * rin[tl + v] : 0.0;
+    const double rh1 = r[1] * sm.pinv[u0 + 1][lane];
+    const double rh2 = (r[2] - sm.pa[u0 + 2][lane] * rh1) * sm.pinv[u0 + 2][lane];
+    const double rc = rh1 - sm.pch[u0 + 1][lane] * rh2;
+    sm.pxr[u0][lane] = r[0] - sm.pc0[w][lane] * rc;
+    sm.pxr[u0 + 1][lane] = rh1;
+    sm.pxr[u0 + 2][lane] = rh2;
+    sm.pxr[u0 + 3][lane] = r[3] - sm.pa3[w][lane] * rh2;
+  }
+  __syncthreads();
+  if (w0) {
+    // level B (warp 0): forward sweep of the 8 rows, then the chunk's two reduced rows
+    double rb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rb[i] = sm.pxr[f_pcb(i)][lane];
+    double rhv[8];
     double rh = 0.0;
 #pragma unroll
-    for (int u = 1; u <= kFPL - 2; ++u) {
-      const double xu = sm.pxr[u][lane];
-      rh = (u == 1 ? xu : xu - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
+    for (int i = 1; i <= 6; ++i) {
+      const int u = f_pcb(i);
+      rh = (i == 1 ? rb[1] : rb[i] - sm.pa[u][lane] * rh) * sm.pinv[u][lane];
+      rhv[i] = rh;
       sm.pxr[u][lane] = rh;
     }
-    rh14 = rh;
-    double rc = rh;
+    double rc = rhv[6];
 #pragma unroll
-    for (int u = kFPL - 3; u >= 1; --u) rc = sm.pxr[u][lane] - sm.pch[u][lane] * rc;
-    double r0 = sm.pxr[0][lane] - sm.pcs[lane] * rc, r1 = sm.pxr[kFPL - 1][lane] - sm.pae[lane] * rh14;
+    for (int i = 5; i >= 1; --i) rc = rhv[i] - sm.pch[f_pcb(i)][lane] * rc;
+    double r0 = rb[0] - sm.pcs[lane] * rc, r1 = rb[7] - sm.pae[lane] * rhv[6];
     for (int l = 0, st = 1; st < 64; ++l, st <<= 1) {
       double nr[2];
 #pragma unroll
@@ -1038,9 +1122,11 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
     const double xe = y1 - la * sm.pgv[2 * lane + 1] - fc * sm.phv[2 * lane + 1];
     sm.pu[lane * kFPL] = xs;
     sm.pu[lane * kFPL + kFPL - 1] = xe;
+    // level B back substitution (cells 3, 4, 7, ..., 12)
     double xn = xe;
 #pragma unroll
-    for (int u = kFPL - 2; u >= 1; --u) {
+    for (int i = 6; i >= 1; --i) {
+      const int u = f_pcb(i);
       xn = sm.pxr[u][lane] - sm.pch[u][lane] * xn - sm.pah[u][lane] * xs;
       sm.pu[lane * kFPL + u] = xn;
     }
@@ -1048,6 +1134,16 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       sm.pxl[0] = Lp;
       sm.pxl[1] = Fn;
     }
+  }
+  __syncthreads();
+  // level A back substitution (warps 0..3): the sub-chunk's two interior cells
+  if (w < kPW) {
+    const int u0 = 4 * w, tl = lane * kFPL + u0;
+    const double xs = sm.pu[tl], xe = sm.pu[tl + 3];
+    const double x2 = sm.pxr[u0 + 2][lane] - sm.pch[u0 + 2][lane] * xe - sm.pah[u0 + 2][lane] * xs;
+    const double x1 = sm.pxr[u0 + 1][lane] - sm.pch[u0 + 1][lane] * x2 - sm.pah[u0 + 1][lane] * xs;
+    sm.pu[tl + 1] = x1;
+    sm.pu[tl + 2] = x2;
   }
   par ^= 1;
   __syncthreads();
@@ -1097,8 +1193,7 @@ __device__ void f_corr_flux(FSmem& sm, const Dev& D, const Inst& I, const FGeo& 
                  xr = j < N - 1 ? f_x<true>(X, G, j + 1) : 0.0;
     const double dL = dsd[t], dR = dsd[t + 1];
     // rho and data parts
-    double fc = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) * f_div(1.0, I.dx) +
-                f_div(I.eps * I.eps, I.c * I.dt) * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
+    double fc = I.wv2 * (dR * (xj - xr) + dL * (xj - xl)) * I.rdx + I.e2cdt * (dR * sm.Om[t + 1] - dL * sm.Om[t]);
     // e/o part: sum_k -w_k v_k^2 [d*_{j+1}(e_{j+1} - e_j) - d*_j (e_j - e_{j-1})]/dx
     const float idxf = __frcp_rn((float)I.dx);
     const float dRc = (float)dR * idxf, dLc = (float)dL * idxf;

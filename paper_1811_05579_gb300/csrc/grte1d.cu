@@ -53,6 +53,7 @@ struct Inst {
   double eps, dt, dx, a, c, Cv;
   double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
   double two_eps, inv_eps; // 2/eps, 1/eps
+  double rdx, e2cdt;       // 1/dx, eps^2/(c dt)
   double bLflux, bRflux;   // sum_k w_k v_k b_L,k and sum_k w_k v_k b_R,k
   int64_t cell_off;        // per-cell arrays
   int64_t elem_off;        // E-like arrays, line k at elem_off + k*N
@@ -1786,6 +1787,8 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
       I.bRflux = fr;
     }
     I.inv_eps = 1.0 / p.eps;
+    I.rdx = 1.0 / I.dx;
+    I.e2cdt = p.eps * p.eps / (p.c * p.dt);
     I.cell_off = coff;
     I.elem_off = eoff;
     I.nelem_off = noff;
@@ -2975,7 +2978,7 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
     fl += w[k] * v[k] * bL[k];
     fr += w[k] * v[k] * bR[k];
   }
-  I.wv = wv; I.wv2 = wv2; I.two_eps = 2.0 / p->eps; I.inv_eps = 1.0 / p->eps; I.bLflux = fl; I.bRflux = fr;
+  I.wv = wv; I.wv2 = wv2; I.two_eps = 2.0 / p->eps; I.inv_eps = 1.0 / p->eps; I.rdx = 1.0 / I.dx; I.e2cdt = p->eps * p->eps / (p->c * p->dt); I.bLflux = fl; I.bRflux = fr;
   I.cell_off = 0; I.elem_off = 0; I.nelem_off = 0; I.red_off = 0; I.ang_off = 0; I.line_off = 0;
   Line lines[kNaMaxAngles];
   for (int k = 0; k < M; ++k) lines[k] = Line{0, k, (int64_t)k * kNaRedLine, (int64_t)k * (5 * N + kNaFacLine)};
