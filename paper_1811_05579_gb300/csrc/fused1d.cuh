@@ -91,7 +91,8 @@ struct FSmem {
   double pcoup[2][2];
   double pxl[2];
   // GMRES state (identical in every CTA)
-  double H[(kMaxRestart + 1) * kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart],
+  double H[(kMaxRestart + 1) * kMaxRestart], hinv[kMaxRestart], g[kMaxRestart + 1], cs[kMaxRestart],
+      sn[kMaxRestart],
       y[kMaxRestart], hc[kMaxRestart + 2];
   int stop;
 };
@@ -547,6 +548,23 @@ __device__ __forceinline__ double f_div(double a, double b) {
   const double r = (double)__frcp_rn((float)b);
   const double q = a * r;
   return q + (a - q * b) * r;
+}
+
+// sqrt(q) and 1/sqrt(q) in binary64 for q >= 0 without the binary64 square root and divide
+// sequences: y = 1/sqrt(q) from a binary32 seed refined by two Newton-Raphson steps
+// y <- y (3 - q y^2)/2 (quadratic convergence: ~2^-22 -> ~2^-44 -> binary64 rounding), and
+// sqrt(q) = q y.  Outside the seed's range (and for 0, inf, NaN) the plain operations.
+__device__ __forceinline__ void f_sqrt_pair(double q, double& r, double& ir) {
+  if (!(q > 1e-36 && q < 1e36)) {
+    r = sqrt(q);
+    ir = 1.0 / r;
+    return;
+  }
+  double y = (double)rsqrtf((float)q);
+  y = y * fma(-0.5 * q, y * y, 1.5);
+  y = y * fma(-0.5 * q, y * y, 1.5);
+  r = q * y;
+  ir = y;
 }
 
 // The multiplier of the correction's flux (sigma_0/T^3, Eq. dis-cor-marshak1 with the
@@ -1147,7 +1165,8 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
   }
   par ^= 1;
   __syncthreads();
-  // z = (r - Gbar u)/alpha, Gbar u = wv2 [gl (u_j - u_{j-1}) + gu (u_j - u_{j+1})] + wv gb u_j
+  // z = (r - Gbar u)/alpha, Gbar u = wv2 [gl (u_j - u_{j-1}) + gu (u_j - u_{j+1})] + wv gb u_j,
+  // from the per-cell coefficients zl, zc, zr (cell coefficient kernel)
   {
     const int t = threadIdx.x;
     const int64_t j = G.c0 + t;
@@ -1156,8 +1175,7 @@ __device__ void f_prec(FSmem& sm, cg::cluster_group& cl, const Dev& D, const Ins
       const double uj = sm.pu[t];
       const double uL = j > 0 ? (t > 0 ? sm.pu[t - 1] : sm.pxl[0]) : 0.0;
       const double uR = j < N - 1 ? (t < kFS - 1 ? sm.pu[t + 1] : sm.pxl[1]) : 0.0;
-      const double Gu = I.wv2 * (D.cf.gl[g] * (uj - uL) + D.cf.gu[g] * (uj - uR)) + I.wv * D.cf.gb[g] * uj;
-      z[t] = (rin[t] - Gu) * D.cf.ralpha[g];
+      z[t] = rin[t] * D.cf.ralpha[g] - D.cf.zc[g] * uj + D.cf.zl[g] * uL + D.cf.zr[g] * uR;
     } else {
       z[t] = 0.0;
     }
@@ -1276,10 +1294,15 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
           },
           [&](int c) { return fabs(v0[c]) * (double)sm.wgt[c]; });
       if (t == 0) {
-        sm.sc[0] = sqrt(sm.sums[0]);
-        sm.sc[1] = sqrt(sm.sums[1]);
-        sm.sc[2] = 1.0 / sm.sc[0];
+        double r, ir;
+        f_sqrt_pair(sm.sums[0], r, ir);
+        sm.sc[0] = r;
+        sm.sc[2] = ir;
         sm.sc[3] = sm.sums[2];
+      } else if (t == 32) {   // another sub-partition's binary64 pipe
+        double r, ir;
+        f_sqrt_pair(sm.sums[1], r, ir);
+        sm.sc[1] = r;
       }
       __syncthreads();
       const double nrm = sm.sc[0], xn = sm.sc[1], inv_nrm = sm.sc[2], rinf_c = sm.sc[3];
@@ -1349,8 +1372,10 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         }
         f_reduce<1, false>(sm, cl, par, 1, [&](int, int c) { return wv[c] * wv[c]; }, [](int) { return 0.0; });
         if (t == 0) {
-          sm.sc[0] = sqrt(sm.sums[0]);
-          sm.sc[1] = sm.sc[0] > 0.0 ? 1.0 / sm.sc[0] : 0.0;
+          double r, ir;
+          f_sqrt_pair(sm.sums[0], r, ir);
+          sm.sc[0] = r;
+          sm.sc[1] = r > 0.0 ? ir : 0.0;
         }
         __syncthreads();
         const double nrmw = sm.sc[0];
@@ -1364,9 +1389,17 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
             hc[i] = tq;
           }
           const double a0 = hc[jc], b0 = hc[jc + 1];
-          const double rr = hypot(a0, b0);
-          const double c0g = rr > 0.0 ? a0 / rr : 1.0, s0g = rr > 0.0 ? b0 / rr : 0.0;
+          const double q = a0 * a0 + b0 * b0;
+          double rr, irr;
+          if (q > 1e-36 && q < 1e36) {
+            f_sqrt_pair(q, rr, irr);
+          } else {
+            rr = hypot(a0, b0);
+            irr = 1.0 / rr;
+          }
+          const double c0g = rr > 0.0 ? a0 * irr : 1.0, s0g = rr > 0.0 ? b0 * irr : 0.0;
           hc[jc] = rr;
+          sm.hinv[jc] = irr;   // 1/H[jc][jc] for the triangular solve
           const double gj = sm.g[jc];
           const double gnext = -s0g * gj;
           sm.cs[jc] = c0g;
@@ -1388,7 +1421,7 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         for (int i = kk - 1; i >= 0; --i) {
           double tq = sm.g[i];
           for (int l = i + 1; l < kk; ++l) tq -= sm.H[i * kMaxRestart + l] * sm.y[l];
-          sm.y[i] = tq / sm.H[i * kMaxRestart + i];
+          sm.y[i] = tq * sm.hinv[i];
         }
       }
       __syncthreads();

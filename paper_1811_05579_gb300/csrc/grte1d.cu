@@ -87,6 +87,9 @@ struct CellCoef {
   // left node of each cell d*/dx and d* eps^2/(c dt), d* the node coefficient of
   // V* = (U*)^{3/4} (Eq. dis-cor-marshak1 with the predicted data)
   double *dsx, *ods;
+  // mixed path: the preconditioner's last step z = r/alpha - zc u_j + zl u_{j-1} + zr u_{j+1}
+  // (z = (r - Gbar u)/alpha, Gbar u = wv2 [gl (u_j - u_{j-1}) + gu (u_j - u_{j+1})] + wv gb u_j)
+  double *zl, *zc, *zr;
 };
 
 // Binary32 copies of the per-cell values that the line and Krylov kernels use per
@@ -238,6 +241,9 @@ __global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_
     f.alpha[gid] = (float)alpha;
     f.kcde[gid] = (float)(D.cf.kcd[gid] * I.inv_eps);
     f.kdxe[gid] = (float)(D.cf.kdx[gid] * I.inv_eps);
+    D.cf.zl[gid] = I.wv2 * D.cf.gl[gid] * D.cf.ralpha[gid];
+    D.cf.zr[gid] = I.wv2 * D.cf.gu[gid] * D.cf.ralpha[gid];
+    D.cf.zc[gid] = (I.wv2 * (D.cf.gl[gid] + D.cf.gu[gid]) + I.wv * D.cf.gb[gid]) * D.cf.ralpha[gid];
     f.dlxe[gid] = (float)(D.cf.dlx[gid] * I.eps);
     f.fR[gid] = (float)D.cf.fR[gid];
     f.fL[gid] = (float)D.cf.fL[gid];
@@ -1868,6 +1874,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
     AL(f.kdx, nc); AL(f.ratio, nc); AL(f.ralpha, nc); AL(f.alpha, nc); AL(f.kcde, nc); AL(f.kdxe, nc);
     AL(f.dlxe, nc); AL(f.P1, nc); AL(f.P2, nc); AL(f.P3, nc); AL(f.Frho, nc); AL(f.Q1, nc); AL(f.Q2, nc);
     AL(f.gU, nc); AL(f.fR, nc); AL(f.fL, nc); AL(f.gbx, nc); AL(f.dsx, nc); AL(f.ods, nc);
+    AL(D.cf.zl, nc); AL(D.cf.zc, nc); AL(D.cf.zr, nc);
   }
   {
     char* p_;
