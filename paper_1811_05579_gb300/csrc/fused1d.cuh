@@ -411,21 +411,42 @@ __device__ void f_line_solve(FSmem& sm, cg::cluster_group& cl, const FGeo& G, in
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n2 * 32; idx += kFT) {
-    const int i = idx >> 5, kk = idx & 31, qq = i >> 1, side = i & 1;
-    const float* e = cl.map_shared_rank(&sm.ends[par][0][0], qq);
-    const float* er = cl.map_shared_rank(&sm.endr[par][0][0], qq);
-    const float* cp = cl.map_shared_rank(&sm.coup[par][0][0], qq);
-    if (side == 0) {
-      sm.ra[i][kk] = (qq > 0) ? cp[kk] : 0.0f;
-      sm.rb[i][kk] = e[0 * 32 + kk];
-      sm.rc[i][kk] = e[1 * 32 + kk];
-      sm.rr[i][kk] = er[0 * 32 + kk];
-    } else {
-      sm.ra[i][kk] = e[2 * 32 + kk];
-      sm.rb[i][kk] = e[3 * 32 + kk];
-      sm.rc[i][kk] = (qq < Q - 1) ? cp[32 + kk] : 0.0f;
-      sm.rr[i][kk] = er[1 * 32 + kk];
+  {
+    // two items (row, angle) per thread, every remote load issued before the stores
+    static_assert(2 * kFT >= 2 * kFQ * 32, "interface gather: two items per thread");
+    float va[2], vb[2], vc[2], vr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = threadIdx.x + h * kFT;
+      const int i = idx >> 5, kk = idx & 31, qq = i >> 1, side = i & 1;
+      va[h] = vb[h] = vc[h] = vr[h] = 0.0f;
+      if (idx < n2 * 32) {
+        const float* e = cl.map_shared_rank(&sm.ends[par][0][0], qq);
+        const float* er = cl.map_shared_rank(&sm.endr[par][0][0], qq);
+        const float* cp = cl.map_shared_rank(&sm.coup[par][0][0], qq);
+        if (side == 0) {
+          va[h] = (qq > 0) ? cp[kk] : 0.0f;
+          vb[h] = e[0 * 32 + kk];
+          vc[h] = e[1 * 32 + kk];
+          vr[h] = er[0 * 32 + kk];
+        } else {
+          va[h] = e[2 * 32 + kk];
+          vb[h] = e[3 * 32 + kk];
+          vc[h] = (qq < Q - 1) ? cp[32 + kk] : 0.0f;
+          vr[h] = er[1 * 32 + kk];
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = threadIdx.x + h * kFT;
+      if (idx < n2 * 32) {
+        const int i = idx >> 5, kk = idx & 31;
+        sm.ra[i][kk] = va[h];
+        sm.rb[i][kk] = vb[h];
+        sm.rc[i][kk] = vc[h];
+        sm.rr[i][kk] = vr[h];
+      }
     }
   }
   __syncthreads();
@@ -1352,12 +1373,14 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
         f_prec(sm, cl, D, I, G, zv, wv, par);
         // classical Gram-Schmidt, twice (CGS2): per pass one block sum of the jc + 1 dot
         // products w.V_i and one cluster sum; the Hessenberg column accumulates in shared
-        // memory
-        if (t < kMaxRestart + 2) sm.hc[t] = 0.0;
-        __syncthreads();
+        // memory.  The second pass also sums |w1|^2, and |w2|^2 = |w1|^2 - |h2|^2 (V
+        // orthonormal): exact to rounding while |h2|^2 is small against |w1|^2, which it is
+        // after a first pass unless w lies almost in span(V); otherwise a separate sum.
         for (int pass = 0; pass < 2; ++pass) {
-          f_reduce<kMaxRestart, false>(sm, cl, par, jc + 1, [&](int i, int c) { return wv[c] * Vi(i)[c]; },
-                                       [](int) { return 0.0; });
+          const int nd = jc + 1 + pass;   // the dot products, and |w1|^2 in the second pass
+          f_reduce<kMaxRestart + 1, false>(
+              sm, cl, par, nd, [&](int i, int c) { return wv[c] * (i <= jc ? Vi(i)[c] : wv[c]); },
+              [](int) { return 0.0; });
           {
             double wj = wv[t];
 #pragma unroll
@@ -1367,17 +1390,32 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
             }
             wv[t] = wj;
           }
-          if (t <= jc) sm.hc[t] += sm.sums[t];
+          if (t <= jc) sm.hc[t] = (pass == 0 ? 0.0 : sm.hc[t]) + sm.sums[t];
+          if (pass == 1 && t == 0) {
+            double h2 = 0.0;
+            for (int i = 0; i <= jc; ++i) h2 += sm.sums[i] * sm.sums[i];
+            const double w1 = sm.sums[jc + 1];
+            const bool pyth = h2 <= 1e-4 * w1;
+            sm.sc[2] = pyth ? 1.0 : 0.0;
+            if (pyth) {
+              double r, ir;
+              f_sqrt_pair(w1 - h2, r, ir);
+              sm.sc[0] = r;
+              sm.sc[1] = r > 0.0 ? ir : 0.0;
+            }
+          }
           __syncthreads();
         }
-        f_reduce<1, false>(sm, cl, par, 1, [&](int, int c) { return wv[c] * wv[c]; }, [](int) { return 0.0; });
-        if (t == 0) {
-          double r, ir;
-          f_sqrt_pair(sm.sums[0], r, ir);
-          sm.sc[0] = r;
-          sm.sc[1] = r > 0.0 ? ir : 0.0;
+        if (sm.sc[2] == 0.0) {
+          f_reduce<1, false>(sm, cl, par, 1, [&](int, int c) { return wv[c] * wv[c]; }, [](int) { return 0.0; });
+          if (t == 0) {
+            double r, ir;
+            f_sqrt_pair(sm.sums[0], r, ir);
+            sm.sc[0] = r;
+            sm.sc[1] = r > 0.0 ? ir : 0.0;
+          }
+          __syncthreads();
         }
-        __syncthreads();
         const double nrmw = sm.sc[0];
         // Givens rotations and the GMRES residual estimate (thread 0; shared with all)
         if (t == 0) {
