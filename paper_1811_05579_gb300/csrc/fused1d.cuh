@@ -562,14 +562,8 @@ __device__ __forceinline__ double f_x(const FVec& X, const FGeo& G, int64_t j) {
   return t < 0 ? X.left : (t >= kFS ? X.right : X.p[t]);
 }
 
-// a / b in binary64 from a binary32 reciprocal and one residual correction (relative
-// error ~1e-14; the binary64 divide is a long FP64 sequence on this part)
-__device__ __forceinline__ double f_div(double a, double b) {
-  if (!(fabs(b) > 1e-30 && fabs(b) < 1e30)) return a / b;   // outside the binary32 range
-  const double r = (double)__frcp_rn((float)b);
-  const double q = a * r;
-  return q + (a - q * b) * r;
-}
+// f_div: a / b in binary64 from a binary32 reciprocal and one residual correction (q_div)
+__device__ __forceinline__ double f_div(double a, double b) { return q_div(a, b); }
 
 // sqrt(q) and 1/sqrt(q) in binary64 for q >= 0 without the binary64 square root and divide
 // sequences: y = 1/sqrt(q) from a binary32 seed refined by two Newton-Raphson steps
@@ -598,7 +592,8 @@ __device__ __forceinline__ double f_vstar(const Dev& D, const Inst& I, const FGe
   const double u = fmax(f_div(D.U[g] + gam * f_x<true>(X, G, i), 1.0 + gam * (I.a * I.c)), 0.0);
   if (u == 0.0) return 0.0;
   if (I.p != 3.0) return pow(u, 0.25 * I.p);          // sigma_0/T^p, p != 3: V* = u^{p/4}
-  if (!(u > 1e-25 && u < 1e25)) return pow(u, 0.75);   // outside the binary32 seed's range
+  // outside the range where u^{3/2} and 4 y^3 = 4 u^{9/4} are normal binary32 numbers
+  if (!(u > 1e-16 && u < 1e16)) return pow(u, 0.75);
   const float uf = (float)u;
   const double y = (double)sqrtf(uf * sqrtf(uf));
   const double y2 = y * y, u2 = u * u;

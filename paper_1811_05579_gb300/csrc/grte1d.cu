@@ -53,7 +53,11 @@ struct Inst {
   double eps, dt, dx, a, c, Cv;
   double wv, wv2;          // sum_k w_k v_k, sum_k w_k v_k^2
   double two_eps, inv_eps; // 2/eps, 1/eps
+  // derived per-instance constants (inst_derive), so that no per-cell kernel divides by them
   double rdx, e2cdt;       // 1/dx, eps^2/(c dt)
+  double rcdt, reps2, rdx2; // 1/(c dt), 1/eps^2, 1/dx^2
+  double gamc, gbc;        // 4 dt/(eps^2 Cv), 2/(eps dx)
+  double adt, cvdt, ekc;   // a/dt, Cv/dt, eps^2 Cv/(c dt^2)
   double bLflux, bRflux;   // sum_k w_k v_k b_L,k and sum_k w_k v_k b_R,k
   int64_t cell_off;        // per-cell arrays
   int64_t elem_off;        // E-like arrays, line k at elem_off + k*N
@@ -63,6 +67,22 @@ struct Inst {
   int line_off;            // first line of this instance
   int64_t fd_off;          // fused solve: the instance's staged data terms (floats)
 };
+
+// The derived constants of an instance from eps, dt, dx, c and Cv.
+static void inst_derive(Inst& I) {
+  I.two_eps = 2.0 / I.eps;
+  I.inv_eps = 1.0 / I.eps;
+  I.rdx = 1.0 / I.dx;
+  I.e2cdt = I.eps * I.eps / (I.c * I.dt);
+  I.rcdt = 1.0 / (I.c * I.dt);
+  I.reps2 = 1.0 / (I.eps * I.eps);
+  I.rdx2 = 1.0 / (I.dx * I.dx);
+  I.gamc = 4.0 * I.dt / (I.eps * I.eps * I.Cv);
+  I.gbc = 2.0 / (I.eps * I.dx);
+  I.adt = I.a / I.dt;
+  I.cvdt = I.Cv / I.dt;
+  I.ekc = I.eps * I.eps * I.Cv / (I.c * I.dt * I.dt);
+}
 
 struct Line {
   int inst, k;
@@ -166,88 +186,110 @@ struct KryT { using type = double; };
 // theta = 1).  d_i = kappa_i / (kappa_i eps^2/(c dt) + sig_i) with sig_i the
 // harmonic mean of the two cells; gl/gu/gb are the tridiagonal streaming operator
 // G (per unit v^2 and v) of kappa v (O_{j+1} - O_j)/dx after eliminating O.
-__global__ void k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start,
-                            int64_t ncell, int use_new_T) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= ncell) return;
+__global__ void __launch_bounds__(256) k_cell_coef(Dev D, int n_inst, const int64_t* __restrict__ cell_inst_start,
+                                                   int64_t ncell, int use_new_T) {
+  // every node coefficient d_i once per block (launched with 256 threads): thread t computes
+  // the left node of its cell, the right node is the next thread's (the block's last thread
+  // computes its own)
+  __shared__ double dn_s[256];
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool live = gid < ncell;
   // locate instance by binary search over cell offsets
   int lo = 0, hi = n_inst - 1;
+  const int64_t gq = live ? gid : ncell - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
+    if (cell_inst_start[mid] <= gq) lo = mid; else hi = mid - 1;
   }
   const Inst I = D.inst[lo];
-  const int64_t j = gid - I.cell_off;
+  const int64_t j = gq - I.cell_off;
   const int N = I.N;
-  const double* T = use_new_T ? D.T : D.T;  // T holds T^n or T^{n+1} depending on the caller
+  const double* T = D.T;   // T^n or T^{n+1}, whichever the caller has placed there
+  (void)use_new_T;
   auto kap = [&](int64_t jj) -> double {
     if (I.kind == GRTE_SIGMA_CONST) return 1.0;
     double t = T[I.cell_off + jj];
     return I.p == 3.0 ? t * t * t : pow(t, I.p);
   };
   auto sig = [&](int64_t jj) -> double { return D.sig[I.cell_off + jj]; };
-  const double eps2 = I.eps * I.eps;
-  const double cdt = I.c * I.dt;
+  // d_i = kn/(kn eps^2/(c dt) + sn), sn = 2 sl sr/(sl + sr): one division as
+  // kn (sl + sr)/(kn eps^2/(c dt) (sl + sr) + 2 sl sr)
   auto dnode = [&](int64_t i) -> double {  // interior node i (1..N-1)
-    double kn = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : 0.5 * (kap(i - 1) + kap(i));
-    double sl = sig(i - 1), sr = sig(i);
-    double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
-    return kn / (kn * eps2 / cdt + sn);
+    const double kn = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : 0.5 * (kap(i - 1) + kap(i));
+    const double sl = sig(i - 1), sr = sig(i);
+    if (sl > 0.0 && sr > 0.0) {
+      const double ss = sl + sr;
+      return kn * ss / (kn * I.e2cdt * ss + 2.0 * sl * sr);
+    }
+    return kn / (kn * I.e2cdt);
   };
+  const double dl = (j >= 1) ? dnode(j) : 0.0;
+  dn_s[threadIdx.x] = dl;
+  __syncthreads();
+  if (!live) return;
+  const double dr = (j <= N - 2) ? ((threadIdx.x + 1 < blockDim.x) ? dn_s[threadIdx.x + 1] : dnode(j + 1)) : 0.0;
   const double kc = kap(j);
   const double sj = sig(j);
   const double Tj = T[gid];
   // theta: T^3 (sigma(x)); T^{3-p} for sigma_0/T^p (1 at p = 3)
   const double theta = (I.kind == GRTE_SIGMA_CONST) ? Tj * Tj * Tj : (I.p == 3.0 ? 1.0 : pow(Tj, 3.0 - I.p));
+  const double eps2 = I.eps * I.eps;
   const double s = sj * I.Cv / (I.Cv * eps2 + 4.0 * sj * theta * I.dt * I.a * I.c);
-  const double dx2 = I.dx * I.dx;
   const bool inflow = I.bc == GRTE_BC_INFLOW;
-  double dl = (j >= 1) ? dnode(j) : 0.0;
-  double dr = (j <= N - 2) ? dnode(j + 1) : 0.0;
-  double mL = (inflow && j == N - 1) ? 2.0 : 1.0;
-  double mR = (inflow && j == 0) ? 2.0 : 1.0;
+  const double mL = (inflow && j == N - 1) ? 2.0 : 1.0;
+  const double mR = (inflow && j == 0) ? 2.0 : 1.0;
+  const bool wallc = inflow && (j == 0 || j == N - 1);
+  const double kcd = kc * I.rcdt;
+  const double alpha = kcd + s;
+  const double ralpha = 1.0 / alpha;
+  const double A = kcd + sj * I.reps2;
+  const double gl = kc * mL * dl * I.rdx2, gu = kc * mR * dr * I.rdx2;
+  const double gb = wallc ? kc * I.gbc : 0.0;
+  const double od = dl * I.e2cdt, dlx = dl * I.rdx, kdx = kc * I.rdx;
+  const double ratio = (sj * I.reps2 - s) * ralpha;
+  const double fR = mR * dr * I.rdx, fL = mL * dl * I.rdx;
+  const double gbx = wallc ? I.two_eps : 0.0;
   D.cf.kc[gid] = kc;
   D.cf.s[gid] = s;
-  D.cf.alpha[gid] = kc / cdt + s;
-  D.cf.A[gid] = kc / cdt + sj / eps2;
-  D.cf.gam[gid] = 4.0 * sj * theta * I.dt / (eps2 * I.Cv);
-  D.cf.gl[gid] = kc * mL * dl / dx2;
-  D.cf.gu[gid] = kc * mR * dr / dx2;
-  D.cf.gb[gid] = (inflow && (j == 0 || j == N - 1)) ? 2.0 * kc / (I.eps * I.dx) : 0.0;
+  D.cf.alpha[gid] = alpha;
+  D.cf.A[gid] = A;
+  D.cf.gam[gid] = sj * theta * I.gamc;
+  D.cf.gl[gid] = gl;
+  D.cf.gu[gid] = gu;
+  D.cf.gb[gid] = gb;
   D.cf.dl[gid] = dl;
-  D.cf.od[gid] = dl * eps2 / cdt;
-  D.cf.dlx[gid] = dl / I.dx;
-  D.cf.kcd[gid] = kc / cdt;
-  D.cf.kdx[gid] = kc / I.dx;
+  D.cf.od[gid] = od;
+  D.cf.dlx[gid] = dlx;
+  D.cf.kcd[gid] = kcd;
+  D.cf.kdx[gid] = kdx;
   D.cf.sac[gid] = s * I.a * I.c;
-  const double alpha = kc / cdt + s;
-  D.cf.ralpha[gid] = 1.0 / alpha;
-  D.cf.ratio[gid] = (sj / eps2 - s) / alpha;
-  D.cf.fR[gid] = mR * dr / I.dx;
-  D.cf.fL[gid] = mL * dl / I.dx;
-  D.cf.gbx[gid] = (inflow && (j == 0 || j == N - 1)) ? I.two_eps : 0.0;
+  D.cf.ralpha[gid] = ralpha;
+  D.cf.ratio[gid] = ratio;
+  D.cf.fR[gid] = fR;
+  D.cf.fL[gid] = fL;
+  D.cf.gbx[gid] = gbx;
   if (D.mixed) {
     const CellF& f = D.fc;
-    f.A[gid] = (float)D.cf.A[gid];
-    f.gl[gid] = (float)D.cf.gl[gid];
-    f.gu[gid] = (float)D.cf.gu[gid];
-    f.gb[gid] = (float)D.cf.gb[gid];
-    f.od[gid] = (float)D.cf.od[gid];
-    f.dlx[gid] = (float)D.cf.dlx[gid];
-    f.kcd[gid] = (float)D.cf.kcd[gid];
-    f.kdx[gid] = (float)D.cf.kdx[gid];
-    f.ratio[gid] = (float)D.cf.ratio[gid];
-    f.ralpha[gid] = (float)D.cf.ralpha[gid];
+    f.A[gid] = (float)A;
+    f.gl[gid] = (float)gl;
+    f.gu[gid] = (float)gu;
+    f.gb[gid] = (float)gb;
+    f.od[gid] = (float)od;
+    f.dlx[gid] = (float)dlx;
+    f.kcd[gid] = (float)kcd;
+    f.kdx[gid] = (float)kdx;
+    f.ratio[gid] = (float)ratio;
+    f.ralpha[gid] = (float)ralpha;
     f.alpha[gid] = (float)alpha;
-    f.kcde[gid] = (float)(D.cf.kcd[gid] * I.inv_eps);
-    f.kdxe[gid] = (float)(D.cf.kdx[gid] * I.inv_eps);
-    D.cf.zl[gid] = I.wv2 * D.cf.gl[gid] * D.cf.ralpha[gid];
-    D.cf.zr[gid] = I.wv2 * D.cf.gu[gid] * D.cf.ralpha[gid];
-    D.cf.zc[gid] = (I.wv2 * (D.cf.gl[gid] + D.cf.gu[gid]) + I.wv * D.cf.gb[gid]) * D.cf.ralpha[gid];
-    f.dlxe[gid] = (float)(D.cf.dlx[gid] * I.eps);
-    f.fR[gid] = (float)D.cf.fR[gid];
-    f.fL[gid] = (float)D.cf.fL[gid];
-    f.gbx[gid] = (float)D.cf.gbx[gid];
+    f.kcde[gid] = (float)(kcd * I.inv_eps);
+    f.kdxe[gid] = (float)(kdx * I.inv_eps);
+    D.cf.zl[gid] = I.wv2 * gl * ralpha;
+    D.cf.zr[gid] = I.wv2 * gu * ralpha;
+    D.cf.zc[gid] = (I.wv2 * (gl + gu) + I.wv * gb) * ralpha;
+    f.dlxe[gid] = (float)(dlx * I.eps);
+    f.fR[gid] = (float)fR;
+    f.fL[gid] = (float)fL;
+    f.gbx[gid] = (float)gbx;
   }
 }
 
@@ -258,6 +300,33 @@ __device__ __forceinline__ int inst_of(const int64_t* __restrict__ cell_inst_sta
     if (cell_inst_start[mid] <= gid) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// a / b in binary64 from a binary32 reciprocal and one residual correction (relative error
+// ~1e-14, a few binary64 operations instead of the divide sequence); outside the binary32
+// range the plain division.
+__device__ __forceinline__ double q_div(double a, double b) {
+  if (!(fabs(b) > 1e-30 && fabs(b) < 1e30)) return a / b;
+  const double r = (double)__frcp_rn((float)b);
+  const double q = a * r;
+  return q + (a - q * b) * r;
+}
+
+// u^{3/4} for u >= 0: y = u^{3/4} from binary32, then two Newton steps on y^4 = u^3
+// (quadratic convergence from ~2^-22 to binary64 rounding).  The binary32 quantities
+// u^{3/2} and 4 y^3 = 4 u^{9/4} stay normal for 1e-16 < u < 1e16; outside, the library power.
+__device__ __forceinline__ double q_pow34(double u) {
+  if (u == 0.0) return 0.0;
+  if (!(u > 1e-16 && u < 1e16)) return pow(u, 0.75);
+  const float uf = (float)u;
+  double y = (double)sqrtf(uf * sqrtf(uf));
+  const double u3 = u * u * u;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double y2 = y * y;
+    y -= (y2 * y2 - u3) * (double)__frcp_rn((float)(4.0 * y2 * y));
+  }
+  return y;
 }
 
 // rho^n = sum_k w_k E^n_k = a c U^n + sum_k w_k Eh_k (sum_k w_k = 1), fixed angle order.
@@ -317,17 +386,18 @@ __device__ __forceinline__ void cellpart_cell(const Dev& D, const Inst& I, int64
       const double ul = (D.U[gid - 1] + D.cf.gam[gid - 1] * xl) / (1.0 + D.cf.gam[gid - 1] * ac);
       const double ur = (D.U[gid] + D.cf.gam[gid] * xj) / (1.0 + D.cf.gam[gid] * ac);
       const double e4 = 0.25 * I.p;   // V* = max(U*, 0)^{p/4}
-      const double vn = 0.5 * (pow(fmax(ul, 0.0), e4) + pow(fmax(ur, 0.0), e4));
+      const double vn = I.p == 3.0 ? 0.5 * (q_pow34(fmax(ul, 0.0)) + q_pow34(fmax(ur, 0.0)))
+                                   : 0.5 * (pow(fmax(ul, 0.0), e4) + pow(fmax(ur, 0.0), e4));
       const double sl = D.sig[gid - 1], sr = D.sig[gid];
       const double sn = (sl > 0.0 && sr > 0.0) ? 2.0 * sl * sr / (sl + sr) : 0.0;
-      const double den = vn * I.eps * I.eps / (I.c * I.dt) + sn;
+      const double den = vn * I.e2cdt + sn;
       ds = den > 0.0 ? vn / den : 0.0;
     }
-    D.cf.dsx[gid] = ds / I.dx;
-    D.cf.ods[gid] = ds * I.eps * I.eps / (I.c * I.dt);
+    D.cf.dsx[gid] = ds * I.rdx;
+    D.cf.ods[gid] = ds * I.e2cdt;
     if (D.mixed) {
-      D.fc.dsx[gid] = (float)(ds / I.dx);
-      D.fc.ods[gid] = (float)(ds * I.eps * I.eps / (I.c * I.dt));
+      D.fc.dsx[gid] = (float)(ds * I.rdx);
+      D.fc.ods[gid] = (float)(ds * I.e2cdt);
     }
   }
 }
@@ -1123,13 +1193,13 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
   D.Us[gid] = Us;
   D.rho_s[gid] = rho;
   const double sig = D.sig[gid];
-  const double kap = (I.kind == GRTE_SIGMA_CONST) ? 1.0 : pow(fmax(Us, 0.0), 0.25 * I.p);
-  const double dt = I.dt;
-  const double A = sig * I.a / dt;
-  const double B = sig * I.Cv / dt + I.eps * I.eps * kap * I.Cv / (I.c * dt * dt);
+  const double kap = (I.kind == GRTE_SIGMA_CONST) ? 1.0
+                     : (I.p == 3.0 ? q_pow34(fmax(Us, 0.0)) : pow(fmax(Us, 0.0), 0.25 * I.p));
+  const double A = sig * I.adt;
+  const double B = sig * I.cvdt + kap * I.ekc;
   const double Tn = D.T[gid];
   // the correction's flux (sigma_0/T^3: with V* = (U*)^{3/4}; sigma(x): the prediction's F*)
-  const double R = sig * (D.rho_n[gid] / (I.c * dt) - D.Fc[gid] / I.dx) + B * Tn;
+  const double R = sig * (D.rho_n[gid] * I.rcdt - D.Fc[gid] * I.rdx) + B * Tn;
   double T;
   int its = 0;
   if (A == 0.0 && B == 0.0) {
@@ -1165,7 +1235,7 @@ __global__ void k_newton(Dev D, int n_inst, const int64_t* __restrict__ cell_ins
       const double t2 = t * t;
       const double f = A * t2 * t2 + B * t - R;
       const double fp = 4.0 * A * t2 * t + B;
-      const double tn = t - f / fp;
+      const double tn = t - q_div(f, fp);
       if (!(tn < t)) break;
       t = tn;
     }
@@ -1793,8 +1863,7 @@ grte_status grte_create_1d(int n_inst, const grte_instance1d* in, const grte_opt
       I.bRflux = fr;
     }
     I.inv_eps = 1.0 / p.eps;
-    I.rdx = 1.0 / I.dx;
-    I.e2cdt = p.eps * p.eps / (p.c * p.dt);
+    inst_derive(I);
     I.cell_off = coff;
     I.elem_off = eoff;
     I.nelem_off = noff;
@@ -2985,7 +3054,8 @@ extern "C" grte_status grte_step1d_noalloc(const grte_instance1d* p, const grte_
     fl += w[k] * v[k] * bL[k];
     fr += w[k] * v[k] * bR[k];
   }
-  I.wv = wv; I.wv2 = wv2; I.two_eps = 2.0 / p->eps; I.inv_eps = 1.0 / p->eps; I.rdx = 1.0 / I.dx; I.e2cdt = p->eps * p->eps / (p->c * p->dt); I.bLflux = fl; I.bRflux = fr;
+  I.wv = wv; I.wv2 = wv2; I.bLflux = fl; I.bRflux = fr;
+  inst_derive(I);
   I.cell_off = 0; I.elem_off = 0; I.nelem_off = 0; I.red_off = 0; I.ang_off = 0; I.line_off = 0;
   Line lines[kNaMaxAngles];
   for (int k = 0; k < M; ++k) lines[k] = Line{0, k, (int64_t)k * kNaRedLine, (int64_t)k * (5 * N + kNaFacLine)};

@@ -148,28 +148,34 @@ def test_equilibrium_preserved_on_gpu(G):
 def test_marshak_config_128_cells_full_run(G, t_end):
     """1D slab, 128 cells, 16 directions, sigma = 1/T^3, eps = 1e-3, T_in = 1e-2, left
     inflow 1, right vacuum, dt = 0.5 dx, run to t = 0.5 (128 steps, the configuration)
-    and on to t = 1 (256 steps), FP64."""
+    and on to t = 1 (256 steps), FP64.  The prediction solve's stopping test bounds each
+    step's deviation from the oracle's direct solve: at the default rtol 1e-13 the front
+    cell drifts ~1e-12 per step (1.4e-10 in I+ after 128 steps); at rtol 1e-15 the whole
+    run stays within 1e-12 in T (measured 7.9e-13 at t = 0.5)."""
     inst = wl.marshak_1d(t_end=t_end)
     v, w = gauss_legendre_half(inst.n_dir)
     P = og.Problem(N=inst.nx, v=v, w=w, sig=inst.sigma, eps=inst.eps, dt=inst.dt, kind="t3",
                    bL=np.ones(v.size), bR=np.zeros(v.size))
     spec = dict(nx=inst.nx, n_angle=v.size, v=v, w=w, sigma=inst.sigma, kind=1, bc=0,
                 bL=P.bL, bR=P.bR, dt=inst.dt, eps=inst.eps)
-    h = G.Grte([spec])
+    h = G.Grte([spec], krylov_rtol=1e-15)
     h.set_state(0, inst.T0)
     h.step(inst.steps)
     Tg = h.T(0, allow=(5,))
     ipg, ing = h.I(0, allow=(5,))
     S = og.run(P, og.equilibrium_state(P, inst.T0), inst.steps)
     ip, im = og.intensity(P, S)
-    # accumulated over the steps: relative 1e-12 per step
-    check(Tg, S.T, np.full(P.N, 1e-12 * inst.steps), "T")
+    runs = inst.steps / 128.0   # the configuration's run (t = 0.5) is 128 steps
+    eT = np.max(np.abs(Tg - S.T) / np.abs(S.T))
+    print("C1 %d steps: T max rel err %.3e" % (inst.steps, eT))
+    check(Tg, S.T, np.full(P.N, 1e-12 * runs), "T")
     # I(+-v) = E +- eps O: rounding is relative to |E| + |eps O| of the cell (I(-v) of the
-    # cold far field is a cancellation down to ~1e-24)
+    # cold far field is a cancellation down to ~1e-24); the front cell's intensity moves
+    # ~2.5x its temperature
     Oc = 0.5 * (S.O[:-1] + S.O[1:])
     scale = np.abs(S.E) + np.abs(P.eps * Oc)
-    check(ipg, ip, 1e-12 * inst.steps, "I+", scale)
-    check(ing, im, 1e-12 * inst.steps, "I-", scale)
+    check(ipg, ip, 4e-12 * runs, "I+", scale)
+    check(ing, im, 4e-12 * runs, "I-", scale)
     h.close()
 
 
