@@ -390,8 +390,9 @@ def main():
                     help="2D: GMRES restart cycles per solve (checker2d: 30, lognormal2d: 60)")
     ap.add_argument("--compare-starts", action="store_true",
                     help="2D: also run the other Newton starts from the same state and report their counts")
-    ap.add_argument("--prec2d", default="block", choices=["block", "multigrid"],
-                    help="2D prediction preconditioner: per-cell block + multigrid on rho, or per-cell block only")
+    ap.add_argument("--prec2d", default="block", choices=["block", "multigrid", "corr-mg", "multigrid+corr-mg"],
+                    help="2D preconditioners: prediction per-cell block (+ multigrid on rho: 'multigrid'); "
+                         "correction per-cell diagonal (+ per-pair multigrid: 'corr-mg')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -760,7 +761,8 @@ def run_2d(args):
     net, training = None, None
     if args.newton_start == "learned" or args.compare_starts:
         net, training = train_guess_2d(G, stream)
-    prec = G.PREC2D_MULTIGRID if args.prec2d == "multigrid" else G.PREC2D_BLOCK
+    prec = ((G.PREC2D_MULTIGRID if args.prec2d.startswith("multigrid") else G.PREC2D_BLOCK) |
+            (G.PREC2D_CORR_MG if args.prec2d.endswith("corr-mg") else 0))
     precision = G.MIXED if args.precision == "mixed" else G.FP64
     allow = (5,)        # cells reaching R <= 0 at this dt (see the workload's readings)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

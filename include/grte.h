@@ -100,13 +100,18 @@ typedef struct {
                             launch (captured once; the Krylov loop runs under device-side
                             conditional nodes, no host round trip inside a step).  Steps
                             taken while per-kernel profiling is on run eagerly.  0: eager    */
-  int prec2d;            /* 2D prediction preconditioner: GRTE_PREC2D_BLOCK (default): the
-                            per-cell angular block (cells uncoupled); GRTE_PREC2D_MULTIGRID:
-                            first a solve preconditioned by block elimination of the (e, rho)
-                            system with the per-cell diagonal of each pair operator and one
-                            multigrid V-cycle on the cells' rho Schur complement (one scale
-                            for all cells), then the per-cell scaled solve with the block
-                            preconditioner.  Ignored by the 1D path                        */
+  int prec2d;            /* 2D preconditioners, a bit set.  Prediction: GRTE_PREC2D_BLOCK
+                            (0, default): the per-cell angular block (cells uncoupled);
+                            GRTE_PREC2D_MULTIGRID (bit 0): first a solve preconditioned by
+                            block elimination of the (e, rho) system with the per-cell
+                            diagonal of each pair operator and one multigrid V-cycle on the
+                            cells' rho Schur complement (one scale for all cells), then the
+                            per-cell scaled solve with the block preconditioner.  Correction
+                            substep 2: the per-cell diagonal (default), or with
+                            GRTE_PREC2D_CORR_MG (bit 1) one V-cycle per direction pair of a
+                            2x2-aggregation multigrid with zebra x/y line smoothers (binary32;
+                            about 23 floats per cell and pair on the finest level).  Ignored
+                            by the 1D path                                                 */
   int solver1d;          /* 1D prediction solve: GRTE_SOLVER_AUTO (default): in GRTE_MIXED, when
                             every instance has 64 <= nx <= 8192 and n_angle <= 32 and the
                             restart length is at most 11 (its Krylov basis is held in shared
@@ -270,7 +275,7 @@ grte_status grte_set_guess(grte_t h, grte_mlp_t m);
  * grte_set_guess), in the cells where the guess lies more than 10^0.05 - 1 (about 12%)
  * below BOUND (elsewhere BOUND is within the network's error of the root and is kept).
  * All three converge to the same root. */
-enum { GRTE_PREC2D_BLOCK = 0, GRTE_PREC2D_MULTIGRID = 1 };
+enum { GRTE_PREC2D_BLOCK = 0, GRTE_PREC2D_MULTIGRID = 1, GRTE_PREC2D_CORR_MG = 2 };
 enum { GRTE_START_BOUND = 0, GRTE_START_PREVIOUS = 1, GRTE_START_LEARNED = 2 };
 grte_status grte_set_newton_start(grte_t h, int mode);
 /* 1: record the features and the converged target of every cell at each step (the last

@@ -32,6 +32,7 @@ struct NvtxRange {
 };
 }  // namespace
 #include "mg2d.cuh"
+#include "mgpair2d.cuh"
 #include "mlp.cuh"
 
 namespace grte2 {
@@ -552,6 +553,55 @@ __global__ void k2_probe_out(D2 D, int cx, int cy, const double* __restrict__ tk
   }
 }
 
+// Per-pair multigrid of the correction (mgpair2d.cuh): probe input e_k = 1 on the cells of
+// colour (cx, cy) for every pair
+__global__ void k2_mp_probe_in(D2 D, int cx, int cy, double* __restrict__ e) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nc) return;
+  const int c = (int)(t % g.nc), p = c % g.Nx, q = c / g.Nx;
+  e[t] = (axis_colour(p, g.Nx, g.bcx == GRTE_BC_PERIODIC) == cx && axis_colour(q, g.Ny, g.bcy == GRTE_BC_PERIODIC) == cy)
+             ? 1.0 : 0.0;
+}
+
+// probe output: (A + G_k) e at cell c is the coupling of c to the one cell of colour
+// (cx, cy) in its 3x3 neighbourhood, stored at that position of pair k's stencil
+// (positions tried in the order 0, +1, -1 per axis, as for the prediction's stencil)
+__global__ void k2_mp_probe_out(D2 D, int cx, int cy, const double* __restrict__ y, float* __restrict__ cr) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const G2& g = D.g;
+  if (t >= (int64_t)g.K * g.nc) return;
+  const int k = (int)(t / g.nc);
+  const int64_t c = t - (int64_t)k * g.nc;
+  const int px = g.bcx == GRTE_BC_PERIODIC, py = g.bcy == GRTE_BC_PERIODIC;
+  const int p = (int)(c % g.Nx), q = (int)(c / g.Nx);
+  const int order[3] = {0, 1, -1};
+  for (int a = 0; a < 3; ++a) {
+    const int dy = order[a], qn = mg::nbr(q, dy, g.Ny, py);
+    if (qn < 0 || axis_colour(qn, g.Ny, py) != cy) continue;
+    for (int b = 0; b < 3; ++b) {
+      const int dx = order[b], pn = mg::nbr(p, dx, g.Nx, px);
+      if (pn < 0 || axis_colour(pn, g.Nx, px) != cx) continue;
+      cr[((int64_t)k * 9 + (dy + 1) * 3 + dx + 1) * g.nc + c] = (float)y[t];
+      return;
+    }
+  }
+}
+
+// the finest level's right side from a residual r (any type), and z = w x (the cell's
+// Krylov scale)
+template <typename S>
+__global__ void k2_mp_in(int64_t n, const S* __restrict__ r, float* __restrict__ b) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)r[t];
+}
+template <typename S>
+__global__ void k2_mp_out(D2 D, CV<S> cv, const float* __restrict__ x, S* __restrict__ z) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)D.g.K * D.g.nc) return;
+  z[t] = cv.wsc[t % D.g.nc] * (S)x[t];
+}
+
 // et_k = D_k r_k
 __global__ void k2_pc_et(D2 D, const double* __restrict__ r, double* __restrict__ et) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1057,6 +1107,11 @@ struct grte2d_ctx {
   float *V32 = nullptr, *Kr32 = nullptr, *Vv32 = nullptr, *tk32 = nullptr;
   std::vector<mg::Level> mgl;        // multigrid levels of the Schur preconditioner (empty: per-cell block only)
   double *mg_M = nullptr, *mg_inv = nullptr;   // coarsest level: dense scratch and inverse
+  // correction substep 2: per-pair multigrid (GRTE_PREC2D_CORR_MG), its V-cycle as one graph
+  std::vector<mp::PLevel> mpl;
+  cudaGraphExec_t mp_graph = nullptr;
+  double* mp_probe = nullptr;   // [k][cell] probe input
+  int mp_nodes = 0;             // kernel launches of one V-cycle graph
   double *dmu = nullptr, *deta = nullptr, *dw = nullptr, *dsig = nullptr;
 };
 
@@ -1133,7 +1188,105 @@ static void apply_M32(grte2d_t h, bool pred, const float* xin, float* y) {
   }
 }
 
+// One V-cycle of the per-pair multigrid on level l (right side in mpl[l].b, iterate in
+// mpl[l].x, zero on entry); returns the kernels launched.  Issued once under stream capture.
+static int mp_vcycle(grte2d_t h, size_t l) {
+  cudaStream_t st = h->stream;
+  const mp::PLevel& L = h->mpl[l];
+  const bool coarsest = l + 1 == h->mpl.size();
+  int nl = 0;
+  const dim3 tb(32, 8);
+  const dim3 trc((L.nx + 31) / 32, (L.ny + 31) / 32, L.K), tcr((L.ny + 31) / 32, (L.nx + 31) / 32, L.K);
+  mp::mp_transpose<<<trc, tb, 0, st>>>(L.b, L.bt, L.nx, L.ny, L.K);
+  ++nl;
+  auto lines = [&](const float* coef, float* x, const float* b, int nf, int ns, int perf, int pers) {
+    for (int par = 0; par < 2; ++par) {
+      const int64_t nt = (int64_t)L.K * ((nf - par + 1) / 2);
+      if (nt == 0) continue;
+      mp::mp_line<<<(unsigned)((nt + mp::kThreadsMp - 1) / mp::kThreadsMp), mp::kThreadsMp, 0, st>>>(
+          coef, x, b, L.cp, nf, ns, L.K, perf, pers, par);
+      ++nl;
+    }
+  };
+  auto sweep_y = [&]() { lines(L.cr, L.x, L.b, L.nx, L.ny, L.perx, L.pery); };
+  auto sweep_x = [&]() {
+    mp::mp_transpose<<<trc, tb, 0, st>>>(L.x, L.xt, L.nx, L.ny, L.K);
+    lines(L.ct, L.xt, L.bt, L.ny, L.nx, L.pery, L.perx);
+    mp::mp_transpose<<<tcr, tb, 0, st>>>(L.xt, L.x, L.ny, L.nx, L.K);
+    nl += 2;
+  };
+  for (int sw = 0; sw < (coarsest ? mp::kCoarseSweeps : 1); ++sw) {
+    sweep_y();
+    sweep_x();
+  }
+  if (!coarsest) {
+    const mp::PLevel& C = h->mpl[l + 1];
+    mp::mp_restrict<<<grid_of((int64_t)C.K * C.n), kThreads, 0, st>>>(L, C);
+    ++nl;
+    nl += mp_vcycle(h, l + 1);
+    mp::mp_prolong<<<grid_of((int64_t)L.K * L.n), kThreads, 0, st>>>(L, C);
+    ++nl;
+    sweep_x();
+    sweep_y();
+  }
+  return nl;
+}
+
+// Per solve: the finest level's stencils by probing the correction operator, the Galerkin
+// levels and the transposed copies; the V-cycle graph is captured on first use (its
+// buffers are fixed for the handle's lifetime).
+static grte_status mp_setup(grte2d_t h) {
+  D2& D = h->D;
+  const G2& g = D.g;
+  cudaStream_t st = h->stream;
+  const int64_t K = g.K, nc = g.nc;
+  mp::PLevel& L0 = h->mpl[0];
+  const int px = g.bcx == GRTE_BC_PERIODIC, py = g.bcy == GRTE_BC_PERIODIC;
+  const int ncx = axis_ncolours(g.Nx, px), ncy = axis_ncolours(g.Ny, py);
+  CK2(cudaMemsetAsync(L0.cr, 0, sizeof(float) * 9 * K * nc, st));
+  for (int cy = 0; cy < ncy; ++cy)
+    for (int cx = 0; cx < ncx; ++cx) {
+      tl_launches++, k2_mp_probe_in<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->mp_probe);
+      tl_launches++, k2_vertex<double, false><<<grid_of(K * g.nv), kThreads, 0, st>>>(D, h->cv, UField{h->mp_probe, nc, nullptr}, h->V);
+      tl_launches++, k2_cell<double, C_MV_CORR, false><<<grid_of(K * nc), kThreads, 0, st>>>(
+          D, h->cv, h->V, UField{h->mp_probe, nc, nullptr}, h->mp_probe, h->Kr, nullptr, h->tk);
+      tl_launches++, k2_mp_probe_out<<<grid_of(K * nc), kThreads, 0, st>>>(D, cx, cy, h->Kr, L0.cr);
+    }
+  for (size_t l = 0; l < h->mpl.size(); ++l) {
+    const mp::PLevel& L = h->mpl[l];
+    if (l > 0) tl_launches++, mp::mp_galerkin<<<grid_of((int64_t)L.K * L.n), kThreads, 0, st>>>(h->mpl[l - 1], L);
+    tl_launches++, mp::mp_stencil_t<<<grid_of((int64_t)L.K * L.n), kThreads, 0, st>>>(L);
+  }
+  CK2(cudaGetLastError());
+  if (!h->mp_graph) {
+    cudaGraph_t gr = nullptr;
+    CK2(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(L0.x, 0, sizeof(float) * K * nc, st);
+    h->mp_nodes = mp_vcycle(h, 0);
+    CK2(cudaStreamEndCapture(st, &gr));
+    const cudaError_t e = cudaGraphInstantiate(&h->mp_graph, gr, 0);
+    cudaGraphDestroy(gr);
+    CK2(e);
+  }
+  return GRTE_OK;
+}
+
+// z = w V-cycle(r) per pair (correction, GRTE_PREC2D_CORR_MG)
+template <typename S>
+static void mp_apply(grte2d_t h, const CV<S>& cv, const S* r, S* z) {
+  const int64_t n = h->D.g.K * h->D.g.nc;
+  cudaStream_t st = h->stream;
+  tl_launches++, k2_mp_in<S><<<grid_of(n), kThreads, 0, st>>>(n, r, h->mpl[0].b);
+  cudaGraphLaunch(h->mp_graph, st);
+  tl_launches += h->mp_nodes;
+  tl_launches++, k2_mp_out<S><<<grid_of(n), kThreads, 0, st>>>(h->D, cv, h->mpl[0].x, z);
+}
+
 static void apply_P32(grte2d_t h, bool pred, const float* r, float* z) {
+  if (!pred && h->mp_graph) {
+    mp_apply<float>(h, h->cv32, r, z);
+    return;
+  }
   if (pred) tl_launches++, k2_prec<float, true><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
   else tl_launches++, k2_prec<float, false><<<grid_of(h->D.g.nc), kThreads, 0, h->stream>>>(h->D, h->cv32, r, z);
 }
@@ -1220,7 +1373,8 @@ static void apply_P(grte2d_t h, bool pred, bool use_mg, const double* r, double*
   D2& D = h->D;
   cudaStream_t st = h->stream;
   if (!pred) {
-    tl_launches++, k2_prec<double, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
+    if (h->mp_graph) mp_apply<double>(h, h->cv, r, z);
+    else tl_launches++, k2_prec<double, false><<<grid_of(D.g.nc), kThreads, 0, st>>>(D, h->cv, r, z);
     return;
   }
   if (!use_mg) {
@@ -1473,6 +1627,7 @@ static grte_status step2(grte2d_t h) {
   tl_launches++, k2_gdiag<<<gc, kThreads, 0, st>>>(D, h->cv);
   mirror_coefficients(h);
   CK2(cudaGetLastError());
+  if (!h->mpl.empty() && (s = mp_setup(h)) != GRTE_OK) return s;
   its = 0;
   s = gmres2(h, false, false, K * nc, its);
   if (s != GRTE_OK) return s;
@@ -1491,6 +1646,7 @@ extern "C" {
 void grte2d_destroy(grte2d_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->mp_graph) cudaGraphExecDestroy(h->mp_graph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -1583,7 +1739,27 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
             alloc2(h, &h->coef, kMaxRestart2 + 1) && alloc2(h, &h->cscale, nc) &&
             alloc2(h, &h->hcol, kMaxRestart2 + 2) && alloc2(h, &h->tk, K * nc);
   if (!ok) return fail2(h, GRTE_ENOMEM, "cudaMalloc failed");
-  if (h->opt.prec2d == GRTE_PREC2D_MULTIGRID) {
+  if (h->opt.prec2d & ~(GRTE_PREC2D_MULTIGRID | GRTE_PREC2D_CORR_MG))
+    return fail2(h, GRTE_EINVAL, "prec2d: a set of GRTE_PREC2D_MULTIGRID and GRTE_PREC2D_CORR_MG");
+  if (h->opt.prec2d & GRTE_PREC2D_CORR_MG) {
+    // levels of 2x2 aggregates down to lines of <= 2 cells in both axes
+    mp::PLevel L{};
+    L.nx = g.Nx; L.ny = g.Ny; L.K = (int)K;
+    L.perx = g.bcx == GRTE_BC_PERIODIC; L.pery = g.bcy == GRTE_BC_PERIODIC;
+    for (;;) {
+      L.n = (int64_t)L.nx * L.ny;
+      const int64_t kn = K * L.n;
+      if (!alloc2(h, &L.cr, 9 * kn) || !alloc2(h, &L.ct, 9 * kn) || !alloc2(h, &L.x, kn) || !alloc2(h, &L.xt, kn) ||
+          !alloc2(h, &L.b, kn) || !alloc2(h, &L.bt, kn) || !alloc2(h, &L.cp, kn))
+        return fail2(h, GRTE_ENOMEM, "cudaMalloc pair multigrid");
+      h->mpl.push_back(L);
+      if (L.nx <= 2 && L.ny <= 2) break;
+      L.nx = (L.nx + 1) / 2;
+      L.ny = (L.ny + 1) / 2;
+    }
+    if (!alloc2(h, &h->mp_probe, K * nc)) return fail2(h, GRTE_ENOMEM, "cudaMalloc pair multigrid");
+  }
+  if (h->opt.prec2d & GRTE_PREC2D_MULTIGRID) {
     // level 0: the cells (one unknown each); then 2x2 aggregation with one unknown per
     // colour class, until the level has at most mg::kDenseMax unknowns
     mg::Level L{};
@@ -1603,8 +1779,6 @@ grte_status grte2d_create(const grte_instance2d* p, const grte_options* opt, grt
     }
     if (!alloc2(h, &h->mg_M, mg::kDenseMax * mg::kDenseMax) || !alloc2(h, &h->mg_inv, mg::kDenseMax * mg::kDenseMax))
       return fail2(h, GRTE_ENOMEM, "cudaMalloc multigrid");
-  } else if (h->opt.prec2d != GRTE_PREC2D_BLOCK) {
-    return fail2(h, GRTE_EINVAL, "prec2d must be GRTE_PREC2D_MULTIGRID or GRTE_PREC2D_BLOCK");
   }
   D.mu = h->dmu; D.eta = h->deta; D.w = h->dw; D.sig = h->dsig;
   h->cv = CV<double>{D.mu, D.eta, D.w, D.kc, D.A, D.alpha, D.dv, D.gd, D.gdi, D.pdi, D.wsc, D.iwsc,

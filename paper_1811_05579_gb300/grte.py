@@ -102,7 +102,7 @@ EXPORTED = ["grte_default_options", "grte_create_1d", "grte_set_state", "grte_st
             "grte_diff_step", "grte_diff_sync", "grte_diff_get_T", "grte_diff_get_Ustar", "grte_diff_last_error",
             "grte_diff_destroy", "grte_mlp_forward_device"]
 START_BOUND, START_PREVIOUS, START_LEARNED = 0, 1, 2
-PREC2D_BLOCK, PREC2D_MULTIGRID = 0, 1
+PREC2D_BLOCK, PREC2D_MULTIGRID, PREC2D_CORR_MG = 0, 1, 2   # prec2d bits: prediction MG, correction MG
 MLP_NPARAMS = 8833
 _fp = ctypes.POINTER(ctypes.c_float)
 KERNELS = ["cell_coef", "rho", "pred_factor", "pred_hom", "pred_full", "gmres", "newton", "corr",
