@@ -47,6 +47,12 @@ GMRES_BYTES_PER_CELL = lambda M, es: M * es + 4 * 8
 # changed since (restart decision read before the CTAs' barriers); until the counters
 # are taken again the line reports traffic as null and gives this figure as context.
 GMRES_TRAFFIC_SLAB6_MIXED_EARLIER = 13.19e6
+# DRAM bytes per k_gmres launch on the 1D slab workload in FP64, the mean over six
+# consecutive launches of all modes (restart 18.4 MB, Arnoldi 3.8 and 3.7 MB, update 3.0
+# and 1.0 MB, one launch whose instances had all stopped 0.07 MB; ncu dram__bytes_read.sum
+# + dram__bytes_write.sum, profiles/ncu_gmres_fp64_slab6.md), taken with the kernel as it
+# stands
+GMRES_DRAM_BYTES_SLAB6_FP64 = 5.00e6
 # Per-cell bytes the fused prediction solve must move besides the state: the binary64
 # inputs it reads once (T^n, U^n, rho^n and the 16 coefficient arrays of the cell) and
 # the outputs rho* and F* (20 x 8 B).
@@ -154,9 +160,12 @@ def roofline_of(prof, runs, prec, hbm_peak, workload):
         earlier = GMRES_TRAFFIC_SLAB6_MIXED_EARLIER if (workload == "slab6" and prec == G.MIXED) else None
         roof = {"kernel": "k_gmres (all modes; Arnoldi step dominant)", "bound": "hbm", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)", "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "traffic": GMRES_DRAM_BYTES_SLAB6_FP64 if (workload == "slab6" and prec == G.FP64) else None,
+                "traffic_source": "ncu dram bytes, mean of six launches of all modes",
                 "traffic_before_last_kernel_change": earlier,
-                "avg_launch_us": avg_s * 1e6, "launches": dom_n, "bytes_per_cell": GMRES_BYTES_PER_CELL(M, es)}
+                "avg_launch_us": avg_s * 1e6, "launches": dom_n, "bytes_per_cell": GMRES_BYTES_PER_CELL(M, es),
+                "bytes_model": "achieved and frac from the byte model: M x %d B flux parts + 4 x 8 B per cell" % es}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s (fp64)", "frac": None, "traffic": None,
@@ -656,23 +665,32 @@ def main():
         dist.destroy_process_group()
 
 
+def dt_2d(n):
+    """Time step of the 2D workloads (their configurations give none): the paper's Table
+    stability3 (the Marshak wave under a hot wall) lowers the stable C = dt/dx from 0.5 at
+    dx = 1/25 to 0.03 at 1/400, about C = 12.5 dx; dt = min(0.5 dx, 12.5 dx^2).  At
+    dt = 0.5 dx the 2D runs (and the oracle: a 32^2 checkerboard reaches T = 4.8 under a
+    unit inflow within 5 steps) empty cells and overshoot."""
+    return min(0.5 / n, 12.5 / (n * n))
+
+
 def checker2d_inputs(n, blocks=8):
     """2D checkerboard slab: sigma_0 = 1 on the 'black' and 100 on the 'white' blocks of a
     blocks x blocks board (block (0, 0) black), times 1/T^3; T_in = 1e-2; eps = 1e-3;
-    inflow a c 1^4 on x = 0, vacuum on the other walls; dt = 0.5 dx; S8 (20 pairs)."""
+    inflow a c 1^4 on x = 0, vacuum on the other walls; dt = dt_2d(n); S8 (20 pairs)."""
     i = np.arange(n) // max(n // blocks, 1)
     sig = np.where(((i[None, :] + i[:, None]) % 2) == 0, 1.0, 100.0)
-    return sig, np.full(n * n, 1e-2), 0.5 / n, 1e-3
+    return sig, np.full(n * n, 1e-2), dt_2d(n), 1e-3
 
 
 def lognormal2d_inputs(n):
     """2D random-smooth slab: sigma_0 = exp(g), g an iid N(0, 1) field smoothed by a
     Gaussian of standard deviation 8 cells (wrapped, separable) and renormalised to unit
     variance, times 1/T^3; T_in = 1e-2; eps = 1e-4; inflow a c 1^4 on x = 0, vacuum on
-    the other walls; dt = 0.5 dx; S8 (20 pairs)."""
+    the other walls; dt = dt_2d(n); S8 (20 pairs)."""
     from paper_1811_05579_gb300 import workloads as wl
     sig = wl.lognormal_sigma_2d(n, seed=wl.BASE_SEED + 5, sd_cells=8.0)
-    return sig, np.full(n * n, 1e-2), 0.5 / n, 1e-4
+    return sig, np.full(n * n, 1e-2), dt_2d(n), 1e-4
 
 
 def inputs_2d(workload, n):
@@ -726,7 +744,7 @@ def train_guess_2d(G, stream):
     Xs, Ys = [], []
     t0 = time.perf_counter()
     for n, sig, eps, seed in runs:
-        h = G.Grte2D(n, n, sig, 0.5 / n, eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream)
+        h = G.Grte2D(n, n, sig, dt_2d(n), eps, kind=G.SIGMA_T3, b_x0=1.0, stream=stream.cuda_stream)
         h.set_state(1e-2 * (1.0 + 0.5 * wl.SplitMix64(seed).uniform(n * n)))
         h.set_sample_logging(True)
         for _ in range(25):
@@ -764,8 +782,8 @@ def run_2d(args):
     prec = ((G.PREC2D_MULTIGRID if args.prec2d.startswith("multigrid") else G.PREC2D_BLOCK) |
             (G.PREC2D_CORR_MG if args.prec2d.endswith("corr-mg") else 0))
     precision = G.MIXED if args.precision == "mixed" else G.FP64
-    # cells reaching R <= 0 at this dt, and solves that stop at their cycle limit once a
-    # state has become unstable at dt = 0.5 dx (both reported in statuses_seen)
+    # cells reaching R <= 0, and solves that stop at their cycle limit (both reported in
+    # statuses_seen)
     allow = (4, 5)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -860,7 +878,7 @@ def run_2d(args):
             "config": {"workload": workload_name_2d(args.workload, n), "n": n, "pairs": 20, "eps": eps,
                        "precision": args.precision,
                        "sigma0": [1, 100] if args.workload == "checker2d" else "exp(N(0,1) smoothed 8 cells)",
-                       "dt": "0.5 dx", "T_in": 1e-2, "prec2d": args.prec2d,
+                       "dt": "min(0.5 dx, 12.5 dx^2) = %.3g" % dt, "T_in": 1e-2, "prec2d": args.prec2d,
                        "newton_start": args.newton_start, "krylov_restart": args.krylov_restart,
                        "krylov_maxcycles": args.krylov_maxcycles,
                        "l2": "flushed between timed steps (flush not timed)", "parallelism": "single"},

@@ -11,8 +11,10 @@
   (the limit equation's maximum principle) by more than 1e-6 relative, and ends with a
   single local maximum (the data are a single bump).
 - marshak_dimensional(): the Marshak wave with units of Sec. 6.6 at the three time steps.
+- long_run(): the slab configuration's 10^4 steps in FP64 and mixed precision side by side.
 
-`python -m paper_1811_05579_gb300.studies` prints one JSON object with all three."""
+`python -m paper_1811_05579_gb300.studies` prints one JSON object with the first three
+(`--long-run` adds the fourth)."""
 import json
 import math
 import sys
@@ -121,11 +123,49 @@ def marshak_dimensional(nx=50, t_end_ns=0.02):
     return rows
 
 
+def long_run(steps=10000, chunk=1000):
+    """The slab configuration's full run (six 8192-cell, 64-direction runs, dt = 0.5 dx,
+    10^4 steps) in FP64 and in mixed precision side by side: per chunk of steps and per
+    run, the largest T of each precision and their largest relative difference.  At this
+    dt a run whose time step exceeds its stability limit (Tables stability1-3: the limit
+    shrinks with dx) grows without bound, and rounding differences between the two
+    precisions grow with it."""
+    runs = wl.slab_1d_runs(steps=1)
+    specs = [dict(nx=r.nx, n_angle=r.n_dir // 2, sigma=r.sigma, kind=r.kind, bc=r.bc,
+                  bL=np.full(r.n_dir // 2, r.bL), bR=np.full(r.n_dir // 2, r.bR), dt=r.dt, eps=r.eps,
+                  a=r.a, c=r.c, Cv=r.Cv) for r in runs]
+    hd = G.Grte(specs)
+    hm = G.Grte(specs, precision=G.MIXED)
+    for i, r in enumerate(runs):
+        hd.set_state(i, r.T0)
+        hm.set_state(i, r.T0)
+    rows = []
+    done = 0
+    while done < steps:
+        n = min(chunk, steps - done)
+        hd.step(n)
+        hm.step(n)
+        done += n
+        row = {"step": done, "runs": []}
+        for i, r in enumerate(runs):
+            Td, Tm = hd.T(i, allow=(4, 5)), hm.T(i, allow=(4, 5))
+            with np.errstate(all="ignore"):
+                d = float(np.max(np.abs(Tm - Td) / np.maximum(np.abs(Td), 1e-300)))
+            row["runs"].append({"sigma0": float(r.sigma[0]), "eps": r.eps, "T_max_fp64": float(np.max(Td)),
+                                "T_max_mixed": float(np.max(Tm)), "t_rel_diff": d})
+        rows.append(row)
+    hd.close()
+    hm.close()
+    return rows
+
+
 def main():
     res = {"convergence_sigma1": convergence(),
            "stability_sigma1": stability(G.SIGMA_CONST),
            "stability_sigma_T3": stability(G.SIGMA_T3),
            "marshak_dimensional": marshak_dimensional()}
+    if "--long-run" in sys.argv:
+        res["long_run_slab6"] = long_run()
     print(json.dumps(res))
     return 0
 
