@@ -17,7 +17,9 @@ def test_checkerboard_inputs():
     assert sig.shape == (64, 64) and T0.shape == (64 * 64,)
     assert set(np.unique(sig)) == {1.0, 100.0}
     assert sig[0, 0] == 1.0 and sig[0, 8] == 100.0 and sig[8, 8] == 1.0   # 8 x 8 board, block (0, 0) black
-    assert np.all(T0 == 1e-2) and dt == 0.5 / 64 and eps == 1e-3
+    # dt = min(0.5 dx, 12.5 dx^2), the trend of Table stability3 (C = 12.5 dx)
+    assert np.all(T0 == 1e-2) and dt == min(0.5 / 64, 12.5 / 64 ** 2) and eps == 1e-3
+    assert abs(bench.dt_2d(512) * 512 - 12.5 / 512) < 1e-15 and bench.dt_2d(16) == 0.5 / 16
     assert bench.workload_name_2d("checker2d", 64) == "2d_checkerboard_64x64_s8"
 
 
@@ -26,7 +28,7 @@ def test_random_smooth_inputs():
     g = np.log(sig)
     assert sig.shape == (96, 96) and np.all(sig > 0)
     assert abs(g.mean()) < 1e-12 and abs(g.std() - 1.0) < 1e-12
-    assert np.all(T0 == 1e-2) and dt == 0.5 / 96 and eps == 1e-4
+    assert np.all(T0 == 1e-2) and dt == min(0.5 / 96, 12.5 / 96 ** 2) and eps == 1e-4
     # seeded: the same field every time
     assert np.array_equal(sig, bench.inputs_2d("lognormal2d", 96)[0])
     assert bench.workload_name_2d("lognormal2d", 96) == "2d_lognormal_96x96_s8"
