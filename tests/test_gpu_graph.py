@@ -35,7 +35,8 @@ def test_graph_step_equals_eager_step(G, precision):
     prec = G.FP64 if precision == "fp64" else G.MIXED
     res = {}
     for use_graph in (False, True):
-        h = G.Grte(specs, precision=prec, use_graph=use_graph)
+        # one line-thread count for both (the autotuner times the candidates per handle)
+        h = G.Grte(specs, precision=prec, use_graph=use_graph, line_threads=256)
         for i, r in enumerate(insts):
             h.set_state(i, r.T0)
         its = []
@@ -59,7 +60,7 @@ def test_graph_rebuilt_after_newton_start_change(G):
     specs = _specs(insts)
     out = []
     for use_graph in (False, True):
-        h = G.Grte(specs, use_graph=use_graph)
+        h = G.Grte(specs, use_graph=use_graph, line_threads=256)
         h.set_state(0, insts[0].T0)
         h.step(3)
         h.set_newton_start(G.START_PREVIOUS)   # changes a value the captured kernels take
