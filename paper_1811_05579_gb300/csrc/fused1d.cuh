@@ -82,6 +82,9 @@ struct FSmem {
   float wgt[kFS];                                       // stopping-test weights
   double zv[kFS];                                       // preconditioner input (slice)
   double sc[4];                                         // scalars computed once (thread 0)
+  long long xmw[kFW];                                   // per-warp max |x| (bit patterns)
+  double xmx[2];                                        // the slice's max |x|, per restart parity
+  double xmall;                                         // the cluster's max |x|
   double wall[2][32];                                   // wall-row right-hand sides (double)
   double red[kFW][kMaxRestart + 2];                     // per-warp partial sums
   double part[2][kMaxRestart + 2];                      // cluster partials (double-buffered)
@@ -1279,8 +1282,23 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
   int cycles = 0, its = 0, stag = 0;
   double beta_prev = 0.0;
   bool first = true;
+  int xpar = 0;
   for (;;) {
     // ---- restart: true residual at x, preconditioned, stopping test --------------------
+    // the slice's max |x| (x >= 0 bit patterns as integers: order preserving), published
+    // before the pass's opening cluster barrier, which also makes it visible to the others
+    {
+      long long mx = real ? __double_as_longlong(fabs(x[j])) : 0;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((t & 31) == 0) sm.xmw[t >> 5] = mx;
+      __syncthreads();
+      if (t == 0) {
+        long long a = sm.xmw[0];
+        for (int w2 = 1; w2 < kFW; ++w2) a = max(a, sm.xmw[w2]);
+        sm.xmx[xpar] = __longlong_as_double(a);
+      }
+    }
     f_pass<true>(sm, cl, D, I, G, x, par, first);
     if (real) {
       const int64_t g = co + j;
@@ -1292,9 +1310,17 @@ __global__ void __launch_bounds__(kFT, 1) k_pred_fused(Dev D, const int* __restr
     } else {
       zv[t] = 0.0;
     }
-    f_reduce<0, true>(sm, cl, par, 0, [](int, int) { return 0.0; },
-                      [&](int c) { return G.c0 + c < N ? fabs(x[G.c0 + c]) : 0.0; });
-    const double xmax = sm.sums[0];
+    // the cluster's max |x|: every slice's value, published before the pass's barrier
+    if (t < 32) {
+      const int lane = t;
+      long long mx = lane < G.Q ? __double_as_longlong(cl.map_shared_rank(&sm.xmx[xpar], lane)[0]) : 0;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) sm.xmall = __longlong_as_double(mx);
+    }
+    __syncthreads();
+    const double xmax = sm.xmall;
+    xpar ^= 1;
     sm.wgt[t] = real ? __frcp_rn((float)(fabs(x[j]) + D.wfloor * xmax + 1e-300)) : 0.0f;
     __syncthreads();
     double* v0 = Vi(0);
