@@ -60,7 +60,7 @@ FUSED_BYTES_PER_CELL = 160
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_pred_fused launch on one 8192-cell,
 # 64-direction slab run (ncu --set full; profiles/ncu_pred_fused_slab1.md), taken with the
 # kernel as it stands; a slab launch carries one such instance per run
-FUSED_DRAM_BYTES_SLAB_INSTANCE = 4.136704e6
+FUSED_DRAM_BYTES_SLAB_INSTANCE = 4.137216e6
 
 
 def job_throughput(updates_per_step, steps, t_ms, world, dist=None, device="cuda"):
