@@ -208,3 +208,30 @@ def test_mixed_precision_cold_checkerboard_and_energy(G):
         h.step(1)
         assert abs(h.energy() - e0) < 1e-8 * e0
     h.close()
+
+
+def test_64x48_one_step_all_preconditioners(G):
+    """A grid large enough for the multi-block Gram-Schmidt reductions and several
+    multigrid levels (64 x 48 cells, 20 pairs), one FP64 step of a warm checkerboard
+    slab against the oracle, with the per-cell preconditioners, the prediction's Schur
+    multigrid, and the correction's per-pair multigrid (Krylov rtol 1e-14, so that the
+    stopping test does not set the difference)."""
+    mu, eta, w = s8_pairs_2d()
+    nx, ny = 64, 48
+    i = np.arange(nx) // (nx // 4)
+    jj = np.arange(ny) // (ny // 4)
+    sig = np.where(((i[None, :] + jj[:, None]) % 2) == 0, 1.0, 100.0)
+    rng = np.random.default_rng(19)
+    T0 = 0.3 * (1.0 + 0.5 * rng.random(nx * ny))
+    P = o2.Problem2D(Nx=nx, Ny=ny, mu=mu, eta=eta, w=w, sig=sig, eps=1e-3, dt=0.5 / nx, kind="t3", bx0=0.2)
+    S1 = o2.run(P, o2.equilibrium_state(P, T0), 1)
+    for name, prec in (("block", G.PREC2D_BLOCK), ("multigrid", G.PREC2D_MULTIGRID),
+                       ("corr-mg", G.PREC2D_CORR_MG)):
+        h = _pair(G, P, T0, prec=prec, krylov_rtol=1e-14)
+        h.step(1)
+        eT, eE = _rel(h.T(), S1.T), _rel(h.E(), S1.E)
+        print("64x48 one step (%s): T %.3e E %.3e" % (name, eT, eE), h.stats())
+        # with the stopping test at 1e-14 the FP64 tolerance of the 1D path holds in 2D
+        # (measured: T 7.8e-14, E 3.1e-13)
+        assert eT < 1e-12 and eE < 1e-12
+        h.close()
