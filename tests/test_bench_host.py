@@ -46,3 +46,25 @@ def test_reference_arm_line_for_the_random_smooth_workload():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_roofline_blocks_carry_measured_traffic_and_label_models():
+    """The dominant kernel's roofline block: achieved = algorithmic bytes per launch /
+    average launch time; traffic = the ncu DRAM bytes where a capture of the current kernel
+    exists (the one-kernel solve per slab run times the runs; k_gmres in FP64 on the slab),
+    and every figure that comes from a byte model says so."""
+    from paper_1811_05579_gb300 import grte as G
+    runs, _ = bench.workload_instances("slab6")
+    r, name = bench.roofline_of({"pred_solve": (10.0, 10)}, runs, G.MIXED, 6689.5, "slab6")
+    assert name == "pred_solve" and r["bound"] == "hbm"
+    assert r["traffic"] == bench.FUSED_DRAM_BYTES_SLAB_INSTANCE * len(runs)
+    nx = sum(q.nx for q in runs)
+    nel = sum(q.nx * (q.n_dir // 2) for q in runs)
+    assert r["algorithmic_bytes_per_launch"] == 2 * 4 * nel + bench.FUSED_BYTES_PER_CELL * nx
+    assert abs(r["achieved"] - r["algorithmic_bytes_per_launch"] / 1e-3 / 1e9) < 1e-9 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 6689.5) < 1e-15
+    r, name = bench.roofline_of({"gmres": (10.0, 100), "pred_hom": (5.0, 100)}, runs, G.FP64, 6689.5, "slab6")
+    assert name == "gmres" and r["traffic"] == bench.GMRES_DRAM_BYTES_SLAB6_FP64
+    assert "byte model" in r["bytes_model"]
+    r, _ = bench.roofline_of({"gmres": (10.0, 100)}, runs, G.MIXED, 6689.5, "slab6")
+    assert r["traffic"] is None   # no capture of the mixed k_gmres since it changed
